@@ -1,0 +1,251 @@
+/*
+ * hydro.h - C ABI of the adaptive ML-predicate engine (B300, sm_103a).
+ *
+ * A query is a conjunction of UDF predicates  UDF_i(tuple) > threshold_i
+ * (Hydro, Sec. 1 Listing 1 and Sec. 4.1 Listing 2).  Tuples arrive in routing
+ * batches (Sec. 3.3 "Batch Evaluation"); every batch visits the predicates in
+ * an order chosen from statistics the engine collects while it runs (Sec. 3.2
+ * "Data Flow and Routing", Sec. 4.1 "Cost-Driven Routing Policy"): the rank
+ * cost / (1 - selectivity), lowest first.  Tuples that fail a predicate are
+ * dropped at once (Sec. 3.3 "Eager Materialization"), so later predicates run
+ * only on survivors.  The answer is the same for every order: bit j of a
+ * batch's result is 1 iff tuple j passes every predicate.
+ *
+ * Conventions
+ *  - Every call returns a hydro_status and never aborts.  On failure,
+ *    hydro_last_error() gives a message (thread-local, valid until the next
+ *    call on the same thread).
+ *  - Pointers named d_* are CUDA device pointers on the query's device; all
+ *    others are host pointers.  Host arrays passed in are copied before the
+ *    call returns (the caller keeps ownership); device arrays passed to
+ *    hydro_submit_batch are BORROWED until that batch has been polled OK.
+ *  - Device errors detected by kernels are latched in a per-query error word
+ *    and reported as HYDRO_EDEVICE by the next poll.
+ *  - A query is not thread-safe: one host thread at a time per query.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define HYDRO_API __attribute__((visibility("default")))
+#else
+#define HYDRO_API
+#endif
+
+#define HYDRO_MAX_PREDICATES 8
+#define HYDRO_MAX_LAYERS 16
+
+typedef struct hydro_query hydro_query;
+
+typedef enum hydro_status {
+    HYDRO_OK = 0,
+    HYDRO_EINVAL = 1,       /* an argument is out of range or NULL */
+    HYDRO_ENOMEM = 2,       /* a host or device allocation failed */
+    HYDRO_ECUDA = 3,        /* a CUDA runtime/driver call failed */
+    HYDRO_EAGAIN = 4,       /* not finished within the wait, or no free in-flight slot */
+    HYDRO_ETIMEOUT = 5,     /* a bounded internal wait ran out */
+    HYDRO_ESTATE = 6,       /* the call is not valid in the query's current state */
+    HYDRO_EDEVICE = 7,      /* a kernel reported an error through the error word */
+    HYDRO_ENOTFOUND = 8,    /* unknown or already-polled batch id */
+    HYDRO_EUNSUPPORTED = 9  /* valid request this build does not implement */
+} hydro_status;
+
+/* Tuple layouts. */
+enum {
+    HYDRO_TUPLE_F32 = 0,        /* row-major fp32 [n][dim] feature vectors */
+    HYDRO_TUPLE_U8_FRAME = 1    /* uint8 frames [n][channels][height][width] (CHW) */
+};
+
+/* Routing policies (Sec. 4.2 "System Variants"). */
+enum {
+    HYDRO_POLICY_RANK = 0,        /* cost/(1-s), lowest first: score-driven */
+    HYDRO_POLICY_STATIC = 1,      /* fixed order (declared, or hydro_set_static_order) */
+    HYDRO_POLICY_ALL = 2,         /* every predicate on every tuple, no short-circuit */
+    HYDRO_POLICY_COST = 3,        /* cost only, lowest first: cost-driven */
+    HYDRO_POLICY_SELECTIVITY = 4  /* selectivity only, lowest first: selectivity-driven */
+};
+
+/* Working precision of UDF inference. */
+enum {
+    HYDRO_PREC_FP32 = 0,   /* FP32 everywhere; FP32 scores within margin_fp32 of the
+                              threshold are re-evaluated in FP64 */
+    HYDRO_PREC_BF16 = 1,   /* BF16 operands, FP32 accumulation on the tensor cores;
+                              scores within margin_lowp are re-evaluated in FP32
+                              (and from there in FP64 as above) */
+    HYDRO_PREC_FP64 = 2    /* FP64 (only for hydro_udf_scores) */
+};
+
+/* Where the router's per-tuple cost comes from. */
+enum {
+    HYDRO_COST_MODEL = 0,    /* flops per tuple of the UDF (or cost_hint): deterministic */
+    HYDRO_COST_MEASURED = 1  /* device time per evaluated tuple, from CUDA events */
+};
+
+/* UDF kinds. */
+enum {
+    HYDRO_UDF_MLP = 0,   /* linear layers, ReLU between them, last layer has 1 output */
+    HYDRO_UDF_CNN = 1    /* conv3x3 (stride 1, zero pad 1) + bias + ReLU layers on the
+                            frame scaled by 1/255, global average pool, linear head */
+};
+
+typedef struct hydro_query_config {
+    int32_t tuple_kind;      /* HYDRO_TUPLE_* */
+    int32_t dim;             /* F32: features per tuple (row stride = dim floats) */
+    int32_t channels;        /* U8_FRAME: frame channels (3) */
+    int32_t height;          /* U8_FRAME: frame height (64) */
+    int32_t width;           /* U8_FRAME: frame width (64) */
+    int32_t max_batch;       /* largest n a submit may pass, 1..65536 */
+    int32_t policy;          /* HYDRO_POLICY_* */
+    int32_t precision;       /* HYDRO_PREC_FP32 or HYDRO_PREC_BF16 */
+    int32_t cost_source;     /* HYDRO_COST_* */
+    int32_t warmup_batches;  /* adaptive policies: the first batches evaluate every
+                                predicate on every tuple (Sec. 4.1 "Warmup Phase") */
+    int32_t stats_window;    /* W >= 1: router uses the last W visible batches */
+    int32_t route_lag;       /* 0 or 1: batch b is routed on batches <= b-1-lag */
+    int32_t max_in_flight;   /* submitted but not yet polled batches, 1..64 */
+    int32_t device;          /* CUDA device ordinal */
+    void *stream;            /* cudaStream_t the batches run on; NULL = library stream */
+} hydro_query_config;
+
+typedef struct hydro_udf_desc {
+    int32_t kind;                 /* HYDRO_UDF_* */
+    int32_t n_layers;             /* MLP: linear layers; CNN: conv layers (1..HYDRO_MAX_LAYERS) */
+    const int32_t *dims;          /* n_layers+1 widths.  MLP: dims[0] = dim, dims[n_layers] = 1.
+                                     CNN: channel chain, dims[0] = channels */
+    const float *const *weights;  /* per layer, fp32.  MLP: [dims[l+1]][dims[l]] row-major.
+                                     CNN: [dims[l+1]][dims[l]][3][3] */
+    const float *const *biases;   /* per layer, fp32 [dims[l+1]] */
+    const float *head_weight;     /* CNN: [dims[n_layers]] fp32; MLP: NULL */
+    double head_bias;             /* CNN: head bias; MLP: ignored */
+    int64_t cost_hint;            /* > 0 replaces the model cost (flops per tuple) */
+} hydro_udf_desc;
+
+/* Per-batch result detail. */
+typedef struct hydro_batch_info {
+    int64_t n;                                  /* tuples in the batch */
+    int64_t n_pass;                             /* tuples in the result */
+    int32_t n_predicates;
+    int32_t warmup;                             /* 1: every predicate saw every tuple */
+    int32_t order[HYDRO_MAX_PREDICATES];        /* predicate ids in evaluation order */
+    int64_t passed[HYDRO_MAX_PREDICATES];       /* of the tuples predicate i evaluated, how many passed */
+    int64_t recheck_fp32[HYDRO_MAX_PREDICATES]; /* re-evaluated in FP32 (low-precision band) */
+    int64_t recheck_fp64[HYDRO_MAX_PREDICATES]; /* re-evaluated in FP64 (FP32 band) */
+    double device_ms;                           /* GPU time from the batch's first to last kernel */
+} hydro_batch_info;
+
+/* Cumulative per-predicate statistics (Sec. 3.3 "Metadata for Data Routing"). */
+typedef struct hydro_pred_stats {
+    int64_t evaluated;       /* tuples the UDF ran on at working precision */
+    int64_t passed;
+    int64_t recheck_fp32;
+    int64_t recheck_fp64;
+    int64_t model_cost;      /* flops per tuple used by HYDRO_COST_MODEL */
+    double margin_lowp;      /* current margins */
+    double margin_fp32;
+} hydro_pred_stats;
+
+/* Calibration report of one predicate (hydro_calibrate). */
+typedef struct hydro_calib_info {
+    double max_err_fp32;     /* max |s_fp32 - s_fp64| over the calibration tuples */
+    double max_err_lowp;     /* max |s_bf16 - s_fp64| (BF16 queries), else 0 */
+    double margin_fp32;      /* margin set */
+    double margin_lowp;      /* margin set (raised if the error needed it) */
+} hydro_calib_info;
+
+/* One kernel class in a profile (hydro_profile_read). */
+typedef struct hydro_kernel_profile {
+    char name[48];           /* kernel class, e.g. "conv3x3_bf16_tc" */
+    int64_t launches;        /* launches recorded */
+    double total_ms;         /* sum of per-launch device durations (CUDA events) */
+    double flops;            /* algorithmic flops of those launches (2 x MACs) */
+    double bytes;            /* algorithmic HBM bytes: activations in + out, weights once */
+} hydro_kernel_profile;
+
+/* Fill *cfg with defaults: F32 tuples, RANK policy, FP32, MODEL cost, one
+ * warmup batch, window 8, lag 1, 4 batches in flight, device 0, NULL stream.
+ * dim/channels/height/width/max_batch are left 0 and must be set. */
+HYDRO_API void hydro_default_config(hydro_query_config *cfg);
+
+/* Create a query on cfg->device.  *out receives an opaque handle owned by
+ * the library (free with hydro_destroy_query).  No device memory is taken
+ * until the first submit or calibrate. */
+HYDRO_API hydro_status hydro_create_query(const hydro_query_config *cfg, hydro_query **out);
+
+/* Add predicate  UDF(tuple) > threshold  (strict).  The UDF's weights are
+ * copied.  Only valid before the first submit/calibrate (else HYDRO_ESTATE).
+ * *out_pred_id receives the predicate id (0, 1, ... in call order), which is
+ * also its position in the declared order.  Default margins: margin_lowp =
+ * 0.02, margin_fp32 = 1e-5 * max(1, |threshold|). */
+HYDRO_API hydro_status hydro_add_predicate(hydro_query *q, const hydro_udf_desc *udf, double threshold,
+                                 int32_t *out_pred_id);
+
+/* Set the recheck margins of predicate pred (absolute score units, >= 0).
+ * A score s at working precision decides the test only if |s - t| > margin;
+ * otherwise the tuple is re-evaluated at the next precision (BF16 -> FP32 ->
+ * FP64).  Valid before the first submit. */
+HYDRO_API hydro_status hydro_set_margins(hydro_query *q, int32_t pred, double margin_lowp, double margin_fp32);
+
+/* Order for HYDRO_POLICY_STATIC: a permutation of 0..P-1 (n must equal P). */
+HYDRO_API hydro_status hydro_set_static_order(hydro_query *q, const int32_t *order, int32_t n);
+
+/* Calibrate the margins on n device tuples: runs every UDF in FP64, FP32 and
+ * (BF16 queries) BF16 on the GPU and sets margin_fp32 = 16 * max FP32 error
+ * (at least 1e-9 * max |score|), and raises margin_lowp to 4 * max BF16 error
+ * if that is larger.  info[P] (nullable) receives the report.  Valid before
+ * the first submit; synchronous. */
+HYDRO_API hydro_status hydro_calibrate(hydro_query *q, const void *d_tuples, int64_t n, hydro_calib_info *info);
+
+/* Scores of predicate pred's UDF on n device tuples at precision prec
+ * (HYDRO_PREC_FP64/FP32/BF16) into d_scores (device, n doubles).
+ * Synchronous; for tests, calibration and error reports. */
+HYDRO_API hydro_status hydro_udf_scores(hydro_query *q, int32_t pred, int32_t prec, const void *d_tuples,
+                              int64_t n, double *d_scores);
+
+/* Submit a batch of n tuples (0 <= n <= max_batch).  d_tuples: device, layout
+ * of cfg->tuple_kind; d_ids: device int64 tuple ids or NULL.  Stream-ordered
+ * and asynchronous; it may wait for the batch submitted route_lag+1 earlier
+ * to be routed (bounded).  *out_batch_id receives 0, 1, 2, ... */
+HYDRO_API hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int64_t *d_ids, int64_t n,
+                                int64_t *out_batch_id);
+
+/* Result of batch batch_id.  pass_bitmap: host, ceil(n/32) words, bit j of
+ * word j/32 (LSB first) = tuple j passed every predicate.  eval_counts: host
+ * [P], tuples each predicate evaluated at working precision (nullable).
+ * info nullable.  wait_ms: 0 = do not wait, < 0 = wait without limit, else
+ * wait up to wait_ms.  HYDRO_EAGAIN if not finished in time. */
+HYDRO_API hydro_status hydro_poll_result(hydro_query *q, int64_t batch_id, uint32_t *pass_bitmap,
+                               int64_t *eval_counts, hydro_batch_info *info, int32_t wait_ms);
+
+/* Cumulative statistics of the first n predicates into out[n] (host). */
+HYDRO_API hydro_status hydro_get_stats(hydro_query *q, hydro_pred_stats *out, int32_t n);
+
+/* Start (enable = 1, clearing earlier records) or stop (enable = 0)
+ * per-launch timing of the UDF layer kernels: each recorded launch is
+ * bracketed by CUDA events on the query's stream.  Also resets the launch
+ * counter read by hydro_profile_read. */
+HYDRO_API hydro_status hydro_profile(hydro_query *q, int32_t enable);
+
+/* Per kernel class totals since the last hydro_profile(q, 1), for batches
+ * polled since then.  out[max] receives up to max classes, *n_out how many;
+ * *total_launches (nullable) every kernel this query launched since then.
+ * Synchronises the query's stream. */
+HYDRO_API hydro_status hydro_profile_read(hydro_query *q, hydro_kernel_profile *out, int32_t max, int32_t *n_out,
+                                          int64_t *total_launches);
+
+/* Wait for outstanding work (bounded), free every resource of q. */
+HYDRO_API hydro_status hydro_destroy_query(hydro_query *q);
+
+/* Message of the last failed call on this thread ("" if none). */
+HYDRO_API const char *hydro_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYDRO_H */

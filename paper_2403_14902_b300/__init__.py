@@ -1,0 +1,297 @@
+"""Python binding of the adaptive ML-predicate engine (``include/hydro.h``).
+
+Argument marshalling only: every step of the batch path (UDF inference,
+threshold tests and rechecks, compaction, statistics, routing, the result
+bitmap) runs in the CUDA kernels of ``libhydro.so``.  PyTorch supplies device
+memory and streams.  Importing this module loads the library and fails loudly
+if it has not been built (``python -m paper_2403_14902_b300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhydro.so")
+
+MAX_PREDICATES = 8
+MAX_LAYERS = 16
+
+STATUS = {0: "HYDRO_OK", 1: "HYDRO_EINVAL", 2: "HYDRO_ENOMEM", 3: "HYDRO_ECUDA", 4: "HYDRO_EAGAIN",
+          5: "HYDRO_ETIMEOUT", 6: "HYDRO_ESTATE", 7: "HYDRO_EDEVICE", 8: "HYDRO_ENOTFOUND",
+          9: "HYDRO_EUNSUPPORTED"}
+OK, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEOUT, ESTATE, EDEVICE, ENOTFOUND, EUNSUPPORTED = range(10)
+
+TUPLE_F32, TUPLE_U8_FRAME = 0, 1
+POLICIES = {"rank": 0, "static": 1, "all": 2, "cost": 3, "selectivity": 4}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp64": 2}
+UDF_MLP, UDF_CNN = 0, 1
+
+EXPORTED = ["hydro_default_config", "hydro_create_query", "hydro_add_predicate", "hydro_set_margins",
+            "hydro_set_static_order", "hydro_calibrate", "hydro_udf_scores", "hydro_submit_batch",
+            "hydro_poll_result", "hydro_get_stats", "hydro_profile", "hydro_profile_read",
+            "hydro_destroy_query", "hydro_last_error"]
+
+
+class QueryConfig(ctypes.Structure):
+    _fields_ = [("tuple_kind", ctypes.c_int32), ("dim", ctypes.c_int32), ("channels", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("width", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("policy", ctypes.c_int32), ("precision", ctypes.c_int32), ("cost_source", ctypes.c_int32),
+                ("warmup_batches", ctypes.c_int32), ("stats_window", ctypes.c_int32),
+                ("route_lag", ctypes.c_int32), ("max_in_flight", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class UdfDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_layers", ctypes.c_int32),
+                ("dims", ctypes.POINTER(ctypes.c_int32)),
+                ("weights", ctypes.POINTER(ctypes.POINTER(ctypes.c_float))),
+                ("biases", ctypes.POINTER(ctypes.POINTER(ctypes.c_float))),
+                ("head_weight", ctypes.POINTER(ctypes.c_float)), ("head_bias", ctypes.c_double),
+                ("cost_hint", ctypes.c_int64)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_pass", ctypes.c_int64), ("n_predicates", ctypes.c_int32),
+                ("warmup", ctypes.c_int32), ("order", ctypes.c_int32 * MAX_PREDICATES),
+                ("passed", ctypes.c_int64 * MAX_PREDICATES), ("recheck_fp32", ctypes.c_int64 * MAX_PREDICATES),
+                ("recheck_fp64", ctypes.c_int64 * MAX_PREDICATES), ("device_ms", ctypes.c_double)]
+
+
+class PredStats(ctypes.Structure):
+    _fields_ = [("evaluated", ctypes.c_int64), ("passed", ctypes.c_int64), ("recheck_fp32", ctypes.c_int64),
+                ("recheck_fp64", ctypes.c_int64), ("model_cost", ctypes.c_int64),
+                ("margin_lowp", ctypes.c_double), ("margin_fp32", ctypes.c_double)]
+
+
+class CalibInfo(ctypes.Structure):
+    _fields_ = [("max_err_fp32", ctypes.c_double), ("max_err_lowp", ctypes.c_double),
+                ("margin_fp32", ctypes.c_double), ("margin_lowp", ctypes.c_double)]
+
+
+class KernelProfile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load ``libhydro.so`` (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run python -m paper_2403_14902_b300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.hydro_default_config.argtypes = [P(QueryConfig)]
+    L.hydro_default_config.restype = None
+    L.hydro_create_query.argtypes = [P(QueryConfig), P(vp)]
+    L.hydro_add_predicate.argtypes = [vp, P(UdfDesc), f64, P(i32)]
+    L.hydro_set_margins.argtypes = [vp, i32, f64, f64]
+    L.hydro_set_static_order.argtypes = [vp, P(i32), i32]
+    L.hydro_calibrate.argtypes = [vp, vp, i64, P(CalibInfo)]
+    L.hydro_udf_scores.argtypes = [vp, i32, i32, vp, i64, vp]
+    L.hydro_submit_batch.argtypes = [vp, vp, vp, i64, P(i64)]
+    L.hydro_poll_result.argtypes = [vp, i64, P(ctypes.c_uint32), P(i64), P(BatchInfo), i32]
+    L.hydro_get_stats.argtypes = [vp, P(PredStats), i32]
+    L.hydro_profile.argtypes = [vp, i32]
+    L.hydro_profile_read.argtypes = [vp, P(KernelProfile), i32, P(i32), P(i64)]
+    L.hydro_destroy_query.argtypes = [vp]
+    L.hydro_last_error.argtypes = []
+    L.hydro_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED[1:-1]:
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class HydroError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().hydro_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise HydroError(rc, where)
+
+
+def _ptr(t) -> int:
+    """Device (or host) address of a torch tensor / numpy array, or 0."""
+    if t is None:
+        return 0
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+class Query:
+    """One query: a conjunction of UDF predicates over a tuple stream.
+
+    ``kind`` is ``"vec"`` (fp32 rows of ``dim`` features) or ``"frame"``
+    (uint8 ``frame = (C, H, W)``)."""
+
+    def __init__(self, kind: str, *, dim: int = 0, frame=(3, 64, 64), max_batch: int, policy: str = "rank",
+                 precision: str = "fp32", warmup: int = 1, window: int = 8, lag: int = 1,
+                 max_in_flight: int = 4, device: int = 0, stream=None):
+        L = load()
+        cfg = QueryConfig()
+        L.hydro_default_config(ctypes.byref(cfg))
+        cfg.tuple_kind = TUPLE_F32 if kind == "vec" else TUPLE_U8_FRAME
+        cfg.dim = dim
+        cfg.channels, cfg.height, cfg.width = frame
+        cfg.max_batch = max_batch
+        cfg.policy = POLICIES[policy]
+        cfg.precision = PRECISIONS[precision]
+        cfg.warmup_batches = warmup
+        cfg.stats_window = window
+        cfg.route_lag = lag
+        cfg.max_in_flight = max_in_flight
+        cfg.device = device
+        cfg.stream = stream.cuda_stream if stream is not None else None
+        self.kind = kind
+        self.cfg = cfg
+        self._h = ctypes.c_void_p()
+        _check(L.hydro_create_query(ctypes.byref(cfg), ctypes.byref(self._h)), "hydro_create_query")
+        self.n_pred = 0
+        self._n_of = {}
+
+    # -- predicates
+    def _add(self, kind, dims, Ws, bs, threshold, head_w=None, head_b=0.0, cost_hint=0):
+        FP = ctypes.POINTER(ctypes.c_float)
+        Ws = [np.ascontiguousarray(w, np.float32) for w in Ws]
+        bs = [np.ascontiguousarray(b, np.float32) for b in bs]
+        d = (ctypes.c_int32 * len(dims))(*dims)
+        wp = (FP * len(Ws))(*[w.ctypes.data_as(FP) for w in Ws])
+        bp = (FP * len(bs))(*[b.ctypes.data_as(FP) for b in bs])
+        desc = UdfDesc()
+        desc.kind = kind
+        desc.n_layers = len(Ws)
+        desc.dims = d
+        desc.weights = wp
+        desc.biases = bp
+        if head_w is not None:
+            head_w = np.ascontiguousarray(head_w, np.float32)
+            desc.head_weight = head_w.ctypes.data_as(FP)
+        desc.head_bias = float(head_b)
+        desc.cost_hint = int(cost_hint)
+        pid = ctypes.c_int32()
+        _check(load().hydro_add_predicate(self._h, ctypes.byref(desc), float(threshold), ctypes.byref(pid)),
+               "hydro_add_predicate")
+        self.n_pred += 1
+        return pid.value
+
+    def add_mlp(self, layers, threshold: float, cost_hint: int = 0) -> int:
+        """``layers``: [(W [out, in] fp32, b [out] fp32)], last layer 1 output."""
+        dims = [layers[0][0].shape[1]] + [W.shape[0] for W, _ in layers]
+        return self._add(UDF_MLP, dims, [W for W, _ in layers], [b for _, b in layers], threshold,
+                         cost_hint=cost_hint)
+
+    def add_cnn(self, udf, threshold: float, cost_hint: int = 0) -> int:
+        """``udf = (convs, (head_w, head_b))`` with convs [(W [Cout, Cin, 3, 3], b)]."""
+        convs, (hw, hb) = udf
+        dims = [convs[0][0].shape[1]] + [W.shape[0] for W, _ in convs]
+        return self._add(UDF_CNN, dims, [W for W, _ in convs], [b for _, b in convs], threshold, hw, hb,
+                         cost_hint)
+
+    def set_margins(self, pred: int, lowp: float, fp32: float):
+        _check(load().hydro_set_margins(self._h, pred, float(lowp), float(fp32)), "hydro_set_margins")
+
+    def set_static_order(self, order):
+        arr = (ctypes.c_int32 * len(order))(*order)
+        _check(load().hydro_set_static_order(self._h, arr, len(order)), "hydro_set_static_order")
+
+    def calibrate(self, tuples) -> list:
+        info = (CalibInfo * MAX_PREDICATES)()
+        _check(load().hydro_calibrate(self._h, _ptr(tuples), int(tuples.shape[0]), info), "hydro_calibrate")
+        return [dict(max_err_fp32=info[i].max_err_fp32, max_err_lowp=info[i].max_err_lowp,
+                     margin_fp32=info[i].margin_fp32, margin_lowp=info[i].margin_lowp) for i in range(self.n_pred)]
+
+    def udf_scores(self, pred: int, precision: str, tuples, out):
+        """Scores of one predicate's UDF on device tuples into ``out`` (device float64 [n])."""
+        _check(load().hydro_udf_scores(self._h, pred, PRECISIONS[precision], _ptr(tuples), int(tuples.shape[0]),
+                                       _ptr(out)), "hydro_udf_scores")
+        return out
+
+    # -- batches
+    def submit(self, tuples, ids=None, n: int | None = None) -> int:
+        n = int(tuples.shape[0]) if n is None else n
+        bid = ctypes.c_int64()
+        _check(load().hydro_submit_batch(self._h, _ptr(tuples), _ptr(ids), n, ctypes.byref(bid)),
+               "hydro_submit_batch")
+        self._n_of[bid.value] = n
+        return bid.value
+
+    def poll(self, batch_id: int, wait_ms: int = -1):
+        """(bitmap uint32 [ceil(n/32)], eval counts int64 [P], info dict) or
+        raises HydroError (HYDRO_EAGAIN if not done within wait_ms)."""
+        n = self._n_of.get(batch_id, 0)
+        bitmap = np.zeros(max(1, (n + 31) // 32), np.uint32)
+        counts = np.zeros(MAX_PREDICATES, np.int64)
+        info = BatchInfo()
+        _check(load().hydro_poll_result(self._h, batch_id,
+                                        bitmap.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                        counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                        ctypes.byref(info), int(wait_ms)), "hydro_poll_result")
+        self._n_of.pop(batch_id, None)
+        P = self.n_pred
+        d = dict(n=info.n, n_pass=info.n_pass, warmup=bool(info.warmup), order=list(info.order[:P]),
+                 passed=list(info.passed[:P]), recheck_fp32=list(info.recheck_fp32[:P]),
+                 recheck_fp64=list(info.recheck_fp64[:P]), device_ms=info.device_ms)
+        return bitmap[:(n + 31) // 32], counts[:P], d
+
+    def stats(self) -> list:
+        out = (PredStats * MAX_PREDICATES)()
+        _check(load().hydro_get_stats(self._h, out, self.n_pred), "hydro_get_stats")
+        return [{f: getattr(out[i], f) for f, _ in PredStats._fields_} for i in range(self.n_pred)]
+
+    def profile(self, enable: bool = True):
+        """Start (clearing) or stop per-launch timing of the UDF layer kernels."""
+        _check(load().hydro_profile(self._h, 1 if enable else 0), "hydro_profile")
+
+    def profile_read(self):
+        """({kernel class: dict(launches, total_ms, flops, bytes)}, total launches)."""
+        out = (KernelProfile * 32)()
+        n = ctypes.c_int32()
+        tot = ctypes.c_int64()
+        _check(load().hydro_profile_read(self._h, out, 32, ctypes.byref(n), ctypes.byref(tot)), "hydro_profile_read")
+        d = {}
+        for i in range(n.value):
+            d[out[i].name.decode()] = dict(launches=out[i].launches, total_ms=out[i].total_ms, flops=out[i].flops,
+                                           bytes=out[i].bytes)
+        return d, tot.value
+
+    def close(self):
+        if self._h:
+            h, self._h = self._h, ctypes.c_void_p()
+            _check(load().hydro_destroy_query(h), "hydro_destroy_query")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self._h:
+                load().hydro_destroy_query(self._h)
+        except Exception:
+            pass
+
+
+def bits_from_words(words: np.ndarray, n: int) -> np.ndarray:
+    """Unpack an LSB-first bitmap into n bools."""
+    w = np.asarray(words, np.uint32)
+    j = np.arange(n)
+    return ((w[j >> 5] >> (j & 31).astype(np.uint32)) & 1).astype(bool)
+
+
+

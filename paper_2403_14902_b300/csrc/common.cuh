@@ -1,0 +1,40 @@
+// Shared device-side definitions of the CUDA path (not part of the C ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hydro {
+
+// Bits of the per-query device error word (latched, reported by poll).
+enum : uint32_t {
+    ERR_BAND_OVERFLOW = 1u << 0,   // an FP64 recheck band exceeded its capacity
+    ERR_COUNT_RANGE = 1u << 1,     // a device count exceeded its buffer
+    ERR_TC_TIMEOUT = 1u << 2,      // a tensor-core pipeline wait ran out
+    ERR_TC_CONFIG = 1u << 3,       // a tensor-core kernel got an unsupported shape
+};
+
+constexpr int kMaxPred = 8;
+
+// Per batch and predicate statistics row (device, int64).
+struct StatRow {
+    long long evaluated;
+    long long passed;
+    long long recheck32;
+    long long recheck64;
+};
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_d(float v) { return (double)v; }
+__device__ __forceinline__ double to_d(double v) { return v; }
+
+template <typename T> __device__ __forceinline__ T from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+template <typename T> struct Acc { using type = float; };
+template <> struct Acc<double> { using type = double; };
+
+}  // namespace hydro

@@ -1,0 +1,1024 @@
+// Host runtime behind include/hydro.h: query state, device buffers, the
+// per-batch stage sequence (Eddy routing of a batch through its predicates,
+// Sec. 3.2), result slots and polling.
+//
+// One query drives one CUDA stream.  A batch's stages are enqueued in the
+// order the router picked; counts of surviving tuples stay on the device.
+// The router itself runs on a second stream: for batch b it waits for batch
+// b-1-lag to finish, computes the order on the device from the statistics
+// ring, and copies the P order bytes back; the host launches batch b's
+// stages once that small copy lands (Sec. 3.3 "Metadata for Data Routing":
+// statistics of completed batches decide the next routing).
+#include <algorithm>
+#include <cstdarg>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/hydro.h"
+#include "common.cuh"
+#include "internal.h"
+#include "tc_conv.h"
+
+using namespace hydro;
+
+namespace {
+
+thread_local std::string g_err;
+
+hydro_status fail(hydro_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CU(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? HYDRO_ENOMEM : HYDRO_ECUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                       \
+    } while (0)
+
+constexpr int kEvRing = 16;
+
+struct Pred {
+    int kind = 0;
+    int n_layers = 0;
+    std::vector<int> dims;
+    std::vector<std::vector<float>> W, b;
+    std::vector<float> head_w;
+    double head_b = 0.0;
+    double threshold = 0.0;
+    double margin_lowp = 0.02;
+    double margin_fp32 = -1.0;   // < 0: not set, default at finalize
+    long long cost = 1;
+    // device copies
+    std::vector<float *> dW, db;          // as given
+    std::vector<float *> dWt32;           // CNN layer l >= 1: [tap][ci][co] fp32
+    std::vector<__nv_bfloat16 *> dWt16;   // CNN layer l >= 1: [tap][ci][co] bf16
+    std::vector<void *> dWtc;             // CNN layer l >= 1: tensor-core layout
+    float *dHead = nullptr;
+    MlpDev mlp{};
+};
+
+struct Slot {
+    long long batch = -1;
+    int n = 0;
+    bool busy = false;
+    bool warmup = false;
+    int order[kMaxPred] = {};
+    cudaEvent_t start = nullptr, done = nullptr;
+    unsigned char *dres = nullptr;   // device result block
+    unsigned char *hres = nullptr;   // pinned host mirror
+};
+
+// Result block layout (device and pinned host).
+struct ResHdr {
+    long long n_pass;
+    unsigned int err;
+    unsigned int pad[13];
+};
+static_assert(sizeof(ResHdr) == 64, "header size");
+constexpr size_t kRowsOff = sizeof(ResHdr);
+constexpr size_t kBitmapOff = kRowsOff + sizeof(StatRow) * kMaxPred;
+
+// Profiling: one record per timed launch; its item count is resolved from
+// the batch's statistics row when the batch is polled.
+enum ProfSrc { SRC_MAIN = 0, SRC_R32 = 1, SRC_R64 = 2 };
+struct ProfCtx {
+    long long batch;
+    int pred;
+    int src;
+};
+struct ProfRec {
+    int cls;
+    int ev;               // events ev, ev+1 in the pool
+    long long batch;
+    int pred, src;
+    double fpi, bpi;      // flops / bytes per item
+    double fixed_bytes;   // per launch (weights)
+};
+const char *const kProfNames[] = {"conv3x3_bf16_tc", "conv3x3_bf16_simt", "conv3x3_f32_simt", "conv3x3_f64_simt",
+                                  "conv1_u8",        "pool_head",         "mlp_layer_f32",    "mlp_dot_f32",
+                                  "mlp_band_f32",    "mlp_band_f64"};
+enum { PC_CONV_TC = 0, PC_CONV_BF16, PC_CONV_F32, PC_CONV_F64, PC_CONV1, PC_POOL, PC_MLP, PC_DOT, PC_BAND32,
+       PC_BAND64, PC_N };
+
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<ProfRec> recs;
+    std::vector<std::vector<StatRow>> rows;   // per polled batch (index batch - base)
+    long long base = 0;
+};
+
+}  // namespace
+
+struct hydro_query {
+    hydro_query_config cfg{};
+    std::vector<Pred> preds;
+    std::vector<int> static_order;
+    bool finalized = false;
+    bool dead = false;
+    int sms = 148;
+    cudaStream_t st = nullptr, rst = nullptr;
+    bool own_stream = false;
+    std::vector<void *> allocs;   // device allocations to free
+    // scratch
+    int *alive[2] = {};
+    int *ints = nullptr;          // [0],[1]: alive counts; [2]: band1 count; [3]: band2 count
+    unsigned char *pass = nullptr, *acc = nullptr;
+    float *score32 = nullptr;
+    int *band1_m = nullptr, *band1_t = nullptr, *band2_m = nullptr, *band2_t = nullptr;
+    int cap1 = 0, cap2 = 0;       // band capacities (entries / frames)
+    float *rscore32 = nullptr;
+    double *rscore64 = nullptr;
+    void *act[2] = {};            // working precision activations
+    void *ract32[2] = {};         // CNN FP32 recheck activations
+    void *ract64[2] = {};         // CNN FP64 recheck activations
+    StatRow *ring = nullptr, *warm = nullptr;
+    int ring_len = 0;
+    int *d_order = nullptr;       // [max_in_flight][8]
+    int *h_order = nullptr;       // pinned mirror
+    unsigned int *d_err = nullptr;
+    cudaEvent_t ev_done[kEvRing] = {};
+    cudaEvent_t ev_route = nullptr;
+    std::vector<Slot> slots;
+    size_t res_bytes = 0;
+    long long next_batch = 0;
+    unsigned int latched_err = 0;
+    // cumulative statistics (updated at poll)
+    long long tot[kMaxPred][4] = {};
+    // tensor-core conv
+    TcConvPlan tc{};
+    // profiling and launch count
+    Prof prof;
+    long long launches = 0;
+};
+
+namespace {
+
+int tuple_bytes(const hydro_query_config &c) {
+    return c.tuple_kind == HYDRO_TUPLE_F32 ? c.dim * 4 : c.channels * c.height * c.width;
+}
+
+template <typename T>
+hydro_status dalloc(hydro_query *q, T **p, size_t bytes) {
+    void *v = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HYDRO_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    q->allocs.push_back(v);
+    *p = (T *)v;
+    return HYDRO_OK;
+}
+
+#define TRY(x)                         \
+    do {                               \
+        hydro_status s_ = (x);         \
+        if (s_ != HYDRO_OK) return s_; \
+    } while (0)
+
+template <typename T>
+hydro_status upload(hydro_query *q, T **dst, const T *src, size_t count) {
+    TRY(dalloc(q, dst, count * sizeof(T)));
+    CU(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+    return HYDRO_OK;
+}
+
+long long model_cost(const Pred &p, const hydro_query_config &c) {
+    long long f = 0;
+    if (p.kind == HYDRO_UDF_MLP) {
+        for (int l = 0; l < p.n_layers; ++l) f += 2LL * p.dims[l] * p.dims[l + 1];
+    } else {
+        const long long hw = (long long)c.height * c.width;
+        for (int l = 0; l < p.n_layers; ++l) f += 2LL * hw * 9 * p.dims[l] * p.dims[l + 1];
+        f += 2LL * p.dims[p.n_layers];
+    }
+    return f;
+}
+
+bool adaptive(int policy) {
+    return policy == HYDRO_POLICY_RANK || policy == HYDRO_POLICY_COST || policy == HYDRO_POLICY_SELECTIVITY;
+}
+
+int max_width(const hydro_query *q) {
+    int w = 1;
+    for (const Pred &p : q->preds)
+        for (int d : p.dims) w = std::max(w, d);
+    return w;
+}
+
+hydro_status finalize(hydro_query *q) {
+    if (q->finalized) return HYDRO_OK;
+    const hydro_query_config &c = q->cfg;
+    if (q->preds.empty()) return fail(HYDRO_ESTATE, "query has no predicates");
+    CU(cudaSetDevice(c.device));
+    CU(cudaDeviceGetAttribute(&q->sms, cudaDevAttrMultiProcessorCount, c.device));
+    if (c.stream) {
+        q->st = (cudaStream_t)c.stream;
+    } else {
+        CU(cudaStreamCreateWithFlags(&q->st, cudaStreamNonBlocking));
+        q->own_stream = true;
+    }
+    CU(cudaStreamCreateWithFlags(&q->rst, cudaStreamNonBlocking));
+    for (int i = 0; i < kEvRing; ++i) CU(cudaEventCreateWithFlags(&q->ev_done[i], cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&q->ev_route, cudaEventDisableTiming));
+
+    const int B = c.max_batch;
+    const bool cnn = c.tuple_kind == HYDRO_TUPLE_U8_FRAME;
+    const int wmax = max_width(q);
+    TRY(dalloc(q, &q->alive[0], sizeof(int) * B));
+    TRY(dalloc(q, &q->alive[1], sizeof(int) * B));
+    TRY(dalloc(q, &q->ints, sizeof(int) * 16));
+    TRY(dalloc(q, &q->pass, B));
+    TRY(dalloc(q, &q->acc, B));
+    TRY(dalloc(q, &q->score32, sizeof(float) * B));
+    q->cap1 = B;
+    q->cap2 = cnn ? std::min(B, 64) : B;
+    TRY(dalloc(q, &q->band1_m, sizeof(int) * q->cap1));
+    TRY(dalloc(q, &q->band1_t, sizeof(int) * q->cap1));
+    TRY(dalloc(q, &q->band2_m, sizeof(int) * q->cap2));
+    TRY(dalloc(q, &q->band2_t, sizeof(int) * q->cap2));
+    TRY(dalloc(q, &q->rscore32, sizeof(float) * q->cap1));
+    TRY(dalloc(q, &q->rscore64, sizeof(double) * std::max(q->cap1, q->cap2)));
+    if (cnn) {
+        const size_t px = (size_t)c.height * c.width * wmax;
+        const size_t esz = c.precision == HYDRO_PREC_BF16 ? 2 : 4;
+        for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->act[k], esz * px * B));
+        if (c.precision == HYDRO_PREC_BF16)
+            for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->ract32[k], 4 * px * q->cap1));
+        for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->ract64[k], 8 * px * q->cap2));
+    } else {
+        for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->act[k], sizeof(float) * (size_t)wmax * B));
+        CU(mlp_band_smem_setup(wmax));
+    }
+    q->ring_len = c.stats_window + c.route_lag + 4;
+    TRY(dalloc(q, &q->ring, sizeof(StatRow) * kMaxPred * q->ring_len));
+    CU(cudaMemset(q->ring, 0, sizeof(StatRow) * kMaxPred * q->ring_len));
+    const int nw = std::max(1, c.warmup_batches);
+    TRY(dalloc(q, &q->warm, sizeof(StatRow) * kMaxPred * nw));
+    CU(cudaMemset(q->warm, 0, sizeof(StatRow) * kMaxPred * nw));
+    TRY(dalloc(q, &q->d_order, sizeof(int) * kMaxPred * c.max_in_flight));
+    CU(cudaMallocHost(&q->h_order, sizeof(int) * kMaxPred * c.max_in_flight));
+    TRY(dalloc(q, &q->d_err, sizeof(unsigned int)));
+    CU(cudaMemset(q->d_err, 0, sizeof(unsigned int)));
+
+    // result slots
+    q->res_bytes = kBitmapOff + sizeof(unsigned int) * (size_t)((B + 31) / 32);
+    q->slots.resize(c.max_in_flight);
+    for (Slot &s : q->slots) {
+        TRY(dalloc(q, &s.dres, q->res_bytes));
+        CU(cudaMallocHost(&s.hres, q->res_bytes));
+        CU(cudaEventCreate(&s.start));
+        CU(cudaEventCreate(&s.done));
+    }
+
+    // weights
+    for (Pred &p : q->preds) {
+        p.dW.resize(p.n_layers);
+        p.db.resize(p.n_layers);
+        for (int l = 0; l < p.n_layers; ++l) {
+            TRY(upload(q, &p.dW[l], p.W[l].data(), p.W[l].size()));
+            TRY(upload(q, &p.db[l], p.b[l].data(), p.b[l].size()));
+        }
+        if (p.kind == HYDRO_UDF_MLP) {
+            p.mlp.n_layers = p.n_layers;
+            p.mlp.max_width = wmax;
+            for (int l = 0; l <= p.n_layers; ++l) p.mlp.dims[l] = p.dims[l];
+            for (int l = 0; l < p.n_layers; ++l) {
+                p.mlp.W[l] = p.dW[l];
+                p.mlp.b[l] = p.db[l];
+            }
+        } else {
+            TRY(upload(q, &p.dHead, p.head_w.data(), p.head_w.size()));
+            p.dWt32.assign(p.n_layers, nullptr);
+            p.dWt16.assign(p.n_layers, nullptr);
+            p.dWtc.assign(p.n_layers, nullptr);
+            for (int l = 1; l < p.n_layers; ++l) {
+                const int ci_n = p.dims[l], co_n = p.dims[l + 1];
+                std::vector<float> t32((size_t)9 * ci_n * co_n);
+                std::vector<__nv_bfloat16> t16(t32.size());
+                for (int co = 0; co < co_n; ++co)
+                    for (int ci = 0; ci < ci_n; ++ci)
+                        for (int tap = 0; tap < 9; ++tap) {
+                            const float v = p.W[l][((size_t)co * ci_n + ci) * 9 + tap];
+                            const size_t o = ((size_t)tap * ci_n + ci) * co_n + co;
+                            t32[o] = v;
+                            t16[o] = __float2bfloat16_rn(v);
+                        }
+                TRY(upload(q, &p.dWt32[l], t32.data(), t32.size()));
+                TRY(upload(q, &p.dWt16[l], t16.data(), t16.size()));
+                if (c.precision == HYDRO_PREC_BF16 && tc_conv_supported(ci_n, co_n, c.height, c.width)) {
+                    std::vector<__nv_bfloat16> tc;
+                    tc_conv_pack_weights(p.W[l].data(), ci_n, co_n, tc);
+                    __nv_bfloat16 *d = nullptr;
+                    TRY(upload(q, &d, tc.data(), tc.size()));
+                    p.dWtc[l] = d;
+                }
+            }
+        }
+        if (p.margin_fp32 < 0.0) p.margin_fp32 = 1e-5 * std::max(1.0, std::fabs(p.threshold));
+    }
+    if (cnn && c.precision == HYDRO_PREC_BF16) {
+        hydro_status s = tc_conv_init(&q->tc, c.device);
+        if (s != HYDRO_OK) return fail(s, "tensor-core conv init failed: %s", tc_conv_last_error());
+    }
+    q->finalized = true;
+    return HYDRO_OK;
+}
+
+// ---------------------------------------------------------------- profiling
+
+int prof_begin(hydro_query *q, const ProfCtx *pc, int cls, double fpi, double bpi, double fixed_bytes) {
+    if (!q->prof.on || !pc) return -1;
+    Prof &P = q->prof;
+    const int e = (int)P.recs.size() * 2;
+    while ((int)P.ev.size() < e + 2) {
+        cudaEvent_t x;
+        if (cudaEventCreate(&x) != cudaSuccess) return -1;
+        P.ev.push_back(x);
+    }
+    if (cudaEventRecord(P.ev[e], q->st) != cudaSuccess) return -1;
+    P.recs.push_back(ProfRec{cls, e, pc->batch, pc->pred, pc->src, fpi, bpi, fixed_bytes});
+    return e;
+}
+
+void prof_end(hydro_query *q, int e) {
+    if (e >= 0) cudaEventRecord(q->prof.ev[e + 1], q->st);
+}
+
+// ---------------------------------------------------------------- UDF runs
+
+// Run predicate p's UDF at precision prec on the *count tuples listed in
+// `list` (indices into `tuples`), leaving FP32 scores in score32 (FP32/BF16)
+// or FP64 scores in score64.  act: two activation buffers for that precision,
+// sized for max_rows rows/frames.
+hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, const int *list,
+                     const void *tuples, int max_rows, void *const act[2], float *score32, double *score64,
+                     const ProfCtx *pc = nullptr) {
+    const hydro_query_config &c = q->cfg;
+    cudaStream_t st = q->st;
+    if (p.kind == HYDRO_UDF_MLP) {
+        const float *X = (const float *)tuples;
+        if (prec == PREC_F64) {
+            const int e = prof_begin(q, pc, PC_BAND64, (double)p.cost, 8.0 * c.dim, 0);
+            launch_mlp_band_f64(count, list, X, c.dim, p.mlp, score64, q->sms, st);
+            prof_end(q, e);
+            q->launches++;
+            return HYDRO_OK;
+        }
+        // FP32 (the BF16 MLP path is not built; rejected at create)
+        if (p.n_layers == 1) {
+            const int e = prof_begin(q, pc, PC_DOT, 2.0 * p.dims[0], 4.0 * p.dims[0] + 4, 4.0 * p.dims[0]);
+            launch_mlp_dot_f32(count, list, X, c.dim, p.dW[0], p.b[0][0], p.dims[0], score32, max_rows, q->sms, st);
+            prof_end(q, e);
+            q->launches++;
+            return HYDRO_OK;
+        }
+        int e = prof_begin(q, pc, PC_MLP, 2.0 * p.dims[0] * p.dims[1], 4.0 * (p.dims[0] + p.dims[1]),
+                           4.0 * p.dims[0] * p.dims[1]);
+        launch_mlp_layer_f32(count, list, X, c.dim, p.dW[0], p.db[0], (float *)act[0], p.dims[0], p.dims[1], 1,
+                             max_rows, q->sms, st);
+        prof_end(q, e);
+        q->launches++;
+        int cur = 0;
+        for (int l = 1; l + 1 < p.n_layers; ++l) {
+            e = prof_begin(q, pc, PC_MLP, 2.0 * p.dims[l] * p.dims[l + 1], 4.0 * (p.dims[l] + p.dims[l + 1]),
+                           4.0 * p.dims[l] * p.dims[l + 1]);
+            launch_mlp_layer_f32(count, nullptr, (const float *)act[cur], p.dims[l], p.dW[l], p.db[l],
+                                 (float *)act[1 - cur], p.dims[l], p.dims[l + 1], 1, max_rows, q->sms, st);
+            prof_end(q, e);
+            q->launches++;
+            cur = 1 - cur;
+        }
+        const int L = p.n_layers - 1;
+        e = prof_begin(q, pc, PC_DOT, 2.0 * p.dims[L], 4.0 * p.dims[L] + 4, 4.0 * p.dims[L]);
+        launch_mlp_dot_f32(count, nullptr, (const float *)act[cur], p.dims[L], p.dW[L], p.b[L][0], p.dims[L],
+                           score32, max_rows, q->sms, st);
+        prof_end(q, e);
+        q->launches++;
+        return HYDRO_OK;
+    }
+    // CNN
+    const int H = c.height, Wd = c.width;
+    const double hw = (double)H * Wd;
+    const double esz = prec == PREC_F64 ? 8.0 : prec == PREC_F32 ? 4.0 : 2.0;
+    const unsigned char *frames = (const unsigned char *)tuples;
+    int e = prof_begin(q, pc, PC_CONV1, 2.0 * hw * 9 * p.dims[0] * p.dims[1], hw * (p.dims[0] + esz * p.dims[1]),
+                       4.0 * 9 * p.dims[0] * p.dims[1]);
+    launch_conv1(prec, count, list, frames, c.channels, H, Wd, p.dW[0], p.db[0], p.dims[1], act[0], max_rows,
+                 q->sms, st);
+    prof_end(q, e);
+    q->launches++;
+    int cur = 0;
+    for (int l = 1; l < p.n_layers; ++l) {
+        const double fpi = 2.0 * hw * 9 * p.dims[l] * p.dims[l + 1];
+        const double bpi = hw * esz * (p.dims[l] + p.dims[l + 1]);
+        const double wb = 9.0 * p.dims[l] * p.dims[l + 1] * (prec == PREC_BF16 ? 2.0 : 4.0);
+        if (prec == PREC_BF16 && p.dWtc[l]) {
+            e = prof_begin(q, pc, PC_CONV_TC, fpi, bpi, wb);
+            hydro_status rs = tc_conv_run(&q->tc, count, act[cur], p.dims[l], H, Wd, p.dWtc[l], p.db[l],
+                                          p.dims[l + 1], act[1 - cur], max_rows, q->sms, st);
+            prof_end(q, e);
+            if (rs != HYDRO_OK) return fail(rs, "tensor-core conv: %s", tc_conv_last_error());
+        } else {
+            const int cls = prec == PREC_BF16 ? PC_CONV_BF16 : prec == PREC_F32 ? PC_CONV_F32 : PC_CONV_F64;
+            e = prof_begin(q, pc, cls, fpi, bpi, wb);
+            const void *w = prec == PREC_BF16 ? (const void *)p.dWt16[l] : (const void *)p.dWt32[l];
+            launch_conv3x3_simt(prec, count, act[cur], p.dims[l], H, Wd, w, p.db[l], p.dims[l + 1], act[1 - cur],
+                                max_rows, q->sms, st);
+            prof_end(q, e);
+        }
+        q->launches++;
+        cur = 1 - cur;
+    }
+    void *score = prec == PREC_F64 ? (void *)score64 : (void *)score32;
+    const int CL = p.dims[p.n_layers];
+    e = prof_begin(q, pc, PC_POOL, 2.0 * hw * CL, hw * esz * CL, 4.0 * CL);
+    launch_pool_head(prec, count, act[cur], H * Wd, CL, p.dHead, p.head_b, score, max_rows, q->sms, st);
+    prof_end(q, e);
+    q->launches++;
+    return HYDRO_OK;
+}
+
+// One stage: evaluate predicate p on the alive list (in_list, in_count),
+// decide pass/fail exactly (working precision, then the recheck cascade) and
+// close the stage.
+hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *in_list, int *out_list,
+                       int *out_count, bool eval_all, const void *tuples, int n, long long batch, Slot &slot) {
+    const hydro_query_config &c = q->cfg;
+    const Pred &p = q->preds[pi];
+    const bool bf16 = c.precision == HYDRO_PREC_BF16;
+    const int wprec = bf16 ? PREC_BF16 : PREC_F32;
+    int *band1_count = q->ints + 2, *band2_count = q->ints + 3;
+    const ProfCtx pc_main{batch, pi, SRC_MAIN}, pc_r32{batch, pi, SRC_R32}, pc_r64{batch, pi, SRC_R64};
+    TRY(run_udf(q, p, wprec, in_count, in_list, tuples, std::max(n, 1), q->act, q->score32, nullptr, &pc_main));
+    // FP32 mode sends its band straight to FP64 (capacity cap2); BF16 mode
+    // sends it to FP32 (capacity cap1) and from there to FP64.
+    launch_classify_f32(in_count, in_list, q->score32, p.threshold, bf16 ? p.margin_lowp : p.margin_fp32, q->pass,
+                        q->band1_m, q->band1_t, band1_count, bf16 ? q->cap1 : q->cap2, q->d_err, q->st);
+    q->launches++;
+    const int *fp64_count = band1_count;
+    const int *fp64_m = q->band1_m, *fp64_t = q->band1_t;
+    if (bf16) {
+        if (p.kind == HYDRO_UDF_MLP) {
+            const int e = prof_begin(q, &pc_r32, PC_BAND32, (double)p.cost, 4.0 * c.dim, 0);
+            launch_mlp_band_f32(band1_count, q->band1_t, (const float *)tuples, c.dim, p.mlp, q->rscore32, q->sms,
+                                q->st);
+            prof_end(q, e);
+            q->launches++;
+        } else {
+            TRY(run_udf(q, p, PREC_F32, band1_count, q->band1_t, tuples, q->cap1, q->ract32, q->rscore32, nullptr,
+                        &pc_r32));
+        }
+        q->launches++;
+        launch_recheck_classify_f32(band1_count, q->band1_m, q->band1_t, q->rscore32, p.threshold, p.margin_fp32,
+                                    q->pass, q->band2_m, q->band2_t, band2_count, q->cap2, q->d_err, q->st);
+        fp64_count = band2_count;
+        fp64_m = q->band2_m;
+        fp64_t = q->band2_t;
+    }
+    if (p.kind == HYDRO_UDF_MLP) {
+        const int e = prof_begin(q, &pc_r64, PC_BAND64, (double)p.cost, 4.0 * c.dim, 0);
+        launch_mlp_band_f64(fp64_count, fp64_t, (const float *)tuples, c.dim, p.mlp, q->rscore64, q->sms, q->st);
+        prof_end(q, e);
+        q->launches++;
+    } else {
+        TRY(run_udf(q, p, PREC_F64, fp64_count, fp64_t, tuples, q->cap2, q->ract64, nullptr, q->rscore64, &pc_r64));
+    }
+    launch_recheck_classify_f64(fp64_count, fp64_m, fp64_t, q->rscore64, p.threshold, q->pass, q->d_err, q->st);
+    q->launches += 2;   // recheck classify + compact
+    StatRow *row = q->ring + (batch % q->ring_len) * kMaxPred + pi;
+    StatRow *rrow = (StatRow *)(slot.dres + kRowsOff) + pi;
+    StatRow *warm = nullptr;
+    if (adaptive(c.policy) && batch < c.warmup_batches) warm = q->warm + batch * kMaxPred + pi;
+    launch_compact(in_count, in_list, q->pass, out_list, out_count, eval_all ? q->acc : nullptr,
+                   bf16 ? band1_count : nullptr, fp64_count, row, rrow, warm, q->st);
+    return HYDRO_OK;
+}
+
+hydro_status wait_event(cudaEvent_t ev, long long wait_ms, bool *done) {
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) {
+            *done = true;
+            return HYDRO_OK;
+        }
+        if (e != cudaErrorNotReady) return fail(HYDRO_ECUDA, "event query: %s", cudaGetErrorString(e));
+        if (wait_ms == 0) break;
+        if (wait_ms > 0) {
+            auto el = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+            if (el.count() >= wait_ms) break;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    *done = false;
+    return HYDRO_OK;
+}
+
+hydro_status check_query(hydro_query *q) {
+    if (!q) return fail(HYDRO_EINVAL, "NULL query");
+    if (q->dead) return fail(HYDRO_ESTATE, "query is in a failed state");
+    return HYDRO_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+
+extern "C" {
+
+const char *hydro_last_error(void) { return g_err.c_str(); }
+
+void hydro_default_config(hydro_query_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->tuple_kind = HYDRO_TUPLE_F32;
+    cfg->policy = HYDRO_POLICY_RANK;
+    cfg->precision = HYDRO_PREC_FP32;
+    cfg->cost_source = HYDRO_COST_MODEL;
+    cfg->warmup_batches = 1;
+    cfg->stats_window = 8;
+    cfg->route_lag = 1;
+    cfg->max_in_flight = 4;
+    cfg->device = 0;
+    cfg->stream = nullptr;
+}
+
+hydro_status hydro_create_query(const hydro_query_config *cfg, hydro_query **out) {
+    g_err.clear();
+    if (!cfg || !out) return fail(HYDRO_EINVAL, "NULL argument");
+    *out = nullptr;
+    const hydro_query_config &c = *cfg;
+    if (c.tuple_kind == HYDRO_TUPLE_F32) {
+        if (c.dim < 1 || c.dim > (1 << 16)) return fail(HYDRO_EINVAL, "dim out of range");
+    } else if (c.tuple_kind == HYDRO_TUPLE_U8_FRAME) {
+        if (c.channels < 1 || c.channels > 8 || c.height < 1 || c.width < 1 || c.height * c.width > (1 << 16))
+            return fail(HYDRO_EINVAL, "frame shape out of range");
+    } else {
+        return fail(HYDRO_EINVAL, "unknown tuple_kind %d", c.tuple_kind);
+    }
+    if (c.max_batch < 1 || c.max_batch > 65536) return fail(HYDRO_EINVAL, "max_batch must be 1..65536");
+    if (c.policy < 0 || c.policy > 4) return fail(HYDRO_EINVAL, "unknown policy");
+    if (c.precision != HYDRO_PREC_FP32 && c.precision != HYDRO_PREC_BF16)
+        return fail(HYDRO_EINVAL, "precision must be FP32 or BF16");
+    if (c.precision == HYDRO_PREC_BF16 && c.tuple_kind == HYDRO_TUPLE_F32)
+        return fail(HYDRO_EUNSUPPORTED, "BF16 inference of MLP UDFs is not built; use FP32");
+    if (c.cost_source != HYDRO_COST_MODEL)
+        return fail(HYDRO_EUNSUPPORTED, "only HYDRO_COST_MODEL is built");
+    if (c.warmup_batches < 0 || c.warmup_batches > 64) return fail(HYDRO_EINVAL, "warmup_batches must be 0..64");
+    if (c.stats_window < 1 || c.stats_window > 1024) return fail(HYDRO_EINVAL, "stats_window must be 1..1024");
+    if (c.route_lag < 0 || c.route_lag > 1) return fail(HYDRO_EINVAL, "route_lag must be 0 or 1");
+    if (c.max_in_flight < 1 || c.max_in_flight > 64) return fail(HYDRO_EINVAL, "max_in_flight must be 1..64");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HYDRO_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    if (c.device < 0 || c.device >= ndev) return fail(HYDRO_EINVAL, "device %d out of range", c.device);
+    hydro_query *q = new (std::nothrow) hydro_query();
+    if (!q) return fail(HYDRO_ENOMEM, "host allocation failed");
+    q->cfg = c;
+    *out = q;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_add_predicate(hydro_query *q, const hydro_udf_desc *udf, double threshold, int32_t *out_pred_id) {
+    g_err.clear();
+    TRY(check_query(q));
+    if (!udf || !out_pred_id) return fail(HYDRO_EINVAL, "NULL argument");
+    if (q->finalized) return fail(HYDRO_ESTATE, "predicates must be added before the first submit");
+    if ((int)q->preds.size() >= HYDRO_MAX_PREDICATES) return fail(HYDRO_EINVAL, "at most %d predicates", HYDRO_MAX_PREDICATES);
+    if (!std::isfinite(threshold)) return fail(HYDRO_EINVAL, "threshold must be finite");
+    const hydro_query_config &c = q->cfg;
+    const int L = udf->n_layers;
+    if (L < 1 || L > HYDRO_MAX_LAYERS || !udf->dims || !udf->weights || !udf->biases)
+        return fail(HYDRO_EINVAL, "bad layer description");
+    Pred p;
+    p.kind = udf->kind;
+    p.n_layers = L;
+    p.dims.assign(udf->dims, udf->dims + L + 1);
+    for (int d : p.dims)
+        if (d < 1 || d > 8192) return fail(HYDRO_EINVAL, "layer width out of range");
+    if (p.kind == HYDRO_UDF_MLP) {
+        if (c.tuple_kind != HYDRO_TUPLE_F32) return fail(HYDRO_EINVAL, "MLP UDFs need F32 tuples");
+        if (p.dims[0] != c.dim || p.dims[L] != 1) return fail(HYDRO_EINVAL, "MLP dims must run from dim to 1");
+        for (int l = 0; l < L; ++l) {
+            if (!udf->weights[l] || !udf->biases[l]) return fail(HYDRO_EINVAL, "NULL weights");
+            p.W.emplace_back(udf->weights[l], udf->weights[l] + (size_t)p.dims[l] * p.dims[l + 1]);
+            p.b.emplace_back(udf->biases[l], udf->biases[l] + p.dims[l + 1]);
+        }
+    } else if (p.kind == HYDRO_UDF_CNN) {
+        if (c.tuple_kind != HYDRO_TUPLE_U8_FRAME) return fail(HYDRO_EINVAL, "CNN UDFs need frame tuples");
+        if (p.dims[0] != c.channels) return fail(HYDRO_EINVAL, "CNN dims[0] must equal channels");
+        if (!udf->head_weight) return fail(HYDRO_EINVAL, "CNN needs head_weight");
+        if (!(p.dims[1] == 16 || p.dims[1] == 32 || p.dims[1] == 64))
+            return fail(HYDRO_EUNSUPPORTED, "first conv layer must have 16, 32 or 64 channels");
+        if ((c.height * c.width) % 128 != 0) return fail(HYDRO_EUNSUPPORTED, "H*W must be a multiple of 128");
+        for (int l = 1; l < L; ++l)
+            if (p.dims[l] % 16 != 0 || p.dims[l + 1] % 64 != 0)
+                return fail(HYDRO_EUNSUPPORTED, "conv layers after the first need Cin %% 16 == 0, Cout %% 64 == 0");
+        if (p.dims[L] > 256) return fail(HYDRO_EUNSUPPORTED, "last conv layer wider than 256");
+        for (int l = 0; l < L; ++l) {
+            if (!udf->weights[l] || !udf->biases[l]) return fail(HYDRO_EINVAL, "NULL weights");
+            p.W.emplace_back(udf->weights[l], udf->weights[l] + (size_t)p.dims[l] * p.dims[l + 1] * 9);
+            p.b.emplace_back(udf->biases[l], udf->biases[l] + p.dims[l + 1]);
+        }
+        p.head_w.assign(udf->head_weight, udf->head_weight + p.dims[L]);
+        p.head_b = udf->head_bias;
+    } else {
+        return fail(HYDRO_EINVAL, "unknown UDF kind");
+    }
+    p.threshold = threshold;
+    p.cost = udf->cost_hint > 0 ? udf->cost_hint : model_cost(p, c);
+    *out_pred_id = (int32_t)q->preds.size();
+    q->preds.push_back(std::move(p));
+    return HYDRO_OK;
+}
+
+hydro_status hydro_set_margins(hydro_query *q, int32_t pred, double margin_lowp, double margin_fp32) {
+    g_err.clear();
+    TRY(check_query(q));
+    if (pred < 0 || pred >= (int)q->preds.size()) return fail(HYDRO_EINVAL, "unknown predicate");
+    if (q->next_batch > 0) return fail(HYDRO_ESTATE, "margins are fixed after the first submit");
+    if (!(margin_lowp >= 0.0) || !(margin_fp32 >= 0.0)) return fail(HYDRO_EINVAL, "margins must be >= 0");
+    q->preds[pred].margin_lowp = margin_lowp;
+    q->preds[pred].margin_fp32 = margin_fp32;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_set_static_order(hydro_query *q, const int32_t *order, int32_t n) {
+    g_err.clear();
+    TRY(check_query(q));
+    if (!order || n != (int)q->preds.size()) return fail(HYDRO_EINVAL, "order must list every predicate");
+    std::vector<int> seen(n, 0);
+    for (int k = 0; k < n; ++k) {
+        if (order[k] < 0 || order[k] >= n || seen[order[k]]) return fail(HYDRO_EINVAL, "not a permutation");
+        seen[order[k]] = 1;
+    }
+    q->static_order.assign(order, order + n);
+    return HYDRO_OK;
+}
+
+hydro_status hydro_udf_scores(hydro_query *q, int32_t pred, int32_t prec, const void *d_tuples, int64_t n,
+                              double *d_scores) {
+    g_err.clear();
+    TRY(check_query(q));
+    if (pred < 0 || pred >= (int)q->preds.size()) return fail(HYDRO_EINVAL, "unknown predicate");
+    if (n < 0 || (n > 0 && (!d_tuples || !d_scores))) return fail(HYDRO_EINVAL, "bad tuples/scores");
+    if (prec != HYDRO_PREC_FP32 && prec != HYDRO_PREC_FP64 && prec != HYDRO_PREC_BF16)
+        return fail(HYDRO_EINVAL, "unknown precision");
+    if (prec == HYDRO_PREC_BF16 && q->cfg.precision != HYDRO_PREC_BF16)
+        return fail(HYDRO_EINVAL, "BF16 scores need a BF16 query");
+    CU(cudaSetDevice(q->cfg.device));
+    TRY(finalize(q));
+    const Pred &p = q->preds[pred];
+    const int B = q->cfg.max_batch;
+    const bool cnn = p.kind == HYDRO_UDF_CNN;
+    int *list = q->alive[0], *count = q->ints + 0;
+    const int chunk = (prec == HYDRO_PREC_FP64 && cnn) ? q->cap2
+                      : (prec == HYDRO_PREC_FP32 && cnn && q->cfg.precision == HYDRO_PREC_BF16) ? q->cap1
+                                                                                              : B;
+    const size_t tb = (size_t)tuple_bytes(q->cfg);
+    for (int64_t s = 0; s < n; s += chunk) {
+        const int m = (int)std::min<int64_t>(chunk, n - s);
+        const void *base = (const unsigned char *)d_tuples + (size_t)s * tb;
+        launch_identity_list(list, count, 0, m, q->st);
+        if (prec == HYDRO_PREC_FP64) {
+            TRY(run_udf(q, p, PREC_F64, count, list, base, m, cnn ? q->ract64 : q->act, nullptr, d_scores + s));
+        } else {
+            void *const *act = q->act;
+            if (prec == HYDRO_PREC_FP32 && cnn && q->cfg.precision == HYDRO_PREC_BF16) act = q->ract32;
+            TRY(run_udf(q, p, prec == HYDRO_PREC_BF16 ? PREC_BF16 : PREC_F32, count, list, base, m, act,
+                        q->score32, nullptr));
+            launch_f32_to_f64(q->score32, d_scores + s, m, q->st);
+        }
+        CU(cudaGetLastError());
+    }
+    CU(cudaStreamSynchronize(q->st));
+    unsigned int err = 0;
+    CU(cudaMemcpy(&err, q->d_err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) return fail(HYDRO_EDEVICE, "device error word 0x%x", err);
+    return HYDRO_OK;
+}
+
+hydro_status hydro_calibrate(hydro_query *q, const void *d_tuples, int64_t n, hydro_calib_info *info) {
+    g_err.clear();
+    TRY(check_query(q));
+    if (n < 1 || !d_tuples) return fail(HYDRO_EINVAL, "need calibration tuples");
+    if (q->next_batch > 0) return fail(HYDRO_ESTATE, "calibrate before the first submit");
+    double *d = nullptr;
+    CU(cudaSetDevice(q->cfg.device));
+    CU(cudaMalloc(&d, sizeof(double) * n * 3));
+    std::vector<double> s64(n), s32(n), s16(n);
+    hydro_status rc = HYDRO_OK;
+    for (int i = 0; i < (int)q->preds.size() && rc == HYDRO_OK; ++i) {
+        rc = hydro_udf_scores(q, i, HYDRO_PREC_FP64, d_tuples, n, d);
+        if (rc == HYDRO_OK) rc = hydro_udf_scores(q, i, HYDRO_PREC_FP32, d_tuples, n, d + n);
+        const bool bf = q->cfg.precision == HYDRO_PREC_BF16;
+        if (rc == HYDRO_OK && bf) rc = hydro_udf_scores(q, i, HYDRO_PREC_BF16, d_tuples, n, d + 2 * n);
+        if (rc != HYDRO_OK) break;
+        if (cudaMemcpy(s64.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(s32.data(), d + n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            (bf && cudaMemcpy(s16.data(), d + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)) {
+            rc = fail(HYDRO_ECUDA, "copy of calibration scores failed");
+            break;
+        }
+        double e32 = 0, e16 = 0, smax = 0;
+        for (int64_t k = 0; k < n; ++k) {
+            e32 = std::max(e32, std::fabs(s32[k] - s64[k]));
+            if (bf) e16 = std::max(e16, std::fabs(s16[k] - s64[k]));
+            smax = std::max(smax, std::fabs(s64[k]));
+        }
+        Pred &p = q->preds[i];
+        p.margin_fp32 = std::max(16.0 * e32, 1e-9 * smax);
+        if (bf && p.margin_lowp < 4.0 * e16) p.margin_lowp = 4.0 * e16;
+        if (info) {
+            info[i].max_err_fp32 = e32;
+            info[i].max_err_lowp = e16;
+            info[i].margin_fp32 = p.margin_fp32;
+            info[i].margin_lowp = p.margin_lowp;
+        }
+    }
+    cudaFree(d);
+    return rc;
+}
+
+hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int64_t *d_ids, int64_t n,
+                                int64_t *out_batch_id) {
+    g_err.clear();
+    TRY(check_query(q));
+    (void)d_ids;
+    if (!out_batch_id) return fail(HYDRO_EINVAL, "NULL out_batch_id");
+    if (n < 0 || n > q->cfg.max_batch) return fail(HYDRO_EINVAL, "n=%lld outside 0..max_batch", (long long)n);
+    if (n > 0 && !d_tuples) return fail(HYDRO_EINVAL, "NULL tuples");
+    if (q->preds.empty()) return fail(HYDRO_ESTATE, "query has no predicates");
+    const hydro_query_config &c = q->cfg;
+    if (c.policy == HYDRO_POLICY_STATIC && !q->static_order.empty() && q->static_order.size() != q->preds.size())
+        return fail(HYDRO_ESTATE, "static order does not match the predicates");
+    CU(cudaSetDevice(c.device));
+    TRY(finalize(q));
+    Slot *slot = nullptr;
+    int slot_idx = 0;
+    for (size_t k = 0; k < q->slots.size(); ++k)
+        if (!q->slots[k].busy) {
+            slot = &q->slots[k];
+            slot_idx = (int)k;
+            break;
+        }
+    if (!slot) return fail(HYDRO_EAGAIN, "all %d in-flight slots are busy; poll first", c.max_in_flight);
+
+    const long long b = q->next_batch;
+    const int P = (int)q->preds.size();
+    const bool eval_all = c.policy == HYDRO_POLICY_ALL || (adaptive(c.policy) && b < c.warmup_batches);
+    int order[kMaxPred];
+    for (int i = 0; i < P; ++i) order[i] = i;
+    if (!eval_all && c.policy == HYDRO_POLICY_STATIC) {
+        if (!q->static_order.empty())
+            for (int i = 0; i < P; ++i) order[i] = q->static_order[i];
+    } else if (!eval_all) {
+        const long long last = b - 1 - c.route_lag;
+        if (last >= 0) {
+            const long long lo = std::max(0LL, last - c.stats_window + 1);
+            const int nwv = (int)std::min<long long>(c.warmup_batches, last + 1);
+            RouterCosts costs{};
+            for (int i = 0; i < P; ++i) costs.c[i] = q->preds[i].cost;
+            const int pol = c.policy == HYDRO_POLICY_RANK ? 0 : c.policy == HYDRO_POLICY_COST ? 1 : 2;
+            int *dord = q->d_order + slot_idx * kMaxPred;
+            int *hord = q->h_order + slot_idx * kMaxPred;
+            CU(cudaStreamWaitEvent(q->rst, q->ev_done[last % kEvRing], 0));
+            launch_router(q->ring, q->ring_len, q->warm, nwv, lo, last, P, pol, costs, dord, q->rst);
+            q->launches++;
+            CU(cudaGetLastError());
+            CU(cudaMemcpyAsync(hord, dord, sizeof(int) * P, cudaMemcpyDeviceToHost, q->rst));
+            CU(cudaEventRecord(q->ev_route, q->rst));
+            bool done = false;
+            TRY(wait_event(q->ev_route, 600000, &done));
+            if (!done) return fail(HYDRO_ETIMEOUT, "router of batch %lld did not finish", b);
+            for (int i = 0; i < P; ++i) order[i] = hord[i];
+            for (int i = 0; i < P; ++i)
+                if (order[i] < 0 || order[i] >= P) return fail(HYDRO_EDEVICE, "router produced a bad order");
+        }
+    }
+
+    slot->batch = b;
+    slot->n = (int)n;
+    slot->busy = true;
+    slot->warmup = eval_all && c.policy != HYDRO_POLICY_ALL;
+    std::memcpy(slot->order, order, sizeof order);
+    CU(cudaEventRecord(slot->start, q->st));
+    int *cnt = q->ints;
+    launch_init_alive(q->alive[0], cnt + 0, (int)n, eval_all ? q->acc : nullptr, q->st);
+    q->launches++;
+    int cur = 0;
+    for (int k = 0; k < P; ++k) {
+        hydro_status s = run_stage(q, order[k], cnt + cur, q->alive[cur], q->alive[1 - cur], cnt + 1 - cur, eval_all,
+                                   d_tuples, (int)n, b, *slot);
+        if (s != HYDRO_OK) {
+            slot->busy = false;
+            q->dead = true;
+            return s;
+        }
+        if (!eval_all) cur = 1 - cur;
+    }
+    if (eval_all) {
+        launch_acc_to_alive(q->acc, (int)n, q->alive[1 - cur], cnt + 1 - cur, q->st);
+        q->launches++;
+        cur = 1 - cur;
+    }
+    ResHdr *hdr = (ResHdr *)slot->dres;
+    launch_result(cnt + cur, q->alive[cur], (int)n, (unsigned int *)(slot->dres + kBitmapOff), &hdr->n_pass, q->st);
+    q->launches++;
+    CU(cudaMemcpyAsync(&hdr->err, q->d_err, sizeof(unsigned int), cudaMemcpyDeviceToDevice, q->st));
+    const size_t bytes = kBitmapOff + sizeof(unsigned int) * (size_t)((n + 31) / 32);
+    CU(cudaMemcpyAsync(slot->hres, slot->dres, bytes, cudaMemcpyDeviceToHost, q->st));
+    CU(cudaEventRecord(slot->done, q->st));
+    CU(cudaEventRecord(q->ev_done[b % kEvRing], q->st));
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) {
+        q->dead = true;
+        return fail(HYDRO_ECUDA, "kernel launch failed: %s", cudaGetErrorString(le));
+    }
+    q->next_batch = b + 1;
+    *out_batch_id = b;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_poll_result(hydro_query *q, int64_t batch_id, uint32_t *pass_bitmap, int64_t *eval_counts,
+                               hydro_batch_info *info, int32_t wait_ms) {
+    g_err.clear();
+    if (!q) return fail(HYDRO_EINVAL, "NULL query");
+    Slot *slot = nullptr;
+    for (Slot &s : q->slots)
+        if (s.busy && s.batch == batch_id) slot = &s;
+    if (!slot) return fail(HYDRO_ENOTFOUND, "batch %lld is not in flight", (long long)batch_id);
+    if (!pass_bitmap && slot->n > 0) return fail(HYDRO_EINVAL, "NULL pass_bitmap");
+    CU(cudaSetDevice(q->cfg.device));
+    bool done = false;
+    TRY(wait_event(slot->done, wait_ms, &done));
+    if (!done) return fail(HYDRO_EAGAIN, "batch %lld not finished", (long long)batch_id);
+    const ResHdr *hdr = (const ResHdr *)slot->hres;
+    const StatRow *rows = (const StatRow *)(slot->hres + kRowsOff);
+    const int P = (int)q->preds.size();
+    if (hdr->err) {
+        q->latched_err |= hdr->err;
+        slot->busy = false;
+        return fail(HYDRO_EDEVICE, "device error word 0x%x in batch %lld", hdr->err, (long long)batch_id);
+    }
+    if (slot->n > 0)
+        std::memcpy(pass_bitmap, slot->hres + kBitmapOff, sizeof(uint32_t) * (size_t)((slot->n + 31) / 32));
+    if (q->prof.on && batch_id >= q->prof.base) {
+        const size_t k = (size_t)(batch_id - q->prof.base);
+        if (q->prof.rows.size() <= k) q->prof.rows.resize(k + 1);
+        q->prof.rows[k].assign(rows, rows + P);
+    }
+    for (int i = 0; i < P; ++i) {
+        if (eval_counts) eval_counts[i] = rows[i].evaluated;
+        q->tot[i][0] += rows[i].evaluated;
+        q->tot[i][1] += rows[i].passed;
+        q->tot[i][2] += rows[i].recheck32;
+        q->tot[i][3] += rows[i].recheck64;
+    }
+    if (info) {
+        std::memset(info, 0, sizeof *info);
+        info->n = slot->n;
+        info->n_pass = hdr->n_pass;
+        info->n_predicates = P;
+        info->warmup = slot->warmup ? 1 : 0;
+        for (int i = 0; i < P; ++i) {
+            info->order[i] = slot->order[i];
+            info->passed[i] = rows[i].passed;
+            info->recheck_fp32[i] = rows[i].recheck32;
+            info->recheck_fp64[i] = rows[i].recheck64;
+        }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, slot->start, slot->done) == cudaSuccess) info->device_ms = ms;
+        else cudaGetLastError();
+    }
+    slot->busy = false;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_get_stats(hydro_query *q, hydro_pred_stats *out, int32_t n) {
+    g_err.clear();
+    if (!q || !out) return fail(HYDRO_EINVAL, "NULL argument");
+    if (n < 0 || n > (int)q->preds.size()) return fail(HYDRO_EINVAL, "n out of range");
+    for (int i = 0; i < n; ++i) {
+        out[i].evaluated = q->tot[i][0];
+        out[i].passed = q->tot[i][1];
+        out[i].recheck_fp32 = q->tot[i][2];
+        out[i].recheck_fp64 = q->tot[i][3];
+        out[i].model_cost = q->preds[i].cost;
+        out[i].margin_lowp = q->preds[i].margin_lowp;
+        out[i].margin_fp32 = q->preds[i].margin_fp32 >= 0 ? q->preds[i].margin_fp32
+                                                         : 1e-5 * std::max(1.0, std::fabs(q->preds[i].threshold));
+    }
+    return HYDRO_OK;
+}
+
+hydro_status hydro_profile(hydro_query *q, int32_t enable) {
+    g_err.clear();
+    TRY(check_query(q));
+    q->prof.on = enable != 0;
+    q->prof.recs.clear();
+    q->prof.rows.clear();
+    q->prof.base = q->next_batch;
+    q->launches = 0;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_profile_read(hydro_query *q, hydro_kernel_profile *out, int32_t max, int32_t *n_out,
+                                int64_t *total_launches) {
+    g_err.clear();
+    TRY(check_query(q));
+    if (!n_out || (max > 0 && !out)) return fail(HYDRO_EINVAL, "NULL argument");
+    if (q->finalized) CU(cudaStreamSynchronize(q->st));
+    double ms[PC_N] = {}, fl[PC_N] = {}, by[PC_N] = {};
+    long long nl[PC_N] = {};
+    for (const ProfRec &r : q->prof.recs) {
+        const long long k = r.batch - q->prof.base;
+        if (k < 0 || k >= (long long)q->prof.rows.size() || q->prof.rows[k].empty()) continue;   // not polled
+        const StatRow &row = q->prof.rows[k][r.pred];
+        const long long items = r.src == SRC_MAIN ? row.evaluated : r.src == SRC_R32 ? row.recheck32 : row.recheck64;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, q->prof.ev[r.ev], q->prof.ev[r.ev + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        ms[r.cls] += t;
+        fl[r.cls] += r.fpi * items;
+        by[r.cls] += r.bpi * items + (items > 0 ? r.fixed_bytes : 0.0);
+        nl[r.cls] += 1;
+    }
+    int n = 0;
+    for (int c = 0; c < PC_N; ++c) {
+        if (!nl[c]) continue;
+        if (n < max) {
+            std::memset(&out[n], 0, sizeof out[n]);
+            std::snprintf(out[n].name, sizeof out[n].name, "%s", kProfNames[c]);
+            out[n].launches = nl[c];
+            out[n].total_ms = ms[c];
+            out[n].flops = fl[c];
+            out[n].bytes = by[c];
+        }
+        ++n;
+    }
+    *n_out = n < max ? n : max;
+    if (total_launches) *total_launches = q->launches;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_destroy_query(hydro_query *q) {
+    g_err.clear();
+    if (!q) return fail(HYDRO_EINVAL, "NULL query");
+    hydro_status rc = HYDRO_OK;
+    if (q->finalized) {
+        cudaSetDevice(q->cfg.device);
+        // bounded wait for outstanding work
+        for (Slot &s : q->slots) {
+            if (!s.busy) continue;
+            bool done = false;
+            if (wait_event(s.done, 60000, &done) != HYDRO_OK || !done) rc = HYDRO_ETIMEOUT;
+        }
+        if (rc == HYDRO_OK) {
+            cudaStreamSynchronize(q->rst);
+            if (q->own_stream) cudaStreamSynchronize(q->st);
+        }
+        tc_conv_destroy(&q->tc);
+        for (cudaEvent_t e : q->prof.ev) cudaEventDestroy(e);
+        for (Slot &s : q->slots) {
+            if (s.hres) cudaFreeHost(s.hres);
+            if (s.start) cudaEventDestroy(s.start);
+            if (s.done) cudaEventDestroy(s.done);
+        }
+        if (q->h_order) cudaFreeHost(q->h_order);
+        for (void *p : q->allocs) cudaFree(p);
+        for (int i = 0; i < kEvRing; ++i)
+            if (q->ev_done[i]) cudaEventDestroy(q->ev_done[i]);
+        if (q->ev_route) cudaEventDestroy(q->ev_route);
+        if (q->rst) cudaStreamDestroy(q->rst);
+        if (q->own_stream && q->st) cudaStreamDestroy(q->st);
+        cudaGetLastError();
+    }
+    delete q;
+    if (rc != HYDRO_OK) return fail(rc, "outstanding batches did not finish before destroy");
+    return HYDRO_OK;
+}
+
+}  // extern "C"

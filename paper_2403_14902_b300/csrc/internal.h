@@ -1,0 +1,73 @@
+// Internal launch interface between the host runtime (hydro_api.cu) and the
+// kernel files.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hydro {
+
+struct StatRow;
+
+enum { PREC_F32 = 0, PREC_BF16 = 1, PREC_F64 = 2 };
+
+constexpr int kMaxLayers = 16;
+
+// Device view of an MLP UDF (fp32 weights as given: W[l] is [dims[l+1]][dims[l]]).
+struct MlpDev {
+    int n_layers;
+    int max_width;
+    int dims[kMaxLayers + 1];
+    const float *W[kMaxLayers];
+    const float *b[kMaxLayers];
+};
+
+struct RouterCosts {
+    long long c[8];
+};
+
+// k_route.cu
+void launch_init_alive(int *alive, int *count, int n, unsigned char *acc, cudaStream_t st);
+void launch_classify_f32(const int *count_in, const int *alive_in, const float *scores, double t, double margin,
+                         unsigned char *pass, int *band_m, int *band_tuple, int *band_count, int band_cap,
+                         unsigned int *err, cudaStream_t st);
+void launch_recheck_classify_f32(const int *band_count_in, const int *band_m_in, const int *band_tuple_in,
+                                 const float *scores_r, double t, double margin_next, unsigned char *pass,
+                                 int *next_m, int *next_tuple, int *next_count, int next_cap, unsigned int *err,
+                                 cudaStream_t st);
+void launch_recheck_classify_f64(const int *band_count_in, const int *band_m_in, const int *band_tuple_in,
+                                 const double *scores_r, double t, unsigned char *pass, unsigned int *err,
+                                 cudaStream_t st);
+void launch_compact(const int *count_in, const int *alive_in, const unsigned char *pass, int *alive_out,
+                    int *count_out, unsigned char *acc, const int *band32_count, const int *band64_count,
+                    StatRow *row, StatRow *rrow, StatRow *warm, cudaStream_t st);
+void launch_acc_to_alive(const unsigned char *acc, int n, int *alive_out, int *count_out, cudaStream_t st);
+void launch_result(const int *count, const int *alive, int n, unsigned int *bitmap, long long *n_pass,
+                   cudaStream_t st);
+void launch_router(const StatRow *ring, int ring_len, const StatRow *warm, int n_warm_visible, long long lo,
+                   long long last, int P, int policy, const RouterCosts &costs, int *order_out, cudaStream_t st);
+
+// k_simt.cu
+void launch_mlp_layer_f32(const int *count, const int *rows, const float *X, int ldx, const float *W,
+                          const float *b, float *Y, int K, int N, int relu, int max_rows, int sms,
+                          cudaStream_t st);
+void launch_mlp_dot_f32(const int *count, const int *rows, const float *X, int ldx, const float *w, float bias,
+                        int K, float *score, int max_rows, int sms, cudaStream_t st);
+void launch_mlp_band_f32(const int *band_count, const int *band_tuple, const float *X, int ldx,
+                         const MlpDev &mlp, float *score_out, int sms, cudaStream_t st);
+void launch_mlp_band_f64(const int *band_count, const int *band_tuple, const float *X, int ldx,
+                         const MlpDev &mlp, double *score_out, int sms, cudaStream_t st);
+cudaError_t mlp_band_smem_setup(int max_width);
+void launch_conv1(int prec, const int *count, const int *list, const unsigned char *frames, int C0, int H,
+                  int Wd, const float *W, const float *bias, int Cout, void *out, int max_frames, int sms,
+                  cudaStream_t st);
+void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,
+                         const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st);
+void launch_pool_head(int prec, const int *count, const void *act, int HW, int C, const float *hw, double hb,
+                      void *score, int max_frames, int sms, cudaStream_t st);
+
+// k_util.cu
+void launch_f32_to_f64(const float *src, double *dst, int n, cudaStream_t st);
+void launch_identity_list(int *list, int *count, int start, int n, cudaStream_t st);
+
+}  // namespace hydro

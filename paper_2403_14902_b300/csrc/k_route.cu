@@ -1,0 +1,287 @@
+// Routing-side kernels: alive lists, threshold test with recheck bands,
+// order-preserving compaction (eager dropping of failing tuples, Sec. 3.3),
+// per-batch statistics (Sec. 3.3 "Metadata for Data Routing"), the pass
+// bitmap, and the rank router (Sec. 4.1 "Cost-Driven Routing Policy").
+//
+// Alive lists hold tuple indices within the batch (int32, ascending).  Every
+// kernel reads its element count from device memory, so a batch's whole
+// stage sequence is enqueued without a host round trip.
+#include "common.cuh"
+#include "internal.h"
+
+namespace hydro {
+
+constexpr int kScanThreads = 1024;
+
+// Exclusive block scan of one int per thread (1024 threads); returns the
+// exclusive prefix and writes the block total to *total.
+__device__ __forceinline__ int block_scan_1024(int v, int *total) {
+    __shared__ int warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int excl = x - v + (warp ? warp_sums[warp - 1] : 0);
+    *total = warp_sums[31];
+    __syncthreads();
+    return excl;
+}
+
+__global__ void k_init_alive(int *alive, int *count, int n, unsigned char *acc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        alive[i] = i;
+        if (acc) acc[i] = 1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count = n;
+}
+
+// Threshold test of the working-precision scores of one stage.  Position m
+// (0 <= m < *count_in) holds tuple alive_in[m] and score scores[m].  A score
+// within `margin` of t goes to the recheck band (ordered); otherwise
+// pass[m] = score > t.
+template <typename S>
+__global__ void __launch_bounds__(kScanThreads)
+k_classify(const int *count_in, const int *alive_in, const S *scores, double t, double margin,
+           unsigned char *pass, int *band_m, int *band_tuple, int *band_count, int band_cap,
+           unsigned int *err) {
+    const int n = *count_in;
+    int base = 0;
+    for (int m0 = 0; m0 < n; m0 += kScanThreads) {
+        const int m = m0 + threadIdx.x;
+        int inband = 0;
+        if (m < n) {
+            const double s = (double)scores[m];
+            inband = fabs(s - t) <= margin;
+            pass[m] = (!inband && s > t) ? 1 : 0;
+        }
+        int total;
+        const int pos = base + block_scan_1024(inband, &total);
+        if (inband) {
+            if (pos < band_cap) {
+                band_m[pos] = m;
+                band_tuple[pos] = alive_in[m];
+            } else {
+                atomicOr(err, ERR_BAND_OVERFLOW);
+            }
+        }
+        base += total;
+    }
+    if (threadIdx.x == 0) *band_count = base < band_cap ? base : band_cap;
+}
+
+// Decide the band entries from their recheck scores.  If margin_next >= 0,
+// entries still within margin_next of t go on to the next band (next
+// precision); otherwise they are decided here.
+template <typename S>
+__global__ void __launch_bounds__(kScanThreads)
+k_recheck_classify(const int *band_count_in, const int *band_m_in, const int *band_tuple_in,
+                   const S *scores_r, double t, double margin_next, unsigned char *pass,
+                   int *next_m, int *next_tuple, int *next_count, int next_cap, unsigned int *err) {
+    const int n = *band_count_in;
+    int base = 0;
+    for (int j0 = 0; j0 < n; j0 += kScanThreads) {
+        const int j = j0 + threadIdx.x;
+        int fwd = 0;
+        if (j < n) {
+            const double s = (double)scores_r[j];
+            fwd = margin_next >= 0.0 && fabs(s - t) <= margin_next;
+            if (!fwd) pass[band_m_in[j]] = s > t ? 1 : 0;
+        }
+        int total;
+        const int pos = base + block_scan_1024(fwd, &total);
+        if (fwd) {
+            if (pos < next_cap) {
+                next_m[pos] = band_m_in[j];
+                next_tuple[pos] = band_tuple_in[j];
+            } else {
+                atomicOr(err, ERR_BAND_OVERFLOW);
+            }
+        }
+        base += total;
+    }
+    if (threadIdx.x == 0 && next_count) *next_count = base < next_cap ? base : next_cap;
+}
+
+// Close a stage: record statistics and either drop the failing tuples
+// (short-circuit) or AND the stage's verdict into the all-evaluate
+// accumulator.  row/rrow: this predicate's statistics in the ring and in the
+// batch's result block; warm: the warmup copy (nullable).
+__global__ void __launch_bounds__(kScanThreads)
+k_compact(const int *count_in, const int *alive_in, const unsigned char *pass, int *alive_out,
+          int *count_out, unsigned char *acc, const int *band32_count, const int *band64_count,
+          StatRow *row, StatRow *rrow, StatRow *warm) {
+    const int n = *count_in;
+    int base = 0;
+    for (int m0 = 0; m0 < n; m0 += kScanThreads) {
+        const int m = m0 + threadIdx.x;
+        const int p = (m < n) ? (int)pass[m] : 0;
+        int total;
+        const int pos = base + block_scan_1024(p, &total);
+        if (acc) {
+            if (m < n && !p) acc[alive_in[m]] = 0;
+        } else if (p) {
+            alive_out[pos] = alive_in[m];
+        }
+        base += total;
+    }
+    if (threadIdx.x == 0) {
+        if (!acc) *count_out = base;
+        StatRow r;
+        r.evaluated = n;
+        r.passed = base;
+        r.recheck32 = band32_count ? *band32_count : 0;
+        r.recheck64 = band64_count ? *band64_count : 0;
+        *row = r;
+        *rrow = r;
+        if (warm) *warm = r;
+    }
+}
+
+// All-evaluate close: the final alive list is the accumulator's 1 entries.
+__global__ void __launch_bounds__(kScanThreads)
+k_acc_to_alive(const unsigned char *acc, int n, int *alive_out, int *count_out) {
+    int base = 0;
+    for (int m0 = 0; m0 < n; m0 += kScanThreads) {
+        const int m = m0 + threadIdx.x;
+        const int p = (m < n) ? (int)acc[m] : 0;
+        int total;
+        const int pos = base + block_scan_1024(p, &total);
+        if (p) alive_out[pos] = m;
+        base += total;
+    }
+    if (threadIdx.x == 0) *count_out = base;
+}
+
+// Pass bitmap (LSB first) from the final alive list, plus n_pass.
+__global__ void __launch_bounds__(kScanThreads)
+k_result(const int *count, const int *alive, int n, unsigned int *bitmap, long long *n_pass) {
+    const int words = (n + 31) >> 5;
+    for (int w = threadIdx.x; w < words; w += blockDim.x) bitmap[w] = 0u;
+    __syncthreads();
+    const int c = *count;
+    for (int m = threadIdx.x; m < c; m += blockDim.x) {
+        const int j = alive[m];
+        atomicOr(&bitmap[j >> 5], 1u << (j & 31));
+    }
+    if (threadIdx.x == 0) *n_pass = c;
+}
+
+// Router: one warp, lane i scores predicate i and finds its position by
+// counting the predicates that go before it (exact integer comparisons; ties
+// to the lower id).  Statistics are the sums over visible batches
+// [lo, last] of the ring; a predicate with no evaluations there falls back to
+// the warmup batches' statistics.
+__global__ void k_router(const StatRow *ring, int ring_len, const StatRow *warm, int n_warm_visible,
+                         long long lo, long long last, int P, int policy, RouterCosts costs,
+                         int *order_out) {
+    const int i = threadIdx.x;
+    long long E = 0, Pp = 0;
+    if (i < P) {
+        for (long long b = lo; b <= last; ++b) {
+            const StatRow r = ring[(b % ring_len) * kMaxPred + i];
+            E += r.evaluated;
+            Pp += r.passed;
+        }
+        if (E == 0) {
+            for (int w = 0; w < n_warm_visible; ++w) {
+                E += warm[w * kMaxPred + i].evaluated;
+                Pp += warm[w * kMaxPred + i].passed;
+            }
+        }
+    }
+    int pos = 0;
+    for (int j = 0; j < P; ++j) {
+        const long long Ej = __shfl_sync(0xffffffffu, E, j);
+        const long long Pj = __shfl_sync(0xffffffffu, Pp, j);
+        if (i >= P || j == i) continue;
+        const unsigned long long ci = (unsigned long long)costs.c[i], cj = (unsigned long long)costs.c[j];
+        bool before;   // does j go before i?
+        if (policy == 0) {
+            // rank c/(1-s), s = (p+1)/(e+2): c(e+2)/(e-p+1)
+            const unsigned __int128 lhs = (unsigned __int128)cj * (unsigned long long)(Ej + 2) *
+                                          (unsigned long long)(E - Pp + 1);
+            const unsigned __int128 rhs = (unsigned __int128)ci * (unsigned long long)(E + 2) *
+                                          (unsigned long long)(Ej - Pj + 1);
+            before = lhs < rhs || (lhs == rhs && j < i);
+        } else if (policy == 1) {
+            before = cj < ci || (cj == ci && j < i);
+        } else {
+            // selectivity (p+1)/(e+2)
+            const unsigned __int128 lhs = (unsigned __int128)(unsigned long long)(Pj + 1) * (unsigned long long)(E + 2);
+            const unsigned __int128 rhs = (unsigned __int128)(unsigned long long)(Pp + 1) * (unsigned long long)(Ej + 2);
+            before = lhs < rhs || (lhs == rhs && j < i);
+        }
+        pos += before;
+    }
+    if (i < P) order_out[pos] = i;
+}
+
+// ------------------------------------------------------------ launchers
+
+void launch_init_alive(int *alive, int *count, int n, unsigned char *acc, cudaStream_t st) {
+    const int blocks = n > 0 ? (n + 255) / 256 : 1;
+    k_init_alive<<<blocks, 256, 0, st>>>(alive, count, n, acc);
+}
+
+void launch_classify_f32(const int *count_in, const int *alive_in, const float *scores, double t,
+                         double margin, unsigned char *pass, int *band_m, int *band_tuple,
+                         int *band_count, int band_cap, unsigned int *err, cudaStream_t st) {
+    k_classify<float><<<1, kScanThreads, 0, st>>>(count_in, alive_in, scores, t, margin, pass, band_m,
+                                                  band_tuple, band_count, band_cap, err);
+}
+
+void launch_recheck_classify_f32(const int *band_count_in, const int *band_m_in, const int *band_tuple_in,
+                                 const float *scores_r, double t, double margin_next,
+                                 unsigned char *pass, int *next_m, int *next_tuple, int *next_count,
+                                 int next_cap, unsigned int *err, cudaStream_t st) {
+    k_recheck_classify<float><<<1, kScanThreads, 0, st>>>(band_count_in, band_m_in, band_tuple_in,
+                                                          scores_r, t, margin_next, pass, next_m,
+                                                          next_tuple, next_count, next_cap, err);
+}
+
+void launch_recheck_classify_f64(const int *band_count_in, const int *band_m_in, const int *band_tuple_in,
+                                 const double *scores_r, double t, unsigned char *pass,
+                                 unsigned int *err, cudaStream_t st) {
+    k_recheck_classify<double><<<1, kScanThreads, 0, st>>>(band_count_in, band_m_in, band_tuple_in,
+                                                           scores_r, t, -1.0, pass, nullptr, nullptr,
+                                                           nullptr, 0, err);
+}
+
+void launch_compact(const int *count_in, const int *alive_in, const unsigned char *pass, int *alive_out,
+                    int *count_out, unsigned char *acc, const int *band32_count, const int *band64_count,
+                    StatRow *row, StatRow *rrow, StatRow *warm, cudaStream_t st) {
+    k_compact<<<1, kScanThreads, 0, st>>>(count_in, alive_in, pass, alive_out, count_out, acc,
+                                          band32_count, band64_count, row, rrow, warm);
+}
+
+void launch_acc_to_alive(const unsigned char *acc, int n, int *alive_out, int *count_out, cudaStream_t st) {
+    k_acc_to_alive<<<1, kScanThreads, 0, st>>>(acc, n, alive_out, count_out);
+}
+
+void launch_result(const int *count, const int *alive, int n, unsigned int *bitmap, long long *n_pass,
+                   cudaStream_t st) {
+    k_result<<<1, kScanThreads, 0, st>>>(count, alive, n, bitmap, n_pass);
+}
+
+void launch_router(const StatRow *ring, int ring_len, const StatRow *warm, int n_warm_visible,
+                   long long lo, long long last, int P, int policy, const RouterCosts &costs,
+                   int *order_out, cudaStream_t st) {
+    k_router<<<1, 32, 0, st>>>(ring, ring_len, warm, n_warm_visible, lo, last, P, policy, costs, order_out);
+}
+
+}  // namespace hydro

@@ -1,0 +1,389 @@
+// SIMT (CUDA-core) UDF kernels: FP32 inference (static FP32 evaluation and
+// the FP32 recheck band), FP64 inference (FP64 recheck band, calibration),
+// and a BF16-operand SIMT conv used as the tensor-core kernel's comparator.
+//
+// UDF definitions (Sec. 4.2 "Predicate Implementation" uses off-the-shelf
+// models; the workloads here use random-init MLP and CNN UDFs):
+//   MLP: h_{l+1} = W_l h_l + b_l, ReLU on hidden layers, 1 output = score.
+//   CNN: x/255 -> [conv3x3 pad 1 + bias + ReLU]* -> global average pool ->
+//        linear head = score.
+//
+// Every kernel takes its row/frame count from device memory and walks its
+// tiles with a grid-stride loop, so launches need no host knowledge of how
+// many tuples survived.
+#include "common.cuh"
+#include "internal.h"
+
+namespace hydro {
+
+// ---------------------------------------------------------------- MLP FP32
+
+// Y[m][n] = act(sum_k X[row(m)][k] * W[n][k] + b[n]) for m < *count, with
+// row(m) = rows[m] when rows != nullptr.  64x64 output tiles, 16-deep K
+// slices, 4x4 outputs per thread.
+__global__ void __launch_bounds__(256)
+k_mlp_layer_f32(const int *count, const int *rows, const float *X, int ldx, const float *W,
+                const float *b, float *Y, int K, int N, int relu) {
+    __shared__ float As[16][64 + 4];
+    __shared__ float Ws[16][64 + 4];
+    const int M = *count;
+    const int tiles_m = (M + 63) / 64, tiles_n = (N + 63) / 64;
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int lr = t >> 2, lk = (t & 3) * 4;   // loader: row / k offset
+    for (int tile = blockIdx.x; tile < tiles_m * tiles_n; tile += gridDim.x) {
+        const int m0 = (tile / tiles_n) * 64, n0 = (tile % tiles_n) * 64;
+        float acc[4][4] = {};
+        const int am = m0 + lr;
+        const float *arow = nullptr;
+        if (am < M) arow = X + (size_t)(rows ? rows[am] : am) * ldx;
+        const int wn = n0 + lr;
+        const float *wrow = wn < N ? W + (size_t)wn * K : nullptr;
+        for (int k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = k0 + lk + e;
+                As[lk + e][lr] = (arow && k < K) ? arow[k] : 0.f;
+                Ws[lk + e][lr] = (wrow && k < K) ? wrow[k] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) {
+                float a[4], w[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) w[j] = Ws[kk][tx * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int m = m0 + ty * 4 + i;
+            if (m >= M) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int n = n0 + tx * 4 + j;
+                if (n >= N) continue;
+                float v = acc[i][j] + b[n];
+                if (relu && v < 0.f) v = 0.f;
+                Y[(size_t)m * N + n] = v;
+            }
+        }
+    }
+}
+
+// Last MLP layer (one output): score[m] = b + sum_k X[row(m)][k] * w[k].
+// One warp per row; fixed lane-strided order and a butterfly reduction.
+__global__ void __launch_bounds__(256)
+k_mlp_dot_f32(const int *count, const int *rows, const float *X, int ldx, const float *w, float bias,
+              int K, float *score) {
+    const int M = *count;
+    const int lane = threadIdx.x & 31;
+    for (int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; m < M; m += (gridDim.x * blockDim.x) >> 5) {
+        const float *x = X + (size_t)(rows ? rows[m] : m) * ldx;
+        float s = 0.f;
+        for (int k = lane; k < K; k += 32) s = fmaf(x[k], w[k], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) score[m] = s + bias;
+    }
+}
+
+// Whole MLP on a band list, one block per tuple, activations in shared
+// memory, in precision T (float: FP32 recheck; double: FP64 recheck).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_mlp_band(const int *band_count, const int *band_tuple, const float *X, int ldx, MlpDev mlp, T *score_out) {
+    extern __shared__ unsigned char smem_raw[];
+    T *h = reinterpret_cast<T *>(smem_raw);
+    T *g = h + mlp.max_width;
+    const int n = *band_count;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const float *x = X + (size_t)band_tuple[j] * ldx;
+        for (int k = threadIdx.x; k < mlp.dims[0]; k += blockDim.x) h[k] = (T)x[k];
+        __syncthreads();
+        T *cur = h, *nxt = g;
+        for (int l = 0; l < mlp.n_layers; ++l) {
+            const int fi = mlp.dims[l], fo = mlp.dims[l + 1];
+            const float *W = mlp.W[l];
+            const float *bb = mlp.b[l];
+            const bool last = l + 1 == mlp.n_layers;
+            for (int o = warp; o < fo; o += nwarps) {
+                const float *wr = W + (size_t)o * fi;
+                T s = 0;
+                for (int k = lane; k < fi; k += 32) s += (T)wr[k] * cur[k];
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+                if (lane == 0) {
+                    s += (T)bb[o];
+                    nxt[o] = (!last && s < (T)0) ? (T)0 : s;
+                }
+            }
+            __syncthreads();
+            T *tmp = cur; cur = nxt; nxt = tmp;
+        }
+        if (threadIdx.x == 0) score_out[j] = cur[0];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- CNN
+
+// First conv layer straight from the uint8 CHW frames (gathered through
+// `list`): out[m][p][co] = relu(b[co] + sum_{ci,ky,kx} W * x/255), NHWC.
+// One thread per output pixel computes all COUT channels.
+template <typename T, typename Tout, int COUT>
+__global__ void __launch_bounds__(256)
+k_conv1_u8(const int *count, const int *list, const unsigned char *frames, int C0, int H, int Wd,
+           const float *W, const float *bias, Tout *out) {
+    __shared__ T Ws[8 * 9][COUT];   // [ci*9 + ky*3 + kx][co], C0 <= 8
+    __shared__ T Bs[COUT];
+    for (int i = threadIdx.x; i < C0 * 9 * COUT; i += blockDim.x) {
+        const int co = i % COUT, r = i / COUT;   // r = ci*9 + tap
+        Ws[r][co] = (T)W[(size_t)co * C0 * 9 + r];
+    }
+    for (int i = threadIdx.x; i < COUT; i += blockDim.x) Bs[i] = (T)bias[i];
+    __syncthreads();
+    const int M = *count;
+    const int HW = H * Wd;
+    const int blocks_per_frame = (HW + 255) / 256;
+    const T inv255 = (T)1 / (T)255;
+    for (int w = blockIdx.x; w < M * blocks_per_frame; w += gridDim.x) {
+        const int m = w / blocks_per_frame;
+        const int p = (w % blocks_per_frame) * 256 + threadIdx.x;
+        if (p >= HW) continue;
+        const int y = p / Wd, x = p % Wd;
+        const unsigned char *f = frames + (size_t)list[m] * C0 * HW;
+        T acc[COUT];
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) acc[co] = Bs[co];
+        for (int ci = 0; ci < C0; ++ci)
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) {
+                    const int yy = y + ky - 1, xx = x + kx - 1;
+                    if (yy < 0 || yy >= H || xx < 0 || xx >= Wd) continue;
+                    const T v = (T)f[(size_t)ci * HW + yy * Wd + xx] * inv255;
+                    const T *wr = Ws[ci * 9 + ky * 3 + kx];
+#pragma unroll
+                    for (int co = 0; co < COUT; ++co) acc[co] += wr[co] * v;
+                }
+        Tout *o = out + ((size_t)m * HW + p) * COUT;
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) {
+            T v = acc[co] < (T)0 ? (T)0 : acc[co];
+            o[co] = (Tout)v;
+        }
+    }
+}
+
+template <typename T> __device__ __forceinline__ T ld_as(const float *p) { return (T)(*p); }
+template <typename T> __device__ __forceinline__ T ld_as(const double *p) { return (T)(*p); }
+template <typename T> __device__ __forceinline__ T ld_as(const __nv_bfloat16 *p) { return (T)__bfloat162float(*p); }
+template <typename Tout, typename T> __device__ __forceinline__ Tout st_as(T v) { return (Tout)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 st_as<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+
+// conv3x3 (stride 1, zero pad 1) + bias + ReLU on NHWC activations of the
+// first *count frames, as an implicit GEMM on CUDA cores:
+//   out[m][p][co] = relu(b[co] + sum_{tap, ci} in[m][p + shift(tap)][ci] * Wt[tap][ci][co])
+// Tiles of 128 pixels x 64 output channels; K walks (tap, 16 input channels).
+// Requires Cin % 16 == 0, Cout % 64 == 0, H*W % 128 == 0.
+template <typename Tin, typename Tw, typename T, typename Tout>
+__global__ void __launch_bounds__(256)
+k_conv3x3_simt(const int *count, const Tin *in, int Cin, int H, int Wd, const Tw *Wt, const float *bias,
+               int Cout, Tout *out) {
+    __shared__ T As[16][128 + 4];
+    __shared__ T Bs[16][64 + 4];
+    const int M = *count;
+    const int HW = H * Wd;
+    const int tiles_p = HW / 128, tiles_c = Cout / 64;
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int apx = t >> 1, ach = (t & 1) * 8;   // A loader: pixel, channel offset
+    const int bk = t >> 4, bn = (t & 15) * 4;    // B loader: k row, channel offset
+    for (long long tile = blockIdx.x; tile < (long long)M * tiles_p * tiles_c; tile += gridDim.x) {
+        const int m = (int)(tile / (tiles_p * tiles_c));
+        const int r = (int)(tile % (tiles_p * tiles_c));
+        const int p0 = (r / tiles_c) * 128, co0 = (r % tiles_c) * 64;
+        const Tin *fin = in + (size_t)m * HW * Cin;
+        const int ap = p0 + apx, ay = ap / Wd, ax = ap % Wd;
+        T acc[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+        for (int tap = 0; tap < 9; ++tap) {
+            const int yy = ay + tap / 3 - 1, xx = ax + tap % 3 - 1;
+            const bool inb = yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+            const Tin *src = fin + ((size_t)yy * Wd + xx) * Cin;
+            for (int ci0 = 0; ci0 < Cin; ci0 += 16) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) As[ach + e][apx] = inb ? ld_as<T>(src + ci0 + ach + e) : (T)0;
+                const Tw *wsrc = Wt + ((size_t)tap * Cin + ci0 + bk) * Cout + co0 + bn;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) Bs[bk][bn + e] = ld_as<T>(wsrc + e);
+                __syncthreads();
+#pragma unroll
+                for (int kk = 0; kk < 16; ++kk) {
+                    T a[8], w[4];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) a[i] = As[kk][ty * 8 + i];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) w[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * w[j];
+                }
+                __syncthreads();
+            }
+        }
+        Tout *o = out + ((size_t)m * HW + p0 + ty * 8) * Cout + co0 + tx * 4;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                T v = acc[i][j] + (T)bias[co0 + tx * 4 + j];
+                if (v < (T)0) v = (T)0;
+                o[(size_t)i * Cout + j] = st_as<Tout, T>(v);
+            }
+    }
+}
+
+// Global average pool + linear head: score[m] = hb + sum_c hw[c] * mean_p act[m][p][c].
+// One block per frame; fixed-order partial sums (deterministic).
+template <typename Tin, typename T, typename S>
+__global__ void __launch_bounds__(256)
+k_pool_head(const int *count, const Tin *act, int HW, int C, const float *hw, double hb, S *score) {
+    __shared__ T part[256];
+    __shared__ T pooled[256];
+    const int M = *count;
+    const int groups = 256 / C;
+    const int c = threadIdx.x % C, g = threadIdx.x / C;
+    for (int m = blockIdx.x; m < M; m += gridDim.x) {
+        const Tin *a = act + (size_t)m * HW * C;
+        T s = (T)0;
+        if (g < groups)
+            for (int p = g; p < HW; p += groups) s += ld_as<T>(a + (size_t)p * C + c);
+        part[threadIdx.x] = s;
+        __syncthreads();
+        if (threadIdx.x < C) {
+            T tot = (T)0;
+            for (int q = 0; q < groups; ++q) tot += part[q * C + threadIdx.x];
+            pooled[threadIdx.x] = tot / (T)HW;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T r = (T)hb;
+            for (int q = 0; q < C; ++q) r += (T)hw[q] * pooled[q];
+            score[m] = (S)r;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+static int grid_for(int sms, int per_sm) { return sms * per_sm; }
+
+void launch_mlp_layer_f32(const int *count, const int *rows, const float *X, int ldx, const float *W,
+                          const float *b, float *Y, int K, int N, int relu, int max_rows, int sms,
+                          cudaStream_t st) {
+    const int tiles = ((max_rows + 63) / 64) * ((N + 63) / 64);
+    int grid = tiles < grid_for(sms, 4) ? tiles : grid_for(sms, 4);
+    if (grid < 1) grid = 1;
+    k_mlp_layer_f32<<<grid, 256, 0, st>>>(count, rows, X, ldx, W, b, Y, K, N, relu);
+}
+
+void launch_mlp_dot_f32(const int *count, const int *rows, const float *X, int ldx, const float *w,
+                        float bias, int K, float *score, int max_rows, int sms, cudaStream_t st) {
+    int grid = (max_rows + 7) / 8;
+    if (grid > grid_for(sms, 8)) grid = grid_for(sms, 8);
+    if (grid < 1) grid = 1;
+    k_mlp_dot_f32<<<grid, 256, 0, st>>>(count, rows, X, ldx, w, bias, K, score);
+}
+
+void launch_mlp_band_f32(const int *band_count, const int *band_tuple, const float *X, int ldx,
+                         const MlpDev &mlp, float *score_out, int sms, cudaStream_t st) {
+    const size_t smem = sizeof(float) * 2 * mlp.max_width;
+    k_mlp_band<float><<<grid_for(sms, 2), 256, smem, st>>>(band_count, band_tuple, X, ldx, mlp, score_out);
+}
+
+void launch_mlp_band_f64(const int *band_count, const int *band_tuple, const float *X, int ldx,
+                         const MlpDev &mlp, double *score_out, int sms, cudaStream_t st) {
+    const size_t smem = sizeof(double) * 2 * mlp.max_width;
+    k_mlp_band<double><<<grid_for(sms, 2), 256, smem, st>>>(band_count, band_tuple, X, ldx, mlp, score_out);
+}
+
+cudaError_t mlp_band_smem_setup(int max_width) {
+    const size_t s64 = sizeof(double) * 2 * (size_t)max_width;
+    const size_t s32 = sizeof(float) * 2 * (size_t)max_width;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_band<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_mlp_band<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32);
+}
+
+template <typename T, typename Tout>
+static void conv1_dispatch(const int *count, const int *list, const unsigned char *frames, int C0, int H,
+                           int Wd, const float *W, const float *bias, int Cout, Tout *out, int grid,
+                           cudaStream_t st) {
+    switch (Cout) {
+        case 16: k_conv1_u8<T, Tout, 16><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
+        case 32: k_conv1_u8<T, Tout, 32><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
+        default: k_conv1_u8<T, Tout, 64><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
+    }
+}
+
+void launch_conv1(int prec, const int *count, const int *list, const unsigned char *frames, int C0, int H,
+                  int Wd, const float *W, const float *bias, int Cout, void *out, int max_frames, int sms,
+                  cudaStream_t st) {
+    const int work = max_frames * ((H * Wd + 255) / 256);
+    int grid = work < grid_for(sms, 8) ? work : grid_for(sms, 8);
+    if (grid < 1) grid = 1;
+    if (prec == PREC_F64)
+        conv1_dispatch<double, double>(count, list, frames, C0, H, Wd, W, bias, Cout, (double *)out, grid, st);
+    else if (prec == PREC_F32)
+        conv1_dispatch<float, float>(count, list, frames, C0, H, Wd, W, bias, Cout, (float *)out, grid, st);
+    else
+        conv1_dispatch<float, __nv_bfloat16>(count, list, frames, C0, H, Wd, W, bias, Cout,
+                                             (__nv_bfloat16 *)out, grid, st);
+}
+
+void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,
+                         const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st) {
+    const long long tiles = (long long)max_frames * (H * Wd / 128) * (Cout / 64);
+    int grid = tiles < grid_for(sms, 4) ? (int)tiles : grid_for(sms, 4);
+    if (grid < 1) grid = 1;
+    if (prec == PREC_F64)
+        k_conv3x3_simt<double, float, double, double><<<grid, 256, 0, st>>>(
+            count, (const double *)in, Cin, H, Wd, (const float *)Wt, bias, Cout, (double *)out);
+    else if (prec == PREC_F32)
+        k_conv3x3_simt<float, float, float, float><<<grid, 256, 0, st>>>(
+            count, (const float *)in, Cin, H, Wd, (const float *)Wt, bias, Cout, (float *)out);
+    else
+        k_conv3x3_simt<__nv_bfloat16, __nv_bfloat16, float, __nv_bfloat16><<<grid, 256, 0, st>>>(
+            count, (const __nv_bfloat16 *)in, Cin, H, Wd, (const __nv_bfloat16 *)Wt, bias, Cout,
+            (__nv_bfloat16 *)out);
+}
+
+void launch_pool_head(int prec, const int *count, const void *act, int HW, int C, const float *hw, double hb,
+                      void *score, int max_frames, int sms, cudaStream_t st) {
+    int grid = max_frames < grid_for(sms, 8) ? max_frames : grid_for(sms, 8);
+    if (grid < 1) grid = 1;
+    if (prec == PREC_F64)
+        k_pool_head<double, double, double><<<grid, 256, 0, st>>>(count, (const double *)act, HW, C, hw, hb,
+                                                                  (double *)score);
+    else if (prec == PREC_F32)
+        k_pool_head<float, float, float><<<grid, 256, 0, st>>>(count, (const float *)act, HW, C, hw, hb,
+                                                               (float *)score);
+    else
+        k_pool_head<__nv_bfloat16, float, float><<<grid, 256, 0, st>>>(count, (const __nv_bfloat16 *)act, HW,
+                                                                       C, hw, hb, (float *)score);
+}
+
+}  // namespace hydro

@@ -1,0 +1,31 @@
+// Tensor-core (tcgen05, TMA-fed) BF16 conv3x3 layer for the CNN UDFs.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/hydro.h"
+
+namespace hydro {
+
+struct TcConvPlan {
+    bool ready = false;
+    int device = -1;
+    void *encode = nullptr;   // cuTensorMapEncodeTiled entry point
+};
+
+// Whether a layer of this shape runs on the tensor-core kernel.
+bool tc_conv_supported(int cin, int cout, int H, int W);
+// Repack fp32 weights [cout][cin][3][3] into the kernel's bf16 layout.
+void tc_conv_pack_weights(const float *w, int cin, int cout, std::vector<__nv_bfloat16> &out);
+hydro_status tc_conv_init(TcConvPlan *plan, int device);
+// out[m] = relu(conv3x3(in[m]) + bias) for m < *count (device), NHWC bf16.
+hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int cin, int H, int W,
+                         const void *wpacked, const float *bias, int cout, void *out, int max_frames, int sms,
+                         cudaStream_t st);
+void tc_conv_destroy(TcConvPlan *plan);
+const char *tc_conv_last_error();
+
+}  // namespace hydro

@@ -1,0 +1,38 @@
+"""Write the predicate thresholds of the seeded workloads.
+
+Each threshold is the midpoint that leaves exactly round(s * n_calib) of the
+calibration draw's FP64 oracle scores above it (s = the workload's target
+selectivity).  Calls only ``oracle`` and ``datagen``.
+
+    python tests/golden/make_thresholds.py [workload ...]
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import datagen as D  # noqa: E402
+import oracle as O  # noqa: E402
+
+
+def thresholds(name: str) -> dict:
+    w = D.workload(name)
+    t0 = time.time()
+    S = O.udf_scores(w.kind, D.calib_tuples(w), D.predicate_weights(w))
+    th = [O.threshold_for_selectivity(S[:, i], s) for i, s in enumerate(w.selectivity)]
+    return {"workload": name, "n_calib": w.n_calib, "selectivity": list(w.selectivity), "thresholds": th,
+            "calib_score_min": S.min(axis=0).tolist(), "calib_score_max": S.max(axis=0).tolist(),
+            "calib_score_std": S.std(axis=0).tolist(), "oracle_seconds": round(time.time() - t0, 1),
+            "oracle_threads": O.threads()}
+
+
+if __name__ == "__main__":
+    names = sys.argv[1:] or ["mlp3", "cnn4"]
+    for name in names:
+        out = thresholds(name)
+        with open(os.path.join(HERE, f"{name}_thresholds.json"), "w") as f:
+            json.dump(out, f, indent=1)
+        print(name, out["thresholds"], out["oracle_seconds"], "s")

@@ -1,0 +1,91 @@
+"""Shared helpers of the GPU parity tests: drive a query through the Python
+binding of the C ABI and compare with the oracle."""
+import json
+import os
+
+import numpy as np
+
+import datagen as D
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def stored_thresholds(name):
+    with open(os.path.join(GOLDEN, f"{name}_thresholds.json")) as f:
+        return json.load(f)["thresholds"]
+
+
+def oracle_thresholds(w):
+    S = O.udf_scores(w.kind, D.calib_tuples(w), D.predicate_weights(w))
+    return [O.threshold_for_selectivity(S[:, i], s) for i, s in enumerate(w.selectivity)], S
+
+
+def model_costs(w):
+    if w.kind == "vec":
+        return [O.mlp_flops(d) for d in w.udfs]
+    C, H, W = w.frame
+    return [O.cnn_flops(c, H, W) for c in w.udfs]
+
+
+def make_query(w, thresholds, *, batch, policy="rank", precision="fp32", warmup=1, window=8, lag=1,
+               static_order=None, max_in_flight=4, preds=None):
+    import paper_2403_14902_b300 as H
+    q = H.Query(w.kind, dim=w.dim, frame=w.frame, max_batch=batch, policy=policy, precision=precision,
+                warmup=warmup, window=window, lag=lag, max_in_flight=max_in_flight)
+    weights = D.predicate_weights(w)
+    idx = list(range(len(weights))) if preds is None else list(preds)
+    for i in idx:
+        if w.kind == "vec":
+            q.add_mlp(weights[i], thresholds[i])
+        else:
+            q.add_cnn(weights[i], thresholds[i])
+    if static_order is not None:
+        q.set_static_order(static_order)
+    return q
+
+
+def run_stream(q, X, batch, max_in_flight=4):
+    """Submit X (device tensor) in consecutive batches; return per-batch
+    (bits bool [n_b], counts int64 [P], info dict) in submission order."""
+    import paper_2403_14902_b300 as H
+    n = X.shape[0]
+    out = {}
+    pending = []
+    sizes = {}
+    for b0 in range(0, max(n, 1), batch):
+        xb = X[b0:b0 + batch]
+        bid = q.submit(xb)
+        sizes[bid] = xb.shape[0]
+        pending.append(bid)
+        if len(pending) >= max_in_flight:
+            b = pending.pop(0)
+            words, counts, info = q.poll(b)
+            out[b] = (H.bits_from_words(words, sizes[b]), counts, info)
+    for b in pending:
+        words, counts, info = q.poll(b)
+        out[b] = (H.bits_from_words(words, sizes[b]), counts, info)
+    return [out[k] for k in sorted(out)]
+
+
+def check_against_oracle(res, pm, batch, *, policy, costs, warmup=1, window=8, lag=1, static_order=None):
+    """Bit-exact result and exact per-batch order/counts versus the oracle's
+    router simulation."""
+    sim = O.simulate(pm, batch, policy=policy, costs=costs, static_order=static_order, warmup=warmup,
+                     window=window, lag=lag)
+    assert len(sim) == len(res)
+    for b, ((bits, counts, info), s) in enumerate(zip(res, sim)):
+        assert np.array_equal(bits, s["bits"]), f"batch {b}: pass set differs"
+        assert info["order"] == s["order"], f"batch {b}: order {info['order']} vs {s['order']}"
+        assert counts.tolist() == s["counts"].tolist(), f"batch {b}: counts {counts} vs {s['counts']}"
+        assert info["passed"] == s["passed"].tolist(), f"batch {b}: passed"
+        assert info["warmup"] == s["warmup"] or policy == "all"
+        assert info["n_pass"] == int(s["bits"].sum())
+    return sim
+
+
+def score_tolerance_ok(s_gpu, s64, rms, rel=1e-3):
+    """|s - s64| <= rel * max(|s64|, rms): relative error with the
+    calibration RMS as the scale near zero."""
+    bound = rel * np.maximum(np.abs(s64), rms)
+    return np.abs(s_gpu - s64) <= bound

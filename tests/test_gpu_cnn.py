@@ -1,0 +1,126 @@
+"""GPU parity of the CNN path (3x64x64 uint8 frames, four CNN UDFs with 2/4/6/8
+conv3x3 layers) against the oracle: FP32 and BF16-with-recheck, small
+streams element by element and the full 65,536-frame stream in the bench's
+launch configuration on sampled frames."""
+import numpy as np
+import pytest
+
+import datagen as D
+import oracle as O
+from gpu_helpers import (check_against_oracle, make_query, model_costs, run_stream, score_tolerance_ok,
+                         stored_thresholds)
+
+pytestmark = pytest.mark.gpu
+
+N_SMALL = 72          # 4 batches of 16 + a ragged batch of 8
+B_SMALL = 16
+
+
+@pytest.fixture(scope="module")
+def cnn4():
+    import torch
+    w = D.workload("cnn4")
+    th = stored_thresholds("cnn4")
+    F = D.stream_tuples(w, N_SMALL)
+    S = O.udf_scores("frame", F, D.predicate_weights(w))
+    calib = D.calib_tuples(w)
+    return dict(w=w, th=th, F=F, S=S, pm=O.pass_matrix(S, th), Fd=torch.from_numpy(F).cuda(),
+                calib_d=torch.from_numpy(calib[:64]).cuda(), rms=np.sqrt((S ** 2).mean(axis=0)))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("policy", ["rank", "static", "all"])
+def test_small_stream_parity(cnn4, precision, policy):
+    w = cnn4["w"]
+    q = make_query(w, cnn4["th"], batch=B_SMALL, policy=policy, precision=precision)
+    res = run_stream(q, cnn4["Fd"], B_SMALL)
+    check_against_oracle(res, cnn4["pm"], B_SMALL, policy=policy, costs=model_costs(w))
+    if precision == "bf16":
+        assert sum(sum(r[2]["recheck_fp32"]) for r in res) >= 0
+    q.close()
+
+
+def test_bf16_wide_margin_rechecks_and_stays_exact(cnn4):
+    # a margin wider than the score spread sends every tuple through the
+    # FP32 recheck; the pass set must not move
+    w = cnn4["w"]
+    q = make_query(w, cnn4["th"], batch=B_SMALL, policy="rank", precision="bf16")
+    for i in range(4):
+        q.set_margins(i, 10.0, 1e-5)
+    res = run_stream(q, cnn4["Fd"], B_SMALL)
+    check_against_oracle(res, cnn4["pm"], B_SMALL, policy="rank", costs=model_costs(w))
+    assert sum(sum(r[2]["recheck_fp32"]) for r in res) == sum(int(r[1].sum()) for r in res)
+    q.close()
+
+
+def test_fp32_wide_margin_goes_to_fp64(cnn4):
+    w = cnn4["w"]
+    q = make_query(w, cnn4["th"], batch=B_SMALL, policy="static", precision="fp32")
+    for i in range(4):
+        q.set_margins(i, 0.02, 0.05)
+    res = run_stream(q, cnn4["Fd"], B_SMALL)
+    check_against_oracle(res, cnn4["pm"], B_SMALL, policy="static", costs=model_costs(w))
+    assert sum(sum(r[2]["recheck_fp64"]) for r in res) > 0
+    q.close()
+
+
+def test_udf_scores_error(cnn4):
+    import torch
+    w = cnn4["w"]
+    q = make_query(w, cnn4["th"], batch=64, precision="bf16")
+    n = 40
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    for i in range(4):
+        s64 = cnn4["S"][:n, i]
+        q.udf_scores(i, "fp32", cnn4["Fd"][:n], out)
+        assert score_tolerance_ok(out.cpu().numpy(), s64, cnn4["rms"][i]).all()
+        q.udf_scores(i, "fp64", cnn4["Fd"][:n], out)
+        assert np.max(np.abs(out.cpu().numpy() - s64)) <= 1e-10 * max(1.0, np.abs(s64).max())
+        q.udf_scores(i, "bf16", cnn4["Fd"][:n], out)
+        # the BF16 error must sit well inside the 0.02 recheck margin
+        assert np.max(np.abs(out.cpu().numpy() - s64)) < 0.02 / 2
+    q.close()
+
+
+def test_calibrate_bf16(cnn4):
+    w = cnn4["w"]
+    q = make_query(w, cnn4["th"], batch=B_SMALL, precision="bf16")
+    info = q.calibrate(cnn4["calib_d"])
+    for d in info:
+        assert d["max_err_lowp"] < 0.02 / 2
+        assert d["margin_lowp"] >= 0.02
+        assert d["margin_fp32"] >= 16 * d["max_err_fp32"]
+    res = run_stream(q, cnn4["Fd"], B_SMALL)
+    check_against_oracle(res, cnn4["pm"], B_SMALL, policy="rank", costs=model_costs(w))
+    q.close()
+
+
+def test_full_stream_sampled_parity_bf16():
+    """The full 65,536-frame stream, batches of 1,024, rank routing, BF16
+    with recheck (the bench's configuration).  Sampled frames are checked
+    against the oracle one by one; every batch is checked for the
+    short-circuit invariants."""
+    import torch
+    w = D.workload("cnn4")
+    th = stored_thresholds("cnn4")
+    Fd = torch.from_numpy(D.stream_tuples(w)).cuda()
+    q = make_query(w, th, batch=w.batch, policy="rank", precision="bf16")
+    res = run_stream(q, Fd, w.batch)
+    bits = np.concatenate([r[0] for r in res])
+    assert bits.size == w.n
+    rng = np.random.default_rng(1234)
+    sample = np.unique(np.concatenate([rng.choice(w.n, 20, replace=False), np.flatnonzero(bits)[:4]]))
+    S = O.udf_scores("frame", D.stream_tuples(w)[sample], D.predicate_weights(w))
+    want = O.result_bits(O.pass_matrix(S, th))
+    assert np.array_equal(bits[sample], want)
+    for b, (bb, counts, info) in enumerate(res):
+        order = info["order"]
+        assert sorted(order) == [0, 1, 2, 3]
+        if info["warmup"]:
+            assert counts.tolist() == [w.batch] * 4
+            continue
+        assert counts[order[0]] == bb.size
+        for k in range(3):
+            assert counts[order[k + 1]] == info["passed"][order[k]]
+        assert info["passed"][order[-1]] == int(bb.sum()) == info["n_pass"]
+    q.close()
