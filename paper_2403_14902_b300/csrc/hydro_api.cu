@@ -432,7 +432,7 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
         if (prec == PREC_BF16 && p.dWtc[l]) {
             e = prof_begin(q, pc, PC_CONV_TC, fpi, bpi, wb);
             hydro_status rs = tc_conv_run(&q->tc, count, act[cur], p.dims[l], H, Wd, p.dWtc[l], p.db[l],
-                                          p.dims[l + 1], act[1 - cur], max_rows, q->sms, st);
+                                          p.dims[l + 1], act[1 - cur], max_rows, q->sms, st, q->d_err);
             prof_end(q, e);
             if (rs != HYDRO_OK) return fail(rs, "tensor-core conv: %s", tc_conv_last_error());
         } else {

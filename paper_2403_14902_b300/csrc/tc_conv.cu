@@ -1,21 +1,469 @@
-// Placeholder until the tcgen05 kernel lands: no shape is supported, so the
-// BF16 path uses the SIMT BF16 conv.
+// BF16 conv3x3 (stride 1, zero pad 1) + bias + ReLU on the 5th-generation
+// tensor cores: tcgen05.mma with the accumulator in TMEM, operands staged in
+// shared memory by TMA, warp-specialised and persistent.
+//
+// Implicit GEMM per CTA tile: M = 128 output pixels (two 64-pixel image rows
+// of one frame), N = Cout (64 or 128), K = 9 taps x Cin.  For one chunk of
+// CC input channels and one horizontal tap kx, a single 4-D TMA box
+// {CC channels, 64 px, 4 rows, 1 frame} at (c0, kx-1, y0-1, frame) holds the
+// input rows y0-1 .. y0+2 shifted by kx-1; the three vertical taps ky are the
+// 128-row windows starting at rows 64*ky of that box, so one load serves
+// three taps.  Out-of-range coordinates are zero-filled by TMA, which is the
+// conv's zero padding.  The matching weights are one 3-D TMA box
+// {CC, Cout, 3 taps}.
+//
+// Roles (192 threads): warp 0 issues TMA, warp 1 owns TMEM and issues the
+// MMAs, warps 2-5 drain the accumulator (bias, ReLU, BF16, NHWC store).  Two
+// TMEM accumulators let the epilogue of one tile overlap the MMAs of the
+// next.  Every mbarrier wait is bounded by the global timer; on expiry the
+// CTA raises ERR_TC_TIMEOUT, drains its issued copies and frees TMEM.
+#include <cuda.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
 #include "tc_conv.h"
 
 namespace hydro {
 
-bool tc_conv_supported(int, int, int, int) { return false; }
-void tc_conv_pack_weights(const float *, int, int, std::vector<__nv_bfloat16> &out) { out.clear(); }
+namespace {
+
+thread_local std::string g_tc_err;
+constexpr unsigned long long kWaitNs = 4000000000ull;   // 4 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `parity` to complete; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned long long limit_ns = kWaitNs) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 0u) {
+            if (*abort_flag) return false;
+            if (gtimer() - t0 > limit_ns) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2,
+                                            int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (K-major, swizzled): start address,
+// leading byte offset (unused for swizzled K-major, 16 B), stride byte offset
+// between 8-row groups, descriptor version 1, swizzle mode in bits 61-63.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo_bytes, uint32_t swizzle) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)(swizzle & 7u) << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+template <int CC, int N, int S>
+struct TcCfg {
+    static constexpr int ROWB = CC * 2;                 // bytes of one pixel's K chunk
+    static constexpr int A_BYTES = 4 * 64 * ROWB;       // 4 image rows x 64 pixels
+    static constexpr int B_TAP = N * ROWB;              // one tap's weights
+    static constexpr int B_BYTES = 3 * B_TAP;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr uint32_t SWZ = CC == 64 ? 2u : 4u;  // 128B or 64B swizzle
+    static constexpr uint32_t SBO = 8 * ROWB;            // 8-row group stride
+    static constexpr int TMEM_COLS = 2 * N;
+    static constexpr int SMEM = S * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+template <int CC, int N, int S>
+__global__ void __launch_bounds__(192, 1)
+k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const int *count,
+             int nchunks, int tiles_per_frame, int HW, const float *__restrict__ bias, __nv_bfloat16 *out,
+             unsigned int *err) {
+    using C = TcCfg<CC, N, S>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * C::STAGE);
+    uint64_t *empty = full + S;
+    uint64_t *tfull = empty + S;
+    uint64_t *tempty = tfull + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int total = (*count) * tiles_per_frame;
+    const int ksteps = nchunks * 3;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer
+            int s = 0;
+            uint32_t ph = 0;
+            uint32_t issued = 0, last_par = 0;   // per stage bit: load in flight, its parity
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const int m = t / tiles_per_frame;
+                const int y0 = (t % tiles_per_frame) * 2;
+                for (int c = 0; c < nchunks && ok; ++c)
+                    for (int kx = 0; kx < 3 && ok; ++kx) {
+                        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        unsigned char *sa = smem + s * C::STAGE;
+                        mbar_expect_tx(&full[s], (uint32_t)C::STAGE);
+                        tma_load_4d(sa, &tmA, &full[s], c * CC, kx - 1, y0 - 1, m);
+                        tma_load_3d(sa + C::A_BYTES, &tmB, &full[s], 0, 0, (c * 3 + kx) * 3);
+                        issued |= 1u << s;
+                        last_par = (last_par & ~(1u << s)) | (ph << s);
+                        if (++s == S) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
+                    }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                // drain the copies this CTA issued before leaving (bounded)
+                volatile int never = 0;
+                for (int k = 0; k < S; ++k)
+                    if (issued & (1u << k)) mbar_wait(&full[k], (last_par >> k) & 1u, &never, 100000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer
+            constexpr uint32_t idesc = idesc_bf16(128, N);
+            int s = 0;
+            uint32_t ph = 0;
+            int tl = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
+                const int buf = tl & 1;
+                const uint32_t tph = (uint32_t)(tl >> 1) & 1u;
+                if (!mbar_wait(&tempty[buf], tph ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem_base + (uint32_t)(buf * N);
+                for (int k = 0; k < ksteps; ++k) {
+                    if (!mbar_wait(&full[s], ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + s * C::STAGE);
+                    const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+                    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                        for (int kk = 0; kk < CC / 16; ++kk) {
+                            const uint64_t ad = smem_desc(sa + ky * 64 * C::ROWB + kk * 32, C::SBO, C::SWZ);
+                            const uint64_t bd = smem_desc(sb + ky * C::B_TAP + kk * 32, C::SBO, C::SWZ);
+                            mma_bf16(dt, ad, bd, idesc, (k | ky | kk) != 0);
+                        }
+                    mma_commit(&empty[s]);
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (ok) mma_commit(&tfull[buf]);
+            }
+            if (!ok) *abort_flag = 1;
+        }
+    } else {
+        // ---- epilogue: warps 2..5, TMEM lane quarter = warp % 4
+        const int qtr = warp & 3;
+        const int row = qtr * 32 + lane;
+        int tl = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
+            const int buf = tl & 1;
+            const uint32_t tph = (uint32_t)(tl >> 1) & 1u;
+            if (!mbar_wait(&tfull[buf], tph, abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const int m = t / tiles_per_frame;
+            const int p0 = (t % tiles_per_frame) * 128;
+            __nv_bfloat16 *o = out + ((size_t)m * HW + p0 + row) * N;
+#pragma unroll
+            for (int c0 = 0; c0 < N; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * N + c0), r);
+                tmem_ld_wait();
+                uint32_t pk[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float v0 = __uint_as_float(r[2 * j]) + __ldg(bias + c0 + 2 * j);
+                    float v1 = __uint_as_float(r[2 * j + 1]) + __ldg(bias + c0 + 2 * j + 1);
+                    v0 = v0 > 0.f ? v0 : 0.f;
+                    v1 = v1 > 0.f ? v1 : 0.f;
+                    pk[j] = pack_bf16x2(v0, v1);
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(o + c0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicOr(err, ERR_TC_TIMEOUT);
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+template <int CC, int N, int S>
+cudaError_t set_smem() {
+    return cudaFuncSetAttribute(k_conv3x3_tc<CC, N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcCfg<CC, N, S>::SMEM);
+}
+
+// Stage counts per (CC, N), sized to ~160-170 KB of shared memory.
+constexpr int kS_64_128 = 2, kS_64_64 = 3, kS_32_128 = 4, kS_32_64 = 4;
+
+}  // namespace
+
+bool tc_conv_supported(int cin, int cout, int H, int W) {
+    if (W != 64 || H < 2 || (H % 2) != 0) return false;
+    if (cout != 64 && cout != 128) return false;
+    return cin == 32 || (cin % 64 == 0 && cin <= 512);
+}
+
+void tc_conv_pack_weights(const float *w, int cin, int cout, std::vector<__nv_bfloat16> &out) {
+    const int CC = cin == 32 ? 32 : 64;
+    const int nch = cin / CC;
+    out.assign((size_t)nch * 9 * cout * CC, __float2bfloat16_rn(0.f));
+    // layout [(c*3 + kx)*3 + ky][co][k], ci = c*CC + k; source W[co][ci][ky][kx]
+    for (int c = 0; c < nch; ++c)
+        for (int kx = 0; kx < 3; ++kx)
+            for (int ky = 0; ky < 3; ++ky)
+                for (int co = 0; co < cout; ++co)
+                    for (int k = 0; k < CC; ++k) {
+                        const int ci = c * CC + k;
+                        const float v = w[(((size_t)co * cin + ci) * 3 + ky) * 3 + kx];
+                        out[((((size_t)(c * 3 + kx) * 3 + ky) * cout + co) * CC) + k] = __float2bfloat16_rn(v);
+                    }
+}
+
 hydro_status tc_conv_init(TcConvPlan *plan, int device) {
-    plan->ready = true;
     plan->device = device;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+    if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !fn) {
+        g_tc_err = "cuTensorMapEncodeTiled entry point not available";
+        return HYDRO_ECUDA;
+    }
+    plan->encode = fn;
+    cudaError_t r = cudaSuccess;
+    if (r == cudaSuccess) r = set_smem<64, 128, kS_64_128>();
+    if (r == cudaSuccess) r = set_smem<64, 64, kS_64_64>();
+    if (r == cudaSuccess) r = set_smem<32, 128, kS_32_128>();
+    if (r == cudaSuccess) r = set_smem<32, 64, kS_32_64>();
+    if (r != cudaSuccess) {
+        g_tc_err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(r);
+        return HYDRO_ECUDA;
+    }
+    plan->ready = true;
     return HYDRO_OK;
 }
-hydro_status tc_conv_run(TcConvPlan *, const int *, const void *, int, int, int, const void *, const float *, int,
-                         void *, int, int, cudaStream_t) {
-    return HYDRO_EUNSUPPORTED;
+
+hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int cin, int H, int W,
+                         const void *wpacked, const float *bias, int cout, void *out, int max_frames, int sms,
+                         cudaStream_t st, unsigned int *err) {
+    if (!plan->ready || !tc_conv_supported(cin, cout, H, W)) {
+        g_tc_err = "tensor-core conv not ready or shape unsupported";
+        return HYDRO_EUNSUPPORTED;
+    }
+    EncodeFn enc = reinterpret_cast<EncodeFn>(plan->encode);
+    const int CC = cin == 32 ? 32 : 64;
+    const int nch = cin / CC;
+    CUtensorMap tmA, tmB;
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)max_frames};
+        const cuuint64_t strides[3] = {(cuuint64_t)cin * 2, (cuuint64_t)W * cin * 2, (cuuint64_t)H * W * cin * 2};
+        const cuuint32_t box[4] = {(cuuint32_t)CC, 64, 4, 1};
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        CUresult r = enc(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(in), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            g_tc_err = "cuTensorMapEncodeTiled(activations) failed: " + std::to_string((int)r);
+            return HYDRO_ECUDA;
+        }
+    }
+    {
+        const cuuint64_t dims[3] = {(cuuint64_t)CC, (cuuint64_t)cout, (cuuint64_t)nch * 9};
+        const cuuint64_t strides[2] = {(cuuint64_t)CC * 2, (cuuint64_t)cout * CC * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)CC, (cuuint32_t)cout, 3};
+        const cuuint32_t es[3] = {1, 1, 1};
+        CUresult r = enc(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(wpacked), dims, strides, box,
+                         es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            g_tc_err = "cuTensorMapEncodeTiled(weights) failed: " + std::to_string((int)r);
+            return HYDRO_ECUDA;
+        }
+    }
+    const int tpf = H * W / 128;
+    long long tiles = (long long)max_frames * tpf;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out);
+    const int HW = H * W;
+    if (CC == 64 && cout == 128)
+        k_conv3x3_tc<64, 128, kS_64_128><<<grid, 192, TcCfg<64, 128, kS_64_128>::SMEM, st>>>(
+            tmA, tmB, count, nch, tpf, HW, bias, o, err);
+    else if (CC == 64)
+        k_conv3x3_tc<64, 64, kS_64_64><<<grid, 192, TcCfg<64, 64, kS_64_64>::SMEM, st>>>(tmA, tmB, count, nch, tpf,
+                                                                                        HW, bias, o, err);
+    else if (cout == 128)
+        k_conv3x3_tc<32, 128, kS_32_128><<<grid, 192, TcCfg<32, 128, kS_32_128>::SMEM, st>>>(
+            tmA, tmB, count, nch, tpf, HW, bias, o, err);
+    else
+        k_conv3x3_tc<32, 64, kS_32_64><<<grid, 192, TcCfg<32, 64, kS_32_64>::SMEM, st>>>(tmA, tmB, count, nch, tpf,
+                                                                                        HW, bias, o, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_tc_err = std::string("launch: ") + cudaGetErrorString(e);
+        return HYDRO_ECUDA;
+    }
+    return HYDRO_OK;
 }
+
 void tc_conv_destroy(TcConvPlan *plan) { plan->ready = false; }
-const char *tc_conv_last_error() { return ""; }
+
+const char *tc_conv_last_error() { return g_tc_err.c_str(); }
 
 }  // namespace hydro

@@ -24,7 +24,7 @@ hydro_status tc_conv_init(TcConvPlan *plan, int device);
 // out[m] = relu(conv3x3(in[m]) + bias) for m < *count (device), NHWC bf16.
 hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int cin, int H, int W,
                          const void *wpacked, const float *bias, int cout, void *out, int max_frames, int sms,
-                         cudaStream_t st);
+                         cudaStream_t st, unsigned int *err);
 void tc_conv_destroy(TcConvPlan *plan);
 const char *tc_conv_last_error();
 
