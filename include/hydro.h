@@ -238,6 +238,32 @@ HYDRO_API hydro_status hydro_profile(hydro_query *q, int32_t enable);
 HYDRO_API hydro_status hydro_profile_read(hydro_query *q, hydro_kernel_profile *out, int32_t max, int32_t *n_out,
                                           int64_t *total_launches);
 
+/* Allocation-free FP32 MLP scores.  The paper has no counterpart: this
+ * entry point is for callers that cannot allocate device memory while they
+ * run, such as code recording a CUDA graph (cudaMalloc is not permitted
+ * during stream capture) or code inside a framework that owns the device
+ * memory pool.  It computes the same scores as hydro_udf_scores(FP32) on an
+ * MLP UDF, with the caller's device buffers:
+ *   d_x        device fp32 [n][dims[0]] tuples
+ *   dims       host, n_layers+1 widths, dims[n_layers] == 1
+ *   d_weights  host array of n_layers DEVICE pointers, layer l [dims[l+1]][dims[l]]
+ *   d_biases   host array of n_layers DEVICE pointers, layer l [dims[l+1]]
+ *   d_scores   device double [n] (output)
+ *   stream     cudaStream_t (NULL = legacy default stream)
+ * The activations between layers live in one static device array of the
+ * library (two buffers of 1,048,576 floats, 8 MiB), which every GPU that
+ * loads the library holds until the process exits; n times the widest
+ * hidden layer must not exceed 1,048,576 (else HYDRO_EINVAL).  It calls no
+ * allocator.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current, so make that
+ * first call before any stream capture.  All calls share the array and keep
+ * the last call's contents: calls whose kernels overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * Asynchronous on `stream`; errors are returned as status codes. */
+HYDRO_API hydro_status hydro_mlp_scores_noalloc(const float *d_x, int64_t n, int32_t n_layers, const int32_t *dims,
+                                                const float *const *d_weights, const float *const *d_biases,
+                                                double *d_scores, void *stream);
+
 /* Wait for outstanding work (bounded), free every resource of q. */
 HYDRO_API hydro_status hydro_destroy_query(hydro_query *q);
 

@@ -32,7 +32,7 @@ UDF_MLP, UDF_CNN = 0, 1
 EXPORTED = ["hydro_default_config", "hydro_create_query", "hydro_add_predicate", "hydro_set_margins",
             "hydro_set_static_order", "hydro_calibrate", "hydro_udf_scores", "hydro_submit_batch",
             "hydro_poll_result", "hydro_get_stats", "hydro_profile", "hydro_profile_read",
-            "hydro_destroy_query", "hydro_last_error"]
+            "hydro_mlp_scores_noalloc", "hydro_destroy_query", "hydro_last_error"]
 
 
 class QueryConfig(ctypes.Structure):
@@ -102,6 +102,7 @@ def load():
     L.hydro_get_stats.argtypes = [vp, P(PredStats), i32]
     L.hydro_profile.argtypes = [vp, i32]
     L.hydro_profile_read.argtypes = [vp, P(KernelProfile), i32, P(i32), P(i64)]
+    L.hydro_mlp_scores_noalloc.argtypes = [vp, i64, i32, P(i32), P(vp), P(vp), vp, vp]
     L.hydro_destroy_query.argtypes = [vp]
     L.hydro_last_error.argtypes = []
     L.hydro_last_error.restype = ctypes.c_char_p
@@ -285,6 +286,20 @@ class Query:
                 load().hydro_destroy_query(self._h)
         except Exception:
             pass
+
+
+def mlp_scores_noalloc(x, weights, biases, out, stream=None):
+    """FP32 MLP scores with no device allocation (see hydro.h): ``x`` device
+    fp32 [n, dim]; ``weights``/``biases`` lists of device fp32 tensors
+    ([out, in] / [out]); ``out`` device float64 [n]."""
+    dims = [int(x.shape[1])] + [int(w.shape[0]) for w in weights]
+    d = (ctypes.c_int32 * len(dims))(*dims)
+    wp = (ctypes.c_void_p * len(weights))(*[w.data_ptr() for w in weights])
+    bp = (ctypes.c_void_p * len(biases))(*[b.data_ptr() for b in biases])
+    s = stream.cuda_stream if stream is not None else None
+    _check(load().hydro_mlp_scores_noalloc(x.data_ptr(), int(x.shape[0]), len(weights), d, wp, bp, out.data_ptr(), s),
+           "hydro_mlp_scores_noalloc")
+    return out
 
 
 def bits_from_words(words: np.ndarray, n: int) -> np.ndarray:

@@ -539,6 +539,8 @@ hydro_status check_query(hydro_query *q) {
 
 }  // namespace
 
+void hydro::set_last_error(const char *msg) { g_err = msg; }
+
 // ================================================================ C ABI
 
 extern "C" {

@@ -66,6 +66,9 @@ void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, in
 void launch_pool_head(int prec, const int *count, const void *act, int HW, int C, const float *hw, double hb,
                       void *score, int max_frames, int sms, cudaStream_t st);
 
+// hydro_api.cu: message returned by hydro_last_error() on this thread
+void set_last_error(const char *msg);
+
 // k_util.cu
 void launch_f32_to_f64(const float *src, double *dst, int n, cudaStream_t st);
 void launch_identity_list(int *list, int *count, int start, int n, cudaStream_t st);
