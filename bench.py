@@ -298,8 +298,11 @@ def ours(args):
         "pass_count_per_step": int(npass[0]),
         "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
                         "tflops": round(v["flops"] / max(v["total_ms"], 1e-9) / 1e9, 2)} for k, v in prof.items()},
-        "recheck": {"fp32": [s["recheck_fp32"] for s in stats], "fp64": [s["recheck_fp64"] for s in stats],
-                    "calib_max_err_bf16": [round(c["max_err_lowp"], 6) for c in calib]},
+        "recheck": {"tf32x3": [s["recheck_tf32"] for s in stats], "fp32": [s["recheck_fp32"] for s in stats],
+                    "fp64": [s["recheck_fp64"] for s in stats],
+                    "calib_max_err_bf16": [round(c["max_err_lowp"], 6) for c in calib],
+                    "calib_max_err_tf32x3": [float("%.3g" % c["max_err_tf32"]) for c in calib],
+                    "calib_max_err_fp32": [float("%.3g" % c["max_err_fp32"]) for c in calib]},
     }
     return out
 

@@ -76,9 +76,14 @@ enum {
     HYDRO_PREC_FP32 = 0,   /* FP32 everywhere; FP32 scores within margin_fp32 of the
                               threshold are re-evaluated in FP64 */
     HYDRO_PREC_BF16 = 1,   /* BF16 operands, FP32 accumulation on the tensor cores;
-                              scores within margin_lowp are re-evaluated in FP32
-                              (and from there in FP64 as above) */
-    HYDRO_PREC_FP64 = 2    /* FP64 (only for hydro_udf_scores) */
+                              scores within margin_lowp are re-evaluated FP32-accurately:
+                              CNN UDFs first by 3xTF32 on the tensor cores (scores within
+                              margin_tf32 go on), then in FP32 on CUDA cores (within
+                              margin_fp32 go on to FP64); MLP UDFs in FP32 then FP64 */
+    HYDRO_PREC_FP64 = 2,   /* FP64 (only for hydro_udf_scores) */
+    HYDRO_PREC_TF32X3 = 3  /* FP32-accurate 3xTF32 on the tensor cores (hi*hi + hi*lo + lo*hi);
+                              the first BF16 recheck level of CNN UDFs (hydro_udf_scores on
+                              BF16 CNN queries) */
 };
 
 /* Where the router's per-tuple cost comes from. */
@@ -134,7 +139,8 @@ typedef struct hydro_batch_info {
     int32_t warmup;                             /* 1: every predicate saw every tuple */
     int32_t order[HYDRO_MAX_PREDICATES];        /* predicate ids in evaluation order */
     int64_t passed[HYDRO_MAX_PREDICATES];       /* of the tuples predicate i evaluated, how many passed */
-    int64_t recheck_fp32[HYDRO_MAX_PREDICATES]; /* re-evaluated in FP32 (low-precision band) */
+    int64_t recheck_tf32[HYDRO_MAX_PREDICATES]; /* re-evaluated by 3xTF32 (low-precision band, CNN) */
+    int64_t recheck_fp32[HYDRO_MAX_PREDICATES]; /* re-evaluated in FP32 on CUDA cores */
     int64_t recheck_fp64[HYDRO_MAX_PREDICATES]; /* re-evaluated in FP64 (FP32 band) */
     double device_ms;                           /* GPU time from the batch's first to last kernel */
 } hydro_batch_info;
@@ -143,10 +149,12 @@ typedef struct hydro_batch_info {
 typedef struct hydro_pred_stats {
     int64_t evaluated;       /* tuples the UDF ran on at working precision */
     int64_t passed;
+    int64_t recheck_tf32;
     int64_t recheck_fp32;
     int64_t recheck_fp64;
     int64_t model_cost;      /* flops per tuple used by HYDRO_COST_MODEL */
     double margin_lowp;      /* current margins */
+    double margin_tf32;
     double margin_fp32;
 } hydro_pred_stats;
 
@@ -154,8 +162,10 @@ typedef struct hydro_pred_stats {
 typedef struct hydro_calib_info {
     double max_err_fp32;     /* max |s_fp32 - s_fp64| over the calibration tuples */
     double max_err_lowp;     /* max |s_bf16 - s_fp64| (BF16 queries), else 0 */
-    double margin_fp32;      /* margin set */
-    double margin_lowp;      /* margin set (raised if the error needed it) */
+    double max_err_tf32;     /* max |s_3xtf32 - s_fp64| (BF16 CNN queries), else 0 */
+    double margin_fp32;      /* margins set */
+    double margin_lowp;      /* (raised if the error needed it) */
+    double margin_tf32;
 } hydro_calib_info;
 
 /* One kernel class in a profile (hydro_profile_read). */
@@ -186,23 +196,27 @@ HYDRO_API hydro_status hydro_add_predicate(hydro_query *q, const hydro_udf_desc 
                                  int32_t *out_pred_id);
 
 /* Set the recheck margins of predicate pred (absolute score units, >= 0).
- * A score s at working precision decides the test only if |s - t| > margin;
- * otherwise the tuple is re-evaluated at the next precision (BF16 -> FP32 ->
- * FP64).  Valid before the first submit. */
-HYDRO_API hydro_status hydro_set_margins(hydro_query *q, int32_t pred, double margin_lowp, double margin_fp32);
+ * A score s at a precision decides the test only if |s - t| > that level's
+ * margin; otherwise the tuple is re-evaluated at the next level
+ * (BF16 -> 3xTF32 (CNN) -> FP32 -> FP64).  Valid before the first submit.
+ * Defaults: margin_lowp 0.02, margin_tf32 5e-3*max(1,|t|), margin_fp32
+ * 1e-5*max(1,|t|). */
+HYDRO_API hydro_status hydro_set_margins(hydro_query *q, int32_t pred, double margin_lowp, double margin_tf32,
+                                         double margin_fp32);
 
 /* Order for HYDRO_POLICY_STATIC: a permutation of 0..P-1 (n must equal P). */
 HYDRO_API hydro_status hydro_set_static_order(hydro_query *q, const int32_t *order, int32_t n);
 
 /* Calibrate the margins on n device tuples: runs every UDF in FP64, FP32 and
- * (BF16 queries) BF16 on the GPU and sets margin_fp32 = 16 * max FP32 error
- * (at least 1e-9 * max |score|), and raises margin_lowp to 4 * max BF16 error
- * if that is larger.  info[P] (nullable) receives the report.  Valid before
- * the first submit; synchronous. */
+ * (BF16 queries) BF16 and 3xTF32 on the GPU and sets margin_fp32 = 16 * max
+ * FP32 error and margin_tf32 = 8 * max 3xTF32 error (each at least
+ * 1e-9 * max |score|), and raises margin_lowp to 4 * max BF16 error if that
+ * is larger.  info[P] (nullable) receives the report.  Valid before the
+ * first submit; synchronous. */
 HYDRO_API hydro_status hydro_calibrate(hydro_query *q, const void *d_tuples, int64_t n, hydro_calib_info *info);
 
 /* Scores of predicate pred's UDF on n device tuples at precision prec
- * (HYDRO_PREC_FP64/FP32/BF16) into d_scores (device, n doubles).
+ * (HYDRO_PREC_FP64/FP32/BF16/TF32X3) into d_scores (device, n doubles).
  * Synchronous; for tests, calibration and error reports. */
 HYDRO_API hydro_status hydro_udf_scores(hydro_query *q, int32_t pred, int32_t prec, const void *d_tuples,
                               int64_t n, double *d_scores);

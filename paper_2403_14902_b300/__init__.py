@@ -26,7 +26,7 @@ OK, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEOUT, ESTATE, EDEVICE, ENOTFOUND, EUNSUPP
 
 TUPLE_F32, TUPLE_U8_FRAME = 0, 1
 POLICIES = {"rank": 0, "static": 1, "all": 2, "cost": 3, "selectivity": 4}
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp64": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp64": 2, "tf32x3": 3}
 UDF_MLP, UDF_CNN = 0, 1
 
 EXPORTED = ["hydro_default_config", "hydro_create_query", "hydro_add_predicate", "hydro_set_margins",
@@ -56,19 +56,21 @@ class UdfDesc(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_pass", ctypes.c_int64), ("n_predicates", ctypes.c_int32),
                 ("warmup", ctypes.c_int32), ("order", ctypes.c_int32 * MAX_PREDICATES),
-                ("passed", ctypes.c_int64 * MAX_PREDICATES), ("recheck_fp32", ctypes.c_int64 * MAX_PREDICATES),
+                ("passed", ctypes.c_int64 * MAX_PREDICATES), ("recheck_tf32", ctypes.c_int64 * MAX_PREDICATES),
+                ("recheck_fp32", ctypes.c_int64 * MAX_PREDICATES),
                 ("recheck_fp64", ctypes.c_int64 * MAX_PREDICATES), ("device_ms", ctypes.c_double)]
 
 
 class PredStats(ctypes.Structure):
-    _fields_ = [("evaluated", ctypes.c_int64), ("passed", ctypes.c_int64), ("recheck_fp32", ctypes.c_int64),
-                ("recheck_fp64", ctypes.c_int64), ("model_cost", ctypes.c_int64),
-                ("margin_lowp", ctypes.c_double), ("margin_fp32", ctypes.c_double)]
+    _fields_ = [("evaluated", ctypes.c_int64), ("passed", ctypes.c_int64), ("recheck_tf32", ctypes.c_int64),
+                ("recheck_fp32", ctypes.c_int64), ("recheck_fp64", ctypes.c_int64), ("model_cost", ctypes.c_int64),
+                ("margin_lowp", ctypes.c_double), ("margin_tf32", ctypes.c_double), ("margin_fp32", ctypes.c_double)]
 
 
 class CalibInfo(ctypes.Structure):
     _fields_ = [("max_err_fp32", ctypes.c_double), ("max_err_lowp", ctypes.c_double),
-                ("margin_fp32", ctypes.c_double), ("margin_lowp", ctypes.c_double)]
+                ("max_err_tf32", ctypes.c_double), ("margin_fp32", ctypes.c_double),
+                ("margin_lowp", ctypes.c_double), ("margin_tf32", ctypes.c_double)]
 
 
 class KernelProfile(ctypes.Structure):
@@ -93,7 +95,7 @@ def load():
     L.hydro_default_config.restype = None
     L.hydro_create_query.argtypes = [P(QueryConfig), P(vp)]
     L.hydro_add_predicate.argtypes = [vp, P(UdfDesc), f64, P(i32)]
-    L.hydro_set_margins.argtypes = [vp, i32, f64, f64]
+    L.hydro_set_margins.argtypes = [vp, i32, f64, f64, f64]
     L.hydro_set_static_order.argtypes = [vp, P(i32), i32]
     L.hydro_calibrate.argtypes = [vp, vp, i64, P(CalibInfo)]
     L.hydro_udf_scores.argtypes = [vp, i32, i32, vp, i64, vp]
@@ -202,8 +204,8 @@ class Query:
         return self._add(UDF_CNN, dims, [W for W, _ in convs], [b for _, b in convs], threshold, hw, hb,
                          cost_hint)
 
-    def set_margins(self, pred: int, lowp: float, fp32: float):
-        _check(load().hydro_set_margins(self._h, pred, float(lowp), float(fp32)), "hydro_set_margins")
+    def set_margins(self, pred: int, lowp: float, tf32: float, fp32: float):
+        _check(load().hydro_set_margins(self._h, pred, float(lowp), float(tf32), float(fp32)), "hydro_set_margins")
 
     def set_static_order(self, order):
         arr = (ctypes.c_int32 * len(order))(*order)
@@ -212,8 +214,7 @@ class Query:
     def calibrate(self, tuples) -> list:
         info = (CalibInfo * MAX_PREDICATES)()
         _check(load().hydro_calibrate(self._h, _ptr(tuples), int(tuples.shape[0]), info), "hydro_calibrate")
-        return [dict(max_err_fp32=info[i].max_err_fp32, max_err_lowp=info[i].max_err_lowp,
-                     margin_fp32=info[i].margin_fp32, margin_lowp=info[i].margin_lowp) for i in range(self.n_pred)]
+        return [{f: getattr(info[i], f) for f, _ in CalibInfo._fields_} for i in range(self.n_pred)]
 
     def udf_scores(self, pred: int, precision: str, tuples, out):
         """Scores of one predicate's UDF on device tuples into ``out`` (device float64 [n])."""
@@ -244,7 +245,8 @@ class Query:
         self._n_of.pop(batch_id, None)
         P = self.n_pred
         d = dict(n=info.n, n_pass=info.n_pass, warmup=bool(info.warmup), order=list(info.order[:P]),
-                 passed=list(info.passed[:P]), recheck_fp32=list(info.recheck_fp32[:P]),
+                 passed=list(info.passed[:P]), recheck_tf32=list(info.recheck_tf32[:P]),
+                 recheck_fp32=list(info.recheck_fp32[:P]),
                  recheck_fp64=list(info.recheck_fp64[:P]), device_ms=info.device_ms)
         return bitmap[:(n + 31) // 32], counts[:P], d
 

@@ -21,8 +21,9 @@ constexpr int kMaxPred = 8;
 struct StatRow {
     long long evaluated;
     long long passed;
-    long long recheck32;
-    long long recheck64;
+    long long recheck_tf32;   // re-evaluated by the FP32-accurate 3xTF32 tensor-core path
+    long long recheck32;      // re-evaluated in FP32 (CUDA cores)
+    long long recheck64;      // re-evaluated in FP64
 };
 
 __device__ __forceinline__ float to_f(float v) { return v; }

@@ -60,13 +60,16 @@ struct Pred {
     double head_b = 0.0;
     double threshold = 0.0;
     double margin_lowp = 0.02;
-    double margin_fp32 = -1.0;   // < 0: not set, default at finalize
+    double margin_tf32 = -1.0;   // < 0: not set, default at finalize
+    double margin_fp32 = -1.0;
     long long cost = 1;
     // device copies
     std::vector<float *> dW, db;          // as given
     std::vector<float *> dWt32;           // CNN layer l >= 1: [tap][ci][co] fp32
     std::vector<__nv_bfloat16 *> dWt16;   // CNN layer l >= 1: [tap][ci][co] bf16
-    std::vector<void *> dWtc;             // CNN layer l >= 1: tensor-core layout
+    std::vector<void *> dWtc;             // CNN layer l >= 1: tensor-core layout (bf16)
+    std::vector<void *> dWts;             // CNN layer l >= 1: tensor-core split-TF32 layout (fp32 hi, lo)
+    bool tc_all = false;                  // every layer l >= 1 has tensor-core weights
     float *dHead = nullptr;
     MlpDev mlp{};
 };
@@ -94,7 +97,7 @@ constexpr size_t kBitmapOff = kRowsOff + sizeof(StatRow) * kMaxPred;
 
 // Profiling: one record per timed launch; its item count is resolved from
 // the batch's statistics row when the batch is polled.
-enum ProfSrc { SRC_MAIN = 0, SRC_R32 = 1, SRC_R64 = 2 };
+enum ProfSrc { SRC_MAIN = 0, SRC_R32 = 1, SRC_R64 = 2, SRC_RTF = 3 };
 struct ProfCtx {
     long long batch;
     int pred;
@@ -110,9 +113,9 @@ struct ProfRec {
 };
 const char *const kProfNames[] = {"conv3x3_bf16_tc", "conv3x3_bf16_simt", "conv3x3_f32_simt", "conv3x3_f64_simt",
                                   "conv1_u8",        "pool_head",         "mlp_layer_f32",    "mlp_dot_f32",
-                                  "mlp_band_f32",    "mlp_band_f64"};
+                                  "mlp_band_f32",    "mlp_band_f64",      "conv3x3_tf32x3_tc"};
 enum { PC_CONV_TC = 0, PC_CONV_BF16, PC_CONV_F32, PC_CONV_F64, PC_CONV1, PC_POOL, PC_MLP, PC_DOT, PC_BAND32,
-       PC_BAND64, PC_N };
+       PC_BAND64, PC_CONV_TF32, PC_N };
 
 struct Prof {
     bool on = false;
@@ -136,16 +139,20 @@ struct hydro_query {
     std::vector<void *> allocs;   // device allocations to free
     // scratch
     int *alive[2] = {};
-    int *ints = nullptr;          // [0],[1]: alive counts; [2]: band1 count; [3]: band2 count
+    int *ints = nullptr;          // [0],[1]: alive counts; [2],[3],[4]: band 1, 2, 3 counts
     unsigned char *pass = nullptr, *acc = nullptr;
     float *score32 = nullptr;
+    // recheck bands: entries (position in the stage, tuple in the batch)
     int *band1_m = nullptr, *band1_t = nullptr, *band2_m = nullptr, *band2_t = nullptr;
-    int cap1 = 0, cap2 = 0;       // band capacities (entries / frames)
-    float *rscore32 = nullptr;
-    double *rscore64 = nullptr;
+    int *band3_m = nullptr, *band3_t = nullptr;
+    int cap1 = 0, cap2 = 0, cap3 = 0;   // band capacities (entries / frames)
+    float *rscore_t = nullptr;    // 3xTF32 recheck scores (band 1)
+    float *rscore32 = nullptr;    // FP32 recheck scores
+    double *rscore64 = nullptr;   // FP64 recheck scores
     void *act[2] = {};            // working precision activations
     void *ract32[2] = {};         // CNN FP32 recheck activations
     void *ract64[2] = {};         // CNN FP64 recheck activations
+    float *partials = nullptr;    // CNN BF16: fused pool+head partials [max_batch][H*W/128*4]
     StatRow *ring = nullptr, *warm = nullptr;
     int ring_len = 0;
     int *d_order = nullptr;       // [max_in_flight][8]
@@ -158,7 +165,7 @@ struct hydro_query {
     long long next_batch = 0;
     unsigned int latched_err = 0;
     // cumulative statistics (updated at poll)
-    long long tot[kMaxPred][4] = {};
+    long long tot[kMaxPred][5] = {};
     // tensor-core conv
     TcConvPlan tc{};
     // profiling and launch count
@@ -247,21 +254,29 @@ hydro_status finalize(hydro_query *q) {
     TRY(dalloc(q, &q->pass, B));
     TRY(dalloc(q, &q->acc, B));
     TRY(dalloc(q, &q->score32, sizeof(float) * B));
+    // band capacities: the FP64 level of CNN UDFs is capped at 64 frames per
+    // stage (ERR_BAND_OVERFLOW beyond), every other level holds a full batch
     q->cap1 = B;
-    q->cap2 = cnn ? std::min(B, 64) : B;
+    q->cap2 = B;
+    q->cap3 = cnn ? std::min(B, 64) : B;
     TRY(dalloc(q, &q->band1_m, sizeof(int) * q->cap1));
     TRY(dalloc(q, &q->band1_t, sizeof(int) * q->cap1));
     TRY(dalloc(q, &q->band2_m, sizeof(int) * q->cap2));
     TRY(dalloc(q, &q->band2_t, sizeof(int) * q->cap2));
-    TRY(dalloc(q, &q->rscore32, sizeof(float) * q->cap1));
-    TRY(dalloc(q, &q->rscore64, sizeof(double) * std::max(q->cap1, q->cap2)));
+    TRY(dalloc(q, &q->band3_m, sizeof(int) * q->cap3));
+    TRY(dalloc(q, &q->band3_t, sizeof(int) * q->cap3));
+    TRY(dalloc(q, &q->rscore_t, sizeof(float) * q->cap1));
+    TRY(dalloc(q, &q->rscore32, sizeof(float) * std::max(q->cap1, q->cap2)));
+    TRY(dalloc(q, &q->rscore64, sizeof(double) * std::max(q->cap1, q->cap3)));
     if (cnn) {
         const size_t px = (size_t)c.height * c.width * wmax;
         const size_t esz = c.precision == HYDRO_PREC_BF16 ? 2 : 4;
         for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->act[k], esz * px * B));
+        if (c.precision == HYDRO_PREC_BF16)   // 3xTF32 (two fp32 planes) and FP32 recheck levels
+            for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->ract32[k], 8 * px * std::max(q->cap1, q->cap2)));
+        for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->ract64[k], 8 * px * q->cap3));
         if (c.precision == HYDRO_PREC_BF16)
-            for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->ract32[k], 4 * px * q->cap1));
-        for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->ract64[k], 8 * px * q->cap2));
+            TRY(dalloc(q, &q->partials, sizeof(float) * (size_t)B * (c.height * c.width / 128) * 4));
     } else {
         for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->act[k], sizeof(float) * (size_t)wmax * B));
         CU(mlp_band_smem_setup(wmax));
@@ -308,6 +323,8 @@ hydro_status finalize(hydro_query *q) {
             p.dWt32.assign(p.n_layers, nullptr);
             p.dWt16.assign(p.n_layers, nullptr);
             p.dWtc.assign(p.n_layers, nullptr);
+            p.dWts.assign(p.n_layers, nullptr);
+            p.tc_all = c.precision == HYDRO_PREC_BF16 && p.n_layers > 1;
             for (int l = 1; l < p.n_layers; ++l) {
                 const int ci_n = p.dims[l], co_n = p.dims[l + 1];
                 std::vector<float> t32((size_t)9 * ci_n * co_n);
@@ -328,10 +345,18 @@ hydro_status finalize(hydro_query *q) {
                     __nv_bfloat16 *d = nullptr;
                     TRY(upload(q, &d, tc.data(), tc.size()));
                     p.dWtc[l] = d;
+                    std::vector<float> ts;
+                    tc_conv_pack_weights_split(p.W[l].data(), ci_n, co_n, ts);
+                    float *ds = nullptr;
+                    TRY(upload(q, &ds, ts.data(), ts.size()));
+                    p.dWts[l] = ds;
+                } else {
+                    p.tc_all = false;
                 }
             }
         }
         if (p.margin_fp32 < 0.0) p.margin_fp32 = 1e-5 * std::max(1.0, std::fabs(p.threshold));
+        if (p.margin_tf32 < 0.0) p.margin_tf32 = 5e-3 * std::max(1.0, std::fabs(p.threshold));
     }
     if (cnn && c.precision == HYDRO_PREC_BF16) {
         hydro_status s = tc_conv_init(&q->tc, c.device);
@@ -416,6 +441,33 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
     // CNN
     const int H = c.height, Wd = c.width;
     const double hw = (double)H * Wd;
+    if (prec == PREC_TF32X3) {
+        if (!p.tc_all || !q->partials) return fail(HYDRO_EUNSUPPORTED, "3xTF32 needs tensor-core CNN layers");
+        // FP32-accurate evaluation on the tensor cores (3xTF32 split form)
+        const unsigned char *frames = (const unsigned char *)tuples;
+        int e = prof_begin(q, pc, PC_CONV1, 2.0 * hw * 9 * p.dims[0] * p.dims[1], hw * (p.dims[0] + 8.0 * p.dims[1]),
+                           4.0 * 9 * p.dims[0] * p.dims[1]);
+        launch_conv1_split(count, list, frames, c.channels, H, Wd, p.dW[0], p.db[0], p.dims[1], (float *)act[0],
+                           max_rows, q->sms, q->st);
+        prof_end(q, e);
+        q->launches++;
+        int cur = 0;
+        for (int l = 1; l < p.n_layers; ++l) {
+            const bool last = l + 1 == p.n_layers;
+            e = prof_begin(q, pc, PC_CONV_TF32, 2.0 * hw * 9 * p.dims[l] * p.dims[l + 1],
+                           hw * 8.0 * (p.dims[l] + (last ? 0 : p.dims[l + 1])), 8.0 * 9 * p.dims[l] * p.dims[l + 1]);
+            hydro_status rs = tc_conv_run(&q->tc, count, act[cur], p.dims[l], H, Wd, p.dWts[l], p.db[l],
+                                          p.dims[l + 1], act[1 - cur], max_rows, q->sms, q->st, q->d_err,
+                                          last ? p.dHead : nullptr, last ? q->partials : nullptr, true);
+            prof_end(q, e);
+            if (rs != HYDRO_OK) return fail(rs, "tensor-core conv (split): %s", tc_conv_last_error());
+            q->launches++;
+            cur = 1 - cur;
+        }
+        tc_head_finalize(count, q->partials, H * Wd / 128 * 4, p.head_b, H * Wd, score32, max_rows, q->sms, q->st);
+        q->launches++;
+        return HYDRO_OK;
+    }
     const double esz = prec == PREC_F64 ? 8.0 : prec == PREC_F32 ? 4.0 : 2.0;
     const unsigned char *frames = (const unsigned char *)tuples;
     int e = prof_begin(q, pc, PC_CONV1, 2.0 * hw * 9 * p.dims[0] * p.dims[1], hw * (p.dims[0] + esz * p.dims[1]),
@@ -425,16 +477,21 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
     prof_end(q, e);
     q->launches++;
     int cur = 0;
+    bool fused_head = false;
     for (int l = 1; l < p.n_layers; ++l) {
         const double fpi = 2.0 * hw * 9 * p.dims[l] * p.dims[l + 1];
         const double bpi = hw * esz * (p.dims[l] + p.dims[l + 1]);
         const double wb = 9.0 * p.dims[l] * p.dims[l + 1] * (prec == PREC_BF16 ? 2.0 : 4.0);
         if (prec == PREC_BF16 && p.dWtc[l]) {
-            e = prof_begin(q, pc, PC_CONV_TC, fpi, bpi, wb);
+            // the last layer folds pooling + head into its epilogue
+            const bool last = l + 1 == p.n_layers && q->partials != nullptr;
+            e = prof_begin(q, pc, PC_CONV_TC, fpi, last ? hw * esz * p.dims[l] : bpi, wb);
             hydro_status rs = tc_conv_run(&q->tc, count, act[cur], p.dims[l], H, Wd, p.dWtc[l], p.db[l],
-                                          p.dims[l + 1], act[1 - cur], max_rows, q->sms, st, q->d_err);
+                                          p.dims[l + 1], act[1 - cur], max_rows, q->sms, st, q->d_err,
+                                          last ? p.dHead : nullptr, last ? q->partials : nullptr);
             prof_end(q, e);
             if (rs != HYDRO_OK) return fail(rs, "tensor-core conv: %s", tc_conv_last_error());
+            fused_head = last;
         } else {
             const int cls = prec == PREC_BF16 ? PC_CONV_BF16 : prec == PREC_F32 ? PC_CONV_F32 : PC_CONV_F64;
             e = prof_begin(q, pc, cls, fpi, bpi, wb);
@@ -446,6 +503,11 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
         q->launches++;
         cur = 1 - cur;
     }
+    if (fused_head) {
+        tc_head_finalize(count, q->partials, H * Wd / 128 * 4, p.head_b, H * Wd, score32, max_rows, q->sms, st);
+        q->launches++;
+        return HYDRO_OK;
+    }
     void *score = prec == PREC_F64 ? (void *)score64 : (void *)score32;
     const int CL = p.dims[p.n_layers];
     e = prof_begin(q, pc, PC_POOL, 2.0 * hw * CL, hw * esz * CL, 4.0 * CL);
@@ -456,58 +518,78 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
 }
 
 // One stage: evaluate predicate p on the alive list (in_list, in_count),
-// decide pass/fail exactly (working precision, then the recheck cascade) and
-// close the stage.
+// decide pass/fail exactly and close the stage.  Scores within a level's
+// margin of the threshold go to the next level of the cascade:
+//   BF16 query, CNN UDF: BF16 tensor cores -> 3xTF32 tensor cores -> FP32 CUDA cores -> FP64
+//   BF16 query, MLP UDF: (not built)
+//   FP32 query:          FP32 -> FP64
 hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *in_list, int *out_list,
                        int *out_count, bool eval_all, const void *tuples, int n, long long batch, Slot &slot) {
     const hydro_query_config &c = q->cfg;
     const Pred &p = q->preds[pi];
     const bool bf16 = c.precision == HYDRO_PREC_BF16;
+    const bool cnn = p.kind == HYDRO_UDF_CNN;
+    const bool tf32_level = bf16 && cnn && p.tc_all && q->partials;
     const int wprec = bf16 ? PREC_BF16 : PREC_F32;
-    int *band1_count = q->ints + 2, *band2_count = q->ints + 3;
-    const ProfCtx pc_main{batch, pi, SRC_MAIN}, pc_r32{batch, pi, SRC_R32}, pc_r64{batch, pi, SRC_R64};
+    int *band1_count = q->ints + 2, *band2_count = q->ints + 3, *band3_count = q->ints + 4;
+    const ProfCtx pc_main{batch, pi, SRC_MAIN}, pc_rtf{batch, pi, SRC_RTF}, pc_r32{batch, pi, SRC_R32},
+        pc_r64{batch, pi, SRC_R64};
     TRY(run_udf(q, p, wprec, in_count, in_list, tuples, std::max(n, 1), q->act, q->score32, nullptr, &pc_main));
-    // FP32 mode sends its band straight to FP64 (capacity cap2); BF16 mode
-    // sends it to FP32 (capacity cap1) and from there to FP64.
+
+    // level 0 -> band 1 (FP32 queries: band 1 is the FP64 band, capacity cap3)
     launch_classify_f32(in_count, in_list, q->score32, p.threshold, bf16 ? p.margin_lowp : p.margin_fp32, q->pass,
-                        q->band1_m, q->band1_t, band1_count, bf16 ? q->cap1 : q->cap2, q->d_err, q->st);
+                        q->band1_m, q->band1_t, band1_count, bf16 ? q->cap1 : q->cap3, q->d_err, q->st);
     q->launches++;
-    const int *fp64_count = band1_count;
-    const int *fp64_m = q->band1_m, *fp64_t = q->band1_t;
+    const int *cnt_tf = nullptr, *cnt_32 = nullptr;
+    const int *b64_count = band1_count, *b64_m = q->band1_m, *b64_t = q->band1_t;
     if (bf16) {
-        if (p.kind == HYDRO_UDF_MLP) {
+        // FP32-level input: band 1 directly, or what 3xTF32 leaves undecided
+        const int *b32_count = band1_count, *b32_m = q->band1_m, *b32_t = q->band1_t;
+        if (tf32_level) {
+            TRY(run_udf(q, p, PREC_TF32X3, band1_count, q->band1_t, tuples, q->cap1, q->ract32, q->rscore_t,
+                        nullptr, &pc_rtf));
+            launch_recheck_classify_f32(band1_count, q->band1_m, q->band1_t, q->rscore_t, p.threshold,
+                                        p.margin_tf32, q->pass, q->band2_m, q->band2_t, band2_count, q->cap2,
+                                        q->d_err, q->st);
+            q->launches++;
+            cnt_tf = band1_count;
+            b32_count = band2_count;
+            b32_m = q->band2_m;
+            b32_t = q->band2_t;
+        }
+        if (!cnn) {
             const int e = prof_begin(q, &pc_r32, PC_BAND32, (double)p.cost, 4.0 * c.dim, 0);
-            launch_mlp_band_f32(band1_count, q->band1_t, (const float *)tuples, c.dim, p.mlp, q->rscore32, q->sms,
-                                q->st);
+            launch_mlp_band_f32(b32_count, b32_t, (const float *)tuples, c.dim, p.mlp, q->rscore32, q->sms, q->st);
             prof_end(q, e);
             q->launches++;
         } else {
-            TRY(run_udf(q, p, PREC_F32, band1_count, q->band1_t, tuples, q->cap1, q->ract32, q->rscore32, nullptr,
-                        &pc_r32));
+            TRY(run_udf(q, p, PREC_F32, b32_count, b32_t, tuples, tf32_level ? q->cap2 : q->cap1, q->ract32,
+                        q->rscore32, nullptr, &pc_r32));
         }
+        launch_recheck_classify_f32(b32_count, b32_m, b32_t, q->rscore32, p.threshold, p.margin_fp32, q->pass,
+                                    q->band3_m, q->band3_t, band3_count, q->cap3, q->d_err, q->st);
         q->launches++;
-        launch_recheck_classify_f32(band1_count, q->band1_m, q->band1_t, q->rscore32, p.threshold, p.margin_fp32,
-                                    q->pass, q->band2_m, q->band2_t, band2_count, q->cap2, q->d_err, q->st);
-        fp64_count = band2_count;
-        fp64_m = q->band2_m;
-        fp64_t = q->band2_t;
+        cnt_32 = b32_count;
+        b64_count = band3_count;
+        b64_m = q->band3_m;
+        b64_t = q->band3_t;
     }
-    if (p.kind == HYDRO_UDF_MLP) {
+    if (!cnn) {
         const int e = prof_begin(q, &pc_r64, PC_BAND64, (double)p.cost, 4.0 * c.dim, 0);
-        launch_mlp_band_f64(fp64_count, fp64_t, (const float *)tuples, c.dim, p.mlp, q->rscore64, q->sms, q->st);
+        launch_mlp_band_f64(b64_count, b64_t, (const float *)tuples, c.dim, p.mlp, q->rscore64, q->sms, q->st);
         prof_end(q, e);
         q->launches++;
     } else {
-        TRY(run_udf(q, p, PREC_F64, fp64_count, fp64_t, tuples, q->cap2, q->ract64, nullptr, q->rscore64, &pc_r64));
+        TRY(run_udf(q, p, PREC_F64, b64_count, b64_t, tuples, q->cap3, q->ract64, nullptr, q->rscore64, &pc_r64));
     }
-    launch_recheck_classify_f64(fp64_count, fp64_m, fp64_t, q->rscore64, p.threshold, q->pass, q->d_err, q->st);
+    launch_recheck_classify_f64(b64_count, b64_m, b64_t, q->rscore64, p.threshold, q->pass, q->d_err, q->st);
     q->launches += 2;   // recheck classify + compact
     StatRow *row = q->ring + (batch % q->ring_len) * kMaxPred + pi;
     StatRow *rrow = (StatRow *)(slot.dres + kRowsOff) + pi;
     StatRow *warm = nullptr;
     if (adaptive(c.policy) && batch < c.warmup_batches) warm = q->warm + batch * kMaxPred + pi;
-    launch_compact(in_count, in_list, q->pass, out_list, out_count, eval_all ? q->acc : nullptr,
-                   bf16 ? band1_count : nullptr, fp64_count, row, rrow, warm, q->st);
+    launch_compact(in_count, in_list, q->pass, out_list, out_count, eval_all ? q->acc : nullptr, cnt_tf, cnt_32,
+                   b64_count, row, rrow, warm, q->st);
     return HYDRO_OK;
 }
 
@@ -654,13 +736,16 @@ hydro_status hydro_add_predicate(hydro_query *q, const hydro_udf_desc *udf, doub
     return HYDRO_OK;
 }
 
-hydro_status hydro_set_margins(hydro_query *q, int32_t pred, double margin_lowp, double margin_fp32) {
+hydro_status hydro_set_margins(hydro_query *q, int32_t pred, double margin_lowp, double margin_tf32,
+                               double margin_fp32) {
     g_err.clear();
     TRY(check_query(q));
     if (pred < 0 || pred >= (int)q->preds.size()) return fail(HYDRO_EINVAL, "unknown predicate");
     if (q->next_batch > 0) return fail(HYDRO_ESTATE, "margins are fixed after the first submit");
-    if (!(margin_lowp >= 0.0) || !(margin_fp32 >= 0.0)) return fail(HYDRO_EINVAL, "margins must be >= 0");
+    if (!(margin_lowp >= 0.0) || !(margin_tf32 >= 0.0) || !(margin_fp32 >= 0.0))
+        return fail(HYDRO_EINVAL, "margins must be >= 0");
     q->preds[pred].margin_lowp = margin_lowp;
+    q->preds[pred].margin_tf32 = margin_tf32;
     q->preds[pred].margin_fp32 = margin_fp32;
     return HYDRO_OK;
 }
@@ -684,19 +769,20 @@ hydro_status hydro_udf_scores(hydro_query *q, int32_t pred, int32_t prec, const 
     TRY(check_query(q));
     if (pred < 0 || pred >= (int)q->preds.size()) return fail(HYDRO_EINVAL, "unknown predicate");
     if (n < 0 || (n > 0 && (!d_tuples || !d_scores))) return fail(HYDRO_EINVAL, "bad tuples/scores");
-    if (prec != HYDRO_PREC_FP32 && prec != HYDRO_PREC_FP64 && prec != HYDRO_PREC_BF16)
+    if (prec != HYDRO_PREC_FP32 && prec != HYDRO_PREC_FP64 && prec != HYDRO_PREC_BF16 && prec != HYDRO_PREC_TF32X3)
         return fail(HYDRO_EINVAL, "unknown precision");
-    if (prec == HYDRO_PREC_BF16 && q->cfg.precision != HYDRO_PREC_BF16)
-        return fail(HYDRO_EINVAL, "BF16 scores need a BF16 query");
+    if ((prec == HYDRO_PREC_BF16 || prec == HYDRO_PREC_TF32X3) && q->cfg.precision != HYDRO_PREC_BF16)
+        return fail(HYDRO_EINVAL, "BF16 and 3xTF32 scores need a BF16 query");
     CU(cudaSetDevice(q->cfg.device));
     TRY(finalize(q));
     const Pred &p = q->preds[pred];
+    if (prec == HYDRO_PREC_TF32X3 && !p.tc_all) return fail(HYDRO_EINVAL, "3xTF32 scores need a tensor-core CNN UDF");
     const int B = q->cfg.max_batch;
     const bool cnn = p.kind == HYDRO_UDF_CNN;
+    const bool recheck_buf = cnn && q->cfg.precision == HYDRO_PREC_BF16 &&
+                             (prec == HYDRO_PREC_FP32 || prec == HYDRO_PREC_TF32X3);
     int *list = q->alive[0], *count = q->ints + 0;
-    const int chunk = (prec == HYDRO_PREC_FP64 && cnn) ? q->cap2
-                      : (prec == HYDRO_PREC_FP32 && cnn && q->cfg.precision == HYDRO_PREC_BF16) ? q->cap1
-                                                                                              : B;
+    const int chunk = (prec == HYDRO_PREC_FP64 && cnn) ? q->cap3 : recheck_buf ? std::min(q->cap1, q->cap2) : B;
     const size_t tb = (size_t)tuple_bytes(q->cfg);
     for (int64_t s = 0; s < n; s += chunk) {
         const int m = (int)std::min<int64_t>(chunk, n - s);
@@ -705,10 +791,9 @@ hydro_status hydro_udf_scores(hydro_query *q, int32_t pred, int32_t prec, const 
         if (prec == HYDRO_PREC_FP64) {
             TRY(run_udf(q, p, PREC_F64, count, list, base, m, cnn ? q->ract64 : q->act, nullptr, d_scores + s));
         } else {
-            void *const *act = q->act;
-            if (prec == HYDRO_PREC_FP32 && cnn && q->cfg.precision == HYDRO_PREC_BF16) act = q->ract32;
-            TRY(run_udf(q, p, prec == HYDRO_PREC_BF16 ? PREC_BF16 : PREC_F32, count, list, base, m, act,
-                        q->score32, nullptr));
+            void *const *act = recheck_buf ? q->ract32 : q->act;
+            const int ip = prec == HYDRO_PREC_BF16 ? PREC_BF16 : prec == HYDRO_PREC_TF32X3 ? PREC_TF32X3 : PREC_F32;
+            TRY(run_udf(q, p, ip, count, list, base, m, act, q->score32, nullptr));
             launch_f32_to_f64(q->score32, d_scores + s, m, q->st);
         }
         CU(cudaGetLastError());
@@ -727,35 +812,43 @@ hydro_status hydro_calibrate(hydro_query *q, const void *d_tuples, int64_t n, hy
     if (q->next_batch > 0) return fail(HYDRO_ESTATE, "calibrate before the first submit");
     double *d = nullptr;
     CU(cudaSetDevice(q->cfg.device));
-    CU(cudaMalloc(&d, sizeof(double) * n * 3));
-    std::vector<double> s64(n), s32(n), s16(n);
+    TRY(finalize(q));
+    CU(cudaMalloc(&d, sizeof(double) * n * 4));
+    std::vector<double> s64(n), s32(n), s16(n), stf(n);
     hydro_status rc = HYDRO_OK;
+    const bool bf = q->cfg.precision == HYDRO_PREC_BF16;
     for (int i = 0; i < (int)q->preds.size() && rc == HYDRO_OK; ++i) {
+        const bool tf = bf && q->preds[i].tc_all;
         rc = hydro_udf_scores(q, i, HYDRO_PREC_FP64, d_tuples, n, d);
         if (rc == HYDRO_OK) rc = hydro_udf_scores(q, i, HYDRO_PREC_FP32, d_tuples, n, d + n);
-        const bool bf = q->cfg.precision == HYDRO_PREC_BF16;
         if (rc == HYDRO_OK && bf) rc = hydro_udf_scores(q, i, HYDRO_PREC_BF16, d_tuples, n, d + 2 * n);
+        if (rc == HYDRO_OK && tf) rc = hydro_udf_scores(q, i, HYDRO_PREC_TF32X3, d_tuples, n, d + 3 * n);
         if (rc != HYDRO_OK) break;
         if (cudaMemcpy(s64.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(s32.data(), d + n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            (bf && cudaMemcpy(s16.data(), d + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)) {
+            (bf && cudaMemcpy(s16.data(), d + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+            (tf && cudaMemcpy(stf.data(), d + 3 * n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)) {
             rc = fail(HYDRO_ECUDA, "copy of calibration scores failed");
             break;
         }
-        double e32 = 0, e16 = 0, smax = 0;
+        double e32 = 0, e16 = 0, etf = 0, smax = 0;
         for (int64_t k = 0; k < n; ++k) {
             e32 = std::max(e32, std::fabs(s32[k] - s64[k]));
             if (bf) e16 = std::max(e16, std::fabs(s16[k] - s64[k]));
+            if (tf) etf = std::max(etf, std::fabs(stf[k] - s64[k]));
             smax = std::max(smax, std::fabs(s64[k]));
         }
         Pred &p = q->preds[i];
         p.margin_fp32 = std::max(16.0 * e32, 1e-9 * smax);
+        if (tf) p.margin_tf32 = std::max(8.0 * etf, 1e-9 * smax);
         if (bf && p.margin_lowp < 4.0 * e16) p.margin_lowp = 4.0 * e16;
         if (info) {
             info[i].max_err_fp32 = e32;
             info[i].max_err_lowp = e16;
+            info[i].max_err_tf32 = etf;
             info[i].margin_fp32 = p.margin_fp32;
             info[i].margin_lowp = p.margin_lowp;
+            info[i].margin_tf32 = p.margin_tf32;
         }
     }
     cudaFree(d);
@@ -896,6 +989,7 @@ hydro_status hydro_poll_result(hydro_query *q, int64_t batch_id, uint32_t *pass_
         q->tot[i][1] += rows[i].passed;
         q->tot[i][2] += rows[i].recheck32;
         q->tot[i][3] += rows[i].recheck64;
+        q->tot[i][4] += rows[i].recheck_tf32;
     }
     if (info) {
         std::memset(info, 0, sizeof *info);
@@ -906,6 +1000,7 @@ hydro_status hydro_poll_result(hydro_query *q, int64_t batch_id, uint32_t *pass_
         for (int i = 0; i < P; ++i) {
             info->order[i] = slot->order[i];
             info->passed[i] = rows[i].passed;
+            info->recheck_tf32[i] = rows[i].recheck_tf32;
             info->recheck_fp32[i] = rows[i].recheck32;
             info->recheck_fp64[i] = rows[i].recheck64;
         }
@@ -924,10 +1019,13 @@ hydro_status hydro_get_stats(hydro_query *q, hydro_pred_stats *out, int32_t n) {
     for (int i = 0; i < n; ++i) {
         out[i].evaluated = q->tot[i][0];
         out[i].passed = q->tot[i][1];
+        out[i].recheck_tf32 = q->tot[i][4];
         out[i].recheck_fp32 = q->tot[i][2];
         out[i].recheck_fp64 = q->tot[i][3];
         out[i].model_cost = q->preds[i].cost;
         out[i].margin_lowp = q->preds[i].margin_lowp;
+        out[i].margin_tf32 = q->preds[i].margin_tf32 >= 0 ? q->preds[i].margin_tf32
+                                                         : 5e-3 * std::max(1.0, std::fabs(q->preds[i].threshold));
         out[i].margin_fp32 = q->preds[i].margin_fp32 >= 0 ? q->preds[i].margin_fp32
                                                          : 1e-5 * std::max(1.0, std::fabs(q->preds[i].threshold));
     }
@@ -957,7 +1055,10 @@ hydro_status hydro_profile_read(hydro_query *q, hydro_kernel_profile *out, int32
         const long long k = r.batch - q->prof.base;
         if (k < 0 || k >= (long long)q->prof.rows.size() || q->prof.rows[k].empty()) continue;   // not polled
         const StatRow &row = q->prof.rows[k][r.pred];
-        const long long items = r.src == SRC_MAIN ? row.evaluated : r.src == SRC_R32 ? row.recheck32 : row.recheck64;
+        const long long items = r.src == SRC_MAIN  ? row.evaluated
+                                : r.src == SRC_RTF ? row.recheck_tf32
+                                : r.src == SRC_R32 ? row.recheck32
+                                                   : row.recheck64;
         float t = 0.f;
         if (cudaEventElapsedTime(&t, q->prof.ev[r.ev], q->prof.ev[r.ev + 1]) != cudaSuccess) {
             cudaGetLastError();

@@ -9,7 +9,7 @@ namespace hydro {
 
 struct StatRow;
 
-enum { PREC_F32 = 0, PREC_BF16 = 1, PREC_F64 = 2 };
+enum { PREC_F32 = 0, PREC_BF16 = 1, PREC_F64 = 2, PREC_TF32X3 = 3 };
 
 constexpr int kMaxLayers = 16;
 
@@ -39,8 +39,8 @@ void launch_recheck_classify_f64(const int *band_count_in, const int *band_m_in,
                                  const double *scores_r, double t, unsigned char *pass, unsigned int *err,
                                  cudaStream_t st);
 void launch_compact(const int *count_in, const int *alive_in, const unsigned char *pass, int *alive_out,
-                    int *count_out, unsigned char *acc, const int *band32_count, const int *band64_count,
-                    StatRow *row, StatRow *rrow, StatRow *warm, cudaStream_t st);
+                    int *count_out, unsigned char *acc, const int *bandt_count, const int *band32_count,
+                    const int *band64_count, StatRow *row, StatRow *rrow, StatRow *warm, cudaStream_t st);
 void launch_acc_to_alive(const unsigned char *acc, int n, int *alive_out, int *count_out, cudaStream_t st);
 void launch_result(const int *count, const int *alive, int n, unsigned int *bitmap, long long *n_pass,
                    cudaStream_t st);
@@ -61,6 +61,10 @@ cudaError_t mlp_band_smem_setup(int max_width);
 void launch_conv1(int prec, const int *count, const int *list, const unsigned char *frames, int C0, int H,
                   int Wd, const float *W, const float *bias, int Cout, void *out, int max_frames, int sms,
                   cudaStream_t st);
+// First conv layer in the FP32-accurate split form [hi(Cout) | lo(Cout)] fp32.
+void launch_conv1_split(const int *count, const int *list, const unsigned char *frames, int C0, int H, int Wd,
+                        const float *W, const float *bias, int Cout, float *out, int max_frames, int sms,
+                        cudaStream_t st);
 void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,
                          const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st);
 void launch_pool_head(int prec, const int *count, const void *act, int HW, int C, const float *hw, double hb,

@@ -123,8 +123,8 @@ k_recheck_classify(const int *band_count_in, const int *band_m_in, const int *ba
 // batch's result block; warm: the warmup copy (nullable).
 __global__ void __launch_bounds__(kScanThreads)
 k_compact(const int *count_in, const int *alive_in, const unsigned char *pass, int *alive_out,
-          int *count_out, unsigned char *acc, const int *band32_count, const int *band64_count,
-          StatRow *row, StatRow *rrow, StatRow *warm) {
+          int *count_out, unsigned char *acc, const int *bandt_count, const int *band32_count,
+          const int *band64_count, StatRow *row, StatRow *rrow, StatRow *warm) {
     const int n = *count_in;
     int base = 0;
     for (int m0 = 0; m0 < n; m0 += kScanThreads) {
@@ -144,6 +144,7 @@ k_compact(const int *count_in, const int *alive_in, const unsigned char *pass, i
         StatRow r;
         r.evaluated = n;
         r.passed = base;
+        r.recheck_tf32 = bandt_count ? *bandt_count : 0;
         r.recheck32 = band32_count ? *band32_count : 0;
         r.recheck64 = band64_count ? *band64_count : 0;
         *row = r;
@@ -263,9 +264,9 @@ void launch_recheck_classify_f64(const int *band_count_in, const int *band_m_in,
 }
 
 void launch_compact(const int *count_in, const int *alive_in, const unsigned char *pass, int *alive_out,
-                    int *count_out, unsigned char *acc, const int *band32_count, const int *band64_count,
-                    StatRow *row, StatRow *rrow, StatRow *warm, cudaStream_t st) {
-    k_compact<<<1, kScanThreads, 0, st>>>(count_in, alive_in, pass, alive_out, count_out, acc,
+                    int *count_out, unsigned char *acc, const int *bandt_count, const int *band32_count,
+                    const int *band64_count, StatRow *row, StatRow *rrow, StatRow *warm, cudaStream_t st) {
+    k_compact<<<1, kScanThreads, 0, st>>>(count_in, alive_in, pass, alive_out, count_out, acc, bandt_count,
                                           band32_count, band64_count, row, rrow, warm);
 }
 

@@ -134,10 +134,68 @@ k_mlp_band(const int *band_count, const int *band_tuple, const float *X, int ldx
 
 // ---------------------------------------------------------------- CNN
 
+// relu(acc) for COUT channels stored as 16-byte vectors (COUT * sizeof(Tout)
+// is a multiple of 16 and o is aligned to it).
+template <typename T, typename Tout, int COUT>
+__device__ __forceinline__ void store_relu_row(const T (&acc)[COUT], Tout *o) {
+    if constexpr (sizeof(Tout) == 2) {
+        uint32_t pk[COUT / 2];
+#pragma unroll
+        for (int j = 0; j < COUT / 2; ++j) {
+            const float a = acc[2 * j] > 0 ? (float)acc[2 * j] : 0.f;
+            const float b = acc[2 * j + 1] > 0 ? (float)acc[2 * j + 1] : 0.f;
+            const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+            pk[j] = *reinterpret_cast<const uint32_t *>(&v);
+        }
+        uint4 *d = reinterpret_cast<uint4 *>(o);
+#pragma unroll
+        for (int j = 0; j < COUT / 8; ++j) d[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+    } else if constexpr (sizeof(Tout) == 4) {
+        float4 *d = reinterpret_cast<float4 *>(o);
+#pragma unroll
+        for (int j = 0; j < COUT / 4; ++j) {
+            float4 v;
+            v.x = acc[4 * j] > 0 ? (float)acc[4 * j] : 0.f;
+            v.y = acc[4 * j + 1] > 0 ? (float)acc[4 * j + 1] : 0.f;
+            v.z = acc[4 * j + 2] > 0 ? (float)acc[4 * j + 2] : 0.f;
+            v.w = acc[4 * j + 3] > 0 ? (float)acc[4 * j + 3] : 0.f;
+            d[j] = v;
+        }
+    } else {
+        double2 *d = reinterpret_cast<double2 *>(o);
+#pragma unroll
+        for (int j = 0; j < COUT / 2; ++j) {
+            double2 v;
+            v.x = acc[2 * j] > 0 ? (double)acc[2 * j] : 0.0;
+            v.y = acc[2 * j + 1] > 0 ? (double)acc[2 * j + 1] : 0.0;
+            d[j] = v;
+        }
+    }
+}
+
+// relu(acc) for COUT channels in the FP32-accurate split form the tensor-core
+// kernel reads: [hi(COUT) | lo(COUT)], hi = value with the low 13 mantissa
+// bits cleared (a TF32 number), lo = value - hi (exact).
+template <int COUT>
+__device__ __forceinline__ void store_relu_row_split(const float (&acc)[COUT], float *o) {
+#pragma unroll
+    for (int j = 0; j < COUT; j += 4) {
+        float hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float v = acc[j + e] > 0.f ? acc[j + e] : 0.f;
+            hi[e] = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+            lo[e] = v - hi[e];
+        }
+        *reinterpret_cast<float4 *>(o + j) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<float4 *>(o + COUT + j) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    }
+}
+
 // First conv layer straight from the uint8 CHW frames (gathered through
 // `list`): out[m][p][co] = relu(b[co] + sum_{ci,ky,kx} W * x/255), NHWC.
 // One thread per output pixel computes all COUT channels.
-template <typename T, typename Tout, int COUT>
+template <typename T, typename Tout, int COUT, bool SPLIT = false>
 __global__ void __launch_bounds__(256)
 k_conv1_u8(const int *count, const int *list, const unsigned char *frames, int C0, int H, int Wd,
            const float *W, const float *bias, Tout *out) {
@@ -174,11 +232,10 @@ k_conv1_u8(const int *count, const int *list, const unsigned char *frames, int C
 #pragma unroll
                     for (int co = 0; co < COUT; ++co) acc[co] += wr[co] * v;
                 }
-        Tout *o = out + ((size_t)m * HW + p) * COUT;
-#pragma unroll
-        for (int co = 0; co < COUT; ++co) {
-            T v = acc[co] < (T)0 ? (T)0 : acc[co];
-            o[co] = (Tout)v;
+        if constexpr (SPLIT) {
+            store_relu_row_split<COUT>(acc, out + ((size_t)m * HW + p) * (2 * COUT));
+        } else {
+            store_relu_row<T, Tout, COUT>(acc, out + ((size_t)m * HW + p) * COUT);
         }
     }
 }
@@ -352,6 +409,19 @@ void launch_conv1(int prec, const int *count, const int *list, const unsigned ch
     else
         conv1_dispatch<float, __nv_bfloat16>(count, list, frames, C0, H, Wd, W, bias, Cout,
                                              (__nv_bfloat16 *)out, grid, st);
+}
+
+void launch_conv1_split(const int *count, const int *list, const unsigned char *frames, int C0, int H, int Wd,
+                        const float *W, const float *bias, int Cout, float *out, int max_frames, int sms,
+                        cudaStream_t st) {
+    const int work = max_frames * ((H * Wd + 255) / 256);
+    int grid = work < grid_for(sms, 8) ? work : grid_for(sms, 8);
+    if (grid < 1) grid = 1;
+    switch (Cout) {
+        case 16: k_conv1_u8<float, float, 16, true><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
+        case 32: k_conv1_u8<float, float, 32, true><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
+        default: k_conv1_u8<float, float, 64, true><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
+    }
 }
 
 void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,

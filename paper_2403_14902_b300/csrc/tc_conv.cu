@@ -154,25 +154,49 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-template <int CC, int N, int S>
+// SPLIT: FP32-accurate variant.  Activations and weights are fp32 values
+// split into a high TF32 part (low 13 mantissa bits cleared) and the exact
+// fp32 remainder; the MMA (kind::tf32) accumulates hi*hi + hi*lo + lo*hi,
+// which keeps about 21 significant bits per product (3xTF32).
+template <int CC, int N, int S, bool SPLIT>
 struct TcCfg {
-    static constexpr int ROWB = CC * 2;                 // bytes of one pixel's K chunk
-    static constexpr int A_BYTES = 4 * 64 * ROWB;       // 4 image rows x 64 pixels
-    static constexpr int B_TAP = N * ROWB;              // one tap's weights
+    static constexpr int ESZ = SPLIT ? 4 : 2;             // operand bytes
+    static constexpr int ROWB = CC * ESZ;                 // bytes of one pixel's K chunk
+    static constexpr int A_BYTES = 4 * 64 * ROWB;         // 4 image rows x 64 pixels
+    static constexpr int B_TAP = N * ROWB;                // one tap's weights
     static constexpr int B_BYTES = 3 * B_TAP;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr uint32_t SWZ = CC == 64 ? 2u : 4u;  // 128B or 64B swizzle
-    static constexpr uint32_t SBO = 8 * ROWB;            // 8-row group stride
+    static constexpr uint32_t SWZ = ROWB == 128 ? 2u : 4u;  // 128B or 64B swizzle
+    static constexpr uint32_t SBO = 8 * ROWB;              // 8-row group stride
     static constexpr int TMEM_COLS = 2 * N;
+    static constexpr int PASSES = SPLIT ? 3 : 1;
     static constexpr int SMEM = S * STAGE + 1024 /*align*/ + 256 /*barriers*/;
 };
 
-template <int CC, int N, int S>
+// Instruction descriptor, kind::tf32: FP32 accumulate, TF32 A and B (format
+// code 2), both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+
+template <int CC, int N, int S, bool SPLIT>
 __global__ void __launch_bounds__(192, 1)
 k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const int *count,
-             int nchunks, int tiles_per_frame, int HW, const float *__restrict__ bias, __nv_bfloat16 *out,
-             unsigned int *err) {
-    using C = TcCfg<CC, N, S>;
+             int nchunks, int cin, int tiles_per_frame, int HW, const float *__restrict__ bias, void *out,
+             const float *__restrict__ head_w, float *partials, unsigned int *err) {
+    using C = TcCfg<CC, N, S, SPLIT>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * C::STAGE);
@@ -184,7 +208,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int total = (*count) * tiles_per_frame;
-    const int ksteps = nchunks * 3;
+    const int ksteps = C::PASSES * nchunks * 3;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -219,16 +243,19 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 const int m = t / tiles_per_frame;
                 const int y0 = (t % tiles_per_frame) * 2;
+                for (int ps = 0; ps < C::PASSES && ok; ++ps)
                 for (int c = 0; c < nchunks && ok; ++c)
                     for (int kx = 0; kx < 3 && ok; ++kx) {
                         if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
                             ok = false;
                             break;
                         }
+                        // passes of the split form: (A hi, B hi), (A hi, B lo), (A lo, B hi)
+                        const int pa = ps == 2 ? 1 : 0, pb = ps == 1 ? 1 : 0;
                         unsigned char *sa = smem + s * C::STAGE;
                         mbar_expect_tx(&full[s], (uint32_t)C::STAGE);
-                        tma_load_4d(sa, &tmA, &full[s], c * CC, kx - 1, y0 - 1, m);
-                        tma_load_3d(sa + C::A_BYTES, &tmB, &full[s], 0, 0, (c * 3 + kx) * 3);
+                        tma_load_4d(sa, &tmA, &full[s], pa * cin + c * CC, kx - 1, y0 - 1, m);
+                        tma_load_3d(sa + C::A_BYTES, &tmB, &full[s], 0, 0, ((pb * nchunks + c) * 3 + kx) * 3);
                         issued |= 1u << s;
                         last_par = (last_par & ~(1u << s)) | (ph << s);
                         if (++s == S) {
@@ -248,7 +275,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer
-            constexpr uint32_t idesc = idesc_bf16(128, N);
+            constexpr uint32_t idesc = SPLIT ? idesc_tf32(128, N) : idesc_bf16(128, N);
             int s = 0;
             uint32_t ph = 0;
             int tl = 0;
@@ -273,10 +300,13 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 #pragma unroll
                     for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-                        for (int kk = 0; kk < CC / 16; ++kk) {
+                        for (int kk = 0; kk < C::ROWB / 32; ++kk) {
                             const uint64_t ad = smem_desc(sa + ky * 64 * C::ROWB + kk * 32, C::SBO, C::SWZ);
                             const uint64_t bd = smem_desc(sb + ky * C::B_TAP + kk * 32, C::SBO, C::SWZ);
-                            mma_bf16(dt, ad, bd, idesc, (k | ky | kk) != 0);
+                            if constexpr (SPLIT)
+                                mma_tf32(dt, ad, bd, idesc, (k | ky | kk) != 0);
+                            else
+                                mma_bf16(dt, ad, bd, idesc, (k | ky | kk) != 0);
                         }
                     mma_commit(&empty[s]);
                     if (++s == S) {
@@ -303,24 +333,69 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             tc_fence_after();
             const int m = t / tiles_per_frame;
             const int p0 = (t % tiles_per_frame) * 128;
-            __nv_bfloat16 *o = out + ((size_t)m * HW + p0 + row) * N;
+            if (head_w) {
+                // last layer of the UDF: fold global average pooling and the
+                // linear head into the epilogue; each warp leaves one partial
+                // sum of hw . relu(conv) over its 32 pixels
+                float hsum = 0.f;
 #pragma unroll
-            for (int c0 = 0; c0 < N; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * N + c0), r);
-                tmem_ld_wait();
-                uint32_t pk[16];
+                for (int c0 = 0; c0 < N; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * N + c0), r);
+                    tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    float v0 = __uint_as_float(r[2 * j]) + __ldg(bias + c0 + 2 * j);
-                    float v1 = __uint_as_float(r[2 * j + 1]) + __ldg(bias + c0 + 2 * j + 1);
-                    v0 = v0 > 0.f ? v0 : 0.f;
-                    v1 = v1 > 0.f ? v1 : 0.f;
-                    pk[j] = pack_bf16x2(v0, v1);
+                    for (int j = 0; j < 32; ++j) {
+                        float v = __uint_as_float(r[j]) + __ldg(bias + c0 + j);
+                        v = v > 0.f ? v : 0.f;
+                        hsum = fmaf(__ldg(head_w + c0 + j), v, hsum);
+                    }
                 }
-                uint4 *dst = reinterpret_cast<uint4 *>(o + c0);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                for (int d = 16; d > 0; d >>= 1) hsum += __shfl_xor_sync(0xffffffffu, hsum, d);
+                if (lane == 0) partials[(size_t)t * 4 + qtr] = hsum;
+            } else if constexpr (SPLIT) {
+                // fp32 output as two planes per pixel: [hi(N) | lo(N)]
+                float *o = static_cast<float *>(out) + ((size_t)m * HW + p0 + row) * (2 * N);
+#pragma unroll
+                for (int c0 = 0; c0 < N; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * N + c0), r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        float v[4], hi[4], lo[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            v[e] = __uint_as_float(r[j + e]) + __ldg(bias + c0 + j + e);
+                            v[e] = v[e] > 0.f ? v[e] : 0.f;
+                            hi[e] = tf32_hi(v[e]);
+                            lo[e] = v[e] - hi[e];
+                        }
+                        *reinterpret_cast<float4 *>(o + c0 + j) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                        *reinterpret_cast<float4 *>(o + N + c0 + j) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                    }
+                }
+            } else {
+                __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out) + ((size_t)m * HW + p0 + row) * N;
+#pragma unroll
+                for (int c0 = 0; c0 < N; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * N + c0), r);
+                    tmem_ld_wait();
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        float v0 = __uint_as_float(r[2 * j]) + __ldg(bias + c0 + 2 * j);
+                        float v1 = __uint_as_float(r[2 * j + 1]) + __ldg(bias + c0 + 2 * j + 1);
+                        v0 = v0 > 0.f ? v0 : 0.f;
+                        v1 = v1 > 0.f ? v1 : 0.f;
+                        pk[j] = pack_bf16x2(v0, v1);
+                    }
+                    uint4 *dst = reinterpret_cast<uint4 *>(o + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -338,18 +413,35 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     if (threadIdx.x == 0 && *abort_flag) atomicOr(err, ERR_TC_TIMEOUT);
 }
 
+// score[m] = hb + (sum of the frame's epilogue partials) / HW, one warp per
+// frame, fixed lane order and butterfly reduction (deterministic).
+__global__ void k_head_finalize(const int *count, const float *partials, int parts_per_frame, double hb, int HW,
+                                float *score) {
+    const int M = *count;
+    const int lane = threadIdx.x & 31;
+    for (int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; m < M; m += (gridDim.x * blockDim.x) >> 5) {
+        const float *pp = partials + (size_t)m * parts_per_frame;
+        float s = 0.f;
+        for (int j = lane; j < parts_per_frame; j += 32) s += pp[j];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (lane == 0) score[m] = (float)(hb + (double)s / (double)HW);
+    }
+}
+
 using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                               const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-template <int CC, int N, int S>
+template <int CC, int N, int S, bool SPLIT>
 cudaError_t set_smem() {
-    return cudaFuncSetAttribute(k_conv3x3_tc<CC, N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                TcCfg<CC, N, S>::SMEM);
+    return cudaFuncSetAttribute(k_conv3x3_tc<CC, N, S, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcCfg<CC, N, S, SPLIT>::SMEM);
 }
 
 // Stage counts per (CC, N), sized to ~160-170 KB of shared memory.
 constexpr int kS_64_128 = 2, kS_64_64 = 3, kS_32_128 = 4, kS_32_64 = 4;
+constexpr int kS_t32_128 = 2, kS_t32_64 = 3;   // split TF32, CC = 32 fp32 channels
 
 }  // namespace
 
@@ -375,6 +467,29 @@ void tc_conv_pack_weights(const float *w, int cin, int cout, std::vector<__nv_bf
                     }
 }
 
+void tc_conv_pack_weights_split(const float *w, int cin, int cout, std::vector<float> &out) {
+    const int CC = 32;
+    const int nch = cin / CC;
+    out.assign((size_t)2 * nch * 9 * cout * CC, 0.f);
+    // layout [((plane*nch + c)*3 + kx)*3 + ky][co][k]; plane 0 = TF32 high part, 1 = remainder
+    for (int plane = 0; plane < 2; ++plane)
+        for (int c = 0; c < nch; ++c)
+            for (int kx = 0; kx < 3; ++kx)
+                for (int ky = 0; ky < 3; ++ky)
+                    for (int co = 0; co < cout; ++co)
+                        for (int k = 0; k < CC; ++k) {
+                            const int ci = c * CC + k;
+                            const float v = w[(((size_t)co * cin + ci) * 3 + ky) * 3 + kx];
+                            uint32_t bits;
+                            std::memcpy(&bits, &v, 4);
+                            bits &= 0xFFFFE000u;
+                            float hi;
+                            std::memcpy(&hi, &bits, 4);
+                            const size_t o = ((((size_t)(plane * nch + c) * 3 + kx) * 3 + ky) * cout + co) * CC + k;
+                            out[o] = plane == 0 ? hi : v - hi;
+                        }
+}
+
 hydro_status tc_conv_init(TcConvPlan *plan, int device) {
     plan->device = device;
     void *fn = nullptr;
@@ -386,10 +501,12 @@ hydro_status tc_conv_init(TcConvPlan *plan, int device) {
     }
     plan->encode = fn;
     cudaError_t r = cudaSuccess;
-    if (r == cudaSuccess) r = set_smem<64, 128, kS_64_128>();
-    if (r == cudaSuccess) r = set_smem<64, 64, kS_64_64>();
-    if (r == cudaSuccess) r = set_smem<32, 128, kS_32_128>();
-    if (r == cudaSuccess) r = set_smem<32, 64, kS_32_64>();
+    if (r == cudaSuccess) r = set_smem<64, 128, kS_64_128, false>();
+    if (r == cudaSuccess) r = set_smem<64, 64, kS_64_64, false>();
+    if (r == cudaSuccess) r = set_smem<32, 128, kS_32_128, false>();
+    if (r == cudaSuccess) r = set_smem<32, 64, kS_32_64, false>();
+    if (r == cudaSuccess) r = set_smem<32, 128, kS_t32_128, true>();
+    if (r == cudaSuccess) r = set_smem<32, 64, kS_t32_64, true>();
     if (r != cudaSuccess) {
         g_tc_err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(r);
         return HYDRO_ECUDA;
@@ -398,40 +515,51 @@ hydro_status tc_conv_init(TcConvPlan *plan, int device) {
     return HYDRO_OK;
 }
 
+void tc_head_finalize(const int *count, const float *partials, int parts_per_frame, double hb, int HW,
+                      float *score, int max_frames, int sms, cudaStream_t st) {
+    int grid = (max_frames + 7) / 8;
+    if (grid > sms * 8) grid = sms * 8;
+    if (grid < 1) grid = 1;
+    k_head_finalize<<<grid, 256, 0, st>>>(count, partials, parts_per_frame, hb, HW, score);
+}
+
 hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int cin, int H, int W,
                          const void *wpacked, const float *bias, int cout, void *out, int max_frames, int sms,
-                         cudaStream_t st, unsigned int *err) {
+                         cudaStream_t st, unsigned int *err, const float *head_w, float *partials, bool split) {
     if (!plan->ready || !tc_conv_supported(cin, cout, H, W)) {
         g_tc_err = "tensor-core conv not ready or shape unsupported";
         return HYDRO_EUNSUPPORTED;
     }
     EncodeFn enc = reinterpret_cast<EncodeFn>(plan->encode);
-    const int CC = cin == 32 ? 32 : 64;
+    // operand chunk: 64 bf16 / 32 bf16 (128 B or 64 B rows); split fp32: 32 (128 B rows)
+    const int CC = split ? 32 : (cin == 32 ? 32 : 64);
+    const int esz = split ? 4 : 2;
+    const int planes = split ? 2 : 1;
     const int nch = cin / CC;
+    const CUtensorMapDataType dt = split ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUtensorMapSwizzle swz = CC * esz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    const cuuint64_t ctot = (cuuint64_t)cin * planes;   // channels stored per pixel
     CUtensorMap tmA, tmB;
     {
-        const cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)max_frames};
-        const cuuint64_t strides[3] = {(cuuint64_t)cin * 2, (cuuint64_t)W * cin * 2, (cuuint64_t)H * W * cin * 2};
+        const cuuint64_t dims[4] = {ctot, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)max_frames};
+        const cuuint64_t strides[3] = {ctot * esz, (cuuint64_t)W * ctot * esz, (cuuint64_t)H * W * ctot * esz};
         const cuuint32_t box[4] = {(cuuint32_t)CC, 64, 4, 1};
         const cuuint32_t es[4] = {1, 1, 1, 1};
-        CUresult r = enc(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(in), dims, strides, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r = enc(&tmA, dt, 4, const_cast<void *>(in), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             g_tc_err = "cuTensorMapEncodeTiled(activations) failed: " + std::to_string((int)r);
             return HYDRO_ECUDA;
         }
     }
     {
-        const cuuint64_t dims[3] = {(cuuint64_t)CC, (cuuint64_t)cout, (cuuint64_t)nch * 9};
-        const cuuint64_t strides[2] = {(cuuint64_t)CC * 2, (cuuint64_t)cout * CC * 2};
+        const cuuint64_t dims[3] = {(cuuint64_t)CC, (cuuint64_t)cout, (cuuint64_t)planes * nch * 9};
+        const cuuint64_t strides[2] = {(cuuint64_t)CC * esz, (cuuint64_t)cout * CC * esz};
         const cuuint32_t box[3] = {(cuuint32_t)CC, (cuuint32_t)cout, 3};
         const cuuint32_t es[3] = {1, 1, 1};
-        CUresult r = enc(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(wpacked), dims, strides, box,
-                         es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r = enc(&tmB, dt, 3, const_cast<void *>(wpacked), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             g_tc_err = "cuTensorMapEncodeTiled(weights) failed: " + std::to_string((int)r);
             return HYDRO_ECUDA;
@@ -440,20 +568,21 @@ hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int
     const int tpf = H * W / 128;
     long long tiles = (long long)max_frames * tpf;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out);
     const int HW = H * W;
-    if (CC == 64 && cout == 128)
-        k_conv3x3_tc<64, 128, kS_64_128><<<grid, 192, TcCfg<64, 128, kS_64_128>::SMEM, st>>>(
-            tmA, tmB, count, nch, tpf, HW, bias, o, err);
-    else if (CC == 64)
-        k_conv3x3_tc<64, 64, kS_64_64><<<grid, 192, TcCfg<64, 64, kS_64_64>::SMEM, st>>>(tmA, tmB, count, nch, tpf,
-                                                                                        HW, bias, o, err);
-    else if (cout == 128)
-        k_conv3x3_tc<32, 128, kS_32_128><<<grid, 192, TcCfg<32, 128, kS_32_128>::SMEM, st>>>(
-            tmA, tmB, count, nch, tpf, HW, bias, o, err);
-    else
-        k_conv3x3_tc<32, 64, kS_32_64><<<grid, 192, TcCfg<32, 64, kS_32_64>::SMEM, st>>>(tmA, tmB, count, nch, tpf,
-                                                                                        HW, bias, o, err);
+#define HYDRO_TC_LAUNCH(CC_, N_, S_, SPLIT_)                                                               \
+    k_conv3x3_tc<CC_, N_, S_, SPLIT_><<<grid, 192, TcCfg<CC_, N_, S_, SPLIT_>::SMEM, st>>>(              \
+        tmA, tmB, count, nch, cin, tpf, HW, bias, out, head_w, partials, err)
+    if (split) {
+        if (cout == 128) HYDRO_TC_LAUNCH(32, 128, kS_t32_128, true);
+        else HYDRO_TC_LAUNCH(32, 64, kS_t32_64, true);
+    } else if (CC == 64) {
+        if (cout == 128) HYDRO_TC_LAUNCH(64, 128, kS_64_128, false);
+        else HYDRO_TC_LAUNCH(64, 64, kS_64_64, false);
+    } else {
+        if (cout == 128) HYDRO_TC_LAUNCH(32, 128, kS_32_128, false);
+        else HYDRO_TC_LAUNCH(32, 64, kS_32_64, false);
+    }
+#undef HYDRO_TC_LAUNCH
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         g_tc_err = std::string("launch: ") + cudaGetErrorString(e);

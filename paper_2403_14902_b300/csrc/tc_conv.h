@@ -20,11 +20,23 @@ struct TcConvPlan {
 bool tc_conv_supported(int cin, int cout, int H, int W);
 // Repack fp32 weights [cout][cin][3][3] into the kernel's bf16 layout.
 void tc_conv_pack_weights(const float *w, int cin, int cout, std::vector<__nv_bfloat16> &out);
+// FP32-accurate split form: [plane(hi, lo)][chunk of 32][kx][ky][cout][32] fp32.
+void tc_conv_pack_weights_split(const float *w, int cin, int cout, std::vector<float> &out);
 hydro_status tc_conv_init(TcConvPlan *plan, int device);
 // out[m] = relu(conv3x3(in[m]) + bias) for m < *count (device), NHWC bf16.
+// With head_w != nullptr the layer is the UDF's last: nothing is stored to
+// `out`; instead partials[(m * H*W/128 + tile) * 4 + q] receives the sum over
+// 32 pixels of head_w . relu(conv + bias) (4 partials per 128-pixel tile).
 hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int cin, int H, int W,
                          const void *wpacked, const float *bias, int cout, void *out, int max_frames, int sms,
-                         cudaStream_t st, unsigned int *err);
+                         cudaStream_t st, unsigned int *err, const float *head_w = nullptr,
+                         float *partials = nullptr, bool split = false);
+// With split = true the layer is FP32-accurate (3xTF32): `in` and `out` are
+// fp32 [frame][pixel][hi(C) | lo(C)] and wpacked comes from
+// tc_conv_pack_weights_split.
+// score[m] = hb + sum(partials of frame m) / HW for m < *count.
+void tc_head_finalize(const int *count, const float *partials, int parts_per_frame, double hb, int HW,
+                      float *score, int max_frames, int sms, cudaStream_t st);
 void tc_conv_destroy(TcConvPlan *plan);
 const char *tc_conv_last_error();
 

@@ -40,16 +40,21 @@ def test_small_stream_parity(cnn4, precision, policy):
     q.close()
 
 
-def test_bf16_wide_margin_rechecks_and_stays_exact(cnn4):
+@pytest.mark.parametrize("tf32_margin", [5e-3, 10.0])
+def test_bf16_wide_margin_rechecks_and_stays_exact(cnn4, tf32_margin):
     # a margin wider than the score spread sends every tuple through the
-    # FP32 recheck; the pass set must not move
+    # 3xTF32 recheck (and with the wide 3xTF32 margin, all of them on through
+    # the FP32 CUDA-core recheck); the pass set must not move
     w = cnn4["w"]
     q = make_query(w, cnn4["th"], batch=B_SMALL, policy="rank", precision="bf16")
     for i in range(4):
-        q.set_margins(i, 10.0, 1e-5)
+        q.set_margins(i, 10.0, tf32_margin, 1e-5)
     res = run_stream(q, cnn4["Fd"], B_SMALL)
     check_against_oracle(res, cnn4["pm"], B_SMALL, policy="rank", costs=model_costs(w))
-    assert sum(sum(r[2]["recheck_fp32"]) for r in res) == sum(int(r[1].sum()) for r in res)
+    evaluated = sum(int(r[1].sum()) for r in res)
+    assert sum(sum(r[2]["recheck_tf32"]) for r in res) == evaluated
+    if tf32_margin >= 10.0:
+        assert sum(sum(r[2]["recheck_fp32"]) for r in res) == evaluated
     q.close()
 
 
@@ -57,7 +62,7 @@ def test_fp32_wide_margin_goes_to_fp64(cnn4):
     w = cnn4["w"]
     q = make_query(w, cnn4["th"], batch=B_SMALL, policy="static", precision="fp32")
     for i in range(4):
-        q.set_margins(i, 0.02, 0.05)
+        q.set_margins(i, 0.02, 5e-3, 0.05)
     res = run_stream(q, cnn4["Fd"], B_SMALL)
     check_against_oracle(res, cnn4["pm"], B_SMALL, policy="static", costs=model_costs(w))
     assert sum(sum(r[2]["recheck_fp64"]) for r in res) > 0
@@ -79,6 +84,10 @@ def test_udf_scores_error(cnn4):
         q.udf_scores(i, "bf16", cnn4["Fd"][:n], out)
         # the BF16 error must sit well inside the 0.02 recheck margin
         assert np.max(np.abs(out.cpu().numpy() - s64)) < 0.02 / 2
+        q.udf_scores(i, "tf32x3", cnn4["Fd"][:n], out)
+        # 3xTF32 is FP32-accurate up to the tensor cores' accumulation
+        assert score_tolerance_ok(out.cpu().numpy(), s64, cnn4["rms"][i]).all()
+        assert np.max(np.abs(out.cpu().numpy() - s64)) < 5e-3
     q.close()
 
 
@@ -90,6 +99,7 @@ def test_calibrate_bf16(cnn4):
         assert d["max_err_lowp"] < 0.02 / 2
         assert d["margin_lowp"] >= 0.02
         assert d["margin_fp32"] >= 16 * d["max_err_fp32"]
+        assert 0 < d["max_err_tf32"] < 5e-3 and d["margin_tf32"] >= 8 * d["max_err_tf32"]
     res = run_stream(q, cnn4["Fd"], B_SMALL)
     check_against_oracle(res, cnn4["pm"], B_SMALL, policy="rank", costs=model_costs(w))
     q.close()

@@ -77,7 +77,7 @@ def test_wide_margin_forces_fp64_recheck_and_stays_exact(mlp3):
     w = mlp3["w"]
     q = make_query(w, mlp3["th"], batch=w.batch)
     for i in range(3):
-        q.set_margins(i, 0.02, 2.0)
+        q.set_margins(i, 0.02, 5e-3, 2.0)
     res = run_stream(q, mlp3["Xd"], w.batch)
     check_against_oracle(res, mlp3["pm"], w.batch, policy="rank", costs=model_costs(w))
     assert sum(sum(r[2]["recheck_fp64"]) for r in res) > 1000
