@@ -20,6 +20,11 @@ for them with the shapes of the build's five configurations):
   four CNN UDFs with 2/4/6/8 conv3x3 layers of 32-128 channels + global
   average pool + linear, target selectivities 0.3/0.6/0.1/0.9, batches of
   1,024.
+* ``drift5`` - 1,048,576 x 512 fp32 tuples in 8 segments whose 8-cluster
+  mixture weights are drawn from Dirichlet(0.5) per segment (so each
+  predicate's selectivity drifts between segments); five MLP UDFs, the first
+  two sharing an upstream embedding 512-1024-256 (heads 256-1 and 256-256-1),
+  then 512-256-1, 512-1024-1024-1, 512-2048-1; batches of 4,096.
 """
 from __future__ import annotations
 
@@ -33,7 +38,7 @@ import numpy as np
 __all__ = [
     "rng", "Workload", "WORKLOADS", "workload", "gmm_tuples", "blob_frames",
     "mlp_weights", "cnn_weights", "tuple_ids", "predicate_weights",
-    "stream_tuples", "calib_tuples",
+    "stream_tuples", "calib_tuples", "embedding_weights", "head_weights", "segment_mixes",
 ]
 
 
@@ -70,6 +75,11 @@ WORKLOADS = {
         udfs=((3, 32, 64), (3, 32, 64, 64, 128), (3, 32, 64, 64, 128, 128, 128),
               (3, 32, 64, 64, 128, 128, 128, 128, 128)),
         selectivity=(0.3, 0.6, 0.1, 0.9), n_calib=256, head_gain=(8.0, 8.0, 6.0, 4.0)),
+    "drift5": Workload(
+        name="drift5", wid=3, kind="vec", n=1048576, batch=4096, dim=512,
+        udfs=((512, 1024, 256, 1), (512, 1024, 256, 256, 1), (512, 256, 1), (512, 1024, 1024, 1), (512, 2048, 1)),
+        selectivity=(0.5, 0.4, 0.5, 0.6, 0.5), n_calib=1024,
+        extra={"segments": 8, "dirichlet": 0.5, "embedding": (512, 1024, 256), "emb_preds": (0, 1)}),
 }
 
 
@@ -91,15 +101,26 @@ def _cluster_means(w: Workload) -> np.ndarray:
     return (g.standard_normal((w.n_clusters, w.dim)) * w.cluster_spread).astype(np.float64)
 
 
+ROW_BLOCK = 4096   # rows per Philox counter block of a vector stream
+
+
 def gmm_tuples(w: Workload, stream: int, n: int, mix: np.ndarray | None = None) -> np.ndarray:
     """``n`` fp32 rows of an isotropic unit-variance Gaussian mixture with
-    ``w.n_clusters`` components (uniform weights unless ``mix``)."""
+    ``w.n_clusters`` components (uniform weights unless ``mix``).  Rows come
+    in blocks of ``ROW_BLOCK``, each from its own Philox counter range, so
+    the first n rows do not depend on how many are drawn."""
     means = _cluster_means(w)
-    g = rng(w.wid, stream)
     p = np.full(w.n_clusters, 1.0 / w.n_clusters) if mix is None else np.asarray(mix, np.float64)
-    comp = g.choice(w.n_clusters, size=n, p=p)
-    x = means[comp] + g.standard_normal((n, w.dim))
-    return np.ascontiguousarray(x.astype(np.float32))
+    out = np.empty((n, w.dim), np.float32)
+    for b0 in range(0, n, ROW_BLOCK):
+        bg = np.random.Philox(key=w.wid * 1000 + stream)
+        bg.advance((b0 // ROW_BLOCK) << 40)
+        g = np.random.Generator(bg)
+        comp = g.choice(w.n_clusters, size=ROW_BLOCK, p=p)
+        x = means[comp] + g.standard_normal((ROW_BLOCK, w.dim))
+        m = min(ROW_BLOCK, n - b0)
+        out[b0:b0 + m] = x[:m]
+    return out
 
 
 FRAME_BLOCK = 256   # frames per Philox counter block of a frame stream
@@ -211,16 +232,68 @@ def cnn_weights(w: Workload, stream: int, chans, gain: float = 1.0) -> tuple:
     return convs, (hw, float(hb))
 
 
+def embedding_weights(w: Workload):
+    """Layers of the shared upstream embedding (stream 30): hidden layers
+    only, so every layer is followed by ReLU; None if the workload has none."""
+    dims = w.extra.get("embedding") if w.extra else None
+    if not dims:
+        return None
+    g = rng(w.wid, 30)
+    layers = []
+    for l in range(len(dims) - 1):
+        fi, fo = dims[l], dims[l + 1]
+        W = ((g.random((fo, fi)) * 2.0 - 1.0) * math.sqrt(6.0 / fi)).astype(np.float32)
+        b = ((g.random(fo) * 2.0 - 1.0) / math.sqrt(fi)).astype(np.float32)
+        layers.append((np.ascontiguousarray(W), b))
+    return layers
+
+
+def head_weights(w: Workload, i: int):
+    """Head layers of predicate i on top of the embedding (stream 10+i)."""
+    emb = w.extra["embedding"]
+    head_dims = w.udfs[i][len(emb) - 1:]
+    return mlp_weights(w, 10 + i, head_dims, _gain(w, i))
+
+
 def predicate_weights(w: Workload):
-    """Weights of every predicate of the workload, predicate i on stream 10+i."""
+    """Full layer lists of every predicate, predicate i on stream 10+i.  A
+    predicate on the shared embedding is the embedding's layers followed by
+    its head's layers (one plain MLP)."""
     if w.kind == "vec":
-        return [mlp_weights(w, 10 + i, d, _gain(w, i)) for i, d in enumerate(w.udfs)]
+        shared = set(w.extra.get("emb_preds", ())) if w.extra else set()
+        emb = embedding_weights(w) if shared else None
+        return [emb + head_weights(w, i) if i in shared else mlp_weights(w, 10 + i, d, _gain(w, i))
+                for i, d in enumerate(w.udfs)]
     return [cnn_weights(w, 10 + i, c, _gain(w, i)) for i, c in enumerate(w.udfs)]
 
 
+def segment_mixes(w: Workload) -> np.ndarray:
+    """[segments, clusters] mixture weights, one Dirichlet(alpha) draw per
+    segment (stream 5)."""
+    S = w.extra["segments"]
+    g = rng(w.wid, 5)
+    return g.dirichlet(np.full(w.n_clusters, w.extra["dirichlet"]), size=S)
+
+
 def stream_tuples(w: Workload, n: int | None = None, start: int = 0) -> np.ndarray:
-    """The workload's tuple stream (stream 1); frames may be sliced by ``start``."""
+    """The workload's tuple stream (stream 1); frames may be sliced by
+    ``start``.  A drifting stream is cut into ``segments`` equal segments,
+    segment s drawn from its own mixture (``segment_mixes``) on stream 100+s;
+    its prefix of n tuples is the first n tuples of that full stream."""
     n = w.n if n is None else n
+    if w.kind == "vec" and w.extra and "segments" in w.extra:
+        assert start == 0
+        S = w.extra["segments"]
+        seg = WORKLOADS[w.name].n // S if w.name in WORKLOADS else w.n // S
+        mixes = segment_mixes(w)
+        parts, left = [], n
+        for s in range(S):
+            if left <= 0:
+                break
+            m = min(seg, left)
+            parts.append(gmm_tuples(w, 100 + s, m, mixes[s]))
+            left -= m
+        return np.ascontiguousarray(np.concatenate(parts)) if parts else np.zeros((0, w.dim), np.float32)
     if w.kind == "vec":
         assert start == 0
         return gmm_tuples(w, 1, n)

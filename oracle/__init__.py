@@ -237,23 +237,48 @@ POLICIES = ("rank", "static", "all", "cost", "selectivity")
 
 
 def simulate(pm: np.ndarray, batch: int, policy: str = "rank", costs=None, static_order=None,
-             warmup: int = 1, window: int = 8, lag: int = 1):
+             warmup: int = 1, window: int = 8, lag: int = 1, groups=None, group_costs=None, ids=None,
+             prefilled=None):
     """Route a stream through the conjunction batch by batch.
 
     ``pm`` is the [n, P] pass matrix of the stream in submission order; the
     stream is cut into consecutive batches of ``batch`` tuples.  Returns a
     list of dicts per batch: ``order``, ``counts`` [P] (tuples each predicate
     evaluated), ``passed`` [P] (of those, how many passed), ``warmup`` flag,
-    and ``bits`` (the batch's result)."""
+    ``bits`` (the batch's result) and ``hits`` [P] (reuse-cache hits).
+
+    Reuse (Sec. 4.3 "Reuse-aware Routing"): ``groups[i]`` names the shared
+    upstream UDF of predicate i (or None).  Its output is cached per tuple id
+    (``ids`` [n], ``prefilled`` ids cached before the query).  A predicate of
+    a group runs the group UDF only on alive tuples whose id is not cached
+    yet, then caches them.  The router's cost of such a predicate for batch b
+    is ``costs[i] + miss_b / n_b * group_costs[g]`` (the estimated cost of
+    the reuse-aware formula, with the hit rate of the batch), where miss_b
+    counts the batch's ids not cached by batches finished lag+1 earlier (or
+    prefilled); ``costs[i]`` is then the head's own cost."""
     assert policy in POLICIES
     n, P = pm.shape
     costs = [1] * P if costs is None else list(costs)
+    groups = [None] * P if groups is None else list(groups)
     declared = list(range(P))
-    stat_e, stat_p = [], []          # per batch, per predicate
+    gnames = sorted({g for g in groups if g is not None})
+    # cache tags per group: 0 absent, -1 prefilled, b+1 computed in batch b
+    tag = {}
+    if gnames:
+        ids = np.arange(n, dtype=np.int64) if ids is None else np.asarray(ids, np.int64)
+        cap = int(ids.max()) + 1 if n else 1
+        if prefilled is not None and len(prefilled):
+            cap = max(cap, int(np.max(prefilled)) + 1)
+        for g in gnames:
+            tag[g] = np.zeros(cap, np.int64)
+            if prefilled is not None:
+                tag[g][np.asarray(prefilled, np.int64)] = -1
+    stat_e, stat_p = [], []
     out = []
     nb = (n + batch - 1) // batch
     for b in range(nb):
         rows = pm[b * batch:(b + 1) * batch]
+        bids = ids[b * batch:(b + 1) * batch] if gnames else None
         nbt = rows.shape[0]
         evaluate_all = policy == "all" or (policy in ("rank", "cost", "selectivity") and b < warmup)
         if evaluate_all:
@@ -266,6 +291,11 @@ def simulate(pm: np.ndarray, batch: int, policy: str = "rank", costs=None, stati
                 order = declared
             else:
                 lo = max(0, last - window + 1)
+                miss = {}
+                for g in gnames:
+                    t = tag[g][bids]
+                    visible = (t == -1) | ((t > 0) & (t - 1 <= last))
+                    miss[g] = int((~visible).sum())
                 keys = []
                 for i in range(P):
                     E = sum(stat_e[x][i] for x in range(lo, last + 1))
@@ -273,26 +303,34 @@ def simulate(pm: np.ndarray, batch: int, policy: str = "rank", costs=None, stati
                     if E == 0:
                         E = sum(stat_e[x][i] for x in range(min(warmup, last + 1)))
                         Pp = sum(stat_p[x][i] for x in range(min(warmup, last + 1)))
+                    c = Fraction(costs[i])
+                    if groups[i] is not None and nbt > 0:
+                        c += Fraction(miss[groups[i]], nbt) * group_costs[groups[i]]
                     if policy == "rank":
-                        keys.append(rank_key(costs[i], E, Pp))
+                        keys.append(c / (1 - smoothed_selectivity(E, Pp)))
                     elif policy == "cost":
-                        keys.append(Fraction(costs[i]))
+                        keys.append(c)
                     else:
                         keys.append(smoothed_selectivity(E, Pp))
                 order = order_by(keys)
         counts = np.zeros(P, np.int64)
         passed = np.zeros(P, np.int64)
-        if evaluate_all:
-            counts[:] = nbt
-            passed[:] = rows.sum(axis=0)
-        else:
-            alive = np.ones(nbt, bool)
-            for i in order:
-                counts[i] = int(alive.sum())
-                passed[i] = int((alive & rows[:, i]).sum())
+        hits = np.zeros(P, np.int64)
+        alive = np.ones(nbt, bool)
+        for i in order:
+            ev = np.ones(nbt, bool) if evaluate_all else alive
+            counts[i] = int(ev.sum())
+            passed[i] = int((ev & rows[:, i]).sum())
+            g = groups[i]
+            if g is not None:
+                idx = bids[ev]
+                absent = tag[g][idx] == 0
+                hits[i] = int((~absent).sum())
+                tag[g][idx[absent]] = b + 1
+            if not evaluate_all:
                 alive &= rows[:, i]
         stat_e.append([int(v) for v in counts])
         stat_p.append([int(v) for v in passed])
         out.append(dict(order=list(order), counts=counts, passed=passed, warmup=evaluate_all,
-                        bits=result_bits(rows)))
+                        bits=result_bits(rows), hits=hits))
     return out

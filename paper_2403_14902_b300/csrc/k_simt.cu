@@ -194,8 +194,9 @@ __device__ __forceinline__ void store_relu_row_split(const float (&acc)[COUT], f
 
 // First conv layer straight from the uint8 CHW frames (gathered through
 // `list`): out[m][p][co] = relu(b[co] + sum_{ci,ky,kx} W * x/255), NHWC.
-// One thread per output pixel computes all COUT channels.
-template <typename T, typename Tout, int COUT, bool SPLIT = false>
+// One thread computes PX consecutive pixels of a row for all COUT channels,
+// so every weight read from shared memory feeds PX multiply-adds.
+template <typename T, typename Tout, int COUT, int PX, bool SPLIT = false>
 __global__ void __launch_bounds__(256)
 k_conv1_u8(const int *count, const int *list, const unsigned char *frames, int C0, int H, int Wd,
            const float *W, const float *bias, Tout *out) {
@@ -209,33 +210,50 @@ k_conv1_u8(const int *count, const int *list, const unsigned char *frames, int C
     __syncthreads();
     const int M = *count;
     const int HW = H * Wd;
-    const int blocks_per_frame = (HW + 255) / 256;
+    const int per_block = 256 * PX;
+    const int blocks_per_frame = (HW + per_block - 1) / per_block;
     const T inv255 = (T)1 / (T)255;
     for (int w = blockIdx.x; w < M * blocks_per_frame; w += gridDim.x) {
         const int m = w / blocks_per_frame;
-        const int p = (w % blocks_per_frame) * 256 + threadIdx.x;
+        const int p = (w % blocks_per_frame) * per_block + threadIdx.x * PX;
         if (p >= HW) continue;
-        const int y = p / Wd, x = p % Wd;
+        const int y = p / Wd, x0 = p % Wd;   // Wd % PX == 0: the PX pixels share row y
         const unsigned char *f = frames + (size_t)list[m] * C0 * HW;
-        T acc[COUT];
+        T acc[PX][COUT];
 #pragma unroll
-        for (int co = 0; co < COUT; ++co) acc[co] = Bs[co];
+        for (int i = 0; i < PX; ++i)
+#pragma unroll
+            for (int co = 0; co < COUT; ++co) acc[i][co] = Bs[co];
         for (int ci = 0; ci < C0; ++ci)
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky)
+            for (int ky = 0; ky < 3; ++ky) {
+                const int yy = y + ky - 1;
+                if (yy < 0 || yy >= H) continue;
+                const unsigned char *row = f + (size_t)ci * HW + (size_t)yy * Wd;
+                T v[PX + 2];
+#pragma unroll
+                for (int j = 0; j < PX + 2; ++j) {
+                    const int xx = x0 - 1 + j;
+                    v[j] = (xx >= 0 && xx < Wd) ? (T)row[xx] * inv255 : (T)0;
+                }
 #pragma unroll
                 for (int kx = 0; kx < 3; ++kx) {
-                    const int yy = y + ky - 1, xx = x + kx - 1;
-                    if (yy < 0 || yy >= H || xx < 0 || xx >= Wd) continue;
-                    const T v = (T)f[(size_t)ci * HW + yy * Wd + xx] * inv255;
                     const T *wr = Ws[ci * 9 + ky * 3 + kx];
 #pragma unroll
-                    for (int co = 0; co < COUT; ++co) acc[co] += wr[co] * v;
+                    for (int co = 0; co < COUT; ++co) {
+                        const T wv = wr[co];
+#pragma unroll
+                        for (int i = 0; i < PX; ++i) acc[i][co] += wv * v[i + kx];
+                    }
                 }
-        if constexpr (SPLIT) {
-            store_relu_row_split<COUT>(acc, out + ((size_t)m * HW + p) * (2 * COUT));
-        } else {
-            store_relu_row<T, Tout, COUT>(acc, out + ((size_t)m * HW + p) * COUT);
+            }
+#pragma unroll
+        for (int i = 0; i < PX; ++i) {
+            if constexpr (SPLIT) {
+                store_relu_row_split<COUT>(acc[i], out + ((size_t)m * HW + p + i) * (2 * COUT));
+            } else {
+                store_relu_row<T, Tout, COUT>(acc[i], out + ((size_t)m * HW + p + i) * COUT);
+            }
         }
     }
 }
@@ -385,43 +403,58 @@ cudaError_t mlp_band_smem_setup(int max_width) {
     return cudaFuncSetAttribute(k_mlp_band<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32);
 }
 
-template <typename T, typename Tout>
+template <typename T, typename Tout, int PX, bool SPLIT = false>
 static void conv1_dispatch(const int *count, const int *list, const unsigned char *frames, int C0, int H,
-                           int Wd, const float *W, const float *bias, int Cout, Tout *out, int grid,
+                           int Wd, const float *W, const float *bias, int Cout, Tout *out, int max_frames, int sms,
                            cudaStream_t st) {
+    const int work = max_frames * ((H * Wd + 256 * PX - 1) / (256 * PX));
+    int grid = work < grid_for(sms, 8) ? work : grid_for(sms, 8);
+    if (grid < 1) grid = 1;
+    constexpr int PX64 = PX > 2 ? 2 : PX;   // 64 channels: fewer pixels per thread (registers)
     switch (Cout) {
-        case 16: k_conv1_u8<T, Tout, 16><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
-        case 32: k_conv1_u8<T, Tout, 32><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
-        default: k_conv1_u8<T, Tout, 64><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
+        case 16: k_conv1_u8<T, Tout, 16, PX, SPLIT><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
+        case 32: k_conv1_u8<T, Tout, 32, PX, SPLIT><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
+        default: {
+            const int work64 = max_frames * ((H * Wd + 256 * PX64 - 1) / (256 * PX64));
+            int g64 = work64 < grid_for(sms, 8) ? work64 : grid_for(sms, 8);
+            if (g64 < 1) g64 = 1;
+            k_conv1_u8<T, Tout, 64, PX64, SPLIT><<<g64, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out);
+            break;
+        }
     }
 }
 
 void launch_conv1(int prec, const int *count, const int *list, const unsigned char *frames, int C0, int H,
                   int Wd, const float *W, const float *bias, int Cout, void *out, int max_frames, int sms,
                   cudaStream_t st) {
-    const int work = max_frames * ((H * Wd + 255) / 256);
-    int grid = work < grid_for(sms, 8) ? work : grid_for(sms, 8);
-    if (grid < 1) grid = 1;
+    const bool px4 = Wd % 4 == 0;
     if (prec == PREC_F64)
-        conv1_dispatch<double, double>(count, list, frames, C0, H, Wd, W, bias, Cout, (double *)out, grid, st);
-    else if (prec == PREC_F32)
-        conv1_dispatch<float, float>(count, list, frames, C0, H, Wd, W, bias, Cout, (float *)out, grid, st);
-    else
-        conv1_dispatch<float, __nv_bfloat16>(count, list, frames, C0, H, Wd, W, bias, Cout,
-                                             (__nv_bfloat16 *)out, grid, st);
+        conv1_dispatch<double, double, 1>(count, list, frames, C0, H, Wd, W, bias, Cout, (double *)out, max_frames,
+                                          sms, st);
+    else if (prec == PREC_F32) {
+        if (px4)
+            conv1_dispatch<float, float, 4>(count, list, frames, C0, H, Wd, W, bias, Cout, (float *)out, max_frames,
+                                            sms, st);
+        else
+            conv1_dispatch<float, float, 1>(count, list, frames, C0, H, Wd, W, bias, Cout, (float *)out, max_frames,
+                                            sms, st);
+    } else {
+        if (px4)
+            conv1_dispatch<float, __nv_bfloat16, 4>(count, list, frames, C0, H, Wd, W, bias, Cout,
+                                                    (__nv_bfloat16 *)out, max_frames, sms, st);
+        else
+            conv1_dispatch<float, __nv_bfloat16, 1>(count, list, frames, C0, H, Wd, W, bias, Cout,
+                                                    (__nv_bfloat16 *)out, max_frames, sms, st);
+    }
 }
 
 void launch_conv1_split(const int *count, const int *list, const unsigned char *frames, int C0, int H, int Wd,
                         const float *W, const float *bias, int Cout, float *out, int max_frames, int sms,
                         cudaStream_t st) {
-    const int work = max_frames * ((H * Wd + 255) / 256);
-    int grid = work < grid_for(sms, 8) ? work : grid_for(sms, 8);
-    if (grid < 1) grid = 1;
-    switch (Cout) {
-        case 16: k_conv1_u8<float, float, 16, true><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
-        case 32: k_conv1_u8<float, float, 32, true><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
-        default: k_conv1_u8<float, float, 64, true><<<grid, 256, 0, st>>>(count, list, frames, C0, H, Wd, W, bias, out); break;
-    }
+    if (Wd % 4 == 0)
+        conv1_dispatch<float, float, 4, true>(count, list, frames, C0, H, Wd, W, bias, Cout, out, max_frames, sms, st);
+    else
+        conv1_dispatch<float, float, 1, true>(count, list, frames, C0, H, Wd, W, bias, Cout, out, max_frames, sms, st);
 }
 
 void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,

@@ -158,17 +158,21 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // split into a high TF32 part (low 13 mantissa bits cleared) and the exact
 // fp32 remainder; the MMA (kind::tf32) accumulates hi*hi + hi*lo + lo*hi,
 // which keeps about 21 significant bits per product (3xTF32).
-template <int CC, int N, int S, bool SPLIT>
+// MT: 128-pixel subtiles per CTA tile (1 or 2).  With MT = 2 one A box of
+// 6 image rows feeds both subtiles and every B box is used twice, which cuts
+// the L2->SM operand traffic per output pixel.
+template <int CC, int N, int S, bool SPLIT, int MT>
 struct TcCfg {
     static constexpr int ESZ = SPLIT ? 4 : 2;             // operand bytes
     static constexpr int ROWB = CC * ESZ;                 // bytes of one pixel's K chunk
-    static constexpr int A_BYTES = 4 * 64 * ROWB;         // 4 image rows x 64 pixels
+    static constexpr int A_ROWS = 2 + 2 * MT;             // image rows per A box (halo included)
+    static constexpr int A_BYTES = A_ROWS * 64 * ROWB;
     static constexpr int B_TAP = N * ROWB;                // one tap's weights
     static constexpr int B_BYTES = 3 * B_TAP;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr uint32_t SWZ = ROWB == 128 ? 2u : 4u;  // 128B or 64B swizzle
     static constexpr uint32_t SBO = 8 * ROWB;              // 8-row group stride
-    static constexpr int TMEM_COLS = 2 * N;
+    static constexpr int TMEM_COLS = 2 * MT * N;          // double-buffered accumulators
     static constexpr int PASSES = SPLIT ? 3 : 1;
     static constexpr int SMEM = S * STAGE + 1024 /*align*/ + 256 /*barriers*/;
 };
@@ -191,12 +195,12 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
 
 __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
-template <int CC, int N, int S, bool SPLIT>
+template <int CC, int N, int S, bool SPLIT, int MT>
 __global__ void __launch_bounds__(192, 1)
 k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const int *count,
              int nchunks, int cin, int tiles_per_frame, int HW, const float *__restrict__ bias, void *out,
              const float *__restrict__ head_w, float *partials, unsigned int *err) {
-    using C = TcCfg<CC, N, S, SPLIT>;
+    using C = TcCfg<CC, N, S, SPLIT, MT>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * C::STAGE);
@@ -242,7 +246,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 const int m = t / tiles_per_frame;
-                const int y0 = (t % tiles_per_frame) * 2;
+                const int y0 = (t % tiles_per_frame) * 2 * MT;
                 for (int ps = 0; ps < C::PASSES && ok; ++ps)
                 for (int c = 0; c < nchunks && ok; ++c)
                     for (int kx = 0; kx < 3 && ok; ++kx) {
@@ -288,7 +292,6 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dt = tmem_base + (uint32_t)(buf * N);
                 for (int k = 0; k < ksteps; ++k) {
                     if (!mbar_wait(&full[s], ph, abort_flag)) {
                         ok = false;
@@ -298,16 +301,22 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     const uint32_t sa = smem_u32(smem + s * C::STAGE);
                     const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
-                    for (int ky = 0; ky < 3; ++ky)
+                    for (int sub = 0; sub < MT; ++sub) {
+                        // subtile sub covers output rows y0 + 2*sub, +1: A rows start at 64*(2*sub + ky)
+                        const uint32_t dt = tmem_base + (uint32_t)((buf * MT + sub) * N);
 #pragma unroll
-                        for (int kk = 0; kk < C::ROWB / 32; ++kk) {
-                            const uint64_t ad = smem_desc(sa + ky * 64 * C::ROWB + kk * 32, C::SBO, C::SWZ);
-                            const uint64_t bd = smem_desc(sb + ky * C::B_TAP + kk * 32, C::SBO, C::SWZ);
-                            if constexpr (SPLIT)
-                                mma_tf32(dt, ad, bd, idesc, (k | ky | kk) != 0);
-                            else
-                                mma_bf16(dt, ad, bd, idesc, (k | ky | kk) != 0);
-                        }
+                        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                            for (int kk = 0; kk < C::ROWB / 32; ++kk) {
+                                const uint64_t ad =
+                                    smem_desc(sa + (2 * sub + ky) * 64 * C::ROWB + kk * 32, C::SBO, C::SWZ);
+                                const uint64_t bd = smem_desc(sb + ky * C::B_TAP + kk * 32, C::SBO, C::SWZ);
+                                if constexpr (SPLIT)
+                                    mma_tf32(dt, ad, bd, idesc, (k | ky | kk) != 0);
+                                else
+                                    mma_bf16(dt, ad, bd, idesc, (k | ky | kk) != 0);
+                            }
+                    }
                     mma_commit(&empty[s]);
                     if (++s == S) {
                         s = 0;
@@ -332,69 +341,73 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             }
             tc_fence_after();
             const int m = t / tiles_per_frame;
-            const int p0 = (t % tiles_per_frame) * 128;
-            if (head_w) {
-                // last layer of the UDF: fold global average pooling and the
-                // linear head into the epilogue; each warp leaves one partial
-                // sum of hw . relu(conv) over its 32 pixels
-                float hsum = 0.f;
 #pragma unroll
-                for (int c0 = 0; c0 < N; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * N + c0), r);
-                    tmem_ld_wait();
+            for (int sub = 0; sub < MT; ++sub) {
+                const int p0 = (t % tiles_per_frame) * 128 * MT + 128 * sub;
+                const uint32_t col0 = (uint32_t)((buf * MT + sub) * N);
+                if (head_w) {
+                    // last layer of the UDF: fold global average pooling and the
+                    // linear head into the epilogue; each warp leaves one partial
+                    // sum of hw . relu(conv) over its 32 pixels
+                    float hsum = 0.f;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        float v = __uint_as_float(r[j]) + __ldg(bias + c0 + j);
-                        v = v > 0.f ? v : 0.f;
-                        hsum = fmaf(__ldg(head_w + c0 + j), v, hsum);
-                    }
-                }
+                    for (int c0 = 0; c0 < N; c0 += 32) {
+                        uint32_t r[32];
+                        tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + col0 + (uint32_t)c0, r);
+                        tmem_ld_wait();
 #pragma unroll
-                for (int d = 16; d > 0; d >>= 1) hsum += __shfl_xor_sync(0xffffffffu, hsum, d);
-                if (lane == 0) partials[(size_t)t * 4 + qtr] = hsum;
-            } else if constexpr (SPLIT) {
-                // fp32 output as two planes per pixel: [hi(N) | lo(N)]
-                float *o = static_cast<float *>(out) + ((size_t)m * HW + p0 + row) * (2 * N);
-#pragma unroll
-                for (int c0 = 0; c0 < N; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * N + c0), r);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        float v[4], hi[4], lo[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            v[e] = __uint_as_float(r[j + e]) + __ldg(bias + c0 + j + e);
-                            v[e] = v[e] > 0.f ? v[e] : 0.f;
-                            hi[e] = tf32_hi(v[e]);
-                            lo[e] = v[e] - hi[e];
+                        for (int j = 0; j < 32; ++j) {
+                            float v = __uint_as_float(r[j]) + __ldg(bias + c0 + j);
+                            v = v > 0.f ? v : 0.f;
+                            hsum = fmaf(__ldg(head_w + c0 + j), v, hsum);
                         }
-                        *reinterpret_cast<float4 *>(o + c0 + j) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-                        *reinterpret_cast<float4 *>(o + N + c0 + j) = make_float4(lo[0], lo[1], lo[2], lo[3]);
                     }
-                }
-            } else {
-                __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out) + ((size_t)m * HW + p0 + row) * N;
 #pragma unroll
-                for (int c0 = 0; c0 < N; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * N + c0), r);
-                    tmem_ld_wait();
-                    uint32_t pk[16];
+                    for (int d = 16; d > 0; d >>= 1) hsum += __shfl_xor_sync(0xffffffffu, hsum, d);
+                    if (lane == 0) partials[((size_t)t * MT + sub) * 4 + qtr] = hsum;
+                } else if constexpr (SPLIT) {
+                    // fp32 output as two planes per pixel: [hi(N) | lo(N)]
+                    float *o = static_cast<float *>(out) + ((size_t)m * HW + p0 + row) * (2 * N);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        float v0 = __uint_as_float(r[2 * j]) + __ldg(bias + c0 + 2 * j);
-                        float v1 = __uint_as_float(r[2 * j + 1]) + __ldg(bias + c0 + 2 * j + 1);
-                        v0 = v0 > 0.f ? v0 : 0.f;
-                        v1 = v1 > 0.f ? v1 : 0.f;
-                        pk[j] = pack_bf16x2(v0, v1);
+                    for (int c0 = 0; c0 < N; c0 += 32) {
+                        uint32_t r[32];
+                        tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + col0 + (uint32_t)c0, r);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4) {
+                            float v[4], hi[4], lo[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                v[e] = __uint_as_float(r[j + e]) + __ldg(bias + c0 + j + e);
+                                v[e] = v[e] > 0.f ? v[e] : 0.f;
+                                hi[e] = tf32_hi(v[e]);
+                                lo[e] = v[e] - hi[e];
+                            }
+                            *reinterpret_cast<float4 *>(o + c0 + j) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                            *reinterpret_cast<float4 *>(o + N + c0 + j) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                        }
                     }
-                    uint4 *dst = reinterpret_cast<uint4 *>(o + c0);
+                } else {
+                    __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out) + ((size_t)m * HW + p0 + row) * N;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    for (int c0 = 0; c0 < N; c0 += 32) {
+                        uint32_t r[32];
+                        tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + col0 + (uint32_t)c0, r);
+                        tmem_ld_wait();
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            float v0 = __uint_as_float(r[2 * j]) + __ldg(bias + c0 + 2 * j);
+                            float v1 = __uint_as_float(r[2 * j + 1]) + __ldg(bias + c0 + 2 * j + 1);
+                            v0 = v0 > 0.f ? v0 : 0.f;
+                            v1 = v1 > 0.f ? v1 : 0.f;
+                            pk[j] = pack_bf16x2(v0, v1);
+                        }
+                        uint4 *dst = reinterpret_cast<uint4 *>(o + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    }
                 }
             }
             tc_fence_before();
@@ -433,20 +446,22 @@ using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, vo
                               const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-template <int CC, int N, int S, bool SPLIT>
+template <int CC, int N, int S, bool SPLIT, int MT>
 cudaError_t set_smem() {
-    return cudaFuncSetAttribute(k_conv3x3_tc<CC, N, S, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                TcCfg<CC, N, S, SPLIT>::SMEM);
+    return cudaFuncSetAttribute(k_conv3x3_tc<CC, N, S, SPLIT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcCfg<CC, N, S, SPLIT, MT>::SMEM);
 }
 
-// Stage counts per (CC, N), sized to ~160-170 KB of shared memory.
-constexpr int kS_64_128 = 2, kS_64_64 = 3, kS_32_128 = 4, kS_32_64 = 4;
+// Two 128-pixel subtiles per CTA tile; stage counts per (CC, N) sized to
+// 180-216 KB of shared memory.
+constexpr int kMT = 2;
+constexpr int kS_64_128 = 2, kS_64_64 = 3, kS_32_128 = 4, kS_32_64 = 6;
 constexpr int kS_t32_128 = 2, kS_t32_64 = 3;   // split TF32, CC = 32 fp32 channels
 
 }  // namespace
 
 bool tc_conv_supported(int cin, int cout, int H, int W) {
-    if (W != 64 || H < 2 || (H % 2) != 0) return false;
+    if (W != 64 || H < 4 || (H % 4) != 0) return false;
     if (cout != 64 && cout != 128) return false;
     return cin == 32 || (cin % 64 == 0 && cin <= 512);
 }
@@ -501,12 +516,12 @@ hydro_status tc_conv_init(TcConvPlan *plan, int device) {
     }
     plan->encode = fn;
     cudaError_t r = cudaSuccess;
-    if (r == cudaSuccess) r = set_smem<64, 128, kS_64_128, false>();
-    if (r == cudaSuccess) r = set_smem<64, 64, kS_64_64, false>();
-    if (r == cudaSuccess) r = set_smem<32, 128, kS_32_128, false>();
-    if (r == cudaSuccess) r = set_smem<32, 64, kS_32_64, false>();
-    if (r == cudaSuccess) r = set_smem<32, 128, kS_t32_128, true>();
-    if (r == cudaSuccess) r = set_smem<32, 64, kS_t32_64, true>();
+    if (r == cudaSuccess) r = set_smem<64, 128, kS_64_128, false, kMT>();
+    if (r == cudaSuccess) r = set_smem<64, 64, kS_64_64, false, kMT>();
+    if (r == cudaSuccess) r = set_smem<32, 128, kS_32_128, false, kMT>();
+    if (r == cudaSuccess) r = set_smem<32, 64, kS_32_64, false, kMT>();
+    if (r == cudaSuccess) r = set_smem<32, 128, kS_t32_128, true, kMT>();
+    if (r == cudaSuccess) r = set_smem<32, 64, kS_t32_64, true, kMT>();
     if (r != cudaSuccess) {
         g_tc_err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(r);
         return HYDRO_ECUDA;
@@ -543,7 +558,7 @@ hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int
     {
         const cuuint64_t dims[4] = {ctot, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)max_frames};
         const cuuint64_t strides[3] = {ctot * esz, (cuuint64_t)W * ctot * esz, (cuuint64_t)H * W * ctot * esz};
-        const cuuint32_t box[4] = {(cuuint32_t)CC, 64, 4, 1};
+        const cuuint32_t box[4] = {(cuuint32_t)CC, 64, (cuuint32_t)(2 + 2 * kMT), 1};
         const cuuint32_t es[4] = {1, 1, 1, 1};
         CUresult r = enc(&tmA, dt, 4, const_cast<void *>(in), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -565,12 +580,12 @@ hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int
             return HYDRO_ECUDA;
         }
     }
-    const int tpf = H * W / 128;
+    const int tpf = H / (2 * kMT);   // CTA tiles per frame (W == 64)
     long long tiles = (long long)max_frames * tpf;
     const int grid = (int)(tiles < sms ? tiles : sms);
     const int HW = H * W;
 #define HYDRO_TC_LAUNCH(CC_, N_, S_, SPLIT_)                                                               \
-    k_conv3x3_tc<CC_, N_, S_, SPLIT_><<<grid, 192, TcCfg<CC_, N_, S_, SPLIT_>::SMEM, st>>>(              \
+    k_conv3x3_tc<CC_, N_, S_, SPLIT_, kMT><<<grid, 192, TcCfg<CC_, N_, S_, SPLIT_, kMT>::SMEM, st>>>(    \
         tmA, tmB, count, nch, cin, tpf, HW, bias, out, head_w, partials, err)
     if (split) {
         if (cout == 128) HYDRO_TC_LAUNCH(32, 128, kS_t32_128, true);

@@ -276,3 +276,34 @@ def test_simulate_policies_order_keys():
         assert sim[2]["order"] == want
     sim = O.simulate(pm, batch=4, policy="all")
     assert all(b["counts"].tolist() == [4, 4, 4] for b in sim)
+
+
+def test_simulate_reuse_hand_worked_trace():
+    # predicates 0 and 1 share an upstream UDF "E" (cost 100) under heads of
+    # cost 1; predicate 2 costs 50 and shares nothing.  Every tuple passes.
+    pm = np.ones((12, 3), bool)
+    kw = dict(batch=4, policy="rank", costs=[1, 1, 50], groups=["E", "E", None], group_costs={"E": 100},
+              ids=np.arange(12), warmup=1, lag=1, window=8)
+    sim = O.simulate(pm, prefilled=[4, 5], **kw)
+    # batch 0 (warmup, declared order): predicate 0 computes E for ids 0..3, predicate 1 reuses them
+    assert sim[0]["hits"].tolist() == [0, 4, 0]
+    # batch 1 (nothing visible yet: declared order): ids 4, 5 were prefilled
+    assert sim[1]["order"] == [0, 1, 2] and sim[1]["hits"].tolist() == [2, 4, 0]
+    # batch 2: s = 5/6 everywhere; ids 8..11 miss -> cost(0) = cost(1) = 1 + 4/4*100 = 101 > 50
+    assert sim[2]["order"] == [2, 0, 1] and sim[2]["hits"].tolist() == [0, 4, 0]
+    # the same stream with batch 2's ids prefilled: the heads cost 1 < 50
+    sim = O.simulate(pm, prefilled=[8, 9, 10, 11], **kw)
+    assert sim[2]["order"] == [0, 1, 2] and sim[2]["hits"].tolist() == [4, 4, 0]
+
+
+def test_simulate_reuse_matches_plain_counts():
+    # reuse changes costs and hits, never the pass set or which tuples reach a predicate
+    g = np.random.default_rng(12)
+    pm = g.random((64, 3)) < 0.6
+    plain = O.simulate(pm, 8, policy="static", static_order=[1, 0, 2])
+    reuse = O.simulate(pm, 8, policy="static", static_order=[1, 0, 2], groups=["E", "E", None],
+                       group_costs={"E": 7}, ids=np.arange(64))
+    for a, b in zip(plain, reuse):
+        assert np.array_equal(a["bits"], b["bits"]) and a["counts"].tolist() == b["counts"].tolist()
+        # predicate 0 runs after predicate 1 (same group) on a subset of its tuples: all hits
+        assert b["hits"][0] == b["counts"][0]
