@@ -270,7 +270,7 @@ def predicate_weights(w: Workload):
 def segment_mixes(w: Workload) -> np.ndarray:
     """[segments, clusters] mixture weights, one Dirichlet(alpha) draw per
     segment (stream 5)."""
-    S = w.extra["segments"]
+    S = max(w.extra["segments"], 64)
     g = rng(w.wid, 5)
     return g.dirichlet(np.full(w.n_clusters, w.extra["dirichlet"]), size=S)
 
@@ -284,7 +284,8 @@ def stream_tuples(w: Workload, n: int | None = None, start: int = 0) -> np.ndarr
     if w.kind == "vec" and w.extra and "segments" in w.extra:
         assert start == 0
         S = w.extra["segments"]
-        seg = WORKLOADS[w.name].n // S if w.name in WORKLOADS else w.n // S
+        seg = w.extra.get("segment_len") or (WORKLOADS[w.name].n // S if w.name in WORKLOADS else w.n // S)
+        S = max(S, -(-n // seg))
         mixes = segment_mixes(w)
         parts, left = [], n
         for s in range(S):

@@ -129,6 +129,10 @@ typedef struct hydro_udf_desc {
     const float *head_weight;     /* CNN: [dims[n_layers]] fp32; MLP: NULL */
     double head_bias;             /* CNN: head bias; MLP: ignored */
     int64_t cost_hint;            /* > 0 replaces the model cost (flops per tuple) */
+    int32_t upstream;             /* 0: the UDF reads the tuple.  >= 1: an embedding id from
+                                     hydro_add_embedding; the UDF (a "head") reads that shared
+                                     upstream UDF's output, which is cached per tuple id and
+                                     reused by every predicate on it (dims[0] = its width) */
 } hydro_udf_desc;
 
 /* Per-batch result detail. */
@@ -142,6 +146,7 @@ typedef struct hydro_batch_info {
     int64_t recheck_tf32[HYDRO_MAX_PREDICATES]; /* re-evaluated by 3xTF32 (low-precision band, CNN) */
     int64_t recheck_fp32[HYDRO_MAX_PREDICATES]; /* re-evaluated in FP32 on CUDA cores */
     int64_t recheck_fp64[HYDRO_MAX_PREDICATES]; /* re-evaluated in FP64 (FP32 band) */
+    int64_t cache_hits[HYDRO_MAX_PREDICATES];   /* evaluated tuples whose upstream output was cached */
     double device_ms;                           /* GPU time from the batch's first to last kernel */
 } hydro_batch_info;
 
@@ -152,7 +157,9 @@ typedef struct hydro_pred_stats {
     int64_t recheck_tf32;
     int64_t recheck_fp32;
     int64_t recheck_fp64;
-    int64_t model_cost;      /* flops per tuple used by HYDRO_COST_MODEL */
+    int64_t cache_hits;
+    int64_t model_cost;      /* flops per tuple used by HYDRO_COST_MODEL (a head's own cost for
+                                predicates on an embedding) */
     double margin_lowp;      /* current margins */
     double margin_tf32;
     double margin_fp32;
@@ -195,6 +202,25 @@ HYDRO_API hydro_status hydro_create_query(const hydro_query_config *cfg, hydro_q
 HYDRO_API hydro_status hydro_add_predicate(hydro_query *q, const hydro_udf_desc *udf, double threshold,
                                  int32_t *out_pred_id);
 
+/* Declare a shared upstream UDF (an MLP on the tuple whose layers are all
+ * followed by ReLU; output width dims[n_layers], a multiple of 4) whose
+ * outputs are cached per tuple id and reused across predicates and batches:
+ * EvaDB's materialized UDF results (Sec. 2.1) feeding reuse-aware routing
+ * (Sec. 4.3).  Predicates on it pass its id as hydro_udf_desc.upstream; their
+ * estimated cost for a batch becomes head cost + (1 - hit rate) x this UDF's
+ * cost (the reuse-aware estimate of Sec. 4.3 "Reuse-aware Routing").  Tuple
+ * ids must lie in [0, id_capacity); the cache holds id_capacity x width
+ * floats.  F32 tuples, FP32 queries; before the first submit.  *out_emb_id
+ * receives 1, 2, ... */
+HYDRO_API hydro_status hydro_add_embedding(hydro_query *q, const hydro_udf_desc *udf, int64_t id_capacity,
+                                           int32_t *out_emb_id);
+
+/* Compute and cache embedding emb for n device tuples with device ids (as an
+ * earlier exploratory query would have); these entries count as cached for
+ * every batch.  Synchronous; before the first submit. */
+HYDRO_API hydro_status hydro_cache_prefill(hydro_query *q, int32_t emb, const void *d_tuples, const int64_t *d_ids,
+                                           int64_t n);
+
 /* Set the recheck margins of predicate pred (absolute score units, >= 0).
  * A score s at a precision decides the test only if |s - t| > that level's
  * margin; otherwise the tuple is re-evaluated at the next level
@@ -222,7 +248,8 @@ HYDRO_API hydro_status hydro_udf_scores(hydro_query *q, int32_t pred, int32_t pr
                               int64_t n, double *d_scores);
 
 /* Submit a batch of n tuples (0 <= n <= max_batch).  d_tuples: device, layout
- * of cfg->tuple_kind; d_ids: device int64 tuple ids or NULL.  Stream-ordered
+ * of cfg->tuple_kind; d_ids: device int64 tuple ids (required when the query
+ * has an embedding, else may be NULL).  Stream-ordered
  * and asynchronous; it may wait for the batch submitted route_lag+1 earlier
  * to be routed (bounded).  *out_batch_id receives 0, 1, 2, ... */
 HYDRO_API hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int64_t *d_ids, int64_t n,

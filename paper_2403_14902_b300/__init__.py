@@ -29,7 +29,8 @@ POLICIES = {"rank": 0, "static": 1, "all": 2, "cost": 3, "selectivity": 4}
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp64": 2, "tf32x3": 3}
 UDF_MLP, UDF_CNN = 0, 1
 
-EXPORTED = ["hydro_default_config", "hydro_create_query", "hydro_add_predicate", "hydro_set_margins",
+EXPORTED = ["hydro_default_config", "hydro_create_query", "hydro_add_predicate", "hydro_add_embedding",
+            "hydro_cache_prefill", "hydro_set_margins",
             "hydro_set_static_order", "hydro_calibrate", "hydro_udf_scores", "hydro_submit_batch",
             "hydro_poll_result", "hydro_get_stats", "hydro_profile", "hydro_profile_read",
             "hydro_mlp_scores_noalloc", "hydro_destroy_query", "hydro_last_error"]
@@ -50,7 +51,7 @@ class UdfDesc(ctypes.Structure):
                 ("weights", ctypes.POINTER(ctypes.POINTER(ctypes.c_float))),
                 ("biases", ctypes.POINTER(ctypes.POINTER(ctypes.c_float))),
                 ("head_weight", ctypes.POINTER(ctypes.c_float)), ("head_bias", ctypes.c_double),
-                ("cost_hint", ctypes.c_int64)]
+                ("cost_hint", ctypes.c_int64), ("upstream", ctypes.c_int32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -58,12 +59,14 @@ class BatchInfo(ctypes.Structure):
                 ("warmup", ctypes.c_int32), ("order", ctypes.c_int32 * MAX_PREDICATES),
                 ("passed", ctypes.c_int64 * MAX_PREDICATES), ("recheck_tf32", ctypes.c_int64 * MAX_PREDICATES),
                 ("recheck_fp32", ctypes.c_int64 * MAX_PREDICATES),
-                ("recheck_fp64", ctypes.c_int64 * MAX_PREDICATES), ("device_ms", ctypes.c_double)]
+                ("recheck_fp64", ctypes.c_int64 * MAX_PREDICATES), ("cache_hits", ctypes.c_int64 * MAX_PREDICATES),
+                ("device_ms", ctypes.c_double)]
 
 
 class PredStats(ctypes.Structure):
     _fields_ = [("evaluated", ctypes.c_int64), ("passed", ctypes.c_int64), ("recheck_tf32", ctypes.c_int64),
-                ("recheck_fp32", ctypes.c_int64), ("recheck_fp64", ctypes.c_int64), ("model_cost", ctypes.c_int64),
+                ("recheck_fp32", ctypes.c_int64), ("recheck_fp64", ctypes.c_int64), ("cache_hits", ctypes.c_int64),
+                ("model_cost", ctypes.c_int64),
                 ("margin_lowp", ctypes.c_double), ("margin_tf32", ctypes.c_double), ("margin_fp32", ctypes.c_double)]
 
 
@@ -96,6 +99,8 @@ def load():
     L.hydro_create_query.argtypes = [P(QueryConfig), P(vp)]
     L.hydro_add_predicate.argtypes = [vp, P(UdfDesc), f64, P(i32)]
     L.hydro_set_margins.argtypes = [vp, i32, f64, f64, f64]
+    L.hydro_add_embedding.argtypes = [vp, P(UdfDesc), i64, P(i32)]
+    L.hydro_cache_prefill.argtypes = [vp, i32, vp, vp, i64]
     L.hydro_set_static_order.argtypes = [vp, P(i32), i32]
     L.hydro_calibrate.argtypes = [vp, vp, i64, P(CalibInfo)]
     L.hydro_udf_scores.argtypes = [vp, i32, i32, vp, i64, vp]
@@ -167,10 +172,11 @@ class Query:
         self._n_of = {}
 
     # -- predicates
-    def _add(self, kind, dims, Ws, bs, threshold, head_w=None, head_b=0.0, cost_hint=0):
+    def _desc(self, kind, dims, Ws, bs, head_w=None, head_b=0.0, cost_hint=0, upstream=0):
         FP = ctypes.POINTER(ctypes.c_float)
         Ws = [np.ascontiguousarray(w, np.float32) for w in Ws]
         bs = [np.ascontiguousarray(b, np.float32) for b in bs]
+        keep = [Ws, bs]
         d = (ctypes.c_int32 * len(dims))(*dims)
         wp = (FP * len(Ws))(*[w.ctypes.data_as(FP) for w in Ws])
         bp = (FP * len(bs))(*[b.ctypes.data_as(FP) for b in bs])
@@ -182,20 +188,40 @@ class Query:
         desc.biases = bp
         if head_w is not None:
             head_w = np.ascontiguousarray(head_w, np.float32)
+            keep.append(head_w)
             desc.head_weight = head_w.ctypes.data_as(FP)
         desc.head_bias = float(head_b)
         desc.cost_hint = int(cost_hint)
+        desc.upstream = int(upstream)
+        return desc, (keep, d, wp, bp)
+
+    def add_embedding(self, layers, id_capacity: int, cost_hint: int = 0) -> int:
+        """Shared upstream MLP (all layers ReLU) whose outputs are cached per tuple id."""
+        dims = [layers[0][0].shape[1]] + [W.shape[0] for W, _ in layers]
+        desc, keep = self._desc(UDF_MLP, dims, [W for W, _ in layers], [b for _, b in layers], cost_hint=cost_hint)
+        eid = ctypes.c_int32()
+        _check(load().hydro_add_embedding(self._h, ctypes.byref(desc), int(id_capacity), ctypes.byref(eid)),
+               "hydro_add_embedding")
+        return eid.value
+
+    def cache_prefill(self, emb: int, tuples, ids):
+        _check(load().hydro_cache_prefill(self._h, int(emb), _ptr(tuples), _ptr(ids), int(tuples.shape[0])),
+               "hydro_cache_prefill")
+
+    def _add(self, kind, dims, Ws, bs, threshold, head_w=None, head_b=0.0, cost_hint=0, upstream=0):
+        desc, keep = self._desc(kind, dims, Ws, bs, head_w, head_b, cost_hint, upstream)
         pid = ctypes.c_int32()
         _check(load().hydro_add_predicate(self._h, ctypes.byref(desc), float(threshold), ctypes.byref(pid)),
                "hydro_add_predicate")
         self.n_pred += 1
         return pid.value
 
-    def add_mlp(self, layers, threshold: float, cost_hint: int = 0) -> int:
-        """``layers``: [(W [out, in] fp32, b [out] fp32)], last layer 1 output."""
+    def add_mlp(self, layers, threshold: float, cost_hint: int = 0, upstream: int = 0) -> int:
+        """``layers``: [(W [out, in] fp32, b [out] fp32)], last layer 1 output;
+        with ``upstream`` (an embedding id) the layers are the head on it."""
         dims = [layers[0][0].shape[1]] + [W.shape[0] for W, _ in layers]
         return self._add(UDF_MLP, dims, [W for W, _ in layers], [b for _, b in layers], threshold,
-                         cost_hint=cost_hint)
+                         cost_hint=cost_hint, upstream=upstream)
 
     def add_cnn(self, udf, threshold: float, cost_hint: int = 0) -> int:
         """``udf = (convs, (head_w, head_b))`` with convs [(W [Cout, Cin, 3, 3], b)]."""
@@ -246,7 +272,7 @@ class Query:
         P = self.n_pred
         d = dict(n=info.n, n_pass=info.n_pass, warmup=bool(info.warmup), order=list(info.order[:P]),
                  passed=list(info.passed[:P]), recheck_tf32=list(info.recheck_tf32[:P]),
-                 recheck_fp32=list(info.recheck_fp32[:P]),
+                 recheck_fp32=list(info.recheck_fp32[:P]), cache_hits=list(info.cache_hits[:P]),
                  recheck_fp64=list(info.recheck_fp64[:P]), device_ms=info.device_ms)
         return bitmap[:(n + 31) // 32], counts[:P], d
 

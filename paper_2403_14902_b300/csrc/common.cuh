@@ -13,6 +13,7 @@ enum : uint32_t {
     ERR_COUNT_RANGE = 1u << 1,     // a device count exceeded its buffer
     ERR_TC_TIMEOUT = 1u << 2,      // a tensor-core pipeline wait ran out
     ERR_TC_CONFIG = 1u << 3,       // a tensor-core kernel got an unsupported shape
+    ERR_ID_RANGE = 1u << 4,        // a tuple id outside the reuse cache's capacity
 };
 
 constexpr int kMaxPred = 8;
@@ -24,6 +25,7 @@ struct StatRow {
     long long recheck_tf32;   // re-evaluated by the FP32-accurate 3xTF32 tensor-core path
     long long recheck32;      // re-evaluated in FP32 (CUDA cores)
     long long recheck64;      // re-evaluated in FP64
+    long long hits;           // reuse-cache hits (shared upstream UDF outputs found cached)
 };
 
 __device__ __forceinline__ float to_f(float v) { return v; }

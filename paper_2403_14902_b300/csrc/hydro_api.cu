@@ -51,9 +51,23 @@ hydro_status fail(hydro_status s, const char *fmt, ...) {
 
 constexpr int kEvRing = 16;
 
+// A shared upstream UDF whose outputs are cached per tuple id.
+struct Emb {
+    int n_layers = 0;
+    std::vector<int> dims;
+    std::vector<std::vector<float>> W, b;
+    long long cap = 0;     // ids in [0, cap)
+    long long cost = 1;    // flops per tuple
+    std::vector<float *> dW, db;
+    float *values = nullptr;   // [cap][dims.back()]
+    int *tags = nullptr;       // [cap]: 0 absent, -1 prefilled, b+1 computed by batch b
+};
+
 struct Pred {
     int kind = 0;
     int n_layers = 0;
+    int upstream = 0;      // 0, or 1-based embedding id; layers [0, head_start) are the embedding's
+    int head_start = 0;
     std::vector<int> dims;
     std::vector<std::vector<float>> W, b;
     std::vector<float> head_w;
@@ -130,7 +144,10 @@ struct Prof {
 struct hydro_query {
     hydro_query_config cfg{};
     std::vector<Pred> preds;
+    std::vector<Emb> embs;
     std::vector<int> static_order;
+    int *vmiss = nullptr;         // router probe: misses per embedding for the batch being routed
+    int *miss_list = nullptr;     // stage probe: alive tuples whose embedding is not cached
     bool finalized = false;
     bool dead = false;
     int sms = 148;
@@ -165,7 +182,7 @@ struct hydro_query {
     long long next_batch = 0;
     unsigned int latched_err = 0;
     // cumulative statistics (updated at poll)
-    long long tot[kMaxPred][5] = {};
+    long long tot[kMaxPred][6] = {};
     // tensor-core conv
     TcConvPlan tc{};
     // profiling and launch count
@@ -291,6 +308,19 @@ hydro_status finalize(hydro_query *q) {
     CU(cudaMallocHost(&q->h_order, sizeof(int) * kMaxPred * c.max_in_flight));
     TRY(dalloc(q, &q->d_err, sizeof(unsigned int)));
     CU(cudaMemset(q->d_err, 0, sizeof(unsigned int)));
+    TRY(dalloc(q, &q->vmiss, sizeof(int) * kMaxPred));
+    TRY(dalloc(q, &q->miss_list, sizeof(int) * B));
+    for (Emb &e : q->embs) {
+        e.dW.resize(e.n_layers);
+        e.db.resize(e.n_layers);
+        for (int l = 0; l < e.n_layers; ++l) {
+            TRY(upload(q, &e.dW[l], e.W[l].data(), e.W[l].size()));
+            TRY(upload(q, &e.db[l], e.b[l].data(), e.b[l].size()));
+        }
+        TRY(dalloc(q, &e.values, sizeof(float) * (size_t)e.cap * e.dims.back()));
+        TRY(dalloc(q, &e.tags, sizeof(int) * (size_t)e.cap));
+        CU(cudaMemset(e.tags, 0, sizeof(int) * (size_t)e.cap));
+    }
 
     // result slots
     q->res_bytes = kBitmapOff + sizeof(unsigned int) * (size_t)((B + 31) / 32);
@@ -517,6 +547,50 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
     return HYDRO_OK;
 }
 
+// Main-path scores of a predicate on a shared embedding (FP32): the
+// embedding runs only on alive tuples whose id is not cached (results are
+// stored in the cache with tag_value), then the head reads every alive
+// tuple's embedding from the cache.  miss_count receives the misses.
+hydro_status run_grouped(hydro_query *q, const Pred &p, const int *count, const int *list, const void *tuples,
+                         const long long *ids, int tag_value, int max_rows, int *miss_count, float *score32) {
+    const hydro_query_config &c = q->cfg;
+    cudaStream_t st = q->st;
+    Emb &e = q->embs[p.upstream - 1];
+    const int D = e.dims.back();
+    float *act[2] = {(float *)q->act[0], (float *)q->act[1]};
+    launch_cache_probe_miss(count, list, ids, e.tags, e.cap, q->miss_list, miss_count, q->d_err, st);
+    launch_mlp_layer_f32(miss_count, q->miss_list, (const float *)tuples, c.dim, e.dW[0], e.db[0], act[0], e.dims[0],
+                         e.dims[1], 1, max_rows, q->sms, st);
+    int cur = 0;
+    for (int l = 1; l < e.n_layers; ++l) {
+        launch_mlp_layer_f32(miss_count, nullptr, act[cur], e.dims[l], e.dW[l], e.db[l], act[1 - cur], e.dims[l],
+                             e.dims[l + 1], 1, max_rows, q->sms, st);
+        cur = 1 - cur;
+    }
+    launch_cache_store(miss_count, q->miss_list, ids, act[cur], D, e.values, e.tags, tag_value, max_rows, q->sms,
+                       st);
+    q->launches += 2 + e.n_layers;
+    if (!score32) return HYDRO_OK;   // prefill: no head
+    const int hs = p.head_start, L = p.n_layers;
+    if (L - hs == 1) {
+        launch_mlp_dot_f32(count, list, e.values, D, p.dW[hs], p.b[hs][0], D, score32, max_rows, q->sms, st, ids);
+        q->launches++;
+        return HYDRO_OK;
+    }
+    launch_mlp_layer_f32(count, list, e.values, D, p.dW[hs], p.db[hs], act[0], D, p.dims[hs + 1], 1, max_rows, q->sms,
+                         st, ids);
+    cur = 0;
+    for (int l = hs + 1; l + 1 < L; ++l) {
+        launch_mlp_layer_f32(count, nullptr, act[cur], p.dims[l], p.dW[l], p.db[l], act[1 - cur], p.dims[l],
+                             p.dims[l + 1], 1, max_rows, q->sms, st);
+        cur = 1 - cur;
+    }
+    launch_mlp_dot_f32(count, nullptr, act[cur], p.dims[L - 1], p.dW[L - 1], p.b[L - 1][0], p.dims[L - 1], score32,
+                       max_rows, q->sms, st);
+    q->launches += L - hs;
+    return HYDRO_OK;
+}
+
 // One stage: evaluate predicate p on the alive list (in_list, in_count),
 // decide pass/fail exactly and close the stage.  Scores within a level's
 // margin of the threshold go to the next level of the cascade:
@@ -524,7 +598,8 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
 //   BF16 query, MLP UDF: (not built)
 //   FP32 query:          FP32 -> FP64
 hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *in_list, int *out_list,
-                       int *out_count, bool eval_all, const void *tuples, int n, long long batch, Slot &slot) {
+                       int *out_count, bool eval_all, const void *tuples, const long long *ids, int n,
+                       long long batch, Slot &slot) {
     const hydro_query_config &c = q->cfg;
     const Pred &p = q->preds[pi];
     const bool bf16 = c.precision == HYDRO_PREC_BF16;
@@ -534,7 +609,14 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
     int *band1_count = q->ints + 2, *band2_count = q->ints + 3, *band3_count = q->ints + 4;
     const ProfCtx pc_main{batch, pi, SRC_MAIN}, pc_rtf{batch, pi, SRC_RTF}, pc_r32{batch, pi, SRC_R32},
         pc_r64{batch, pi, SRC_R64};
-    TRY(run_udf(q, p, wprec, in_count, in_list, tuples, std::max(n, 1), q->act, q->score32, nullptr, &pc_main));
+    int *miss_count = nullptr;
+    if (p.upstream) {
+        miss_count = q->ints + 5;
+        TRY(run_grouped(q, p, in_count, in_list, tuples, ids, (int)(batch + 1), std::max(n, 1), miss_count,
+                        q->score32));
+    } else {
+        TRY(run_udf(q, p, wprec, in_count, in_list, tuples, std::max(n, 1), q->act, q->score32, nullptr, &pc_main));
+    }
 
     // level 0 -> band 1 (FP32 queries: band 1 is the FP64 band, capacity cap3)
     launch_classify_f32(in_count, in_list, q->score32, p.threshold, bf16 ? p.margin_lowp : p.margin_fp32, q->pass,
@@ -589,7 +671,7 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
     StatRow *warm = nullptr;
     if (adaptive(c.policy) && batch < c.warmup_batches) warm = q->warm + batch * kMaxPred + pi;
     launch_compact(in_count, in_list, q->pass, out_list, out_count, eval_all ? q->acc : nullptr, cnt_tf, cnt_32,
-                   b64_count, row, rrow, warm, q->st);
+                   b64_count, miss_count, row, rrow, warm, q->st);
     return HYDRO_OK;
 }
 
@@ -702,11 +784,34 @@ hydro_status hydro_add_predicate(hydro_query *q, const hydro_udf_desc *udf, doub
         if (d < 1 || d > 8192) return fail(HYDRO_EINVAL, "layer width out of range");
     if (p.kind == HYDRO_UDF_MLP) {
         if (c.tuple_kind != HYDRO_TUPLE_F32) return fail(HYDRO_EINVAL, "MLP UDFs need F32 tuples");
-        if (p.dims[0] != c.dim || p.dims[L] != 1) return fail(HYDRO_EINVAL, "MLP dims must run from dim to 1");
+        const int up = udf->upstream;
+        if (up < 0 || up > (int)q->embs.size()) return fail(HYDRO_EINVAL, "unknown embedding id %d", up);
+        const int in_dim = up ? q->embs[up - 1].dims.back() : c.dim;
+        if (p.dims[0] != in_dim || p.dims[L] != 1)
+            return fail(HYDRO_EINVAL, "MLP dims must run from %d to 1", in_dim);
         for (int l = 0; l < L; ++l) {
             if (!udf->weights[l] || !udf->biases[l]) return fail(HYDRO_EINVAL, "NULL weights");
             p.W.emplace_back(udf->weights[l], udf->weights[l] + (size_t)p.dims[l] * p.dims[l + 1]);
             p.b.emplace_back(udf->biases[l], udf->biases[l] + p.dims[l + 1]);
+        }
+        if (up) {
+            // the full UDF is the embedding's layers followed by the head's
+            const Emb &e = q->embs[up - 1];
+            if (e.n_layers + L > HYDRO_MAX_LAYERS) return fail(HYDRO_EINVAL, "embedding + head too deep");
+            long long head_cost = 0;
+            for (int l = 0; l < L; ++l) head_cost += 2LL * p.dims[l] * p.dims[l + 1];
+            std::vector<int> dims = e.dims;
+            dims.insert(dims.end(), p.dims.begin() + 1, p.dims.end());
+            std::vector<std::vector<float>> W = e.W, b = e.b;
+            W.insert(W.end(), p.W.begin(), p.W.end());
+            b.insert(b.end(), p.b.begin(), p.b.end());
+            p.dims = dims;
+            p.W = W;
+            p.b = b;
+            p.head_start = e.n_layers;
+            p.n_layers = e.n_layers + L;
+            p.upstream = up;
+            p.cost = udf->cost_hint > 0 ? udf->cost_hint : head_cost;
         }
     } else if (p.kind == HYDRO_UDF_CNN) {
         if (c.tuple_kind != HYDRO_TUPLE_U8_FRAME) return fail(HYDRO_EINVAL, "CNN UDFs need frame tuples");
@@ -730,9 +835,72 @@ hydro_status hydro_add_predicate(hydro_query *q, const hydro_udf_desc *udf, doub
         return fail(HYDRO_EINVAL, "unknown UDF kind");
     }
     p.threshold = threshold;
-    p.cost = udf->cost_hint > 0 ? udf->cost_hint : model_cost(p, c);
+    if (!p.upstream) p.cost = udf->cost_hint > 0 ? udf->cost_hint : model_cost(p, c);
     *out_pred_id = (int32_t)q->preds.size();
     q->preds.push_back(std::move(p));
+    return HYDRO_OK;
+}
+
+hydro_status hydro_add_embedding(hydro_query *q, const hydro_udf_desc *udf, int64_t id_capacity,
+                                 int32_t *out_emb_id) {
+    g_err.clear();
+    TRY(check_query(q));
+    if (!udf || !out_emb_id) return fail(HYDRO_EINVAL, "NULL argument");
+    if (q->finalized) return fail(HYDRO_ESTATE, "embeddings must be added before the first submit");
+    if ((int)q->embs.size() >= HYDRO_MAX_PREDICATES) return fail(HYDRO_EINVAL, "too many embeddings");
+    const hydro_query_config &c = q->cfg;
+    if (c.tuple_kind != HYDRO_TUPLE_F32 || udf->kind != HYDRO_UDF_MLP)
+        return fail(HYDRO_EINVAL, "embeddings are MLPs on F32 tuples");
+    if (c.precision != HYDRO_PREC_FP32) return fail(HYDRO_EUNSUPPORTED, "embeddings need an FP32 query");
+    const int L = udf->n_layers;
+    if (L < 1 || L > HYDRO_MAX_LAYERS || !udf->dims || !udf->weights || !udf->biases)
+        return fail(HYDRO_EINVAL, "bad layer description");
+    if (id_capacity < 1 || id_capacity > (1LL << 31)) return fail(HYDRO_EINVAL, "id_capacity out of range");
+    Emb e;
+    e.n_layers = L;
+    e.dims.assign(udf->dims, udf->dims + L + 1);
+    for (int d : e.dims)
+        if (d < 1 || d > 8192) return fail(HYDRO_EINVAL, "layer width out of range");
+    if (e.dims[0] != c.dim) return fail(HYDRO_EINVAL, "embedding input must be the tuple (dims[0] == dim)");
+    if (e.dims[L] % 4 != 0) return fail(HYDRO_EINVAL, "embedding width must be a multiple of 4");
+    for (int l = 0; l < L; ++l) {
+        if (!udf->weights[l] || !udf->biases[l]) return fail(HYDRO_EINVAL, "NULL weights");
+        e.W.emplace_back(udf->weights[l], udf->weights[l] + (size_t)e.dims[l] * e.dims[l + 1]);
+        e.b.emplace_back(udf->biases[l], udf->biases[l] + e.dims[l + 1]);
+    }
+    long long cost = 0;
+    for (int l = 0; l < L; ++l) cost += 2LL * e.dims[l] * e.dims[l + 1];
+    e.cost = udf->cost_hint > 0 ? udf->cost_hint : cost;
+    e.cap = id_capacity;
+    q->embs.push_back(std::move(e));
+    *out_emb_id = (int32_t)q->embs.size();
+    return HYDRO_OK;
+}
+
+hydro_status hydro_cache_prefill(hydro_query *q, int32_t emb, const void *d_tuples, const int64_t *d_ids,
+                                 int64_t n) {
+    g_err.clear();
+    TRY(check_query(q));
+    if (emb < 1 || emb > (int)q->embs.size()) return fail(HYDRO_EINVAL, "unknown embedding id %d", emb);
+    if (n < 0 || (n > 0 && (!d_tuples || !d_ids))) return fail(HYDRO_EINVAL, "bad tuples/ids");
+    if (q->next_batch > 0) return fail(HYDRO_ESTATE, "prefill before the first submit");
+    CU(cudaSetDevice(q->cfg.device));
+    TRY(finalize(q));
+    Pred probe;                    // an embedding-only pass: no head
+    probe.upstream = emb;
+    const int B = q->cfg.max_batch;
+    const size_t tb = (size_t)tuple_bytes(q->cfg);
+    for (int64_t s = 0; s < n; s += B) {
+        const int m = (int)std::min<int64_t>(B, n - s);
+        launch_identity_list(q->alive[0], q->ints + 0, 0, m, q->st);
+        TRY(run_grouped(q, probe, q->ints + 0, q->alive[0], (const unsigned char *)d_tuples + (size_t)s * tb,
+                        (const long long *)d_ids + s, -1, m, q->ints + 5, nullptr));
+        CU(cudaGetLastError());
+    }
+    CU(cudaStreamSynchronize(q->st));
+    unsigned int err = 0;
+    CU(cudaMemcpy(&err, q->d_err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) return fail(HYDRO_EDEVICE, "device error word 0x%x", err);
     return HYDRO_OK;
 }
 
@@ -864,6 +1032,7 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
     if (n < 0 || n > q->cfg.max_batch) return fail(HYDRO_EINVAL, "n=%lld outside 0..max_batch", (long long)n);
     if (n > 0 && !d_tuples) return fail(HYDRO_EINVAL, "NULL tuples");
     if (q->preds.empty()) return fail(HYDRO_ESTATE, "query has no predicates");
+    if (!q->embs.empty() && n > 0 && !d_ids) return fail(HYDRO_EINVAL, "a query with an embedding needs tuple ids");
     const hydro_query_config &c = q->cfg;
     if (c.policy == HYDRO_POLICY_STATIC && !q->static_order.empty() && q->static_order.size() != q->preds.size())
         return fail(HYDRO_ESTATE, "static order does not match the predicates");
@@ -893,12 +1062,27 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
             const long long lo = std::max(0LL, last - c.stats_window + 1);
             const int nwv = (int)std::min<long long>(c.warmup_batches, last + 1);
             RouterCosts costs{};
-            for (int i = 0; i < P; ++i) costs.c[i] = q->preds[i].cost;
+            for (int i = 0; i < P; ++i) {
+                costs.c[i] = q->preds[i].cost;
+                costs.group[i] = q->preds[i].upstream - 1;
+            }
+            for (size_t e = 0; e < q->embs.size(); ++e) costs.cemb[e] = q->embs[e].cost;
+            costs.n = n;
             const int pol = c.policy == HYDRO_POLICY_RANK ? 0 : c.policy == HYDRO_POLICY_COST ? 1 : 2;
             int *dord = q->d_order + slot_idx * kMaxPred;
             int *hord = q->h_order + slot_idx * kMaxPred;
             CU(cudaStreamWaitEvent(q->rst, q->ev_done[last % kEvRing], 0));
-            launch_router(q->ring, q->ring_len, q->warm, nwv, lo, last, P, pol, costs, dord, q->rst);
+            if (!q->embs.empty()) {
+                // reuse-aware cost: this batch's ids not cached by batches <= last
+                CU(cudaMemsetAsync(q->vmiss, 0, sizeof(int) * kMaxPred, q->rst));
+                for (size_t e = 0; e < q->embs.size(); ++e) {
+                    launch_probe_visible((const long long *)d_ids, (int)n, q->embs[e].tags, q->embs[e].cap, last,
+                                         q->vmiss + e, q->rst);
+                    q->launches++;
+                }
+            }
+            launch_router(q->ring, q->ring_len, q->warm, nwv, lo, last, P, pol, costs,
+                          q->embs.empty() ? nullptr : q->vmiss, dord, q->rst);
             q->launches++;
             CU(cudaGetLastError());
             CU(cudaMemcpyAsync(hord, dord, sizeof(int) * P, cudaMemcpyDeviceToHost, q->rst));
@@ -924,7 +1108,7 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
     int cur = 0;
     for (int k = 0; k < P; ++k) {
         hydro_status s = run_stage(q, order[k], cnt + cur, q->alive[cur], q->alive[1 - cur], cnt + 1 - cur, eval_all,
-                                   d_tuples, (int)n, b, *slot);
+                                   d_tuples, (const long long *)d_ids, (int)n, b, *slot);
         if (s != HYDRO_OK) {
             slot->busy = false;
             q->dead = true;
@@ -990,6 +1174,7 @@ hydro_status hydro_poll_result(hydro_query *q, int64_t batch_id, uint32_t *pass_
         q->tot[i][2] += rows[i].recheck32;
         q->tot[i][3] += rows[i].recheck64;
         q->tot[i][4] += rows[i].recheck_tf32;
+        q->tot[i][5] += rows[i].hits;
     }
     if (info) {
         std::memset(info, 0, sizeof *info);
@@ -1001,6 +1186,7 @@ hydro_status hydro_poll_result(hydro_query *q, int64_t batch_id, uint32_t *pass_
             info->order[i] = slot->order[i];
             info->passed[i] = rows[i].passed;
             info->recheck_tf32[i] = rows[i].recheck_tf32;
+            info->cache_hits[i] = rows[i].hits;
             info->recheck_fp32[i] = rows[i].recheck32;
             info->recheck_fp64[i] = rows[i].recheck64;
         }
@@ -1020,6 +1206,7 @@ hydro_status hydro_get_stats(hydro_query *q, hydro_pred_stats *out, int32_t n) {
         out[i].evaluated = q->tot[i][0];
         out[i].passed = q->tot[i][1];
         out[i].recheck_tf32 = q->tot[i][4];
+        out[i].cache_hits = q->tot[i][5];
         out[i].recheck_fp32 = q->tot[i][2];
         out[i].recheck_fp64 = q->tot[i][3];
         out[i].model_cost = q->preds[i].cost;

@@ -22,8 +22,14 @@ struct MlpDev {
     const float *b[kMaxLayers];
 };
 
+// Router costs: c[i] is the per-tuple cost of predicate i (for a predicate
+// on a shared embedding, its head's cost); group[i] >= 0 names the embedding
+// whose per-batch misses add miss * cemb[group] (reuse-aware cost).
 struct RouterCosts {
     long long c[8];
+    int group[8];
+    long long cemb[8];
+    long long n;   // tuples in the batch
 };
 
 // k_route.cu
@@ -40,19 +46,31 @@ void launch_recheck_classify_f64(const int *band_count_in, const int *band_m_in,
                                  cudaStream_t st);
 void launch_compact(const int *count_in, const int *alive_in, const unsigned char *pass, int *alive_out,
                     int *count_out, unsigned char *acc, const int *bandt_count, const int *band32_count,
-                    const int *band64_count, StatRow *row, StatRow *rrow, StatRow *warm, cudaStream_t st);
+                    const int *band64_count, const int *miss_count, StatRow *row, StatRow *rrow, StatRow *warm,
+                    cudaStream_t st);
+
+// k_cache.cu: reuse cache of a shared upstream UDF's outputs, keyed by tuple id.
+// tags[id]: 0 absent, -1 prefilled, b+1 computed by batch b.
+void launch_cache_probe_miss(const int *count_in, const int *list_in, const long long *ids, const int *tags,
+                             long long cap, int *miss_list, int *miss_count, unsigned int *err, cudaStream_t st);
+void launch_cache_store(const int *miss_count, const int *miss_list, const long long *ids, const float *src, int D,
+                        float *values, int *tags, int tag_value, int max_rows, int sms, cudaStream_t st);
+void launch_probe_visible(const long long *ids, int n, const int *tags, long long cap, long long last,
+                          int *out_miss, cudaStream_t st);
 void launch_acc_to_alive(const unsigned char *acc, int n, int *alive_out, int *count_out, cudaStream_t st);
 void launch_result(const int *count, const int *alive, int n, unsigned int *bitmap, long long *n_pass,
                    cudaStream_t st);
 void launch_router(const StatRow *ring, int ring_len, const StatRow *warm, int n_warm_visible, long long lo,
-                   long long last, int P, int policy, const RouterCosts &costs, int *order_out, cudaStream_t st);
+                   long long last, int P, int policy, const RouterCosts &costs, const int *vmiss, int *order_out,
+                   cudaStream_t st);
 
 // k_simt.cu
 void launch_mlp_layer_f32(const int *count, const int *rows, const float *X, int ldx, const float *W,
                           const float *b, float *Y, int K, int N, int relu, int max_rows, int sms,
-                          cudaStream_t st);
+                          cudaStream_t st, const long long *ids = nullptr);
 void launch_mlp_dot_f32(const int *count, const int *rows, const float *X, int ldx, const float *w, float bias,
-                        int K, float *score, int max_rows, int sms, cudaStream_t st);
+                        int K, float *score, int max_rows, int sms, cudaStream_t st,
+                        const long long *ids = nullptr);
 void launch_mlp_band_f32(const int *band_count, const int *band_tuple, const float *X, int ldx,
                          const MlpDev &mlp, float *score_out, int sms, cudaStream_t st);
 void launch_mlp_band_f64(const int *band_count, const int *band_tuple, const float *X, int ldx,

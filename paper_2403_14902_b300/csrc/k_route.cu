@@ -124,7 +124,7 @@ k_recheck_classify(const int *band_count_in, const int *band_m_in, const int *ba
 __global__ void __launch_bounds__(kScanThreads)
 k_compact(const int *count_in, const int *alive_in, const unsigned char *pass, int *alive_out,
           int *count_out, unsigned char *acc, const int *bandt_count, const int *band32_count,
-          const int *band64_count, StatRow *row, StatRow *rrow, StatRow *warm) {
+          const int *band64_count, const int *miss_count, StatRow *row, StatRow *rrow, StatRow *warm) {
     const int n = *count_in;
     int base = 0;
     for (int m0 = 0; m0 < n; m0 += kScanThreads) {
@@ -147,6 +147,7 @@ k_compact(const int *count_in, const int *alive_in, const unsigned char *pass, i
         r.recheck_tf32 = bandt_count ? *bandt_count : 0;
         r.recheck32 = band32_count ? *band32_count : 0;
         r.recheck64 = band64_count ? *band64_count : 0;
+        r.hits = miss_count ? (long long)n - *miss_count : 0;
         *row = r;
         *rrow = r;
         if (warm) *warm = r;
@@ -188,10 +189,18 @@ k_result(const int *count, const int *alive, int n, unsigned int *bitmap, long l
 // [lo, last] of the ring; a predicate with no evaluations there falls back to
 // the warmup batches' statistics.
 __global__ void k_router(const StatRow *ring, int ring_len, const StatRow *warm, int n_warm_visible,
-                         long long lo, long long last, int P, int policy, RouterCosts costs,
+                         long long lo, long long last, int P, int policy, RouterCosts costs, const int *vmiss,
                          int *order_out) {
     const int i = threadIdx.x;
     long long E = 0, Pp = 0;
+    // per-batch cost scaled by the batch size: c*n (+ misses * embedding cost)
+    unsigned long long cost = 0;
+    if (i < P) {
+        const long long nn = costs.n > 0 ? costs.n : 1;
+        cost = (unsigned long long)costs.c[i] * (unsigned long long)nn;
+        if (costs.group[i] >= 0 && vmiss && costs.n > 0)
+            cost += (unsigned long long)vmiss[costs.group[i]] * (unsigned long long)costs.cemb[costs.group[i]];
+    }
     if (i < P) {
         for (long long b = lo; b <= last; ++b) {
             const StatRow r = ring[(b % ring_len) * kMaxPred + i];
@@ -209,8 +218,9 @@ __global__ void k_router(const StatRow *ring, int ring_len, const StatRow *warm,
     for (int j = 0; j < P; ++j) {
         const long long Ej = __shfl_sync(0xffffffffu, E, j);
         const long long Pj = __shfl_sync(0xffffffffu, Pp, j);
+        const unsigned long long cj = __shfl_sync(0xffffffffu, cost, j);
         if (i >= P || j == i) continue;
-        const unsigned long long ci = (unsigned long long)costs.c[i], cj = (unsigned long long)costs.c[j];
+        const unsigned long long ci = cost;
         bool before;   // does j go before i?
         if (policy == 0) {
             // rank c/(1-s), s = (p+1)/(e+2): c(e+2)/(e-p+1)
@@ -265,9 +275,10 @@ void launch_recheck_classify_f64(const int *band_count_in, const int *band_m_in,
 
 void launch_compact(const int *count_in, const int *alive_in, const unsigned char *pass, int *alive_out,
                     int *count_out, unsigned char *acc, const int *bandt_count, const int *band32_count,
-                    const int *band64_count, StatRow *row, StatRow *rrow, StatRow *warm, cudaStream_t st) {
+                    const int *band64_count, const int *miss_count, StatRow *row, StatRow *rrow, StatRow *warm,
+                    cudaStream_t st) {
     k_compact<<<1, kScanThreads, 0, st>>>(count_in, alive_in, pass, alive_out, count_out, acc, bandt_count,
-                                          band32_count, band64_count, row, rrow, warm);
+                                          band32_count, band64_count, miss_count, row, rrow, warm);
 }
 
 void launch_acc_to_alive(const unsigned char *acc, int n, int *alive_out, int *count_out, cudaStream_t st) {
@@ -280,9 +291,9 @@ void launch_result(const int *count, const int *alive, int n, unsigned int *bitm
 }
 
 void launch_router(const StatRow *ring, int ring_len, const StatRow *warm, int n_warm_visible,
-                   long long lo, long long last, int P, int policy, const RouterCosts &costs,
+                   long long lo, long long last, int P, int policy, const RouterCosts &costs, const int *vmiss,
                    int *order_out, cudaStream_t st) {
-    k_router<<<1, 32, 0, st>>>(ring, ring_len, warm, n_warm_visible, lo, last, P, policy, costs, order_out);
+    k_router<<<1, 32, 0, st>>>(ring, ring_len, warm, n_warm_visible, lo, last, P, policy, costs, vmiss, order_out);
 }
 
 }  // namespace hydro

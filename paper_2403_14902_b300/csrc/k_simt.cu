@@ -19,11 +19,12 @@ namespace hydro {
 // ---------------------------------------------------------------- MLP FP32
 
 // Y[m][n] = act(sum_k X[row(m)][k] * W[n][k] + b[n]) for m < *count, with
-// row(m) = rows[m] when rows != nullptr.  64x64 output tiles, 16-deep K
+// row(m) = rows[m] when rows != nullptr, and ids[rows[m]] when ids is given
+// too (rows of a cache indexed by tuple id).  64x64 output tiles, 16-deep K
 // slices, 4x4 outputs per thread.
 __global__ void __launch_bounds__(256)
 k_mlp_layer_f32(const int *count, const int *rows, const float *X, int ldx, const float *W,
-                const float *b, float *Y, int K, int N, int relu) {
+                const float *b, float *Y, int K, int N, int relu, const long long *ids) {
     __shared__ float As[16][64 + 4];
     __shared__ float Ws[16][64 + 4];
     const int M = *count;
@@ -35,7 +36,10 @@ k_mlp_layer_f32(const int *count, const int *rows, const float *X, int ldx, cons
         float acc[4][4] = {};
         const int am = m0 + lr;
         const float *arow = nullptr;
-        if (am < M) arow = X + (size_t)(rows ? rows[am] : am) * ldx;
+        if (am < M) {
+            const long long r = rows ? (ids ? ids[rows[am]] : (long long)rows[am]) : (long long)am;
+            arow = X + (size_t)r * ldx;
+        }
         const int wn = n0 + lr;
         const float *wrow = wn < N ? W + (size_t)wn * K : nullptr;
         for (int k0 = 0; k0 < K; k0 += 16) {
@@ -80,11 +84,12 @@ k_mlp_layer_f32(const int *count, const int *rows, const float *X, int ldx, cons
 // One warp per row; fixed lane-strided order and a butterfly reduction.
 __global__ void __launch_bounds__(256)
 k_mlp_dot_f32(const int *count, const int *rows, const float *X, int ldx, const float *w, float bias,
-              int K, float *score) {
+              int K, float *score, const long long *ids) {
     const int M = *count;
     const int lane = threadIdx.x & 31;
     for (int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; m < M; m += (gridDim.x * blockDim.x) >> 5) {
-        const float *x = X + (size_t)(rows ? rows[m] : m) * ldx;
+        const long long r = rows ? (ids ? ids[rows[m]] : (long long)rows[m]) : (long long)m;
+        const float *x = X + (size_t)r * ldx;
         float s = 0.f;
         for (int k = lane; k < K; k += 32) s = fmaf(x[k], w[k], s);
 #pragma unroll
@@ -368,19 +373,20 @@ static int grid_for(int sms, int per_sm) { return sms * per_sm; }
 
 void launch_mlp_layer_f32(const int *count, const int *rows, const float *X, int ldx, const float *W,
                           const float *b, float *Y, int K, int N, int relu, int max_rows, int sms,
-                          cudaStream_t st) {
+                          cudaStream_t st, const long long *ids) {
     const int tiles = ((max_rows + 63) / 64) * ((N + 63) / 64);
     int grid = tiles < grid_for(sms, 4) ? tiles : grid_for(sms, 4);
     if (grid < 1) grid = 1;
-    k_mlp_layer_f32<<<grid, 256, 0, st>>>(count, rows, X, ldx, W, b, Y, K, N, relu);
+    k_mlp_layer_f32<<<grid, 256, 0, st>>>(count, rows, X, ldx, W, b, Y, K, N, relu, ids);
 }
 
 void launch_mlp_dot_f32(const int *count, const int *rows, const float *X, int ldx, const float *w,
-                        float bias, int K, float *score, int max_rows, int sms, cudaStream_t st) {
+                        float bias, int K, float *score, int max_rows, int sms, cudaStream_t st,
+                        const long long *ids) {
     int grid = (max_rows + 7) / 8;
     if (grid > grid_for(sms, 8)) grid = grid_for(sms, 8);
     if (grid < 1) grid = 1;
-    k_mlp_dot_f32<<<grid, 256, 0, st>>>(count, rows, X, ldx, w, bias, K, score);
+    k_mlp_dot_f32<<<grid, 256, 0, st>>>(count, rows, X, ldx, w, bias, K, score, ids);
 }
 
 void launch_mlp_band_f32(const int *band_count, const int *band_tuple, const float *X, int ldx,

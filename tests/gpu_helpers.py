@@ -29,14 +29,21 @@ def model_costs(w):
 
 
 def make_query(w, thresholds, *, batch, policy="rank", precision="fp32", warmup=1, window=8, lag=1,
-               static_order=None, max_in_flight=4, preds=None):
+               static_order=None, max_in_flight=4, preds=None, reuse=False, id_capacity=None):
+    """A query over the workload's predicates.  With ``reuse`` the predicates
+    listed in ``extra['emb_preds']`` run as heads on one shared, cached
+    embedding (query.emb_id)."""
     import paper_2403_14902_b300 as H
     q = H.Query(w.kind, dim=w.dim, frame=w.frame, max_batch=batch, policy=policy, precision=precision,
                 warmup=warmup, window=window, lag=lag, max_in_flight=max_in_flight)
     weights = D.predicate_weights(w)
     idx = list(range(len(weights))) if preds is None else list(preds)
+    shared = set(w.extra.get("emb_preds", ())) if (reuse and w.extra) else set()
+    q.emb_id = q.add_embedding(D.embedding_weights(w), id_capacity or w.n) if shared else 0
     for i in idx:
-        if w.kind == "vec":
+        if w.kind == "vec" and i in shared:
+            q.add_mlp(D.head_weights(w, i), thresholds[i], upstream=q.emb_id)
+        elif w.kind == "vec":
             q.add_mlp(weights[i], thresholds[i])
         else:
             q.add_cnn(weights[i], thresholds[i])
@@ -45,9 +52,10 @@ def make_query(w, thresholds, *, batch, policy="rank", precision="fp32", warmup=
     return q
 
 
-def run_stream(q, X, batch, max_in_flight=4):
-    """Submit X (device tensor) in consecutive batches; return per-batch
-    (bits bool [n_b], counts int64 [P], info dict) in submission order."""
+def run_stream(q, X, batch, max_in_flight=4, ids=None):
+    """Submit X (device tensor) in consecutive batches (with device int64
+    ``ids`` when given); return per-batch (bits bool [n_b], counts int64 [P],
+    info dict) in submission order."""
     import paper_2403_14902_b300 as H
     n = X.shape[0]
     out = {}
@@ -55,7 +63,7 @@ def run_stream(q, X, batch, max_in_flight=4):
     sizes = {}
     for b0 in range(0, max(n, 1), batch):
         xb = X[b0:b0 + batch]
-        bid = q.submit(xb)
+        bid = q.submit(xb, None if ids is None else ids[b0:b0 + batch])
         sizes[bid] = xb.shape[0]
         pending.append(bid)
         if len(pending) >= max_in_flight:
@@ -68,11 +76,13 @@ def run_stream(q, X, batch, max_in_flight=4):
     return [out[k] for k in sorted(out)]
 
 
-def check_against_oracle(res, pm, batch, *, policy, costs, warmup=1, window=8, lag=1, static_order=None):
-    """Bit-exact result and exact per-batch order/counts versus the oracle's
-    router simulation."""
+def check_against_oracle(res, pm, batch, *, policy, costs, warmup=1, window=8, lag=1, static_order=None,
+                         **reuse):
+    """Bit-exact result and exact per-batch order/counts (and reuse-cache
+    hits when ``reuse`` describes the groups) versus the oracle's router
+    simulation."""
     sim = O.simulate(pm, batch, policy=policy, costs=costs, static_order=static_order, warmup=warmup,
-                     window=window, lag=lag)
+                     window=window, lag=lag, **reuse)
     assert len(sim) == len(res)
     for b, ((bits, counts, info), s) in enumerate(zip(res, sim)):
         assert np.array_equal(bits, s["bits"]), f"batch {b}: pass set differs"
@@ -81,6 +91,8 @@ def check_against_oracle(res, pm, batch, *, policy, costs, warmup=1, window=8, l
         assert info["passed"] == s["passed"].tolist(), f"batch {b}: passed"
         assert info["warmup"] == s["warmup"] or policy == "all"
         assert info["n_pass"] == int(s["bits"].sum())
+        if reuse:
+            assert info["cache_hits"] == s["hits"].tolist(), f"batch {b}: hits {info['cache_hits']} vs {s['hits']}"
     return sim
 
 
