@@ -11,7 +11,13 @@ One step = the whole stream through the query (64 batches submitted and
 polled).  Inputs (805 MB) exceed L2 (126 MB), so no flush is needed between
 steps.  Printed as one JSON line on rank 0.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload cnn4|drift5]
+
+``--workload drift5`` measures the drifting 1,048,576-tuple stream (512-d
+fp32, five MLP predicates, two of them heads on a shared embedding whose
+outputs are cached per tuple id): adaptive reuse-aware rank routing against
+the best static order (profiled selectivities, brute force over orders) and
+the declared order, all FP32 with the FP64 recheck.
 
 Under torchrun (N > 1) every rank runs an independent replica of the
 workload on its own GPU (the path shards by tuples with no exchange step);
@@ -46,6 +52,20 @@ def load_peaks():
             d = json.load(f)
         return d, "measured"
     return dict(PEAKS_FALLBACK), "fallback"
+
+
+def measured_traffic_ratio():
+    """DRAM bytes / algorithmic bytes of the tensor-core BF16 conv, from the
+    committed ncu summary (1,024-frame 128->128 launch), or None."""
+    p = os.path.join(ROOT, "profiles", "conv3x3_tc_bf16__cnn4_layers.md")
+    try:
+        with open(p) as f:
+            for line in f:
+                if line.startswith("| DRAM traffic / algorithmic bytes"):
+                    return float(line.split("|")[2].split("=")[-1].strip())
+    except (OSError, ValueError, IndexError):
+        return None
+    return None
 
 
 def thresholds(name):
@@ -208,7 +228,287 @@ def cpu_baseline(w, th, n_frames=32, start=0):
     dt = time.perf_counter() - t0
     O.result_bits(O.pass_matrix(S, th))
     return {"value": n_frames / dt, "unit": "tuples/s", "cores": O.threads(), "kind": "oracle",
-            "sample": f"{n_frames} frames of the {w.n}-frame stream, all 4 UDFs in FP64 ({dt:.1f} s)"}
+            "sample": f"{n_frames} tuples of the {w.n}-tuple stream, every UDF in FP64 ({dt:.1f} s)"}
+
+
+def fp32_simt_peak_tflops():
+    """CUDA-core FP32 peak from unit counts and clocks: SMs x 128 FP32 lanes x
+    2 flops (FMA) x max SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peaks, _ = load_peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def best_static_order(costs, groups, group_cost, sel):
+    """Order minimising the expected per-tuple cost under independence (the
+    paper's "Best Reordering" from profiled statistics, by brute force): a
+    predicate on the shared embedding pays the embedding's cost only when it
+    is the first of its group in the order."""
+    from itertools import permutations
+    best = None
+    for perm in permutations(range(len(costs))):
+        total, surv, seen = 0.0, 1.0, set()
+        for i in perm:
+            c = costs[i]
+            if groups[i] is not None and groups[i] not in seen:
+                c += group_cost
+                seen.add(groups[i])
+            total += c * surv
+            surv *= sel[i]
+        if best is None or total < best[1]:
+            best = (list(perm), total)
+    return best[0]
+
+
+def ours_drift5(args):
+    import torch
+    ws, rank = dist_init("nccl")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_2403_14902_b300 as H
+    w = D.workload("drift5")
+    th = thresholds("drift5")
+    Xh = torch.from_numpy(D.stream_tuples(w))
+    X = Xh.cuda()
+    ids = torch.arange(w.n, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    mif = 8
+    shared = set(w.extra["emb_preds"])
+    calib = torch.from_numpy(D.calib_tuples(w)).cuda()
+
+    def make(policy, order=None):
+        q = H.Query("vec", dim=w.dim, max_batch=w.batch, policy=policy, max_in_flight=mif, stream=stream)
+        e = q.add_embedding(D.embedding_weights(w), w.n)
+        full = D.predicate_weights(w)
+        for i in range(len(w.udfs)):
+            if i in shared:
+                q.add_mlp(D.head_weights(w, i), th[i], upstream=e)
+            else:
+                q.add_mlp(full[i], th[i])
+        if order is not None:
+            q.set_static_order(order)
+        q.calibrate(calib)
+        return q, e
+
+    def step_fn(q, e):
+        def f():
+            q.cache_clear(e)        # every pass starts from an empty cache
+            pending, n_pass = [], 0
+            for b0 in range(0, w.n, w.batch):
+                pending.append(q.submit(X[b0:b0 + w.batch], ids[b0:b0 + w.batch]))
+                if len(pending) >= mif:
+                    n_pass += q.poll(pending.pop(0))[2]["n_pass"]
+            for b in pending:
+                n_pass += q.poll(b)[2]["n_pass"]
+            return n_pass
+        return f
+
+    # profile pass: every predicate on every tuple gives the global selectivities
+    qa, ea = make("all")
+    step_fn(qa, ea)()
+    st_all = qa.stats()
+    qa.close()
+    sel = [s["passed"] / max(1, s["evaluated"]) for s in st_all]
+    costs = [s["model_cost"] for s in st_all]
+    groups = ["E" if i in shared else None for i in range(len(costs))]
+    emb = w.extra["embedding"]
+    c_emb = sum(2 * emb[l] * emb[l + 1] for l in range(len(emb) - 1))
+    best = best_static_order(costs, groups, c_emb, sel)
+
+    results = {}
+    for name, policy, order, steps in [("adaptive", "rank", None, args.steps), ("best_static", "static", best, args.steps),
+                                       ("declared_static", "static", None, 1)]:
+        q, e = make(policy, order)
+        f = step_fn(q, e)
+        for _ in range(args.warmup if name != "declared_static" else 1):
+            f()
+        clocks = ClockSampler(local)
+        if name == "adaptive":
+            clocks.start()
+            q.profile(True)
+        secs, npass = timed(f, steps, stream, local)
+        secs = max_over_ranks(secs, device=torch.device("cuda", local))
+        entry = {"value": aggregate(w.n, steps, secs, ws), "ms_per_step": secs / steps * 1000.0,
+                 "pass_count": int(npass[0]), "steps": steps}
+        if name == "adaptive":
+            entry["prof"], entry["launches"] = q.profile_read()
+            entry["clocks"] = clocks.stop()
+            entry["stats"] = q.stats()
+            # end to end from pinned host memory
+            Xp = Xh.pin_memory()
+            bufs = [torch.empty((w.batch, w.dim), dtype=torch.float32, device="cuda") for _ in range(mif)]
+
+            def hstep():
+                q.cache_clear(e)
+                pending, n_pass, k = [], 0, 0
+                with torch.cuda.stream(stream):
+                    for b0 in range(0, w.n, w.batch):
+                        buf = bufs[k % mif]
+                        k += 1
+                        buf.copy_(Xp[b0:b0 + w.batch], non_blocking=True)
+                        pending.append(q.submit(buf, ids[b0:b0 + w.batch]))
+                        if len(pending) >= mif:
+                            n_pass += q.poll(pending.pop(0))[2]["n_pass"]
+                    for b in pending:
+                        n_pass += q.poll(b)[2]["n_pass"]
+                return n_pass
+            hstep()
+            esecs, _ = timed(hstep, 2, stream, local)
+            entry["e2e"] = aggregate(w.n, 2, max_over_ranks(esecs, device=torch.device("cuda", local)), ws)
+        q.close()
+        results[name] = entry
+    assert len({r["pass_count"] for r in results.values()}) == 1, "pass sets differ between routing policies"
+    if rank != 0:
+        return None
+    a = results["adaptive"]
+    prof = a["prof"]
+    peak = fp32_simt_peak_tflops()
+    roof = None
+    if prof:
+        name, d = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
+        achieved = d["flops"] / (d["total_ms"] / 1000.0) / 1e12
+        roof = {"bound": "alu", "kernel": name, "achieved": round(achieved, 2), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "FP32 CUDA-core peak: SMs x 128 lanes x 2 x max SM clock (derived)",
+                "launches": d["launches"], "avg_launch_ms": round(d["total_ms"] / max(1, d["launches"]), 4)}
+    nb = (w.n + w.batch - 1) // w.batch
+    return {
+        "metric": METRIC, "value": round(a["value"], 1), "unit": "tuples/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(a["ms_per_step"], 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": f"drift5: {w.n} x 512 fp32 tuples, 8 Dirichlet(0.5) drift segments, 5 MLP "
+                               "predicates (two heads on a cached shared 512-1024-256 embedding), batches of "
+                               f"{w.batch}, reuse-aware rank routing, FP32 + FP64 recheck",
+                   "global_batch": w.n, "routing_batch": w.batch, "parallelism": f"replicas{ws}",
+                   "l2": "inputs 2 GiB > 126 MB L2, no flush"},
+        "roofline": roof,
+        "cpu_baseline": cpu_baseline(w, th, n_frames=2048),
+        "e2e": {"value": round(a["e2e"], 1), "unit": "tuples/s", "h2d_bytes_per_step": int(w.n * w.dim * 4),
+                "d2h_bytes_per_step": nb * (4 * ((w.batch + 31) // 32) + 64 + 48 * 8)},
+        "gpu_launches": int(a["launches"]),
+        "clocks": a["clocks"],
+        "baselines": {k: {"value": round(v["value"], 1), "unit": "tuples/s", "ms_per_step": round(v["ms_per_step"], 3)}
+                      for k, v in results.items() if k != "adaptive"},
+        "best_static_order": best, "profiled_selectivity": [round(x, 4) for x in sel],
+        "speedup_vs_best_static": round(a["value"] / results["best_static"]["value"], 3),
+        "speedup_vs_declared_static": round(a["value"] / results["declared_static"]["value"], 3),
+        "pass_count_per_step": a["pass_count"],
+        "cache_hits": [s["cache_hits"] for s in a["stats"]],
+        "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
+                        "tflops": round(v["flops"] / max(v["total_ms"], 1e-9) / 1e9, 2)} for k, v in prof.items()},
+    }
+
+
+def ours_drift6(args):
+    """Learned per-tuple routing on the drifting stream with six MLPs of cost
+    ratio 1:2:4:8:16:32, against per-batch rank routing and static orders."""
+    import torch
+    ws, rank = dist_init("nccl")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_2403_14902_b300 as H
+    w = D.workload("drift6")
+    th = thresholds("drift6")
+    Xh = torch.from_numpy(D.stream_tuples(w))
+    X = Xh.cuda()
+    stream = torch.cuda.Stream()
+    mif = 8
+    full = D.predicate_weights(w)
+    calib = torch.from_numpy(D.calib_tuples(w)).cuda()
+
+    def make(policy, order=None):
+        q = H.Query("vec", dim=w.dim, max_batch=w.batch, policy=policy, max_in_flight=mif, stream=stream,
+                    proxy_refresh=w.extra["refresh"], proxy_hidden=w.extra["proxy_hidden"])
+        for i in range(len(w.udfs)):
+            q.add_mlp(full[i], th[i])
+        if order is not None:
+            q.set_static_order(order)
+        q.calibrate(calib)
+        return q
+
+    def step_fn(q):
+        return lambda: run_step(q, X, w.batch, mif)
+
+    qa = make("all")
+    step_fn(qa)()
+    st_all = qa.stats()
+    qa.close()
+    sel = [s["passed"] / max(1, s["evaluated"]) for s in st_all]
+    costs = [s["model_cost"] for s in st_all]
+    best = best_static_order(costs, [None] * len(costs), 0, sel)
+    results = {}
+    for name, policy, order, steps in [("learned", "learned", None, args.steps), ("rank", "rank", None, args.steps),
+                                       ("best_static", "static", best, args.steps),
+                                       ("declared_static", "static", None, 1)]:
+        q = make(policy, order)
+        f = step_fn(q)
+        for _ in range(args.warmup if name != "declared_static" else 1):
+            f()
+        clocks = ClockSampler(local)
+        if name == "learned":
+            clocks.start()
+            q.profile(True)
+        secs, npass = timed(f, steps, stream, local)
+        secs = max_over_ranks(secs, device=torch.device("cuda", local))
+        entry = {"value": aggregate(w.n, steps, secs, ws), "ms_per_step": secs / steps * 1000.0,
+                 "pass_count": int(npass[0])}
+        st = q.stats()
+        entry["evaluations"] = sum(s["evaluated"] for s in st)
+        entry["eval_flops"] = sum(s["evaluated"] * s["model_cost"] for s in st)
+        if name == "learned":
+            entry["prof"], entry["launches"] = q.profile_read()
+            entry["clocks"] = clocks.stop()
+            Xp = Xh.pin_memory()
+            bufs = [torch.empty((w.batch, w.dim), dtype=torch.float32, device="cuda") for _ in range(mif)]
+            hstep = lambda: run_step_host(q, Xp, bufs, w.batch, mif, stream)  # noqa: E731
+            hstep()
+            esecs, _ = timed(hstep, 2, stream, local)
+            entry["e2e"] = aggregate(w.n, 2, max_over_ranks(esecs, device=torch.device("cuda", local)), ws)
+        q.close()
+        results[name] = entry
+    assert len({r["pass_count"] for r in results.values()}) == 1, "pass sets differ between routing policies"
+    if rank != 0:
+        return None
+    a = results["learned"]
+    prof = a["prof"]
+    peak = fp32_simt_peak_tflops()
+    roof = None
+    if prof:
+        name, d = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
+        achieved = d["flops"] / (d["total_ms"] / 1000.0) / 1e12
+        roof = {"bound": "alu", "kernel": name, "achieved": round(achieved, 2), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "FP32 CUDA-core peak: SMs x 128 lanes x 2 x max SM clock (derived)",
+                "launches": d["launches"], "avg_launch_ms": round(d["total_ms"] / max(1, d["launches"]), 4)}
+    nb = (w.n + w.batch - 1) // w.batch
+    return {
+        "metric": METRIC, "value": round(a["value"], 1), "unit": "tuples/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(a["ms_per_step"], 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": f"drift6: {w.n} x 512 fp32 tuples, 8 Dirichlet(0.5) drift segments, 6 MLP "
+                               "predicates 512-h-1 (cost 1:2:4:8:16:32), learned 512-64-6 proxy picks per-tuple "
+                               f"orders (refresh every 16 batches), batches of {w.batch}, FP32 + FP64 recheck",
+                   "global_batch": w.n, "routing_batch": w.batch, "parallelism": f"replicas{ws}",
+                   "l2": "inputs 2 GiB > 126 MB L2, no flush"},
+        "roofline": roof,
+        "cpu_baseline": cpu_baseline(w, th, n_frames=4096),
+        "e2e": {"value": round(a["e2e"], 1), "unit": "tuples/s", "h2d_bytes_per_step": int(w.n * w.dim * 4),
+                "d2h_bytes_per_step": nb * (4 * ((w.batch + 31) // 32) + 64 + 48 * 8)},
+        "gpu_launches": int(a["launches"]),
+        "clocks": a["clocks"],
+        "baselines": {k: {"value": round(v["value"], 1), "unit": "tuples/s", "ms_per_step": round(v["ms_per_step"], 3),
+                          "eval_gflop_per_step": round(v["eval_flops"] / 1e9, 2)}
+                      for k, v in results.items() if k != "learned"},
+        "eval_gflop_per_step": round(a["eval_flops"] / 1e9, 2),
+        "best_static_order": best, "profiled_selectivity": [round(x, 4) for x in sel],
+        "speedup_vs_rank": round(a["value"] / results["rank"]["value"], 3),
+        "speedup_vs_best_static": round(a["value"] / results["best_static"]["value"], 3),
+        "pass_count_per_step": a["pass_count"],
+        "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
+                        "tflops": round(v["flops"] / max(v["total_ms"], 1e-9) / 1e9, 2)} for k, v in prof.items()},
+    }
 
 
 def ours(args):
@@ -269,8 +569,12 @@ def ours(args):
         name, d = dom
         achieved = d["flops"] / (d["total_ms"] / 1000.0) / 1e12
         peak = float(peaks["bf16_tflops_sustained"])
+        ratio = measured_traffic_ratio() if name == "conv3x3_bf16_tc" else None
+        traffic = round(d["bytes"] / max(1, d["launches"]) * ratio) if ratio else None
         roof = {"bound": "tensor", "kernel": name, "achieved": round(achieved, 2), "peak": peak,
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "traffic_note": "ncu DRAM bytes of a 1,024-frame 128->128 launch relative to its algorithmic "
+                                "bytes, scaled to this run's algorithmic bytes per launch" if traffic else None,
                 "peak_source": f"bf16_tflops_sustained ({src})", "launches": d["launches"],
                 "avg_launch_ms": round(d["total_ms"] / max(1, d["launches"]), 4)}
     h2d = int(np.prod(Xh.shape))
@@ -316,9 +620,10 @@ def reference(args):
     if rank != 0:
         return None
     import oracle as O
-    w = D.workload(WORKLOAD)
-    th = thresholds(WORKLOAD)
-    n = 8
+    name = args.workload
+    w = D.workload(name)
+    th = thresholds(name)
+    n = 8 if w.kind == "frame" else 4096
     F = D.stream_tuples(w, n)
     ws_ = D.predicate_weights(w)
     for _ in range(args.warmup):
@@ -331,9 +636,9 @@ def reference(args):
     return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "tuples/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1000.0, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: oracle on {n} frames of the {w.n}-frame stream per step"},
+            "config": {"workload": f"{name}: oracle on {n} tuples of the {w.n}-tuple stream per step"},
             "cpu_baseline": {"value": round(value, 3), "unit": "tuples/s", "cores": O.threads(), "kind": "oracle",
-                             "sample": f"{n} frames per step, all 4 UDFs in FP64"},
+                             "sample": f"{n} tuples per step, every UDF in FP64"},
             "e2e": {"value": round(value, 3), "unit": "tuples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -343,8 +648,12 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["cnn4", "drift5", "drift6"], default=WORKLOAD)
     args = ap.parse_args(argv)
-    out = reference(args) if args.impl == "reference" else ours(args)
+    if args.impl == "reference":
+        out = reference(args)
+    else:
+        out = {"cnn4": ours, "drift5": ours_drift5, "drift6": ours_drift6}[args.workload](args)
     if out is not None:
         print(json.dumps(out), flush=True)
 

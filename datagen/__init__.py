@@ -80,6 +80,13 @@ WORKLOADS = {
         udfs=((512, 1024, 256, 1), (512, 1024, 256, 256, 1), (512, 256, 1), (512, 1024, 1024, 1), (512, 2048, 1)),
         selectivity=(0.5, 0.4, 0.5, 0.6, 0.5), n_calib=1024,
         extra={"segments": 8, "dirichlet": 0.5, "embedding": (512, 1024, 256), "emb_preds": (0, 1)}),
+    # the same drifting stream (workload id 3, same streams) under six MLPs
+    # 512-h-1 with h = 64 * 2^k, so costs grow 1:2:4:8:16:32
+    "drift6": Workload(
+        name="drift6", wid=3, kind="vec", n=1048576, batch=4096, dim=512,
+        udfs=tuple((512, 64 << k, 1) for k in range(6)),
+        selectivity=(0.6, 0.5, 0.4, 0.5, 0.3, 0.5), n_calib=1024,
+        extra={"segments": 8, "dirichlet": 0.5, "weight_stream": 40, "proxy_hidden": 64, "refresh": 16}),
 }
 
 
@@ -262,7 +269,8 @@ def predicate_weights(w: Workload):
     if w.kind == "vec":
         shared = set(w.extra.get("emb_preds", ())) if w.extra else set()
         emb = embedding_weights(w) if shared else None
-        return [emb + head_weights(w, i) if i in shared else mlp_weights(w, 10 + i, d, _gain(w, i))
+        base = w.extra.get("weight_stream", 10) if w.extra else 10
+        return [emb + head_weights(w, i) if i in shared else mlp_weights(w, base + i, d, _gain(w, i))
                 for i, d in enumerate(w.udfs)]
     return [cnn_weights(w, 10 + i, c, _gain(w, i)) for i, c in enumerate(w.udfs)]
 

@@ -68,7 +68,11 @@ enum {
     HYDRO_POLICY_STATIC = 1,      /* fixed order (declared, or hydro_set_static_order) */
     HYDRO_POLICY_ALL = 2,         /* every predicate on every tuple, no short-circuit */
     HYDRO_POLICY_COST = 3,        /* cost only, lowest first: cost-driven */
-    HYDRO_POLICY_SELECTIVITY = 4  /* selectivity only, lowest first: selectivity-driven */
+    HYDRO_POLICY_SELECTIVITY = 4, /* selectivity only, lowest first: selectivity-driven */
+    HYDRO_POLICY_LEARNED = 5      /* per-tuple order from a learned proxy of the pass
+                                     probabilities (content-based routing, Sec. 2.2), trained
+                                     online on the evaluated outcomes; rank routing until the
+                                     first refresh.  FP32 MLP predicates only */
 };
 
 /* Working precision of UDF inference. */
@@ -116,6 +120,11 @@ typedef struct hydro_query_config {
     int32_t max_in_flight;   /* submitted but not yet polled batches, 1..64 */
     int32_t device;          /* CUDA device ordinal */
     void *stream;            /* cudaStream_t the batches run on; NULL = library stream */
+    int32_t proxy_hidden;    /* LEARNED: proxy MLP hidden width (default 64) */
+    int32_t proxy_refresh;   /* LEARNED: retrain after every this many batches (default 16) */
+    int32_t proxy_epochs;    /* LEARNED: passes over the last proxy_refresh batches per retrain (2) */
+    float proxy_lr;          /* LEARNED: Adam learning rate (1e-3) */
+    int32_t proxy_seed;      /* LEARNED: seed of the proxy's initial weights */
 } hydro_query_config;
 
 typedef struct hydro_udf_desc {
@@ -217,9 +226,14 @@ HYDRO_API hydro_status hydro_add_embedding(hydro_query *q, const hydro_udf_desc 
 
 /* Compute and cache embedding emb for n device tuples with device ids (as an
  * earlier exploratory query would have); these entries count as cached for
- * every batch.  Synchronous; before the first submit. */
+ * every later batch.  Stream-ordered after the batches already submitted;
+ * synchronous (returns when the cache holds them). */
 HYDRO_API hydro_status hydro_cache_prefill(hydro_query *q, int32_t emb, const void *d_tuples, const int64_t *d_ids,
                                            int64_t n);
+
+/* Forget every cached output of embedding emb (asynchronous on the query's
+ * stream, ordered after the batches already submitted). */
+HYDRO_API hydro_status hydro_cache_clear(hydro_query *q, int32_t emb);
 
 /* Set the recheck margins of predicate pred (absolute score units, >= 0).
  * A score s at a precision decides the test only if |s - t| > that level's
@@ -263,6 +277,12 @@ HYDRO_API hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, 
 HYDRO_API hydro_status hydro_poll_result(hydro_query *q, int64_t batch_id, uint32_t *pass_bitmap,
                                int64_t *eval_counts, hydro_batch_info *info, int32_t wait_ms);
 
+/* Per-tuple trace of the most recently submitted batch (polled, no later
+ * submit): order[n * 8] receives each tuple's predicate order (first P
+ * bytes used) and visited[n] the bit set of predicates it was evaluated on.
+ * For per-batch policies every tuple shows the batch's order.  Synchronous. */
+HYDRO_API hydro_status hydro_debug_trace(hydro_query *q, int64_t batch_id, uint8_t *order, uint8_t *visited);
+
 /* Cumulative statistics of the first n predicates into out[n] (host). */
 HYDRO_API hydro_status hydro_get_stats(hydro_query *q, hydro_pred_stats *out, int32_t n);
 
@@ -304,6 +324,15 @@ HYDRO_API hydro_status hydro_profile_read(hydro_query *q, hydro_kernel_profile *
 HYDRO_API hydro_status hydro_mlp_scores_noalloc(const float *d_x, int64_t n, int32_t n_layers, const int32_t *dims,
                                                 const float *const *d_weights, const float *const *d_biases,
                                                 double *d_scores, void *stream);
+
+/* Failure-detection self-test of the kernels' bounded waits: a kernel waits
+ * on an mbarrier that nothing completes, with a limit of limit_ns (1e3 ..
+ * 1e10); the wait must run out, the kernel return and the context stay
+ * usable.  Returns HYDRO_ETIMEOUT when that happened (the expected outcome).
+ * No counterpart in the paper (its deadlock avoidance is a queue-capacity
+ * rule, Sec. 3.3 "Deadlock Prevention"); every spin in this library's
+ * kernels is bounded the same way. */
+HYDRO_API hydro_status hydro_selftest_bounded_wait(int32_t device, int64_t limit_ns);
 
 /* Wait for outstanding work (bounded), free every resource of q. */
 HYDRO_API hydro_status hydro_destroy_query(hydro_query *q);

@@ -334,3 +334,42 @@ def simulate(pm: np.ndarray, batch: int, policy: str = "rank", costs=None, stati
         out.append(dict(order=list(order), counts=counts, passed=passed, warmup=evaluate_all,
                         bits=result_bits(rows), hits=hits))
     return out
+
+
+# ------------------------------------------------------------- concurrent model
+
+def concurrent_makespan(order, costs, sel, n: int, passes=None) -> float:
+    """Makespan of a conjunction whose predicates run concurrently, each on its
+    own resource (Sec. 4.1 "Example comparison": one predicate on the GPU, the
+    other on the CPU): tuples flow through the predicates in ``order``, each
+    resource serves its queue first-come first-served, a tuple that fails is
+    dropped.  ``passes[k][j]`` says whether tuple j passes the k-th predicate
+    of the order (default: tuple j passes predicate i iff
+    floor((j+1) s_i) > floor(j s_i), an even spread of round(n s_i) passes)."""
+    P = len(order)
+    if passes is None:
+        passes = [[int((j + 1) * sel[i]) > int(j * sel[i]) for j in range(n)] for i in order]
+    ready = [0.0] * n                  # when tuple j is available for the next stage
+    alive = [True] * n
+    end = 0.0
+    for k, i in enumerate(order):
+        free = 0.0                     # the resource of predicate i
+        for j in sorted(range(n), key=lambda j: (ready[j], j)):
+            if not alive[j]:
+                continue
+            start = max(free, ready[j])
+            free = start + costs[i]
+            ready[j] = free
+            end = max(end, free)
+            alive[j] = alive[j] and passes[k][j]
+    return end
+
+
+def fluid_makespan(order, costs, sel, n: int) -> float:
+    """Large-n limit of ``concurrent_makespan``: the slowest resource bounds
+    the makespan, n * max_k c_{pi_k} * prod_{j<k} s_{pi_j}."""
+    surv, worst = float(n), 0.0
+    for i in order:
+        worst = max(worst, surv * costs[i])
+        surv *= sel[i]
+    return worst

@@ -25,15 +25,15 @@ STATUS = {0: "HYDRO_OK", 1: "HYDRO_EINVAL", 2: "HYDRO_ENOMEM", 3: "HYDRO_ECUDA",
 OK, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEOUT, ESTATE, EDEVICE, ENOTFOUND, EUNSUPPORTED = range(10)
 
 TUPLE_F32, TUPLE_U8_FRAME = 0, 1
-POLICIES = {"rank": 0, "static": 1, "all": 2, "cost": 3, "selectivity": 4}
+POLICIES = {"rank": 0, "static": 1, "all": 2, "cost": 3, "selectivity": 4, "learned": 5}
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp64": 2, "tf32x3": 3}
 UDF_MLP, UDF_CNN = 0, 1
 
 EXPORTED = ["hydro_default_config", "hydro_create_query", "hydro_add_predicate", "hydro_add_embedding",
-            "hydro_cache_prefill", "hydro_set_margins",
+            "hydro_cache_prefill", "hydro_cache_clear", "hydro_set_margins",
             "hydro_set_static_order", "hydro_calibrate", "hydro_udf_scores", "hydro_submit_batch",
-            "hydro_poll_result", "hydro_get_stats", "hydro_profile", "hydro_profile_read",
-            "hydro_mlp_scores_noalloc", "hydro_destroy_query", "hydro_last_error"]
+            "hydro_poll_result", "hydro_debug_trace", "hydro_get_stats", "hydro_profile", "hydro_profile_read",
+            "hydro_mlp_scores_noalloc", "hydro_selftest_bounded_wait", "hydro_destroy_query", "hydro_last_error"]
 
 
 class QueryConfig(ctypes.Structure):
@@ -42,7 +42,8 @@ class QueryConfig(ctypes.Structure):
                 ("policy", ctypes.c_int32), ("precision", ctypes.c_int32), ("cost_source", ctypes.c_int32),
                 ("warmup_batches", ctypes.c_int32), ("stats_window", ctypes.c_int32),
                 ("route_lag", ctypes.c_int32), ("max_in_flight", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("proxy_hidden", ctypes.c_int32), ("proxy_refresh", ctypes.c_int32),
+                ("proxy_epochs", ctypes.c_int32), ("proxy_lr", ctypes.c_float), ("proxy_seed", ctypes.c_int32)]
 
 
 class UdfDesc(ctypes.Structure):
@@ -101,15 +102,18 @@ def load():
     L.hydro_set_margins.argtypes = [vp, i32, f64, f64, f64]
     L.hydro_add_embedding.argtypes = [vp, P(UdfDesc), i64, P(i32)]
     L.hydro_cache_prefill.argtypes = [vp, i32, vp, vp, i64]
+    L.hydro_cache_clear.argtypes = [vp, i32]
     L.hydro_set_static_order.argtypes = [vp, P(i32), i32]
     L.hydro_calibrate.argtypes = [vp, vp, i64, P(CalibInfo)]
     L.hydro_udf_scores.argtypes = [vp, i32, i32, vp, i64, vp]
     L.hydro_submit_batch.argtypes = [vp, vp, vp, i64, P(i64)]
     L.hydro_poll_result.argtypes = [vp, i64, P(ctypes.c_uint32), P(i64), P(BatchInfo), i32]
     L.hydro_get_stats.argtypes = [vp, P(PredStats), i32]
+    L.hydro_debug_trace.argtypes = [vp, i64, P(ctypes.c_uint8), P(ctypes.c_uint8)]
     L.hydro_profile.argtypes = [vp, i32]
     L.hydro_profile_read.argtypes = [vp, P(KernelProfile), i32, P(i32), P(i64)]
     L.hydro_mlp_scores_noalloc.argtypes = [vp, i64, i32, P(i32), P(vp), P(vp), vp, vp]
+    L.hydro_selftest_bounded_wait.argtypes = [i32, i64]
     L.hydro_destroy_query.argtypes = [vp]
     L.hydro_last_error.argtypes = []
     L.hydro_last_error.restype = ctypes.c_char_p
@@ -148,7 +152,8 @@ class Query:
 
     def __init__(self, kind: str, *, dim: int = 0, frame=(3, 64, 64), max_batch: int, policy: str = "rank",
                  precision: str = "fp32", warmup: int = 1, window: int = 8, lag: int = 1,
-                 max_in_flight: int = 4, device: int = 0, stream=None):
+                 max_in_flight: int = 4, device: int = 0, stream=None, proxy_hidden: int = 64,
+                 proxy_refresh: int = 16, proxy_epochs: int = 2, proxy_lr: float = 1e-3, proxy_seed: int = 1):
         L = load()
         cfg = QueryConfig()
         L.hydro_default_config(ctypes.byref(cfg))
@@ -164,6 +169,11 @@ class Query:
         cfg.max_in_flight = max_in_flight
         cfg.device = device
         cfg.stream = stream.cuda_stream if stream is not None else None
+        cfg.proxy_hidden = proxy_hidden
+        cfg.proxy_refresh = proxy_refresh
+        cfg.proxy_epochs = proxy_epochs
+        cfg.proxy_lr = proxy_lr
+        cfg.proxy_seed = proxy_seed
         self.kind = kind
         self.cfg = cfg
         self._h = ctypes.c_void_p()
@@ -207,6 +217,9 @@ class Query:
     def cache_prefill(self, emb: int, tuples, ids):
         _check(load().hydro_cache_prefill(self._h, int(emb), _ptr(tuples), _ptr(ids), int(tuples.shape[0])),
                "hydro_cache_prefill")
+
+    def cache_clear(self, emb: int):
+        _check(load().hydro_cache_clear(self._h, int(emb)), "hydro_cache_clear")
 
     def _add(self, kind, dims, Ws, bs, threshold, head_w=None, head_b=0.0, cost_hint=0, upstream=0):
         desc, keep = self._desc(kind, dims, Ws, bs, head_w, head_b, cost_hint, upstream)
@@ -275,6 +288,14 @@ class Query:
                  recheck_fp32=list(info.recheck_fp32[:P]), cache_hits=list(info.cache_hits[:P]),
                  recheck_fp64=list(info.recheck_fp64[:P]), device_ms=info.device_ms)
         return bitmap[:(n + 31) // 32], counts[:P], d
+
+    def debug_trace(self, batch_id: int, n: int):
+        """(order uint8 [n, P], visited uint8 [n]) of the most recent batch (learned router)."""
+        order = np.zeros((max(n, 1), MAX_PREDICATES), np.uint8)
+        visited = np.zeros(max(n, 1), np.uint8)
+        _check(load().hydro_debug_trace(self._h, batch_id, order.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                        visited.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))), "hydro_debug_trace")
+        return order[:n, :self.n_pred], visited[:n]
 
     def stats(self) -> list:
         out = (PredStats * MAX_PREDICATES)()

@@ -11,6 +11,7 @@
 // statistics of completed batches decide the next routing).
 #include <algorithm>
 #include <cstdarg>
+#include <random>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -24,6 +25,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "tc_conv.h"
+#include "tc_gemm.h"
 
 using namespace hydro;
 
@@ -84,6 +86,8 @@ struct Pred {
     std::vector<void *> dWtc;             // CNN layer l >= 1: tensor-core layout (bf16)
     std::vector<void *> dWts;             // CNN layer l >= 1: tensor-core split-TF32 layout (fp32 hi, lo)
     bool tc_all = false;                  // every layer l >= 1 has tensor-core weights
+    std::vector<__nv_bfloat16 *> dW16;    // MLP hidden layers: bf16 weights for the tensor cores
+    bool tc_mlp = false;                  // MLP: every hidden layer runs on the tensor cores
     float *dHead = nullptr;
     MlpDev mlp{};
 };
@@ -111,7 +115,7 @@ constexpr size_t kBitmapOff = kRowsOff + sizeof(StatRow) * kMaxPred;
 
 // Profiling: one record per timed launch; its item count is resolved from
 // the batch's statistics row when the batch is polled.
-enum ProfSrc { SRC_MAIN = 0, SRC_R32 = 1, SRC_R64 = 2, SRC_RTF = 3 };
+enum ProfSrc { SRC_MAIN = 0, SRC_R32 = 1, SRC_R64 = 2, SRC_RTF = 3, SRC_MISS = 4 };
 struct ProfCtx {
     long long batch;
     int pred;
@@ -127,9 +131,10 @@ struct ProfRec {
 };
 const char *const kProfNames[] = {"conv3x3_bf16_tc", "conv3x3_bf16_simt", "conv3x3_f32_simt", "conv3x3_f64_simt",
                                   "conv1_u8",        "pool_head",         "mlp_layer_f32",    "mlp_dot_f32",
-                                  "mlp_band_f32",    "mlp_band_f64",      "conv3x3_tf32x3_tc"};
+                                  "mlp_band_f32",    "mlp_band_f64",      "conv3x3_tf32x3_tc", "mlp_layer_bf16_tc",
+                                  "gather_rows_bf16"};
 enum { PC_CONV_TC = 0, PC_CONV_BF16, PC_CONV_F32, PC_CONV_F64, PC_CONV1, PC_POOL, PC_MLP, PC_DOT, PC_BAND32,
-       PC_BAND64, PC_CONV_TF32, PC_N };
+       PC_BAND64, PC_CONV_TF32, PC_MLP_TC, PC_GATHER, PC_N };
 
 struct Prof {
     bool on = false;
@@ -147,6 +152,26 @@ struct hydro_query {
     std::vector<Emb> embs;
     std::vector<int> static_order;
     int *vmiss = nullptr;         // router probe: misses per embedding for the batch being routed
+    // learned per-tuple routing (HYDRO_POLICY_LEARNED)
+    unsigned char *order_t = nullptr;   // [B][8] per-tuple predicate order
+    unsigned char *okf = nullptr, *label = nullptr, *visited = nullptr;   // [B] per tuple
+    int *queues = nullptr, *qcount = nullptr;   // [8][B], [8]
+    float *qscore = nullptr;                    // [8][B]
+    int *bandg = nullptr, *bandt = nullptr;     // [B]
+    std::vector<float *> gact;                  // per predicate, two [B][width] buffers
+    int *d_fallback = nullptr, *h_fallback = nullptr;
+    GroupedMlps gmlps{};
+    int ph = 64;
+    float *pW1 = nullptr, *pb1 = nullptr, *pW2 = nullptr, *pb2 = nullptr;
+    float *pg = nullptr, *pm = nullptr, *pv = nullptr;   // gradients and Adam moments, same layout as params
+    float *pH = nullptr, *pZ = nullptr, *pdZ = nullptr, *pdH = nullptr, *pinv = nullptr;
+    float *ringX = nullptr;
+    unsigned char *ringL = nullptr, *ringM = nullptr;
+    std::vector<int> ring_n;
+    bool proxy_ready = false;
+    int adam_t = 0;
+    long long last_learned_batch = -1;
+    int last_n = 0;
     int *miss_list = nullptr;     // stage probe: alive tuples whose embedding is not cached
     bool finalized = false;
     bool dead = false;
@@ -169,7 +194,10 @@ struct hydro_query {
     void *act[2] = {};            // working precision activations
     void *ract32[2] = {};         // CNN FP32 recheck activations
     void *ract64[2] = {};         // CNN FP64 recheck activations
-    float *partials = nullptr;    // CNN BF16: fused pool+head partials [max_batch][H*W/128*4]
+    float *partials = nullptr;    // BF16: fused (pool+)head partials [max_batch][tiles]
+    __nv_bfloat16 *stage16 = nullptr;   // BF16 MLP: gathered first-layer operand [max_batch][dim]
+    __nv_bfloat16 *act16[2] = {};       // BF16 MLP: hidden activations
+    void *gemm_encode = nullptr;
     StatRow *ring = nullptr, *warm = nullptr;
     int ring_len = 0;
     int *d_order = nullptr;       // [max_in_flight][8]
@@ -236,7 +264,8 @@ long long model_cost(const Pred &p, const hydro_query_config &c) {
 }
 
 bool adaptive(int policy) {
-    return policy == HYDRO_POLICY_RANK || policy == HYDRO_POLICY_COST || policy == HYDRO_POLICY_SELECTIVITY;
+    return policy == HYDRO_POLICY_RANK || policy == HYDRO_POLICY_COST || policy == HYDRO_POLICY_SELECTIVITY ||
+           policy == HYDRO_POLICY_LEARNED;
 }
 
 int max_width(const hydro_query *q) {
@@ -244,6 +273,68 @@ int max_width(const hydro_query *q) {
     for (const Pred &p : q->preds)
         for (int d : p.dims) w = std::max(w, d);
     return w;
+}
+
+hydro_status finalize_learned(hydro_query *q) {
+    const hydro_query_config &c = q->cfg;
+    const int B = c.max_batch, P = (int)q->preds.size(), D = c.dim;
+    for (const Pred &p : q->preds)
+        if (p.kind != HYDRO_UDF_MLP || p.upstream)
+            return fail(HYDRO_EUNSUPPORTED, "the learned router takes MLP predicates on the tuple");
+    TRY(dalloc(q, &q->order_t, (size_t)B * kMaxPred));
+    TRY(dalloc(q, &q->okf, B));
+    TRY(dalloc(q, &q->label, B));
+    TRY(dalloc(q, &q->visited, B));
+    TRY(dalloc(q, &q->queues, sizeof(int) * kMaxPred * B));
+    TRY(dalloc(q, &q->qcount, sizeof(int) * kMaxPred));
+    TRY(dalloc(q, &q->qscore, sizeof(float) * kMaxPred * B));
+    TRY(dalloc(q, &q->bandg, sizeof(int) * B));
+    TRY(dalloc(q, &q->bandt, sizeof(int) * B));
+    TRY(dalloc(q, &q->d_fallback, sizeof(int) * kMaxPred));
+    CU(cudaMallocHost(&q->h_fallback, sizeof(int) * kMaxPred));
+    q->gact.assign(2 * P, nullptr);
+    int wmax = 1;
+    for (int i = 0; i < P; ++i) {
+        int w = 1;
+        for (int d : q->preds[i].dims) w = std::max(w, d);
+        wmax = std::max(wmax, w);
+        for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->gact[2 * i + k], sizeof(float) * (size_t)B * w));
+        q->gmlps.m[i] = q->preds[i].mlp;
+    }
+    q->gmlps.max_width = wmax;
+    CU(grouped_band_smem_setup(wmax));
+    // proxy MLP D -> H -> P (ReLU, then logits), seeded uniform init
+    const int H = q->ph = c.proxy_hidden > 0 ? c.proxy_hidden : 64;
+    const size_t nparam = (size_t)H * D + H + (size_t)P * H + P;
+    std::vector<float> init(nparam, 0.f);
+    std::mt19937 gen((unsigned)c.proxy_seed);
+    std::uniform_real_distribution<float> u1(-std::sqrt(6.f / D), std::sqrt(6.f / D));
+    std::uniform_real_distribution<float> u2(-1.f / std::sqrt((float)H), 1.f / std::sqrt((float)H));
+    for (size_t k = 0; k < (size_t)H * D; ++k) init[k] = u1(gen);
+    for (size_t k = 0; k < (size_t)P * H; ++k) init[(size_t)H * D + H + k] = u2(gen);
+    float *params = nullptr;
+    TRY(dalloc(q, &params, sizeof(float) * nparam));
+    CU(cudaMemcpy(params, init.data(), sizeof(float) * nparam, cudaMemcpyHostToDevice));
+    q->pW1 = params;
+    q->pb1 = q->pW1 + (size_t)H * D;
+    q->pW2 = q->pb1 + H;
+    q->pb2 = q->pW2 + (size_t)P * H;
+    TRY(dalloc(q, &q->pg, sizeof(float) * nparam));
+    TRY(dalloc(q, &q->pm, sizeof(float) * nparam));
+    TRY(dalloc(q, &q->pv, sizeof(float) * nparam));
+    CU(cudaMemset(q->pm, 0, sizeof(float) * nparam));
+    CU(cudaMemset(q->pv, 0, sizeof(float) * nparam));
+    TRY(dalloc(q, &q->pH, sizeof(float) * (size_t)B * H));
+    TRY(dalloc(q, &q->pZ, sizeof(float) * (size_t)B * kMaxPred));
+    TRY(dalloc(q, &q->pdZ, sizeof(float) * (size_t)B * kMaxPred));
+    TRY(dalloc(q, &q->pdH, sizeof(float) * (size_t)B * H));
+    TRY(dalloc(q, &q->pinv, sizeof(float)));
+    const int R = std::max(1, c.proxy_refresh);
+    TRY(dalloc(q, &q->ringX, sizeof(float) * (size_t)R * B * D));
+    TRY(dalloc(q, &q->ringL, (size_t)R * B));
+    TRY(dalloc(q, &q->ringM, (size_t)R * B));
+    q->ring_n.assign(R, 0);
+    return HYDRO_OK;
 }
 
 hydro_status finalize(hydro_query *q) {
@@ -297,6 +388,13 @@ hydro_status finalize(hydro_query *q) {
     } else {
         for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->act[k], sizeof(float) * (size_t)wmax * B));
         CU(mlp_band_smem_setup(wmax));
+        if (c.precision == HYDRO_PREC_BF16) {
+            TRY(dalloc(q, &q->stage16, sizeof(__nv_bfloat16) * (size_t)B * c.dim));
+            for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->act16[k], sizeof(__nv_bfloat16) * (size_t)wmax * B));
+            TRY(dalloc(q, &q->partials, sizeof(float) * (size_t)B * std::max(1, wmax / 64)));
+            hydro_status s = tc_gemm_init(&q->gemm_encode);
+            if (s != HYDRO_OK) return fail(s, "tensor-core GEMM init failed: %s", tc_gemm_last_error());
+        }
     }
     q->ring_len = c.stats_window + c.route_lag + 4;
     TRY(dalloc(q, &q->ring, sizeof(StatRow) * kMaxPred * q->ring_len));
@@ -339,6 +437,19 @@ hydro_status finalize(hydro_query *q) {
         for (int l = 0; l < p.n_layers; ++l) {
             TRY(upload(q, &p.dW[l], p.W[l].data(), p.W[l].size()));
             TRY(upload(q, &p.db[l], p.b[l].data(), p.b[l].size()));
+        }
+        if (p.kind == HYDRO_UDF_MLP && c.precision == HYDRO_PREC_BF16 && !p.upstream && p.n_layers >= 2 &&
+            c.dim % 8 == 0) {
+            p.tc_mlp = true;
+            for (int l = 0; l + 1 < p.n_layers; ++l) p.tc_mlp = p.tc_mlp && tc_gemm_supported(p.dims[l], p.dims[l + 1]);
+            if (p.tc_mlp) {
+                p.dW16.assign(p.n_layers, nullptr);
+                for (int l = 0; l + 1 < p.n_layers; ++l) {
+                    std::vector<__nv_bfloat16> w16(p.W[l].size());
+                    for (size_t k = 0; k < w16.size(); ++k) w16[k] = __float2bfloat16_rn(p.W[l][k]);
+                    TRY(upload(q, &p.dW16[l], w16.data(), w16.size()));
+                }
+            }
         }
         if (p.kind == HYDRO_UDF_MLP) {
             p.mlp.n_layers = p.n_layers;
@@ -392,6 +503,7 @@ hydro_status finalize(hydro_query *q) {
         hydro_status s = tc_conv_init(&q->tc, c.device);
         if (s != HYDRO_OK) return fail(s, "tensor-core conv init failed: %s", tc_conv_last_error());
     }
+    if (c.policy == HYDRO_POLICY_LEARNED) TRY(finalize_learned(q));
     q->finalized = true;
     return HYDRO_OK;
 }
@@ -436,7 +548,35 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
             q->launches++;
             return HYDRO_OK;
         }
-        // FP32 (the BF16 MLP path is not built; rejected at create)
+        if (prec == PREC_BF16 && p.tc_mlp && ((uintptr_t)X % 16) == 0) {
+            // BF16 tensor cores: gather the rows, hidden layers on tcgen05, the
+            // one-output last layer folded into the last hidden layer's epilogue
+            int e = prof_begin(q, pc, PC_GATHER, 0.0, 6.0 * c.dim, 0.0);
+            launch_gather_bf16(count, list, X, c.dim, c.dim, q->stage16, max_rows, q->sms, st);
+            prof_end(q, e);
+            q->launches++;
+            const __nv_bfloat16 *in = q->stage16;
+            int cur = 0;
+            const int L = p.n_layers;
+            for (int l = 0; l + 1 < L; ++l) {
+                const bool last = l + 2 == L;
+                e = prof_begin(q, pc, PC_MLP_TC, 2.0 * p.dims[l] * p.dims[l + 1],
+                               2.0 * (p.dims[l] + (last ? 0 : p.dims[l + 1])), 2.0 * p.dims[l] * p.dims[l + 1]);
+                hydro_status rs = tc_gemm_run(q->gemm_encode, count, in, p.dims[l], p.dW16[l], p.db[l], p.dims[l + 1],
+                                              q->act16[cur], max_rows, q->sms, st, q->d_err,
+                                              last ? p.dW[L - 1] : nullptr, last ? q->partials : nullptr);
+                prof_end(q, e);
+                if (rs != HYDRO_OK) return fail(rs, "tensor-core GEMM: %s", tc_gemm_last_error());
+                q->launches++;
+                in = q->act16[cur];
+                cur = 1 - cur;
+            }
+            tc_head_finalize(count, q->partials, tc_gemm_col_tiles(p.dims[L - 1]), (double)p.b[L - 1][0], 1, score32,
+                             max_rows, q->sms, st);
+            q->launches++;
+            return HYDRO_OK;
+        }
+        // FP32 on CUDA cores
         if (p.n_layers == 1) {
             const int e = prof_begin(q, pc, PC_DOT, 2.0 * p.dims[0], 4.0 * p.dims[0] + 4, 4.0 * p.dims[0]);
             launch_mlp_dot_f32(count, list, X, c.dim, p.dW[0], p.b[0][0], p.dims[0], score32, max_rows, q->sms, st);
@@ -552,19 +692,28 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
 // stored in the cache with tag_value), then the head reads every alive
 // tuple's embedding from the cache.  miss_count receives the misses.
 hydro_status run_grouped(hydro_query *q, const Pred &p, const int *count, const int *list, const void *tuples,
-                         const long long *ids, int tag_value, int max_rows, int *miss_count, float *score32) {
+                         const long long *ids, int tag_value, int max_rows, int *miss_count, float *score32,
+                         const ProfCtx *pc = nullptr) {
+    ProfCtx pc_miss{0, 0, SRC_MISS};
+    if (pc) pc_miss = ProfCtx{pc->batch, pc->pred, SRC_MISS};
     const hydro_query_config &c = q->cfg;
     cudaStream_t st = q->st;
     Emb &e = q->embs[p.upstream - 1];
     const int D = e.dims.back();
     float *act[2] = {(float *)q->act[0], (float *)q->act[1]};
     launch_cache_probe_miss(count, list, ids, e.tags, e.cap, q->miss_list, miss_count, q->d_err, st);
+    int ev = prof_begin(q, pc ? &pc_miss : nullptr, PC_MLP, 2.0 * e.dims[0] * e.dims[1],
+                        4.0 * (e.dims[0] + e.dims[1]), 4.0 * e.dims[0] * e.dims[1]);
     launch_mlp_layer_f32(miss_count, q->miss_list, (const float *)tuples, c.dim, e.dW[0], e.db[0], act[0], e.dims[0],
                          e.dims[1], 1, max_rows, q->sms, st);
+    prof_end(q, ev);
     int cur = 0;
     for (int l = 1; l < e.n_layers; ++l) {
+        ev = prof_begin(q, pc ? &pc_miss : nullptr, PC_MLP, 2.0 * e.dims[l] * e.dims[l + 1],
+                        4.0 * (e.dims[l] + e.dims[l + 1]), 4.0 * e.dims[l] * e.dims[l + 1]);
         launch_mlp_layer_f32(miss_count, nullptr, act[cur], e.dims[l], e.dW[l], e.db[l], act[1 - cur], e.dims[l],
                              e.dims[l + 1], 1, max_rows, q->sms, st);
+        prof_end(q, ev);
         cur = 1 - cur;
     }
     launch_cache_store(miss_count, q->miss_list, ids, act[cur], D, e.values, e.tags, tag_value, max_rows, q->sms,
@@ -577,12 +726,17 @@ hydro_status run_grouped(hydro_query *q, const Pred &p, const int *count, const 
         q->launches++;
         return HYDRO_OK;
     }
+    ev = prof_begin(q, pc, PC_MLP, 2.0 * D * p.dims[hs + 1], 4.0 * (D + p.dims[hs + 1]), 4.0 * D * p.dims[hs + 1]);
     launch_mlp_layer_f32(count, list, e.values, D, p.dW[hs], p.db[hs], act[0], D, p.dims[hs + 1], 1, max_rows, q->sms,
                          st, ids);
+    prof_end(q, ev);
     cur = 0;
     for (int l = hs + 1; l + 1 < L; ++l) {
+        ev = prof_begin(q, pc, PC_MLP, 2.0 * p.dims[l] * p.dims[l + 1], 4.0 * (p.dims[l] + p.dims[l + 1]),
+                        4.0 * p.dims[l] * p.dims[l + 1]);
         launch_mlp_layer_f32(count, nullptr, act[cur], p.dims[l], p.dW[l], p.db[l], act[1 - cur], p.dims[l],
                              p.dims[l + 1], 1, max_rows, q->sms, st);
+        prof_end(q, ev);
         cur = 1 - cur;
     }
     launch_mlp_dot_f32(count, nullptr, act[cur], p.dims[L - 1], p.dW[L - 1], p.b[L - 1][0], p.dims[L - 1], score32,
@@ -613,7 +767,7 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
     if (p.upstream) {
         miss_count = q->ints + 5;
         TRY(run_grouped(q, p, in_count, in_list, tuples, ids, (int)(batch + 1), std::max(n, 1), miss_count,
-                        q->score32));
+                        q->score32, &pc_main));
     } else {
         TRY(run_udf(q, p, wprec, in_count, in_list, tuples, std::max(n, 1), q->act, q->score32, nullptr, &pc_main));
     }
@@ -675,6 +829,175 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
     return HYDRO_OK;
 }
 
+// A batch under the learned router: per-tuple orders (proxy, or the batch's
+// rank order until the proxy is trained), then P rounds; round r splits the
+// alive tuples by the r-th predicate of their order into one queue per
+// predicate and evaluates all queues with grouped launches (FP32, FP64
+// recheck within margin_fp32).  Leaves the final alive list in
+// q->alive[*cur_out], its count in q->ints[*cur_out].
+hydro_status run_batch_learned(hydro_query *q, long long b, const int *order, bool eval_all, const void *tuples,
+                               int n, Slot &slot, int *cur_out) {
+    const hydro_query_config &c = q->cfg;
+    const int P = (int)q->preds.size(), B = c.max_batch;
+    cudaStream_t st = q->st;
+    const float *X = (const float *)tuples;
+    int *cnt = q->ints;
+    StatRow *row = q->ring + (b % q->ring_len) * kMaxPred;
+    StatRow *rrow = (StatRow *)(slot.dres + kRowsOff);
+    launch_zero_rows(row, rrow, P, q->visited, q->label, n, st);
+    launch_init_alive(q->alive[0], cnt + 0, n, nullptr, st);
+    RouterCosts costs{};
+    for (int i = 0; i < P; ++i) costs.c[i] = q->preds[i].cost;
+    if (q->proxy_ready && !eval_all) {
+        launch_mlp_layer_f32(cnt + 0, nullptr, X, c.dim, q->pW1, q->pb1, q->pH, c.dim, q->ph, 1, std::max(n, 1),
+                             q->sms, st);
+        launch_mlp_layer_f32(cnt + 0, nullptr, q->pH, q->ph, q->pW2, q->pb2, q->pZ, q->ph, P, 0, std::max(n, 1),
+                             q->sms, st);
+        launch_tuple_order(n, P, q->pZ, P, costs, nullptr, q->order_t, q->sms, st);
+        q->launches += 3;
+    } else {
+        for (int i = 0; i < P; ++i) q->h_fallback[i] = order[i];
+        CU(cudaMemcpyAsync(q->d_fallback, q->h_fallback, sizeof(int) * P, cudaMemcpyHostToDevice, st));
+        launch_tuple_order(n, P, nullptr, 0, costs, q->d_fallback, q->order_t, q->sms, st);
+        q->launches++;
+    }
+    RoundTests tests{};
+    for (int i = 0; i < P; ++i) {
+        tests.t[i] = q->preds[i].threshold;
+        tests.margin[i] = q->preds[i].margin_fp32;
+    }
+    int maxL = 0;
+    for (const Pred &p : q->preds) maxL = std::max(maxL, p.n_layers);
+    int cur = 0;
+    for (int r = 0; r < P; ++r) {
+        launch_partition(cnt + cur, q->alive[cur], q->order_t, r, P, q->queues, B, q->qcount, st);
+        for (int l = 0; l + 1 < maxL; ++l) {
+            GroupedLayers g{};
+            int tiles = 0;
+            for (int i = 0; i < P; ++i) {
+                const Pred &p = q->preds[i];
+                if (l + 1 >= p.n_layers) continue;
+                GroupLayer &L = g.l[g.n++];
+                L.count = q->qcount + i;
+                L.rows = l == 0 ? q->queues + (size_t)i * B : nullptr;
+                L.X = l == 0 ? X : q->gact[2 * i + (l - 1) % 2];
+                L.ldx = l == 0 ? c.dim : p.dims[l];
+                L.W = p.dW[l];
+                L.b = p.db[l];
+                L.Y = q->gact[2 * i + l % 2];
+                L.K = p.dims[l];
+                L.N = p.dims[l + 1];
+                L.relu = 1;
+                tiles += ((B + 63) / 64) * ((L.N + 63) / 64);
+            }
+            if (g.n) {
+                launch_grouped_layer_f32(g, tiles, q->sms, st);
+                q->launches++;
+            }
+        }
+        GroupedLayers dots{};
+        for (int i = 0; i < P; ++i) {
+            const Pred &p = q->preds[i];
+            const int L = p.n_layers - 1;
+            GroupLayer &G = dots.l[dots.n++];
+            G.count = q->qcount + i;
+            G.rows = L == 0 ? q->queues + (size_t)i * B : nullptr;
+            G.X = L == 0 ? X : q->gact[2 * i + (L - 1) % 2];
+            G.ldx = L == 0 ? c.dim : p.dims[L];
+            G.W = p.dW[L];
+            G.bconst = p.b[L][0];
+            G.K = p.dims[L];
+            G.N = 1;
+        }
+        launch_grouped_dot_f32(dots, q->qscore, B, P * B, q->sms, st);
+        launch_grouped_classify(P, q->qcount, q->queues, B, q->qscore, B, tests, q->okf, q->label, q->visited,
+                                q->bandg, q->bandt, cnt + 2, B, row, rrow, q->d_err, st);
+        launch_grouped_band_f64(cnt + 2, q->bandg, q->bandt, X, c.dim, q->gmlps, tests, q->okf, q->label, row, rrow,
+                                q->sms, st);
+        q->launches += 4;
+        if (!eval_all) {
+            launch_survivors(cnt + cur, q->alive[cur], q->okf, q->alive[1 - cur], cnt + 1 - cur, st);
+            q->launches++;
+            cur = 1 - cur;
+        }
+    }
+    if (eval_all) {
+        launch_full_label_acc(q->label, n, P, q->acc, st);
+        launch_acc_to_alive(q->acc, n, q->alive[1 - cur], cnt + 1 - cur, st);
+        q->launches += 2;
+        cur = 1 - cur;
+    }
+    if (adaptive(c.policy) && b < c.warmup_batches)
+        CU(cudaMemcpyAsync(q->warm + b * kMaxPred, row, sizeof(StatRow) * P, cudaMemcpyDeviceToDevice, st));
+    // outcomes for the proxy's training ring
+    const int R = (int)q->ring_n.size();
+    const int rs = (int)(b % R);
+    if (n > 0) {
+        CU(cudaMemcpyAsync(q->ringX + (size_t)rs * B * c.dim, X, sizeof(float) * (size_t)n * c.dim,
+                           cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpyAsync(q->ringL + (size_t)rs * B, q->label, n, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpyAsync(q->ringM + (size_t)rs * B, q->visited, n, cudaMemcpyDeviceToDevice, st));
+    }
+    q->ring_n[rs] = n;
+    q->last_learned_batch = b;
+    q->last_n = n;
+    *cur_out = cur;
+    return HYDRO_OK;
+}
+
+// Retrain the proxy on the training ring (enqueued after the batch that
+// filled the ring; batches submitted later use the new weights).
+hydro_status train_proxy(hydro_query *q) {
+    const hydro_query_config &c = q->cfg;
+    const int P = (int)q->preds.size(), D = c.dim, H = q->ph, B = c.max_batch;
+    const size_t nW1 = (size_t)H * D;
+    for (int e = 0; e < std::max(1, c.proxy_epochs); ++e)
+        for (size_t s = 0; s < q->ring_n.size(); ++s) {
+            const int M = q->ring_n[s];
+            if (M <= 0) continue;
+            const float *Xs = q->ringX + s * (size_t)B * D;
+            launch_identity_list(q->alive[0], q->ints + 7, 0, M, q->st);
+            launch_mlp_layer_f32(q->ints + 7, nullptr, Xs, D, q->pW1, q->pb1, q->pH, D, H, 1, M, q->sms, q->st);
+            launch_mlp_layer_f32(q->ints + 7, nullptr, q->pH, H, q->pW2, q->pb2, q->pZ, H, P, 0, M, q->sms, q->st);
+            ProxyTrain pt{};
+            pt.M = M;
+            pt.P = P;
+            pt.H = H;
+            pt.D = D;
+            pt.sms = q->sms;
+            pt.t = ++q->adam_t;
+            pt.lr = c.proxy_lr;
+            pt.X = Xs;
+            pt.Hact = q->pH;
+            pt.Z = q->pZ;
+            pt.dZ = q->pdZ;
+            pt.dH = q->pdH;
+            pt.inv_pairs = q->pinv;
+            pt.label = q->ringL + s * (size_t)B;
+            pt.mask = q->ringM + s * (size_t)B;
+            pt.W1 = q->pW1;
+            pt.b1 = q->pb1;
+            pt.W2 = q->pW2;
+            pt.b2 = q->pb2;
+            pt.gW1 = q->pg;
+            pt.gb1 = q->pg + nW1;
+            pt.gW2 = pt.gb1 + H;
+            pt.gb2 = pt.gW2 + (size_t)P * H;
+            pt.mW1 = q->pm;
+            pt.mb1 = q->pm + nW1;
+            pt.mW2 = pt.mb1 + H;
+            pt.mb2 = pt.mW2 + (size_t)P * H;
+            pt.vW1 = q->pv;
+            pt.vb1 = q->pv + nW1;
+            pt.vW2 = pt.vb1 + H;
+            pt.vb2 = pt.vW2 + (size_t)P * H;
+            launch_proxy_train_step(pt, q->st);
+            q->launches += 12;
+        }
+    q->proxy_ready = true;
+    return HYDRO_OK;
+}
+
 hydro_status wait_event(cudaEvent_t ev, long long wait_ms, bool *done) {
     auto t0 = std::chrono::steady_clock::now();
     for (;;) {
@@ -724,6 +1047,11 @@ void hydro_default_config(hydro_query_config *cfg) {
     cfg->max_in_flight = 4;
     cfg->device = 0;
     cfg->stream = nullptr;
+    cfg->proxy_hidden = 64;
+    cfg->proxy_refresh = 16;
+    cfg->proxy_epochs = 2;
+    cfg->proxy_lr = 1e-3f;
+    cfg->proxy_seed = 1;
 }
 
 hydro_status hydro_create_query(const hydro_query_config *cfg, hydro_query **out) {
@@ -740,11 +1068,17 @@ hydro_status hydro_create_query(const hydro_query_config *cfg, hydro_query **out
         return fail(HYDRO_EINVAL, "unknown tuple_kind %d", c.tuple_kind);
     }
     if (c.max_batch < 1 || c.max_batch > 65536) return fail(HYDRO_EINVAL, "max_batch must be 1..65536");
-    if (c.policy < 0 || c.policy > 4) return fail(HYDRO_EINVAL, "unknown policy");
+    if (c.policy < 0 || c.policy > 5) return fail(HYDRO_EINVAL, "unknown policy");
+    if (c.policy == HYDRO_POLICY_LEARNED) {
+        if (c.tuple_kind != HYDRO_TUPLE_F32 || c.precision != HYDRO_PREC_FP32)
+            return fail(HYDRO_EUNSUPPORTED, "the learned router needs F32 tuples and an FP32 query");
+        if (c.proxy_hidden < 0 || c.proxy_hidden > 1024 || c.proxy_refresh < 0 || c.proxy_epochs < 0 ||
+            !(c.proxy_lr >= 0.f))
+            return fail(HYDRO_EINVAL, "bad proxy settings");
+    }
     if (c.precision != HYDRO_PREC_FP32 && c.precision != HYDRO_PREC_BF16)
         return fail(HYDRO_EINVAL, "precision must be FP32 or BF16");
-    if (c.precision == HYDRO_PREC_BF16 && c.tuple_kind == HYDRO_TUPLE_F32)
-        return fail(HYDRO_EUNSUPPORTED, "BF16 inference of MLP UDFs is not built; use FP32");
+
     if (c.cost_source != HYDRO_COST_MODEL)
         return fail(HYDRO_EUNSUPPORTED, "only HYDRO_COST_MODEL is built");
     if (c.warmup_batches < 0 || c.warmup_batches > 64) return fail(HYDRO_EINVAL, "warmup_batches must be 0..64");
@@ -877,13 +1211,23 @@ hydro_status hydro_add_embedding(hydro_query *q, const hydro_udf_desc *udf, int6
     return HYDRO_OK;
 }
 
+hydro_status hydro_cache_clear(hydro_query *q, int32_t emb) {
+    g_err.clear();
+    TRY(check_query(q));
+    if (emb < 1 || emb > (int)q->embs.size()) return fail(HYDRO_EINVAL, "unknown embedding id %d", emb);
+    CU(cudaSetDevice(q->cfg.device));
+    TRY(finalize(q));
+    Emb &e = q->embs[emb - 1];
+    CU(cudaMemsetAsync(e.tags, 0, sizeof(int) * (size_t)e.cap, q->st));
+    return HYDRO_OK;
+}
+
 hydro_status hydro_cache_prefill(hydro_query *q, int32_t emb, const void *d_tuples, const int64_t *d_ids,
                                  int64_t n) {
     g_err.clear();
     TRY(check_query(q));
     if (emb < 1 || emb > (int)q->embs.size()) return fail(HYDRO_EINVAL, "unknown embedding id %d", emb);
     if (n < 0 || (n > 0 && (!d_tuples || !d_ids))) return fail(HYDRO_EINVAL, "bad tuples/ids");
-    if (q->next_batch > 0) return fail(HYDRO_ESTATE, "prefill before the first submit");
     CU(cudaSetDevice(q->cfg.device));
     TRY(finalize(q));
     Pred probe;                    // an embedding-only pass: no head
@@ -1068,7 +1412,9 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
             }
             for (size_t e = 0; e < q->embs.size(); ++e) costs.cemb[e] = q->embs[e].cost;
             costs.n = n;
-            const int pol = c.policy == HYDRO_POLICY_RANK ? 0 : c.policy == HYDRO_POLICY_COST ? 1 : 2;
+            const int pol = (c.policy == HYDRO_POLICY_RANK || c.policy == HYDRO_POLICY_LEARNED) ? 0
+                            : c.policy == HYDRO_POLICY_COST                                      ? 1
+                                                                                                 : 2;
             int *dord = q->d_order + slot_idx * kMaxPred;
             int *hord = q->h_order + slot_idx * kMaxPred;
             CU(cudaStreamWaitEvent(q->rst, q->ev_done[last % kEvRing], 0));
@@ -1103,10 +1449,20 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
     std::memcpy(slot->order, order, sizeof order);
     CU(cudaEventRecord(slot->start, q->st));
     int *cnt = q->ints;
-    launch_init_alive(q->alive[0], cnt + 0, (int)n, eval_all ? q->acc : nullptr, q->st);
-    q->launches++;
     int cur = 0;
-    for (int k = 0; k < P; ++k) {
+    const bool learned = c.policy == HYDRO_POLICY_LEARNED;
+    if (learned) {
+        hydro_status s = run_batch_learned(q, b, order, eval_all, d_tuples, (int)n, *slot, &cur);
+        if (s != HYDRO_OK) {
+            slot->busy = false;
+            q->dead = true;
+            return s;
+        }
+    } else {
+        launch_init_alive(q->alive[0], cnt + 0, (int)n, eval_all ? q->acc : nullptr, q->st);
+        q->launches++;
+    }
+    for (int k = 0; k < P && !learned; ++k) {
         hydro_status s = run_stage(q, order[k], cnt + cur, q->alive[cur], q->alive[1 - cur], cnt + 1 - cur, eval_all,
                                    d_tuples, (const long long *)d_ids, (int)n, b, *slot);
         if (s != HYDRO_OK) {
@@ -1116,7 +1472,7 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
         }
         if (!eval_all) cur = 1 - cur;
     }
-    if (eval_all) {
+    if (eval_all && !learned) {
         launch_acc_to_alive(q->acc, (int)n, q->alive[1 - cur], cnt + 1 - cur, q->st);
         q->launches++;
         cur = 1 - cur;
@@ -1129,6 +1485,8 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
     CU(cudaMemcpyAsync(slot->hres, slot->dres, bytes, cudaMemcpyDeviceToHost, q->st));
     CU(cudaEventRecord(slot->done, q->st));
     CU(cudaEventRecord(q->ev_done[b % kEvRing], q->st));
+    if (learned && c.proxy_refresh > 0 && (b + 1) % c.proxy_refresh == 0 && b + 1 > c.warmup_batches)
+        TRY(train_proxy(q));
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) {
         q->dead = true;
@@ -1198,6 +1556,23 @@ hydro_status hydro_poll_result(hydro_query *q, int64_t batch_id, uint32_t *pass_
     return HYDRO_OK;
 }
 
+hydro_status hydro_debug_trace(hydro_query *q, int64_t batch_id, uint8_t *order, uint8_t *visited) {
+    g_err.clear();
+    TRY(check_query(q));
+    if (q->cfg.policy != HYDRO_POLICY_LEARNED) return fail(HYDRO_EUNSUPPORTED, "trace is kept by the learned router");
+    if (batch_id != q->last_learned_batch || batch_id != q->next_batch - 1)
+        return fail(HYDRO_ENOTFOUND, "trace is only kept for the most recently submitted batch");
+    for (const Slot &s : q->slots)
+        if (s.busy && s.batch == batch_id) return fail(HYDRO_ESTATE, "poll the batch first");
+    CU(cudaSetDevice(q->cfg.device));
+    CU(cudaStreamSynchronize(q->st));
+    if (q->last_n > 0) {
+        if (order) CU(cudaMemcpy(order, q->order_t, (size_t)q->last_n * kMaxPred, cudaMemcpyDeviceToHost));
+        if (visited) CU(cudaMemcpy(visited, q->visited, (size_t)q->last_n, cudaMemcpyDeviceToHost));
+    }
+    return HYDRO_OK;
+}
+
 hydro_status hydro_get_stats(hydro_query *q, hydro_pred_stats *out, int32_t n) {
     g_err.clear();
     if (!q || !out) return fail(HYDRO_EINVAL, "NULL argument");
@@ -1242,10 +1617,11 @@ hydro_status hydro_profile_read(hydro_query *q, hydro_kernel_profile *out, int32
         const long long k = r.batch - q->prof.base;
         if (k < 0 || k >= (long long)q->prof.rows.size() || q->prof.rows[k].empty()) continue;   // not polled
         const StatRow &row = q->prof.rows[k][r.pred];
-        const long long items = r.src == SRC_MAIN  ? row.evaluated
-                                : r.src == SRC_RTF ? row.recheck_tf32
-                                : r.src == SRC_R32 ? row.recheck32
-                                                   : row.recheck64;
+        const long long items = r.src == SRC_MAIN   ? row.evaluated
+                                : r.src == SRC_RTF  ? row.recheck_tf32
+                                : r.src == SRC_R32  ? row.recheck32
+                                : r.src == SRC_MISS ? row.evaluated - row.hits
+                                                    : row.recheck64;
         float t = 0.f;
         if (cudaEventElapsedTime(&t, q->prof.ev[r.ev], q->prof.ev[r.ev + 1]) != cudaSuccess) {
             cudaGetLastError();
@@ -1274,6 +1650,23 @@ hydro_status hydro_profile_read(hydro_query *q, hydro_kernel_profile *out, int32
     return HYDRO_OK;
 }
 
+hydro_status hydro_selftest_bounded_wait(int32_t device, int64_t limit_ns) {
+    g_err.clear();
+    if (limit_ns < 1000 || limit_ns > 10000000000LL) return fail(HYDRO_EINVAL, "limit_ns must be 1e3..1e10");
+    CU(cudaSetDevice(device));
+    int *d = nullptr;
+    CU(cudaMalloc(&d, sizeof(int)));
+    int h = -1;
+    cudaError_t e = cudaMemset(d, 0xff, sizeof(int));
+    if (e == cudaSuccess) e = wait_selftest((unsigned long long)limit_ns, d, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(HYDRO_ECUDA, "self-test: %s", cudaGetErrorString(e));
+    if (h == 1) return fail(HYDRO_ETIMEOUT, "the wait ran out after %lld ns, as designed", (long long)limit_ns);
+    return fail(HYDRO_EDEVICE, "the wait did not run out (status %d)", h);
+}
+
 hydro_status hydro_destroy_query(hydro_query *q) {
     g_err.clear();
     if (!q) return fail(HYDRO_EINVAL, "NULL query");
@@ -1298,6 +1691,7 @@ hydro_status hydro_destroy_query(hydro_query *q) {
             if (s.done) cudaEventDestroy(s.done);
         }
         if (q->h_order) cudaFreeHost(q->h_order);
+        if (q->h_fallback) cudaFreeHost(q->h_fallback);
         for (void *p : q->allocs) cudaFree(p);
         for (int i = 0; i < kEvRing; ++i)
             if (q->ev_done[i]) cudaEventDestroy(q->ev_done[i]);

@@ -88,6 +88,64 @@ void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, in
 void launch_pool_head(int prec, const int *count, const void *act, int HW, int C, const float *hw, double hb,
                       void *score, int max_frames, int sms, cudaStream_t st);
 
+// k_learned.cu: per-tuple routing by a learned proxy, grouped per-predicate queues
+struct GroupLayer {
+    const int *count;    // rows of this group (device)
+    const int *rows;     // row indices into X (nullable: rows 0..count-1)
+    const float *X;
+    int ldx;
+    const float *W;      // [N][K]
+    const float *b;      // [N] (hidden layers)
+    float bconst;        // bias of a one-output last layer
+    float *Y;            // [rows][N] (hidden layers)
+    int K, N, relu;
+};
+struct GroupedLayers {
+    int n;
+    GroupLayer l[8];
+};
+struct RoundTests {
+    double t[8];
+    double margin[8];
+};
+struct GroupedMlps {
+    int max_width;
+    MlpDev m[8];
+};
+struct ProxyTrain {
+    int M, P, H, D, sms, t;
+    float lr;
+    const float *X;            // [M][D] minibatch features
+    const float *Hact;         // [M][H] hidden activations (forward)
+    const float *Z;            // [M][P] logits (forward)
+    float *dZ, *dH, *inv_pairs;
+    const unsigned char *label, *mask;   // per tuple: pass bits / evaluated bits
+    float *W1, *b1, *W2, *b2;
+    float *gW1, *gb1, *gW2, *gb2;
+    float *mW1, *vW1, *mb1, *vb1, *mW2, *vW2, *mb2, *vb2;
+};
+void launch_tuple_order(int n, int P, const float *logits, int ldz, const RouterCosts &costs, const int *fallback,
+                        unsigned char *order, int sms, cudaStream_t st);
+void launch_partition(const int *count, const int *alive, const unsigned char *order, int r, int P, int *queues,
+                      int qstride, int *qcount, cudaStream_t st);
+void launch_grouped_layer_f32(const GroupedLayers &g, int max_tiles, int sms, cudaStream_t st);
+void launch_grouped_dot_f32(const GroupedLayers &g, float *score, int sstride, int max_rows, int sms,
+                            cudaStream_t st);
+void launch_grouped_classify(int P, const int *qcount, const int *queues, int qstride, const float *score,
+                             int sstride, const RoundTests &tests, unsigned char *ok, unsigned char *label,
+                             unsigned char *visited, int *band_g, int *band_t, int *band_count, int band_cap,
+                             StatRow *row, StatRow *rrow, unsigned int *err, cudaStream_t st);
+void launch_grouped_band_f64(const int *band_count, const int *band_g, const int *band_t, const float *X, int ldx,
+                             const GroupedMlps &mlps, const RoundTests &tests, unsigned char *ok,
+                             unsigned char *label, StatRow *row, StatRow *rrow, int sms, cudaStream_t st);
+cudaError_t grouped_band_smem_setup(int max_width);
+void launch_survivors(const int *count_in, const int *alive_in, const unsigned char *ok, int *alive_out,
+                      int *count_out, cudaStream_t st);
+void launch_zero_rows(StatRow *row, StatRow *rrow, int P, unsigned char *visited, unsigned char *label, int n,
+                      cudaStream_t st);
+void launch_full_label_acc(const unsigned char *label, int n, int P, unsigned char *acc, cudaStream_t st);
+void launch_proxy_train_step(const ProxyTrain &pt, cudaStream_t st);
+
 // hydro_api.cu: message returned by hydro_last_error() on this thread
 void set_last_error(const char *msg);
 

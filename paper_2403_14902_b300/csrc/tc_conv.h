@@ -38,6 +38,8 @@ hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int
 void tc_head_finalize(const int *count, const float *partials, int parts_per_frame, double hb, int HW,
                       float *score, int max_frames, int sms, cudaStream_t st);
 void tc_conv_destroy(TcConvPlan *plan);
+// Launch the bounded-wait self-test (an mbarrier wait nothing completes).
+cudaError_t wait_selftest(unsigned long long limit_ns, int *d_status, cudaStream_t st);
 const char *tc_conv_last_error();
 
 }  // namespace hydro

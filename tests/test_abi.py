@@ -59,7 +59,7 @@ def test_default_config():
     cfg = H.QueryConfig()
     H.load().hydro_default_config(ctypes.byref(cfg))
     assert (cfg.policy, cfg.precision, cfg.warmup_batches, cfg.stats_window, cfg.route_lag,
-            cfg.max_in_flight) == (0, 0, 1, 8, 1, 4)
+            cfg.max_in_flight, cfg.proxy_hidden, cfg.proxy_refresh) == (0, 0, 1, 8, 1, 4, 64, 16)
 
 
 def test_create_rejects_bad_config_without_touching_a_device():

@@ -307,3 +307,34 @@ def test_simulate_reuse_matches_plain_counts():
         assert np.array_equal(a["bits"], b["bits"]) and a["counts"].tolist() == b["counts"].tolist()
         # predicate 0 runs after predicate 1 (same group) on a subset of its tuples: all hits
         assert b["hits"][0] == b["counts"][0]
+
+
+def test_concurrent_worked_example_color_first():
+    # Sec. 4.1 "Example comparison": color (cost 1, s 0.6) then breed (cost 2):
+    # 10 units of color, six survivors to breed -> 14 time units
+    ex = _golden()["worked_example"]
+    assert O.concurrent_makespan([0, 1], [1, 2], [0.6, 0.1], 10) == ex["concurrent_time_color_first"]
+    # breed first: the breed resource alone needs 20 units
+    assert O.fluid_makespan([1, 0], [1, 2], [0.6, 0.1], 10) == ex["concurrent_time_breed_first"]
+    assert O.concurrent_makespan([1, 0], [1, 2], [0.6, 0.1], 10) >= 20
+
+
+def test_synthetic_sweep_claims():
+    # Sec. 4.2 "Sensitive Analysis using Synthetic Queries": A costs 10, B 20;
+    # s_B in {0.1, 0.5, 0.9}, s_A from 0.1 to 0.9.  Under concurrency the
+    # cost-driven order (A first) is never slower than score- or
+    # selectivity-driven, and selectivity-driven is the worst on average.
+    c = [10, 20]
+    totals = {"cost": 0.0, "score": 0.0, "selectivity": 0.0}
+    for sB in (0.1, 0.5, 0.9):
+        for sA in [k / 10 for k in range(1, 10)]:
+            s = [sA, sB]
+            orders = {"cost": O.order_by([Fraction(10), Fraction(20)]),
+                      "score": O.order_by([Fraction(10) / (1 - Fraction(sA).limit_denominator(10)),
+                                           Fraction(20) / (1 - Fraction(sB).limit_denominator(10))]),
+                      "selectivity": O.order_by([Fraction(sA).limit_denominator(10), Fraction(sB).limit_denominator(10)])}
+            t = {k: O.concurrent_makespan(o, c, s, 100) for k, o in orders.items()}
+            assert t["cost"] <= t["score"] and t["cost"] <= t["selectivity"]
+            for k in totals:
+                totals[k] += t[k]
+    assert totals["selectivity"] >= totals["score"] >= totals["cost"]
