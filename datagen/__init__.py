@@ -25,6 +25,14 @@ for them with the shapes of the build's five configurations):
   predicate's selectivity drifts between segments); five MLP UDFs, the first
   two sharing an upstream embedding 512-1024-256 (heads 256-1 and 256-256-1),
   then 512-256-1, 512-1024-1024-1, 512-2048-1; batches of 4,096.
+* ``drift6`` - the same drifting stream under six MLPs 512-h-1, h = 64 ... 2048
+  (costs 1:2:4:8:16:32), for per-tuple routing by a learned proxy.
+* ``mq64`` - 64 concurrent queries over 512-dim fp32 tuples: query q has a
+  lognormal tuple count (median 20,000, clipped to 1,000 ... 200,000), its
+  own Dirichlet(0.5) cluster mixture, and a conjunction of 2-6 distinct UDFs
+  drawn from one shared pool of eight MLPs (hidden widths 256 ... 2048) with
+  per-slot target selectivities uniform in [0.2, 0.9]; each query is routed
+  in chunks of 4,096 of its own tuples.
 """
 from __future__ import annotations
 
@@ -39,6 +47,7 @@ __all__ = [
     "rng", "Workload", "WORKLOADS", "workload", "gmm_tuples", "blob_frames",
     "mlp_weights", "cnn_weights", "tuple_ids", "predicate_weights",
     "stream_tuples", "calib_tuples", "embedding_weights", "head_weights", "segment_mixes",
+    "mq_queries", "mq_pool_weights", "mq_tuples", "mq_calib_tuples", "mq_stacked_step",
 ]
 
 
@@ -87,6 +96,15 @@ WORKLOADS = {
         udfs=tuple((512, 64 << k, 1) for k in range(6)),
         selectivity=(0.6, 0.5, 0.4, 0.5, 0.3, 0.5), n_calib=1024,
         extra={"segments": 8, "dirichlet": 0.5, "weight_stream": 40, "proxy_hidden": 64, "refresh": 16}),
+    # 64 queries over one pool of eight MLP UDFs; ``n`` caps a query's
+    # tuple count, ``batch`` is the per-query chunk of one step
+    "mq64": Workload(
+        name="mq64", wid=5, kind="vec", n=200000, batch=4096, dim=512,
+        udfs=((512, 256, 1), (512, 512, 1), (512, 1024, 1), (512, 2048, 1), (512, 512, 256, 1),
+              (512, 1024, 512, 1), (512, 2048, 1024, 1), (512, 1024, 1024, 1)),
+        selectivity=(), n_calib=1024,
+        extra={"queries": 64, "median": 20000, "sigma": 1.0, "min_n": 1000, "min_p": 2, "max_p": 6,
+               "sel_lo": 0.2, "sel_hi": 0.9, "dirichlet": 0.5}),
 }
 
 
@@ -314,3 +332,55 @@ def calib_tuples(w: Workload) -> np.ndarray:
     if w.kind == "vec":
         return gmm_tuples(w, 2, w.n_calib)
     return blob_frames(w, 2, w.n_calib)
+
+
+# ----------------------------------------------------------------- many queries
+
+def mq_queries(w: Workload) -> list:
+    """The concurrent queries of a pool workload (stream 6): per query its
+    tuple count ``n``, pool UDF ids ``udfs`` (distinct, in slot order),
+    target selectivities ``selectivity`` per slot and cluster mixture ``mix``."""
+    e = w.extra
+    g = rng(w.wid, 6)
+    out = []
+    for _ in range(e["queries"]):
+        n = int(round(e["median"] * math.exp(e["sigma"] * g.standard_normal())))
+        n = min(max(n, e["min_n"]), w.n)
+        P = int(g.integers(e["min_p"], e["max_p"] + 1))
+        udfs = [int(u) for u in g.permutation(len(w.udfs))[:P]]
+        sel = [float(v) for v in g.uniform(e["sel_lo"], e["sel_hi"], size=P)]
+        mix = g.dirichlet(np.full(w.n_clusters, e["dirichlet"]))
+        out.append(dict(n=n, udfs=udfs, selectivity=sel, mix=mix))
+    return out
+
+
+def mq_pool_weights(w: Workload) -> list:
+    """Layers of every pool UDF, UDF u on stream 10+u."""
+    return [mlp_weights(w, 10 + u, d) for u, d in enumerate(w.udfs)]
+
+
+def mq_tuples(w: Workload, q: int, n: int | None = None, queries=None) -> np.ndarray:
+    """Query q's tuple stream (stream 100+q), its first ``n`` tuples."""
+    qs = mq_queries(w) if queries is None else queries
+    n = qs[q]["n"] if n is None else n
+    return gmm_tuples(w, 100 + q, n, qs[q]["mix"])
+
+
+def mq_calib_tuples(w: Workload, q: int, queries=None) -> np.ndarray:
+    """Query q's calibration draw (stream 400+q), from its own mixture."""
+    qs = mq_queries(w) if queries is None else queries
+    return gmm_tuples(w, 400 + q, w.n_calib, qs[q]["mix"])
+
+
+def mq_stacked_step(streams, counts_done, chunk: int):
+    """One step's input: the next ``chunk`` (or fewer) tuples of every query
+    stacked query after query.  Returns (stacked rows, per-query counts)."""
+    parts, counts = [], []
+    for q, X in enumerate(streams):
+        lo = counts_done[q]
+        m = max(0, min(chunk, X.shape[0] - lo))
+        parts.append(X[lo:lo + m])
+        counts.append(m)
+    dim = streams[0].shape[1] if streams else 0
+    rows = np.concatenate(parts) if parts else np.zeros((0, dim), np.float32)
+    return np.ascontiguousarray(rows), counts

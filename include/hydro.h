@@ -334,6 +334,139 @@ HYDRO_API hydro_status hydro_mlp_scores_noalloc(const float *d_x, int64_t n, int
  * kernels is bounded the same way. */
 HYDRO_API hydro_status hydro_selftest_bounded_wait(int32_t device, int64_t limit_ns);
 
+/* ------------------------------------------------------------ sessions
+ *
+ * Many concurrent queries over one shared pool of MLP UDFs.  The paper's
+ * Laminar operator (Sec. 5.1 "Batch-agnostic Parallelization", Sec. 5.3
+ * "Data-Aware Load Balancing") runs several predicate workers at once because
+ * one worker on small routing batches leaves the GPU mostly idle (Sec. 5.2
+ * "GPU Utilization Study": about 20 %).  A session does the same work
+ * inside the GPU: in a step, every query contributes its next chunk of
+ * tuples; in round r every surviving tuple goes to the pool UDF of the r-th
+ * predicate of its query's current order; all queries' work on one UDF forms
+ * one group, and all groups of a layer depth run in ONE persistent grouped
+ * launch whose tile scheduler balances the uneven group sizes.  A step's
+ * launches are stream-ordered and device-driven (counts, orders and lists
+ * live on the GPU), so they replay from a captured CUDA graph.
+ *
+ * Each query is routed exactly as a single query would be with route_lag 0
+ * (Sec. 4.1): its k-th step with tuples is its batch k, ordered by rank
+ * cost/(1-s) over its own window of earlier batches (ties to the lower slot),
+ * its first warmup_batches batches evaluating every predicate on every tuple.
+ * Its pass set, orders and counts therefore equal those of that query run
+ * alone over the same chunks.
+ */
+#define HYDRO_MAX_QUERIES 256
+#define HYDRO_MAX_POOL 8
+
+typedef struct hydro_session hydro_session;
+
+typedef struct hydro_session_config {
+    int32_t dim;              /* features per fp32 tuple row; a multiple of 64 */
+    int32_t max_step_tuples;  /* largest sum of counts one step may pass, 1..4194304 */
+    int32_t precision;        /* HYDRO_PREC_FP32 or HYDRO_PREC_BF16 (tensor cores, pool UDFs
+                                 whose widths are multiples of 64) */
+    int32_t warmup_batches;   /* per query, as in hydro_query_config */
+    int32_t stats_window;     /* per query, W >= 1 */
+    int32_t use_graphs;       /* 1: each in-flight slot replays its step from a CUDA graph
+                                 captured at its first use; 0: launch kernel by kernel */
+    int32_t autotune;         /* 1: at the first submit, time every tensor-core tile width
+                                 (64/128/256 columns) of every pool layer and keep the fastest */
+    int32_t max_in_flight;    /* submitted, unpolled steps, 1..8 */
+    int32_t device;           /* CUDA device ordinal */
+    void *stream;             /* cudaStream_t the steps run on; NULL = library stream */
+} hydro_session_config;
+
+/* Per query result of one step (hydro_session_poll). */
+typedef struct hydro_step_query {
+    int64_t n;                                   /* the query's tuples in the step */
+    int64_t n_pass;                              /* of them, in the result */
+    int64_t batch;                               /* the query's batch number (-1: no tuples) */
+    int32_t warmup;                              /* 1: every predicate saw every tuple */
+    int32_t order[HYDRO_MAX_PREDICATES];         /* slots in evaluation order (first n_preds) */
+    int64_t evaluated[HYDRO_MAX_PREDICATES];     /* per slot: tuples evaluated at working precision */
+    int64_t passed[HYDRO_MAX_PREDICATES];        /* per slot: of those, passed */
+    int64_t recheck_fp32[HYDRO_MAX_PREDICATES];  /* per slot: re-evaluated in FP32 (BF16 sessions) */
+    int64_t recheck_fp64[HYDRO_MAX_PREDICATES];  /* per slot: re-evaluated in FP64 */
+} hydro_step_query;
+
+/* Autotuner record of one pool layer (hydro_session_tuning). */
+typedef struct hydro_tile_choice {
+    int32_t udf, layer;       /* pool UDF and hidden layer */
+    int32_t K, N;             /* layer shape */
+    int32_t tile_n;           /* chosen tensor-core tile width (columns) */
+    double us[3];             /* measured microseconds for tile widths 64, 128, 256 (0: not tried) */
+} hydro_tile_choice;
+
+/* Defaults: FP32, warmup 1, window 8, graphs on, autotune on, 2 in flight,
+ * device 0, NULL stream; dim and max_step_tuples must be set. */
+HYDRO_API void hydro_session_default_config(hydro_session_config *cfg);
+
+HYDRO_API hydro_status hydro_session_create(const hydro_session_config *cfg, hydro_session **out);
+
+/* Add pool UDF *out_udf = 0, 1, ... (an MLP, dims[0] = dim, dims[n_layers] = 1,
+ * at most HYDRO_MAX_POOL).  Weights copied.  Before the first submit.
+ * Default margins: margin_lowp 0.02, margin_fp32 1e-5. */
+HYDRO_API hydro_status hydro_session_add_udf(hydro_session *s, const hydro_udf_desc *udf, int32_t *out_udf);
+
+/* Add query *out_query = 0, 1, ...: the conjunction over slots k < n_preds
+ * (1..HYDRO_MAX_PREDICATES) of  pool UDF udfs[k] (distinct) > thresholds[k].
+ * Before the first submit. */
+HYDRO_API hydro_status hydro_session_add_query(hydro_session *s, int32_t n_preds, const int32_t *udfs,
+                                               const double *thresholds, int32_t *out_query);
+
+/* Margins of pool UDF udf (absolute score units): a working-precision score
+ * within margin_lowp (BF16) or margin_fp32 (FP32 scores) of a threshold is
+ * re-evaluated at the next precision (BF16 -> FP32 -> FP64). */
+HYDRO_API hydro_status hydro_session_set_margins(hydro_session *s, int32_t udf, double margin_lowp,
+                                                 double margin_fp32);
+
+/* Calibrate every pool UDF's margins on n device tuples, with the rule of
+ * hydro_calibrate (margin_fp32 = 16 x max FP32 error, margin_lowp raised to
+ * 4 x max BF16 error).  info[n_udfs] nullable.  Synchronous. */
+HYDRO_API hydro_status hydro_session_calibrate(hydro_session *s, const void *d_tuples, int64_t n,
+                                               hydro_calib_info *info);
+
+/* Scores of pool UDF udf on n device tuples at HYDRO_PREC_FP64/FP32/BF16 into
+ * d_scores (device, n doubles).  Synchronous. */
+HYDRO_API hydro_status hydro_session_udf_scores(hydro_session *s, int32_t udf, int32_t prec, const void *d_tuples,
+                                                int64_t n, double *d_scores);
+
+/* Submit one step.  d_tuples: device fp32 rows, counts[0] rows of query 0,
+ * then counts[1] rows of query 1, ... (BORROWED until the step is polled).
+ * counts: host [n_queries], each >= 0, sum <= max_step_tuples.  A query with
+ * count 0 sits the step out (its batch number does not advance).
+ * Asynchronous; *out_step receives 0, 1, 2, ... */
+HYDRO_API hydro_status hydro_session_submit(hydro_session *s, const void *d_tuples, const int32_t *counts,
+                                            int64_t *out_step);
+
+/* Result of a step.  pass_bitmap: host, ceil(total/32) words, bit j = the
+ * j-th stacked tuple passed every predicate of its query.  per_query: host
+ * [n_queries] (nullable).  device_ms (nullable): GPU time of the step.
+ * wait_ms as in hydro_poll_result; HYDRO_EAGAIN if not finished. */
+HYDRO_API hydro_status hydro_session_poll(hydro_session *s, int64_t step, uint32_t *pass_bitmap,
+                                          hydro_step_query *per_query, double *device_ms, int32_t wait_ms);
+
+/* Autotuner records (after the first submit): out[max], *n_out written. */
+HYDRO_API hydro_status hydro_session_tuning(hydro_session *s, hydro_tile_choice *out, int32_t max, int32_t *n_out);
+
+/* Start (enable = 1, clearing earlier records) or stop per-class timing of a
+ * session's kernels: while on, steps launch kernel by kernel (no graph)
+ * with CUDA events around each launch class; also resets the launch counter.
+ * No step may be in flight. */
+HYDRO_API hydro_status hydro_session_profile(hydro_session *s, int32_t enable);
+
+/* Per kernel class launches and device ms of the steps polled since the
+ * last hydro_session_profile(s, 1) (flops and bytes are left 0: they depend
+ * on the per-query counts the caller reads from the polls); *total_launches
+ * (nullable) = kernel launches of all steps polled since then, graph
+ * replays included. */
+HYDRO_API hydro_status hydro_session_profile_read(hydro_session *s, hydro_kernel_profile *out, int32_t max,
+                                                  int32_t *n_out, int64_t *total_launches);
+
+/* Wait for outstanding steps (bounded), free every resource of s. */
+HYDRO_API hydro_status hydro_session_destroy(hydro_session *s);
+
 /* Wait for outstanding work (bounded), free every resource of q. */
 HYDRO_API hydro_status hydro_destroy_query(hydro_query *q);
 

@@ -33,7 +33,14 @@ EXPORTED = ["hydro_default_config", "hydro_create_query", "hydro_add_predicate",
             "hydro_cache_prefill", "hydro_cache_clear", "hydro_set_margins",
             "hydro_set_static_order", "hydro_calibrate", "hydro_udf_scores", "hydro_submit_batch",
             "hydro_poll_result", "hydro_debug_trace", "hydro_get_stats", "hydro_profile", "hydro_profile_read",
-            "hydro_mlp_scores_noalloc", "hydro_selftest_bounded_wait", "hydro_destroy_query", "hydro_last_error"]
+            "hydro_mlp_scores_noalloc", "hydro_selftest_bounded_wait",
+            "hydro_session_default_config", "hydro_session_create", "hydro_session_add_udf",
+            "hydro_session_add_query", "hydro_session_set_margins", "hydro_session_calibrate",
+            "hydro_session_udf_scores", "hydro_session_submit", "hydro_session_poll", "hydro_session_tuning",
+            "hydro_session_profile", "hydro_session_profile_read",
+            "hydro_session_destroy", "hydro_destroy_query", "hydro_last_error"]
+MAX_QUERIES = 256
+MAX_POOL = 8
 
 
 class QueryConfig(ctypes.Structure):
@@ -77,6 +84,26 @@ class CalibInfo(ctypes.Structure):
                 ("margin_lowp", ctypes.c_double), ("margin_tf32", ctypes.c_double)]
 
 
+class SessionConfig(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("max_step_tuples", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("warmup_batches", ctypes.c_int32), ("stats_window", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("max_in_flight", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class StepQuery(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_pass", ctypes.c_int64), ("batch", ctypes.c_int64),
+                ("warmup", ctypes.c_int32), ("order", ctypes.c_int32 * MAX_PREDICATES),
+                ("evaluated", ctypes.c_int64 * MAX_PREDICATES), ("passed", ctypes.c_int64 * MAX_PREDICATES),
+                ("recheck_fp32", ctypes.c_int64 * MAX_PREDICATES),
+                ("recheck_fp64", ctypes.c_int64 * MAX_PREDICATES)]
+
+
+class TileChoice(ctypes.Structure):
+    _fields_ = [("udf", ctypes.c_int32), ("layer", ctypes.c_int32), ("K", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("tile_n", ctypes.c_int32), ("us", ctypes.c_double * 3)]
+
+
 class KernelProfile(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
@@ -115,10 +142,24 @@ def load():
     L.hydro_mlp_scores_noalloc.argtypes = [vp, i64, i32, P(i32), P(vp), P(vp), vp, vp]
     L.hydro_selftest_bounded_wait.argtypes = [i32, i64]
     L.hydro_destroy_query.argtypes = [vp]
+    L.hydro_session_default_config.argtypes = [P(SessionConfig)]
+    L.hydro_session_create.argtypes = [P(SessionConfig), P(vp)]
+    L.hydro_session_add_udf.argtypes = [vp, P(UdfDesc), P(i32)]
+    L.hydro_session_add_query.argtypes = [vp, i32, P(i32), P(f64), P(i32)]
+    L.hydro_session_set_margins.argtypes = [vp, i32, f64, f64]
+    L.hydro_session_calibrate.argtypes = [vp, vp, i64, P(CalibInfo)]
+    L.hydro_session_udf_scores.argtypes = [vp, i32, i32, vp, i64, vp]
+    L.hydro_session_submit.argtypes = [vp, vp, P(i32), P(i64)]
+    L.hydro_session_poll.argtypes = [vp, i64, P(ctypes.c_uint32), P(StepQuery), P(f64), i32]
+    L.hydro_session_tuning.argtypes = [vp, P(TileChoice), i32, P(i32)]
+    L.hydro_session_destroy.argtypes = [vp]
+    L.hydro_session_profile.argtypes = [vp, i32]
+    L.hydro_session_profile_read.argtypes = [vp, P(KernelProfile), i32, P(i32), P(i64)]
     L.hydro_last_error.argtypes = []
     L.hydro_last_error.restype = ctypes.c_char_p
     for name in EXPORTED[1:-1]:
         getattr(L, name).restype = ctypes.c_int
+    L.hydro_session_default_config.restype = None
     _lib = L
     return L
 
@@ -359,3 +400,128 @@ def bits_from_words(words: np.ndarray, n: int) -> np.ndarray:
 
 
 
+
+
+class Session:
+    """Many concurrent queries over one pool of MLP UDFs (``hydro_session_*``).
+
+    Each step stacks every query's next chunk of fp32 rows; ``submit`` takes
+    the stacked device tensor and the per-query counts, ``poll`` returns the
+    pass bitmap words, a per-query report and the step's GPU time."""
+
+    def __init__(self, *, dim: int, max_step_tuples: int, precision: str = "fp32", warmup: int = 1,
+                 window: int = 8, graphs: bool = True, autotune: bool = True, max_in_flight: int = 2,
+                 device: int = 0, stream=None):
+        L = load()
+        cfg = SessionConfig()
+        L.hydro_session_default_config(ctypes.byref(cfg))
+        cfg.dim = dim
+        cfg.max_step_tuples = max_step_tuples
+        cfg.precision = PRECISIONS[precision]
+        cfg.warmup_batches = warmup
+        cfg.stats_window = window
+        cfg.use_graphs = 1 if graphs else 0
+        cfg.autotune = 1 if autotune else 0
+        cfg.max_in_flight = max_in_flight
+        cfg.device = device
+        cfg.stream = stream.cuda_stream if stream is not None else None
+        self._h = ctypes.c_void_p()
+        _check(L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(self._h)), "hydro_session_create")
+        self.n_udf = 0
+        self.queries = []
+
+    def add_udf(self, layers) -> int:
+        """Pool MLP from [(W [out, in], b [out]), ...]; returns its id."""
+        FP = ctypes.POINTER(ctypes.c_float)
+        Ws = [np.ascontiguousarray(w, np.float32) for w, _ in layers]
+        bs = [np.ascontiguousarray(b, np.float32) for _, b in layers]
+        dims = [Ws[0].shape[1]] + [w.shape[0] for w in Ws]
+        d = (ctypes.c_int32 * len(dims))(*dims)
+        desc = UdfDesc()
+        desc.kind = UDF_MLP
+        desc.n_layers = len(Ws)
+        desc.dims = d
+        desc.weights = (FP * len(Ws))(*[w.ctypes.data_as(FP) for w in Ws])
+        desc.biases = (FP * len(bs))(*[b.ctypes.data_as(FP) for b in bs])
+        out = ctypes.c_int32()
+        _check(load().hydro_session_add_udf(self._h, ctypes.byref(desc), ctypes.byref(out)), "hydro_session_add_udf")
+        self.n_udf += 1
+        return out.value
+
+    def add_query(self, udfs, thresholds) -> int:
+        n = len(udfs)
+        u = (ctypes.c_int32 * n)(*udfs)
+        t = (ctypes.c_double * n)(*thresholds)
+        out = ctypes.c_int32()
+        _check(load().hydro_session_add_query(self._h, n, u, t, ctypes.byref(out)), "hydro_session_add_query")
+        self.queries.append(list(udfs))
+        return out.value
+
+    def set_margins(self, udf: int, lowp: float, fp32: float):
+        _check(load().hydro_session_set_margins(self._h, udf, lowp, fp32), "hydro_session_set_margins")
+
+    def calibrate(self, tuples) -> list:
+        info = (CalibInfo * MAX_POOL)()
+        _check(load().hydro_session_calibrate(self._h, _ptr(tuples), int(tuples.shape[0]), info),
+               "hydro_session_calibrate")
+        return [{f: getattr(info[i], f) for f, _ in CalibInfo._fields_} for i in range(self.n_udf)]
+
+    def udf_scores(self, udf: int, precision: str, tuples, out):
+        _check(load().hydro_session_udf_scores(self._h, udf, PRECISIONS[precision], _ptr(tuples),
+                                               int(tuples.shape[0]), _ptr(out)), "hydro_session_udf_scores")
+
+    def submit(self, tuples, counts) -> int:
+        Q = len(self.queries)
+        c = (ctypes.c_int32 * Q)(*[int(v) for v in counts])
+        sid = ctypes.c_int64()
+        _check(load().hydro_session_submit(self._h, _ptr(tuples), c, ctypes.byref(sid)), "hydro_session_submit")
+        self._last_total = int(sum(int(v) for v in counts))
+        return sid.value
+
+    def poll(self, step: int, total: int | None = None, wait_ms: int = -1):
+        """(bitmap words uint32, [per-query dict], device_ms)."""
+        Q = len(self.queries)
+        total = self._last_total if total is None else total
+        words = np.zeros(max(1, (total + 31) // 32), np.uint32)
+        per = (StepQuery * max(Q, 1))()
+        ms = ctypes.c_double()
+        _check(load().hydro_session_poll(self._h, step, words.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), per,
+                                         ctypes.byref(ms), wait_ms), "hydro_session_poll")
+        out = []
+        for q in range(Q):
+            r = per[q]
+            P = len(self.queries[q])
+            out.append(dict(n=r.n, n_pass=r.n_pass, batch=r.batch, warmup=bool(r.warmup), order=list(r.order[:P]),
+                            evaluated=list(r.evaluated[:P]), passed=list(r.passed[:P]),
+                            recheck_fp32=list(r.recheck_fp32[:P]), recheck_fp64=list(r.recheck_fp64[:P])))
+        return words, out, ms.value
+
+    def profile(self, enable: bool = True):
+        _check(load().hydro_session_profile(self._h, 1 if enable else 0), "hydro_session_profile")
+
+    def profile_read(self):
+        """({kernel class: dict(launches, total_ms)}, total launches)."""
+        out = (KernelProfile * 16)()
+        n = ctypes.c_int32()
+        tot = ctypes.c_int64()
+        _check(load().hydro_session_profile_read(self._h, out, 16, ctypes.byref(n), ctypes.byref(tot)),
+               "hydro_session_profile_read")
+        return {out[i].name.decode(): dict(launches=out[i].launches, total_ms=out[i].total_ms)
+                for i in range(n.value)}, tot.value
+
+    def tuning(self) -> list:
+        out = (TileChoice * 64)()
+        n = ctypes.c_int32()
+        _check(load().hydro_session_tuning(self._h, out, 64, ctypes.byref(n)), "hydro_session_tuning")
+        return [dict(udf=o.udf, layer=o.layer, K=o.K, N=o.N, tile_n=o.tile_n, us=list(o.us)) for o in out[:n.value]]
+
+    def close(self):
+        if self._h:
+            h, self._h = self._h, ctypes.c_void_p()
+            _check(load().hydro_session_destroy(h), "hydro_session_destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -164,7 +164,7 @@ struct hydro_query {
     int ph = 64;
     float *pW1 = nullptr, *pb1 = nullptr, *pW2 = nullptr, *pb2 = nullptr;
     float *pg = nullptr, *pm = nullptr, *pv = nullptr;   // gradients and Adam moments, same layout as params
-    float *pH = nullptr, *pZ = nullptr, *pdZ = nullptr, *pdH = nullptr, *pinv = nullptr;
+    float *pH = nullptr, *pZ = nullptr, *pdZ = nullptr, *pdH = nullptr, *pinv = nullptr, *ppart = nullptr;
     float *ringX = nullptr;
     unsigned char *ringL = nullptr, *ringM = nullptr;
     std::vector<int> ring_n;
@@ -328,6 +328,7 @@ hydro_status finalize_learned(hydro_query *q) {
     TRY(dalloc(q, &q->pZ, sizeof(float) * (size_t)B * kMaxPred));
     TRY(dalloc(q, &q->pdZ, sizeof(float) * (size_t)B * kMaxPred));
     TRY(dalloc(q, &q->pdH, sizeof(float) * (size_t)B * H));
+    TRY(dalloc(q, &q->ppart, sizeof(float) * proxy_grad_part_floats(B, D, H, P)));
     TRY(dalloc(q, &q->pinv, sizeof(float)));
     const int R = std::max(1, c.proxy_refresh);
     TRY(dalloc(q, &q->ringX, sizeof(float) * (size_t)R * B * D));
@@ -793,11 +794,14 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
             b32_m = q->band2_m;
             b32_t = q->band2_t;
         }
-        if (!cnn) {
+        if (!cnn && p.upstream) {
             const int e = prof_begin(q, &pc_r32, PC_BAND32, (double)p.cost, 4.0 * c.dim, 0);
             launch_mlp_band_f32(b32_count, b32_t, (const float *)tuples, c.dim, p.mlp, q->rscore32, q->sms, q->st);
             prof_end(q, e);
             q->launches++;
+        } else if (!cnn) {
+            // the band as a (short) GEMM: weight tiles shared by the band's rows
+            TRY(run_udf(q, p, PREC_F32, b32_count, b32_t, tuples, q->cap1, q->act, q->rscore32, nullptr, &pc_r32));
         } else {
             TRY(run_udf(q, p, PREC_F32, b32_count, b32_t, tuples, tf32_level ? q->cap2 : q->cap1, q->ract32,
                         q->rscore32, nullptr, &pc_r32));
@@ -972,6 +976,7 @@ hydro_status train_proxy(hydro_query *q) {
             pt.Z = q->pZ;
             pt.dZ = q->pdZ;
             pt.dH = q->pdH;
+            pt.part = q->ppart;
             pt.inv_pairs = q->pinv;
             pt.label = q->ringL + s * (size_t)B;
             pt.mask = q->ringM + s * (size_t)B;

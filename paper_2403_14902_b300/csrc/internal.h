@@ -119,11 +119,18 @@ struct ProxyTrain {
     const float *Hact;         // [M][H] hidden activations (forward)
     const float *Z;            // [M][P] logits (forward)
     float *dZ, *dH, *inv_pairs;
+    float *part;               // per-chunk gradient partials, proxy_grad_part_floats(M, D, H, P)
     const unsigned char *label, *mask;   // per tuple: pass bits / evaluated bits
     float *W1, *b1, *W2, *b2;
     float *gW1, *gb1, *gW2, *gb2;
     float *mW1, *vW1, *mb1, *vb1, *mW2, *vW2, *mb2, *vb2;
 };
+// Floats of the per-chunk gradient partials of one training step over M rows.
+inline size_t proxy_grad_part_floats(int M, int D, int H, int P) {
+    const size_t chunks = (size_t)(M + 255) / 256;
+    const size_t a = (size_t)H * D + H, b = (size_t)P * H + P;
+    return chunks * (a > b ? a : b);
+}
 void launch_tuple_order(int n, int P, const float *logits, int ldz, const RouterCosts &costs, const int *fallback,
                         unsigned char *order, int sms, cudaStream_t st);
 void launch_partition(const int *count, const int *alive, const unsigned char *order, int r, int P, int *queues,

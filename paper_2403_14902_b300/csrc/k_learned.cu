@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "simt_tile.cuh"
 
 namespace hydro {
 
@@ -108,54 +109,6 @@ k_partition(const int *count, const int *alive, const unsigned char *order, int 
 
 // ------------------------------------------------------------ grouped layers
 
-// One tile of Y = act(X[rows] W^T + b): 64x64 outputs, K in slices of 16.
-__device__ __forceinline__ void mlp_tile_f32(int M, int m0, int n0, const int *rows, const float *X, int ldx,
-                                             const float *W, const float *b, float *Y, int K, int N, int relu,
-                                             float (&As)[16][68], float (&Ws)[16][68]) {
-    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-    const int lr = t >> 2, lk = (t & 3) * 4;
-    float acc[4][4] = {};
-    const int am = m0 + lr;
-    const float *arow = am < M ? X + (size_t)(rows ? rows[am] : am) * ldx : nullptr;
-    const int wn = n0 + lr;
-    const float *wrow = wn < N ? W + (size_t)wn * K : nullptr;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int k = k0 + lk + e;
-            As[lk + e][lr] = (arow && k < K) ? arow[k] : 0.f;
-            Ws[lk + e][lr] = (wrow && k < K) ? wrow[k] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float a[4], w[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) w[j] = Ws[kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int m = m0 + ty * 4 + i;
-        if (m >= M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int n = n0 + tx * 4 + j;
-            if (n >= N) continue;
-            float v = acc[i][j] + (b ? b[n] : 0.f);
-            if (relu && v < 0.f) v = 0.f;
-            Y[(size_t)m * N + n] = v;
-        }
-    }
-}
-
 // All groups' hidden layers of one depth in one launch: tiles are numbered
 // group by group and walked grid-stride, so uneven queues share the SMs.
 __global__ void __launch_bounds__(256) k_grouped_layer_f32(GroupedLayers g) {
@@ -174,8 +127,8 @@ __global__ void __launch_bounds__(256) k_grouped_layer_f32(GroupedLayers g) {
         const GroupLayer &L = g.l[i];
         const int local = tile - start[i];
         const int tn = (L.N + 63) / 64;
-        mlp_tile_f32(*L.count, (local / tn) * 64, (local % tn) * 64, L.rows, L.X, L.ldx, L.W, L.b, L.Y, L.K, L.N,
-                     L.relu, As, Ws);
+        mlp_tile_f32(*L.count, (local / tn) * 64, (local % tn) * 64, L.rows, L.X, L.ldx, L.W, L.b, L.Y, L.N, L.K,
+                     L.N, L.relu, As, Ws);
     }
 }
 
@@ -356,23 +309,68 @@ __global__ void k_inv_pairs(int M, const unsigned char *mask, float *inv_pairs) 
     if (threadIdx.x == 0) *inv_pairs = tot > 0 ? 1.f / (float)tot : 0.f;
 }
 
-// G[a][b] = sum_m A[m][a] * B[m][b] (A [M x NA], B [M x NB]) and, when gb is
-// given, gb[a] = sum_m A[m][a]: weight and bias gradients, fixed summation
-// order (deterministic).  One thread per output.
-__global__ void k_grad_outer(int M, int NA, int NB, const float *A, const float *B, float *G, float *gb) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < NA * NB) {
-        const int a = idx / NB, b = idx % NB;
-        float s = 0.f;
-        for (int m = 0; m < M; ++m) s = fmaf(A[(size_t)m * NA + a], B[(size_t)m * NB + b], s);
-        G[idx] = s;
+// Weight and bias gradients G[a][b] = sum_m A[m][a] * B[m][b] and
+// gb[a] = sum_m A[m][a] (A [M x NA], B [M x NB]) in two deterministic steps.
+// Step 1, one CTA per 64x64 output tile and chunk of kGChunk rows:
+// Gp[c][a][b] and gbp[c][a] over the rows of chunk c (16-row slices staged in
+// shared memory, 4x4 outputs per thread).  Step 2 sums the chunks in order.
+constexpr int kGChunk = 256;
+
+__global__ void __launch_bounds__(256)
+k_grad_outer_part(int M, int NA, int NB, const float *__restrict__ A, const float *__restrict__ B, float *Gp,
+                  float *gbp) {
+    __shared__ __align__(16) float As[16][64];
+    __shared__ __align__(16) float Bs[16][64];
+    const int a0 = blockIdx.y * 64, b0 = blockIdx.x * 64, c = blockIdx.z;
+    const int m0 = c * kGChunk, m1 = min(M, m0 + kGChunk);
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    float acc[4][4] = {};
+    float colsum = 0.f;
+    for (int k0 = m0; k0 < m1; k0 += 16) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = t + e * 256, r = idx >> 6, col = idx & 63, m = k0 + r;
+            As[r][col] = (m < m1 && a0 + col < NA) ? A[(size_t)m * NA + a0 + col] : 0.f;
+            Bs[r][col] = (m < m1 && b0 + col < NB) ? B[(size_t)m * NB + b0 + col] : 0.f;
+        }
+        __syncthreads();
+        if (gbp && blockIdx.x == 0 && t < 64)
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) colsum += As[kk][t];
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const float4 a = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
     }
-    if (gb && idx < NA) {
+    float *G = Gp + (size_t)c * NA * NB;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int a = a0 + ty * 4 + i;
+        if (a >= NA) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int b = b0 + tx * 4 + j;
+            if (b < NB) G[(size_t)a * NB + b] = acc[i][j];
+        }
+    }
+    if (gbp && blockIdx.x == 0 && t < 64 && a0 + t < NA) gbp[(size_t)c * NA + a0 + t] = colsum;
+}
+
+__global__ void k_sum_chunks(int chunks, int n, const float *__restrict__ part, float *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float s = 0.f;
-        for (int m = 0; m < M; ++m) s += A[(size_t)m * NA + idx];
-        gb[idx] = s;
+        for (int c = 0; c < chunks; ++c) s += part[(size_t)c * n + i];
+        out[i] = s;
     }
 }
+
 
 // dH[m][j] = (H[m][j] > 0) * sum_p dZ[m][p] * W2[p][j]
 __global__ void k_grad_hidden(int M, int P, int Hd, const float *dZ, const float *W2, const float *H, float *dH) {
@@ -465,14 +463,23 @@ void launch_full_label_acc(const unsigned char *label, int n, int P, unsigned ch
     k_full_label_acc<<<lgrid(n, 256, 148, 4), 256, 0, st>>>(label, n, P, acc);
 }
 
+void grad_outer(int M, int NA, int NB, const float *A, const float *B, float *G, float *gb, float *part,
+                int sms, cudaStream_t st) {
+    const int chunks = (M + kGChunk - 1) / kGChunk;
+    float *gbp = part + (size_t)chunks * NA * NB;
+    k_grad_outer_part<<<dim3((NB + 63) / 64, (NA + 63) / 64, chunks), 256, 0, st>>>(M, NA, NB, A, B, part, gbp);
+    k_sum_chunks<<<lgrid((long long)NA * NB, 256, sms, 4), 256, 0, st>>>(chunks, NA * NB, part, G);
+    k_sum_chunks<<<1, 256, 0, st>>>(chunks, NA, gbp, gb);
+}
+
 void launch_proxy_train_step(const ProxyTrain &pt, cudaStream_t st) {
     const int M = pt.M, P = pt.P, Hd = pt.H, D = pt.D;
     k_inv_pairs<<<1, 256, 0, st>>>(M, pt.mask, pt.inv_pairs);
     k_bce_grad<<<lgrid((long long)M * P, 256, pt.sms, 8), 256, 0, st>>>(M, P, pt.Z, pt.label, pt.mask, pt.inv_pairs,
                                                                        pt.dZ);
-    k_grad_outer<<<(P * Hd + 255) / 256, 256, 0, st>>>(M, P, Hd, pt.dZ, pt.Hact, pt.gW2, pt.gb2);
+    grad_outer(M, P, Hd, pt.dZ, pt.Hact, pt.gW2, pt.gb2, pt.part, pt.sms, st);
     k_grad_hidden<<<lgrid((long long)M * Hd, 256, pt.sms, 8), 256, 0, st>>>(M, P, Hd, pt.dZ, pt.W2, pt.Hact, pt.dH);
-    k_grad_outer<<<(Hd * D + 255) / 256, 256, 0, st>>>(M, Hd, D, pt.dH, pt.X, pt.gW1, pt.gb1);
+    grad_outer(M, Hd, D, pt.dH, pt.X, pt.gW1, pt.gb1, pt.part, pt.sms, st);
     k_adam<<<lgrid(Hd * D, 256, pt.sms, 4), 256, 0, st>>>(Hd * D, pt.W1, pt.gW1, pt.mW1, pt.vW1, pt.lr, pt.t);
     k_adam<<<1, 256, 0, st>>>(Hd, pt.b1, pt.gb1, pt.mb1, pt.vb1, pt.lr, pt.t);
     k_adam<<<lgrid(P * Hd, 256, pt.sms, 4), 256, 0, st>>>(P * Hd, pt.W2, pt.gW2, pt.mW2, pt.vW2, pt.lr, pt.t);

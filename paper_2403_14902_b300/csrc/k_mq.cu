@@ -1,0 +1,496 @@
+// Kernels of multi-query session steps (rounds of grouped launches).
+//
+// A step stacks every query's chunk; round r sends each surviving tuple to
+// the pool UDF of the r-th slot of its query's order (Sec. 4.1 rank order per
+// query, Sec. 3.3 eager dropping), evaluates all groups per layer depth in one
+// persistent launch (Sec. 5.1 "Batch-agnostic Parallelization": many workers'
+// work on one GPU at once), tests the scores against each tuple's own query
+// threshold, rechecks the band around it at higher precision, and keeps the
+// survivors.  Queue and list order is by atomics: every verdict and count is
+// per tuple, so the results do not depend on it.
+#include <math.h>
+
+#include "mq.h"
+#include "simt_tile.cuh"
+
+namespace hydro {
+
+namespace {
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Append `want` lanes' items to a list whose length is *counter: one atomic
+// per distinct counter among the warp's active lanes.  Returns each wanting
+// lane's position.
+__device__ __forceinline__ int warp_append(int *counter, bool want) {
+    const unsigned active = __activemask();
+    const unsigned mask = __ballot_sync(active, want);
+    if (!want) return -1;
+    const unsigned peers = __match_any_sync(mask, reinterpret_cast<uintptr_t>(counter));
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane_id() == leader) base = atomicAdd(counter, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + __popc(peers & ((1u << lane_id()) - 1u));
+}
+
+// Add 1 to *p for every active lane that passes want: one atomic per
+// distinct address.
+__device__ __forceinline__ void warp_count(unsigned long long *p, bool want) {
+    const unsigned active = __activemask();
+    const unsigned mask = __ballot_sync(active, want);
+    if (!want) return;
+    const unsigned peers = __match_any_sync(mask, reinterpret_cast<uintptr_t>(p));
+    if (lane_id() == __ffs(peers) - 1) atomicAdd(p, (unsigned long long)__popc(peers));
+}
+
+__device__ __forceinline__ unsigned long long *ctr(StatRow *r, int field) {
+    return reinterpret_cast<unsigned long long *>(r) + field;
+}
+enum { F_EVAL = 0, F_PASS = 1, F_R32 = 3, F_R64 = 4 };
+
+int grid_for(long long work, int per_block, int sms, int per_sm) {
+    long long g = (work + per_block - 1) / per_block;
+    const long long cap = (long long)sms * per_sm;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+// ------------------------------------------------------------ step setup
+
+// Offsets of the step, query of every tuple, first alive list (every tuple),
+// cleared per-tuple flags, statistics and round counters.
+__global__ void __launch_bounds__(256) k_mq_init(MqDev d) {
+    __shared__ int s_off[kMqMaxQ + 1];
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int q = 0; q < d.Q; ++q) {
+            s_off[q] = o;
+            o += d.hdr->counts[q];
+        }
+        s_off[d.Q] = o;
+    }
+    __syncthreads();
+    const int n = min(s_off[d.Q], d.cap);
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i <= d.Q; i += blockDim.x) d.off[i] = s_off[i];
+        for (int i = threadIdx.x; i < d.Q * kMqSlots; i += blockDim.x) d.rows[i] = StatRow{};
+        for (int i = threadIdx.x; i < d.Q; i += blockDim.x) d.npass[i] = 0;
+        if (threadIdx.x == 0) {
+            if (s_off[d.Q] > d.cap) atomicOr(d.err, ERR_COUNT_RANGE);
+            RoundCounters z{};
+            z.alive[0] = n;
+            *d.rc = z;
+        }
+    }
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        int lo = 0, hi = d.Q - 1;   // last q with s_off[q] <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        d.qid[e] = (unsigned char)lo;
+        d.alive[0][e] = e;
+        d.visited[e] = 0;
+        d.label[e] = 0;
+        d.ok[e] = 0;
+    }
+}
+
+// Per query (one warp each): its batch number, warmup flag and slot order
+// for the step from its own statistics of the batches before (lag 0): the
+// window [b - W, b - 1], falling back to the warmup batches for a slot not
+// evaluated in the window; rank c (e + 2) / (e - p + 1) compared exactly in
+// 128-bit integers, ties to the lower slot.
+__global__ void k_mq_router(MqDev d, MqHist h) {
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int i = lane_id();
+    if (q >= d.Q) return;
+    const int count = d.hdr->counts[q];
+    const int P = d.np[q];
+    if (count <= 0) {
+        if (i == 0) {
+            d.bidx[q] = -1;
+            d.evall[q] = 0;
+        }
+        if (i < kMqSlots) d.order[q * kMqSlots + i] = (unsigned char)i;
+        return;
+    }
+    const long long b = h.bdone[q];
+    if (i == 0) d.bidx[q] = b;
+    if (b < h.warmup || b == 0) {
+        if (i == 0) d.evall[q] = b < h.warmup ? 1 : 0;
+        if (i < kMqSlots) d.order[q * kMqSlots + i] = (unsigned char)i;
+        return;
+    }
+    if (i == 0) d.evall[q] = 0;
+    const long long last = b - 1;
+    const long long lo = last - h.window + 1 > 0 ? last - h.window + 1 : 0;
+    long long E = 0, Pp = 0;
+    unsigned long long c = 0;
+    if (i < P) {
+        c = (unsigned long long)d.cost[q * kMqSlots + i];
+        for (long long bb = lo; bb <= last; ++bb) {
+            const StatRow &r = h.ring[((size_t)q * h.R + (size_t)(bb % h.R)) * kMqSlots + i];
+            E += r.evaluated;
+            Pp += r.passed;
+        }
+        if (E == 0) {
+            const int nw = (int)(h.warmup < last + 1 ? h.warmup : last + 1);
+            for (int w = 0; w < nw; ++w) {
+                const StatRow &r = h.warm[((size_t)q * h.warmup + w) * kMqSlots + i];
+                E += r.evaluated;
+                Pp += r.passed;
+            }
+        }
+    }
+    int pos = 0;
+    for (int j = 0; j < P; ++j) {
+        const long long Ej = __shfl_sync(0xffffffffu, E, j);
+        const long long Pj = __shfl_sync(0xffffffffu, Pp, j);
+        const unsigned long long cj = __shfl_sync(0xffffffffu, c, j);
+        if (i >= P || j == i) continue;
+        const unsigned __int128 lhs = (unsigned __int128)cj * (unsigned long long)(Ej + 2) * (unsigned long long)(E - Pp + 1);
+        const unsigned __int128 rhs = (unsigned __int128)c * (unsigned long long)(E + 2) * (unsigned long long)(Ej - Pj + 1);
+        pos += (lhs < rhs || (lhs == rhs && j < i)) ? 1 : 0;
+    }
+    if (i < P) d.order[q * kMqSlots + pos] = (unsigned char)i;
+}
+
+// ------------------------------------------------------------ rounds
+
+// Round r: every alive tuple joins the queue of the pool UDF of its query's
+// r-th slot.  Also clears the next alive list's length.
+__global__ void __launch_bounds__(256) k_mq_partition(MqDev d, int r) {
+    const int cur = r & 1;
+    const int n = d.rc->alive[cur];
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.rc->alive[cur ^ 1] = 0;
+    for (int m0 = blockIdx.x * blockDim.x; m0 < n; m0 += gridDim.x * blockDim.x) {
+        const int m = m0 + threadIdx.x;
+        int e = 0, g = 0;
+        const bool live = m < n;
+        if (live) {
+            e = d.alive[cur][m];
+            const int q = d.qid[e];
+            const int slot = d.order[q * kMqSlots + r];
+            g = d.udf[q * kMqSlots + slot];
+        }
+        const int pos = warp_append(live ? &d.rc->q[g] : nullptr, live);
+        if (live) d.queues[(size_t)g * d.cap + pos] = e;
+    }
+}
+
+// Stacked grouped FP32 layer: tiles group by group, rows of group g at
+// off_g; depth 0 reads X rows through the queue lists.
+__global__ void __launch_bounds__(256) k_mq_layer_f32(MqLayers L) {
+    __shared__ float As[16][68];
+    __shared__ float Ws[16][68];
+    int off[kMqPool + 1], start[kMqPool + 1];
+    off[0] = 0;
+    start[0] = 0;
+    for (int g = 0; g < L.n; ++g) {
+        const int c = L.counts[g];
+        off[g + 1] = off[g] + c;
+        start[g + 1] = start[g] + (L.l[g].W ? ((c + 63) / 64) * ((L.l[g].N + 63) / 64) : 0);
+    }
+    const float *X = L.hdr->X;
+    for (int tile = blockIdx.x; tile < start[L.n]; tile += gridDim.x) {
+        int g = 0;
+        while (tile >= start[g + 1]) ++g;
+        const MqLayer &l = L.l[g];
+        const int local = tile - start[g], tn = (l.N + 63) / 64;
+        const int *rows = L.rows ? L.rows + (size_t)g * L.cap : nullptr;
+        const float *in = rows ? X : l.in + (size_t)off[g] * l.ldin;
+        mlp_tile_f32(L.counts[g], (local / tn) * 64, (local % tn) * 64, rows, in, rows ? L.ldx : l.ldin, l.W, l.b,
+                     L.Y + (size_t)off[g] * L.ldy, L.ldy, l.K, l.N, 1, As, Ws);
+    }
+}
+
+// Stacked grouped one-output last layer: a warp per row; score[g*sstride + m].
+__global__ void __launch_bounds__(256) k_mq_dot_f32(MqLayers L, float *score, int sstride) {
+    int off[kMqPool + 1];
+    off[0] = 0;
+    for (int g = 0; g < L.n; ++g) off[g + 1] = off[g] + L.counts[g];
+    const float *X = L.hdr->X;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < off[L.n]; w += (gridDim.x * blockDim.x) >> 5) {
+        int g = 0;
+        while (w >= off[g + 1]) ++g;
+        const MqLayer &l = L.l[g];
+        if (!l.W) continue;
+        const int m = w - off[g];
+        const float *x = L.rows ? X + (size_t)L.rows[(size_t)g * L.cap + m] * L.ldx : l.in + (size_t)w * l.ldin;
+        float s = 0.f;
+        for (int k = lane_id(); k < l.K; k += 32) s = fmaf(x[k], l.W[k], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane_id() == 0) score[(size_t)g * sstride + m] = s + l.bconst;
+    }
+}
+
+// Decide the entries of a level.  Level 0: the round queues' working-
+// precision scores; a score within the margin of its tuple's threshold goes
+// to the next level's band queue (BF16: the FP32 band, else the FP64 band).
+// Level 1: the FP32 band's scores, margin_fp32, undecided -> FP64 band.
+__global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int level, int bf16) {
+    const int *cnts = level == 0 ? d.rc->q : d.rc->b32;
+    const int *lists = level == 0 ? d.queues : d.bq32;
+    const float *sc = level == 0 ? d.score : d.rscore;
+    const float *margin = (level == 0 && bf16) ? d.margin_lowp : d.margin_fp32;
+    int *next_cnt = (level == 0 && bf16) ? d.rc->b32 : d.rc->b64;
+    int *next_list = (level == 0 && bf16) ? d.bq32 : d.bq64;
+    int off[kMqPool + 1];
+    off[0] = 0;
+    for (int g = 0; g < d.G; ++g) off[g + 1] = off[g] + cnts[g];
+    for (int i0 = blockIdx.x * blockDim.x; i0 < off[d.G]; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const bool live = i < off[d.G];
+        int g = 0, m = 0, e = 0, q = 0, slot = 0;
+        bool inband = false, pass = false;
+        if (live) {
+            while (i >= off[g + 1]) ++g;
+            m = i - off[g];
+            e = lists[(size_t)g * d.cap + m];
+            q = d.qid[e];
+            slot = d.order[q * kMqSlots + r];
+            const double t = d.thr[q * kMqSlots + slot];
+            const double s = (double)sc[(size_t)g * d.cap + m];
+            inband = fabs(s - t) <= (double)margin[g];
+            pass = !inband && s > t;
+            if (level == 0) d.visited[e] |= (unsigned char)(1u << slot);
+            d.ok[e] = (unsigned char)pass;
+            if (pass) d.label[e] |= (unsigned char)(1u << slot);
+        }
+        StatRow *row = d.rows + q * kMqSlots + slot;
+        if (level == 0) warp_count(ctr(row, F_EVAL), live);
+        warp_count(ctr(row, F_PASS), live && pass);
+        const int pos = warp_append(live && inband ? &next_cnt[g] : nullptr, live && inband);
+        if (live && inband) next_list[(size_t)g * d.cap + pos] = e;
+        // entries going on to FP64 are counted by the FP64 recheck
+        if (level == 0 && bf16) warp_count(ctr(row, F_R32), live && inband);
+    }
+}
+
+// FP64 recheck of the FP64 band: a block per entry runs its UDF in FP64 from
+// the tuple and decides the test exactly (no margin).
+__global__ void __launch_bounds__(256) k_mq_band64(MqDev d, int r, GroupedMlps mlps) {
+    extern __shared__ unsigned char smem_raw[];
+    double *h = reinterpret_cast<double *>(smem_raw);
+    double *g2 = h + mlps.max_width;
+    int off[kMqPool + 1];
+    off[0] = 0;
+    for (int g = 0; g < d.G; ++g) off[g + 1] = off[g] + d.rc->b64[g];
+    const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const float *X = d.hdr->X;
+    for (int j = blockIdx.x; j < off[d.G]; j += gridDim.x) {
+        int g = 0;
+        while (j >= off[g + 1]) ++g;
+        const int e = d.bq64[(size_t)g * d.cap + (j - off[g])];
+        const MlpDev &mlp = mlps.m[g];
+        const float *x = X + (size_t)e * d.dim;
+        for (int k = threadIdx.x; k < mlp.dims[0]; k += blockDim.x) h[k] = (double)x[k];
+        __syncthreads();
+        double *cur = h, *nxt = g2;
+        for (int l = 0; l < mlp.n_layers; ++l) {
+            const int fi = mlp.dims[l], fo = mlp.dims[l + 1];
+            const bool last = l + 1 == mlp.n_layers;
+            for (int o = warp; o < fo; o += nwarps) {
+                const float *wr = mlp.W[l] + (size_t)o * fi;
+                double s = 0;
+                for (int k = lane; k < fi; k += 32) s += (double)wr[k] * cur[k];
+#pragma unroll
+                for (int dd = 16; dd > 0; dd >>= 1) s += __shfl_xor_sync(0xffffffffu, s, dd);
+                if (lane == 0) {
+                    s += (double)mlp.b[l][o];
+                    nxt[o] = (!last && s < 0.0) ? 0.0 : s;
+                }
+            }
+            __syncthreads();
+            double *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+        if (threadIdx.x == 0) {
+            const int q = d.qid[e];
+            const int slot = d.order[q * kMqSlots + r];
+            const bool pass = cur[0] > d.thr[q * kMqSlots + slot];
+            d.ok[e] = (unsigned char)pass;
+            StatRow *row = d.rows + q * kMqSlots + slot;
+            if (pass) {
+                d.label[e] |= (unsigned char)(1u << slot);
+                atomicAdd(ctr(row, F_PASS), 1ull);
+            }
+            atomicAdd(ctr(row, F_R64), 1ull);
+        }
+        __syncthreads();
+    }
+}
+
+// Next alive list: tuples that passed (or whose query is in a warmup batch)
+// and have a slot left.  Clears the round's queue and band counters.
+__global__ void __launch_bounds__(256) k_mq_survivors(MqDev d, int r) {
+    const int cur = r & 1;
+    const int n = d.rc->alive[cur];
+    for (int m0 = blockIdx.x * blockDim.x; m0 < n; m0 += gridDim.x * blockDim.x) {
+        const int m = m0 + threadIdx.x;
+        bool keep = false;
+        int e = 0;
+        if (m < n) {
+            e = d.alive[cur][m];
+            const int q = d.qid[e];
+            keep = (d.ok[e] || d.evall[q]) && r + 1 < d.np[q];
+        }
+        const int pos = warp_append(keep ? &d.rc->alive[cur ^ 1] : nullptr, keep);
+        if (keep) d.alive[cur ^ 1][pos] = e;
+    }
+}
+
+__global__ void k_mq_clear_round(RoundCounters *rc) {
+    const int i = threadIdx.x;
+    if (i < kMqPool) {
+        rc->q[i] = 0;
+        rc->b32[i] = 0;
+        rc->b64[i] = 0;
+    }
+}
+
+// Result bitmap (bit e: every slot of e's query passed) and passes per query.
+__global__ void __launch_bounds__(256) k_mq_result(MqDev d, unsigned int *bitmap) {
+    const int n = min(d.off[d.Q], d.cap);
+    const int words = (n + 31) / 32;
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < words; w += gridDim.x * blockDim.x) {
+        unsigned int bits = 0;
+        for (int j = 0; j < 32; ++j) {
+            const int e = w * 32 + j;
+            if (e >= n) break;
+            const int q = d.qid[e];
+            const unsigned full = (1u << d.np[q]) - 1u;
+            if (((unsigned)d.label[e] & full) == full) {
+                bits |= 1u << j;
+                atomicAdd(reinterpret_cast<unsigned long long *>(&d.npass[q]), 1ull);
+            }
+        }
+        bitmap[w] = bits;
+    }
+}
+
+// Statistics of the step into each query's history, and the step's
+// per-query report into the result slot.
+__global__ void k_mq_commit(MqDev d, MqHist h, StatRow *res_rows, unsigned char *res_order, unsigned char *res_evall,
+                            long long *res_bidx, long long *res_npass, int *res_total) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *res_total = d.off[d.Q];
+    if (i >= d.Q * kMqSlots) return;
+    const int q = i / kMqSlots, slot = i % kMqSlots;
+    const long long b = d.bidx[q];
+    const StatRow row = d.rows[i];
+    res_rows[i] = row;
+    res_order[i] = d.order[i];
+    if (slot == 0) {
+        res_evall[q] = d.evall[q];
+        res_bidx[q] = b;
+        res_npass[q] = d.npass[q];
+    }
+    if (b < 0) return;
+    h.ring[((size_t)q * h.R + (size_t)(b % h.R)) * kMqSlots + slot] = row;
+    if (b < h.warmup) h.warm[((size_t)q * h.warmup + b) * kMqSlots + slot] = row;
+    if (slot == 0) h.bdone[q] = b + 1;
+}
+
+// FP64 scores of one MLP on n rows (calibration).
+__global__ void __launch_bounds__(256) k_mq_scores_f64(MlpDev mlp, int max_width, const float *X, int ldx, int n,
+                                                       double *out) {
+    extern __shared__ unsigned char smem_raw[];
+    double *h = reinterpret_cast<double *>(smem_raw);
+    double *g2 = h + max_width;
+    const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const float *x = X + (size_t)j * ldx;
+        for (int k = threadIdx.x; k < mlp.dims[0]; k += blockDim.x) h[k] = (double)x[k];
+        __syncthreads();
+        double *cur = h, *nxt = g2;
+        for (int l = 0; l < mlp.n_layers; ++l) {
+            const int fi = mlp.dims[l], fo = mlp.dims[l + 1];
+            const bool last = l + 1 == mlp.n_layers;
+            for (int o = warp; o < fo; o += nwarps) {
+                const float *wr = mlp.W[l] + (size_t)o * fi;
+                double s = 0;
+                for (int k = lane; k < fi; k += 32) s += (double)wr[k] * cur[k];
+#pragma unroll
+                for (int dd = 16; dd > 0; dd >>= 1) s += __shfl_xor_sync(0xffffffffu, s, dd);
+                if (lane == 0) {
+                    s += (double)mlp.b[l][o];
+                    nxt[o] = (!last && s < 0.0) ? 0.0 : s;
+                }
+            }
+            __syncthreads();
+            double *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+        if (threadIdx.x == 0) out[j] = cur[0];
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+void mq_launch_init(const MqDev &d, cudaStream_t st, int sms) {
+    k_mq_init<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d);
+}
+
+void mq_launch_router(const MqDev &d, const MqHist &h, cudaStream_t st) {
+    k_mq_router<<<(d.Q * 32 + 255) / 256, 256, 0, st>>>(d, h);
+}
+
+void mq_launch_partition(const MqDev &d, int r, cudaStream_t st, int sms) {
+    if (r > 0) k_mq_clear_round<<<1, 32, 0, st>>>(d.rc);
+    k_mq_partition<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r);
+}
+
+void mq_launch_layers_f32(const MqLayers &L, cudaStream_t st, int sms) {
+    k_mq_layer_f32<<<sms * 4, 256, 0, st>>>(L);
+}
+
+void mq_launch_dots_f32(const MqLayers &L, float *score, int sstride, cudaStream_t st, int sms) {
+    k_mq_dot_f32<<<sms * 8, 256, 0, st>>>(L, score, sstride);
+}
+
+void mq_launch_classify(const MqDev &d, int r, int level, bool bf16, cudaStream_t st, int sms) {
+    k_mq_classify<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r, level, bf16 ? 1 : 0);
+}
+
+void mq_launch_band64(const MqDev &d, int r, const GroupedMlps &mlps, cudaStream_t st, int sms) {
+    const size_t smem = sizeof(double) * 2 * (size_t)mlps.max_width;
+    k_mq_band64<<<sms * 2, 256, smem, st>>>(d, r, mlps);
+}
+
+void mq_launch_survivors(const MqDev &d, int r, cudaStream_t st, int sms) {
+    k_mq_survivors<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r);
+}
+
+void mq_launch_result(const MqDev &d, unsigned int *bitmap, cudaStream_t st, int sms) {
+    k_mq_result<<<grid_for((d.cap + 31) / 32, 256, sms, 4), 256, 0, st>>>(d, bitmap);
+}
+
+void mq_launch_commit(const MqDev &d, const MqHist &h, StatRow *res_rows, unsigned char *res_order,
+                      unsigned char *res_evall, long long *res_bidx, long long *res_npass, int *res_total,
+                      cudaStream_t st) {
+    k_mq_commit<<<(d.Q * kMqSlots + 255) / 256, 256, 0, st>>>(d, h, res_rows, res_order, res_evall, res_bidx,
+                                                              res_npass, res_total);
+}
+
+cudaError_t mq_band_smem_setup(int max_width) {
+    const int smem = (int)(sizeof(double) * 2 * (size_t)max_width);
+    cudaError_t e = cudaFuncSetAttribute(k_mq_band64, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_mq_scores_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+void mq_launch_scores_f64(const MlpDev &mlp, int max_width, const float *X, int ldx, int n, double *out,
+                          cudaStream_t st, int sms) {
+    const size_t smem = sizeof(double) * 2 * (size_t)max_width;
+    k_mq_scores_f64<<<grid_for(n, 1, sms, 4), 256, smem, st>>>(mlp, max_width, X, ldx, n, out);
+}
+
+}  // namespace hydro

@@ -1,0 +1,956 @@
+// Multi-query sessions: many queries over one pool of MLP UDFs, one step at a
+// time, every step a fixed, device-driven launch sequence (replayed from a
+// CUDA graph per in-flight slot).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstddef>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/hydro.h"
+#include "common.cuh"
+#include "internal.h"
+#include "mq.h"
+#include "tc_gemm.h"
+
+using namespace hydro;
+
+namespace {
+
+hydro_status fail(hydro_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    set_last_error(buf);
+    return s;
+}
+
+#define CU(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? HYDRO_ENOMEM : HYDRO_ECUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                       \
+    } while (0)
+
+#define TRY(x)                         \
+    do {                               \
+        hydro_status s_ = (x);         \
+        if (s_ != HYDRO_OK) return s_; \
+    } while (0)
+
+struct Udf {
+    int n_layers = 0;
+    std::vector<int> dims;
+    std::vector<std::vector<float>> W, b;
+    long long cost = 0;
+    double margin_lowp = 0.02, margin_fp32 = 1e-5;
+    std::vector<float *> dW, db;
+    std::vector<__nv_bfloat16 *> dW16;
+    std::vector<int> nt;     // tensor-core tile width per hidden layer (0: widest dividing N)
+    MlpDev mlp{};
+};
+
+struct Query {
+    int P = 0;
+    int udf[kMqSlots] = {};
+    double thr[kMqSlots] = {};
+};
+
+// Kernel classes of the session profile.
+const char *const kSessProf[] = {"gemm_grouped_bf16_tc", "gather_grouped_bf16", "head_finalize_grouped",
+                                 "layer_grouped_f32",    "dot_grouped_f32",     "band_f64",
+                                 "route_partition_classify"};
+enum { SP_GEMM = 0, SP_GATHER, SP_FINAL, SP_LAYER, SP_DOT, SP_BAND64, SP_CTRL, SP_N };
+
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+struct Slot {
+    std::vector<ProfRec> prof;     // this step's timed launches (profiling on)
+    long long launches = 0;
+    bool busy = false;
+    long long step = -1;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    StepHdr *h_hdr = nullptr;      // pinned
+    unsigned int *bitmap = nullptr;
+    StatRow *rows = nullptr;
+    unsigned char *order = nullptr, *evall = nullptr;
+    long long *bidx = nullptr, *npass = nullptr;
+    int *total = nullptr;
+    std::vector<int> counts;
+};
+
+}  // namespace
+
+struct hydro_session {
+    hydro_session_config cfg{};
+    std::vector<Udf> udfs;
+    std::vector<Query> queries;
+    bool finalized = false, dead = false, own_stream = false;
+    int sms = 0, wmax = 0, max_hidden = 0, maxP = 0;
+    cudaStream_t st = nullptr;
+    std::vector<void *> allocs;
+    std::vector<void *> host_allocs;
+    MqDev d{};
+    MqHist h{};
+    StepHdr *d_hdr = nullptr;
+    float *act32[2] = {};
+    __nv_bfloat16 *stage16 = nullptr, *act16[2] = {};
+    float *partials = nullptr;
+    int pstride = 1;
+    void *encode = nullptr;
+    float *d_margin_lowp = nullptr, *d_margin_fp32 = nullptr;
+    GroupedMlps mlps{};
+    std::vector<Slot> slots;
+    long long next_step = 0;
+    std::vector<hydro_tile_choice> tuning;
+    // profiling (hydro_session_profile): per class launches and device ms
+    bool prof_on = false;
+    Slot *prof_slot = nullptr;
+    double prof_ms[SP_N] = {};
+    long long prof_n[SP_N] = {};
+    long long launches = 0;         // kernel launches of polled steps since profiling was (re)started
+    long long step_launches = 0;    // launches of the step being enqueued
+};
+
+namespace {
+
+template <typename T>
+hydro_status dalloc(hydro_session *s, T **p, size_t bytes) {
+    void *v = nullptr;
+    CU(cudaMalloc(&v, bytes < 16 ? 16 : bytes));
+    s->allocs.push_back(v);
+    *p = (T *)v;
+    return HYDRO_OK;
+}
+
+template <typename T>
+hydro_status upload(hydro_session *s, T **dst, const T *src, size_t count) {
+    TRY(dalloc(s, dst, count * sizeof(T)));
+    CU(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+    return HYDRO_OK;
+}
+
+hydro_status check(hydro_session *s) {
+    if (!s) return fail(HYDRO_EINVAL, "NULL session");
+    if (s->dead) return fail(HYDRO_ESTATE, "session is in a failed state");
+    return HYDRO_OK;
+}
+
+bool bf16(const hydro_session *s) { return s->cfg.precision == HYDRO_PREC_BF16; }
+
+// Bracket the launches of one class with events (profiling steps only).
+int prof_begin(hydro_session *s, int cls) {
+    if (!s->prof_slot) return -1;
+    ProfRec r{cls, nullptr, nullptr};
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return -1;
+    cudaEventRecord(r.a, s->st);
+    s->prof_slot->prof.push_back(r);
+    return (int)s->prof_slot->prof.size() - 1;
+}
+void prof_end(hydro_session *s, int i) {
+    if (i >= 0 && s->prof_slot) cudaEventRecord(s->prof_slot->prof[i].b, s->st);
+}
+
+// Device addresses of the round counters' arrays.
+int *rc_q(const MqDev &d) { return reinterpret_cast<int *>(reinterpret_cast<char *>(d.rc) + offsetof(RoundCounters, q)); }
+int *rc_b32(const MqDev &d) {
+    return reinterpret_cast<int *>(reinterpret_cast<char *>(d.rc) + offsetof(RoundCounters, b32));
+}
+
+// Rows of all queues of the round as one stacked operand: the layers of one
+// depth for every group (BF16 on the tensor cores).
+hydro_status eval_tc(hydro_session *s, const int *counts, const int *lists, float *score) {
+    const MqDev &d = s->d;
+    int pe = prof_begin(s, SP_GATHER);
+    launch_gather_grouped_bf16(d.G, counts, lists, d.cap, reinterpret_cast<const float *const *>(s->d_hdr), d.dim,
+                               d.dim, s->stage16, d.cap, s->sms, s->st);
+    prof_end(s, pe);
+    s->step_launches++;
+    TcHeads heads{};
+    for (int dd = 0; dd < s->max_hidden; ++dd) {
+        TcGemmGroup gr[kMaxGroups];
+        for (int g = 0; g < d.G; ++g) {
+            const Udf &u = s->udfs[g];
+            const bool has = dd + 1 < u.n_layers;
+            const bool head = dd + 2 == u.n_layers;
+            gr[g] = TcGemmGroup{counts + g,
+                                dd == 0 ? s->stage16 : s->act16[(dd - 1) % 2],
+                                dd == 0 ? d.dim : s->wmax,
+                                d.cap,
+                                has ? u.dW16[dd] : nullptr,
+                                has ? u.db[dd] : nullptr,
+                                head ? u.dW[u.n_layers - 1] : nullptr,
+                                has ? u.dims[dd] : 0,
+                                has ? u.dims[dd + 1] : 0,
+                                has ? u.nt[dd] : 0};
+            if (head) {
+                heads.b[g] = u.b[u.n_layers - 1][0];
+                heads.tiles[g] = u.nt[dd] ? u.dims[dd + 1] / u.nt[dd] : tc_gemm_col_tiles(u.dims[dd + 1]);
+            }
+        }
+        pe = prof_begin(s, SP_GEMM);
+        hydro_status rs = tc_gemm_grouped_run(s->encode, gr, d.G, s->act16[dd % 2], s->wmax, s->partials, s->pstride,
+                                              s->sms, s->st, d.err);
+        prof_end(s, pe);
+        if (rs != HYDRO_OK) return fail(rs, "grouped tensor-core GEMM: %s", tc_gemm_last_error());
+        s->step_launches++;
+    }
+    pe = prof_begin(s, SP_FINAL);
+    launch_head_finalize_grouped(d.G, counts, heads, s->partials, s->pstride, score, d.cap, d.cap, s->sms, s->st);
+    prof_end(s, pe);
+    s->step_launches++;
+    return HYDRO_OK;
+}
+
+// The same in FP32 on the CUDA cores (hidden layers per depth, then the
+// one-output layer).
+void eval_f32(hydro_session *s, const int *counts, const int *lists, float *score) {
+    const MqDev &d = s->d;
+    for (int dd = 0; dd < s->max_hidden; ++dd) {
+        MqLayers L{};
+        L.n = d.G;
+        L.counts = counts;
+        L.rows = dd == 0 ? lists : nullptr;
+        L.cap = d.cap;
+        L.hdr = s->d_hdr;
+        L.ldx = d.dim;
+        L.Y = s->act32[dd % 2];
+        L.ldy = s->wmax;
+        for (int g = 0; g < d.G; ++g) {
+            const Udf &u = s->udfs[g];
+            if (dd + 1 >= u.n_layers) continue;
+            L.l[g] = MqLayer{u.dW[dd], u.db[dd], 0.f, dd == 0 ? nullptr : s->act32[(dd - 1) % 2], s->wmax,
+                             u.dims[dd], u.dims[dd + 1]};
+        }
+        const int pe = prof_begin(s, SP_LAYER);
+        mq_launch_layers_f32(L, s->st, s->sms);
+        prof_end(s, pe);
+        s->step_launches++;
+    }
+    MqLayers L{};
+    L.n = d.G;
+    L.counts = counts;
+    L.rows = nullptr;
+    L.cap = d.cap;
+    L.hdr = s->d_hdr;
+    L.ldx = d.dim;
+    for (int g = 0; g < d.G; ++g) {
+        const Udf &u = s->udfs[g];
+        const int last = u.n_layers - 1;
+        L.l[g] = MqLayer{u.dW[last], nullptr, u.b[last][0], s->act32[(last - 1) % 2], s->wmax, u.dims[last], 1};
+    }
+    const int pe = prof_begin(s, SP_DOT);
+    mq_launch_dots_f32(L, score, d.cap, s->st, s->sms);
+    prof_end(s, pe);
+    s->step_launches++;
+}
+
+// One step's launches, all stream-ordered on s->st (captured into a graph
+// when graphs are on).
+hydro_status enqueue_step(hydro_session *s, Slot &slot) {
+    const MqDev &d = s->d;
+    const bool bf = bf16(s);
+    CU(cudaMemcpyAsync(s->d_hdr, slot.h_hdr, sizeof(StepHdr), cudaMemcpyHostToDevice, s->st));
+    s->step_launches = 0;
+    int pe = prof_begin(s, SP_CTRL);
+    mq_launch_init(d, s->st, s->sms);
+    mq_launch_router(d, s->h, s->st);
+    prof_end(s, pe);
+    s->step_launches += 2;
+    for (int r = 0; r < s->maxP; ++r) {
+        pe = prof_begin(s, SP_CTRL);
+        mq_launch_partition(d, r, s->st, s->sms);
+        prof_end(s, pe);
+        s->step_launches += r > 0 ? 2 : 1;
+        if (bf) {
+            TRY(eval_tc(s, rc_q(d), d.queues, d.score));
+        } else {
+            eval_f32(s, rc_q(d), d.queues, d.score);
+        }
+        pe = prof_begin(s, SP_CTRL);
+        mq_launch_classify(d, r, 0, bf, s->st, s->sms);
+        prof_end(s, pe);
+        s->step_launches++;
+        if (bf) {
+            eval_f32(s, rc_b32(d), d.bq32, d.rscore);
+            pe = prof_begin(s, SP_CTRL);
+            mq_launch_classify(d, r, 1, bf, s->st, s->sms);
+            prof_end(s, pe);
+            s->step_launches++;
+        }
+        pe = prof_begin(s, SP_BAND64);
+        mq_launch_band64(d, r, s->mlps, s->st, s->sms);
+        prof_end(s, pe);
+        pe = prof_begin(s, SP_CTRL);
+        mq_launch_survivors(d, r, s->st, s->sms);
+        prof_end(s, pe);
+        s->step_launches += 2;
+    }
+    pe = prof_begin(s, SP_CTRL);
+    mq_launch_result(d, slot.bitmap, s->st, s->sms);
+    mq_launch_commit(d, s->h, slot.rows, slot.order, slot.evall, slot.bidx, slot.npass, slot.total, s->st);
+    prof_end(s, pe);
+    s->step_launches += 2;
+    slot.launches = s->step_launches;
+    CU(cudaGetLastError());
+    return HYDRO_OK;
+}
+
+hydro_status autotune(hydro_session *s) {
+    // time every tile width of every hidden layer on a stacked operand of
+    // min(cap, 16384) rows (one group), keep the fastest
+    const int rows = std::min(s->d.cap, 16384);
+    int *d_rows = nullptr;
+    TRY(dalloc(s, &d_rows, sizeof(int)));
+    CU(cudaMemcpy(d_rows, &rows, sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemset(s->stage16, 0, sizeof(__nv_bfloat16) * (size_t)s->d.cap * s->d.dim));
+    CU(cudaMemset(s->act16[0], 0, sizeof(__nv_bfloat16) * (size_t)s->d.cap * s->wmax));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    for (size_t ui = 0; ui < s->udfs.size(); ++ui) {
+        Udf &u = s->udfs[ui];
+        for (int l = 0; l + 1 < u.n_layers; ++l) {
+            hydro_tile_choice rec{};
+            rec.udf = (int)ui;
+            rec.layer = l;
+            rec.K = u.dims[l];
+            rec.N = u.dims[l + 1];
+            double best = 1e30;
+            int best_nt = 0;
+            for (int k = 0; k < 3; ++k) {
+                const int nt = 64 << k;
+                if (rec.N % nt) continue;
+                TcGemmGroup g{d_rows, l == 0 ? s->stage16 : s->act16[0], l == 0 ? s->d.dim : s->wmax, s->d.cap,
+                              u.dW16[l], u.db[l], nullptr, rec.K, rec.N, nt};
+                float ms = 0;
+                for (int rep = 0; rep < 4; ++rep) {
+                    if (rep == 1) CU(cudaEventRecord(e0, s->st));
+                    hydro_status rs = tc_gemm_grouped_run(s->encode, &g, 1, s->act16[1], s->wmax, s->partials,
+                                                          s->pstride, s->sms, s->st, s->d.err);
+                    if (rs != HYDRO_OK) return fail(rs, "autotune: %s", tc_gemm_last_error());
+                }
+                CU(cudaEventRecord(e1, s->st));
+                CU(cudaEventSynchronize(e1));
+                CU(cudaEventElapsedTime(&ms, e0, e1));
+                rec.us[k] = ms * 1000.0 / 3.0;
+                if (rec.us[k] < best) {
+                    best = rec.us[k];
+                    best_nt = nt;
+                }
+            }
+            u.nt[l] = best_nt;
+            rec.tile_n = best_nt;
+            s->tuning.push_back(rec);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    unsigned int err = 0;
+    CU(cudaMemcpy(&err, s->d.err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) return fail(HYDRO_EDEVICE, "device error word 0x%x during autotuning", err);
+    return HYDRO_OK;
+}
+
+hydro_status finalize(hydro_session *s) {
+    if (s->finalized) return HYDRO_OK;
+    const hydro_session_config &c = s->cfg;
+    if (s->udfs.empty()) return fail(HYDRO_ESTATE, "session has no UDFs");
+    if (s->queries.empty()) return fail(HYDRO_ESTATE, "session has no queries");
+    CU(cudaSetDevice(c.device));
+    CU(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, c.device));
+    if (c.stream) {
+        s->st = (cudaStream_t)c.stream;
+    } else {
+        CU(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
+        s->own_stream = true;
+    }
+    const int Q = (int)s->queries.size(), G = (int)s->udfs.size(), cap = c.max_step_tuples;
+    s->wmax = 64;
+    s->max_hidden = 0;
+    for (const Udf &u : s->udfs) {
+        s->max_hidden = std::max(s->max_hidden, u.n_layers - 1);
+        for (int l = 1; l < u.n_layers; ++l) s->wmax = std::max(s->wmax, u.dims[l]);
+    }
+    s->maxP = 0;
+    for (const Query &q : s->queries) s->maxP = std::max(s->maxP, q.P);
+
+    // weights
+    s->mlps.max_width = std::max(s->wmax, c.dim);
+    for (int g = 0; g < G; ++g) {
+        Udf &u = s->udfs[g];
+        u.dW.assign(u.n_layers, nullptr);
+        u.db.assign(u.n_layers, nullptr);
+        u.dW16.assign(u.n_layers, nullptr);
+        u.nt.assign(u.n_layers, 0);
+        for (int l = 0; l < u.n_layers; ++l) {
+            TRY(upload(s, &u.dW[l], u.W[l].data(), u.W[l].size()));
+            TRY(upload(s, &u.db[l], u.b[l].data(), u.b[l].size()));
+            if (bf16(s) && l + 1 < u.n_layers) {
+                std::vector<__nv_bfloat16> w16(u.W[l].size());
+                for (size_t k = 0; k < w16.size(); ++k) w16[k] = __float2bfloat16_rn(u.W[l][k]);
+                TRY(upload(s, &u.dW16[l], w16.data(), w16.size()));
+            }
+        }
+        u.mlp.n_layers = u.n_layers;
+        u.mlp.max_width = s->mlps.max_width;
+        for (int l = 0; l <= u.n_layers; ++l) u.mlp.dims[l] = u.dims[l];
+        for (int l = 0; l < u.n_layers; ++l) {
+            u.mlp.W[l] = u.dW[l];
+            u.mlp.b[l] = u.db[l];
+        }
+        s->mlps.m[g] = u.mlp;
+    }
+    CU(mq_band_smem_setup(s->mlps.max_width));
+
+    // query tables
+    std::vector<unsigned char> np(Q), udf((size_t)Q * kMqSlots, 0);
+    std::vector<double> thr((size_t)Q * kMqSlots, 0.0);
+    std::vector<long long> cost((size_t)Q * kMqSlots, 0);
+    for (int q = 0; q < Q; ++q) {
+        np[q] = (unsigned char)s->queries[q].P;
+        for (int k = 0; k < s->queries[q].P; ++k) {
+            udf[(size_t)q * kMqSlots + k] = (unsigned char)s->queries[q].udf[k];
+            thr[(size_t)q * kMqSlots + k] = s->queries[q].thr[k];
+            cost[(size_t)q * kMqSlots + k] = s->udfs[s->queries[q].udf[k]].cost;
+        }
+    }
+    MqDev &d = s->d;
+    d.Q = Q;
+    d.G = G;
+    d.cap = cap;
+    d.dim = c.dim;
+    unsigned char *np_d, *udf_d;
+    double *thr_d;
+    long long *cost_d;
+    TRY(upload(s, &np_d, np.data(), np.size()));
+    TRY(upload(s, &udf_d, udf.data(), udf.size()));
+    TRY(upload(s, &thr_d, thr.data(), thr.size()));
+    TRY(upload(s, &cost_d, cost.data(), cost.size()));
+    d.np = np_d;
+    d.udf = udf_d;
+    d.thr = thr_d;
+    d.cost = cost_d;
+    TRY(dalloc(s, &s->d_hdr, sizeof(StepHdr)));
+    d.hdr = s->d_hdr;
+    TRY(dalloc(s, &d.off, sizeof(int) * (Q + 1)));
+    TRY(dalloc(s, &d.qid, (size_t)cap));
+    TRY(dalloc(s, &d.order, (size_t)Q * kMqSlots));
+    TRY(dalloc(s, &d.evall, (size_t)Q));
+    TRY(dalloc(s, &d.bidx, sizeof(long long) * Q));
+    TRY(dalloc(s, &d.rows, sizeof(StatRow) * Q * kMqSlots));
+    TRY(dalloc(s, &d.npass, sizeof(long long) * Q));
+    TRY(dalloc(s, &d.visited, (size_t)cap));
+    TRY(dalloc(s, &d.label, (size_t)cap));
+    TRY(dalloc(s, &d.ok, (size_t)cap));
+    TRY(dalloc(s, &d.alive[0], sizeof(int) * (size_t)cap));
+    TRY(dalloc(s, &d.alive[1], sizeof(int) * (size_t)cap));
+    TRY(dalloc(s, &d.queues, sizeof(int) * (size_t)G * cap));
+    TRY(dalloc(s, &d.bq32, sizeof(int) * (size_t)G * cap));
+    TRY(dalloc(s, &d.bq64, sizeof(int) * (size_t)G * cap));
+    TRY(dalloc(s, &d.rc, sizeof(RoundCounters)));
+    CU(cudaMemset(d.rc, 0, sizeof(RoundCounters)));
+    TRY(dalloc(s, &d.score, sizeof(float) * (size_t)G * cap));
+    TRY(dalloc(s, &d.rscore, sizeof(float) * (size_t)G * cap));
+    TRY(dalloc(s, &s->d_margin_lowp, sizeof(float) * kMqPool));
+    TRY(dalloc(s, &s->d_margin_fp32, sizeof(float) * kMqPool));
+    d.margin_lowp = s->d_margin_lowp;
+    d.margin_fp32 = s->d_margin_fp32;
+    TRY(dalloc(s, &d.err, sizeof(unsigned int)));
+    CU(cudaMemset(d.err, 0, sizeof(unsigned int)));
+    for (int k = 0; k < 2; ++k) TRY(dalloc(s, &s->act32[k], sizeof(float) * (size_t)cap * s->wmax));
+    if (bf16(s)) {
+        for (const Udf &u : s->udfs)
+            for (int l = 0; l + 1 < u.n_layers; ++l)
+                if (!tc_gemm_supported(u.dims[l], u.dims[l + 1]))
+                    return fail(HYDRO_EUNSUPPORTED, "BF16 sessions need layer widths that are multiples of 64");
+        TRY(dalloc(s, &s->stage16, sizeof(__nv_bfloat16) * (size_t)cap * c.dim));
+        for (int k = 0; k < 2; ++k) TRY(dalloc(s, &s->act16[k], sizeof(__nv_bfloat16) * (size_t)cap * s->wmax));
+        s->pstride = s->wmax / 64;
+        TRY(dalloc(s, &s->partials, sizeof(float) * (size_t)cap * s->pstride));
+        hydro_status rs = tc_gemm_init(&s->encode);
+        if (rs != HYDRO_OK) return fail(rs, "tensor-core GEMM init: %s", tc_gemm_last_error());
+    }
+
+    // statistics history
+    MqHist &h = s->h;
+    h.R = c.stats_window + 2;
+    h.warmup = c.warmup_batches;
+    h.window = c.stats_window;
+    TRY(dalloc(s, &h.ring, sizeof(StatRow) * (size_t)Q * h.R * kMqSlots));
+    TRY(dalloc(s, &h.warm, sizeof(StatRow) * (size_t)Q * std::max(1, h.warmup) * kMqSlots));
+    TRY(dalloc(s, &h.bdone, sizeof(long long) * Q));
+    CU(cudaMemset(h.ring, 0, sizeof(StatRow) * (size_t)Q * h.R * kMqSlots));
+    CU(cudaMemset(h.warm, 0, sizeof(StatRow) * (size_t)Q * std::max(1, h.warmup) * kMqSlots));
+    CU(cudaMemset(h.bdone, 0, sizeof(long long) * Q));
+
+    // in-flight slots
+    s->slots.resize(c.max_in_flight);
+    for (Slot &sl : s->slots) {
+        CU(cudaEventCreate(&sl.ev0));
+        CU(cudaEventCreate(&sl.ev1));
+        void *hp = nullptr;
+        CU(cudaMallocHost(&hp, sizeof(StepHdr)));
+        s->host_allocs.push_back(hp);
+        sl.h_hdr = (StepHdr *)hp;
+        memset(sl.h_hdr, 0, sizeof(StepHdr));
+        TRY(dalloc(s, &sl.bitmap, sizeof(unsigned int) * ((size_t)cap / 32 + 1)));
+        TRY(dalloc(s, &sl.rows, sizeof(StatRow) * (size_t)Q * kMqSlots));
+        TRY(dalloc(s, &sl.order, (size_t)Q * kMqSlots));
+        TRY(dalloc(s, &sl.evall, (size_t)Q));
+        TRY(dalloc(s, &sl.bidx, sizeof(long long) * Q));
+        TRY(dalloc(s, &sl.npass, sizeof(long long) * Q));
+        TRY(dalloc(s, &sl.total, sizeof(int)));
+    }
+    s->finalized = true;
+    return HYDRO_OK;
+}
+
+hydro_status upload_margins(hydro_session *s) {
+    float lo[kMqPool] = {}, f32[kMqPool] = {};
+    for (size_t g = 0; g < s->udfs.size(); ++g) {
+        lo[g] = (float)s->udfs[g].margin_lowp;
+        f32[g] = (float)s->udfs[g].margin_fp32;
+    }
+    CU(cudaMemcpy(s->d_margin_lowp, lo, sizeof lo, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(s->d_margin_fp32, f32, sizeof f32, cudaMemcpyHostToDevice));
+    return HYDRO_OK;
+}
+
+hydro_status wait_ev(cudaEvent_t ev, long long wait_ms, bool *done) {
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) {
+            *done = true;
+            return HYDRO_OK;
+        }
+        if (e != cudaErrorNotReady) return fail(HYDRO_ECUDA, "event query: %s", cudaGetErrorString(e));
+        if (wait_ms == 0) break;
+        if (wait_ms > 0) {
+            auto el = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+            if (el.count() >= wait_ms) break;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    *done = false;
+    return HYDRO_OK;
+}
+
+__global__ void k_single_queue(RoundCounters *rc, int g, int n, int *queues, int cap) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kMqPool) {
+        rc->q[i] = i == g ? n : 0;
+        rc->b32[i] = 0;
+        rc->b64[i] = 0;
+    }
+    for (int m = i; m < n; m += gridDim.x * blockDim.x) queues[(size_t)g * cap + m] = m;
+}
+
+__global__ void k_score_to_f64(const float *src, double *dst, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (double)src[i];
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+
+extern "C" {
+
+void hydro_session_default_config(hydro_session_config *cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->precision = HYDRO_PREC_FP32;
+    cfg->warmup_batches = 1;
+    cfg->stats_window = 8;
+    cfg->use_graphs = 1;
+    cfg->autotune = 1;
+    cfg->max_in_flight = 2;
+}
+
+hydro_status hydro_session_create(const hydro_session_config *cfg, hydro_session **out) {
+    set_last_error("");
+    if (!cfg || !out) return fail(HYDRO_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (cfg->dim < 64 || cfg->dim % 64) return fail(HYDRO_EINVAL, "dim must be a positive multiple of 64");
+    if (cfg->max_step_tuples < 1 || cfg->max_step_tuples > (1 << 22))
+        return fail(HYDRO_EINVAL, "max_step_tuples outside 1..4194304");
+    if (cfg->precision != HYDRO_PREC_FP32 && cfg->precision != HYDRO_PREC_BF16)
+        return fail(HYDRO_EINVAL, "precision must be FP32 or BF16");
+    if (cfg->warmup_batches < 0 || cfg->stats_window < 1) return fail(HYDRO_EINVAL, "bad warmup/window");
+    if (cfg->max_in_flight < 1 || cfg->max_in_flight > 8) return fail(HYDRO_EINVAL, "max_in_flight outside 1..8");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
+        return fail(HYDRO_EINVAL, "no CUDA device %d", cfg->device);
+    hydro_session *s = new hydro_session();
+    s->cfg = *cfg;
+    *out = s;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_session_add_udf(hydro_session *s, const hydro_udf_desc *udf, int32_t *out_udf) {
+    set_last_error("");
+    TRY(check(s));
+    if (s->finalized) return fail(HYDRO_ESTATE, "UDFs must be added before the first submit");
+    if (!udf || udf->kind != HYDRO_UDF_MLP || udf->upstream) return fail(HYDRO_EINVAL, "pool UDFs are plain MLPs");
+    if ((int)s->udfs.size() >= HYDRO_MAX_POOL) return fail(HYDRO_EINVAL, "pool is full (%d)", HYDRO_MAX_POOL);
+    const int L = udf->n_layers;
+    if (L < 2 || L > HYDRO_MAX_LAYERS || !udf->dims || !udf->weights || !udf->biases)
+        return fail(HYDRO_EINVAL, "a pool MLP has 2..%d layers with weights and biases", HYDRO_MAX_LAYERS);
+    if (udf->dims[0] != s->cfg.dim || udf->dims[L] != 1) return fail(HYDRO_EINVAL, "dims[0] must be dim, last 1");
+    Udf u;
+    u.n_layers = L;
+    u.dims.assign(udf->dims, udf->dims + L + 1);
+    long long flops = 0;
+    for (int l = 0; l < L; ++l) {
+        if (u.dims[l + 1] < 1 || u.dims[l + 1] > 65536) return fail(HYDRO_EINVAL, "bad width");
+        if (!udf->weights[l] || !udf->biases[l]) return fail(HYDRO_EINVAL, "NULL weights of layer %d", l);
+        u.W.emplace_back(udf->weights[l], udf->weights[l] + (size_t)u.dims[l] * u.dims[l + 1]);
+        u.b.emplace_back(udf->biases[l], udf->biases[l] + u.dims[l + 1]);
+        flops += 2LL * u.dims[l] * u.dims[l + 1];
+    }
+    u.cost = udf->cost_hint > 0 ? udf->cost_hint : flops;
+    s->udfs.push_back(std::move(u));
+    if (out_udf) *out_udf = (int32_t)s->udfs.size() - 1;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_session_add_query(hydro_session *s, int32_t n_preds, const int32_t *udfs, const double *thresholds,
+                                     int32_t *out_query) {
+    set_last_error("");
+    TRY(check(s));
+    if (s->finalized) return fail(HYDRO_ESTATE, "queries must be added before the first submit");
+    if ((int)s->queries.size() >= HYDRO_MAX_QUERIES) return fail(HYDRO_EINVAL, "too many queries");
+    if (n_preds < 1 || n_preds > HYDRO_MAX_PREDICATES || !udfs || !thresholds)
+        return fail(HYDRO_EINVAL, "a query has 1..%d predicates", HYDRO_MAX_PREDICATES);
+    Query q;
+    q.P = n_preds;
+    unsigned seen = 0;
+    for (int k = 0; k < n_preds; ++k) {
+        if (udfs[k] < 0 || udfs[k] >= (int)s->udfs.size()) return fail(HYDRO_EINVAL, "unknown pool UDF %d", udfs[k]);
+        if (seen & (1u << udfs[k])) return fail(HYDRO_EINVAL, "pool UDF %d used twice in one query", udfs[k]);
+        seen |= 1u << udfs[k];
+        q.udf[k] = udfs[k];
+        q.thr[k] = thresholds[k];
+    }
+    s->queries.push_back(q);
+    if (out_query) *out_query = (int32_t)s->queries.size() - 1;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_session_set_margins(hydro_session *s, int32_t udf, double margin_lowp, double margin_fp32) {
+    set_last_error("");
+    TRY(check(s));
+    if (udf < 0 || udf >= (int)s->udfs.size()) return fail(HYDRO_EINVAL, "unknown pool UDF");
+    if (!(margin_lowp >= 0) || !(margin_fp32 >= 0)) return fail(HYDRO_EINVAL, "margins must be >= 0");
+    if (s->next_step > 0) return fail(HYDRO_ESTATE, "margins are fixed after the first submit");
+    s->udfs[udf].margin_lowp = margin_lowp;
+    s->udfs[udf].margin_fp32 = margin_fp32;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_session_udf_scores(hydro_session *s, int32_t udf, int32_t prec, const void *d_tuples, int64_t n,
+                                      double *d_scores) {
+    set_last_error("");
+    TRY(check(s));
+    if (udf < 0 || udf >= (int)s->udfs.size()) return fail(HYDRO_EINVAL, "unknown pool UDF");
+    if (n < 0 || (n > 0 && (!d_tuples || !d_scores))) return fail(HYDRO_EINVAL, "bad tuples/scores");
+    if (prec != HYDRO_PREC_FP64 && prec != HYDRO_PREC_FP32 && prec != HYDRO_PREC_BF16)
+        return fail(HYDRO_EINVAL, "precision must be FP64, FP32 or BF16");
+    if (prec == HYDRO_PREC_BF16 && !bf16(s)) return fail(HYDRO_EINVAL, "BF16 scores need a BF16 session");
+    CU(cudaSetDevice(s->cfg.device));
+    TRY(finalize(s));
+    for (Slot &sl : s->slots)
+        if (sl.busy) return fail(HYDRO_ESTATE, "poll every step before scoring");
+    const float *X = (const float *)d_tuples;
+    if (prec == HYDRO_PREC_FP64) {
+        if (n > 0) mq_launch_scores_f64(s->udfs[udf].mlp, s->mlps.max_width, X, s->cfg.dim, (int)n, d_scores, s->st, s->sms);
+    } else {
+        float *score_g = s->d.score + (size_t)udf * s->d.cap;
+        for (int64_t o = 0; o < n; o += s->d.cap) {
+            const int m = (int)std::min<int64_t>(s->d.cap, n - o);
+            StepHdr hh{};
+            hh.X = X + (size_t)o * s->cfg.dim;
+            CU(cudaMemcpyAsync(s->d_hdr, &hh, sizeof(void *), cudaMemcpyHostToDevice, s->st));
+            k_single_queue<<<std::max(1, std::min((m + 255) / 256, s->sms * 4)), 256, 0, s->st>>>(s->d.rc, udf, m,
+                                                                                                   s->d.queues, s->d.cap);
+            if (prec == HYDRO_PREC_BF16) {
+                TRY(eval_tc(s, rc_q(s->d), s->d.queues, s->d.score));
+            } else {
+                eval_f32(s, rc_q(s->d), s->d.queues, s->d.score);
+            }
+            k_score_to_f64<<<(m + 255) / 256, 256, 0, s->st>>>(score_g, d_scores + o, m);
+            CU(cudaStreamSynchronize(s->st));
+        }
+    }
+    CU(cudaStreamSynchronize(s->st));
+    unsigned int err = 0;
+    CU(cudaMemcpy(&err, s->d.err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) return fail(HYDRO_EDEVICE, "device error word 0x%x", err);
+    return HYDRO_OK;
+}
+
+hydro_status hydro_session_calibrate(hydro_session *s, const void *d_tuples, int64_t n, hydro_calib_info *info) {
+    set_last_error("");
+    TRY(check(s));
+    if (n < 1 || !d_tuples) return fail(HYDRO_EINVAL, "need calibration tuples");
+    if (s->next_step > 0) return fail(HYDRO_ESTATE, "calibrate before the first submit");
+    CU(cudaSetDevice(s->cfg.device));
+    TRY(finalize(s));
+    double *d = nullptr;
+    CU(cudaMalloc(&d, sizeof(double) * n * 3));
+    std::vector<double> s64(n), s32(n), s16(n);
+    hydro_status rc = HYDRO_OK;
+    const bool bf = bf16(s);
+    for (int g = 0; g < (int)s->udfs.size() && rc == HYDRO_OK; ++g) {
+        rc = hydro_session_udf_scores(s, g, HYDRO_PREC_FP64, d_tuples, n, d);
+        if (rc == HYDRO_OK) rc = hydro_session_udf_scores(s, g, HYDRO_PREC_FP32, d_tuples, n, d + n);
+        if (rc == HYDRO_OK && bf) rc = hydro_session_udf_scores(s, g, HYDRO_PREC_BF16, d_tuples, n, d + 2 * n);
+        if (rc != HYDRO_OK) break;
+        if (cudaMemcpy(s64.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(s32.data(), d + n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            (bf && cudaMemcpy(s16.data(), d + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)) {
+            rc = fail(HYDRO_ECUDA, "copy of calibration scores failed");
+            break;
+        }
+        double e32 = 0, e16 = 0, smax = 0;
+        for (int64_t k = 0; k < n; ++k) {
+            e32 = std::max(e32, std::fabs(s32[k] - s64[k]));
+            if (bf) e16 = std::max(e16, std::fabs(s16[k] - s64[k]));
+            smax = std::max(smax, std::fabs(s64[k]));
+        }
+        Udf &u = s->udfs[g];
+        u.margin_fp32 = std::max(16.0 * e32, 1e-9 * smax);
+        if (bf && u.margin_lowp < 4.0 * e16) u.margin_lowp = 4.0 * e16;
+        if (info) {
+            info[g] = hydro_calib_info{};
+            info[g].max_err_fp32 = e32;
+            info[g].max_err_lowp = e16;
+            info[g].margin_fp32 = u.margin_fp32;
+            info[g].margin_lowp = u.margin_lowp;
+        }
+    }
+    cudaFree(d);
+    return rc;
+}
+
+hydro_status hydro_session_submit(hydro_session *s, const void *d_tuples, const int32_t *counts, int64_t *out_step) {
+    set_last_error("");
+    TRY(check(s));
+    if (!counts || !out_step) return fail(HYDRO_EINVAL, "NULL counts or out_step");
+    CU(cudaSetDevice(s->cfg.device));
+    TRY(finalize(s));
+    const int Q = (int)s->queries.size();
+    long long total = 0;
+    for (int q = 0; q < Q; ++q) {
+        if (counts[q] < 0) return fail(HYDRO_EINVAL, "count of query %d is negative", q);
+        total += counts[q];
+    }
+    if (total > s->cfg.max_step_tuples) return fail(HYDRO_EINVAL, "step of %lld tuples > max_step_tuples", total);
+    if (total > 0 && !d_tuples) return fail(HYDRO_EINVAL, "NULL tuples");
+    Slot *slot = nullptr;
+    for (Slot &sl : s->slots)
+        if (!sl.busy) {
+            slot = &sl;
+            break;
+        }
+    if (!slot) return fail(HYDRO_EAGAIN, "all %d in-flight slots are busy; poll first", s->cfg.max_in_flight);
+    if (s->next_step == 0) {
+        TRY(upload_margins(s));
+        if (s->cfg.autotune && bf16(s)) TRY(autotune(s));
+    }
+    slot->h_hdr->X = (const float *)d_tuples;
+    for (int q = 0; q < Q; ++q) slot->h_hdr->counts[q] = counts[q];
+    slot->counts.assign(counts, counts + Q);
+    for (ProfRec &r : slot->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    slot->prof.clear();
+    if (s->cfg.use_graphs && !s->prof_on) {
+        if (!slot->exec) {
+            cudaGraph_t graph = nullptr;
+            CU(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+            hydro_status rs = enqueue_step(s, *slot);
+            cudaError_t ce = cudaStreamEndCapture(s->st, &graph);
+            if (rs != HYDRO_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rs;
+            }
+            if (ce != cudaSuccess) return fail(HYDRO_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&slot->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return fail(HYDRO_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+        }
+        CU(cudaEventRecord(slot->ev0, s->st));
+        CU(cudaGraphLaunch(slot->exec, s->st));
+    } else {
+        CU(cudaEventRecord(slot->ev0, s->st));
+        s->prof_slot = s->prof_on ? slot : nullptr;
+        hydro_status rs = enqueue_step(s, *slot);
+        s->prof_slot = nullptr;
+        TRY(rs);
+    }
+    CU(cudaEventRecord(slot->ev1, s->st));
+    slot->busy = true;
+    slot->step = s->next_step;
+    *out_step = s->next_step++;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_session_poll(hydro_session *s, int64_t step, uint32_t *pass_bitmap, hydro_step_query *per_query,
+                                double *device_ms, int32_t wait_ms) {
+    set_last_error("");
+    TRY(check(s));
+    Slot *slot = nullptr;
+    for (Slot &sl : s->slots)
+        if (sl.busy && sl.step == step) slot = &sl;
+    if (!slot) return fail(HYDRO_ENOTFOUND, "step %lld is not in flight", (long long)step);
+    CU(cudaSetDevice(s->cfg.device));
+    bool done = false;
+    TRY(wait_ev(slot->ev1, wait_ms, &done));
+    if (!done) return fail(HYDRO_EAGAIN, "step %lld not finished", (long long)step);
+    slot->busy = false;
+    s->launches += slot->launches;
+    for (ProfRec &r : slot->prof) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            s->prof_ms[r.cls] += ms;
+            s->prof_n[r.cls]++;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    slot->prof.clear();
+    unsigned int err = 0;
+    CU(cudaMemcpy(&err, s->d.err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) {
+        s->dead = true;
+        return fail(HYDRO_EDEVICE, "device error word 0x%x", err);
+    }
+    const int Q = (int)s->queries.size();
+    int total = 0;
+    CU(cudaMemcpy(&total, slot->total, sizeof(int), cudaMemcpyDeviceToHost));
+    if (pass_bitmap && total > 0)
+        CU(cudaMemcpy(pass_bitmap, slot->bitmap, sizeof(uint32_t) * ((size_t)(total + 31) / 32),
+                      cudaMemcpyDeviceToHost));
+    if (per_query) {
+        std::vector<StatRow> rows((size_t)Q * kMqSlots);
+        std::vector<unsigned char> order((size_t)Q * kMqSlots), evall(Q);
+        std::vector<long long> bidx(Q), npass(Q);
+        CU(cudaMemcpy(rows.data(), slot->rows, sizeof(StatRow) * rows.size(), cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(order.data(), slot->order, order.size(), cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(evall.data(), slot->evall, evall.size(), cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(bidx.data(), slot->bidx, sizeof(long long) * Q, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(npass.data(), slot->npass, sizeof(long long) * Q, cudaMemcpyDeviceToHost));
+        for (int q = 0; q < Q; ++q) {
+            hydro_step_query &o = per_query[q];
+            o = hydro_step_query{};
+            o.n = slot->counts[q];
+            o.n_pass = npass[q];
+            o.batch = bidx[q];
+            o.warmup = evall[q];
+            for (int k = 0; k < HYDRO_MAX_PREDICATES; ++k) {
+                const bool used = k < s->queries[q].P;
+                o.order[k] = used ? order[(size_t)q * kMqSlots + k] : -1;
+                const StatRow &r = rows[(size_t)q * kMqSlots + k];
+                o.evaluated[k] = r.evaluated;
+                o.passed[k] = r.passed;
+                o.recheck_fp32[k] = r.recheck32;
+                o.recheck_fp64[k] = r.recheck64;
+            }
+        }
+    }
+    if (device_ms) {
+        float ms = 0;
+        CU(cudaEventElapsedTime(&ms, slot->ev0, slot->ev1));
+        *device_ms = ms;
+    }
+    return HYDRO_OK;
+}
+
+hydro_status hydro_session_tuning(hydro_session *s, hydro_tile_choice *out, int32_t max, int32_t *n_out) {
+    set_last_error("");
+    TRY(check(s));
+    if (!n_out || (max > 0 && !out)) return fail(HYDRO_EINVAL, "NULL output");
+    const int n = std::min<int>(max, (int)s->tuning.size());
+    for (int i = 0; i < n; ++i) out[i] = s->tuning[i];
+    *n_out = n;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_session_profile(hydro_session *s, int32_t enable) {
+    set_last_error("");
+    TRY(check(s));
+    for (Slot &sl : s->slots)
+        if (sl.busy) return fail(HYDRO_ESTATE, "poll every step before switching profiling");
+    s->prof_on = enable != 0;
+    for (int k = 0; k < SP_N; ++k) {
+        s->prof_ms[k] = 0;
+        s->prof_n[k] = 0;
+    }
+    s->launches = 0;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_session_profile_read(hydro_session *s, hydro_kernel_profile *out, int32_t max, int32_t *n_out,
+                                        int64_t *total_launches) {
+    set_last_error("");
+    TRY(check(s));
+    if (!n_out || (max > 0 && !out)) return fail(HYDRO_EINVAL, "NULL output");
+    int n = 0;
+    for (int k = 0; k < SP_N && n < max; ++k) {
+        if (!s->prof_n[k]) continue;
+        hydro_kernel_profile &o = out[n++];
+        memset(&o, 0, sizeof o);
+        snprintf(o.name, sizeof o.name, "%s", kSessProf[k]);
+        o.launches = s->prof_n[k];
+        o.total_ms = s->prof_ms[k];
+    }
+    *n_out = n;
+    if (total_launches) *total_launches = s->launches;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_session_destroy(hydro_session *s) {
+    set_last_error("");
+    if (!s) return fail(HYDRO_EINVAL, "NULL session");
+    cudaSetDevice(s->cfg.device);
+    for (Slot &sl : s->slots) {
+        if (sl.busy && sl.ev1) {
+            bool done = false;
+            wait_ev(sl.ev1, 60000, &done);
+        }
+        if (sl.exec) cudaGraphExecDestroy(sl.exec);
+        for (ProfRec &r : sl.prof) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        if (sl.ev0) cudaEventDestroy(sl.ev0);
+        if (sl.ev1) cudaEventDestroy(sl.ev1);
+    }
+    if (s->st) cudaStreamSynchronize(s->st);
+    for (void *p : s->allocs) cudaFree(p);
+    for (void *p : s->host_allocs) cudaFreeHost(p);
+    if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+    delete s;
+    return HYDRO_OK;
+}
+
+}  // extern "C"

@@ -9,6 +9,7 @@
 // layer (one output) is folded into the epilogue of the last hidden layer:
 // each row leaves one partial head . relu(...) per column tile, summed in a
 // fixed order by a finalize kernel.
+#include <cstring>
 #include <string>
 
 #include "common.cuh"
@@ -22,35 +23,64 @@ namespace {
 using namespace tcx;
 thread_local std::string g_gemm_err;
 
-template <int NT, int S>
-struct GemmCfg {
-    static constexpr int A_BYTES = 128 * 128;   // 128 rows x 64 bf16
-    static constexpr int B_BYTES = NT * 128;    // NT rows x 64 bf16
-    static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int TMEM_COLS = 2 * NT;
-    static constexpr int SMEM = S * STAGE + 1024 + 256;
+// One launch serves up to kMaxGroups MLP layers ("groups"): group g owns the
+// rows [off_g, off_g + count_g) of the stacked operand (off_g = sum of the
+// earlier groups' counts, read on the device), its own weights, K, N and
+// column-tile width NT_g (64, 128 or 256), all carried in the launch's
+// parameters; tiles are numbered group by group and walked persistently.
+constexpr int kA_BYTES = 128 * 128;   // 128 rows x 64 bf16 (one 128-byte swizzled K slice)
+constexpr int kMaxStages = 8;
+
+struct __align__(64) TcGroup {
+    CUtensorMap tmA, tmB;
+    const int *count;         // rows of the group (device)
+    const float *bias;        // [N]
+    const float *head_w;      // [N]: fold the one-output head into the epilogue; nullptr: store Y
+    int K, N, NT, pad;
 };
 
-template <int NT, int S>
-__global__ void __launch_bounds__(192, 1)
-k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const int *count,
-               int K, int N, const float *__restrict__ bias, __nv_bfloat16 *Y, const float *__restrict__ head_w,
-               float *partials, unsigned int *err) {
-    using C = GemmCfg<NT, S>;
+struct TcLaunch {
+    TcGroup g[kMaxGroups];
+    __nv_bfloat16 *Y;         // stacked outputs, row stride ldy (elements)
+    float *partials;          // stacked head partials, row stride pstride
+    unsigned int *err;
+    int n, ldy, pstride, S, stage_bytes, tmem_cols;
+};
+
+__device__ __forceinline__ void group_layout(const TcLaunch &L, int *off, int *cnt, int *start) {
+    int o = 0, t = 0;
+    for (int g = 0; g < L.n; ++g) {
+        const int c = *L.g[g].count;
+        off[g] = o;
+        cnt[g] = c;
+        start[g] = t;
+        o += c;
+        if (L.g[g].NT) t += ((c + 127) / 128) * (L.g[g].N / L.g[g].NT);
+    }
+    start[L.n] = t;
+}
+
+__device__ __forceinline__ int tile_group(const int *start, int n, int t) {
+    int g = 0;
+    while (g + 1 < n && t >= start[g + 1]) ++g;   // groups without tiles have start[g] == start[g + 1]
+    return g;
+}
+
+__global__ void __launch_bounds__(192, 1) k_gemm_grouped_bf16_tc(const __grid_constant__ TcLaunch L) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * C::STAGE);
-    uint64_t *empty = full + S;
-    uint64_t *tfull = empty + S;
+    const int S = L.S;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * L.stage_bytes);
+    uint64_t *empty = full + kMaxStages;
+    uint64_t *tfull = empty + kMaxStages;
     uint64_t *tempty = tfull + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int M = *count;
-    const int tiles_n = N / NT;
-    const int total = ((M + 127) / 128) * tiles_n;
-    const int kblocks = K / 64;
+    int off[kMaxGroups], cnt[kMaxGroups], start[kMaxGroups + 1];
+    group_layout(L, off, cnt, start);
+    const int total = start[L.n];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -66,7 +96,7 @@ k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"((uint32_t)C::TMEM_COLS)
+                     "r"((uint32_t)L.tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -74,6 +104,7 @@ k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    const int half = L.tmem_cols / 2;   // columns per accumulator buffer
 
     if (warp == 0) {
         if (lane == 0) {
@@ -81,16 +112,20 @@ k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             uint32_t ph = 0, issued = 0, last_par = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const int m0 = (t / tiles_n) * 128, n0 = (t % tiles_n) * NT;
-                for (int kb = 0; kb < kblocks; ++kb) {
+                const int g = tile_group(start, L.n, t);
+                const TcGroup &G = L.g[g];
+                const int tiles_n = G.N / G.NT, local = t - start[g];
+                const int m0 = off[g] + (local / tiles_n) * 128, n0 = (local % tiles_n) * G.NT;
+                const uint32_t bytes = (uint32_t)(kA_BYTES + G.NT * 128);
+                for (int kb = 0; kb < G.K / 64; ++kb) {
                     if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
-                    unsigned char *sa = smem + s * C::STAGE;
-                    mbar_expect_tx(&full[s], (uint32_t)C::STAGE);
-                    tma_load_2d(sa, &tmA, &full[s], kb * 64, m0);
-                    tma_load_2d(sa + C::A_BYTES, &tmB, &full[s], kb * 64, n0);
+                    unsigned char *sa = smem + s * L.stage_bytes;
+                    mbar_expect_tx(&full[s], bytes);
+                    tma_load_2d(sa, &G.tmA, &full[s], kb * 64, m0);
+                    tma_load_2d(sa + kA_BYTES, &G.tmB, &full[s], kb * 64, n0);
                     issued |= 1u << s;
                     last_par = (last_par & ~(1u << s)) | (ph << s);
                     if (++s == S) {
@@ -108,12 +143,14 @@ k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(128, NT);
             int s = 0;
             uint32_t ph = 0;
             int tl = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
+                const int g = tile_group(start, L.n, t);
+                const int NT = L.g[g].NT, kblocks = L.g[g].K / 64;
+                const uint32_t idesc = idesc_bf16(128, NT);
                 const int buf = tl & 1;
                 const uint32_t tph = (uint32_t)(tl >> 1) & 1u;
                 if (!mbar_wait(&tempty[buf], tph ^ 1u, abort_flag)) {
@@ -121,15 +158,15 @@ k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dt = tmem_base + (uint32_t)(buf * NT);
+                const uint32_t dt = tmem_base + (uint32_t)(buf * half);
                 for (int kb = 0; kb < kblocks; ++kb) {
                     if (!mbar_wait(&full[s], ph, abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = smem_u32(smem + s * C::STAGE);
-                    const uint32_t sb = sa + C::A_BYTES;
+                    const uint32_t sa = smem_u32(smem + s * L.stage_bytes);
+                    const uint32_t sb = sa + kA_BYTES;
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
                         mma_bf16(dt, smem_desc(sa + kk * 32, 1024, 2u), smem_desc(sb + kk * 32, 1024, 2u), idesc,
@@ -146,7 +183,6 @@ k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else {
         const int qtr = warp & 3;
-        const int row = qtr * 32 + lane;
         int tl = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
             const int buf = tl & 1;
@@ -156,37 +192,44 @@ k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 break;
             }
             tc_fence_after();
-            const int tn = t % tiles_n;
-            const int m = (t / tiles_n) * 128 + row, n0 = tn * NT;
+            const int g = tile_group(start, L.n, t);
+            const TcGroup &G = L.g[g];
+            const int NT = G.NT, tiles_n = G.N / NT, local = t - start[g];
+            const int tn = local % tiles_n;
+            const int m = (local / tiles_n) * 128 + qtr * 32 + lane, n0 = tn * NT;
+            const bool live = m < cnt[g];
+            const size_t row = (size_t)off[g] + m;
+            const float *bias = G.bias + n0;
+            const float *hw = G.head_w ? G.head_w + n0 : nullptr;
             float hsum = 0.f;
 #pragma unroll 1
             for (int c0 = 0; c0 < NT; c0 += 32) {
                 uint32_t r[32];
-                tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * NT + c0), r);
+                tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * half + c0), r);
                 tmem_ld_wait();
-                if (head_w) {
+                if (hw) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        float v = __uint_as_float(r[j]) + __ldg(bias + n0 + c0 + j);
+                        float v = __uint_as_float(r[j]) + __ldg(bias + c0 + j);
                         v = v > 0.f ? v : 0.f;
-                        hsum = fmaf(__ldg(head_w + n0 + c0 + j), v, hsum);
+                        hsum = fmaf(__ldg(hw + c0 + j), v, hsum);
                     }
-                } else if (m < M) {
+                } else if (live) {
                     uint32_t pk[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        float v0 = __uint_as_float(r[2 * j]) + __ldg(bias + n0 + c0 + 2 * j);
-                        float v1 = __uint_as_float(r[2 * j + 1]) + __ldg(bias + n0 + c0 + 2 * j + 1);
+                        float v0 = __uint_as_float(r[2 * j]) + __ldg(bias + c0 + 2 * j);
+                        float v1 = __uint_as_float(r[2 * j + 1]) + __ldg(bias + c0 + 2 * j + 1);
                         v0 = v0 > 0.f ? v0 : 0.f;
                         v1 = v1 > 0.f ? v1 : 0.f;
                         pk[j] = pack_bf16x2(v0, v1);
                     }
-                    uint4 *dst = reinterpret_cast<uint4 *>(Y + (size_t)m * N + n0 + c0);
+                    uint4 *dst = reinterpret_cast<uint4 *>(L.Y + row * L.ldy + n0 + c0);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
                 }
             }
-            if (head_w && m < M) partials[(size_t)m * tiles_n + tn] = hsum;
+            if (hw && live) L.partials[row * L.pstride + tn] = hsum;
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[buf]);
@@ -197,10 +240,10 @@ k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                     "r"((uint32_t)C::TMEM_COLS)
+                     "r"((uint32_t)L.tmem_cols)
                      : "memory");
     }
-    if (threadIdx.x == 0 && *abort_flag) atomicOr(err, ERR_TC_TIMEOUT);
+    if (threadIdx.x == 0 && *abort_flag) atomicOr(L.err, ERR_TC_TIMEOUT);
 }
 
 // Gather the listed fp32 rows into a dense BF16 matrix, 8 values per thread:
@@ -224,23 +267,55 @@ using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, vo
                               const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-template <int NT, int S>
-cudaError_t gemm_smem() {
-    return cudaFuncSetAttribute(k_gemm_bf16_tc<NT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                GemmCfg<NT, S>::SMEM);
-}
+constexpr int kGemmSmem = 197888;   // S * stage + 1024 (alignment) + 256 (barriers), every NT
 
-constexpr int kS256 = 4, kS128 = 6, kS64 = 8;
-
-bool encode2d(EncodeFn enc, CUtensorMap *m, const void *base, int inner, long long outer, int box_inner,
+bool encode2d(EncodeFn enc, CUtensorMap *m, const void *base, int inner, long long outer, int ld, int box_inner,
               int box_outer) {
     const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-    const cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
     const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
     const cuuint32_t es[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int col_tile(int N) { return N % 256 == 0 ? 256 : N % 128 == 0 ? 128 : 64; }
+
+// Stacked rows: group g's rows follow the earlier groups' rows.
+__global__ void k_gather_grouped_bf16(int n, const int *counts, const int *queues, int qstride,
+                                      const float *const *Xp, int ldx, int K, __nv_bfloat16 *out) {
+    const float *X = *Xp;
+    int off[kMaxGroups + 1];
+    off[0] = 0;
+    for (int g = 0; g < n; ++g) off[g + 1] = off[g] + counts[g];
+    const int per_row = K / 8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)off[n] * per_row;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(i / per_row), q = (int)(i % per_row);
+        int g = 0;
+        while (e >= off[g + 1]) ++g;
+        const int src = queues[(size_t)g * qstride + (e - off[g])];
+        const float4 *p = reinterpret_cast<const float4 *>(X + (size_t)src * ldx) + 2 * q;
+        const float4 a = p[0], b = p[1];
+        reinterpret_cast<uint4 *>(out + (size_t)e * K)[q] =
+            make_uint4(pack_bf16x2(a.x, a.y), pack_bf16x2(a.z, a.w), pack_bf16x2(b.x, b.y), pack_bf16x2(b.z, b.w));
+    }
+}
+
+__global__ void k_head_finalize_grouped(int n, const int *counts, TcHeads heads, const float *partials, int pstride,
+                                        float *score, int sstride) {
+    int off[kMaxGroups + 1];
+    off[0] = 0;
+    for (int g = 0; g < n; ++g) off[g + 1] = off[g] + counts[g];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < off[n]; e += gridDim.x * blockDim.x) {
+        int g = 0;
+        while (e >= off[g + 1]) ++g;
+        const float *pp = partials + (size_t)e * pstride;
+        float s = 0.f;
+        for (int j = 0; j < heads.tiles[g]; ++j) s += pp[j];
+        score[(size_t)g * sstride + (e - off[g])] = (float)((double)heads.b[g] + (double)s);
+    }
 }
 
 }  // namespace
@@ -256,9 +331,7 @@ hydro_status tc_gemm_init(void **encode) {
         return HYDRO_ECUDA;
     }
     *encode = fn;
-    cudaError_t r = gemm_smem<256, kS256>();
-    if (r == cudaSuccess) r = gemm_smem<128, kS128>();
-    if (r == cudaSuccess) r = gemm_smem<64, kS64>();
+    cudaError_t r = cudaFuncSetAttribute(k_gemm_grouped_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
     if (r != cudaSuccess) {
         g_gemm_err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(r);
         return HYDRO_ECUDA;
@@ -266,31 +339,56 @@ hydro_status tc_gemm_init(void **encode) {
     return HYDRO_OK;
 }
 
-hydro_status tc_gemm_run(void *encode, const int *count, const __nv_bfloat16 *X, int K, const __nv_bfloat16 *W,
-                         const float *bias, int N, __nv_bfloat16 *Y, int max_rows, int sms, cudaStream_t st,
-                         unsigned int *err, const float *head_w, float *partials) {
-    if (!encode || !tc_gemm_supported(K, N) || max_rows < 1) {
-        g_gemm_err = "tensor-core GEMM not ready or shape unsupported";
+hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n, __nv_bfloat16 *Y, int ldy,
+                                 float *partials, int pstride, int sms, cudaStream_t st, unsigned int *err) {
+    if (!encode || n < 1 || n > kMaxGroups || (ldy % 8) != 0) {
+        g_gemm_err = "tensor-core GEMM not ready or bad group list";
         return HYDRO_EUNSUPPORTED;
     }
     EncodeFn enc = reinterpret_cast<EncodeFn>(encode);
-    const int NT = N % 256 == 0 ? 256 : N % 128 == 0 ? 128 : 64;
-    CUtensorMap tmA, tmB;
-    if (!encode2d(enc, &tmA, X, K, max_rows, 64, 128) || !encode2d(enc, &tmB, W, K, N, 64, NT)) {
-        g_gemm_err = "cuTensorMapEncodeTiled failed";
-        return HYDRO_ECUDA;
+    TcLaunch L;
+    memset(&L, 0, sizeof L);
+    int nt_max = 64;
+    long long tiles = 0;
+    for (int g = 0; g < n; ++g) {
+        const TcGemmGroup &h = groups[g];
+        if (!h.W) {   // rows only: the group takes its place in the stacking, no tiles
+            L.g[g].count = h.count;
+            continue;
+        }
+        if (!tc_gemm_supported(h.K, h.N) || (h.nt && (h.nt % 64 || h.nt > 256 || h.N % h.nt)) || h.x_rows < 1 || (h.ldx % 8) != 0 || h.ldx < h.K ||
+            (!h.head_w && h.N > ldy) || (h.head_w && h.N / (h.nt ? h.nt : col_tile(h.N)) > pstride)) {
+            g_gemm_err = "tensor-core GEMM: unsupported group shape";
+            return HYDRO_EUNSUPPORTED;
+        }
+        TcGroup &G = L.g[g];
+        G.K = h.K;
+        G.N = h.N;
+        G.NT = h.nt ? h.nt : col_tile(h.N);
+        G.count = h.count;
+        G.bias = h.bias;
+        G.head_w = h.head_w;
+        nt_max = G.NT > nt_max ? G.NT : nt_max;
+        if (!encode2d(enc, &G.tmA, h.X, h.K, h.x_rows, h.ldx, 64, 128) ||
+            !encode2d(enc, &G.tmB, h.W, h.K, h.N, h.K, 64, G.NT)) {
+            g_gemm_err = "cuTensorMapEncodeTiled failed";
+            return HYDRO_ECUDA;
+        }
+        tiles += ((h.x_rows + 127) / 128) * (h.N / G.NT);
     }
-    const long long tiles = (long long)((max_rows + 127) / 128) * (N / NT);
+    L.n = n;
+    L.Y = Y;
+    L.ldy = ldy;
+    L.partials = partials;
+    L.pstride = pstride;
+    L.err = err;
+    L.stage_bytes = kA_BYTES + nt_max * 128;
+    L.S = (kGemmSmem - 1280) / L.stage_bytes;
+    if (L.S > kMaxStages) L.S = kMaxStages;
+    L.tmem_cols = 2 * nt_max;
+    if (tiles == 0) return HYDRO_OK;   // only rows-only groups
     const int grid = (int)(tiles < sms ? tiles : sms);
-    if (NT == 256)
-        k_gemm_bf16_tc<256, kS256><<<grid, 192, GemmCfg<256, kS256>::SMEM, st>>>(tmA, tmB, count, K, N, bias, Y,
-                                                                                 head_w, partials, err);
-    else if (NT == 128)
-        k_gemm_bf16_tc<128, kS128><<<grid, 192, GemmCfg<128, kS128>::SMEM, st>>>(tmA, tmB, count, K, N, bias, Y,
-                                                                                 head_w, partials, err);
-    else
-        k_gemm_bf16_tc<64, kS64><<<grid, 192, GemmCfg<64, kS64>::SMEM, st>>>(tmA, tmB, count, K, N, bias, Y, head_w,
-                                                                             partials, err);
+    k_gemm_grouped_bf16_tc<<<grid, 192, kGemmSmem, st>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         g_gemm_err = std::string("launch: ") + cudaGetErrorString(e);
@@ -299,7 +397,14 @@ hydro_status tc_gemm_run(void *encode, const int *count, const __nv_bfloat16 *X,
     return HYDRO_OK;
 }
 
-int tc_gemm_col_tiles(int N) { return N / (N % 256 == 0 ? 256 : N % 128 == 0 ? 128 : 64); }
+hydro_status tc_gemm_run(void *encode, const int *count, const __nv_bfloat16 *X, int K, const __nv_bfloat16 *W,
+                         const float *bias, int N, __nv_bfloat16 *Y, int max_rows, int sms, cudaStream_t st,
+                         unsigned int *err, const float *head_w, float *partials) {
+    TcGemmGroup g{count, X, K, max_rows, W, bias, head_w, K, N, 0};
+    return tc_gemm_grouped_run(encode, &g, 1, Y, N, partials, tc_gemm_col_tiles(N), sms, st, err);
+}
+
+int tc_gemm_col_tiles(int N) { return N / col_tile(N); }
 
 void launch_gather_bf16(const int *count, const int *rows, const float *X, int ldx, int K, __nv_bfloat16 *out,
                         int max_rows, int sms, cudaStream_t st) {
@@ -308,6 +413,23 @@ void launch_gather_bf16(const int *count, const int *rows, const float *X, int l
     if (grid > sms * 8) grid = sms * 8;
     if (grid < 1) grid = 1;
     k_gather_bf16<<<grid, 256, 0, st>>>(count, rows, X, ldx, K, out);
+}
+
+void launch_gather_grouped_bf16(int n, const int *counts, const int *queues, int qstride, const float *const *Xp,
+                                int ldx, int K, __nv_bfloat16 *out, int max_rows, int sms, cudaStream_t st) {
+    long long work = (long long)max_rows * (K / 8);
+    int grid = (int)((work + 255) / 256);
+    if (grid > sms * 8) grid = sms * 8;
+    if (grid < 1) grid = 1;
+    k_gather_grouped_bf16<<<grid, 256, 0, st>>>(n, counts, queues, qstride, Xp, ldx, K, out);
+}
+
+void launch_head_finalize_grouped(int n, const int *counts, const TcHeads &heads, const float *partials, int pstride,
+                                  float *score, int sstride, int max_rows, int sms, cudaStream_t st) {
+    int grid = (max_rows + 255) / 256;
+    if (grid > sms * 4) grid = sms * 4;
+    if (grid < 1) grid = 1;
+    k_head_finalize_grouped<<<grid, 256, 0, st>>>(n, counts, heads, partials, pstride, score, sstride);
 }
 
 const char *tc_gemm_last_error() { return g_gemm_err.c_str(); }

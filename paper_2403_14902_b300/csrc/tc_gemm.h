@@ -8,6 +8,28 @@
 
 namespace hydro {
 
+constexpr int kMaxGroups = 8;
+
+// One layer of one group of a grouped launch.  The group's rows are stacked
+// after the earlier groups' rows (row offset = sum of the earlier counts).
+struct TcGemmGroup {
+    const int *count;            // rows of the group (device)
+    const __nv_bfloat16 *X;      // stacked operand, row stride ldx elements (multiple of 8)
+    int ldx;
+    long long x_rows;            // rows of X's allocation
+    const __nv_bfloat16 *W;      // [N][K]
+    const float *bias;           // [N]
+    const float *head_w;         // [N] one-output head folded into the epilogue, or nullptr (store Y)
+    int K, N;
+    int nt;                      // column-tile width 64/128/256 dividing N; 0: the widest that divides
+};
+// A group with W == nullptr contributes only its row count to the stacking.
+
+struct TcHeads {                 // per group: head bias and column tiles of the last hidden layer
+    float b[kMaxGroups];
+    int tiles[kMaxGroups];
+};
+
 // Layer shape K -> N runs on the tensor cores (K, N multiples of 64).
 bool tc_gemm_supported(int K, int N);
 // Look up the tensor-map encoder and set kernel attributes (once per query).
@@ -20,6 +42,18 @@ hydro_status tc_gemm_run(void *encode, const int *count, const __nv_bfloat16 *X,
                          const float *bias, int N, __nv_bfloat16 *Y, int max_rows, int sms, cudaStream_t st,
                          unsigned int *err, const float *head_w = nullptr, float *partials = nullptr);
 int tc_gemm_col_tiles(int N);
+// All groups' layers of one depth in one persistent launch.  Y (stacked,
+// row stride ldy) receives the groups without a head; partials (stacked, row
+// stride pstride) the head partials of the others.
+hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n, __nv_bfloat16 *Y, int ldy,
+                                 float *partials, int pstride, int sms, cudaStream_t st, unsigned int *err);
+// out[off_g + m] = bf16(X[queues[g * qstride + m]]) for m < counts[g], X = *Xp
+// (read on the device, so a captured launch follows the pointer's updates).
+void launch_gather_grouped_bf16(int n, const int *counts, const int *queues, int qstride, const float *const *Xp,
+                                int ldx, int K, __nv_bfloat16 *out, int max_rows, int sms, cudaStream_t st);
+// score[g * sstride + m] = heads.b[g] + sum_j partials[(off_g + m) * pstride + j], j < heads.tiles[g].
+void launch_head_finalize_grouped(int n, const int *counts, const TcHeads &heads, const float *partials, int pstride,
+                                  float *score, int sstride, int max_rows, int sms, cudaStream_t st);
 // out[m] = bf16(X[rows[m]]) for m < *count (K % 8 == 0, 16-byte aligned rows).
 void launch_gather_bf16(const int *count, const int *rows, const float *X, int ldx, int K, __nv_bfloat16 *out,
                         int max_rows, int sms, cudaStream_t st);

@@ -18,8 +18,25 @@ import datagen as D  # noqa: E402
 import oracle as O  # noqa: E402
 
 
+def mq_thresholds(name: str) -> dict:
+    """Per query and slot: the threshold leaving the slot's target
+    selectivity of the query's own calibration draw above it."""
+    w = D.workload(name)
+    t0 = time.time()
+    qs = D.mq_queries(w)
+    pool = D.mq_pool_weights(w)
+    th = []
+    for q, Q in enumerate(qs):
+        S = O.udf_scores("vec", D.mq_calib_tuples(w, q, qs), [pool[u] for u in Q["udfs"]])
+        th.append([O.threshold_for_selectivity(S[:, k], s) for k, s in enumerate(Q["selectivity"])])
+    return {"workload": name, "n_calib": w.n_calib, "thresholds": th, "oracle_seconds": round(time.time() - t0, 1),
+            "oracle_threads": O.threads()}
+
+
 def thresholds(name: str) -> dict:
     w = D.workload(name)
+    if w.extra and "queries" in w.extra:
+        return mq_thresholds(name)
     t0 = time.time()
     S = O.udf_scores(w.kind, D.calib_tuples(w), D.predicate_weights(w))
     th = [O.threshold_for_selectivity(S[:, i], s) for i, s in enumerate(w.selectivity)]

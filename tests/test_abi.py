@@ -42,17 +42,47 @@ int main(void) {
          sizeof(hydro_batch_info), sizeof(hydro_pred_stats), sizeof(hydro_calib_info));
   printf("%zu %zu %zu %zu\n", offsetof(hydro_query_config, stream), offsetof(hydro_udf_desc, head_bias),
          offsetof(hydro_batch_info, device_ms), offsetof(hydro_pred_stats, margin_fp32));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(hydro_session_config), offsetof(hydro_session_config, stream),
+         sizeof(hydro_step_query), offsetof(hydro_step_query, evaluated), sizeof(hydro_tile_choice),
+         offsetof(hydro_tile_choice, us));
   return 0;
 }
 ''')
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
-    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:3]
     assert [int(x) for x in a.split()] == [ctypes.sizeof(H.QueryConfig), ctypes.sizeof(H.UdfDesc),
                                           ctypes.sizeof(H.BatchInfo), ctypes.sizeof(H.PredStats),
                                           ctypes.sizeof(H.CalibInfo)]
     assert [int(x) for x in b.split()] == [H.QueryConfig.stream.offset, H.UdfDesc.head_bias.offset,
                                           H.BatchInfo.device_ms.offset, H.PredStats.margin_fp32.offset]
+    assert [int(x) for x in c.split()] == [ctypes.sizeof(H.SessionConfig), H.SessionConfig.stream.offset,
+                                          ctypes.sizeof(H.StepQuery), H.StepQuery.evaluated.offset,
+                                          ctypes.sizeof(H.TileChoice), H.TileChoice.us.offset]
+
+
+def test_session_defaults_and_rejections_without_a_device():
+    L = H.load()
+    cfg = H.SessionConfig()
+    L.hydro_session_default_config(ctypes.byref(cfg))
+    assert (cfg.precision, cfg.warmup_batches, cfg.stats_window, cfg.use_graphs, cfg.autotune,
+            cfg.max_in_flight) == (0, 1, 8, 1, 1, 2)
+    h = ctypes.c_void_p()
+    cfg.max_step_tuples = 1024
+    cfg.dim = 100                      # not a multiple of 64
+    assert L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
+    assert b"dim" in L.hydro_last_error()
+    cfg.dim = 512
+    cfg.max_step_tuples = 0
+    assert L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
+    cfg.max_step_tuples = 1024
+    cfg.max_in_flight = 9
+    assert L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
+    assert L.hydro_session_create(None, ctypes.byref(h)) == H.EINVAL
+    assert L.hydro_session_destroy(None) == H.EINVAL
+    assert L.hydro_session_poll(None, 0, None, None, None, 0) == H.EINVAL
+    sid = ctypes.c_int64()
+    assert L.hydro_session_submit(None, None, None, ctypes.byref(sid)) == H.EINVAL
 
 
 def test_default_config():

@@ -1,0 +1,262 @@
+"""GPU parity of multi-query sessions: many queries over one pool of MLP UDFs,
+each step stacking every query's next chunk, against the oracle run per query
+(each query alone, batches = its chunks, rank routing with lag 0)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import datagen as D
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def mq_thresholds():
+    with open(os.path.join(GOLDEN, "mq64_thresholds.json")) as f:
+        return json.load(f)["thresholds"]
+
+
+def make_session(w, qs, th, *, precision="fp32", cap, graphs=True, autotune=True, warmup=1, window=8,
+                 queries=None):
+    import paper_2403_14902_b300 as H
+    s = H.Session(dim=w.dim, max_step_tuples=cap, precision=precision, graphs=graphs, autotune=autotune,
+                  warmup=warmup, window=window)
+    for layers in D.mq_pool_weights(w):
+        s.add_udf(layers)
+    for q in (range(len(qs)) if queries is None else queries):
+        s.add_query(qs[q]["udfs"], th[q])
+    return s
+
+
+def run_session(s, streams, chunk):
+    """All steps until every stream is consumed; per step (counts, bits,
+    per-query report)."""
+    import torch
+
+    import paper_2403_14902_b300 as H
+    done = [0] * len(streams)
+    out = []
+    while any(done[q] < streams[q].shape[0] for q in range(len(streams))) or not out:
+        rows, counts = D.mq_stacked_step(streams, done, chunk)
+        Xd = torch.from_numpy(rows).cuda() if rows.shape[0] else torch.empty((0, streams[0].shape[1]), device="cuda")
+        sid = s.submit(Xd, counts)
+        words, per, ms = s.poll(sid)
+        out.append((counts, H.bits_from_words(words, rows.shape[0]), per))
+        done = [d + c for d, c in zip(done, counts)]
+    return out
+
+
+def oracle_per_query(w, qs, th, streams, chunk, queries, warmup=1, window=8):
+    pool = D.mq_pool_weights(w)
+    sims = {}
+    for k, q in enumerate(queries):
+        Q = qs[q]
+        S = O.udf_scores("vec", streams[k], [pool[u] for u in Q["udfs"]])
+        pm = O.pass_matrix(S, th[q])
+        costs = [O.mlp_flops(w.udfs[u]) for u in Q["udfs"]]
+        sims[k] = O.simulate(pm, chunk, policy="rank", costs=costs, warmup=warmup, window=window, lag=0)
+    return sims
+
+
+def check_steps(res, sims, n_queries):
+    batch_of = [0] * n_queries
+    for counts, bits, per in res:
+        off = 0
+        for k in range(n_queries):
+            c = counts[k]
+            r = per[k]
+            if c == 0:
+                assert r["batch"] == -1 and r["n"] == 0
+                continue
+            b = batch_of[k]
+            s = sims[k][b]
+            assert r["batch"] == b
+            assert np.array_equal(bits[off:off + c], s["bits"]), f"query {k} batch {b}: pass set"
+            assert r["warmup"] == s["warmup"]
+            assert r["order"] == s["order"], f"query {k} batch {b}: order {r['order']} vs {s['order']}"
+            assert r["evaluated"] == s["counts"].tolist(), f"query {k} batch {b}: counts"
+            assert r["passed"] == s["passed"].tolist(), f"query {k} batch {b}: passed"
+            assert r["n_pass"] == int(s["bits"].sum())
+            batch_of[k] += 1
+            off += c
+    for k in range(n_queries):
+        assert batch_of[k] == len(sims[k])
+
+
+@pytest.fixture(scope="module")
+def small():
+    """Ten queries of the 64-query workload, each cut to at most 2,500 of its
+    tuples, chunks of 640: several steps, ragged tails, queries finishing at
+    different steps."""
+    w = D.workload("mq64")
+    qs = D.mq_queries(w)
+    th = mq_thresholds()
+    queries = list(range(10))
+    streams = [D.mq_tuples(w, q, min(qs[q]["n"], 300 + 220 * q), qs) for q in queries]
+    chunk = 640
+    sims = oracle_per_query(w, qs, th, streams, chunk, queries)
+    calib = np.concatenate([D.mq_calib_tuples(w, q, qs)[:128] for q in queries])
+    return dict(w=w, qs=qs, th=th, queries=queries, streams=streams, chunk=chunk, sims=sims, calib=calib)
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_session_fp32_exact(small, graphs):
+    import torch
+    s = make_session(small["w"], small["qs"], small["th"], cap=len(small["queries"]) * small["chunk"],
+                     graphs=graphs, queries=small["queries"])
+    s.calibrate(torch.from_numpy(small["calib"]).cuda())
+    res = run_session(s, small["streams"], small["chunk"])
+    check_steps(res, small["sims"], len(small["queries"]))
+    s.close()
+
+
+@pytest.mark.parametrize("autotune", [True, False])
+def test_session_bf16_exact(small, autotune):
+    import torch
+    s = make_session(small["w"], small["qs"], small["th"], precision="bf16",
+                     cap=len(small["queries"]) * small["chunk"], autotune=autotune, queries=small["queries"])
+    info = s.calibrate(torch.from_numpy(small["calib"]).cuda())
+    for d in info:
+        assert d["margin_lowp"] >= 4 * d["max_err_lowp"] > 0
+    res = run_session(s, small["streams"], small["chunk"])
+    check_steps(res, small["sims"], len(small["queries"]))
+    assert sum(sum(r["recheck_fp32"]) for _, _, per in res for r in per) > 0
+    if autotune:
+        t = s.tuning()
+        assert len(t) == sum(len(d) - 2 for d in small["w"].udfs)
+        for rec in t:
+            assert rec["tile_n"] in (64, 128, 256) and rec["N"] % rec["tile_n"] == 0
+            assert rec["us"][rec["tile_n"].bit_length() - 7] == min(u for u in rec["us"] if u > 0)
+    s.close()
+
+
+def test_session_wide_margins_recheck_everything(small):
+    import torch
+    s = make_session(small["w"], small["qs"], small["th"], precision="bf16",
+                     cap=len(small["queries"]) * small["chunk"], queries=small["queries"])
+    s.calibrate(torch.from_numpy(small["calib"]).cuda())
+    for u in range(8):
+        s.set_margins(u, 1e3, 1e3)
+    res = run_session(s, small["streams"], small["chunk"])
+    check_steps(res, small["sims"], len(small["queries"]))
+    ev = sum(sum(r["evaluated"]) for _, _, per in res for r in per)
+    assert sum(sum(r["recheck_fp64"]) for _, _, per in res for r in per) == ev
+    s.close()
+
+
+def test_session_scores_against_oracle(small):
+    import torch
+    w = small["w"]
+    s = make_session(w, small["qs"], small["th"], precision="bf16", cap=1000, queries=small["queries"])
+    X = small["streams"][3][:1000]
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    out = torch.empty(X.shape[0], dtype=torch.float64, device="cuda")
+    pool = D.mq_pool_weights(w)
+    for u in range(8):
+        S = O.udf_scores("vec", X, [pool[u]])[:, 0]
+        rms = np.sqrt((S ** 2).mean())
+        s.udf_scores(u, "fp64", Xd, out)
+        assert np.max(np.abs(out.cpu().numpy() - S)) <= 1e-9 * max(1.0, np.abs(S).max())
+        s.udf_scores(u, "fp32", Xd, out)
+        assert np.max(np.abs(out.cpu().numpy() - S) / np.maximum(np.abs(S), rms)) < 1e-3
+        s.udf_scores(u, "bf16", Xd, out)
+        assert np.median(np.abs(out.cpu().numpy() - S) / np.maximum(np.abs(S), rms)) < 1e-2
+    s.close()
+
+
+def test_session_idle_queries_and_empty_step(small):
+    """Steps where some queries sit out (count 0), a one-tuple chunk, and an
+    empty step: the idle queries' batch numbers do not advance."""
+    import torch
+    w, qs, th = small["w"], small["qs"], small["th"]
+    queries = [0, 1, 2]
+    streams = [D.mq_tuples(w, q, 700, qs) for q in queries]
+    plan = [[300, 0, 1], [0, 0, 0], [300, 300, 0], [100, 400, 299]]   # per step, per query
+    s = make_session(w, qs, th, cap=1024, queries=queries)
+    import paper_2403_14902_b300 as H
+    done = [0, 0, 0]
+    batches = [[] for _ in queries]
+    for counts in plan:
+        rows = np.concatenate([streams[k][done[k]:done[k] + c] for k, c in enumerate(counts)])
+        Xd = torch.from_numpy(np.ascontiguousarray(rows)).cuda() if len(rows) else torch.empty((0, w.dim), device="cuda")
+        sid = s.submit(Xd, counts)
+        words, per, _ = s.poll(sid)
+        bits = H.bits_from_words(words, len(rows))
+        off = 0
+        for k, c in enumerate(counts):
+            if c:
+                batches[k].append((c, bits[off:off + c], per[k]))
+            else:
+                assert per[k]["batch"] == -1
+            off += c
+            done[k] += c
+    pool = D.mq_pool_weights(w)
+    for k, q in enumerate(queries):
+        X = np.concatenate([streams[k][:done[k]]])
+        pm = O.pass_matrix(O.udf_scores("vec", X, [pool[u] for u in qs[q]["udfs"]]), th[q])
+        costs = [O.mlp_flops(w.udfs[u]) for u in qs[q]["udfs"]]
+        lo = 0
+        for b, (c, bits, r) in enumerate(batches[k]):
+            # the query's batches are its non-empty chunks, of varying size
+            assert r["batch"] == b
+            assert np.array_equal(bits, O.result_bits(pm[lo:lo + c]))
+            if b == 0:
+                assert r["warmup"] and r["evaluated"] == [c] * len(costs)
+            else:
+                assert r["evaluated"] == O.static_counts(pm[lo:lo + c], r["order"]).tolist()
+            lo += c
+    s.close()
+
+
+def test_session_full_workload_sampled():
+    """All 64 queries (1.6 M tuples), chunks of 4,096, BF16 with graphs and
+    autotuning: sampled tuples of every query against the oracle, and per
+    step the counting identities of eager dropping along each query's order."""
+    import torch
+
+    import paper_2403_14902_b300 as H
+    w = D.workload("mq64")
+    qs = D.mq_queries(w)
+    th = mq_thresholds()
+    streams = [D.mq_tuples(w, q, None, qs) for q in range(len(qs))]
+    chunk = w.batch
+    s = make_session(w, qs, th, precision="bf16", cap=len(qs) * chunk)
+    calib = np.concatenate([D.mq_calib_tuples(w, q, qs)[:64] for q in range(len(qs))])
+    s.calibrate(torch.from_numpy(calib).cuda())
+    bits_q = [[] for _ in qs]
+    done = [0] * len(qs)
+    while any(done[q] < streams[q].shape[0] for q in range(len(qs))):
+        rows, counts = D.mq_stacked_step(streams, done, chunk)
+        sid = s.submit(torch.from_numpy(rows).cuda(), counts)
+        words, per, _ = s.poll(sid)
+        bits = H.bits_from_words(words, rows.shape[0])
+        off = 0
+        for q, c in enumerate(counts):
+            if c == 0:
+                continue
+            r = per[q]
+            bits_q[q].append(bits[off:off + c])
+            ev = r["evaluated"]
+            if r["warmup"]:
+                assert ev == [c] * len(ev)
+            else:
+                o = r["order"]
+                assert ev[o[0]] == c
+                for a, b in zip(o[:-1], o[1:]):
+                    assert ev[b] == r["passed"][a]
+                assert r["n_pass"] == r["passed"][o[-1]]
+            off += c
+        done = [d + c for d, c in zip(done, counts)]
+    pool = D.mq_pool_weights(w)
+    rng = np.random.default_rng(11)
+    for q in range(len(qs)):
+        b = np.concatenate(bits_q[q])
+        n = b.shape[0]
+        idx = np.unique(np.concatenate([rng.choice(n, min(n, 60), replace=False), np.flatnonzero(b)[:20]]))
+        S = O.udf_scores("vec", streams[q][idx], [pool[u] for u in qs[q]["udfs"]])
+        assert np.array_equal(b[idx], O.result_bits(O.pass_matrix(S, th[q]))), f"query {q}"
+    s.close()
