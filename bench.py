@@ -719,12 +719,14 @@ def ours_mq64(args):
             run_all(s, stats=stats)
             entry["prof"], _ = s.profile_read()
             s.profile(False)
+            # BF16 level: every evaluation; split-BF16 level: its rechecks over K x 3
             gemm_flops = 0
             for per in stats:
                 for q, r in enumerate(per):
                     for k, u in enumerate(qs[q]["udfs"]):
-                        gemm_flops += r["evaluated"][k] * mq_hidden_flops(w, u)
+                        gemm_flops += (r["evaluated"][k] + 3 * r["recheck_split"][k]) * mq_hidden_flops(w, u)
             entry["gemm_flops"] = gemm_flops
+            entry["recheck_split"] = sum(sum(r["recheck_split"]) for per in stats for r in per)
             entry["recheck_fp32"] = sum(sum(r["recheck_fp32"]) for per in stats for r in per)
             entry["recheck_fp64"] = sum(sum(r["recheck_fp64"]) for per in stats for r in per)
             entry["evaluated"] = sum(sum(r["evaluated"]) for per in stats for r in per)
@@ -824,7 +826,8 @@ def ours_mq64(args):
         "speedup_vs_sequential_fp32": round(a["value"] / results["sequential_fp32"]["value"], 3),
         "speedup_vs_session_fp32": round(a["value"] / results["fp32_graphs"]["value"], 3),
         "pass_count_per_step": a["pass_count"],
-        "recheck": {"evaluated": a["evaluated"], "fp32": a["recheck_fp32"], "fp64": a["recheck_fp64"]},
+        "recheck": {"evaluated": a["evaluated"], "split_bf16": a["recheck_split"], "fp32": a["recheck_fp32"],
+                    "fp64": a["recheck_fp64"]},
         "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3)} for k, v in a["prof"].items()},
         "tuning": [{"udf": t["udf"], "layer": t["layer"], "K": t["K"], "N": t["N"], "tile_n": t["tile_n"],
                     "us": [round(x, 2) for x in t["us"]]} for t in a["tuning"]],

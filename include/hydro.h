@@ -85,9 +85,14 @@ enum {
                               margin_tf32 go on), then in FP32 on CUDA cores (within
                               margin_fp32 go on to FP64); MLP UDFs in FP32 then FP64 */
     HYDRO_PREC_FP64 = 2,   /* FP64 (only for hydro_udf_scores) */
-    HYDRO_PREC_TF32X3 = 3  /* FP32-accurate 3xTF32 on the tensor cores (hi*hi + hi*lo + lo*hi);
+    HYDRO_PREC_TF32X3 = 3, /* FP32-accurate 3xTF32 on the tensor cores (hi*hi + hi*lo + lo*hi);
                               the first BF16 recheck level of CNN UDFs (hydro_udf_scores on
                               BF16 CNN queries) */
+    HYDRO_PREC_BF16X3 = 4  /* split BF16 on the tensor cores: x = hi + lo with hi = bf16(x),
+                              lo = bf16(x - hi), products hi*hi + hi*lo + lo*hi in one BF16 GEMM
+                              over [hi | hi | lo] x [W_hi | W_lo | W_hi] (about 16 significant bits);
+                              the first recheck level of BF16 sessions
+                              (hydro_session_udf_scores) */
 };
 
 /* Where the router's per-tuple cost comes from. */
@@ -386,6 +391,7 @@ typedef struct hydro_step_query {
     int32_t order[HYDRO_MAX_PREDICATES];         /* slots in evaluation order (first n_preds) */
     int64_t evaluated[HYDRO_MAX_PREDICATES];     /* per slot: tuples evaluated at working precision */
     int64_t passed[HYDRO_MAX_PREDICATES];        /* per slot: of those, passed */
+    int64_t recheck_split[HYDRO_MAX_PREDICATES]; /* per slot: re-evaluated in split BF16 (BF16 sessions) */
     int64_t recheck_fp32[HYDRO_MAX_PREDICATES];  /* per slot: re-evaluated in FP32 (BF16 sessions) */
     int64_t recheck_fp64[HYDRO_MAX_PREDICATES];  /* per slot: re-evaluated in FP64 */
 } hydro_step_query;
@@ -415,20 +421,24 @@ HYDRO_API hydro_status hydro_session_add_udf(hydro_session *s, const hydro_udf_d
 HYDRO_API hydro_status hydro_session_add_query(hydro_session *s, int32_t n_preds, const int32_t *udfs,
                                                const double *thresholds, int32_t *out_query);
 
-/* Margins of pool UDF udf (absolute score units): a working-precision score
- * within margin_lowp (BF16) or margin_fp32 (FP32 scores) of a threshold is
- * re-evaluated at the next precision (BF16 -> FP32 -> FP64). */
+/* Margins of pool UDF udf (absolute score units, >= 0): a score within its
+ * level's margin of a threshold is re-evaluated at the next level (BF16
+ * sessions: BF16 -> split BF16 -> FP32 -> FP64; FP32 sessions: FP32 -> FP64).
+ * Defaults: margin_lowp 0.02, margin_split 1e-3, margin_fp32 1e-5.  Before
+ * the first submit. */
 HYDRO_API hydro_status hydro_session_set_margins(hydro_session *s, int32_t udf, double margin_lowp,
-                                                 double margin_fp32);
+                                                 double margin_split, double margin_fp32);
 
 /* Calibrate every pool UDF's margins on n device tuples, with the rule of
- * hydro_calibrate (margin_fp32 = 16 x max FP32 error, margin_lowp raised to
- * 4 x max BF16 error).  info[n_udfs] nullable.  Synchronous. */
+ * hydro_calibrate (margin_fp32 = 16 x max FP32 error, margin_split = 8 x max
+ * split-BF16 error, each at least 1e-9 x max |score|; margin_lowp raised to
+ * 4 x max BF16 error).  info[n_udfs] nullable (max_err_tf32 / margin_tf32
+ * report the split-BF16 level).  Synchronous. */
 HYDRO_API hydro_status hydro_session_calibrate(hydro_session *s, const void *d_tuples, int64_t n,
                                                hydro_calib_info *info);
 
-/* Scores of pool UDF udf on n device tuples at HYDRO_PREC_FP64/FP32/BF16 into
- * d_scores (device, n doubles).  Synchronous. */
+/* Scores of pool UDF udf on n device tuples at HYDRO_PREC_FP64/FP32/BF16/
+ * BF16X3 into d_scores (device, n doubles).  Synchronous. */
 HYDRO_API hydro_status hydro_session_udf_scores(hydro_session *s, int32_t udf, int32_t prec, const void *d_tuples,
                                                 int64_t n, double *d_scores);
 

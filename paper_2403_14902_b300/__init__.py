@@ -26,7 +26,7 @@ OK, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEOUT, ESTATE, EDEVICE, ENOTFOUND, EUNSUPP
 
 TUPLE_F32, TUPLE_U8_FRAME = 0, 1
 POLICIES = {"rank": 0, "static": 1, "all": 2, "cost": 3, "selectivity": 4, "learned": 5}
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp64": 2, "tf32x3": 3}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp64": 2, "tf32x3": 3, "bf16x3": 4}
 UDF_MLP, UDF_CNN = 0, 1
 
 EXPORTED = ["hydro_default_config", "hydro_create_query", "hydro_add_predicate", "hydro_add_embedding",
@@ -95,7 +95,7 @@ class StepQuery(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_pass", ctypes.c_int64), ("batch", ctypes.c_int64),
                 ("warmup", ctypes.c_int32), ("order", ctypes.c_int32 * MAX_PREDICATES),
                 ("evaluated", ctypes.c_int64 * MAX_PREDICATES), ("passed", ctypes.c_int64 * MAX_PREDICATES),
-                ("recheck_fp32", ctypes.c_int64 * MAX_PREDICATES),
+                ("recheck_split", ctypes.c_int64 * MAX_PREDICATES), ("recheck_fp32", ctypes.c_int64 * MAX_PREDICATES),
                 ("recheck_fp64", ctypes.c_int64 * MAX_PREDICATES)]
 
 
@@ -146,7 +146,7 @@ def load():
     L.hydro_session_create.argtypes = [P(SessionConfig), P(vp)]
     L.hydro_session_add_udf.argtypes = [vp, P(UdfDesc), P(i32)]
     L.hydro_session_add_query.argtypes = [vp, i32, P(i32), P(f64), P(i32)]
-    L.hydro_session_set_margins.argtypes = [vp, i32, f64, f64]
+    L.hydro_session_set_margins.argtypes = [vp, i32, f64, f64, f64]
     L.hydro_session_calibrate.argtypes = [vp, vp, i64, P(CalibInfo)]
     L.hydro_session_udf_scores.argtypes = [vp, i32, i32, vp, i64, vp]
     L.hydro_session_submit.argtypes = [vp, vp, P(i32), P(i64)]
@@ -457,8 +457,8 @@ class Session:
         self.queries.append(list(udfs))
         return out.value
 
-    def set_margins(self, udf: int, lowp: float, fp32: float):
-        _check(load().hydro_session_set_margins(self._h, udf, lowp, fp32), "hydro_session_set_margins")
+    def set_margins(self, udf: int, lowp: float, split: float, fp32: float):
+        _check(load().hydro_session_set_margins(self._h, udf, lowp, split, fp32), "hydro_session_set_margins")
 
     def calibrate(self, tuples) -> list:
         info = (CalibInfo * MAX_POOL)()
@@ -493,7 +493,7 @@ class Session:
             P = len(self.queries[q])
             out.append(dict(n=r.n, n_pass=r.n_pass, batch=r.batch, warmup=bool(r.warmup), order=list(r.order[:P]),
                             evaluated=list(r.evaluated[:P]), passed=list(r.passed[:P]),
-                            recheck_fp32=list(r.recheck_fp32[:P]), recheck_fp64=list(r.recheck_fp64[:P])))
+                            recheck_split=list(r.recheck_split[:P]), recheck_fp32=list(r.recheck_fp32[:P]), recheck_fp64=list(r.recheck_fp64[:P])))
         return words, out, ms.value
 
     def profile(self, enable: bool = True):

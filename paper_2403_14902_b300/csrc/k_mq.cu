@@ -47,7 +47,7 @@ __device__ __forceinline__ void warp_count(unsigned long long *p, bool want) {
 __device__ __forceinline__ unsigned long long *ctr(StatRow *r, int field) {
     return reinterpret_cast<unsigned long long *>(r) + field;
 }
-enum { F_EVAL = 0, F_PASS = 1, F_R32 = 3, F_R64 = 4 };
+enum { F_EVAL = 0, F_PASS = 1, F_RX3 = 2, F_R32 = 3, F_R64 = 4 };
 
 int grid_for(long long work, int per_block, int sms, int per_sm) {
     long long g = (work + per_block - 1) / per_block;
@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(256) k_mq_partition(MqDev d, int r) {
             const int slot = d.order[q * kMqSlots + r];
             g = d.udf[q * kMqSlots + slot];
         }
-        const int pos = warp_append(live ? &d.rc->q[g] : nullptr, live);
-        if (live) d.queues[(size_t)g * d.cap + pos] = e;
+        const int pos = warp_append(live ? &d.rc->n[LV_MAIN][g] : nullptr, live);
+        if (live) d.list[LV_MAIN][(size_t)g * d.cap + pos] = e;
     }
 }
 
@@ -228,20 +228,25 @@ __global__ void __launch_bounds__(256) k_mq_dot_f32(MqLayers L, float *score, in
     }
 }
 
-// Decide the entries of a level.  Level 0: the round queues' working-
-// precision scores; a score within the margin of its tuple's threshold goes
-// to the next level's band queue (BF16: the FP32 band, else the FP64 band).
-// Level 1: the FP32 band's scores, margin_fp32, undecided -> FP64 band.
-__global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int level, int bf16) {
-    const int *cnts = level == 0 ? d.rc->q : d.rc->b32;
-    const int *lists = level == 0 ? d.queues : d.bq32;
-    const float *sc = level == 0 ? d.score : d.rscore;
-    const float *margin = (level == 0 && bf16) ? d.margin_lowp : d.margin_fp32;
-    int *next_cnt = (level == 0 && bf16) ? d.rc->b32 : d.rc->b64;
-    int *next_list = (level == 0 && bf16) ? d.bq32 : d.bq64;
+// Decide the entries of level `in`: the score of each list entry against
+// its tuple's own threshold; within the level's margin the entry goes on to
+// level `out`'s list of the same group.  Level 0 counts the evaluations and
+// marks the slot visited; levels 1 and 2 count their rechecks (the FP64
+// level counts its own).  The split-BF16 level runs only on a band of at
+// least kMinSplitRows rows: below that its launches return at once and every
+// entry passes on to the FP32 level unscored.
+__global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int in, int out) {
+    const int *cnts = d.rc->n[in];
+    const int *lists = d.list[in];
+    const float *sc = d.score[in];
+    const float *margin = d.margin[in];
+    int *next_cnt = d.rc->n[out];
+    int *next_list = d.list[out];
+    const int rfield = in == LV_X3 ? F_RX3 : in == LV_F32 ? F_R32 : -1;
     int off[kMqPool + 1];
     off[0] = 0;
     for (int g = 0; g < d.G; ++g) off[g + 1] = off[g] + cnts[g];
+    const bool skipped = in == LV_X3 && off[d.G] < kMinSplitRows;
     for (int i0 = blockIdx.x * blockDim.x; i0 < off[d.G]; i0 += gridDim.x * blockDim.x) {
         const int i = i0 + threadIdx.x;
         const bool live = i < off[d.G];
@@ -253,39 +258,140 @@ __global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int level, 
             e = lists[(size_t)g * d.cap + m];
             q = d.qid[e];
             slot = d.order[q * kMqSlots + r];
-            const double t = d.thr[q * kMqSlots + slot];
-            const double s = (double)sc[(size_t)g * d.cap + m];
-            inband = fabs(s - t) <= (double)margin[g];
-            pass = !inband && s > t;
-            if (level == 0) d.visited[e] |= (unsigned char)(1u << slot);
-            d.ok[e] = (unsigned char)pass;
-            if (pass) d.label[e] |= (unsigned char)(1u << slot);
+            if (skipped) {
+                inband = true;
+            } else {
+                const double t = d.thr[q * kMqSlots + slot];
+                const double s = (double)sc[(size_t)g * d.cap + m];
+                inband = fabs(s - t) <= (double)margin[g];
+                pass = !inband && s > t;
+                d.ok[e] = (unsigned char)pass;
+                if (pass) d.label[e] |= (unsigned char)(1u << slot);
+            }
+            if (in == LV_MAIN) d.visited[e] |= (unsigned char)(1u << slot);
         }
         StatRow *row = d.rows + q * kMqSlots + slot;
-        if (level == 0) warp_count(ctr(row, F_EVAL), live);
+        if (in == LV_MAIN) warp_count(ctr(row, F_EVAL), live);
         warp_count(ctr(row, F_PASS), live && pass);
         const int pos = warp_append(live && inband ? &next_cnt[g] : nullptr, live && inband);
         if (live && inband) next_list[(size_t)g * d.cap + pos] = e;
-        // entries going on to FP64 are counted by the FP64 recheck
-        if (level == 0 && bf16) warp_count(ctr(row, F_R32), live && inband);
+        if (rfield >= 0) warp_count(ctr(row, rfield), live && !skipped);
     }
 }
 
-// FP64 recheck of the FP64 band: a block per entry runs its UDF in FP64 from
-// the tuple and decides the test exactly (no margin).
+// Band levels run layer-parallel: a warp per (entry, output neuron) of one
+// hidden layer, entries stacked group by group (the first `cap_lv` of the
+// level), activations in T (float: the FP32 level, double: FP64).
+__device__ __forceinline__ void band_offsets(const MqDev &d, const GroupedMlps &mlps, int level, int cap_lv,
+                                             int depth, int *off, int *wstart) {
+    const int *cnts = d.rc->n[level];
+    off[0] = 0;
+    wstart[0] = 0;
+    for (int g = 0; g < d.G; ++g) {
+        const int lim = max(0, min(cnts[g], cap_lv - off[g]));
+        off[g + 1] = off[g] + lim;
+        const MlpDev &m = mlps.m[g];
+        wstart[g + 1] = wstart[g] + (depth >= 0 && depth + 1 < m.n_layers ? lim * m.dims[depth + 1] : 0);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mq_band_layer(MqDev d, GroupedMlps mlps, int level, int depth, T *act0,
+                                                       T *act1, int ld, int cap_lv) {
+    int off[kMqPool + 1], wstart[kMqPool + 1];
+    band_offsets(d, mlps, level, cap_lv, depth, off, wstart);
+    const T *in_act = (depth & 1) ? act0 : act1;   // depth - 1 wrote act[(depth - 1) & 1]
+    T *out_act = (depth & 1) ? act1 : act0;
+    const float *X = d.hdr->X;
+    const int *list = d.list[level];
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < wstart[d.G]; w += (gridDim.x * blockDim.x) >> 5) {
+        int g = 0;
+        while (w >= wstart[g + 1]) ++g;
+        const MlpDev &m = mlps.m[g];
+        const int N = m.dims[depth + 1], K = m.dims[depth];
+        const int local = w - wstart[g];
+        const int el = local / N, o = local % N;
+        const int j = off[g] + el;
+        const float *wr = m.W[depth] + (size_t)o * K;
+        T s = 0;
+        if (depth == 0) {
+            const float *x = X + (size_t)list[(size_t)g * d.cap + el] * d.dim;
+            for (int k = lane_id(); k < K; k += 32) s += (T)wr[k] * (T)x[k];
+        } else {
+            const T *x = in_act + (size_t)j * ld;
+            for (int k = lane_id(); k < K; k += 32) s += (T)wr[k] * x[k];
+        }
+#pragma unroll
+        for (int dd = 16; dd > 0; dd >>= 1) s += __shfl_xor_sync(0xffffffffu, s, dd);
+        if (lane_id() == 0) {
+            s += (T)m.b[depth][o];
+            out_act[(size_t)j * ld + o] = s > (T)0 ? s : (T)0;
+        }
+    }
+}
+
+// The one-output last layer, a warp per entry.  FP32 level: the score into
+// the level's score list (decided by the level's classify).  FP64 level: the
+// exact verdict and its statistics.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mq_band_final(MqDev d, GroupedMlps mlps, int level, int r, T *act0,
+                                                       T *act1, int ld, int cap_lv) {
+    int off[kMqPool + 1], wstart[kMqPool + 1];
+    band_offsets(d, mlps, level, cap_lv, -1, off, wstart);
+    const float *X = d.hdr->X;
+    const int *list = d.list[level];
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < off[d.G]; j += (gridDim.x * blockDim.x) >> 5) {
+        int g = 0;
+        while (j >= off[g + 1]) ++g;
+        const MlpDev &m = mlps.m[g];
+        const int L = m.n_layers, K = m.dims[L - 1];
+        const int el = j - off[g];
+        const int e = list[(size_t)g * d.cap + el];
+        const float *wr = m.W[L - 1];
+        T s = 0;
+        if (L == 1) {
+            const float *x = X + (size_t)e * d.dim;
+            for (int k = lane_id(); k < K; k += 32) s += (T)wr[k] * (T)x[k];
+        } else {
+            const T *x = (((L - 2) & 1) ? act1 : act0) + (size_t)j * ld;
+            for (int k = lane_id(); k < K; k += 32) s += (T)wr[k] * x[k];
+        }
+#pragma unroll
+        for (int dd = 16; dd > 0; dd >>= 1) s += __shfl_xor_sync(0xffffffffu, s, dd);
+        if (lane_id() != 0) continue;
+        s += (T)m.b[L - 1][0];
+        if (sizeof(T) == 4) {
+            d.score[LV_F32][(size_t)g * d.cap + el] = (float)s;
+            continue;
+        }
+        const int q = d.qid[e];
+        const int slot = d.order[q * kMqSlots + r];
+        const bool pass = (double)s > d.thr[q * kMqSlots + slot];
+        d.ok[e] = (unsigned char)pass;
+        StatRow *row = d.rows + q * kMqSlots + slot;
+        if (pass) {
+            d.label[e] |= (unsigned char)(1u << slot);
+            atomicAdd(ctr(row, F_PASS), 1ull);
+        }
+        atomicAdd(ctr(row, F_R64), 1ull);
+    }
+}
+
+// FP64 level, entries beyond the first cap64 (counted over all groups): a
+// block per entry runs its UDF in FP64 from the tuple and decides exactly.
 __global__ void __launch_bounds__(256) k_mq_band64(MqDev d, int r, GroupedMlps mlps) {
     extern __shared__ unsigned char smem_raw[];
     double *h = reinterpret_cast<double *>(smem_raw);
     double *g2 = h + mlps.max_width;
     int off[kMqPool + 1];
     off[0] = 0;
-    for (int g = 0; g < d.G; ++g) off[g + 1] = off[g] + d.rc->b64[g];
+    for (int g = 0; g < d.G; ++g) off[g + 1] = off[g] + d.rc->n[LV_F64][g];
     const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const float *X = d.hdr->X;
-    for (int j = blockIdx.x; j < off[d.G]; j += gridDim.x) {
+    for (int j = d.cap64 + blockIdx.x; j < off[d.G]; j += gridDim.x) {
         int g = 0;
         while (j >= off[g + 1]) ++g;
-        const int e = d.bq64[(size_t)g * d.cap + (j - off[g])];
+        const int e = d.list[LV_F64][(size_t)g * d.cap + (j - off[g])];
         const MlpDev &mlp = mlps.m[g];
         const float *x = X + (size_t)e * d.dim;
         for (int k = threadIdx.x; k < mlp.dims[0]; k += blockDim.x) h[k] = (double)x[k];
@@ -347,11 +453,7 @@ __global__ void __launch_bounds__(256) k_mq_survivors(MqDev d, int r) {
 
 __global__ void k_mq_clear_round(RoundCounters *rc) {
     const int i = threadIdx.x;
-    if (i < kMqPool) {
-        rc->q[i] = 0;
-        rc->b32[i] = 0;
-        rc->b64[i] = 0;
-    }
+    if (i < LV_N * kMqPool) (&rc->n[0][0])[i] = 0;
 }
 
 // Result bitmap (bit e: every slot of e's query passed) and passes per query.
@@ -444,7 +546,7 @@ void mq_launch_router(const MqDev &d, const MqHist &h, cudaStream_t st) {
 }
 
 void mq_launch_partition(const MqDev &d, int r, cudaStream_t st, int sms) {
-    if (r > 0) k_mq_clear_round<<<1, 32, 0, st>>>(d.rc);
+    if (r > 0) k_mq_clear_round<<<1, LV_N * kMqPool, 0, st>>>(d.rc);
     k_mq_partition<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r);
 }
 
@@ -456,13 +558,24 @@ void mq_launch_dots_f32(const MqLayers &L, float *score, int sstride, cudaStream
     k_mq_dot_f32<<<sms * 8, 256, 0, st>>>(L, score, sstride);
 }
 
-void mq_launch_classify(const MqDev &d, int r, int level, bool bf16, cudaStream_t st, int sms) {
-    k_mq_classify<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r, level, bf16 ? 1 : 0);
+void mq_launch_classify(const MqDev &d, int r, int in, int out, cudaStream_t st, int sms) {
+    k_mq_classify<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r, in, out);
 }
 
-void mq_launch_band64(const MqDev &d, int r, const GroupedMlps &mlps, cudaStream_t st, int sms) {
+void mq_launch_band32(const MqDev &d, int r, const GroupedMlps &mlps, int max_hidden, float *act0, float *act1,
+                      int ld, cudaStream_t st, int sms) {
+    for (int depth = 0; depth < max_hidden; ++depth)
+        k_mq_band_layer<float><<<sms * 8, 256, 0, st>>>(d, mlps, LV_F32, depth, act0, act1, ld, d.cap);
+    k_mq_band_final<float><<<sms * 2, 256, 0, st>>>(d, mlps, LV_F32, r, act0, act1, ld, d.cap);
+}
+
+void mq_launch_band64(const MqDev &d, int r, const GroupedMlps &mlps, int max_hidden, cudaStream_t st, int sms) {
+    for (int depth = 0; depth < max_hidden; ++depth)
+        k_mq_band_layer<double><<<sms * 8, 256, 0, st>>>(d, mlps, LV_F64, depth, d.act64[0], d.act64[1], d.ld64,
+                                                         d.cap64);
+    k_mq_band_final<double><<<sms * 2, 256, 0, st>>>(d, mlps, LV_F64, r, d.act64[0], d.act64[1], d.ld64, d.cap64);
     const size_t smem = sizeof(double) * 2 * (size_t)mlps.max_width;
-    k_mq_band64<<<sms * 2, 256, smem, st>>>(d, r, mlps);
+    k_mq_band64<<<sms, 256, smem, st>>>(d, r, mlps);
 }
 
 void mq_launch_survivors(const MqDev &d, int r, cudaStream_t st, int sms) {

@@ -21,12 +21,22 @@ struct StepHdr {
     int counts[kMqMaxQ];       // rows per query
 };
 
+// Precision levels of a round.  Every entry of a level's lists is decided
+// there or sent to the next level's list of the same group.
+//   BF16 sessions: 0 BF16 -> 1 split BF16 (tensor cores) -> 2 FP32 -> 3 FP64
+//   FP32 sessions: 0 FP32 -> 3 FP64
+enum { LV_MAIN = 0, LV_X3 = 1, LV_F32 = 2, LV_F64 = 3, LV_N = 4 };
+
+// The split-BF16 level runs only on bands of at least this many rows (all
+// groups together); smaller bands go straight to the FP32 level, whose
+// layer-parallel kernels finish a few rows sooner than one tensor-core tile
+// pass over K x 3.
+constexpr int kMinSplitRows = 256;
+
 // Round counters of one step, device.
 struct RoundCounters {
     int alive[2];              // alive list sizes (ping-pong)
-    int q[kMqPool];            // per group: queue length of the round
-    int b32[kMqPool];          // per group: FP32 band (BF16 sessions)
-    int b64[kMqPool];          // per group: FP64 band
+    int n[LV_N][kMqPool];      // per level and group: list length
 };
 
 // Device tables and per-step buffers of a session.
@@ -46,13 +56,12 @@ struct MqDev {
     long long *npass;              // [Q]
     unsigned char *visited, *label, *ok;   // [cap] per tuple
     int *alive[2];                 // [cap]
-    int *queues;                   // [G][cap] round queues
-    int *bq32, *bq64;              // [G][cap] band queues
+    int *list[LV_N];               // per level [G][cap]: round queues (level 0) and band lists
     RoundCounters *rc;
-    float *score;                  // [G][cap] working-precision scores of the round's queues
-    float *rscore;                 // [G][cap] FP32 scores of the FP32 band
-    const float *margin_lowp;      // [G]
-    const float *margin_fp32;      // [G]
+    float *score[LV_F64];          // per level below FP64: [G][cap] scores of the level's lists
+    const float *margin[LV_F64];   // per level below FP64: [G] margins (absolute score units)
+    double *act64[2];              // FP64 band activations [cap64][max width]
+    int cap64, ld64;               // FP64 band entries handled layer-parallel per round; row stride
     unsigned int *err;
 };
 
@@ -92,10 +101,17 @@ void mq_launch_router(const MqDev &d, const MqHist &h, cudaStream_t st);
 void mq_launch_partition(const MqDev &d, int r, cudaStream_t st, int sms);
 void mq_launch_layers_f32(const MqLayers &L, cudaStream_t st, int sms);
 void mq_launch_dots_f32(const MqLayers &L, float *score, int sstride, cudaStream_t st, int sms);
-// level 0: score of the round queues vs margin_lowp (BF16) or margin_fp32 (FP32
-// sessions); level 1: FP32 band scores vs margin_fp32.
-void mq_launch_classify(const MqDev &d, int r, int level, bool bf16, cudaStream_t st, int sms);
-void mq_launch_band64(const MqDev &d, int r, const GroupedMlps &mlps, cudaStream_t st, int sms);
+// Decide the entries of level `in` with that level's scores and margins;
+// undecided entries go to level `out`'s lists.
+void mq_launch_classify(const MqDev &d, int r, int in, int out, cudaStream_t st, int sms);
+// The FP64 level: every entry's UDF in FP64, its layers spread over all SMs
+// (a warp per output neuron), the first cap64 entries of the round; the rest
+// a block per entry.  Decides exactly.
+void mq_launch_band64(const MqDev &d, int r, const GroupedMlps &mlps, int max_hidden, cudaStream_t st, int sms);
+// The FP32 level of BF16 sessions, layer-parallel like the FP64 level;
+// writes the level's scores (act0/act1: [cap][ld] floats).
+void mq_launch_band32(const MqDev &d, int r, const GroupedMlps &mlps, int max_hidden, float *act0, float *act1,
+                      int ld, cudaStream_t st, int sms);
 void mq_launch_survivors(const MqDev &d, int r, cudaStream_t st, int sms);
 void mq_launch_result(const MqDev &d, unsigned int *bitmap, cudaStream_t st, int sms);
 void mq_launch_commit(const MqDev &d, const MqHist &h, StatRow *res_rows, unsigned char *res_order,

@@ -54,9 +54,10 @@ struct Udf {
     std::vector<int> dims;
     std::vector<std::vector<float>> W, b;
     long long cost = 0;
-    double margin_lowp = 0.02, margin_fp32 = 1e-5;
+    double margin_lowp = 0.02, margin_x3 = 1e-3, margin_fp32 = 1e-5;
     std::vector<float *> dW, db;
     std::vector<__nv_bfloat16 *> dW16;
+    std::vector<__nv_bfloat16 *> dW3;   // split-BF16 weights [N][3K] = [W_hi | W_lo | W_hi]
     std::vector<int> nt;     // tensor-core tile width per hidden layer (0: widest dividing N)
     MlpDev mlp{};
 };
@@ -110,10 +111,11 @@ struct hydro_session {
     StepHdr *d_hdr = nullptr;
     float *act32[2] = {};
     __nv_bfloat16 *stage16 = nullptr, *act16[2] = {};
+    __nv_bfloat16 *stage3 = nullptr, *act3[2] = {};   // split-BF16 operands (3x the columns)
     float *partials = nullptr;
     int pstride = 1;
     void *encode = nullptr;
-    float *d_margin_lowp = nullptr, *d_margin_fp32 = nullptr;
+    float *d_margin[LV_F64] = {};
     GroupedMlps mlps{};
     std::vector<Slot> slots;
     long long next_step = 0;
@@ -166,19 +168,27 @@ void prof_end(hydro_session *s, int i) {
     if (i >= 0 && s->prof_slot) cudaEventRecord(s->prof_slot->prof[i].b, s->st);
 }
 
-// Device addresses of the round counters' arrays.
-int *rc_q(const MqDev &d) { return reinterpret_cast<int *>(reinterpret_cast<char *>(d.rc) + offsetof(RoundCounters, q)); }
-int *rc_b32(const MqDev &d) {
-    return reinterpret_cast<int *>(reinterpret_cast<char *>(d.rc) + offsetof(RoundCounters, b32));
+// Device address of one level's per-group list lengths.
+int *rc_n(const MqDev &d, int level) {
+    return reinterpret_cast<int *>(reinterpret_cast<char *>(d.rc) + offsetof(RoundCounters, n)) + level * kMqPool;
 }
 
-// Rows of all queues of the round as one stacked operand: the layers of one
-// depth for every group (BF16 on the tensor cores).
-hydro_status eval_tc(hydro_session *s, const int *counts, const int *lists, float *score) {
+// Rows of all lists of a level as one stacked operand: the layers of one
+// depth for every group in one launch (BF16 on the tensor cores; split3: the
+// split-BF16 form, operands [hi | hi | lo] against [W_hi | W_lo | W_hi]).
+hydro_status eval_tc(hydro_session *s, const int *counts, const int *lists, float *score, bool split3,
+                     int min_rows = 0) {
     const MqDev &d = s->d;
+    const int x = split3 ? 3 : 1;
+    __nv_bfloat16 *stage = split3 ? s->stage3 : s->stage16;
+    __nv_bfloat16 *const *act = split3 ? s->act3 : s->act16;
     int pe = prof_begin(s, SP_GATHER);
-    launch_gather_grouped_bf16(d.G, counts, lists, d.cap, reinterpret_cast<const float *const *>(s->d_hdr), d.dim,
-                               d.dim, s->stage16, d.cap, s->sms, s->st);
+    if (split3)
+        launch_gather_grouped_bf16x3(d.G, counts, lists, d.cap, reinterpret_cast<const float *const *>(s->d_hdr),
+                                     d.dim, d.dim, stage, d.cap, s->sms, s->st, min_rows);
+    else
+        launch_gather_grouped_bf16(d.G, counts, lists, d.cap, reinterpret_cast<const float *const *>(s->d_hdr), d.dim,
+                                   d.dim, stage, d.cap, s->sms, s->st);
     prof_end(s, pe);
     s->step_launches++;
     TcHeads heads{};
@@ -189,13 +199,13 @@ hydro_status eval_tc(hydro_session *s, const int *counts, const int *lists, floa
             const bool has = dd + 1 < u.n_layers;
             const bool head = dd + 2 == u.n_layers;
             gr[g] = TcGemmGroup{counts + g,
-                                dd == 0 ? s->stage16 : s->act16[(dd - 1) % 2],
-                                dd == 0 ? d.dim : s->wmax,
+                                dd == 0 ? stage : act[(dd - 1) % 2],
+                                x * (dd == 0 ? d.dim : s->wmax),
                                 d.cap,
-                                has ? u.dW16[dd] : nullptr,
+                                has ? (split3 ? u.dW3[dd] : u.dW16[dd]) : nullptr,
                                 has ? u.db[dd] : nullptr,
                                 head ? u.dW[u.n_layers - 1] : nullptr,
-                                has ? u.dims[dd] : 0,
+                                has ? x * u.dims[dd] : 0,
                                 has ? u.dims[dd + 1] : 0,
                                 has ? u.nt[dd] : 0};
             if (head) {
@@ -204,14 +214,15 @@ hydro_status eval_tc(hydro_session *s, const int *counts, const int *lists, floa
             }
         }
         pe = prof_begin(s, SP_GEMM);
-        hydro_status rs = tc_gemm_grouped_run(s->encode, gr, d.G, s->act16[dd % 2], s->wmax, s->partials, s->pstride,
-                                              s->sms, s->st, d.err);
+        hydro_status rs = tc_gemm_grouped_run(s->encode, gr, d.G, act[dd % 2], x * s->wmax, s->partials, s->pstride,
+                                              s->sms, s->st, d.err, split3, min_rows);
         prof_end(s, pe);
         if (rs != HYDRO_OK) return fail(rs, "grouped tensor-core GEMM: %s", tc_gemm_last_error());
         s->step_launches++;
     }
     pe = prof_begin(s, SP_FINAL);
-    launch_head_finalize_grouped(d.G, counts, heads, s->partials, s->pstride, score, d.cap, d.cap, s->sms, s->st);
+    launch_head_finalize_grouped(d.G, counts, heads, s->partials, s->pstride, score, d.cap, d.cap, s->sms, s->st,
+                                 min_rows);
     prof_end(s, pe);
     s->step_launches++;
     return HYDRO_OK;
@@ -272,30 +283,35 @@ hydro_status enqueue_step(hydro_session *s, Slot &slot) {
     mq_launch_router(d, s->h, s->st);
     prof_end(s, pe);
     s->step_launches += 2;
+    auto classify = [&](int r, int in, int out) {
+        const int p = prof_begin(s, SP_CTRL);
+        mq_launch_classify(d, r, in, out, s->st, s->sms);
+        prof_end(s, p);
+        s->step_launches++;
+    };
     for (int r = 0; r < s->maxP; ++r) {
         pe = prof_begin(s, SP_CTRL);
         mq_launch_partition(d, r, s->st, s->sms);
         prof_end(s, pe);
         s->step_launches += r > 0 ? 2 : 1;
         if (bf) {
-            TRY(eval_tc(s, rc_q(d), d.queues, d.score));
-        } else {
-            eval_f32(s, rc_q(d), d.queues, d.score);
-        }
-        pe = prof_begin(s, SP_CTRL);
-        mq_launch_classify(d, r, 0, bf, s->st, s->sms);
-        prof_end(s, pe);
-        s->step_launches++;
-        if (bf) {
-            eval_f32(s, rc_b32(d), d.bq32, d.rscore);
-            pe = prof_begin(s, SP_CTRL);
-            mq_launch_classify(d, r, 1, bf, s->st, s->sms);
+            TRY(eval_tc(s, rc_n(d, LV_MAIN), d.list[LV_MAIN], d.score[LV_MAIN], false));
+            classify(r, LV_MAIN, LV_X3);
+            TRY(eval_tc(s, rc_n(d, LV_X3), d.list[LV_X3], d.score[LV_X3], true, kMinSplitRows));
+            classify(r, LV_X3, LV_F32);
+            pe = prof_begin(s, SP_LAYER);
+            mq_launch_band32(d, r, s->mlps, s->max_hidden, s->act32[0], s->act32[1], s->wmax, s->st, s->sms);
             prof_end(s, pe);
-            s->step_launches++;
+            s->step_launches += s->max_hidden + 1;
+            classify(r, LV_F32, LV_F64);
+        } else {
+            eval_f32(s, rc_n(d, LV_MAIN), d.list[LV_MAIN], d.score[LV_MAIN]);
+            classify(r, LV_MAIN, LV_F64);
         }
         pe = prof_begin(s, SP_BAND64);
-        mq_launch_band64(d, r, s->mlps, s->st, s->sms);
+        mq_launch_band64(d, r, s->mlps, s->max_hidden, s->st, s->sms);
         prof_end(s, pe);
+        s->step_launches += s->max_hidden + 1;
         pe = prof_begin(s, SP_CTRL);
         mq_launch_survivors(d, r, s->st, s->sms);
         prof_end(s, pe);
@@ -397,14 +413,26 @@ hydro_status finalize(hydro_session *s) {
         u.dW.assign(u.n_layers, nullptr);
         u.db.assign(u.n_layers, nullptr);
         u.dW16.assign(u.n_layers, nullptr);
+        u.dW3.assign(u.n_layers, nullptr);
         u.nt.assign(u.n_layers, 0);
         for (int l = 0; l < u.n_layers; ++l) {
             TRY(upload(s, &u.dW[l], u.W[l].data(), u.W[l].size()));
             TRY(upload(s, &u.db[l], u.b[l].data(), u.b[l].size()));
             if (bf16(s) && l + 1 < u.n_layers) {
-                std::vector<__nv_bfloat16> w16(u.W[l].size());
-                for (size_t k = 0; k < w16.size(); ++k) w16[k] = __float2bfloat16_rn(u.W[l][k]);
+                const int K = u.dims[l], N = u.dims[l + 1];
+                std::vector<__nv_bfloat16> w16(u.W[l].size()), w3((size_t)N * 3 * K);
+                for (int n = 0; n < N; ++n)
+                    for (int k = 0; k < K; ++k) {
+                        const float v = u.W[l][(size_t)n * K + k];
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+                        w16[(size_t)n * K + k] = hi;
+                        w3[(size_t)n * 3 * K + k] = hi;
+                        w3[(size_t)n * 3 * K + K + k] = lo;
+                        w3[(size_t)n * 3 * K + 2 * K + k] = hi;
+                    }
                 TRY(upload(s, &u.dW16[l], w16.data(), w16.size()));
+                TRY(upload(s, &u.dW3[l], w3.data(), w3.size()));
             }
         }
         u.mlp.n_layers = u.n_layers;
@@ -460,17 +488,17 @@ hydro_status finalize(hydro_session *s) {
     TRY(dalloc(s, &d.ok, (size_t)cap));
     TRY(dalloc(s, &d.alive[0], sizeof(int) * (size_t)cap));
     TRY(dalloc(s, &d.alive[1], sizeof(int) * (size_t)cap));
-    TRY(dalloc(s, &d.queues, sizeof(int) * (size_t)G * cap));
-    TRY(dalloc(s, &d.bq32, sizeof(int) * (size_t)G * cap));
-    TRY(dalloc(s, &d.bq64, sizeof(int) * (size_t)G * cap));
+    for (int lv = 0; lv < LV_N; ++lv) TRY(dalloc(s, &d.list[lv], sizeof(int) * (size_t)G * cap));
     TRY(dalloc(s, &d.rc, sizeof(RoundCounters)));
     CU(cudaMemset(d.rc, 0, sizeof(RoundCounters)));
-    TRY(dalloc(s, &d.score, sizeof(float) * (size_t)G * cap));
-    TRY(dalloc(s, &d.rscore, sizeof(float) * (size_t)G * cap));
-    TRY(dalloc(s, &s->d_margin_lowp, sizeof(float) * kMqPool));
-    TRY(dalloc(s, &s->d_margin_fp32, sizeof(float) * kMqPool));
-    d.margin_lowp = s->d_margin_lowp;
-    d.margin_fp32 = s->d_margin_fp32;
+    for (int lv = 0; lv < LV_F64; ++lv) {
+        TRY(dalloc(s, &d.score[lv], sizeof(float) * (size_t)G * cap));
+        TRY(dalloc(s, &s->d_margin[lv], sizeof(float) * kMqPool));
+        d.margin[lv] = s->d_margin[lv];
+    }
+    d.cap64 = std::min(cap, 8192);
+    d.ld64 = s->mlps.max_width;
+    for (int k = 0; k < 2; ++k) TRY(dalloc(s, &d.act64[k], sizeof(double) * (size_t)d.cap64 * d.ld64));
     TRY(dalloc(s, &d.err, sizeof(unsigned int)));
     CU(cudaMemset(d.err, 0, sizeof(unsigned int)));
     for (int k = 0; k < 2; ++k) TRY(dalloc(s, &s->act32[k], sizeof(float) * (size_t)cap * s->wmax));
@@ -481,6 +509,8 @@ hydro_status finalize(hydro_session *s) {
                     return fail(HYDRO_EUNSUPPORTED, "BF16 sessions need layer widths that are multiples of 64");
         TRY(dalloc(s, &s->stage16, sizeof(__nv_bfloat16) * (size_t)cap * c.dim));
         for (int k = 0; k < 2; ++k) TRY(dalloc(s, &s->act16[k], sizeof(__nv_bfloat16) * (size_t)cap * s->wmax));
+        TRY(dalloc(s, &s->stage3, sizeof(__nv_bfloat16) * (size_t)cap * 3 * c.dim));
+        for (int k = 0; k < 2; ++k) TRY(dalloc(s, &s->act3[k], sizeof(__nv_bfloat16) * (size_t)cap * 3 * s->wmax));
         s->pstride = s->wmax / 64;
         TRY(dalloc(s, &s->partials, sizeof(float) * (size_t)cap * s->pstride));
         hydro_status rs = tc_gemm_init(&s->encode);
@@ -522,13 +552,16 @@ hydro_status finalize(hydro_session *s) {
 }
 
 hydro_status upload_margins(hydro_session *s) {
-    float lo[kMqPool] = {}, f32[kMqPool] = {};
+    // level 0 of a FP32 session decides at FP32 accuracy: its margin is margin_fp32
+    float m[LV_F64][kMqPool] = {};
     for (size_t g = 0; g < s->udfs.size(); ++g) {
-        lo[g] = (float)s->udfs[g].margin_lowp;
-        f32[g] = (float)s->udfs[g].margin_fp32;
+        const Udf &u = s->udfs[g];
+        m[LV_MAIN][g] = (float)(bf16(s) ? u.margin_lowp : u.margin_fp32);
+        m[LV_X3][g] = (float)u.margin_x3;
+        m[LV_F32][g] = (float)u.margin_fp32;
     }
-    CU(cudaMemcpy(s->d_margin_lowp, lo, sizeof lo, cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(s->d_margin_fp32, f32, sizeof f32, cudaMemcpyHostToDevice));
+    for (int lv = 0; lv < LV_F64; ++lv)
+        CU(cudaMemcpy(s->d_margin[lv], m[lv], sizeof m[lv], cudaMemcpyHostToDevice));
     return HYDRO_OK;
 }
 
@@ -554,11 +587,7 @@ hydro_status wait_ev(cudaEvent_t ev, long long wait_ms, bool *done) {
 
 __global__ void k_single_queue(RoundCounters *rc, int g, int n, int *queues, int cap) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < kMqPool) {
-        rc->q[i] = i == g ? n : 0;
-        rc->b32[i] = 0;
-        rc->b64[i] = 0;
-    }
+    if (i < LV_N * kMqPool) (&rc->n[0][0])[i] = i == g ? n : 0;   // level 0, group g
     for (int m = i; m < n; m += gridDim.x * blockDim.x) queues[(size_t)g * cap + m] = m;
 }
 
@@ -654,13 +683,16 @@ hydro_status hydro_session_add_query(hydro_session *s, int32_t n_preds, const in
     return HYDRO_OK;
 }
 
-hydro_status hydro_session_set_margins(hydro_session *s, int32_t udf, double margin_lowp, double margin_fp32) {
+hydro_status hydro_session_set_margins(hydro_session *s, int32_t udf, double margin_lowp, double margin_split,
+                                       double margin_fp32) {
     set_last_error("");
     TRY(check(s));
     if (udf < 0 || udf >= (int)s->udfs.size()) return fail(HYDRO_EINVAL, "unknown pool UDF");
-    if (!(margin_lowp >= 0) || !(margin_fp32 >= 0)) return fail(HYDRO_EINVAL, "margins must be >= 0");
+    if (!(margin_lowp >= 0) || !(margin_split >= 0) || !(margin_fp32 >= 0))
+        return fail(HYDRO_EINVAL, "margins must be >= 0");
     if (s->next_step > 0) return fail(HYDRO_ESTATE, "margins are fixed after the first submit");
     s->udfs[udf].margin_lowp = margin_lowp;
+    s->udfs[udf].margin_x3 = margin_split;
     s->udfs[udf].margin_fp32 = margin_fp32;
     return HYDRO_OK;
 }
@@ -671,9 +703,10 @@ hydro_status hydro_session_udf_scores(hydro_session *s, int32_t udf, int32_t pre
     TRY(check(s));
     if (udf < 0 || udf >= (int)s->udfs.size()) return fail(HYDRO_EINVAL, "unknown pool UDF");
     if (n < 0 || (n > 0 && (!d_tuples || !d_scores))) return fail(HYDRO_EINVAL, "bad tuples/scores");
-    if (prec != HYDRO_PREC_FP64 && prec != HYDRO_PREC_FP32 && prec != HYDRO_PREC_BF16)
-        return fail(HYDRO_EINVAL, "precision must be FP64, FP32 or BF16");
-    if (prec == HYDRO_PREC_BF16 && !bf16(s)) return fail(HYDRO_EINVAL, "BF16 scores need a BF16 session");
+    if (prec != HYDRO_PREC_FP64 && prec != HYDRO_PREC_FP32 && prec != HYDRO_PREC_BF16 && prec != HYDRO_PREC_BF16X3)
+        return fail(HYDRO_EINVAL, "precision must be FP64, FP32, BF16 or BF16X3");
+    if ((prec == HYDRO_PREC_BF16 || prec == HYDRO_PREC_BF16X3) && !bf16(s))
+        return fail(HYDRO_EINVAL, "BF16 and split-BF16 scores need a BF16 session");
     CU(cudaSetDevice(s->cfg.device));
     TRY(finalize(s));
     for (Slot &sl : s->slots)
@@ -682,18 +715,19 @@ hydro_status hydro_session_udf_scores(hydro_session *s, int32_t udf, int32_t pre
     if (prec == HYDRO_PREC_FP64) {
         if (n > 0) mq_launch_scores_f64(s->udfs[udf].mlp, s->mlps.max_width, X, s->cfg.dim, (int)n, d_scores, s->st, s->sms);
     } else {
-        float *score_g = s->d.score + (size_t)udf * s->d.cap;
+        float *score_g = s->d.score[LV_MAIN] + (size_t)udf * s->d.cap;
         for (int64_t o = 0; o < n; o += s->d.cap) {
             const int m = (int)std::min<int64_t>(s->d.cap, n - o);
             StepHdr hh{};
             hh.X = X + (size_t)o * s->cfg.dim;
             CU(cudaMemcpyAsync(s->d_hdr, &hh, sizeof(void *), cudaMemcpyHostToDevice, s->st));
-            k_single_queue<<<std::max(1, std::min((m + 255) / 256, s->sms * 4)), 256, 0, s->st>>>(s->d.rc, udf, m,
-                                                                                                   s->d.queues, s->d.cap);
-            if (prec == HYDRO_PREC_BF16) {
-                TRY(eval_tc(s, rc_q(s->d), s->d.queues, s->d.score));
+            k_single_queue<<<std::max(1, std::min((m + 255) / 256, s->sms * 4)), 256, 0, s->st>>>(
+                s->d.rc, udf, m, s->d.list[LV_MAIN], s->d.cap);
+            if (prec == HYDRO_PREC_BF16 || prec == HYDRO_PREC_BF16X3) {
+                TRY(eval_tc(s, rc_n(s->d, LV_MAIN), s->d.list[LV_MAIN], s->d.score[LV_MAIN],
+                            prec == HYDRO_PREC_BF16X3));
             } else {
-                eval_f32(s, rc_q(s->d), s->d.queues, s->d.score);
+                eval_f32(s, rc_n(s->d, LV_MAIN), s->d.list[LV_MAIN], s->d.score[LV_MAIN]);
             }
             k_score_to_f64<<<(m + 255) / 256, 256, 0, s->st>>>(score_g, d_scores + o, m);
             CU(cudaStreamSynchronize(s->st));
@@ -714,36 +748,42 @@ hydro_status hydro_session_calibrate(hydro_session *s, const void *d_tuples, int
     CU(cudaSetDevice(s->cfg.device));
     TRY(finalize(s));
     double *d = nullptr;
-    CU(cudaMalloc(&d, sizeof(double) * n * 3));
-    std::vector<double> s64(n), s32(n), s16(n);
+    CU(cudaMalloc(&d, sizeof(double) * n * 4));
+    std::vector<double> s64(n), s32(n), s16(n), s3(n);
     hydro_status rc = HYDRO_OK;
     const bool bf = bf16(s);
     for (int g = 0; g < (int)s->udfs.size() && rc == HYDRO_OK; ++g) {
         rc = hydro_session_udf_scores(s, g, HYDRO_PREC_FP64, d_tuples, n, d);
         if (rc == HYDRO_OK) rc = hydro_session_udf_scores(s, g, HYDRO_PREC_FP32, d_tuples, n, d + n);
         if (rc == HYDRO_OK && bf) rc = hydro_session_udf_scores(s, g, HYDRO_PREC_BF16, d_tuples, n, d + 2 * n);
+        if (rc == HYDRO_OK && bf) rc = hydro_session_udf_scores(s, g, HYDRO_PREC_BF16X3, d_tuples, n, d + 3 * n);
         if (rc != HYDRO_OK) break;
         if (cudaMemcpy(s64.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(s32.data(), d + n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            (bf && cudaMemcpy(s16.data(), d + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)) {
+            (bf && cudaMemcpy(s16.data(), d + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+            (bf && cudaMemcpy(s3.data(), d + 3 * n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)) {
             rc = fail(HYDRO_ECUDA, "copy of calibration scores failed");
             break;
         }
-        double e32 = 0, e16 = 0, smax = 0;
+        double e32 = 0, e16 = 0, e3 = 0, smax = 0;
         for (int64_t k = 0; k < n; ++k) {
             e32 = std::max(e32, std::fabs(s32[k] - s64[k]));
             if (bf) e16 = std::max(e16, std::fabs(s16[k] - s64[k]));
+            if (bf) e3 = std::max(e3, std::fabs(s3[k] - s64[k]));
             smax = std::max(smax, std::fabs(s64[k]));
         }
         Udf &u = s->udfs[g];
         u.margin_fp32 = std::max(16.0 * e32, 1e-9 * smax);
+        if (bf) u.margin_x3 = std::max(8.0 * e3, 1e-9 * smax);
         if (bf && u.margin_lowp < 4.0 * e16) u.margin_lowp = 4.0 * e16;
         if (info) {
             info[g] = hydro_calib_info{};
             info[g].max_err_fp32 = e32;
             info[g].max_err_lowp = e16;
+            info[g].max_err_tf32 = e3;
             info[g].margin_fp32 = u.margin_fp32;
             info[g].margin_lowp = u.margin_lowp;
+            info[g].margin_tf32 = u.margin_x3;
         }
     }
     cudaFree(d);
@@ -872,6 +912,7 @@ hydro_status hydro_session_poll(hydro_session *s, int64_t step, uint32_t *pass_b
                 const StatRow &r = rows[(size_t)q * kMqSlots + k];
                 o.evaluated[k] = r.evaluated;
                 o.passed[k] = r.passed;
+                o.recheck_split[k] = r.recheck_tf32;
                 o.recheck_fp32[k] = r.recheck32;
                 o.recheck_fp64[k] = r.recheck64;
             }

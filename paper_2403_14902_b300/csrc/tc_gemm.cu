@@ -45,6 +45,8 @@ struct TcLaunch {
     float *partials;          // stacked head partials, row stride pstride
     unsigned int *err;
     int n, ldy, pstride, S, stage_bytes, tmem_cols;
+    int split3;               // store Y as [hi | hi | lo] BF16 splits (3N columns) for a split-BF16 next layer
+    int min_rows;             // fewer stacked rows than this in all groups: no tiles
 };
 
 __device__ __forceinline__ void group_layout(const TcLaunch &L, int *off, int *cnt, int *start) {
@@ -58,6 +60,8 @@ __device__ __forceinline__ void group_layout(const TcLaunch &L, int *off, int *c
         if (L.g[g].NT) t += ((c + 127) / 128) * (L.g[g].N / L.g[g].NT);
     }
     start[L.n] = t;
+    if (o < L.min_rows)
+        for (int g = 0; g <= L.n; ++g) start[g] = 0;
 }
 
 __device__ __forceinline__ int tile_group(const int *start, int n, int t) {
@@ -215,7 +219,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_grouped_bf16_tc(const __grid_co
                         hsum = fmaf(__ldg(hw + c0 + j), v, hsum);
                     }
                 } else if (live) {
-                    uint32_t pk[16];
+                    uint32_t pk[16], lo[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         float v0 = __uint_as_float(r[2 * j]) + __ldg(bias + c0 + 2 * j);
@@ -223,10 +227,23 @@ __global__ void __launch_bounds__(192, 1) k_gemm_grouped_bf16_tc(const __grid_co
                         v0 = v0 > 0.f ? v0 : 0.f;
                         v1 = v1 > 0.f ? v1 : 0.f;
                         pk[j] = pack_bf16x2(v0, v1);
+                        if (L.split3) {
+                            const float h0 = __uint_as_float(pk[j] << 16), h1 = __uint_as_float(pk[j] & 0xFFFF0000u);
+                            lo[j] = pack_bf16x2(v0 - h0, v1 - h1);
+                        }
                     }
                     uint4 *dst = reinterpret_cast<uint4 *>(L.Y + row * L.ldy + n0 + c0);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    if (L.split3) {
+                        uint4 *d1 = reinterpret_cast<uint4 *>(L.Y + row * L.ldy + G.N + n0 + c0);
+                        uint4 *d2 = reinterpret_cast<uint4 *>(L.Y + row * L.ldy + 2 * G.N + n0 + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            d1[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                            d2[j] = make_uint4(lo[4 * j], lo[4 * j + 1], lo[4 * j + 2], lo[4 * j + 3]);
+                        }
+                    }
                 }
             }
             if (hw && live) L.partials[row * L.pstride + tn] = hsum;
@@ -303,11 +320,45 @@ __global__ void k_gather_grouped_bf16(int n, const int *counts, const int *queue
     }
 }
 
-__global__ void k_head_finalize_grouped(int n, const int *counts, TcHeads heads, const float *partials, int pstride,
-                                        float *score, int sstride) {
+// Split-BF16 operand rows [hi | hi | lo] (3K columns): hi = bf16(x),
+// lo = bf16(x - hi), so that with weights [W_hi | W_lo | W_hi] one BF16 GEMM
+// over 3K sums hi*W_hi + hi*W_lo + lo*W_hi.
+__global__ void k_gather_grouped_bf16x3(int n, const int *counts, const int *queues, int qstride,
+                                        const float *const *Xp, int ldx, int K, __nv_bfloat16 *out, int min_rows) {
+    const float *X = *Xp;
     int off[kMaxGroups + 1];
     off[0] = 0;
     for (int g = 0; g < n; ++g) off[g + 1] = off[g] + counts[g];
+    if (off[n] < min_rows) return;
+    const int per_row = K / 8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)off[n] * per_row;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(i / per_row), q = (int)(i % per_row);
+        int g = 0;
+        while (e >= off[g + 1]) ++g;
+        const int src = queues[(size_t)g * qstride + (e - off[g])];
+        const float4 *p = reinterpret_cast<const float4 *>(X + (size_t)src * ldx) + 2 * q;
+        const float4 a = p[0], b = p[1];
+        const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            hi[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
+            lo[j] = pack_bf16x2(v[2 * j] - __uint_as_float(hi[j] << 16), v[2 * j + 1] - __uint_as_float(hi[j] & 0xFFFF0000u));
+        }
+        uint4 *row = reinterpret_cast<uint4 *>(out + (size_t)e * 3 * K);
+        row[q] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        row[per_row + q] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        row[2 * per_row + q] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+}
+
+__global__ void k_head_finalize_grouped(int n, const int *counts, TcHeads heads, const float *partials, int pstride,
+                                        float *score, int sstride, int min_rows) {
+    int off[kMaxGroups + 1];
+    off[0] = 0;
+    for (int g = 0; g < n; ++g) off[g + 1] = off[g] + counts[g];
+    if (off[n] < min_rows) return;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < off[n]; e += gridDim.x * blockDim.x) {
         int g = 0;
         while (e >= off[g + 1]) ++g;
@@ -340,7 +391,8 @@ hydro_status tc_gemm_init(void **encode) {
 }
 
 hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n, __nv_bfloat16 *Y, int ldy,
-                                 float *partials, int pstride, int sms, cudaStream_t st, unsigned int *err) {
+                                 float *partials, int pstride, int sms, cudaStream_t st, unsigned int *err,
+                                 bool split3, int min_rows) {
     if (!encode || n < 1 || n > kMaxGroups || (ldy % 8) != 0) {
         g_gemm_err = "tensor-core GEMM not ready or bad group list";
         return HYDRO_EUNSUPPORTED;
@@ -357,7 +409,7 @@ hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n,
             continue;
         }
         if (!tc_gemm_supported(h.K, h.N) || (h.nt && (h.nt % 64 || h.nt > 256 || h.N % h.nt)) || h.x_rows < 1 || (h.ldx % 8) != 0 || h.ldx < h.K ||
-            (!h.head_w && h.N > ldy) || (h.head_w && h.N / (h.nt ? h.nt : col_tile(h.N)) > pstride)) {
+            (!h.head_w && (split3 ? 3 * h.N : h.N) > ldy) || (h.head_w && h.N / (h.nt ? h.nt : col_tile(h.N)) > pstride)) {
             g_gemm_err = "tensor-core GEMM: unsupported group shape";
             return HYDRO_EUNSUPPORTED;
         }
@@ -386,6 +438,8 @@ hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n,
     L.S = (kGemmSmem - 1280) / L.stage_bytes;
     if (L.S > kMaxStages) L.S = kMaxStages;
     L.tmem_cols = 2 * nt_max;
+    L.split3 = split3 ? 1 : 0;
+    L.min_rows = min_rows;
     if (tiles == 0) return HYDRO_OK;   // only rows-only groups
     const int grid = (int)(tiles < sms ? tiles : sms);
     k_gemm_grouped_bf16_tc<<<grid, 192, kGemmSmem, st>>>(L);
@@ -424,12 +478,22 @@ void launch_gather_grouped_bf16(int n, const int *counts, const int *queues, int
     k_gather_grouped_bf16<<<grid, 256, 0, st>>>(n, counts, queues, qstride, Xp, ldx, K, out);
 }
 
+void launch_gather_grouped_bf16x3(int n, const int *counts, const int *queues, int qstride, const float *const *Xp,
+                                  int ldx, int K, __nv_bfloat16 *out, int max_rows, int sms, cudaStream_t st,
+                                  int min_rows) {
+    long long work = (long long)max_rows * (K / 8);
+    int grid = (int)((work + 255) / 256);
+    if (grid > sms * 8) grid = sms * 8;
+    if (grid < 1) grid = 1;
+    k_gather_grouped_bf16x3<<<grid, 256, 0, st>>>(n, counts, queues, qstride, Xp, ldx, K, out, min_rows);
+}
+
 void launch_head_finalize_grouped(int n, const int *counts, const TcHeads &heads, const float *partials, int pstride,
-                                  float *score, int sstride, int max_rows, int sms, cudaStream_t st) {
+                                  float *score, int sstride, int max_rows, int sms, cudaStream_t st, int min_rows) {
     int grid = (max_rows + 255) / 256;
     if (grid > sms * 4) grid = sms * 4;
     if (grid < 1) grid = 1;
-    k_head_finalize_grouped<<<grid, 256, 0, st>>>(n, counts, heads, partials, pstride, score, sstride);
+    k_head_finalize_grouped<<<grid, 256, 0, st>>>(n, counts, heads, partials, pstride, score, sstride, min_rows);
 }
 
 const char *tc_gemm_last_error() { return g_gemm_err.c_str(); }

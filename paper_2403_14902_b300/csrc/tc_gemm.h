@@ -45,15 +45,25 @@ int tc_gemm_col_tiles(int N);
 // All groups' layers of one depth in one persistent launch.  Y (stacked,
 // row stride ldy) receives the groups without a head; partials (stacked, row
 // stride pstride) the head partials of the others.
+// split3: store Y rows as [hi | hi | lo] BF16 splits (3N columns, ldy >= 3N)
+// for a split-BF16 next layer.  min_rows: with fewer stacked rows than this
+// (read on the device) the launch does nothing.
 hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n, __nv_bfloat16 *Y, int ldy,
-                                 float *partials, int pstride, int sms, cudaStream_t st, unsigned int *err);
+                                 float *partials, int pstride, int sms, cudaStream_t st, unsigned int *err,
+                                 bool split3 = false, int min_rows = 0);
 // out[off_g + m] = bf16(X[queues[g * qstride + m]]) for m < counts[g], X = *Xp
 // (read on the device, so a captured launch follows the pointer's updates).
 void launch_gather_grouped_bf16(int n, const int *counts, const int *queues, int qstride, const float *const *Xp,
                                 int ldx, int K, __nv_bfloat16 *out, int max_rows, int sms, cudaStream_t st);
+// Split-BF16 rows: out[off_g + m] = [hi | hi | lo] of X[queues[g * qstride + m]]
+// (3K columns), hi = bf16(x), lo = bf16(x - hi).
+void launch_gather_grouped_bf16x3(int n, const int *counts, const int *queues, int qstride, const float *const *Xp,
+                                  int ldx, int K, __nv_bfloat16 *out, int max_rows, int sms, cudaStream_t st,
+                                  int min_rows = 0);
 // score[g * sstride + m] = heads.b[g] + sum_j partials[(off_g + m) * pstride + j], j < heads.tiles[g].
 void launch_head_finalize_grouped(int n, const int *counts, const TcHeads &heads, const float *partials, int pstride,
-                                  float *score, int sstride, int max_rows, int sms, cudaStream_t st);
+                                  float *score, int sstride, int max_rows, int sms, cudaStream_t st,
+                                  int min_rows = 0);
 // out[m] = bf16(X[rows[m]]) for m < *count (K % 8 == 0, 16-byte aligned rows).
 void launch_gather_bf16(const int *count, const int *rows, const float *X, int ldx, int K, __nv_bfloat16 *out,
                         int max_rows, int sms, cudaStream_t st);

@@ -122,9 +122,14 @@ def test_session_bf16_exact(small, autotune):
     info = s.calibrate(torch.from_numpy(small["calib"]).cuda())
     for d in info:
         assert d["margin_lowp"] >= 4 * d["max_err_lowp"] > 0
+        # the split-BF16 level is far closer to exact than BF16
+        assert 0 < d["max_err_tf32"] < 0.02 * d["max_err_lowp"]
+        assert d["margin_tf32"] >= 8 * d["max_err_tf32"]
     res = run_session(s, small["streams"], small["chunk"])
     check_steps(res, small["sims"], len(small["queries"]))
-    assert sum(sum(r["recheck_fp32"]) for _, _, per in res for r in per) > 0
+    split = sum(sum(r["recheck_split"]) for _, _, per in res for r in per)
+    f32 = sum(sum(r["recheck_fp32"]) for _, _, per in res for r in per)
+    assert split + f32 > 0
     if autotune:
         t = s.tuning()
         assert len(t) == sum(len(d) - 2 for d in small["w"].udfs)
@@ -140,9 +145,32 @@ def test_session_wide_margins_recheck_everything(small):
                      cap=len(small["queries"]) * small["chunk"], queries=small["queries"])
     s.calibrate(torch.from_numpy(small["calib"]).cuda())
     for u in range(8):
-        s.set_margins(u, 1e3, 1e3)
+        s.set_margins(u, 1e3, 1e3, 1e3)
     res = run_session(s, small["streams"], small["chunk"])
     check_steps(res, small["sims"], len(small["queries"]))
+    ev = sum(sum(r["evaluated"]) for _, _, per in res for r in per)
+    for key in ("recheck_fp32", "recheck_fp64"):
+        assert sum(sum(r[key]) for _, _, per in res for r in per) == ev
+    # the split level ran on the rounds whose band reached its minimum size
+    split = sum(sum(r["recheck_split"]) for _, _, per in res for r in per)
+    assert 6400 <= split < ev
+    s.close()
+
+
+def test_session_fp64_band_beyond_layer_parallel_capacity(small):
+    """FP32 session, every score sent to FP64, chunks of 1,024: the first
+    round's FP64 band (8,664 entries) exceeds the 8,192 entries run layer-
+    parallel; the rest run a block per entry.  Still exact."""
+    import torch
+    chunk = 1024
+    s = make_session(small["w"], small["qs"], small["th"], cap=len(small["queries"]) * chunk,
+                     queries=small["queries"])
+    for u in range(8):
+        s.set_margins(u, 0.0, 0.0, 1e3)
+    res = run_session(s, small["streams"], chunk)
+    sims = oracle_per_query(small["w"], small["qs"], small["th"], small["streams"], chunk, small["queries"])
+    check_steps(res, sims, len(small["queries"]))
+    assert sum(res[0][0]) > 8192
     ev = sum(sum(r["evaluated"]) for _, _, per in res for r in per)
     assert sum(sum(r["recheck_fp64"]) for _, _, per in res for r in per) == ev
     s.close()
@@ -165,6 +193,8 @@ def test_session_scores_against_oracle(small):
         assert np.max(np.abs(out.cpu().numpy() - S) / np.maximum(np.abs(S), rms)) < 1e-3
         s.udf_scores(u, "bf16", Xd, out)
         assert np.median(np.abs(out.cpu().numpy() - S) / np.maximum(np.abs(S), rms)) < 1e-2
+        s.udf_scores(u, "bf16x3", Xd, out)
+        assert np.max(np.abs(out.cpu().numpy() - S) / np.maximum(np.abs(S), rms)) < 2e-4
     s.close()
 
 
