@@ -44,6 +44,25 @@ __device__ __forceinline__ void warp_count(unsigned long long *p, bool want) {
     if (lane_id() == __ffs(peers) - 1) atomicAdd(p, (unsigned long long)__popc(peers));
 }
 
+// True in the last block of the grid to finish (the others' writes are
+// visible to it).  The ticket is reset for the next launch.
+__device__ __forceinline__ bool last_block(int *ticket) {
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+        if (last) *ticket = 0;
+    }
+    __syncthreads();
+    return last;
+}
+
+__device__ __forceinline__ void set_cond(const Cond &c, bool v) {
+    if (c.h) cudaGraphSetConditional((cudaGraphConditionalHandle)c.h, v ? 1u : 0u);
+    if (c.flag) *c.flag = v ? 1 : 0;
+}
+
 __device__ __forceinline__ unsigned long long *ctr(StatRow *r, int field) {
     return reinterpret_cast<unsigned long long *>(r) + field;
 }
@@ -60,7 +79,7 @@ int grid_for(long long work, int per_block, int sms, int per_sm) {
 
 // Offsets of the step, query of every tuple, first alive list (every tuple),
 // cleared per-tuple flags, statistics and round counters.
-__global__ void __launch_bounds__(256) k_mq_init(MqDev d) {
+__global__ void __launch_bounds__(256) k_mq_init(MqDev d, Cond round0) {
     __shared__ int s_off[kMqMaxQ + 1];
     if (threadIdx.x == 0) {
         int o = 0;
@@ -76,11 +95,14 @@ __global__ void __launch_bounds__(256) k_mq_init(MqDev d) {
         for (int i = threadIdx.x; i <= d.Q; i += blockDim.x) d.off[i] = s_off[i];
         for (int i = threadIdx.x; i < d.Q * kMqSlots; i += blockDim.x) d.rows[i] = StatRow{};
         for (int i = threadIdx.x; i < d.Q; i += blockDim.x) d.npass[i] = 0;
+        for (int i = threadIdx.x; i < kMqGates; i += blockDim.x) d.gates[i] = 0;
+        __syncthreads();
         if (threadIdx.x == 0) {
             if (s_off[d.Q] > d.cap) atomicOr(d.err, ERR_COUNT_RANGE);
             RoundCounters z{};
             z.alive[0] = n;
             *d.rc = z;
+            set_cond(round0, n > 0);
         }
     }
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -235,7 +257,7 @@ __global__ void __launch_bounds__(256) k_mq_dot_f32(MqLayers L, float *score, in
 // level counts its own).  The split-BF16 level runs only on a band of at
 // least kMinSplitRows rows: below that its launches return at once and every
 // entry passes on to the FP32 level unscored.
-__global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int in, int out) {
+__global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int in, int out, Cond next, int next_min) {
     const int *cnts = d.rc->n[in];
     const int *lists = d.list[in];
     const float *sc = d.score[in];
@@ -276,6 +298,12 @@ __global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int in, int
         const int pos = warp_append(live && inband ? &next_cnt[g] : nullptr, live && inband);
         if (live && inband) next_list[(size_t)g * d.cap + pos] = e;
         if (rfield >= 0) warp_count(ctr(row, rfield), live && !skipped);
+    }
+    if (next.flag && last_block(&d.rc->ticket[in]) && threadIdx.x == 0) {
+        __threadfence();
+        int tot = 0;
+        for (int g = 0; g < d.G; ++g) tot += *((volatile int *)&next_cnt[g]);
+        set_cond(next, tot >= next_min);
     }
 }
 
@@ -434,7 +462,7 @@ __global__ void __launch_bounds__(256) k_mq_band64(MqDev d, int r, GroupedMlps m
 
 // Next alive list: tuples that passed (or whose query is in a warmup batch)
 // and have a slot left.  Clears the round's queue and band counters.
-__global__ void __launch_bounds__(256) k_mq_survivors(MqDev d, int r) {
+__global__ void __launch_bounds__(256) k_mq_survivors(MqDev d, int r, Cond next_round) {
     const int cur = r & 1;
     const int n = d.rc->alive[cur];
     for (int m0 = blockIdx.x * blockDim.x; m0 < n; m0 += gridDim.x * blockDim.x) {
@@ -448,6 +476,10 @@ __global__ void __launch_bounds__(256) k_mq_survivors(MqDev d, int r) {
         }
         const int pos = warp_append(keep ? &d.rc->alive[cur ^ 1] : nullptr, keep);
         if (keep) d.alive[cur ^ 1][pos] = e;
+    }
+    if (next_round.flag && last_block(&d.rc->ticket[LV_N]) && threadIdx.x == 0) {
+        __threadfence();
+        set_cond(next_round, *((volatile int *)&d.rc->alive[cur ^ 1]) > 0);
     }
 }
 
@@ -479,9 +511,10 @@ __global__ void __launch_bounds__(256) k_mq_result(MqDev d, unsigned int *bitmap
 // Statistics of the step into each query's history, and the step's
 // per-query report into the result slot.
 __global__ void k_mq_commit(MqDev d, MqHist h, StatRow *res_rows, unsigned char *res_order, unsigned char *res_evall,
-                            long long *res_bidx, long long *res_npass, int *res_total) {
+                            long long *res_bidx, long long *res_npass, int *res_total, int *res_gates) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *res_total = d.off[d.Q];
+    if (i < kMqGates) res_gates[i] = d.gates[i];
     if (i >= d.Q * kMqSlots) return;
     const int q = i / kMqSlots, slot = i % kMqSlots;
     const long long b = d.bidx[q];
@@ -537,8 +570,8 @@ __global__ void __launch_bounds__(256) k_mq_scores_f64(MlpDev mlp, int max_width
 
 }  // namespace
 
-void mq_launch_init(const MqDev &d, cudaStream_t st, int sms) {
-    k_mq_init<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d);
+void mq_launch_init(const MqDev &d, cudaStream_t st, int sms, Cond round0) {
+    k_mq_init<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, round0);
 }
 
 void mq_launch_router(const MqDev &d, const MqHist &h, cudaStream_t st) {
@@ -558,8 +591,8 @@ void mq_launch_dots_f32(const MqLayers &L, float *score, int sstride, cudaStream
     k_mq_dot_f32<<<sms * 8, 256, 0, st>>>(L, score, sstride);
 }
 
-void mq_launch_classify(const MqDev &d, int r, int in, int out, cudaStream_t st, int sms) {
-    k_mq_classify<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r, in, out);
+void mq_launch_classify(const MqDev &d, int r, int in, int out, cudaStream_t st, int sms, Cond next, int next_min) {
+    k_mq_classify<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r, in, out, next, next_min);
 }
 
 void mq_launch_band32(const MqDev &d, int r, const GroupedMlps &mlps, int max_hidden, float *act0, float *act1,
@@ -578,8 +611,8 @@ void mq_launch_band64(const MqDev &d, int r, const GroupedMlps &mlps, int max_hi
     k_mq_band64<<<sms, 256, smem, st>>>(d, r, mlps);
 }
 
-void mq_launch_survivors(const MqDev &d, int r, cudaStream_t st, int sms) {
-    k_mq_survivors<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r);
+void mq_launch_survivors(const MqDev &d, int r, cudaStream_t st, int sms, Cond next_round) {
+    k_mq_survivors<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r, next_round);
 }
 
 void mq_launch_result(const MqDev &d, unsigned int *bitmap, cudaStream_t st, int sms) {
@@ -588,9 +621,10 @@ void mq_launch_result(const MqDev &d, unsigned int *bitmap, cudaStream_t st, int
 
 void mq_launch_commit(const MqDev &d, const MqHist &h, StatRow *res_rows, unsigned char *res_order,
                       unsigned char *res_evall, long long *res_bidx, long long *res_npass, int *res_total,
-                      cudaStream_t st) {
-    k_mq_commit<<<(d.Q * kMqSlots + 255) / 256, 256, 0, st>>>(d, h, res_rows, res_order, res_evall, res_bidx,
-                                                              res_npass, res_total);
+                      int *res_gates, cudaStream_t st) {
+    const int n = d.Q * kMqSlots > kMqGates ? d.Q * kMqSlots : kMqGates;
+    k_mq_commit<<<(n + 255) / 256, 256, 0, st>>>(d, h, res_rows, res_order, res_evall, res_bidx, res_npass, res_total,
+                                                 res_gates);
 }
 
 cudaError_t mq_band_smem_setup(int max_width) {

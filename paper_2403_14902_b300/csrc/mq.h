@@ -37,7 +37,18 @@ constexpr int kMinSplitRows = 256;
 struct RoundCounters {
     int alive[2];              // alive list sizes (ping-pong)
     int n[LV_N][kMqPool];      // per level and group: list length
+    int ticket[LV_N + 1];      // last-block detection of the classify (per input level) and survivors kernels
 };
+
+// Condition of a captured step's IF node: the handle (0: launched without a
+// graph) and a device flag that records the value for the launch count.
+// A kernel's last block sets the condition of the node that follows it.
+struct Cond {
+    unsigned long long h = 0;
+    int *flag = nullptr;
+};
+constexpr int kMqMaxRounds = kMqSlots;
+constexpr int kMqGates = 4 * kMqMaxRounds;   // per round: round, split, FP32 band, FP64 band
 
 // Device tables and per-step buffers of a session.
 struct MqDev {
@@ -63,6 +74,7 @@ struct MqDev {
     double *act64[2];              // FP64 band activations [cap64][max width]
     int cap64, ld64;               // FP64 band entries handled layer-parallel per round; row stride
     unsigned int *err;
+    int *gates;                    // [kMqGates] condition values of the step (0 unless set)
 };
 
 // Per-query statistics history (device).
@@ -96,14 +108,17 @@ struct MqLayers {
     int ldy;
 };
 
-void mq_launch_init(const MqDev &d, cudaStream_t st, int sms);
+// h_round0: set to (step has tuples).
+void mq_launch_init(const MqDev &d, cudaStream_t st, int sms, Cond round0 = Cond());
 void mq_launch_router(const MqDev &d, const MqHist &h, cudaStream_t st);
 void mq_launch_partition(const MqDev &d, int r, cudaStream_t st, int sms);
 void mq_launch_layers_f32(const MqLayers &L, cudaStream_t st, int sms);
 void mq_launch_dots_f32(const MqLayers &L, float *score, int sstride, cudaStream_t st, int sms);
 // Decide the entries of level `in` with that level's scores and margins;
 // undecided entries go to level `out`'s lists.
-void mq_launch_classify(const MqDev &d, int r, int in, int out, cudaStream_t st, int sms);
+// h_next: set to (level `out` holds at least next_min entries).
+void mq_launch_classify(const MqDev &d, int r, int in, int out, cudaStream_t st, int sms, Cond next = Cond(),
+                        int next_min = 1);
 // The FP64 level: every entry's UDF in FP64, its layers spread over all SMs
 // (a warp per output neuron), the first cap64 entries of the round; the rest
 // a block per entry.  Decides exactly.
@@ -112,11 +127,12 @@ void mq_launch_band64(const MqDev &d, int r, const GroupedMlps &mlps, int max_hi
 // writes the level's scores (act0/act1: [cap][ld] floats).
 void mq_launch_band32(const MqDev &d, int r, const GroupedMlps &mlps, int max_hidden, float *act0, float *act1,
                       int ld, cudaStream_t st, int sms);
-void mq_launch_survivors(const MqDev &d, int r, cudaStream_t st, int sms);
+// h_next_round: set to (the next alive list is not empty).
+void mq_launch_survivors(const MqDev &d, int r, cudaStream_t st, int sms, Cond next_round = Cond());
 void mq_launch_result(const MqDev &d, unsigned int *bitmap, cudaStream_t st, int sms);
 void mq_launch_commit(const MqDev &d, const MqHist &h, StatRow *res_rows, unsigned char *res_order,
                       unsigned char *res_evall, long long *res_bidx, long long *res_npass, int *res_total,
-                      cudaStream_t st);
+                      int *res_gates, cudaStream_t st);
 cudaError_t mq_band_smem_setup(int max_width);
 // FP64 scores of one UDF on n rows of X (block per row), for calibration.
 void mq_launch_scores_f64(const MlpDev &mlp, int max_width, const float *X, int ldx, int n, double *out,

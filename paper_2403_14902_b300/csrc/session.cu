@@ -81,7 +81,10 @@ struct ProfRec {
 
 struct Slot {
     std::vector<ProfRec> prof;     // this step's timed launches (profiling on)
-    long long launches = 0;
+    long long launches = 0;        // launches outside conditional regions (all, without a graph)
+    long long gate_body[kMqGates] = {};   // launches inside each conditional region
+    bool conditional = false;
+    int *gates = nullptr;          // device copy of the step's condition values
     bool busy = false;
     long long step = -1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -126,7 +129,15 @@ struct hydro_session {
     double prof_ms[SP_N] = {};
     long long prof_n[SP_N] = {};
     long long launches = 0;         // kernel launches of polled steps since profiling was (re)started
-    long long step_launches = 0;    // launches of the step being enqueued
+    long long step_launches = 0;    // launches of the step being enqueued (current region)
+    // graph capture with conditional regions
+    bool capturing = false;
+    int if_depth = 0;
+    cudaStream_t helper[2] = {};
+    std::vector<long long> frames;
+    unsigned long long handles[kMqGates] = {};   // created on first use (an unused handle fails instantiation)
+    cudaGraph_t cap_graph = nullptr;
+    hydro_status handle_err = HYDRO_OK;
 };
 
 namespace {
@@ -271,58 +282,137 @@ void eval_f32(hydro_session *s, const int *counts, const int *lists, float *scor
     s->step_launches++;
 }
 
+// Conditional regions of a captured step.  In graph mode each round is an
+// IF node (run while tuples are alive) and inside it the split-BF16, FP32
+// and FP64 levels are IF nodes (run when their band is not empty); the
+// kernel before each node sets its condition on the device.  Bodies are
+// captured on helper streams.  Launch accounting: launches inside a body
+// are counted for that body's gate, the rest for every step.
+hydro_status open_if(hydro_session *s, Slot &slot, int gate, cudaStream_t *saved) {
+    if (!s->capturing) return HYDRO_OK;
+    if (!s->handles[gate] || s->handle_err != HYDRO_OK) return fail(HYDRO_ECUDA, "conditional region without handle");
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    CU(cudaStreamGetCaptureInfo(s->st, &cs, nullptr, &g, &deps, &ed, &nd));
+    alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
+    memset(pbuf, 0, sizeof pbuf);
+    cudaGraphNodeParams &p = *reinterpret_cast<cudaGraphNodeParams *>(pbuf);   // zeroed, as the API requires
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = s->handles[gate];
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CU(cudaGraphAddNode(&node, g, deps, ed, nd, &p));
+    CU(cudaStreamUpdateCaptureDependencies(s->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    if (s->if_depth >= 2) return fail(HYDRO_ECUDA, "conditional regions nest at most twice");
+    cudaStream_t hs = s->helper[s->if_depth++];
+    CU(cudaStreamBeginCaptureToGraph(hs, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    *saved = s->st;
+    s->st = hs;
+    s->frames.push_back(s->step_launches);
+    s->step_launches = 0;
+    (void)slot;
+    return HYDRO_OK;
+}
+
+hydro_status close_if(hydro_session *s, Slot &slot, int gate, cudaStream_t saved) {
+    if (!s->capturing) return HYDRO_OK;
+    cudaGraph_t out = nullptr;
+    CU(cudaStreamEndCapture(s->st, &out));
+    s->st = saved;
+    s->if_depth--;
+    slot.gate_body[gate] = s->step_launches;
+    s->step_launches = s->frames.back();
+    s->frames.pop_back();
+    return HYDRO_OK;
+}
+
+Cond cond_of(hydro_session *s, int gate) {
+    Cond c;
+    if (s->capturing) {
+        if (!s->handles[gate]) {
+            cudaGraphConditionalHandle h;
+            if (cudaGraphConditionalHandleCreate(&h, s->cap_graph, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+                s->handle_err = fail(HYDRO_ECUDA, "conditional handle create failed");
+            else
+                s->handles[gate] = (unsigned long long)h;
+        }
+        c.h = s->handles[gate];
+        c.flag = s->d.gates + gate;
+    }
+    return c;
+}
+
 // One step's launches, all stream-ordered on s->st (captured into a graph
 // when graphs are on).
 hydro_status enqueue_step(hydro_session *s, Slot &slot) {
     const MqDev &d = s->d;
     const bool bf = bf16(s);
+    auto gate = [](int r, int k) { return 4 * r + k; };   // k: 0 round, 1 split, 2 FP32 band, 3 FP64 band
     CU(cudaMemcpyAsync(s->d_hdr, slot.h_hdr, sizeof(StepHdr), cudaMemcpyHostToDevice, s->st));
     s->step_launches = 0;
+    s->frames.clear();
+    for (int k = 0; k < kMqGates; ++k) slot.gate_body[k] = 0;
     int pe = prof_begin(s, SP_CTRL);
-    mq_launch_init(d, s->st, s->sms);
+    mq_launch_init(d, s->st, s->sms, cond_of(s, gate(0, 0)));
     mq_launch_router(d, s->h, s->st);
     prof_end(s, pe);
     s->step_launches += 2;
-    auto classify = [&](int r, int in, int out) {
+    auto classify = [&](int r, int in, int out, Cond next, int next_min) {
         const int p = prof_begin(s, SP_CTRL);
-        mq_launch_classify(d, r, in, out, s->st, s->sms);
+        mq_launch_classify(d, r, in, out, s->st, s->sms, next, next_min);
         prof_end(s, p);
         s->step_launches++;
     };
+    cudaStream_t sv_round = nullptr, sv = nullptr;
     for (int r = 0; r < s->maxP; ++r) {
+        TRY(open_if(s, slot, gate(r, 0), &sv_round));
         pe = prof_begin(s, SP_CTRL);
         mq_launch_partition(d, r, s->st, s->sms);
         prof_end(s, pe);
         s->step_launches += r > 0 ? 2 : 1;
         if (bf) {
             TRY(eval_tc(s, rc_n(d, LV_MAIN), d.list[LV_MAIN], d.score[LV_MAIN], false));
-            classify(r, LV_MAIN, LV_X3);
+            classify(r, LV_MAIN, LV_X3, cond_of(s, gate(r, 1)), kMinSplitRows);
+            TRY(open_if(s, slot, gate(r, 1), &sv));
             TRY(eval_tc(s, rc_n(d, LV_X3), d.list[LV_X3], d.score[LV_X3], true, kMinSplitRows));
-            classify(r, LV_X3, LV_F32);
+            TRY(close_if(s, slot, gate(r, 1), sv));
+            classify(r, LV_X3, LV_F32, cond_of(s, gate(r, 2)), 1);
+            TRY(open_if(s, slot, gate(r, 2), &sv));
             pe = prof_begin(s, SP_LAYER);
             mq_launch_band32(d, r, s->mlps, s->max_hidden, s->act32[0], s->act32[1], s->wmax, s->st, s->sms);
             prof_end(s, pe);
             s->step_launches += s->max_hidden + 1;
-            classify(r, LV_F32, LV_F64);
+            classify(r, LV_F32, LV_F64, cond_of(s, gate(r, 3)), 1);
+            TRY(close_if(s, slot, gate(r, 2), sv));
         } else {
             eval_f32(s, rc_n(d, LV_MAIN), d.list[LV_MAIN], d.score[LV_MAIN]);
-            classify(r, LV_MAIN, LV_F64);
+            classify(r, LV_MAIN, LV_F64, cond_of(s, gate(r, 3)), 1);
         }
+        TRY(open_if(s, slot, gate(r, 3), &sv));
         pe = prof_begin(s, SP_BAND64);
         mq_launch_band64(d, r, s->mlps, s->max_hidden, s->st, s->sms);
         prof_end(s, pe);
-        s->step_launches += s->max_hidden + 1;
+        s->step_launches += s->max_hidden + 2;
+        TRY(close_if(s, slot, gate(r, 3), sv));
         pe = prof_begin(s, SP_CTRL);
-        mq_launch_survivors(d, r, s->st, s->sms);
+        mq_launch_survivors(d, r, s->st, s->sms, r + 1 < s->maxP ? cond_of(s, gate(r + 1, 0)) : Cond());
         prof_end(s, pe);
-        s->step_launches += 2;
+        s->step_launches++;
+        TRY(close_if(s, slot, gate(r, 0), sv_round));
     }
     pe = prof_begin(s, SP_CTRL);
     mq_launch_result(d, slot.bitmap, s->st, s->sms);
-    mq_launch_commit(d, s->h, slot.rows, slot.order, slot.evall, slot.bidx, slot.npass, slot.total, s->st);
+    mq_launch_commit(d, s->h, slot.rows, slot.order, slot.evall, slot.bidx, slot.npass, slot.total, slot.gates,
+                     s->st);
     prof_end(s, pe);
     s->step_launches += 2;
     slot.launches = s->step_launches;
+    slot.conditional = s->capturing;
     CU(cudaGetLastError());
     return HYDRO_OK;
 }
@@ -501,6 +591,9 @@ hydro_status finalize(hydro_session *s) {
     for (int k = 0; k < 2; ++k) TRY(dalloc(s, &d.act64[k], sizeof(double) * (size_t)d.cap64 * d.ld64));
     TRY(dalloc(s, &d.err, sizeof(unsigned int)));
     CU(cudaMemset(d.err, 0, sizeof(unsigned int)));
+    TRY(dalloc(s, &d.gates, sizeof(int) * kMqGates));
+    CU(cudaMemset(d.gates, 0, sizeof(int) * kMqGates));
+    for (int k = 0; k < 2; ++k) CU(cudaStreamCreateWithFlags(&s->helper[k], cudaStreamNonBlocking));
     for (int k = 0; k < 2; ++k) TRY(dalloc(s, &s->act32[k], sizeof(float) * (size_t)cap * s->wmax));
     if (bf16(s)) {
         for (const Udf &u : s->udfs)
@@ -546,6 +639,7 @@ hydro_status finalize(hydro_session *s) {
         TRY(dalloc(s, &sl.bidx, sizeof(long long) * Q));
         TRY(dalloc(s, &sl.npass, sizeof(long long) * Q));
         TRY(dalloc(s, &sl.total, sizeof(int)));
+        TRY(dalloc(s, &sl.gates, sizeof(int) * kMqGates));
     }
     s->finalized = true;
     return HYDRO_OK;
@@ -826,14 +920,37 @@ hydro_status hydro_session_submit(hydro_session *s, const void *d_tuples, const 
     if (s->cfg.use_graphs && !s->prof_on) {
         if (!slot->exec) {
             cudaGraph_t graph = nullptr;
-            CU(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+            CU(cudaGraphCreate(&graph, 0));
+            for (int k = 0; k < kMqGates; ++k) s->handles[k] = 0;
+            s->cap_graph = graph;
+            s->handle_err = HYDRO_OK;
+            cudaError_t be = cudaStreamBeginCaptureToGraph(s->st, graph, nullptr, nullptr, 0,
+                                                           cudaStreamCaptureModeThreadLocal);
+            if (be != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return fail(HYDRO_ECUDA, "capture: %s", cudaGetErrorString(be));
+            }
+            s->capturing = true;
+            s->if_depth = 0;
+            const cudaStream_t main_st = s->st;
             hydro_status rs = enqueue_step(s, *slot);
-            cudaError_t ce = cudaStreamEndCapture(s->st, &graph);
+            s->capturing = false;
+            // a failure inside a region leaves helper captures open: close them
+            while (s->if_depth > 0) {
+                cudaGraph_t g2 = nullptr;
+                cudaStreamEndCapture(s->helper[--s->if_depth], &g2);
+            }
+            s->st = main_st;
+            cudaGraph_t out = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(s->st, &out);
             if (rs != HYDRO_OK) {
-                if (graph) cudaGraphDestroy(graph);
+                cudaGraphDestroy(graph);
                 return rs;
             }
-            if (ce != cudaSuccess) return fail(HYDRO_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+            if (ce != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return fail(HYDRO_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+            }
             ce = cudaGraphInstantiate(&slot->exec, graph, 0);
             cudaGraphDestroy(graph);
             if (ce != cudaSuccess) return fail(HYDRO_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
@@ -868,6 +985,11 @@ hydro_status hydro_session_poll(hydro_session *s, int64_t step, uint32_t *pass_b
     if (!done) return fail(HYDRO_EAGAIN, "step %lld not finished", (long long)step);
     slot->busy = false;
     s->launches += slot->launches;
+    if (slot->conditional) {
+        int g[kMqGates];
+        CU(cudaMemcpy(g, slot->gates, sizeof g, cudaMemcpyDeviceToHost));
+        for (int k = 0; k < kMqGates; ++k) s->launches += g[k] ? slot->gate_body[k] : 0;
+    }
     for (ProfRec &r : slot->prof) {
         float ms = 0;
         if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
@@ -987,6 +1109,8 @@ hydro_status hydro_session_destroy(hydro_session *s) {
         if (sl.ev1) cudaEventDestroy(sl.ev1);
     }
     if (s->st) cudaStreamSynchronize(s->st);
+    for (int k = 0; k < 2; ++k)
+        if (s->helper[k]) cudaStreamDestroy(s->helper[k]);
     for (void *p : s->allocs) cudaFree(p);
     for (void *p : s->host_allocs) cudaFreeHost(p);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);

@@ -290,3 +290,21 @@ def test_session_full_workload_sampled():
         S = O.udf_scores("vec", streams[q][idx], [pool[u] for u in qs[q]["udfs"]])
         assert np.array_equal(b[idx], O.result_bits(O.pass_matrix(S, th[q]))), f"query {q}"
     s.close()
+
+
+def test_session_graph_skips_empty_regions(small):
+    """With graphs, each round and each recheck level is a conditional region
+    that runs only when it has work: same results, fewer kernel launches than
+    launching every kernel of every round."""
+    import torch
+    counts = {}
+    for graphs in (True, False):
+        s = make_session(small["w"], small["qs"], small["th"], precision="bf16",
+                         cap=len(small["queries"]) * small["chunk"], graphs=graphs, queries=small["queries"])
+        s.calibrate(torch.from_numpy(small["calib"]).cuda())
+        s.profile(False)   # resets the launch counter
+        res = run_session(s, small["streams"], small["chunk"])
+        check_steps(res, small["sims"], len(small["queries"]))
+        counts[graphs] = s.profile_read()[1]
+        s.close()
+    assert 0 < counts[True] < counts[False]
