@@ -834,6 +834,60 @@ def ours_mq64(args):
     }
 
 
+# ---------------------------------------------------------------- GEMM alone
+
+def ours_gemm_bf16(args):
+    """The tensor-core MLP layers alone: the widest pool UDF of the 64-query
+    workload (512-2048-1024-1) on 65,536 tuples per step through a query
+    that evaluates every tuple (one predicate, policy all, BF16), with
+    per-launch CUDA-event timing of the gather and the GEMM launches."""
+    import torch
+    ws, rank = dist_init("nccl")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_2403_14902_b300 as H
+    w = D.workload("mq64")
+    qs = D.mq_queries(w)
+    layers = D.mq_pool_weights(w)[6]
+    M = 65536
+    X = torch.from_numpy(np.concatenate([D.mq_tuples(w, q, 4096, qs) for q in range(M // 4096)])).cuda()
+    stream = torch.cuda.Stream()
+    q = H.Query("vec", dim=w.dim, max_batch=M, policy="all", precision="bf16", max_in_flight=1, stream=stream)
+    q.add_mlp(layers, 0.0)
+    q.set_margins(0, 0.0, 0.0, 0.0)   # no recheck: the GEMMs alone decide
+    f = lambda: q.poll(q.submit(X))[2]["n_pass"]  # noqa: E731
+    for _ in range(args.warmup):
+        f()
+    q.profile(True)
+    secs, npass = timed(f, args.steps, stream, local)
+    prof, launches = q.profile_read()
+    q.close()
+    secs = max_over_ranks(secs, device=torch.device("cuda", local))
+    if rank != 0:
+        return None
+    peaks, src = load_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]))
+    g = prof.get("mlp_layer_bf16_tc")
+    achieved = g["flops"] / (g["total_ms"] / 1000.0) / 1e12
+    return {
+        "metric": "tensor-core MLP GEMM throughput (BF16, FP32 accumulate)", "value": round(achieved, 2),
+        "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(secs / args.steps * 1000.0, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"gemm_bf16: MLP 512-2048-1024-1 on {M} x 512 fp32 tuples per step (gather to BF16, "
+                               "512->2048 stored, 2048->1024 with the one-output layer fused)",
+                   "rows": M, "l2": "fp32 input 134 MB, layer-2 operand 268 MB > 126 MB L2"},
+        "roofline": {"bound": "tensor", "kernel": "k_gemm_grouped_bf16_tc", "achieved": round(achieved, 2),
+                     "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": f"bf16_tflops_sustained ({src})", "launches": g["launches"],
+                     "avg_launch_ms": round(g["total_ms"] / max(1, g["launches"]), 4)},
+        "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
+                        "tflops": round(v["flops"] / max(v["total_ms"], 1e-9) / 1e9, 2),
+                        "gbs": round(v["bytes"] / max(v["total_ms"], 1e-9) / 1e6, 1)} for k, v in prof.items()},
+        "gpu_launches": int(launches), "tuples_per_s": round(aggregate(M, args.steps, secs, ws), 1),
+    }
+
+
 # ---------------------------------------------------------------- reference arm
 
 def reference(args):
@@ -848,6 +902,8 @@ def reference(args):
     th = thresholds(name)
     if name == "mq64":
         return reference_mq64(args, w, th)
+    if name == "gemm_bf16":
+        return reference_gemm(args)
     n = 8 if w.kind == "frame" else 4096
     F = D.stream_tuples(w, n)
     ws_ = D.predicate_weights(w)
@@ -865,6 +921,31 @@ def reference(args):
             "cpu_baseline": {"value": round(value, 3), "unit": "tuples/s", "cores": O.threads(), "kind": "oracle",
                              "sample": f"{n} tuples per step, every UDF in FP64"},
             "e2e": {"value": round(value, 3), "unit": "tuples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def reference_gemm(args):
+    """Oracle per step: the 512-2048-1024-1 UDF in FP64 on 1,024 tuples."""
+    import oracle as O
+    ws, _ = dist_env()[:2]
+    w = D.workload("mq64")
+    layers = D.mq_pool_weights(w)[6]
+    X = D.mq_tuples(w, 0, 1024)
+    for _ in range(args.warmup):
+        O.udf_scores("vec", X[:8], [layers])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.udf_scores("vec", X, [layers])
+    dt = time.perf_counter() - t0
+    flops = 2 * (512 * 2048 + 2048 * 1024) * X.shape[0] * args.steps
+    value = flops / dt / 1e12
+    return {"impl": "reference", "metric": "tensor-core MLP GEMM throughput (BF16, FP32 accumulate)",
+            "value": round(value, 5), "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1000.0, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "gemm_bf16: oracle FP64 MLP 512-2048-1024-1 on 1,024 tuples per step"},
+            "cpu_baseline": {"value": round(value, 5), "unit": "TFLOP/s", "cores": O.threads(), "kind": "oracle",
+                             "sample": "1,024 tuples per step"},
+            "e2e": {"value": round(value, 5), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def reference_mq64(args, w, th):
@@ -901,12 +982,13 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cnn4", "drift5", "drift6", "mq64"], default=WORKLOAD)
+    ap.add_argument("--workload", choices=["cnn4", "drift5", "drift6", "mq64", "gemm_bf16"], default=WORKLOAD)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         out = reference(args)
     else:
-        out = {"cnn4": ours, "drift5": ours_drift5, "drift6": ours_drift6, "mq64": ours_mq64}[args.workload](args)
+        out = {"cnn4": ours, "drift5": ours_drift5, "drift6": ours_drift6, "mq64": ours_mq64,
+               "gemm_bf16": ours_gemm_bf16}[args.workload](args)
     if out is not None:
         print(json.dumps(out), flush=True)
 

@@ -442,8 +442,9 @@ HYDRO_API hydro_status hydro_session_calibrate(hydro_session *s, const void *d_t
 HYDRO_API hydro_status hydro_session_udf_scores(hydro_session *s, int32_t udf, int32_t prec, const void *d_tuples,
                                                 int64_t n, double *d_scores);
 
-/* Submit one step.  d_tuples: device fp32 rows, counts[0] rows of query 0,
- * then counts[1] rows of query 1, ... (BORROWED until the step is polled).
+/* Submit one step.  d_tuples: device fp32 rows, 16-byte aligned, counts[0]
+ * rows of query 0, then counts[1] rows of query 1, ... (BORROWED until the
+ * step is polled).
  * counts: host [n_queries], each >= 0, sum <= max_step_tuples.  A query with
  * count 0 sits the step out (its batch number does not advance).
  * Asynchronous; *out_step receives 0, 1, 2, ... */

@@ -392,7 +392,7 @@ hydro_status finalize(hydro_query *q) {
         if (c.precision == HYDRO_PREC_BF16) {
             TRY(dalloc(q, &q->stage16, sizeof(__nv_bfloat16) * (size_t)B * c.dim));
             for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->act16[k], sizeof(__nv_bfloat16) * (size_t)wmax * B));
-            TRY(dalloc(q, &q->partials, sizeof(float) * (size_t)B * std::max(1, wmax / 64)));
+            TRY(dalloc(q, &q->partials, sizeof(float) * (size_t)B * 2 * std::max(1, wmax / 64)));
             hydro_status s = tc_gemm_init(&q->gemm_encode);
             if (s != HYDRO_OK) return fail(s, "tensor-core GEMM init failed: %s", tc_gemm_last_error());
         }

@@ -257,7 +257,11 @@ __global__ void __launch_bounds__(256) k_mq_dot_f32(MqLayers L, float *score, in
 // level counts its own).  The split-BF16 level runs only on a band of at
 // least kMinSplitRows rows: below that its launches return at once and every
 // entry passes on to the FP32 level unscored.
-__global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int in, int out, Cond next, int next_min) {
+// heads.tiles[g] > 0 (tensor-core levels): the entry's score is summed here
+// from the GEMM's head partials (row i of the stacked operand, fixed order)
+// plus the head bias, instead of read from the level's score list.
+__global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int in, int out, Cond next, int next_min,
+                                                     TcHeads heads, const float *partials, int pstride) {
     const int *cnts = d.rc->n[in];
     const int *lists = d.list[in];
     const float *sc = d.score[in];
@@ -284,7 +288,15 @@ __global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int in, int
                 inband = true;
             } else {
                 const double t = d.thr[q * kMqSlots + slot];
-                const double s = (double)sc[(size_t)g * d.cap + m];
+                double s;
+                if (partials) {
+                    const float *pp = partials + (size_t)i * pstride;
+                    float a = 0.f;
+                    for (int j = 0; j < heads.tiles[g]; ++j) a += pp[j];
+                    s = (double)heads.b[g] + (double)a;
+                } else {
+                    s = (double)sc[(size_t)g * d.cap + m];
+                }
                 inband = fabs(s - t) <= (double)margin[g];
                 pass = !inband && s > t;
                 d.ok[e] = (unsigned char)pass;
@@ -305,6 +317,41 @@ __global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int in, int
         for (int g = 0; g < d.G; ++g) tot += *((volatile int *)&next_cnt[g]);
         set_cond(next, tot >= next_min);
     }
+}
+
+// Lane `lane`'s share of the dot product w . x over K (fp32 weights, x in
+// float or T): 16-byte loads and four independent accumulators when K is a
+// multiple of 128 (every row 16-byte aligned), else one element at a time.
+__device__ __forceinline__ void load4(const float *p, float (&v)[4]) {
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+}
+__device__ __forceinline__ void load4(const float *p, double (&v)[4]) {
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+}
+__device__ __forceinline__ void load4(const double *p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+template <typename T, typename X>
+__device__ __forceinline__ T lane_dot(const float *w, const X *x, int K) {
+    const int lane = lane_id();
+    if ((K & 127) == 0) {
+        T a[4] = {0, 0, 0, 0};
+        for (int k = 4 * lane; k < K; k += 128) {
+            float wv[4];
+            T xv[4];
+            load4(w + k, wv);
+            load4(x + k, xv);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] += (T)wv[i] * xv[i];
+        }
+        return (a[0] + a[1]) + (a[2] + a[3]);
+    }
+    T s = 0;
+    for (int k = lane; k < K; k += 32) s += (T)w[k] * (T)x[k];
+    return s;
 }
 
 // Band levels run layer-parallel: a warp per (entry, output neuron) of one
@@ -341,14 +388,8 @@ __global__ void __launch_bounds__(256) k_mq_band_layer(MqDev d, GroupedMlps mlps
         const int el = local / N, o = local % N;
         const int j = off[g] + el;
         const float *wr = m.W[depth] + (size_t)o * K;
-        T s = 0;
-        if (depth == 0) {
-            const float *x = X + (size_t)list[(size_t)g * d.cap + el] * d.dim;
-            for (int k = lane_id(); k < K; k += 32) s += (T)wr[k] * (T)x[k];
-        } else {
-            const T *x = in_act + (size_t)j * ld;
-            for (int k = lane_id(); k < K; k += 32) s += (T)wr[k] * x[k];
-        }
+        T s = depth == 0 ? lane_dot<T>(wr, X + (size_t)list[(size_t)g * d.cap + el] * d.dim, K)
+                         : lane_dot<T>(wr, in_act + (size_t)j * ld, K);
 #pragma unroll
         for (int dd = 16; dd > 0; dd >>= 1) s += __shfl_xor_sync(0xffffffffu, s, dd);
         if (lane_id() == 0) {
@@ -358,12 +399,12 @@ __global__ void __launch_bounds__(256) k_mq_band_layer(MqDev d, GroupedMlps mlps
     }
 }
 
-// The one-output last layer, a warp per entry.  FP32 level: the score into
-// the level's score list (decided by the level's classify).  FP64 level: the
-// exact verdict and its statistics.
+// The one-output last layer, a warp per entry, and the verdict.  FP32 level:
+// decided unless within margin_fp32 of the threshold, else on to the FP64
+// level (whose condition `next` the last block sets).  FP64 level: exact.
 template <typename T>
 __global__ void __launch_bounds__(256) k_mq_band_final(MqDev d, GroupedMlps mlps, int level, int r, T *act0,
-                                                       T *act1, int ld, int cap_lv) {
+                                                       T *act1, int ld, int cap_lv, Cond next) {
     int off[kMqPool + 1], wstart[kMqPool + 1];
     band_offsets(d, mlps, level, cap_lv, -1, off, wstart);
     const float *X = d.hdr->X;
@@ -376,32 +417,42 @@ __global__ void __launch_bounds__(256) k_mq_band_final(MqDev d, GroupedMlps mlps
         const int el = j - off[g];
         const int e = list[(size_t)g * d.cap + el];
         const float *wr = m.W[L - 1];
-        T s = 0;
-        if (L == 1) {
-            const float *x = X + (size_t)e * d.dim;
-            for (int k = lane_id(); k < K; k += 32) s += (T)wr[k] * (T)x[k];
-        } else {
-            const T *x = (((L - 2) & 1) ? act1 : act0) + (size_t)j * ld;
-            for (int k = lane_id(); k < K; k += 32) s += (T)wr[k] * x[k];
-        }
+        T s = L == 1 ? lane_dot<T>(wr, X + (size_t)e * d.dim, K)
+                     : lane_dot<T>(wr, (((L - 2) & 1) ? act1 : act0) + (size_t)j * ld, K);
 #pragma unroll
         for (int dd = 16; dd > 0; dd >>= 1) s += __shfl_xor_sync(0xffffffffu, s, dd);
         if (lane_id() != 0) continue;
         s += (T)m.b[L - 1][0];
-        if (sizeof(T) == 4) {
-            d.score[LV_F32][(size_t)g * d.cap + el] = (float)s;
-            continue;
-        }
         const int q = d.qid[e];
         const int slot = d.order[q * kMqSlots + r];
-        const bool pass = (double)s > d.thr[q * kMqSlots + slot];
-        d.ok[e] = (unsigned char)pass;
+        const double t = d.thr[q * kMqSlots + slot];
         StatRow *row = d.rows + q * kMqSlots + slot;
+        bool pass;
+        if (sizeof(T) == 4) {
+            // FP32: the float score, then the FP32 test
+            const double sf = (double)(float)s;
+            atomicAdd(ctr(row, F_R32), 1ull);
+            if (fabs(sf - t) <= (double)d.margin[LV_F32][g]) {
+                const int pos = atomicAdd(&d.rc->n[LV_F64][g], 1);
+                d.list[LV_F64][(size_t)g * d.cap + pos] = e;
+                continue;
+            }
+            pass = sf > t;
+        } else {
+            pass = (double)s > t;
+            atomicAdd(ctr(row, F_R64), 1ull);
+        }
+        d.ok[e] = (unsigned char)pass;
         if (pass) {
             d.label[e] |= (unsigned char)(1u << slot);
             atomicAdd(ctr(row, F_PASS), 1ull);
         }
-        atomicAdd(ctr(row, F_R64), 1ull);
+    }
+    if (next.flag && last_block(&d.rc->ticket[level]) && threadIdx.x == 0) {
+        __threadfence();
+        int tot = 0;
+        for (int g = 0; g < d.G; ++g) tot += *((volatile int *)&d.rc->n[LV_F64][g]);
+        set_cond(next, tot > 0);
     }
 }
 
@@ -465,6 +516,8 @@ __global__ void __launch_bounds__(256) k_mq_band64(MqDev d, int r, GroupedMlps m
 __global__ void __launch_bounds__(256) k_mq_survivors(MqDev d, int r, Cond next_round) {
     const int cur = r & 1;
     const int n = d.rc->alive[cur];
+    // every level of this round is done: clear the level lists for the next round
+    if (blockIdx.x == 0 && threadIdx.x < LV_N * kMqPool) (&d.rc->n[0][0])[threadIdx.x] = 0;
     for (int m0 = blockIdx.x * blockDim.x; m0 < n; m0 += gridDim.x * blockDim.x) {
         const int m = m0 + threadIdx.x;
         bool keep = false;
@@ -483,10 +536,6 @@ __global__ void __launch_bounds__(256) k_mq_survivors(MqDev d, int r, Cond next_
     }
 }
 
-__global__ void k_mq_clear_round(RoundCounters *rc) {
-    const int i = threadIdx.x;
-    if (i < LV_N * kMqPool) (&rc->n[0][0])[i] = 0;
-}
 
 // Result bitmap (bit e: every slot of e's query passed) and passes per query.
 __global__ void __launch_bounds__(256) k_mq_result(MqDev d, unsigned int *bitmap) {
@@ -579,7 +628,6 @@ void mq_launch_router(const MqDev &d, const MqHist &h, cudaStream_t st) {
 }
 
 void mq_launch_partition(const MqDev &d, int r, cudaStream_t st, int sms) {
-    if (r > 0) k_mq_clear_round<<<1, LV_N * kMqPool, 0, st>>>(d.rc);
     k_mq_partition<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r);
 }
 
@@ -591,22 +639,27 @@ void mq_launch_dots_f32(const MqLayers &L, float *score, int sstride, cudaStream
     k_mq_dot_f32<<<sms * 8, 256, 0, st>>>(L, score, sstride);
 }
 
-void mq_launch_classify(const MqDev &d, int r, int in, int out, cudaStream_t st, int sms, Cond next, int next_min) {
-    k_mq_classify<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r, in, out, next, next_min);
+void mq_launch_classify(const MqDev &d, int r, int in, int out, cudaStream_t st, int sms, Cond next, int next_min,
+                        const TcHeads *heads, const float *partials, int pstride) {
+    TcHeads h{};
+    if (heads) h = *heads;
+    k_mq_classify<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r, in, out, next, next_min, h,
+                                                                partials, pstride);
 }
 
 void mq_launch_band32(const MqDev &d, int r, const GroupedMlps &mlps, int max_hidden, float *act0, float *act1,
-                      int ld, cudaStream_t st, int sms) {
+                      int ld, cudaStream_t st, int sms, Cond next) {
     for (int depth = 0; depth < max_hidden; ++depth)
         k_mq_band_layer<float><<<sms * 8, 256, 0, st>>>(d, mlps, LV_F32, depth, act0, act1, ld, d.cap);
-    k_mq_band_final<float><<<sms * 2, 256, 0, st>>>(d, mlps, LV_F32, r, act0, act1, ld, d.cap);
+    k_mq_band_final<float><<<sms * 2, 256, 0, st>>>(d, mlps, LV_F32, r, act0, act1, ld, d.cap, next);
 }
 
 void mq_launch_band64(const MqDev &d, int r, const GroupedMlps &mlps, int max_hidden, cudaStream_t st, int sms) {
     for (int depth = 0; depth < max_hidden; ++depth)
         k_mq_band_layer<double><<<sms * 8, 256, 0, st>>>(d, mlps, LV_F64, depth, d.act64[0], d.act64[1], d.ld64,
                                                          d.cap64);
-    k_mq_band_final<double><<<sms * 2, 256, 0, st>>>(d, mlps, LV_F64, r, d.act64[0], d.act64[1], d.ld64, d.cap64);
+    k_mq_band_final<double><<<sms * 2, 256, 0, st>>>(d, mlps, LV_F64, r, d.act64[0], d.act64[1], d.ld64, d.cap64,
+                                                     Cond());
     const size_t smem = sizeof(double) * 2 * (size_t)mlps.max_width;
     k_mq_band64<<<sms, 256, smem, st>>>(d, r, mlps);
 }

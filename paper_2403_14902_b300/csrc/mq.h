@@ -8,6 +8,7 @@
 #include "../../include/hydro.h"
 #include "common.cuh"
 #include "internal.h"
+#include "tc_gemm.h"
 
 namespace hydro {
 
@@ -116,17 +117,21 @@ void mq_launch_layers_f32(const MqLayers &L, cudaStream_t st, int sms);
 void mq_launch_dots_f32(const MqLayers &L, float *score, int sstride, cudaStream_t st, int sms);
 // Decide the entries of level `in` with that level's scores and margins;
 // undecided entries go to level `out`'s lists.
-// h_next: set to (level `out` holds at least next_min entries).
+// next: set to (level `out` holds at least next_min entries).  With
+// partials (tensor-core levels) the scores are summed from the GEMM's head
+// partials (heads: per group bias and partials per row) in this kernel.
 void mq_launch_classify(const MqDev &d, int r, int in, int out, cudaStream_t st, int sms, Cond next = Cond(),
-                        int next_min = 1);
+                        int next_min = 1, const TcHeads *heads = nullptr, const float *partials = nullptr,
+                        int pstride = 0);
 // The FP64 level: every entry's UDF in FP64, its layers spread over all SMs
 // (a warp per output neuron), the first cap64 entries of the round; the rest
 // a block per entry.  Decides exactly.
 void mq_launch_band64(const MqDev &d, int r, const GroupedMlps &mlps, int max_hidden, cudaStream_t st, int sms);
-// The FP32 level of BF16 sessions, layer-parallel like the FP64 level;
-// writes the level's scores (act0/act1: [cap][ld] floats).
+// The FP32 level of BF16 sessions, layer-parallel like the FP64 level, with
+// its own test (margin_fp32; undecided entries go to the FP64 level, whose
+// condition `next` it sets; act0/act1: [cap][ld] floats).
 void mq_launch_band32(const MqDev &d, int r, const GroupedMlps &mlps, int max_hidden, float *act0, float *act1,
-                      int ld, cudaStream_t st, int sms);
+                      int ld, cudaStream_t st, int sms, Cond next = Cond());
 // h_next_round: set to (the next alive list is not empty).
 void mq_launch_survivors(const MqDev &d, int r, cudaStream_t st, int sms, Cond next_round = Cond());
 void mq_launch_result(const MqDev &d, unsigned int *bitmap, cudaStream_t st, int sms);

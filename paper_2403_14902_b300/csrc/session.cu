@@ -187,8 +187,10 @@ int *rc_n(const MqDev &d, int level) {
 // Rows of all lists of a level as one stacked operand: the layers of one
 // depth for every group in one launch (BF16 on the tensor cores; split3: the
 // split-BF16 form, operands [hi | hi | lo] against [W_hi | W_lo | W_hi]).
+// heads_out: return the heads and leave the head partials for a fused
+// classify (no finalize launch); else finalize into score.
 hydro_status eval_tc(hydro_session *s, const int *counts, const int *lists, float *score, bool split3,
-                     int min_rows = 0) {
+                     int min_rows = 0, TcHeads *heads_out = nullptr) {
     const MqDev &d = s->d;
     const int x = split3 ? 3 : 1;
     __nv_bfloat16 *stage = split3 ? s->stage3 : s->stage16;
@@ -221,7 +223,7 @@ hydro_status eval_tc(hydro_session *s, const int *counts, const int *lists, floa
                                 has ? u.nt[dd] : 0};
             if (head) {
                 heads.b[g] = u.b[u.n_layers - 1][0];
-                heads.tiles[g] = u.nt[dd] ? u.dims[dd + 1] / u.nt[dd] : tc_gemm_col_tiles(u.dims[dd + 1]);
+                heads.tiles[g] = tc_gemm_head_parts(u.dims[dd + 1], u.nt[dd]);
             }
         }
         pe = prof_begin(s, SP_GEMM);
@@ -230,6 +232,10 @@ hydro_status eval_tc(hydro_session *s, const int *counts, const int *lists, floa
         prof_end(s, pe);
         if (rs != HYDRO_OK) return fail(rs, "grouped tensor-core GEMM: %s", tc_gemm_last_error());
         s->step_launches++;
+    }
+    if (heads_out) {
+        *heads_out = heads;
+        return HYDRO_OK;
     }
     pe = prof_begin(s, SP_FINAL);
     launch_head_finalize_grouped(d.G, counts, heads, s->partials, s->pstride, score, d.cap, d.cap, s->sms, s->st,
@@ -362,32 +368,35 @@ hydro_status enqueue_step(hydro_session *s, Slot &slot) {
     mq_launch_router(d, s->h, s->st);
     prof_end(s, pe);
     s->step_launches += 2;
-    auto classify = [&](int r, int in, int out, Cond next, int next_min) {
+    auto classify = [&](int r, int in, int out, Cond next, int next_min, const TcHeads *heads = nullptr) {
         const int p = prof_begin(s, SP_CTRL);
-        mq_launch_classify(d, r, in, out, s->st, s->sms, next, next_min);
+        mq_launch_classify(d, r, in, out, s->st, s->sms, next, next_min, heads, heads ? s->partials : nullptr,
+                           s->pstride);
         prof_end(s, p);
         s->step_launches++;
     };
+    TcHeads heads{};
     cudaStream_t sv_round = nullptr, sv = nullptr;
     for (int r = 0; r < s->maxP; ++r) {
         TRY(open_if(s, slot, gate(r, 0), &sv_round));
         pe = prof_begin(s, SP_CTRL);
         mq_launch_partition(d, r, s->st, s->sms);
         prof_end(s, pe);
-        s->step_launches += r > 0 ? 2 : 1;
+        s->step_launches++;
         if (bf) {
-            TRY(eval_tc(s, rc_n(d, LV_MAIN), d.list[LV_MAIN], d.score[LV_MAIN], false));
-            classify(r, LV_MAIN, LV_X3, cond_of(s, gate(r, 1)), kMinSplitRows);
+            TRY(eval_tc(s, rc_n(d, LV_MAIN), d.list[LV_MAIN], d.score[LV_MAIN], false, 0, &heads));
+            classify(r, LV_MAIN, LV_X3, cond_of(s, gate(r, 1)), kMinSplitRows, &heads);
             TRY(open_if(s, slot, gate(r, 1), &sv));
-            TRY(eval_tc(s, rc_n(d, LV_X3), d.list[LV_X3], d.score[LV_X3], true, kMinSplitRows));
+            TRY(eval_tc(s, rc_n(d, LV_X3), d.list[LV_X3], d.score[LV_X3], true, kMinSplitRows, &heads));
             TRY(close_if(s, slot, gate(r, 1), sv));
-            classify(r, LV_X3, LV_F32, cond_of(s, gate(r, 2)), 1);
+            // decides the split level's entries, or forwards them all when it was skipped
+            classify(r, LV_X3, LV_F32, cond_of(s, gate(r, 2)), 1, &heads);
             TRY(open_if(s, slot, gate(r, 2), &sv));
             pe = prof_begin(s, SP_LAYER);
-            mq_launch_band32(d, r, s->mlps, s->max_hidden, s->act32[0], s->act32[1], s->wmax, s->st, s->sms);
+            mq_launch_band32(d, r, s->mlps, s->max_hidden, s->act32[0], s->act32[1], s->wmax, s->st, s->sms,
+                             cond_of(s, gate(r, 3)));
             prof_end(s, pe);
             s->step_launches += s->max_hidden + 1;
-            classify(r, LV_F32, LV_F64, cond_of(s, gate(r, 3)), 1);
             TRY(close_if(s, slot, gate(r, 2), sv));
         } else {
             eval_f32(s, rc_n(d, LV_MAIN), d.list[LV_MAIN], d.score[LV_MAIN]);
@@ -604,7 +613,7 @@ hydro_status finalize(hydro_session *s) {
         for (int k = 0; k < 2; ++k) TRY(dalloc(s, &s->act16[k], sizeof(__nv_bfloat16) * (size_t)cap * s->wmax));
         TRY(dalloc(s, &s->stage3, sizeof(__nv_bfloat16) * (size_t)cap * 3 * c.dim));
         for (int k = 0; k < 2; ++k) TRY(dalloc(s, &s->act3[k], sizeof(__nv_bfloat16) * (size_t)cap * 3 * s->wmax));
-        s->pstride = s->wmax / 64;
+        s->pstride = 2 * (s->wmax / 64);
         TRY(dalloc(s, &s->partials, sizeof(float) * (size_t)cap * s->pstride));
         hydro_status rs = tc_gemm_init(&s->encode);
         if (rs != HYDRO_OK) return fail(rs, "tensor-core GEMM init: %s", tc_gemm_last_error());
@@ -797,6 +806,7 @@ hydro_status hydro_session_udf_scores(hydro_session *s, int32_t udf, int32_t pre
     TRY(check(s));
     if (udf < 0 || udf >= (int)s->udfs.size()) return fail(HYDRO_EINVAL, "unknown pool UDF");
     if (n < 0 || (n > 0 && (!d_tuples || !d_scores))) return fail(HYDRO_EINVAL, "bad tuples/scores");
+    if ((uintptr_t)d_tuples % 16) return fail(HYDRO_EINVAL, "tuples must be 16-byte aligned");
     if (prec != HYDRO_PREC_FP64 && prec != HYDRO_PREC_FP32 && prec != HYDRO_PREC_BF16 && prec != HYDRO_PREC_BF16X3)
         return fail(HYDRO_EINVAL, "precision must be FP64, FP32, BF16 or BF16X3");
     if ((prec == HYDRO_PREC_BF16 || prec == HYDRO_PREC_BF16X3) && !bf16(s))
@@ -898,6 +908,7 @@ hydro_status hydro_session_submit(hydro_session *s, const void *d_tuples, const 
     }
     if (total > s->cfg.max_step_tuples) return fail(HYDRO_EINVAL, "step of %lld tuples > max_step_tuples", total);
     if (total > 0 && !d_tuples) return fail(HYDRO_EINVAL, "NULL tuples");
+    if ((uintptr_t)d_tuples % 16) return fail(HYDRO_EINVAL, "tuples must be 16-byte aligned");
     Slot *slot = nullptr;
     for (Slot &sl : s->slots)
         if (!sl.busy) {

@@ -70,7 +70,13 @@ __device__ __forceinline__ int tile_group(const int *start, int n, int t) {
     return g;
 }
 
-__global__ void __launch_bounds__(192, 1) k_gemm_grouped_bf16_tc(const __grid_constant__ TcLaunch L) {
+// Warp roles: 0 TMA, 1 MMA (owns TMEM), 2-9 epilogue.  Epilogue warp w reads
+// TMEM lanes 32 (w % 4) .. + 31 (its rows) and one half of the tile's
+// columns, (w - 2) / 4; a head partial is left per row, tile and half.
+constexpr int kGemmThreads = 320;
+constexpr int kEpiWarps = 8;
+
+__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const __grid_constant__ TcLaunch L) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int S = L.S;
@@ -93,7 +99,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_grouped_bf16_tc(const __grid_co
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
+            mbar_init(&tempty[b], kEpiWarps);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -187,6 +193,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_grouped_bf16_tc(const __grid_co
         }
     } else {
         const int qtr = warp & 3;
+        const int chalf = (warp - 2) >> 2;
         int tl = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
             const int buf = tl & 1;
@@ -207,7 +214,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_grouped_bf16_tc(const __grid_co
             const float *hw = G.head_w ? G.head_w + n0 : nullptr;
             float hsum = 0.f;
 #pragma unroll 1
-            for (int c0 = 0; c0 < NT; c0 += 32) {
+            for (int c0 = chalf * (NT >> 1); c0 < (chalf + 1) * (NT >> 1); c0 += 32) {
                 uint32_t r[32];
                 tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * half + c0), r);
                 tmem_ld_wait();
@@ -246,7 +253,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_grouped_bf16_tc(const __grid_co
                     }
                 }
             }
-            if (hw && live) L.partials[row * L.pstride + tn] = hsum;
+            if (hw && live) L.partials[row * L.pstride + 2 * tn + chalf] = hsum;
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[buf]);
@@ -409,7 +416,8 @@ hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n,
             continue;
         }
         if (!tc_gemm_supported(h.K, h.N) || (h.nt && (h.nt % 64 || h.nt > 256 || h.N % h.nt)) || h.x_rows < 1 || (h.ldx % 8) != 0 || h.ldx < h.K ||
-            (!h.head_w && (split3 ? 3 * h.N : h.N) > ldy) || (h.head_w && h.N / (h.nt ? h.nt : col_tile(h.N)) > pstride)) {
+            (!h.head_w && (split3 ? 3 * h.N : h.N) > ldy) ||
+            (h.head_w && 2 * (h.N / (h.nt ? h.nt : col_tile(h.N))) > pstride)) {
             g_gemm_err = "tensor-core GEMM: unsupported group shape";
             return HYDRO_EUNSUPPORTED;
         }
@@ -442,7 +450,7 @@ hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n,
     L.min_rows = min_rows;
     if (tiles == 0) return HYDRO_OK;   // only rows-only groups
     const int grid = (int)(tiles < sms ? tiles : sms);
-    k_gemm_grouped_bf16_tc<<<grid, 192, kGemmSmem, st>>>(L);
+    k_gemm_grouped_bf16_tc<<<grid, kGemmThreads, kGemmSmem, st>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         g_gemm_err = std::string("launch: ") + cudaGetErrorString(e);
@@ -458,7 +466,9 @@ hydro_status tc_gemm_run(void *encode, const int *count, const __nv_bfloat16 *X,
     return tc_gemm_grouped_run(encode, &g, 1, Y, N, partials, tc_gemm_col_tiles(N), sms, st, err);
 }
 
-int tc_gemm_col_tiles(int N) { return N / col_tile(N); }
+int tc_gemm_col_tiles(int N) { return 2 * (N / col_tile(N)); }
+
+int tc_gemm_head_parts(int N, int nt) { return 2 * (N / (nt ? nt : col_tile(N))); }
 
 void launch_gather_bf16(const int *count, const int *rows, const float *X, int ldx, int K, __nv_bfloat16 *out,
                         int max_rows, int sms, cudaStream_t st) {

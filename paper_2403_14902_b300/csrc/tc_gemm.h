@@ -25,7 +25,7 @@ struct TcGemmGroup {
 };
 // A group with W == nullptr contributes only its row count to the stacking.
 
-struct TcHeads {                 // per group: head bias and column tiles of the last hidden layer
+struct TcHeads {                 // per group: head bias and head partials per row of the last hidden layer
     float b[kMaxGroups];
     int tiles[kMaxGroups];
 };
@@ -37,11 +37,14 @@ hydro_status tc_gemm_init(void **encode);
 // Y[m] = relu(X[m] W^T + bias) (bf16, [rows][N]) for m < *count; X is bf16
 // [max_rows][K], W bf16 [N][K].  With head_w (the UDF's one-output last layer,
 // fp32 [N]) nothing is stored to Y: partials[m * tc_gemm_col_tiles(N) + j]
-// receives head_w . relu(...) over column tile j.
+// receives head_w . relu(...) over column half-tile j.
 hydro_status tc_gemm_run(void *encode, const int *count, const __nv_bfloat16 *X, int K, const __nv_bfloat16 *W,
                          const float *bias, int N, __nv_bfloat16 *Y, int max_rows, int sms, cudaStream_t st,
                          unsigned int *err, const float *head_w = nullptr, float *partials = nullptr);
+// Head partials per row of a fused-head layer of width N (two per column
+// tile: the epilogue's column halves); nt as in TcGemmGroup.
 int tc_gemm_col_tiles(int N);
+int tc_gemm_head_parts(int N, int nt);
 // All groups' layers of one depth in one persistent launch.  Y (stacked,
 // row stride ldy) receives the groups without a head; partials (stacked, row
 // stride pstride) the head partials of the others.
