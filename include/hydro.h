@@ -380,6 +380,18 @@ typedef struct hydro_session_config {
     int32_t max_in_flight;    /* submitted, unpolled steps, 1..8 */
     int32_t device;           /* CUDA device ordinal */
     void *stream;             /* cudaStream_t the steps run on; NULL = library stream */
+    int32_t learned;          /* 1: per-tuple orders from a learned proxy of the pass probabilities
+                                 (content-based routing, Sec. 2.2), as HYDRO_POLICY_LEARNED does for
+                                 one query: a proxy MLP dim -> proxy_hidden -> P predicts each slot's
+                                 pass probability p, each tuple visits its slots by c (1 + e^z),
+                                 z = logit(p); trained online (Adam, masked BCE) on the outcomes of
+                                 the last proxy_refresh steps every proxy_refresh steps; rank orders
+                                 until the first training.  Sessions with one query only */
+    int32_t proxy_hidden;     /* learned: proxy hidden width (default 64) */
+    int32_t proxy_refresh;    /* learned: train after every this many steps (default 16) */
+    int32_t proxy_epochs;     /* learned: passes over the stored steps per training (default 1) */
+    float proxy_lr;           /* learned: Adam learning rate (default 1e-3) */
+    int32_t proxy_seed;       /* learned: seed of the proxy's initial weights */
 } hydro_session_config;
 
 /* Per query result of one step (hydro_session_poll). */
@@ -405,7 +417,8 @@ typedef struct hydro_tile_choice {
 } hydro_tile_choice;
 
 /* Defaults: FP32, warmup 1, window 8, graphs on, autotune on, 2 in flight,
- * device 0, NULL stream; dim and max_step_tuples must be set. */
+ * device 0, NULL stream, not learned (proxy 64 hidden, refresh 16, 1 epoch,
+ * lr 1e-3, seed 1); dim and max_step_tuples must be set. */
 HYDRO_API void hydro_session_default_config(hydro_session_config *cfg);
 
 HYDRO_API hydro_status hydro_session_create(const hydro_session_config *cfg, hydro_session **out);
@@ -457,6 +470,12 @@ HYDRO_API hydro_status hydro_session_submit(hydro_session *s, const void *d_tupl
  * wait_ms as in hydro_poll_result; HYDRO_EAGAIN if not finished. */
 HYDRO_API hydro_status hydro_session_poll(hydro_session *s, int64_t step, uint32_t *pass_bitmap,
                                           hydro_step_query *per_query, double *device_ms, int32_t wait_ms);
+
+/* Per-tuple trace of step `step` (polled, and the last step submitted):
+ * order[total * 8] receives each stacked tuple's slot order (first n_preds
+ * bytes of its query used) and visited[total] the bit set of slots it was
+ * evaluated on.  Synchronous. */
+HYDRO_API hydro_status hydro_session_debug_trace(hydro_session *s, int64_t step, uint8_t *order, uint8_t *visited);
 
 /* Autotuner records (after the first submit): out[max], *n_out written. */
 HYDRO_API hydro_status hydro_session_tuning(hydro_session *s, hydro_tile_choice *out, int32_t max, int32_t *n_out);

@@ -37,7 +37,7 @@ EXPORTED = ["hydro_default_config", "hydro_create_query", "hydro_add_predicate",
             "hydro_session_default_config", "hydro_session_create", "hydro_session_add_udf",
             "hydro_session_add_query", "hydro_session_set_margins", "hydro_session_calibrate",
             "hydro_session_udf_scores", "hydro_session_submit", "hydro_session_poll", "hydro_session_tuning",
-            "hydro_session_profile", "hydro_session_profile_read",
+            "hydro_session_profile", "hydro_session_profile_read", "hydro_session_debug_trace",
             "hydro_session_destroy", "hydro_destroy_query", "hydro_last_error"]
 MAX_QUERIES = 256
 MAX_POOL = 8
@@ -88,7 +88,9 @@ class SessionConfig(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("max_step_tuples", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("warmup_batches", ctypes.c_int32), ("stats_window", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("max_in_flight", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("learned", ctypes.c_int32), ("proxy_hidden", ctypes.c_int32),
+                ("proxy_refresh", ctypes.c_int32), ("proxy_epochs", ctypes.c_int32), ("proxy_lr", ctypes.c_float),
+                ("proxy_seed", ctypes.c_int32)]
 
 
 class StepQuery(ctypes.Structure):
@@ -154,6 +156,7 @@ def load():
     L.hydro_session_tuning.argtypes = [vp, P(TileChoice), i32, P(i32)]
     L.hydro_session_destroy.argtypes = [vp]
     L.hydro_session_profile.argtypes = [vp, i32]
+    L.hydro_session_debug_trace.argtypes = [vp, i64, P(ctypes.c_uint8), P(ctypes.c_uint8)]
     L.hydro_session_profile_read.argtypes = [vp, P(KernelProfile), i32, P(i32), P(i64)]
     L.hydro_last_error.argtypes = []
     L.hydro_last_error.restype = ctypes.c_char_p
@@ -411,7 +414,8 @@ class Session:
 
     def __init__(self, *, dim: int, max_step_tuples: int, precision: str = "fp32", warmup: int = 1,
                  window: int = 8, graphs: bool = True, autotune: bool = True, max_in_flight: int = 2,
-                 device: int = 0, stream=None):
+                 device: int = 0, stream=None, learned: bool = False, proxy_hidden: int = 64,
+                 proxy_refresh: int = 16, proxy_epochs: int = 1, proxy_lr: float = 1e-3, proxy_seed: int = 1):
         L = load()
         cfg = SessionConfig()
         L.hydro_session_default_config(ctypes.byref(cfg))
@@ -425,6 +429,12 @@ class Session:
         cfg.max_in_flight = max_in_flight
         cfg.device = device
         cfg.stream = stream.cuda_stream if stream is not None else None
+        cfg.learned = 1 if learned else 0
+        cfg.proxy_hidden = proxy_hidden
+        cfg.proxy_refresh = proxy_refresh
+        cfg.proxy_epochs = proxy_epochs
+        cfg.proxy_lr = proxy_lr
+        cfg.proxy_seed = proxy_seed
         self._h = ctypes.c_void_p()
         _check(L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(self._h)), "hydro_session_create")
         self.n_udf = 0
@@ -508,6 +518,15 @@ class Session:
                "hydro_session_profile_read")
         return {out[i].name.decode(): dict(launches=out[i].launches, total_ms=out[i].total_ms)
                 for i in range(n.value)}, tot.value
+
+    def debug_trace(self, step: int, total: int):
+        """(order uint8 [total, 8], visited uint8 [total]) of a polled step."""
+        order = np.zeros((max(total, 1), 8), np.uint8)
+        visited = np.zeros(max(total, 1), np.uint8)
+        _check(load().hydro_session_debug_trace(self._h, step, order.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                                visited.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))),
+               "hydro_session_debug_trace")
+        return order[:total], visited[:total]
 
     def tuning(self) -> list:
         out = (TileChoice * 64)()

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libhydro.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["hydro_api.cu", "k_route.cu", "k_simt.cu", "k_util.cu", "tc_conv.cu", "k_noalloc.cu", "k_cache.cu", "k_learned.cu", "tc_gemm.cu", "k_mq.cu", "session.cu"]
+SOURCES = ["hydro_api.cu", "k_route.cu", "k_simt.cu", "k_util.cu", "tc_conv.cu", "k_noalloc.cu", "k_cache.cu", "k_learned.cu", "tc_gemm.cu", "k_mq.cu", "session.cu", "tc_conv1.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr"]

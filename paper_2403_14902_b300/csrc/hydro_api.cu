@@ -643,8 +643,12 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
     const unsigned char *frames = (const unsigned char *)tuples;
     int e = prof_begin(q, pc, PC_CONV1, 2.0 * hw * 9 * p.dims[0] * p.dims[1], hw * (p.dims[0] + esz * p.dims[1]),
                        4.0 * 9 * p.dims[0] * p.dims[1]);
-    launch_conv1(prec, count, list, frames, c.channels, H, Wd, p.dW[0], p.db[0], p.dims[1], act[0], max_rows,
-                 q->sms, st);
+    if (prec == PREC_BF16 && tc_conv1_supported(c.channels, H, Wd, p.dims[1]))
+        launch_conv1_tc(count, list, frames, c.channels, H, Wd, p.dW[0], p.db[0], (__nv_bfloat16 *)act[0], max_rows,
+                        q->sms, q->d_err, st);
+    else
+        launch_conv1(prec, count, list, frames, c.channels, H, Wd, p.dW[0], p.db[0], p.dims[1], act[0], max_rows,
+                     q->sms, st);
     prof_end(q, e);
     q->launches++;
     int cur = 0;

@@ -63,6 +63,12 @@ __device__ __forceinline__ void set_cond(const Cond &c, bool v) {
     if (c.flag) *c.flag = v ? 1 : 0;
 }
 
+// Slot of tuple e (query q) in round r: its own order (learned sessions) or
+// its query's.
+__device__ __forceinline__ int slot_of(const MqDev &d, int e, int q, int r) {
+    return d.order_t ? d.order_t[(size_t)e * kMqSlots + r] : d.order[q * kMqSlots + r];
+}
+
 __device__ __forceinline__ unsigned long long *ctr(StatRow *r, int field) {
     return reinterpret_cast<unsigned long long *>(r) + field;
 }
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(256) k_mq_partition(MqDev d, int r) {
         if (live) {
             e = d.alive[cur][m];
             const int q = d.qid[e];
-            const int slot = d.order[q * kMqSlots + r];
+            const int slot = slot_of(d, e, q, r);
             g = d.udf[q * kMqSlots + slot];
         }
         const int pos = warp_append(live ? &d.rc->n[LV_MAIN][g] : nullptr, live);
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(256) k_mq_layer_f32(MqLayers L) {
         const int *rows = L.rows ? L.rows + (size_t)g * L.cap : nullptr;
         const float *in = rows ? X : l.in + (size_t)off[g] * l.ldin;
         mlp_tile_f32(L.counts[g], (local / tn) * 64, (local % tn) * 64, rows, in, rows ? L.ldx : l.ldin, l.W, l.b,
-                     L.Y + (size_t)off[g] * L.ldy, L.ldy, l.K, l.N, 1, As, Ws);
+                     L.Y + (size_t)off[g] * L.ldy, L.ldy, l.K, l.N, l.norelu ? 0 : 1, As, Ws);
     }
 }
 
@@ -283,7 +289,7 @@ __global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int in, int
             m = i - off[g];
             e = lists[(size_t)g * d.cap + m];
             q = d.qid[e];
-            slot = d.order[q * kMqSlots + r];
+            slot = slot_of(d, e, q, r);
             if (skipped) {
                 inband = true;
             } else {
@@ -354,9 +360,12 @@ __device__ __forceinline__ T lane_dot(const float *w, const X *x, int K) {
     return s;
 }
 
-// Band levels run layer-parallel: a warp per (entry, output neuron) of one
-// hidden layer, entries stacked group by group (the first `cap_lv` of the
-// level), activations in T (float: the FP32 level, double: FP64).
+// Band levels run layer-parallel: a warp per (output neuron, block of up to
+// kBandE entries) of one hidden layer, so each weight row is read once per
+// block; entries stacked group by group (the first `cap_lv` of the level),
+// activations in T (float: the FP32 level, double: FP64).
+constexpr int kBandE = 8;
+
 __device__ __forceinline__ void band_offsets(const MqDev &d, const GroupedMlps &mlps, int level, int cap_lv,
                                              int depth, int *off, int *wstart) {
     const int *cnts = d.rc->n[level];
@@ -366,7 +375,8 @@ __device__ __forceinline__ void band_offsets(const MqDev &d, const GroupedMlps &
         const int lim = max(0, min(cnts[g], cap_lv - off[g]));
         off[g + 1] = off[g] + lim;
         const MlpDev &m = mlps.m[g];
-        wstart[g + 1] = wstart[g] + (depth >= 0 && depth + 1 < m.n_layers ? lim * m.dims[depth + 1] : 0);
+        const int blocks = (lim + kBandE - 1) / kBandE;
+        wstart[g + 1] = wstart[g] + (depth >= 0 && depth + 1 < m.n_layers ? blocks * m.dims[depth + 1] : 0);
     }
 }
 
@@ -379,22 +389,61 @@ __global__ void __launch_bounds__(256) k_mq_band_layer(MqDev d, GroupedMlps mlps
     T *out_act = (depth & 1) ? act1 : act0;
     const float *X = d.hdr->X;
     const int *list = d.list[level];
+    const int lane = lane_id();
     for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < wstart[d.G]; w += (gridDim.x * blockDim.x) >> 5) {
         int g = 0;
         while (w >= wstart[g + 1]) ++g;
         const MlpDev &m = mlps.m[g];
         const int N = m.dims[depth + 1], K = m.dims[depth];
         const int local = w - wstart[g];
-        const int el = local / N, o = local % N;
-        const int j = off[g] + el;
+        const int o = local % N, e0 = (local / N) * kBandE;
+        const int ne = min(kBandE, (off[g + 1] - off[g]) - e0);
         const float *wr = m.W[depth] + (size_t)o * K;
-        T s = depth == 0 ? lane_dot<T>(wr, X + (size_t)list[(size_t)g * d.cap + el] * d.dim, K)
-                         : lane_dot<T>(wr, in_act + (size_t)j * ld, K);
+        const void *xr[kBandE];
 #pragma unroll
-        for (int dd = 16; dd > 0; dd >>= 1) s += __shfl_xor_sync(0xffffffffu, s, dd);
-        if (lane_id() == 0) {
-            s += (T)m.b[depth][o];
-            out_act[(size_t)j * ld + o] = s > (T)0 ? s : (T)0;
+        for (int e = 0; e < kBandE; ++e) {
+            const int el = e0 + (e < ne ? e : 0);
+            xr[e] = depth == 0 ? (const void *)(X + (size_t)list[(size_t)g * d.cap + el] * d.dim)
+                               : (const void *)(in_act + (size_t)(off[g] + el) * ld);
+        }
+        T acc[kBandE];
+#pragma unroll
+        for (int e = 0; e < kBandE; ++e) acc[e] = 0;
+        if ((K & 127) == 0) {
+#pragma unroll 2
+            for (int k = 4 * lane; k < K; k += 128) {
+                float wv[4];
+                load4(wr + k, wv);
+#pragma unroll
+                for (int e = 0; e < kBandE; ++e) {
+                    if (e >= ne) break;
+                    T xv[4];
+                    if (depth == 0) load4(static_cast<const float *>(xr[e]) + k, xv);
+                    else load4(static_cast<const T *>(xr[e]) + k, xv);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[e] += (T)wv[i] * xv[i];
+                }
+            }
+        } else {
+            for (int k = lane; k < K; k += 32) {
+                const T wk = (T)wr[k];
+#pragma unroll
+                for (int e = 0; e < kBandE; ++e) {
+                    if (e >= ne) break;
+                    const T xk = depth == 0 ? (T) static_cast<const float *>(xr[e])[k] : static_cast<const T *>(xr[e])[k];
+                    acc[e] += wk * xk;
+                }
+            }
+        }
+        const T bo = (T)m.b[depth][o];
+#pragma unroll
+        for (int e = 0; e < kBandE; ++e) {
+            if (e >= ne) break;
+            T s = acc[e];
+#pragma unroll
+            for (int dd = 16; dd > 0; dd >>= 1) s += __shfl_xor_sync(0xffffffffu, s, dd);
+            s += bo;
+            if (lane == 0) out_act[(size_t)(off[g] + e0 + e) * ld + o] = s > (T)0 ? s : (T)0;
         }
     }
 }
@@ -424,7 +473,7 @@ __global__ void __launch_bounds__(256) k_mq_band_final(MqDev d, GroupedMlps mlps
         if (lane_id() != 0) continue;
         s += (T)m.b[L - 1][0];
         const int q = d.qid[e];
-        const int slot = d.order[q * kMqSlots + r];
+        const int slot = slot_of(d, e, q, r);
         const double t = d.thr[q * kMqSlots + slot];
         StatRow *row = d.rows + q * kMqSlots + slot;
         bool pass;
@@ -497,7 +546,7 @@ __global__ void __launch_bounds__(256) k_mq_band64(MqDev d, int r, GroupedMlps m
         }
         if (threadIdx.x == 0) {
             const int q = d.qid[e];
-            const int slot = d.order[q * kMqSlots + r];
+            const int slot = slot_of(d, e, q, r);
             const bool pass = cur[0] > d.thr[q * kMqSlots + slot];
             d.ok[e] = (unsigned char)pass;
             StatRow *row = d.rows + q * kMqSlots + slot;
@@ -579,6 +628,31 @@ __global__ void k_mq_commit(MqDev d, MqHist h, StatRow *res_rows, unsigned char 
     h.ring[((size_t)q * h.R + (size_t)(b % h.R)) * kMqSlots + slot] = row;
     if (b < h.warmup) h.warm[((size_t)q * h.warmup + b) * kMqSlots + slot] = row;
     if (slot == 0) h.bdone[q] = b + 1;
+}
+
+__global__ void __launch_bounds__(256) k_mq_tuple_order(MqDev d, const float *logits, int ldz, const int *ready) {
+    const int n = min(d.off[d.Q], d.cap);
+    const bool use_proxy = logits && ready && *ready;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int q = d.qid[e];
+        const int P = d.np[q];
+        unsigned char *o = d.order_t + (size_t)e * kMqSlots;
+        if (d.evall[q] || !use_proxy) {
+            for (int k = 0; k < kMqSlots; ++k) o[k] = d.evall[q] ? (unsigned char)k : d.order[q * kMqSlots + k];
+            continue;
+        }
+        float key[kMqSlots];
+        for (int i = 0; i < P; ++i) {
+            const float z = fminf(fmaxf(logits[(size_t)e * ldz + i], -30.f), 30.f);
+            key[i] = (float)d.cost[q * kMqSlots + i] * (1.f + expf(z));
+        }
+        for (int i = 0; i < P; ++i) {
+            int pos = 0;
+            for (int j = 0; j < P; ++j) pos += (key[j] < key[i] || (key[j] == key[i] && j < i)) ? 1 : 0;
+            o[pos] = (unsigned char)i;
+        }
+        for (int k = P; k < kMqSlots; ++k) o[k] = (unsigned char)k;
+    }
 }
 
 // FP64 scores of one MLP on n rows (calibration).
@@ -678,6 +752,10 @@ void mq_launch_commit(const MqDev &d, const MqHist &h, StatRow *res_rows, unsign
     const int n = d.Q * kMqSlots > kMqGates ? d.Q * kMqSlots : kMqGates;
     k_mq_commit<<<(n + 255) / 256, 256, 0, st>>>(d, h, res_rows, res_order, res_evall, res_bidx, res_npass, res_total,
                                                  res_gates);
+}
+
+void mq_launch_tuple_order(const MqDev &d, const float *logits, int ldz, const int *ready, cudaStream_t st, int sms) {
+    k_mq_tuple_order<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, logits, ldz, ready);
 }
 
 cudaError_t mq_band_smem_setup(int max_width) {

@@ -76,6 +76,7 @@ struct MqDev {
     int cap64, ld64;               // FP64 band entries handled layer-parallel per round; row stride
     unsigned int *err;
     int *gates;                    // [kMqGates] condition values of the step (0 unless set)
+    unsigned char *order_t;        // learned sessions: [cap][8] slot order of each tuple (else nullptr)
 };
 
 // Per-query statistics history (device).
@@ -96,6 +97,7 @@ struct MqLayer {
     const float *in;               // stacked input (depth >= 1), row stride ldin
     int ldin;
     int K, N;
+    int norelu;                    // 1: no ReLU (logits)
 };
 struct MqLayers {
     MqLayer l[kMqPool];
@@ -139,6 +141,10 @@ void mq_launch_commit(const MqDev &d, const MqHist &h, StatRow *res_rows, unsign
                       unsigned char *res_evall, long long *res_bidx, long long *res_npass, int *res_total,
                       int *res_gates, cudaStream_t st);
 cudaError_t mq_band_smem_setup(int max_width);
+// Learned sessions: each tuple's slot order.  Warmup batch: declared order;
+// proxy trained (*ready): slots by c_i (1 + e^{z_i}) of the tuple's logits
+// z (row stride ldz), ties to the lower slot; else the query's rank order.
+void mq_launch_tuple_order(const MqDev &d, const float *logits, int ldz, const int *ready, cudaStream_t st, int sms);
 // FP64 scores of one UDF on n rows of X (block per row), for calibration.
 void mq_launch_scores_f64(const MlpDev &mlp, int max_width, const float *X, int ldx, int n, double *out,
                           cudaStream_t st, int sms);

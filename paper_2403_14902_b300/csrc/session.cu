@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <random>
 #include <cstdarg>
 #include <cstddef>
 #include <cmath>
@@ -138,6 +139,19 @@ struct hydro_session {
     unsigned long long handles[kMqGates] = {};   // created on first use (an unused handle fails instantiation)
     cudaGraph_t cap_graph = nullptr;
     hydro_status handle_err = HYDRO_OK;
+    // learned routing (one query): proxy D -> H -> P, its training state and ring of outcomes
+    int ph = 0;
+    float *pW1 = nullptr, *pb1 = nullptr, *pW2 = nullptr, *pb2 = nullptr;
+    float *pg = nullptr, *pm = nullptr, *pv = nullptr;
+    float *pH = nullptr, *pZ = nullptr, *pdZ = nullptr, *pdH = nullptr, *pinv = nullptr, *ppart = nullptr;
+    int *p_ready = nullptr, *p_count = nullptr, *p_rows = nullptr;
+    int *h_one = nullptr;                 // pinned 1
+    float *ringX = nullptr;
+    unsigned char *ringL = nullptr, *ringM = nullptr;
+    std::vector<int> ring_n;
+    long long learned_batches = 0;
+    int adam_t = 0;
+    long long last_step_total = -1;       // stacked tuples of the most recent step (debug trace)
 };
 
 namespace {
@@ -368,6 +382,31 @@ hydro_status enqueue_step(hydro_session *s, Slot &slot) {
     mq_launch_router(d, s->h, s->st);
     prof_end(s, pe);
     s->step_launches += 2;
+    if (s->cfg.learned) {
+        // proxy logits of every tuple (identity rows of the first alive list), then each tuple's order
+        const int P = s->queries[0].P;
+        MqLayers L1{};
+        L1.n = 1;
+        L1.counts = &d.rc->alive[0];
+        L1.rows = d.alive[0];
+        L1.cap = d.cap;
+        L1.hdr = s->d_hdr;
+        L1.ldx = d.dim;
+        L1.Y = s->pH;
+        L1.ldy = s->ph;
+        L1.l[0] = MqLayer{s->pW1, s->pb1, 0.f, nullptr, 0, d.dim, s->ph, 0};
+        MqLayers L2 = L1;
+        L2.rows = nullptr;
+        L2.Y = s->pZ;
+        L2.ldy = P;
+        L2.l[0] = MqLayer{s->pW2, s->pb2, 0.f, s->pH, s->ph, s->ph, P, 1};
+        pe = prof_begin(s, SP_CTRL);
+        mq_launch_layers_f32(L1, s->st, s->sms);
+        mq_launch_layers_f32(L2, s->st, s->sms);
+        mq_launch_tuple_order(d, s->pZ, P, s->p_ready, s->st, s->sms);
+        prof_end(s, pe);
+        s->step_launches += 3;
+    }
     auto classify = [&](int r, int in, int out, Cond next, int next_min, const TcHeads *heads = nullptr) {
         const int p = prof_begin(s, SP_CTRL);
         mq_launch_classify(d, r, in, out, s->st, s->sms, next, next_min, heads, heads ? s->partials : nullptr,
@@ -619,6 +658,50 @@ hydro_status finalize(hydro_session *s) {
         if (rs != HYDRO_OK) return fail(rs, "tensor-core GEMM init: %s", tc_gemm_last_error());
     }
 
+    if (c.learned) {
+        const int P = s->queries[0].P, D = c.dim;
+        const int H = s->ph = c.proxy_hidden > 0 ? c.proxy_hidden : 64;
+        const size_t nparam = (size_t)H * D + H + (size_t)P * H + P;
+        std::vector<float> init(nparam, 0.f);
+        std::mt19937 gen((unsigned)c.proxy_seed);
+        std::uniform_real_distribution<float> u1(-std::sqrt(6.f / D), std::sqrt(6.f / D));
+        std::uniform_real_distribution<float> u2(-1.f / std::sqrt((float)H), 1.f / std::sqrt((float)H));
+        for (size_t k = 0; k < (size_t)H * D; ++k) init[k] = u1(gen);
+        for (size_t k = 0; k < (size_t)P * H; ++k) init[(size_t)H * D + H + k] = u2(gen);
+        float *params = nullptr;
+        TRY(upload(s, &params, init.data(), nparam));
+        s->pW1 = params;
+        s->pb1 = s->pW1 + (size_t)H * D;
+        s->pW2 = s->pb1 + H;
+        s->pb2 = s->pW2 + (size_t)P * H;
+        TRY(dalloc(s, &s->pg, sizeof(float) * nparam));
+        TRY(dalloc(s, &s->pm, sizeof(float) * nparam));
+        TRY(dalloc(s, &s->pv, sizeof(float) * nparam));
+        CU(cudaMemset(s->pm, 0, sizeof(float) * nparam));
+        CU(cudaMemset(s->pv, 0, sizeof(float) * nparam));
+        TRY(dalloc(s, &s->pH, sizeof(float) * (size_t)cap * H));
+        TRY(dalloc(s, &s->pZ, sizeof(float) * (size_t)cap * kMqSlots));
+        TRY(dalloc(s, &s->pdZ, sizeof(float) * (size_t)cap * kMqSlots));
+        TRY(dalloc(s, &s->pdH, sizeof(float) * (size_t)cap * H));
+        TRY(dalloc(s, &s->ppart, sizeof(float) * proxy_grad_part_floats(cap, D, H, P)));
+        TRY(dalloc(s, &s->pinv, sizeof(float)));
+        TRY(dalloc(s, &s->p_ready, sizeof(int)));
+        CU(cudaMemset(s->p_ready, 0, sizeof(int)));
+        TRY(dalloc(s, &s->p_count, sizeof(int)));
+        TRY(dalloc(s, &s->p_rows, sizeof(int) * (size_t)cap));
+        void *hp = nullptr;
+        CU(cudaMallocHost(&hp, sizeof(int)));
+        s->host_allocs.push_back(hp);
+        s->h_one = (int *)hp;
+        *s->h_one = 1;
+        const int R = std::max(1, c.proxy_refresh);
+        TRY(dalloc(s, &s->ringX, sizeof(float) * (size_t)R * cap * D));
+        TRY(dalloc(s, &s->ringL, (size_t)R * cap));
+        TRY(dalloc(s, &s->ringM, (size_t)R * cap));
+        s->ring_n.assign(R, 0);
+        TRY(dalloc(s, &d.order_t, (size_t)cap * kMqSlots));
+    }
+
     // statistics history
     MqHist &h = s->h;
     h.R = c.stats_window + 2;
@@ -668,6 +751,74 @@ hydro_status upload_margins(hydro_session *s) {
     return HYDRO_OK;
 }
 
+// Learned sessions, after a step: keep its tuples and outcomes in the
+// training ring; every proxy_refresh batches retrain the proxy on the ring
+// (masked BCE on the slots each tuple was evaluated on, Adam) and mark it
+// ready.  Stream-ordered after the step, outside its graph.
+hydro_status learned_after_step(hydro_session *s, const Slot &slot) {
+    const int n = slot.counts[0];
+    if (n <= 0) return HYDRO_OK;
+    const hydro_session_config &c = s->cfg;
+    const int D = c.dim, H = s->ph, P = s->queries[0].P, cap = s->d.cap;
+    const int R = (int)s->ring_n.size();
+    const int rs = (int)(s->learned_batches % R);
+    CU(cudaMemcpyAsync(s->ringX + (size_t)rs * cap * D, slot.h_hdr->X, sizeof(float) * (size_t)n * D,
+                       cudaMemcpyDeviceToDevice, s->st));
+    CU(cudaMemcpyAsync(s->ringL + (size_t)rs * cap, s->d.label, n, cudaMemcpyDeviceToDevice, s->st));
+    CU(cudaMemcpyAsync(s->ringM + (size_t)rs * cap, s->d.visited, n, cudaMemcpyDeviceToDevice, s->st));
+    s->ring_n[rs] = n;
+    s->learned_batches++;
+    if (s->learned_batches % R) return HYDRO_OK;
+    const size_t nW1 = (size_t)H * D;
+    for (int e = 0; e < std::max(1, c.proxy_epochs); ++e)
+        for (int k = 0; k < R; ++k) {
+            const int M = s->ring_n[k];
+            if (M <= 0) continue;
+            const float *Xs = s->ringX + (size_t)k * cap * D;
+            launch_identity_list(s->p_rows, s->p_count, 0, M, s->st);
+            launch_mlp_layer_f32(s->p_count, nullptr, Xs, D, s->pW1, s->pb1, s->pH, D, H, 1, M, s->sms, s->st);
+            launch_mlp_layer_f32(s->p_count, nullptr, s->pH, H, s->pW2, s->pb2, s->pZ, H, P, 0, M, s->sms, s->st);
+            ProxyTrain pt{};
+            pt.M = M;
+            pt.P = P;
+            pt.H = H;
+            pt.D = D;
+            pt.sms = s->sms;
+            pt.t = ++s->adam_t;
+            pt.lr = c.proxy_lr;
+            pt.X = Xs;
+            pt.Hact = s->pH;
+            pt.Z = s->pZ;
+            pt.dZ = s->pdZ;
+            pt.dH = s->pdH;
+            pt.inv_pairs = s->pinv;
+            pt.part = s->ppart;
+            pt.label = s->ringL + (size_t)k * cap;
+            pt.mask = s->ringM + (size_t)k * cap;
+            pt.W1 = s->pW1;
+            pt.b1 = s->pb1;
+            pt.W2 = s->pW2;
+            pt.b2 = s->pb2;
+            pt.gW1 = s->pg;
+            pt.gb1 = s->pg + nW1;
+            pt.gW2 = pt.gb1 + H;
+            pt.gb2 = pt.gW2 + (size_t)P * H;
+            pt.mW1 = s->pm;
+            pt.mb1 = s->pm + nW1;
+            pt.mW2 = pt.mb1 + H;
+            pt.mb2 = pt.mW2 + (size_t)P * H;
+            pt.vW1 = s->pv;
+            pt.vb1 = s->pv + nW1;
+            pt.vW2 = pt.vb1 + H;
+            pt.vb2 = pt.vW2 + (size_t)P * H;
+            launch_proxy_train_step(pt, s->st);
+            s->launches += 16;
+        }
+    CU(cudaMemcpyAsync(s->p_ready, s->h_one, sizeof(int), cudaMemcpyHostToDevice, s->st));
+    CU(cudaGetLastError());
+    return HYDRO_OK;
+}
+
 hydro_status wait_ev(cudaEvent_t ev, long long wait_ms, bool *done) {
     auto t0 = std::chrono::steady_clock::now();
     for (;;) {
@@ -714,6 +865,11 @@ void hydro_session_default_config(hydro_session_config *cfg) {
     cfg->use_graphs = 1;
     cfg->autotune = 1;
     cfg->max_in_flight = 2;
+    cfg->proxy_hidden = 64;
+    cfg->proxy_refresh = 16;
+    cfg->proxy_epochs = 1;
+    cfg->proxy_lr = 1e-3f;
+    cfg->proxy_seed = 1;
 }
 
 hydro_status hydro_session_create(const hydro_session_config *cfg, hydro_session **out) {
@@ -727,6 +883,9 @@ hydro_status hydro_session_create(const hydro_session_config *cfg, hydro_session
         return fail(HYDRO_EINVAL, "precision must be FP32 or BF16");
     if (cfg->warmup_batches < 0 || cfg->stats_window < 1) return fail(HYDRO_EINVAL, "bad warmup/window");
     if (cfg->max_in_flight < 1 || cfg->max_in_flight > 8) return fail(HYDRO_EINVAL, "max_in_flight outside 1..8");
+    if (cfg->learned && (cfg->proxy_hidden < 0 || cfg->proxy_hidden > 1024 || cfg->proxy_refresh < 1 ||
+                         cfg->proxy_refresh > 256 || cfg->proxy_epochs < 0 || !(cfg->proxy_lr > 0.f)))
+        return fail(HYDRO_EINVAL, "bad proxy settings");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
         return fail(HYDRO_EINVAL, "no CUDA device %d", cfg->device);
@@ -769,6 +928,7 @@ hydro_status hydro_session_add_query(hydro_session *s, int32_t n_preds, const in
     TRY(check(s));
     if (s->finalized) return fail(HYDRO_ESTATE, "queries must be added before the first submit");
     if ((int)s->queries.size() >= HYDRO_MAX_QUERIES) return fail(HYDRO_EINVAL, "too many queries");
+    if (s->cfg.learned && !s->queries.empty()) return fail(HYDRO_EINVAL, "learned sessions have one query");
     if (n_preds < 1 || n_preds > HYDRO_MAX_PREDICATES || !udfs || !thresholds)
         return fail(HYDRO_EINVAL, "a query has 1..%d predicates", HYDRO_MAX_PREDICATES);
     Query q;
@@ -976,6 +1136,8 @@ hydro_status hydro_session_submit(hydro_session *s, const void *d_tuples, const 
         TRY(rs);
     }
     CU(cudaEventRecord(slot->ev1, s->st));
+    if (s->cfg.learned) TRY(learned_after_step(s, *slot));
+    s->last_step_total = total;
     slot->busy = true;
     slot->step = s->next_step;
     *out_step = s->next_step++;
@@ -1055,6 +1217,26 @@ hydro_status hydro_session_poll(hydro_session *s, int64_t step, uint32_t *pass_b
         float ms = 0;
         CU(cudaEventElapsedTime(&ms, slot->ev0, slot->ev1));
         *device_ms = ms;
+    }
+    return HYDRO_OK;
+}
+
+hydro_status hydro_session_debug_trace(hydro_session *s, int64_t step, uint8_t *order, uint8_t *visited) {
+    set_last_error("");
+    TRY(check(s));
+    if (!order || !visited) return fail(HYDRO_EINVAL, "NULL output");
+    if (step != s->next_step - 1 || s->last_step_total < 0) return fail(HYDRO_ESTATE, "only the last step has a trace");
+    for (Slot &sl : s->slots)
+        if (sl.busy) return fail(HYDRO_ESTATE, "poll the step first");
+    const size_t n = (size_t)s->last_step_total;
+    CU(cudaMemcpy(visited, s->d.visited, n, cudaMemcpyDeviceToHost));
+    if (s->d.order_t) {
+        CU(cudaMemcpy(order, s->d.order_t, n * kMqSlots, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<unsigned char> qid(n), ord((size_t)s->d.Q * kMqSlots);
+        CU(cudaMemcpy(qid.data(), s->d.qid, n, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(ord.data(), s->d.order, ord.size(), cudaMemcpyDeviceToHost));
+        for (size_t e = 0; e < n; ++e) memcpy(order + e * kMqSlots, ord.data() + (size_t)qid[e] * kMqSlots, kMqSlots);
     }
     return HYDRO_OK;
 }

@@ -18,6 +18,12 @@ struct TcConvPlan {
 
 // Whether a layer of this shape runs on the tensor-core kernel.
 bool tc_conv_supported(int cin, int cout, int H, int W);
+// First conv layer on the tensor cores (BF16 output): uint8 frames with C0 <= 3
+// channels, Cout == 32, H*W a multiple of 128.
+bool tc_conv1_supported(int C0, int H, int W, int Cout);
+void launch_conv1_tc(const int *count, const int *list, const unsigned char *frames, int C0, int H, int Wd,
+                     const float *W, const float *bias, __nv_bfloat16 *out, int max_frames, int sms,
+                     unsigned int *err, cudaStream_t st);
 // Repack fp32 weights [cout][cin][3][3] into the kernel's bf16 layout.
 void tc_conv_pack_weights(const float *w, int cin, int cout, std::vector<__nv_bfloat16> &out);
 // FP32-accurate split form: [plane(hi, lo)][chunk of 32][kx][ky][cout][32] fp32.

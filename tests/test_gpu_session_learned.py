@@ -1,0 +1,94 @@
+"""GPU checks of learned per-tuple routing in sessions (one query, six MLP
+predicates of cost ratio 1:2:4:8:16:32 on the drifting stream).  The proxy's
+probabilities are not pinned (parity unpinned); what is pinned: the pass set
+is exact, every tuple is evaluated on exactly the prefix of its own order up
+to its first failing predicate, the counts follow from those sets, and until
+the first training the orders are the query's rank orders (lag 0)."""
+import numpy as np
+import pytest
+
+import datagen as D
+import oracle as O
+from gpu_helpers import model_costs, oracle_thresholds
+
+pytestmark = pytest.mark.gpu
+
+B = 1024
+NB = 14
+REFRESH = 4
+
+
+@pytest.fixture(scope="module")
+def drift6():
+    import torch
+    w = D.workload("drift6", n=NB * B, extra=dict(D.WORKLOADS["drift6"].extra, segment_len=2 * B))
+    th, _ = oracle_thresholds(w)
+    X = D.stream_tuples(w)
+    S = O.udf_scores("vec", X, D.predicate_weights(w))
+    return dict(w=w, th=th, X=X, pm=O.pass_matrix(S, th), Xd=torch.from_numpy(X).cuda(),
+                calib=torch.from_numpy(D.calib_tuples(w)).cuda())
+
+
+def check_step(pm_b, bits, r, order, visited, P):
+    assert np.array_equal(bits, O.result_bits(pm_b))
+    assert all(sorted(o[:P].tolist()) == list(range(P)) for o in order)
+    want = np.zeros(len(bits), np.uint8)
+    for t in range(len(bits)):
+        if r["warmup"]:
+            want[t] = (1 << P) - 1
+            continue
+        for i in order[t][:P]:
+            want[t] |= 1 << int(i)
+            if not pm_b[t, i]:
+                break
+    assert np.array_equal(visited, want)
+    for i in range(P):
+        ev = ((visited >> i) & 1).astype(bool)
+        assert r["evaluated"][i] == int(ev.sum())
+        assert r["passed"][i] == int((ev & pm_b[:, i]).sum())
+
+
+@pytest.mark.parametrize("precision,graphs", [("fp32", True), ("bf16", True), ("bf16", False)])
+def test_learned_session_exact_and_prefix_consistent(drift6, precision, graphs):
+    import paper_2403_14902_b300 as H
+    w = drift6["w"]
+    P = len(w.udfs)
+    s = H.Session(dim=w.dim, max_step_tuples=B, precision=precision, graphs=graphs, learned=True,
+                  proxy_refresh=REFRESH, proxy_epochs=3, proxy_lr=3e-3)
+    for layers in D.predicate_weights(w):
+        s.add_udf(layers)
+    s.add_query(list(range(P)), drift6["th"])
+    s.calibrate(drift6["calib"])
+    sim = O.simulate(drift6["pm"], B, policy="rank", costs=model_costs(w), lag=0)
+    varied = 0
+    for b in range(NB):
+        sid = s.submit(drift6["Xd"][b * B:(b + 1) * B], [B])
+        words, per, _ = s.poll(sid)
+        order, visited = s.debug_trace(sid, B)
+        r = per[0]
+        check_step(drift6["pm"][b * B:(b + 1) * B], H.bits_from_words(words, B), r, order, visited, P)
+        if b < REFRESH:
+            # before the first training: the query's rank order for every tuple
+            assert r["order"] == sim[b]["order"]
+            assert (order[:, :P] == np.asarray(r["order"], np.uint8)[None, :]).all()
+            assert r["evaluated"] == sim[b]["counts"].tolist()
+        else:
+            varied += len({tuple(o[:P]) for o in order}) > 1
+    assert varied > 0, "the trained proxy never produced tuple-specific orders"
+    s.close()
+
+
+def test_learned_session_config_checks():
+    import paper_2403_14902_b300 as H
+    w = D.workload("drift6")
+    with pytest.raises(H.HydroError) as e:
+        H.Session(dim=w.dim, max_step_tuples=B, learned=True, proxy_refresh=0)
+    assert e.value.status == H.EINVAL
+    s = H.Session(dim=w.dim, max_step_tuples=B, learned=True)
+    for layers in D.predicate_weights(w)[:2]:
+        s.add_udf(layers)
+    s.add_query([0, 1], [0.0, 0.0])
+    with pytest.raises(H.HydroError) as e:
+        s.add_query([0], [0.0])          # one query per learned session
+    assert e.value.status == H.EINVAL
+    s.close()
