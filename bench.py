@@ -470,10 +470,10 @@ def ours_drift6(args):
         results[name] = entry
     # the same query as a one-query session: BF16 tensor cores, CUDA graphs,
     # per-tuple orders from the proxy (learned) or per-batch rank orders
-    def session(learned, precision):
-        s = H.Session(dim=w.dim, max_step_tuples=w.batch, precision=precision, graphs=True, autotune=True,
+    def session(learned, precision, K):
+        s = H.Session(dim=w.dim, max_step_tuples=K * w.batch, precision=precision, graphs=True, autotune=True,
                       max_in_flight=2, stream=stream, learned=learned, proxy_refresh=w.extra["refresh"],
-                      proxy_hidden=w.extra["proxy_hidden"])
+                      proxy_hidden=w.extra["proxy_hidden"], batches_per_step=K, lag=K - 1)
         for i in range(len(w.udfs)):
             s.add_udf(full[i])
         s.add_query(list(range(len(w.udfs))), th)
@@ -481,24 +481,32 @@ def ours_drift6(args):
         return s
 
     def run_session(s, stats=None):
+        # each step: the next K batches of 4,096 (K = s.K)
         pending, npass = [], 0
 
-        def drain(sid):
+        def drain(item):
             nonlocal npass
-            r = s.poll(sid, total=w.batch)[1][0]
-            npass += r["n_pass"]
-            if stats is not None:
-                stats.append(r)
-        for b0 in range(0, w.n, w.batch):
-            pending.append(s.submit(X[b0:b0 + w.batch], [w.batch]))
+            sid, n = item
+            for r in s.poll(sid, total=n)[1]:
+                if r["batch"] >= 0:
+                    npass += r["n_pass"]
+                    if stats is not None:
+                        stats.append(r)
+        step = s.K * w.batch
+        for b0 in range(0, w.n, step):
+            n = min(step, w.n - b0)
+            counts = [max(0, min(w.batch, n - k * w.batch)) for k in range(s.K)]
+            pending.append((s.submit(X[b0:b0 + n], counts), n))
             if len(pending) >= 2:
                 drain(pending.pop(0))
-        for sid in pending:
-            drain(sid)
+        for item in pending:
+            drain(item)
         return npass
-    for name, learned, precision in [("learned_session_bf16", True, "bf16"), ("rank_session_bf16", False, "bf16"),
-                                     ("learned_session_fp32", True, "fp32")]:
-        s = session(learned, precision)
+    for name, learned, precision, K in [("learned_session_bf16", True, "bf16", 4),
+                                        ("learned_session_bf16_k1", True, "bf16", 1),
+                                        ("rank_session_bf16", False, "bf16", 4),
+                                        ("learned_session_fp32", True, "fp32", 4)]:
+        s = session(learned, precision, K)
         f = lambda: run_session(s)  # noqa: E731
         for _ in range(args.warmup):
             f()
@@ -519,20 +527,24 @@ def ours_drift6(args):
             entry["prof"], _ = s.profile_read()
             s.profile(False)
             Xp = Xh.pin_memory()
-            buf = [torch.empty((w.batch, w.dim), dtype=torch.float32, device="cuda") for _ in range(2)]
+            buf = [torch.empty((4 * w.batch, w.dim), dtype=torch.float32, device="cuda") for _ in range(2)]
 
             def host_run():
                 pending, k = [], 0
+                step = s.K * w.batch
                 with torch.cuda.stream(stream):
-                    for b0 in range(0, w.n, w.batch):
+                    for b0 in range(0, w.n, step):
+                        n = min(step, w.n - b0)
+                        counts = [max(0, min(w.batch, n - j * w.batch)) for j in range(s.K)]
                         bb = buf[k % 2]
                         k += 1
-                        bb.copy_(Xp[b0:b0 + w.batch], non_blocking=True)
-                        pending.append(s.submit(bb, [w.batch]))
+                        bb[:n].copy_(Xp[b0:b0 + n], non_blocking=True)
+                        pending.append((s.submit(bb, counts), n))
                         if len(pending) >= 2:
-                            s.poll(pending.pop(0), total=w.batch)
-                    for sid in pending:
-                        s.poll(sid, total=w.batch)
+                            sid, nn = pending.pop(0)
+                            s.poll(sid, total=nn)
+                    for sid, nn in pending:
+                        s.poll(sid, total=nn)
             host_run()
             esecs, _ = timed(host_run, 2, stream, local)
             entry["e2e"] = aggregate(w.n, 2, max_over_ranks(esecs, device=torch.device("cuda", local)), ws)
@@ -565,8 +577,9 @@ def ours_drift6(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"drift6: {w.n} x 512 fp32 tuples, 8 Dirichlet(0.5) drift segments, 6 MLP "
                                "predicates 512-h-1 (cost 1:2:4:8:16:32), learned 512-64-6 proxy picks per-tuple "
-                               f"orders (trained every 16 batches), batches of {w.batch}, one-query session: BF16 "
-                               "tensor cores + split-BF16/FP32/FP64 recheck, CUDA graphs",
+                               f"orders (trained every 16 batches), batches of {w.batch}, one-query session with 4 "
+                               "batches per step (route lag 3): BF16 tensor cores + split-BF16/FP32/FP64 recheck, "
+                               "CUDA graphs",
                    "global_batch": w.n, "routing_batch": w.batch, "parallelism": f"replicas{ws}",
                    "l2": "inputs 2 GiB > 126 MB L2, no flush"},
         "roofline": roof,
@@ -689,18 +702,28 @@ def ours(args):
 
 # ---------------------------------------------------------------- many queries
 
+def mq_plan(w, streams, K):
+    """Step plan: every query's next K chunks per step (entry q*K + k)."""
+    plan, done = [], [0] * len(streams)
+    while any(done[q] < streams[q].shape[0] for q in range(len(streams))):
+        parts, counts = [], []
+        for q, X in enumerate(streams):
+            for _ in range(K):
+                m = max(0, min(w.batch, X.shape[0] - done[q]))
+                parts.append(X[done[q]:done[q] + m])
+                counts.append(m)
+                done[q] += m
+        plan.append((np.ascontiguousarray(np.concatenate(parts)), counts))
+    return plan
+
+
 def mq_setup(w):
     """Queries, thresholds, host streams and the step plan of the pool
     workload (every query's next chunk per step, stacked)."""
     qs = D.mq_queries(w)
     th = thresholds(w.name)
     streams = [D.mq_tuples(w, q, None, qs) for q in range(len(qs))]
-    plan, done = [], [0] * len(qs)
-    while any(done[q] < streams[q].shape[0] for q in range(len(qs))):
-        rows, counts = D.mq_stacked_step(streams, done, w.batch)
-        plan.append((rows, counts))
-        done = [d + c for d, c in zip(done, counts)]
-    return qs, th, streams, plan
+    return qs, th, streams, mq_plan(w, streams, 1)
 
 
 def mq_hidden_flops(w, u):
@@ -730,9 +753,11 @@ def ours_mq64(args):
     calib = torch.from_numpy(np.concatenate([D.mq_calib_tuples(w, q, qs)[:16] for q in range(Q)])).cuda()
     cap = Q * w.batch
 
-    def make(precision, graphs=True):
-        s = H.Session(dim=w.dim, max_step_tuples=cap, precision=precision, graphs=graphs, autotune=True,
-                      max_in_flight=2, stream=stream)
+    plans = {1: dev_plan}
+
+    def make(precision, graphs=True, K=1):
+        s = H.Session(dim=w.dim, max_step_tuples=cap * K, precision=precision, graphs=graphs, autotune=True,
+                      max_in_flight=2, stream=stream, batches_per_step=K, lag=K - 1)
         for layers in pool:
             s.add_udf(layers)
         for q in range(Q):
@@ -742,6 +767,8 @@ def ours_mq64(args):
 
     def run_all(s, events=None, stats=None):
         pending, npass = [], 0
+        if s.K not in plans:
+            plans[s.K] = [(torch.from_numpy(rows).cuda(), counts) for rows, counts in mq_plan(w, streams, s.K)]
 
         def drain(sid):
             nonlocal npass
@@ -749,7 +776,7 @@ def ours_mq64(args):
             npass += sum(r["n_pass"] for r in per)
             if stats is not None:
                 stats.append(per)
-        for X, counts in dev_plan:
+        for X, counts in plans[s.K]:
             pending.append((s.submit(X, counts), int(sum(counts))))
             if events is not None:
                 ev = torch.cuda.Event(enable_timing=True)
@@ -762,11 +789,15 @@ def ours_mq64(args):
         return npass
 
     results = {}
-    variants = [("bf16_graphs", "bf16", True), ("fp32_graphs", "fp32", True), ("bf16_no_graphs", "bf16", False)]
+    variants = [("bf16_graphs", "bf16", True, 1), ("bf16_graphs_k2", "bf16", True, 2), ("fp32_graphs", "fp32", True, 1),
+                ("bf16_no_graphs", "bf16", False, 1)]
     if args.headline_only:
-        variants = variants[:1]
-    for name, precision, graphs in variants:
-        s = make(precision, graphs)
+        # profilers cannot see kernels inside graphs with conditional nodes: launch kernel by kernel
+        variants = [("bf16_graphs", "bf16", not args.no_graphs, 1)]
+    for name, precision, graphs, K in variants:
+        s = make(precision, graphs, K)
+        if K > 1:
+            run_all(s)   # builds this K's device plan outside the timed region
         for _ in range(args.warmup):
             run_all(s)
         clocks = ClockSampler(local)
@@ -1070,6 +1101,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--headline-only", action="store_true",
                     help="mq64: time the headline variant only (for profiling runs)")
+    ap.add_argument("--no-graphs", action="store_true", help="with --headline-only: launch without CUDA graphs")
     ap.add_argument("--workload", choices=["cnn4", "drift5", "drift6", "mq64", "gemm_bf16"], default=WORKLOAD)
     args = ap.parse_args(argv)
     if args.impl == "reference":

@@ -392,6 +392,12 @@ typedef struct hydro_session_config {
     int32_t proxy_epochs;     /* learned: passes over the stored steps per training (default 1) */
     float proxy_lr;           /* learned: Adam learning rate (default 1e-3) */
     int32_t proxy_seed;       /* learned: seed of the proxy's initial weights */
+    int32_t batches_per_step; /* K, 1..8: routing batches of each query one step may hold; with K > 1
+                                 counts (submit) and the per-query results (poll) have n_queries x K
+                                 entries, entry q K + k being query q's k-th batch of the step */
+    int32_t route_lag;        /* a query's batch b is routed on its batches <= b - 1 - route_lag
+                                 (Sec. 4.1 with a lag, as hydro_query_config.route_lag); must be
+                                 >= K - 1 so that every batch of a step sees only earlier steps */
 } hydro_session_config;
 
 /* Per query result of one step (hydro_session_poll). */
@@ -418,7 +424,8 @@ typedef struct hydro_tile_choice {
 
 /* Defaults: FP32, warmup 1, window 8, graphs on, autotune on, 2 in flight,
  * device 0, NULL stream, not learned (proxy 64 hidden, refresh 16, 1 epoch,
- * lr 1e-3, seed 1); dim and max_step_tuples must be set. */
+ * lr 1e-3, seed 1), one batch per step, route lag 0; dim and
+ * max_step_tuples must be set. */
 HYDRO_API void hydro_session_default_config(hydro_session_config *cfg);
 
 HYDRO_API hydro_status hydro_session_create(const hydro_session_config *cfg, hydro_session **out);
@@ -457,8 +464,10 @@ HYDRO_API hydro_status hydro_session_udf_scores(hydro_session *s, int32_t udf, i
 
 /* Submit one step.  d_tuples: device fp32 rows, 16-byte aligned, counts[0]
  * rows of query 0, then counts[1] rows of query 1, ... (BORROWED until the
- * step is polled).
- * counts: host [n_queries], each >= 0, sum <= max_step_tuples.  A query with
+ * step is polled).  With K = batches_per_step > 1, counts has n_queries x K
+ * entries (query q's batches k = 0..K-1 at q K + k, stacked in that order; a
+ * query's non-empty batches come first).
+ * counts: host, each >= 0, sum <= max_step_tuples.  A query with
  * count 0 sits the step out (its batch number does not advance).
  * Asynchronous; *out_step receives 0, 1, 2, ... */
 HYDRO_API hydro_status hydro_session_submit(hydro_session *s, const void *d_tuples, const int32_t *counts,
@@ -466,7 +475,7 @@ HYDRO_API hydro_status hydro_session_submit(hydro_session *s, const void *d_tupl
 
 /* Result of a step.  pass_bitmap: host, ceil(total/32) words, bit j = the
  * j-th stacked tuple passed every predicate of its query.  per_query: host
- * [n_queries] (nullable).  device_ms (nullable): GPU time of the step.
+ * [n_queries x K] (nullable), one entry per (query, batch of the step).  device_ms (nullable): GPU time of the step.
  * wait_ms as in hydro_poll_result; HYDRO_EAGAIN if not finished. */
 HYDRO_API hydro_status hydro_session_poll(hydro_session *s, int64_t step, uint32_t *pass_bitmap,
                                           hydro_step_query *per_query, double *device_ms, int32_t wait_ms);

@@ -90,7 +90,7 @@ class SessionConfig(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("max_in_flight", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("learned", ctypes.c_int32), ("proxy_hidden", ctypes.c_int32),
                 ("proxy_refresh", ctypes.c_int32), ("proxy_epochs", ctypes.c_int32), ("proxy_lr", ctypes.c_float),
-                ("proxy_seed", ctypes.c_int32)]
+                ("proxy_seed", ctypes.c_int32), ("batches_per_step", ctypes.c_int32), ("route_lag", ctypes.c_int32)]
 
 
 class StepQuery(ctypes.Structure):
@@ -415,7 +415,8 @@ class Session:
     def __init__(self, *, dim: int, max_step_tuples: int, precision: str = "fp32", warmup: int = 1,
                  window: int = 8, graphs: bool = True, autotune: bool = True, max_in_flight: int = 2,
                  device: int = 0, stream=None, learned: bool = False, proxy_hidden: int = 64,
-                 proxy_refresh: int = 16, proxy_epochs: int = 1, proxy_lr: float = 1e-3, proxy_seed: int = 1):
+                 proxy_refresh: int = 16, proxy_epochs: int = 1, proxy_lr: float = 1e-3, proxy_seed: int = 1,
+                 batches_per_step: int = 1, lag: int = 0):
         L = load()
         cfg = SessionConfig()
         L.hydro_session_default_config(ctypes.byref(cfg))
@@ -435,6 +436,9 @@ class Session:
         cfg.proxy_epochs = proxy_epochs
         cfg.proxy_lr = proxy_lr
         cfg.proxy_seed = proxy_seed
+        cfg.batches_per_step = batches_per_step
+        cfg.route_lag = lag
+        self.K = batches_per_step
         self._h = ctypes.c_void_p()
         _check(L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(self._h)), "hydro_session_create")
         self.n_udf = 0
@@ -481,7 +485,8 @@ class Session:
                                                int(tuples.shape[0]), _ptr(out)), "hydro_session_udf_scores")
 
     def submit(self, tuples, counts) -> int:
-        Q = len(self.queries)
+        """counts: per query (K = 1) or per (query, batch) q*K + k."""
+        Q = len(self.queries) * self.K
         c = (ctypes.c_int32 * Q)(*[int(v) for v in counts])
         sid = ctypes.c_int64()
         _check(load().hydro_session_submit(self._h, _ptr(tuples), c, ctypes.byref(sid)), "hydro_session_submit")
@@ -489,8 +494,8 @@ class Session:
         return sid.value
 
     def poll(self, step: int, total: int | None = None, wait_ms: int = -1):
-        """(bitmap words uint32, [per-query dict], device_ms)."""
-        Q = len(self.queries)
+        """(bitmap words uint32, [per (query, batch) dict], device_ms)."""
+        Q = len(self.queries) * self.K
         total = self._last_total if total is None else total
         words = np.zeros(max(1, (total + 31) // 32), np.uint32)
         per = (StepQuery * max(Q, 1))()
@@ -500,7 +505,7 @@ class Session:
         out = []
         for q in range(Q):
             r = per[q]
-            P = len(self.queries[q])
+            P = len(self.queries[q // self.K])
             out.append(dict(n=r.n, n_pass=r.n_pass, batch=r.batch, warmup=bool(r.warmup), order=list(r.order[:P]),
                             evaluated=list(r.evaluated[:P]), passed=list(r.passed[:P]),
                             recheck_split=list(r.recheck_split[:P]), recheck_fp32=list(r.recheck_fp32[:P]), recheck_fp64=list(r.recheck_fp64[:P])))

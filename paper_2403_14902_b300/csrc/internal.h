@@ -20,6 +20,7 @@ struct MlpDev {
     int dims[kMaxLayers + 1];
     const float *W[kMaxLayers];
     const float *b[kMaxLayers];
+    const float *WT[kMaxLayers];   // transposed weights [in][out] (sessions' band levels), else nullptr
 };
 
 // Router costs: c[i] is the per-tuple cost of predicate i (for a predicate

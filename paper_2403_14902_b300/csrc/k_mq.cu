@@ -63,8 +63,11 @@ __device__ __forceinline__ void set_cond(const Cond &c, bool v) {
     if (c.flag) *c.flag = v ? 1 : 0;
 }
 
-// Slot of tuple e (query q) in round r: its own order (learned sessions) or
-// its query's.
+// Query (tables, history) of virtual query v.
+__device__ __forceinline__ int rq(const MqDev &d, int v) { return v / d.K; }
+
+// Slot of tuple e (batch v) in round r: its own order (learned sessions) or
+// its batch's.
 __device__ __forceinline__ int slot_of(const MqDev &d, int e, int q, int r) {
     return d.order_t ? d.order_t[(size_t)e * kMqSlots + r] : d.order[q * kMqSlots + r];
 }
@@ -136,7 +139,8 @@ __global__ void k_mq_router(MqDev d, MqHist h) {
     const int i = lane_id();
     if (q >= d.Q) return;
     const int count = d.hdr->counts[q];
-    const int P = d.np[q];
+    const int qq = rq(d, q);
+    const int P = d.np[qq];
     if (count <= 0) {
         if (i == 0) {
             d.bidx[q] = -1;
@@ -145,29 +149,30 @@ __global__ void k_mq_router(MqDev d, MqHist h) {
         if (i < kMqSlots) d.order[q * kMqSlots + i] = (unsigned char)i;
         return;
     }
-    const long long b = h.bdone[q];
+    // sub-batches are filled in order, so this is the query's batch bdone + k
+    const long long b = h.bdone[qq] + (q - qq * d.K);
     if (i == 0) d.bidx[q] = b;
-    if (b < h.warmup || b == 0) {
+    const long long last = b - 1 - h.lag;
+    if (b < h.warmup || last < 0) {
         if (i == 0) d.evall[q] = b < h.warmup ? 1 : 0;
         if (i < kMqSlots) d.order[q * kMqSlots + i] = (unsigned char)i;
         return;
     }
     if (i == 0) d.evall[q] = 0;
-    const long long last = b - 1;
     const long long lo = last - h.window + 1 > 0 ? last - h.window + 1 : 0;
     long long E = 0, Pp = 0;
     unsigned long long c = 0;
     if (i < P) {
-        c = (unsigned long long)d.cost[q * kMqSlots + i];
+        c = (unsigned long long)d.cost[qq * kMqSlots + i];
         for (long long bb = lo; bb <= last; ++bb) {
-            const StatRow &r = h.ring[((size_t)q * h.R + (size_t)(bb % h.R)) * kMqSlots + i];
+            const StatRow &r = h.ring[((size_t)qq * h.R + (size_t)(bb % h.R)) * kMqSlots + i];
             E += r.evaluated;
             Pp += r.passed;
         }
         if (E == 0) {
             const int nw = (int)(h.warmup < last + 1 ? h.warmup : last + 1);
             for (int w = 0; w < nw; ++w) {
-                const StatRow &r = h.warm[((size_t)q * h.warmup + w) * kMqSlots + i];
+                const StatRow &r = h.warm[((size_t)qq * h.warmup + w) * kMqSlots + i];
                 E += r.evaluated;
                 Pp += r.passed;
             }
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(256) k_mq_partition(MqDev d, int r) {
             e = d.alive[cur][m];
             const int q = d.qid[e];
             const int slot = slot_of(d, e, q, r);
-            g = d.udf[q * kMqSlots + slot];
+            g = d.udf[rq(d, q) * kMqSlots + slot];
         }
         const int pos = warp_append(live ? &d.rc->n[LV_MAIN][g] : nullptr, live);
         if (live) d.list[LV_MAIN][(size_t)g * d.cap + pos] = e;
@@ -293,7 +298,7 @@ __global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int in, int
             if (skipped) {
                 inband = true;
             } else {
-                const double t = d.thr[q * kMqSlots + slot];
+                const double t = d.thr[rq(d, q) * kMqSlots + slot];
                 double s;
                 if (partials) {
                     const float *pp = partials + (size_t)i * pstride;
@@ -360,11 +365,14 @@ __device__ __forceinline__ T lane_dot(const float *w, const X *x, int K) {
     return s;
 }
 
-// Band levels run layer-parallel: a warp per (output neuron, block of up to
-// kBandE entries) of one hidden layer, so each weight row is read once per
-// block; entries stacked group by group (the first `cap_lv` of the level),
-// activations in T (float: the FP32 level, double: FP64).
-constexpr int kBandE = 8;
+// Band levels run layer-parallel as skinny GEMMs: a CTA computes 32 output
+// neurons (lane = neuron, coalesced loads of the transposed weights
+// WT[k][n]) for up to kBandE entries (accumulators in registers), its 8
+// warps splitting K and summing through shared memory.  Entries are stacked
+// group by group (the first `cap_lv` of the level); activations in T
+// (float: the FP32 level, double: FP64).
+constexpr int kBandE = 16;
+constexpr int kBandWarps = 8;
 
 __device__ __forceinline__ void band_offsets(const MqDev &d, const GroupedMlps &mlps, int level, int cap_lv,
                                              int depth, int *off, int *wstart) {
@@ -376,15 +384,103 @@ __device__ __forceinline__ void band_offsets(const MqDev &d, const GroupedMlps &
         off[g + 1] = off[g] + lim;
         const MlpDev &m = mlps.m[g];
         const int blocks = (lim + kBandE - 1) / kBandE;
+        wstart[g + 1] = wstart[g] + (depth >= 0 && depth + 1 < m.n_layers ? blocks * ((m.dims[depth + 1] + 31) / 32) : 0);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kBandWarps) k_mq_band_layer(MqDev d, GroupedMlps mlps, int level, int depth,
+                                                                   T *act0, T *act1, int ld, int cap_lv) {
+    __shared__ T part[kBandWarps][kBandE][32];
+    int off[kMqPool + 1], wstart[kMqPool + 1];
+    band_offsets(d, mlps, level, cap_lv, depth, off, wstart);
+    const T *in_act = (depth & 1) ? act0 : act1;   // depth - 1 wrote act[(depth - 1) & 1]
+    T *out_act = (depth & 1) ? act1 : act0;
+    const float *X = d.hdr->X;
+    const int *list = d.list[level];
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    for (int item = blockIdx.x; item < wstart[d.G]; item += gridDim.x) {
+        int g = 0;
+        while (item >= wstart[g + 1]) ++g;
+        const MlpDev &m = mlps.m[g];
+        const int N = m.dims[depth + 1], K = m.dims[depth];
+        const int nt = (N + 31) / 32, local = item - wstart[g];
+        const int o = (local % nt) * 32 + lane, e0 = (local / nt) * kBandE;
+        const int ne = min(kBandE, (off[g + 1] - off[g]) - e0);
+        const float *WT = m.WT[depth];
+        // this warp's share of K
+        const int kc = (K + kBandWarps - 1) / kBandWarps;
+        const int k0 = warp * kc, k1 = min(K, k0 + kc);
+        T acc[kBandE];
+#pragma unroll
+        for (int e = 0; e < kBandE; ++e) acc[e] = 0;
+        if (o < N) {
+            if (depth == 0) {
+                const float *xr[kBandE];
+#pragma unroll
+                for (int e = 0; e < kBandE; ++e)
+                    xr[e] = X + (size_t)list[(size_t)g * d.cap + e0 + (e < ne ? e : 0)] * d.dim;
+#pragma unroll 4
+                for (int k = k0; k < k1; ++k) {
+                    const T wk = (T)WT[(size_t)k * N + o];
+#pragma unroll
+                    for (int e = 0; e < kBandE; ++e)
+                        if (e < ne) acc[e] += wk * (T)xr[e][k];
+                }
+            } else {
+                const T *xr[kBandE];
+#pragma unroll
+                for (int e = 0; e < kBandE; ++e) xr[e] = in_act + (size_t)(off[g] + e0 + (e < ne ? e : 0)) * ld;
+#pragma unroll 4
+                for (int k = k0; k < k1; ++k) {
+                    const T wk = (T)WT[(size_t)k * N + o];
+#pragma unroll
+                    for (int e = 0; e < kBandE; ++e)
+                        if (e < ne) acc[e] += wk * xr[e][k];
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < kBandE; ++e) part[warp][e][lane] = acc[e];
+        __syncthreads();
+        // warp w sums entries w, w + 8 over the 8 warps' shares
+        for (int e = warp; e < ne; e += kBandWarps) {
+            T s = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < kBandWarps; ++w2) s += part[w2][e][lane];
+            if (o < N) {
+                s += (T)m.b[depth][o];
+                out_act[(size_t)(off[g] + e0 + e) * ld + o] = s > (T)0 ? s : (T)0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// For bands of a few entries (the FP64 level): a warp per (output neuron,
+// block of up to kWpnE entries), spreading even one entry's layer over all
+// SMs; each weight row is read once per block.
+constexpr int kWpnE = 8;
+
+__device__ __forceinline__ void wpn_offsets(const MqDev &d, const GroupedMlps &mlps, int level, int cap_lv,
+                                             int depth, int *off, int *wstart) {
+    const int *cnts = d.rc->n[level];
+    off[0] = 0;
+    wstart[0] = 0;
+    for (int g = 0; g < d.G; ++g) {
+        const int lim = max(0, min(cnts[g], cap_lv - off[g]));
+        off[g + 1] = off[g] + lim;
+        const MlpDev &m = mlps.m[g];
+        const int blocks = (lim + kWpnE - 1) / kWpnE;
         wstart[g + 1] = wstart[g] + (depth >= 0 && depth + 1 < m.n_layers ? blocks * m.dims[depth + 1] : 0);
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_mq_band_layer(MqDev d, GroupedMlps mlps, int level, int depth, T *act0,
+__global__ void __launch_bounds__(256) k_mq_band_layer_wpn(MqDev d, GroupedMlps mlps, int level, int depth, T *act0,
                                                        T *act1, int ld, int cap_lv) {
     int off[kMqPool + 1], wstart[kMqPool + 1];
-    band_offsets(d, mlps, level, cap_lv, depth, off, wstart);
+    wpn_offsets(d, mlps, level, cap_lv, depth, off, wstart);
     const T *in_act = (depth & 1) ? act0 : act1;   // depth - 1 wrote act[(depth - 1) & 1]
     T *out_act = (depth & 1) ? act1 : act0;
     const float *X = d.hdr->X;
@@ -396,26 +492,26 @@ __global__ void __launch_bounds__(256) k_mq_band_layer(MqDev d, GroupedMlps mlps
         const MlpDev &m = mlps.m[g];
         const int N = m.dims[depth + 1], K = m.dims[depth];
         const int local = w - wstart[g];
-        const int o = local % N, e0 = (local / N) * kBandE;
-        const int ne = min(kBandE, (off[g + 1] - off[g]) - e0);
+        const int o = local % N, e0 = (local / N) * kWpnE;
+        const int ne = min(kWpnE, (off[g + 1] - off[g]) - e0);
         const float *wr = m.W[depth] + (size_t)o * K;
-        const void *xr[kBandE];
+        const void *xr[kWpnE];
 #pragma unroll
-        for (int e = 0; e < kBandE; ++e) {
+        for (int e = 0; e < kWpnE; ++e) {
             const int el = e0 + (e < ne ? e : 0);
             xr[e] = depth == 0 ? (const void *)(X + (size_t)list[(size_t)g * d.cap + el] * d.dim)
                                : (const void *)(in_act + (size_t)(off[g] + el) * ld);
         }
-        T acc[kBandE];
+        T acc[kWpnE];
 #pragma unroll
-        for (int e = 0; e < kBandE; ++e) acc[e] = 0;
+        for (int e = 0; e < kWpnE; ++e) acc[e] = 0;
         if ((K & 127) == 0) {
 #pragma unroll 2
             for (int k = 4 * lane; k < K; k += 128) {
                 float wv[4];
                 load4(wr + k, wv);
 #pragma unroll
-                for (int e = 0; e < kBandE; ++e) {
+                for (int e = 0; e < kWpnE; ++e) {
                     if (e >= ne) break;
                     T xv[4];
                     if (depth == 0) load4(static_cast<const float *>(xr[e]) + k, xv);
@@ -428,7 +524,7 @@ __global__ void __launch_bounds__(256) k_mq_band_layer(MqDev d, GroupedMlps mlps
             for (int k = lane; k < K; k += 32) {
                 const T wk = (T)wr[k];
 #pragma unroll
-                for (int e = 0; e < kBandE; ++e) {
+                for (int e = 0; e < kWpnE; ++e) {
                     if (e >= ne) break;
                     const T xk = depth == 0 ? (T) static_cast<const float *>(xr[e])[k] : static_cast<const T *>(xr[e])[k];
                     acc[e] += wk * xk;
@@ -437,7 +533,7 @@ __global__ void __launch_bounds__(256) k_mq_band_layer(MqDev d, GroupedMlps mlps
         }
         const T bo = (T)m.b[depth][o];
 #pragma unroll
-        for (int e = 0; e < kBandE; ++e) {
+        for (int e = 0; e < kWpnE; ++e) {
             if (e >= ne) break;
             T s = acc[e];
 #pragma unroll
@@ -474,7 +570,7 @@ __global__ void __launch_bounds__(256) k_mq_band_final(MqDev d, GroupedMlps mlps
         s += (T)m.b[L - 1][0];
         const int q = d.qid[e];
         const int slot = slot_of(d, e, q, r);
-        const double t = d.thr[q * kMqSlots + slot];
+        const double t = d.thr[rq(d, q) * kMqSlots + slot];
         StatRow *row = d.rows + q * kMqSlots + slot;
         bool pass;
         if (sizeof(T) == 4) {
@@ -547,7 +643,7 @@ __global__ void __launch_bounds__(256) k_mq_band64(MqDev d, int r, GroupedMlps m
         if (threadIdx.x == 0) {
             const int q = d.qid[e];
             const int slot = slot_of(d, e, q, r);
-            const bool pass = cur[0] > d.thr[q * kMqSlots + slot];
+            const bool pass = cur[0] > d.thr[rq(d, q) * kMqSlots + slot];
             d.ok[e] = (unsigned char)pass;
             StatRow *row = d.rows + q * kMqSlots + slot;
             if (pass) {
@@ -574,7 +670,7 @@ __global__ void __launch_bounds__(256) k_mq_survivors(MqDev d, int r, Cond next_
         if (m < n) {
             e = d.alive[cur][m];
             const int q = d.qid[e];
-            keep = (d.ok[e] || d.evall[q]) && r + 1 < d.np[q];
+            keep = (d.ok[e] || d.evall[q]) && r + 1 < d.np[rq(d, q)];
         }
         const int pos = warp_append(keep ? &d.rc->alive[cur ^ 1] : nullptr, keep);
         if (keep) d.alive[cur ^ 1][pos] = e;
@@ -596,7 +692,7 @@ __global__ void __launch_bounds__(256) k_mq_result(MqDev d, unsigned int *bitmap
             const int e = w * 32 + j;
             if (e >= n) break;
             const int q = d.qid[e];
-            const unsigned full = (1u << d.np[q]) - 1u;
+            const unsigned full = (1u << d.np[rq(d, q)]) - 1u;
             if (((unsigned)d.label[e] & full) == full) {
                 bits |= 1u << j;
                 atomicAdd(reinterpret_cast<unsigned long long *>(&d.npass[q]), 1ull);
@@ -625,9 +721,10 @@ __global__ void k_mq_commit(MqDev d, MqHist h, StatRow *res_rows, unsigned char 
         res_npass[q] = d.npass[q];
     }
     if (b < 0) return;
-    h.ring[((size_t)q * h.R + (size_t)(b % h.R)) * kMqSlots + slot] = row;
-    if (b < h.warmup) h.warm[((size_t)q * h.warmup + b) * kMqSlots + slot] = row;
-    if (slot == 0) h.bdone[q] = b + 1;
+    const int qq = rq(d, q);
+    h.ring[((size_t)qq * h.R + (size_t)(b % h.R)) * kMqSlots + slot] = row;
+    if (b < h.warmup) h.warm[((size_t)qq * h.warmup + b) * kMqSlots + slot] = row;
+    if (slot == 0) atomicMax(reinterpret_cast<unsigned long long *>(&h.bdone[qq]), (unsigned long long)(b + 1));
 }
 
 __global__ void __launch_bounds__(256) k_mq_tuple_order(MqDev d, const float *logits, int ldz, const int *ready) {
@@ -635,7 +732,8 @@ __global__ void __launch_bounds__(256) k_mq_tuple_order(MqDev d, const float *lo
     const bool use_proxy = logits && ready && *ready;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const int q = d.qid[e];
-        const int P = d.np[q];
+        const int qq = rq(d, q);
+        const int P = d.np[qq];
         unsigned char *o = d.order_t + (size_t)e * kMqSlots;
         if (d.evall[q] || !use_proxy) {
             for (int k = 0; k < kMqSlots; ++k) o[k] = d.evall[q] ? (unsigned char)k : d.order[q * kMqSlots + k];
@@ -644,7 +742,7 @@ __global__ void __launch_bounds__(256) k_mq_tuple_order(MqDev d, const float *lo
         float key[kMqSlots];
         for (int i = 0; i < P; ++i) {
             const float z = fminf(fmaxf(logits[(size_t)e * ldz + i], -30.f), 30.f);
-            key[i] = (float)d.cost[q * kMqSlots + i] * (1.f + expf(z));
+            key[i] = (float)d.cost[qq * kMqSlots + i] * (1.f + expf(z));
         }
         for (int i = 0; i < P; ++i) {
             int pos = 0;
@@ -702,7 +800,7 @@ void mq_launch_router(const MqDev &d, const MqHist &h, cudaStream_t st) {
 }
 
 void mq_launch_partition(const MqDev &d, int r, cudaStream_t st, int sms) {
-    k_mq_partition<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r);
+    k_mq_partition<<<grid_for(d.cap, 256, sms, 2), 256, 0, st>>>(d, r);
 }
 
 void mq_launch_layers_f32(const MqLayers &L, cudaStream_t st, int sms) {
@@ -717,21 +815,21 @@ void mq_launch_classify(const MqDev &d, int r, int in, int out, cudaStream_t st,
                         const TcHeads *heads, const float *partials, int pstride) {
     TcHeads h{};
     if (heads) h = *heads;
-    k_mq_classify<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r, in, out, next, next_min, h,
+    k_mq_classify<<<grid_for(d.cap, 256, sms, 2), 256, 0, st>>>(d, r, in, out, next, next_min, h,
                                                                 partials, pstride);
 }
 
 void mq_launch_band32(const MqDev &d, int r, const GroupedMlps &mlps, int max_hidden, float *act0, float *act1,
                       int ld, cudaStream_t st, int sms, Cond next) {
     for (int depth = 0; depth < max_hidden; ++depth)
-        k_mq_band_layer<float><<<sms * 8, 256, 0, st>>>(d, mlps, LV_F32, depth, act0, act1, ld, d.cap);
+        k_mq_band_layer<float><<<sms * 4, 32 * kBandWarps, 0, st>>>(d, mlps, LV_F32, depth, act0, act1, ld, d.cap);
     k_mq_band_final<float><<<sms * 2, 256, 0, st>>>(d, mlps, LV_F32, r, act0, act1, ld, d.cap, next);
 }
 
 void mq_launch_band64(const MqDev &d, int r, const GroupedMlps &mlps, int max_hidden, cudaStream_t st, int sms) {
     for (int depth = 0; depth < max_hidden; ++depth)
-        k_mq_band_layer<double><<<sms * 8, 256, 0, st>>>(d, mlps, LV_F64, depth, d.act64[0], d.act64[1], d.ld64,
-                                                         d.cap64);
+        k_mq_band_layer_wpn<double><<<sms * 8, 256, 0, st>>>(d, mlps, LV_F64, depth, d.act64[0], d.act64[1], d.ld64,
+                                                             d.cap64);
     k_mq_band_final<double><<<sms * 2, 256, 0, st>>>(d, mlps, LV_F64, r, d.act64[0], d.act64[1], d.ld64, d.cap64,
                                                      Cond());
     const size_t smem = sizeof(double) * 2 * (size_t)mlps.max_width;
@@ -739,7 +837,7 @@ void mq_launch_band64(const MqDev &d, int r, const GroupedMlps &mlps, int max_hi
 }
 
 void mq_launch_survivors(const MqDev &d, int r, cudaStream_t st, int sms, Cond next_round) {
-    k_mq_survivors<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, r, next_round);
+    k_mq_survivors<<<grid_for(d.cap, 256, sms, 2), 256, 0, st>>>(d, r, next_round);
 }
 
 void mq_launch_result(const MqDev &d, unsigned int *bitmap, cudaStream_t st, int sms) {

@@ -51,19 +51,23 @@ struct Cond {
 constexpr int kMqMaxRounds = kMqSlots;
 constexpr int kMqGates = 4 * kMqMaxRounds;   // per round: round, split, FP32 band, FP64 band
 
-// Device tables and per-step buffers of a session.
+// Device tables and per-step buffers of a session.  A step holds up to K
+// routing batches of each query: "virtual query" v = q * K + k is query q's
+// k-th batch of the step; per-step arrays are indexed by v (Q of them),
+// the query tables and histories by q = v / K.
 struct MqDev {
     int Q, G, cap, dim;
+    int K;                         // batches per query per step
     const StepHdr *hdr;
     int *off;                      // [Q+1] stacked offsets of the step
     unsigned char *qid;            // [cap] query of each stacked tuple
-    const unsigned char *np;       // [Q] predicates per query
-    const unsigned char *udf;      // [Q][8] pool UDF of each slot
-    const double *thr;             // [Q][8] thresholds
-    const long long *cost;         // [Q][8] model cost of each slot's UDF
-    unsigned char *order;          // [Q][8] slot order of the step
+    const unsigned char *np;       // [Q / K] predicates per query
+    const unsigned char *udf;      // [Q / K][8] pool UDF of each slot
+    const double *thr;             // [Q / K][8] thresholds
+    const long long *cost;         // [Q / K][8] model cost of each slot's UDF
+    unsigned char *order;          // [Q][8] slot order of each batch of the step
     unsigned char *evall;          // [Q] 1: warmup batch (every slot on every tuple)
-    long long *bidx;               // [Q] the query's batch number this step (-1: no tuples)
+    long long *bidx;               // [Q] the batch's number in its query (-1: no tuples)
     StatRow *rows;                 // [Q][8] step statistics per slot
     long long *npass;              // [Q]
     unsigned char *visited, *label, *ok;   // [cap] per tuple
@@ -81,11 +85,12 @@ struct MqDev {
 
 // Per-query statistics history (device).
 struct MqHist {
-    StatRow *ring;                 // [Q][R][8]
+    StatRow *ring;                 // [queries][R][8]
     int R;
-    StatRow *warm;                 // [Q][warmup][8]
+    StatRow *warm;                 // [queries][warmup][8]
     int warmup, window;
-    long long *bdone;              // [Q] batches completed
+    int lag;                       // batch b is routed on batches <= b - 1 - lag
+    long long *bdone;              // [queries] batches completed
 };
 
 // One depth of the stacked grouped FP32 layers.  Group g's rows are

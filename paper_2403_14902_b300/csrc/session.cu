@@ -56,7 +56,7 @@ struct Udf {
     std::vector<std::vector<float>> W, b;
     long long cost = 0;
     double margin_lowp = 0.02, margin_x3 = 1e-3, margin_fp32 = 1e-5;
-    std::vector<float *> dW, db;
+    std::vector<float *> dW, db, dWT;
     std::vector<__nv_bfloat16 *> dW16;
     std::vector<__nv_bfloat16 *> dW3;   // split-BF16 weights [N][3K] = [W_hi | W_lo | W_hi]
     std::vector<int> nt;     // tensor-core tile width per hidden layer (0: widest dividing N)
@@ -149,7 +149,7 @@ struct hydro_session {
     float *ringX = nullptr;
     unsigned char *ringL = nullptr, *ringM = nullptr;
     std::vector<int> ring_n;
-    long long learned_batches = 0;
+    long long learned_batches = 0, learned_steps = 0;
     int adam_t = 0;
     long long last_step_total = -1;       // stacked tuples of the most recent step (debug trace)
 };
@@ -534,7 +534,8 @@ hydro_status finalize(hydro_session *s) {
         CU(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
         s->own_stream = true;
     }
-    const int Q = (int)s->queries.size(), G = (int)s->udfs.size(), cap = c.max_step_tuples;
+    const int NQ = (int)s->queries.size(), G = (int)s->udfs.size(), cap = c.max_step_tuples;
+    const int K = c.batches_per_step, Q = NQ * K;   // Q: batches of one step (virtual queries)
     s->wmax = 64;
     s->max_hidden = 0;
     for (const Udf &u : s->udfs) {
@@ -550,12 +551,20 @@ hydro_status finalize(hydro_session *s) {
         Udf &u = s->udfs[g];
         u.dW.assign(u.n_layers, nullptr);
         u.db.assign(u.n_layers, nullptr);
+        u.dWT.assign(u.n_layers, nullptr);
         u.dW16.assign(u.n_layers, nullptr);
         u.dW3.assign(u.n_layers, nullptr);
         u.nt.assign(u.n_layers, 0);
         for (int l = 0; l < u.n_layers; ++l) {
             TRY(upload(s, &u.dW[l], u.W[l].data(), u.W[l].size()));
             TRY(upload(s, &u.db[l], u.b[l].data(), u.b[l].size()));
+            {
+                const int K = u.dims[l], N = u.dims[l + 1];
+                std::vector<float> wt((size_t)K * N);
+                for (int n = 0; n < N; ++n)
+                    for (int k = 0; k < K; ++k) wt[(size_t)k * N + n] = u.W[l][(size_t)n * K + k];
+                TRY(upload(s, &u.dWT[l], wt.data(), wt.size()));
+            }
             if (bf16(s) && l + 1 < u.n_layers) {
                 const int K = u.dims[l], N = u.dims[l + 1];
                 std::vector<__nv_bfloat16> w16(u.W[l].size()), w3((size_t)N * 3 * K);
@@ -579,16 +588,17 @@ hydro_status finalize(hydro_session *s) {
         for (int l = 0; l < u.n_layers; ++l) {
             u.mlp.W[l] = u.dW[l];
             u.mlp.b[l] = u.db[l];
+            u.mlp.WT[l] = u.dWT[l];
         }
         s->mlps.m[g] = u.mlp;
     }
     CU(mq_band_smem_setup(s->mlps.max_width));
 
     // query tables
-    std::vector<unsigned char> np(Q), udf((size_t)Q * kMqSlots, 0);
-    std::vector<double> thr((size_t)Q * kMqSlots, 0.0);
-    std::vector<long long> cost((size_t)Q * kMqSlots, 0);
-    for (int q = 0; q < Q; ++q) {
+    std::vector<unsigned char> np(NQ), udf((size_t)NQ * kMqSlots, 0);
+    std::vector<double> thr((size_t)NQ * kMqSlots, 0.0);
+    std::vector<long long> cost((size_t)NQ * kMqSlots, 0);
+    for (int q = 0; q < NQ; ++q) {
         np[q] = (unsigned char)s->queries[q].P;
         for (int k = 0; k < s->queries[q].P; ++k) {
             udf[(size_t)q * kMqSlots + k] = (unsigned char)s->queries[q].udf[k];
@@ -598,6 +608,7 @@ hydro_status finalize(hydro_session *s) {
     }
     MqDev &d = s->d;
     d.Q = Q;
+    d.K = K;
     d.G = G;
     d.cap = cap;
     d.dim = c.dim;
@@ -694,7 +705,7 @@ hydro_status finalize(hydro_session *s) {
         s->host_allocs.push_back(hp);
         s->h_one = (int *)hp;
         *s->h_one = 1;
-        const int R = std::max(1, c.proxy_refresh);
+        const int R = (std::max(1, c.proxy_refresh) + K - 1) / K;   // steps holding proxy_refresh batches
         TRY(dalloc(s, &s->ringX, sizeof(float) * (size_t)R * cap * D));
         TRY(dalloc(s, &s->ringL, (size_t)R * cap));
         TRY(dalloc(s, &s->ringM, (size_t)R * cap));
@@ -704,15 +715,16 @@ hydro_status finalize(hydro_session *s) {
 
     // statistics history
     MqHist &h = s->h;
-    h.R = c.stats_window + 2;
+    h.R = c.stats_window + c.route_lag + 2;
+    h.lag = c.route_lag;
     h.warmup = c.warmup_batches;
     h.window = c.stats_window;
-    TRY(dalloc(s, &h.ring, sizeof(StatRow) * (size_t)Q * h.R * kMqSlots));
-    TRY(dalloc(s, &h.warm, sizeof(StatRow) * (size_t)Q * std::max(1, h.warmup) * kMqSlots));
-    TRY(dalloc(s, &h.bdone, sizeof(long long) * Q));
-    CU(cudaMemset(h.ring, 0, sizeof(StatRow) * (size_t)Q * h.R * kMqSlots));
-    CU(cudaMemset(h.warm, 0, sizeof(StatRow) * (size_t)Q * std::max(1, h.warmup) * kMqSlots));
-    CU(cudaMemset(h.bdone, 0, sizeof(long long) * Q));
+    TRY(dalloc(s, &h.ring, sizeof(StatRow) * (size_t)NQ * h.R * kMqSlots));
+    TRY(dalloc(s, &h.warm, sizeof(StatRow) * (size_t)NQ * std::max(1, h.warmup) * kMqSlots));
+    TRY(dalloc(s, &h.bdone, sizeof(long long) * NQ));
+    CU(cudaMemset(h.ring, 0, sizeof(StatRow) * (size_t)NQ * h.R * kMqSlots));
+    CU(cudaMemset(h.warm, 0, sizeof(StatRow) * (size_t)NQ * std::max(1, h.warmup) * kMqSlots));
+    CU(cudaMemset(h.bdone, 0, sizeof(long long) * NQ));
 
     // in-flight slots
     s->slots.resize(c.max_in_flight);
@@ -756,19 +768,26 @@ hydro_status upload_margins(hydro_session *s) {
 // (masked BCE on the slots each tuple was evaluated on, Adam) and mark it
 // ready.  Stream-ordered after the step, outside its graph.
 hydro_status learned_after_step(hydro_session *s, const Slot &slot) {
-    const int n = slot.counts[0];
+    int n = 0, nb = 0;   // the step's tuples and batches (one query)
+    for (int k = 0; k < s->cfg.batches_per_step; ++k) {
+        n += slot.counts[k];
+        nb += slot.counts[k] > 0;
+    }
     if (n <= 0) return HYDRO_OK;
     const hydro_session_config &c = s->cfg;
     const int D = c.dim, H = s->ph, P = s->queries[0].P, cap = s->d.cap;
-    const int R = (int)s->ring_n.size();
-    const int rs = (int)(s->learned_batches % R);
+    const int R = (int)s->ring_n.size();   // steps kept: those holding the last proxy_refresh batches
+    const int rs = (int)(s->learned_steps % R);
     CU(cudaMemcpyAsync(s->ringX + (size_t)rs * cap * D, slot.h_hdr->X, sizeof(float) * (size_t)n * D,
                        cudaMemcpyDeviceToDevice, s->st));
     CU(cudaMemcpyAsync(s->ringL + (size_t)rs * cap, s->d.label, n, cudaMemcpyDeviceToDevice, s->st));
     CU(cudaMemcpyAsync(s->ringM + (size_t)rs * cap, s->d.visited, n, cudaMemcpyDeviceToDevice, s->st));
     s->ring_n[rs] = n;
-    s->learned_batches++;
-    if (s->learned_batches % R) return HYDRO_OK;
+    s->learned_steps++;
+    const long long before = s->learned_batches;
+    s->learned_batches += nb;
+    const int refresh = std::max(1, c.proxy_refresh);
+    if (before / refresh == s->learned_batches / refresh) return HYDRO_OK;
     const size_t nW1 = (size_t)H * D;
     for (int e = 0; e < std::max(1, c.proxy_epochs); ++e)
         for (int k = 0; k < R; ++k) {
@@ -870,6 +889,8 @@ void hydro_session_default_config(hydro_session_config *cfg) {
     cfg->proxy_epochs = 1;
     cfg->proxy_lr = 1e-3f;
     cfg->proxy_seed = 1;
+    cfg->batches_per_step = 1;
+    cfg->route_lag = 0;
 }
 
 hydro_status hydro_session_create(const hydro_session_config *cfg, hydro_session **out) {
@@ -883,6 +904,9 @@ hydro_status hydro_session_create(const hydro_session_config *cfg, hydro_session
         return fail(HYDRO_EINVAL, "precision must be FP32 or BF16");
     if (cfg->warmup_batches < 0 || cfg->stats_window < 1) return fail(HYDRO_EINVAL, "bad warmup/window");
     if (cfg->max_in_flight < 1 || cfg->max_in_flight > 8) return fail(HYDRO_EINVAL, "max_in_flight outside 1..8");
+    if (cfg->batches_per_step < 1 || cfg->batches_per_step > 8 || cfg->route_lag < cfg->batches_per_step - 1 ||
+        cfg->route_lag > 64)
+        return fail(HYDRO_EINVAL, "batches_per_step 1..8 with route_lag >= batches_per_step - 1 (<= 64)");
     if (cfg->learned && (cfg->proxy_hidden < 0 || cfg->proxy_hidden > 1024 || cfg->proxy_refresh < 1 ||
                          cfg->proxy_refresh > 256 || cfg->proxy_epochs < 0 || !(cfg->proxy_lr > 0.f)))
         return fail(HYDRO_EINVAL, "bad proxy settings");
@@ -927,7 +951,8 @@ hydro_status hydro_session_add_query(hydro_session *s, int32_t n_preds, const in
     set_last_error("");
     TRY(check(s));
     if (s->finalized) return fail(HYDRO_ESTATE, "queries must be added before the first submit");
-    if ((int)s->queries.size() >= HYDRO_MAX_QUERIES) return fail(HYDRO_EINVAL, "too many queries");
+    if (((int)s->queries.size() + 1) * s->cfg.batches_per_step > HYDRO_MAX_QUERIES)
+        return fail(HYDRO_EINVAL, "too many queries (queries x batches_per_step <= %d)", HYDRO_MAX_QUERIES);
     if (s->cfg.learned && !s->queries.empty()) return fail(HYDRO_EINVAL, "learned sessions have one query");
     if (n_preds < 1 || n_preds > HYDRO_MAX_PREDICATES || !udfs || !thresholds)
         return fail(HYDRO_EINVAL, "a query has 1..%d predicates", HYDRO_MAX_PREDICATES);
@@ -1060,10 +1085,12 @@ hydro_status hydro_session_submit(hydro_session *s, const void *d_tuples, const 
     if (!counts || !out_step) return fail(HYDRO_EINVAL, "NULL counts or out_step");
     CU(cudaSetDevice(s->cfg.device));
     TRY(finalize(s));
-    const int Q = (int)s->queries.size();
+    const int K = s->cfg.batches_per_step, Q = (int)s->queries.size() * K;
     long long total = 0;
     for (int q = 0; q < Q; ++q) {
-        if (counts[q] < 0) return fail(HYDRO_EINVAL, "count of query %d is negative", q);
+        if (counts[q] < 0) return fail(HYDRO_EINVAL, "count of entry %d is negative", q);
+        if (q % K && counts[q] > 0 && counts[q - 1] == 0)
+            return fail(HYDRO_EINVAL, "query %d: a non-empty batch after an empty one", q / K);
         total += counts[q];
     }
     if (total > s->cfg.max_step_tuples) return fail(HYDRO_EINVAL, "step of %lld tuples > max_step_tuples", total);
@@ -1179,7 +1206,7 @@ hydro_status hydro_session_poll(hydro_session *s, int64_t step, uint32_t *pass_b
         s->dead = true;
         return fail(HYDRO_EDEVICE, "device error word 0x%x", err);
     }
-    const int Q = (int)s->queries.size();
+    const int Q = (int)s->queries.size() * s->cfg.batches_per_step;
     int total = 0;
     CU(cudaMemcpy(&total, slot->total, sizeof(int), cudaMemcpyDeviceToHost));
     if (pass_bitmap && total > 0)
@@ -1202,7 +1229,7 @@ hydro_status hydro_session_poll(hydro_session *s, int64_t step, uint32_t *pass_b
             o.batch = bidx[q];
             o.warmup = evall[q];
             for (int k = 0; k < HYDRO_MAX_PREDICATES; ++k) {
-                const bool used = k < s->queries[q].P;
+                const bool used = k < s->queries[q / s->cfg.batches_per_step].P;
                 o.order[k] = used ? order[(size_t)q * kMqSlots + k] : -1;
                 const StatRow &r = rows[(size_t)q * kMqSlots + k];
                 o.evaluated[k] = r.evaluated;

@@ -308,3 +308,69 @@ def test_session_graph_skips_empty_regions(small):
         counts[graphs] = s.profile_read()[1]
         s.close()
     assert 0 < counts[True] < counts[False]
+
+
+def run_session_multi(s, streams, chunk, K):
+    """Steps of up to K consecutive chunks per query (entry q*K + k)."""
+    import torch
+
+    import paper_2403_14902_b300 as H
+    done = [0] * len(streams)
+    out = []
+    while any(done[q] < streams[q].shape[0] for q in range(len(streams))):
+        parts, counts = [], []
+        for q, X in enumerate(streams):
+            for k in range(K):
+                lo = done[q]
+                m = max(0, min(chunk, X.shape[0] - lo))
+                parts.append(X[lo:lo + m])
+                counts.append(m)
+                done[q] += m
+        rows = np.ascontiguousarray(np.concatenate(parts))
+        sid = s.submit(torch.from_numpy(rows).cuda(), counts)
+        words, per, _ = s.poll(sid)
+        out.append((counts, H.bits_from_words(words, rows.shape[0]), per))
+    return out
+
+
+@pytest.mark.parametrize("K,lag,precision", [(2, 1, "bf16"), (3, 2, "fp32"), (2, 3, "bf16")])
+def test_session_several_batches_per_step(small, K, lag, precision):
+    """Each step holds up to K consecutive batches of every query, routed with
+    lag >= K - 1: orders, counts and pass sets equal the oracle's per-query
+    simulation with that lag."""
+    import torch
+
+    import paper_2403_14902_b300 as H
+    w, qs, th = small["w"], small["qs"], small["th"]
+    chunk = 320
+    s = H.Session(dim=w.dim, max_step_tuples=len(small["queries"]) * chunk * K, precision=precision,
+                  batches_per_step=K, lag=lag)
+    for layers in D.mq_pool_weights(w):
+        s.add_udf(layers)
+    for q in small["queries"]:
+        s.add_query(qs[q]["udfs"], th[q])
+    s.calibrate(torch.from_numpy(small["calib"]).cuda())
+    res = run_session_multi(s, small["streams"], chunk, K)
+    pool = D.mq_pool_weights(w)
+    for k, q in enumerate(small["queries"]):
+        pm = O.pass_matrix(O.udf_scores("vec", small["streams"][k], [pool[u] for u in qs[q]["udfs"]]), th[q])
+        sim = O.simulate(pm, chunk, policy="rank", costs=[O.mlp_flops(w.udfs[u]) for u in qs[q]["udfs"]], lag=lag)
+        b = 0
+        for counts, bits, per in res:
+            off = sum(counts[:k * K])
+            for j in range(K):
+                c = counts[k * K + j]
+                r = per[k * K + j]
+                if c == 0:
+                    assert r["batch"] == -1
+                    continue
+                sm = sim[b]
+                assert r["batch"] == b
+                assert np.array_equal(bits[off:off + c], sm["bits"])
+                assert r["order"] == sm["order"], (q, b, r["order"], sm["order"])
+                assert r["evaluated"] == sm["counts"].tolist()
+                assert r["passed"] == sm["passed"].tolist()
+                off += c
+                b += 1
+        assert b == len(sim)
+    s.close()

@@ -92,3 +92,37 @@ def test_learned_session_config_checks():
         s.add_query([0], [0.0])          # one query per learned session
     assert e.value.status == H.EINVAL
     s.close()
+
+
+def test_learned_session_several_batches_per_step(drift6):
+    """Four routing batches per step (lag 3): the proxy is trained after every
+    four steps (16 batches); results stay exact and prefix-consistent."""
+    import paper_2403_14902_b300 as H
+    w = drift6["w"]
+    P = len(w.udfs)
+    K = 4
+    s = H.Session(dim=w.dim, max_step_tuples=K * B, precision="bf16", learned=True, proxy_refresh=REFRESH * 2,
+                  proxy_epochs=3, proxy_lr=3e-3, batches_per_step=K, lag=K - 1)
+    for layers in D.predicate_weights(w):
+        s.add_udf(layers)
+    s.add_query(list(range(P)), drift6["th"])
+    s.calibrate(drift6["calib"])
+    sim = O.simulate(drift6["pm"], B, policy="rank", costs=model_costs(w), lag=K - 1)
+    nsteps = (NB + K - 1) // K
+    for st in range(nsteps):
+        b0 = st * K
+        counts = [B if b0 + k < NB else 0 for k in range(K)]
+        n = sum(counts)
+        sid = s.submit(drift6["Xd"][b0 * B:b0 * B + n], counts)
+        words, per, _ = s.poll(sid, total=n)
+        order, visited = s.debug_trace(sid, n)
+        bits = H.bits_from_words(words, n)
+        for k in range(K):
+            if not counts[k]:
+                continue
+            b = b0 + k
+            sl = slice(k * B, (k + 1) * B)
+            check_step(drift6["pm"][b * B:(b + 1) * B], bits[sl], per[k], order[sl], visited[sl], P)
+            if b < 2 * REFRESH:
+                assert per[k]["order"] == sim[b]["order"]
+    s.close()
