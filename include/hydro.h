@@ -130,6 +130,11 @@ typedef struct hydro_query_config {
     int32_t proxy_epochs;    /* LEARNED: passes over the last proxy_refresh batches per retrain (2) */
     float proxy_lr;          /* LEARNED: Adam learning rate (1e-3) */
     int32_t proxy_seed;      /* LEARNED: seed of the proxy's initial weights */
+    int32_t lanes;           /* 1 (default) or 2: batches alternate between two streams, each with
+                                its own scratch, so that with route_lag >= 1 batch b + 1 runs while
+                                batch b finishes (its order never waits for batch b).  The batches
+                                then run on library streams that wait for the caller's stream at
+                                each submit.  Not with embeddings or the LEARNED policy */
 } hydro_query_config;
 
 typedef struct hydro_udf_desc {

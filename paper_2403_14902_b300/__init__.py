@@ -50,7 +50,8 @@ class QueryConfig(ctypes.Structure):
                 ("warmup_batches", ctypes.c_int32), ("stats_window", ctypes.c_int32),
                 ("route_lag", ctypes.c_int32), ("max_in_flight", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("proxy_hidden", ctypes.c_int32), ("proxy_refresh", ctypes.c_int32),
-                ("proxy_epochs", ctypes.c_int32), ("proxy_lr", ctypes.c_float), ("proxy_seed", ctypes.c_int32)]
+                ("proxy_epochs", ctypes.c_int32), ("proxy_lr", ctypes.c_float), ("proxy_seed", ctypes.c_int32),
+                ("lanes", ctypes.c_int32)]
 
 
 class UdfDesc(ctypes.Structure):
@@ -197,7 +198,8 @@ class Query:
     def __init__(self, kind: str, *, dim: int = 0, frame=(3, 64, 64), max_batch: int, policy: str = "rank",
                  precision: str = "fp32", warmup: int = 1, window: int = 8, lag: int = 1,
                  max_in_flight: int = 4, device: int = 0, stream=None, proxy_hidden: int = 64,
-                 proxy_refresh: int = 16, proxy_epochs: int = 2, proxy_lr: float = 1e-3, proxy_seed: int = 1):
+                 proxy_refresh: int = 16, proxy_epochs: int = 2, proxy_lr: float = 1e-3, proxy_seed: int = 1,
+                 lanes: int = 1):
         L = load()
         cfg = QueryConfig()
         L.hydro_default_config(ctypes.byref(cfg))
@@ -218,6 +220,7 @@ class Query:
         cfg.proxy_epochs = proxy_epochs
         cfg.proxy_lr = proxy_lr
         cfg.proxy_seed = proxy_seed
+        cfg.lanes = lanes
         self.kind = kind
         self.cfg = cfg
         self._h = ctypes.c_void_p()

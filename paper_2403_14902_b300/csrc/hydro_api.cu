@@ -146,6 +146,21 @@ struct Prof {
 
 }  // namespace
 
+// Per-batch scratch of one stream lane.
+struct LaneBufs {
+    int *alive[2] = {};
+    int *ints = nullptr;
+    unsigned char *pass = nullptr, *acc = nullptr;
+    float *score32 = nullptr;
+    int *band1_m = nullptr, *band1_t = nullptr, *band2_m = nullptr, *band2_t = nullptr;
+    int *band3_m = nullptr, *band3_t = nullptr;
+    float *rscore_t = nullptr, *rscore32 = nullptr;
+    double *rscore64 = nullptr;
+    void *act[2] = {}, *ract32[2] = {}, *ract64[2] = {};
+    float *partials = nullptr;
+    __nv_bfloat16 *stage16 = nullptr, *act16[2] = {};
+};
+
 struct hydro_query {
     hydro_query_config cfg{};
     std::vector<Pred> preds;
@@ -216,6 +231,13 @@ struct hydro_query {
     // profiling and launch count
     Prof prof;
     long long launches = 0;
+    // stream lanes: batch b runs on lane b % n_lanes, each with its own scratch and stream
+    int n_lanes = 1;
+    LaneBufs lanes[2];
+    cudaStream_t lane_st[2] = {};
+    bool own_lane_st[2] = {};
+    cudaEvent_t ev_user = nullptr;   // input-ready point on the caller's stream (the batch's lane waits on it)
+    cudaStream_t home_st = nullptr;  // with two lanes: the caller's (or the library's) stream
 };
 
 namespace {
@@ -338,22 +360,9 @@ hydro_status finalize_learned(hydro_query *q) {
     return HYDRO_OK;
 }
 
-hydro_status finalize(hydro_query *q) {
-    if (q->finalized) return HYDRO_OK;
+// Per-batch scratch buffers of the current lane (the q-> fields).
+hydro_status alloc_scratch(hydro_query *q) {
     const hydro_query_config &c = q->cfg;
-    if (q->preds.empty()) return fail(HYDRO_ESTATE, "query has no predicates");
-    CU(cudaSetDevice(c.device));
-    CU(cudaDeviceGetAttribute(&q->sms, cudaDevAttrMultiProcessorCount, c.device));
-    if (c.stream) {
-        q->st = (cudaStream_t)c.stream;
-    } else {
-        CU(cudaStreamCreateWithFlags(&q->st, cudaStreamNonBlocking));
-        q->own_stream = true;
-    }
-    CU(cudaStreamCreateWithFlags(&q->rst, cudaStreamNonBlocking));
-    for (int i = 0; i < kEvRing; ++i) CU(cudaEventCreateWithFlags(&q->ev_done[i], cudaEventDisableTiming));
-    CU(cudaEventCreateWithFlags(&q->ev_route, cudaEventDisableTiming));
-
     const int B = c.max_batch;
     const bool cnn = c.tuple_kind == HYDRO_TUPLE_U8_FRAME;
     const int wmax = max_width(q);
@@ -396,6 +405,108 @@ hydro_status finalize(hydro_query *q) {
             hydro_status s = tc_gemm_init(&q->gemm_encode);
             if (s != HYDRO_OK) return fail(s, "tensor-core GEMM init failed: %s", tc_gemm_last_error());
         }
+    }
+    return HYDRO_OK;
+}
+
+void save_lane(hydro_query *q, int l) {
+    LaneBufs &L = q->lanes[l];
+    for (int k = 0; k < 2; ++k) {
+        L.alive[k] = q->alive[k];
+        L.act[k] = q->act[k];
+        L.ract32[k] = q->ract32[k];
+        L.ract64[k] = q->ract64[k];
+        L.act16[k] = q->act16[k];
+    }
+    L.ints = q->ints;
+    L.pass = q->pass;
+    L.acc = q->acc;
+    L.score32 = q->score32;
+    L.band1_m = q->band1_m;
+    L.band1_t = q->band1_t;
+    L.band2_m = q->band2_m;
+    L.band2_t = q->band2_t;
+    L.band3_m = q->band3_m;
+    L.band3_t = q->band3_t;
+    L.rscore_t = q->rscore_t;
+    L.rscore32 = q->rscore32;
+    L.rscore64 = q->rscore64;
+    L.partials = q->partials;
+    L.stage16 = q->stage16;
+}
+
+// Make lane l current: its scratch and its stream.
+void load_lane(hydro_query *q, int l) {
+    const LaneBufs &L = q->lanes[l];
+    for (int k = 0; k < 2; ++k) {
+        q->alive[k] = L.alive[k];
+        q->act[k] = L.act[k];
+        q->ract32[k] = L.ract32[k];
+        q->ract64[k] = L.ract64[k];
+        q->act16[k] = L.act16[k];
+    }
+    q->ints = L.ints;
+    q->pass = L.pass;
+    q->acc = L.acc;
+    q->score32 = L.score32;
+    q->band1_m = L.band1_m;
+    q->band1_t = L.band1_t;
+    q->band2_m = L.band2_m;
+    q->band2_t = L.band2_t;
+    q->band3_m = L.band3_m;
+    q->band3_t = L.band3_t;
+    q->rscore_t = L.rscore_t;
+    q->rscore32 = L.rscore32;
+    q->rscore64 = L.rscore64;
+    q->partials = L.partials;
+    q->stage16 = L.stage16;
+    q->st = q->lane_st[l];
+}
+
+// Every lane's work done; lane 0 current (calls that use the scratch outside batches).
+hydro_status quiesce(hydro_query *q) {
+    for (int l = 0; l < q->n_lanes; ++l)
+        if (q->lane_st[l]) CU(cudaStreamSynchronize(q->lane_st[l]));
+    if (q->n_lanes > 1) load_lane(q, 0);
+    return HYDRO_OK;
+}
+
+hydro_status finalize(hydro_query *q) {
+    if (q->finalized) return HYDRO_OK;
+    const hydro_query_config &c = q->cfg;
+    if (q->preds.empty()) return fail(HYDRO_ESTATE, "query has no predicates");
+    CU(cudaSetDevice(c.device));
+    CU(cudaDeviceGetAttribute(&q->sms, cudaDevAttrMultiProcessorCount, c.device));
+    if (c.stream) {
+        q->st = (cudaStream_t)c.stream;
+    } else {
+        CU(cudaStreamCreateWithFlags(&q->st, cudaStreamNonBlocking));
+        q->own_stream = true;
+    }
+    CU(cudaStreamCreateWithFlags(&q->rst, cudaStreamNonBlocking));
+    for (int i = 0; i < kEvRing; ++i) CU(cudaEventCreateWithFlags(&q->ev_done[i], cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&q->ev_route, cudaEventDisableTiming));
+
+    const int B = c.max_batch;
+    const bool cnn = c.tuple_kind == HYDRO_TUPLE_U8_FRAME;
+    const int wmax = max_width(q);
+    TRY(alloc_scratch(q));
+    q->lane_st[0] = q->st;
+    save_lane(q, 0);
+    q->n_lanes = c.lanes == 2 ? 2 : 1;
+    if (q->n_lanes == 2) {
+        if (!q->embs.empty() || c.policy == HYDRO_POLICY_LEARNED)
+            return fail(HYDRO_EUNSUPPORTED, "two lanes need a query without embeddings and not LEARNED");
+        TRY(alloc_scratch(q));
+        save_lane(q, 1);
+        // both lanes on library streams; each batch waits for the caller's stream (q->st)
+        for (int l = 0; l < 2; ++l) {
+            CU(cudaStreamCreateWithFlags(&q->lane_st[l], cudaStreamNonBlocking));
+            q->own_lane_st[l] = true;
+        }
+        CU(cudaEventCreateWithFlags(&q->ev_user, cudaEventDisableTiming));
+        q->home_st = q->st;
+        load_lane(q, 0);
     }
     q->ring_len = c.stats_window + c.route_lag + 4;
     TRY(dalloc(q, &q->ring, sizeof(StatRow) * kMaxPred * q->ring_len));
@@ -1093,6 +1204,8 @@ hydro_status hydro_create_query(const hydro_query_config *cfg, hydro_query **out
     if (c.warmup_batches < 0 || c.warmup_batches > 64) return fail(HYDRO_EINVAL, "warmup_batches must be 0..64");
     if (c.stats_window < 1 || c.stats_window > 1024) return fail(HYDRO_EINVAL, "stats_window must be 1..1024");
     if (c.route_lag < 0 || c.route_lag > 1) return fail(HYDRO_EINVAL, "route_lag must be 0 or 1");
+    if (c.lanes < 0 || c.lanes > 2) return fail(HYDRO_EINVAL, "lanes must be 1 or 2");
+    if (c.lanes == 2 && c.route_lag < 1) return fail(HYDRO_EINVAL, "two lanes need route_lag 1");
     if (c.max_in_flight < 1 || c.max_in_flight > 64) return fail(HYDRO_EINVAL, "max_in_flight must be 1..64");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -1223,6 +1336,7 @@ hydro_status hydro_add_embedding(hydro_query *q, const hydro_udf_desc *udf, int6
 hydro_status hydro_cache_clear(hydro_query *q, int32_t emb) {
     g_err.clear();
     TRY(check_query(q));
+    if (q->finalized) TRY(quiesce(q));
     if (emb < 1 || emb > (int)q->embs.size()) return fail(HYDRO_EINVAL, "unknown embedding id %d", emb);
     CU(cudaSetDevice(q->cfg.device));
     TRY(finalize(q));
@@ -1235,6 +1349,7 @@ hydro_status hydro_cache_prefill(hydro_query *q, int32_t emb, const void *d_tupl
                                  int64_t n) {
     g_err.clear();
     TRY(check_query(q));
+    if (q->finalized) TRY(quiesce(q));
     if (emb < 1 || emb > (int)q->embs.size()) return fail(HYDRO_EINVAL, "unknown embedding id %d", emb);
     if (n < 0 || (n > 0 && (!d_tuples || !d_ids))) return fail(HYDRO_EINVAL, "bad tuples/ids");
     CU(cudaSetDevice(q->cfg.device));
@@ -1288,6 +1403,7 @@ hydro_status hydro_udf_scores(hydro_query *q, int32_t pred, int32_t prec, const 
                               double *d_scores) {
     g_err.clear();
     TRY(check_query(q));
+    if (q->finalized) TRY(quiesce(q));
     if (pred < 0 || pred >= (int)q->preds.size()) return fail(HYDRO_EINVAL, "unknown predicate");
     if (n < 0 || (n > 0 && (!d_tuples || !d_scores))) return fail(HYDRO_EINVAL, "bad tuples/scores");
     if (prec != HYDRO_PREC_FP32 && prec != HYDRO_PREC_FP64 && prec != HYDRO_PREC_BF16 && prec != HYDRO_PREC_TF32X3)
@@ -1329,6 +1445,7 @@ hydro_status hydro_udf_scores(hydro_query *q, int32_t pred, int32_t prec, const 
 hydro_status hydro_calibrate(hydro_query *q, const void *d_tuples, int64_t n, hydro_calib_info *info) {
     g_err.clear();
     TRY(check_query(q));
+    if (q->finalized) TRY(quiesce(q));
     if (n < 1 || !d_tuples) return fail(HYDRO_EINVAL, "need calibration tuples");
     if (q->next_batch > 0) return fail(HYDRO_ESTATE, "calibrate before the first submit");
     double *d = nullptr;
@@ -1451,6 +1568,12 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
         }
     }
 
+    if (q->n_lanes > 1) {
+        // this batch's lane; it starts after the caller's work so far (its inputs)
+        load_lane(q, (int)(b % q->n_lanes));
+        CU(cudaEventRecord(q->ev_user, q->home_st));
+        CU(cudaStreamWaitEvent(q->st, q->ev_user, 0));
+    }
     slot->batch = b;
     slot->n = (int)n;
     slot->busy = true;
@@ -1568,6 +1691,7 @@ hydro_status hydro_poll_result(hydro_query *q, int64_t batch_id, uint32_t *pass_
 hydro_status hydro_debug_trace(hydro_query *q, int64_t batch_id, uint8_t *order, uint8_t *visited) {
     g_err.clear();
     TRY(check_query(q));
+    if (q->finalized) TRY(quiesce(q));
     if (q->cfg.policy != HYDRO_POLICY_LEARNED) return fail(HYDRO_EUNSUPPORTED, "trace is kept by the learned router");
     if (batch_id != q->last_learned_batch || batch_id != q->next_batch - 1)
         return fail(HYDRO_ENOTFOUND, "trace is only kept for the most recently submitted batch");
@@ -1618,6 +1742,7 @@ hydro_status hydro_profile_read(hydro_query *q, hydro_kernel_profile *out, int32
                                 int64_t *total_launches) {
     g_err.clear();
     TRY(check_query(q));
+    if (q->finalized) TRY(quiesce(q));
     if (!n_out || (max > 0 && !out)) return fail(HYDRO_EINVAL, "NULL argument");
     if (q->finalized) CU(cudaStreamSynchronize(q->st));
     double ms[PC_N] = {}, fl[PC_N] = {}, by[PC_N] = {};
@@ -1690,8 +1815,12 @@ hydro_status hydro_destroy_query(hydro_query *q) {
         }
         if (rc == HYDRO_OK) {
             cudaStreamSynchronize(q->rst);
+            for (int l = 0; l < q->n_lanes; ++l)
+                if (q->own_lane_st[l]) cudaStreamSynchronize(q->lane_st[l]);
+            if (q->n_lanes > 1) q->st = q->home_st;
             if (q->own_stream) cudaStreamSynchronize(q->st);
         }
+        if (q->n_lanes > 1) q->st = q->home_st;
         tc_conv_destroy(&q->tc);
         for (cudaEvent_t e : q->prof.ev) cudaEventDestroy(e);
         for (Slot &s : q->slots) {
@@ -1705,6 +1834,9 @@ hydro_status hydro_destroy_query(hydro_query *q) {
         for (int i = 0; i < kEvRing; ++i)
             if (q->ev_done[i]) cudaEventDestroy(q->ev_done[i]);
         if (q->ev_route) cudaEventDestroy(q->ev_route);
+        if (q->ev_user) cudaEventDestroy(q->ev_user);
+        for (int l = 0; l < 2; ++l)
+            if (q->own_lane_st[l] && q->lane_st[l]) cudaStreamDestroy(q->lane_st[l]);
         if (q->rst) cudaStreamDestroy(q->rst);
         if (q->own_stream && q->st) cudaStreamDestroy(q->st);
         cudaGetLastError();

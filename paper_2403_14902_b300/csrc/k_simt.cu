@@ -337,18 +337,21 @@ k_conv3x3_simt(const int *count, const Tin *in, int Cin, int H, int Wd, const Tw
 
 // Global average pool + linear head: score[m] = hb + sum_c hw[c] * mean_p act[m][p][c].
 // One block per frame; fixed-order partial sums (deterministic).
+constexpr int kPoolThreads = 1024;   // per frame: C channels x (1024 / C) pixel groups
+
 template <typename Tin, typename T, typename S>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kPoolThreads)
 k_pool_head(const int *count, const Tin *act, int HW, int C, const float *hw, double hb, S *score) {
-    __shared__ T part[256];
+    __shared__ T part[kPoolThreads];
     __shared__ T pooled[256];
     const int M = *count;
-    const int groups = 256 / C;
+    const int groups = kPoolThreads / C;
     const int c = threadIdx.x % C, g = threadIdx.x / C;
     for (int m = blockIdx.x; m < M; m += gridDim.x) {
         const Tin *a = act + (size_t)m * HW * C;
         T s = (T)0;
         if (g < groups)
+#pragma unroll 8
             for (int p = g; p < HW; p += groups) s += ld_as<T>(a + (size_t)p * C + c);
         part[threadIdx.x] = s;
         __syncthreads();
@@ -482,17 +485,17 @@ void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, in
 
 void launch_pool_head(int prec, const int *count, const void *act, int HW, int C, const float *hw, double hb,
                       void *score, int max_frames, int sms, cudaStream_t st) {
-    int grid = max_frames < grid_for(sms, 8) ? max_frames : grid_for(sms, 8);
+    int grid = max_frames < grid_for(sms, 2) ? max_frames : grid_for(sms, 2);
     if (grid < 1) grid = 1;
     if (prec == PREC_F64)
-        k_pool_head<double, double, double><<<grid, 256, 0, st>>>(count, (const double *)act, HW, C, hw, hb,
-                                                                  (double *)score);
+        k_pool_head<double, double, double><<<grid, kPoolThreads, 0, st>>>(count, (const double *)act, HW, C, hw, hb,
+                                                                           (double *)score);
     else if (prec == PREC_F32)
-        k_pool_head<float, float, float><<<grid, 256, 0, st>>>(count, (const float *)act, HW, C, hw, hb,
-                                                               (float *)score);
+        k_pool_head<float, float, float><<<grid, kPoolThreads, 0, st>>>(count, (const float *)act, HW, C, hw, hb,
+                                                                        (float *)score);
     else
-        k_pool_head<__nv_bfloat16, float, float><<<grid, 256, 0, st>>>(count, (const __nv_bfloat16 *)act, HW,
-                                                                       C, hw, hb, (float *)score);
+        k_pool_head<__nv_bfloat16, float, float><<<grid, kPoolThreads, 0, st>>>(count, (const __nv_bfloat16 *)act,
+                                                                                HW, C, hw, hb, (float *)score);
 }
 
 }  // namespace hydro

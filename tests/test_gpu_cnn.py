@@ -134,3 +134,27 @@ def test_full_stream_sampled_parity_bf16():
             assert counts[order[k + 1]] == info["passed"][order[k]]
         assert info["passed"][order[-1]] == int(bb.sum()) == info["n_pass"]
     q.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp32"])
+def test_two_lanes_match_one_lane_and_oracle(cnn4, precision):
+    """Batches alternating between two stream lanes (route lag 1): the same
+    orders, counts and pass sets as the oracle's simulation."""
+    import paper_2403_14902_b300 as H
+    w = cnn4["w"]
+    q = H.Query("frame", frame=w.frame, max_batch=B_SMALL, policy="rank", precision=precision, lanes=2,
+                max_in_flight=4)
+    for i, udf in enumerate(D.predicate_weights(w)):
+        q.add_cnn(udf, cnn4["th"][i])
+    if precision == "bf16":
+        q.calibrate(cnn4["calib_d"])
+    res = run_stream(q, cnn4["Fd"], B_SMALL, max_in_flight=4)
+    check_against_oracle(res, cnn4["pm"], B_SMALL, policy="rank", costs=model_costs(w))
+    q.close()
+
+
+def test_two_lanes_need_route_lag():
+    import paper_2403_14902_b300 as H
+    with pytest.raises(H.HydroError) as e:
+        H.Query("frame", frame=(3, 64, 64), max_batch=8, lanes=2, lag=0)
+    assert e.value.status == H.EINVAL

@@ -146,3 +146,18 @@ def test_api_errors_on_device(mlp3):
         q.add_mlp(D.predicate_weights(w)[0], 0.0)   # after the first submit
     assert e.value.status == H.ESTATE
     q.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_two_lanes_exact(mlp3, precision):
+    import torch
+
+    import paper_2403_14902_b300 as H
+    w = mlp3["w"]
+    q = H.Query("vec", dim=w.dim, max_batch=w.batch, policy="rank", precision=precision, lanes=2, max_in_flight=4)
+    for i, layers in enumerate(D.predicate_weights(w)):
+        q.add_mlp(layers, mlp3["th"][i])
+    q.calibrate(torch.from_numpy(D.calib_tuples(w)).cuda())
+    res = run_stream(q, mlp3["Xd"], w.batch, max_in_flight=4)
+    check_against_oracle(res, mlp3["pm"], w.batch, policy="rank", costs=model_costs(w))
+    q.close()
