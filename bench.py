@@ -165,10 +165,10 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- our arm
 
-def build_query(H, w, th, *, policy, precision, stream, max_in_flight=8, lanes=2):
-    """Two stream lanes: batch b + 1 runs while batch b finishes (route lag 1)."""
+def build_query(H, w, th, *, policy, precision, stream, max_in_flight=8, lanes=2, lag=1):
+    """Stream lanes: up to `lanes` consecutive batches run at once (route lag >= lanes - 1)."""
     q = H.Query(w.kind, frame=w.frame, max_batch=w.batch, policy=policy, precision=precision,
-                max_in_flight=max_in_flight, stream=stream, lanes=lanes)
+                max_in_flight=max_in_flight, stream=stream, lanes=lanes, lag=lag)
     for i, udf in enumerate(D.predicate_weights(w)):
         q.add_cnn(udf, th[i])
     return q
@@ -613,7 +613,8 @@ def ours(args):
     X = Xh.cuda()
     stream = torch.cuda.Stream()
     mif = 8
-    q = build_query(H, w, th, policy="rank", precision="bf16", stream=stream, max_in_flight=mif)
+    q = build_query(H, w, th, policy="rank", precision="bf16", stream=stream, max_in_flight=mif, lanes=args.lanes,
+                    lag=args.lag)
     calib = q.calibrate(torch.from_numpy(D.calib_tuples(w)[:64]).cuda())
     step = lambda: run_step(q, X, w.batch, mif)  # noqa: E731
     for _ in range(args.warmup):
@@ -640,7 +641,8 @@ def ours(args):
     q.close()
 
     # static-order FP32 baseline (declared order, the paper's "No Reordering")
-    qs = build_query(H, w, th, policy="static", precision="fp32", stream=stream, max_in_flight=mif)
+    qs = build_query(H, w, th, policy="static", precision="fp32", stream=stream, max_in_flight=mif,
+                     lanes=args.lanes, lag=args.lag)
     qs.calibrate(torch.from_numpy(D.calib_tuples(w)[:16]).cuda())
     sstep = lambda: run_step(qs, X, w.batch, mif)  # noqa: E731
     sstep()
@@ -681,6 +683,7 @@ def ours(args):
                                f"layers, 32-128 ch), selectivities 0.3/0.6/0.1/0.9, batches of {w.batch}, rank "
                                "c/(1-s) routing, BF16 tensor cores + FP32/FP64 recheck within 0.02",
                    "global_batch": w.n, "routing_batch": w.batch, "parallelism": f"replicas{ws}",
+                   "lanes": args.lanes, "route_lag": args.lag,
                    "l2": "inputs 805 MB > 126 MB L2, no flush"},
         "roofline": roof,
         "cpu_baseline": cpu_baseline(w, th),
@@ -1111,6 +1114,8 @@ def main(argv=None):
     ap.add_argument("--headline-only", action="store_true",
                     help="mq64: time the headline variant only (for profiling runs)")
     ap.add_argument("--no-graphs", action="store_true", help="with --headline-only: launch without CUDA graphs")
+    ap.add_argument("--lanes", type=int, default=4, help="cnn4: stream lanes of the query (1..4)")
+    ap.add_argument("--lag", type=int, default=3, help="cnn4: route lag (>= lanes - 1)")
     ap.add_argument("--workload", choices=["cnn4", "drift5", "drift6", "mq64", "gemm_bf16"], default=WORKLOAD)
     args = ap.parse_args(argv)
     if args.impl == "reference":

@@ -146,6 +146,8 @@ struct Prof {
 
 }  // namespace
 
+constexpr int kMaxLanes = 4;
+
 // Per-batch scratch of one stream lane.
 struct LaneBufs {
     int *alive[2] = {};
@@ -233,9 +235,9 @@ struct hydro_query {
     long long launches = 0;
     // stream lanes: batch b runs on lane b % n_lanes, each with its own scratch and stream
     int n_lanes = 1;
-    LaneBufs lanes[2];
-    cudaStream_t lane_st[2] = {};
-    bool own_lane_st[2] = {};
+    LaneBufs lanes[kMaxLanes];
+    cudaStream_t lane_st[kMaxLanes] = {};
+    bool own_lane_st[kMaxLanes] = {};
     cudaEvent_t ev_user = nullptr;   // input-ready point on the caller's stream (the batch's lane waits on it)
     cudaStream_t home_st = nullptr;  // with two lanes: the caller's (or the library's) stream
 };
@@ -493,14 +495,16 @@ hydro_status finalize(hydro_query *q) {
     TRY(alloc_scratch(q));
     q->lane_st[0] = q->st;
     save_lane(q, 0);
-    q->n_lanes = c.lanes == 2 ? 2 : 1;
-    if (q->n_lanes == 2) {
+    q->n_lanes = std::max(1, c.lanes);
+    if (q->n_lanes > 1) {
         if (!q->embs.empty() || c.policy == HYDRO_POLICY_LEARNED)
-            return fail(HYDRO_EUNSUPPORTED, "two lanes need a query without embeddings and not LEARNED");
-        TRY(alloc_scratch(q));
-        save_lane(q, 1);
-        // both lanes on library streams; each batch waits for the caller's stream (q->st)
-        for (int l = 0; l < 2; ++l) {
+            return fail(HYDRO_EUNSUPPORTED, "lanes need a query without embeddings and not LEARNED");
+        for (int l = 1; l < q->n_lanes; ++l) {
+            TRY(alloc_scratch(q));
+            save_lane(q, l);
+        }
+        // every lane on a library stream; each batch waits for the caller's stream (q->st)
+        for (int l = 0; l < q->n_lanes; ++l) {
             CU(cudaStreamCreateWithFlags(&q->lane_st[l], cudaStreamNonBlocking));
             q->own_lane_st[l] = true;
         }
@@ -1203,9 +1207,9 @@ hydro_status hydro_create_query(const hydro_query_config *cfg, hydro_query **out
         return fail(HYDRO_EUNSUPPORTED, "only HYDRO_COST_MODEL is built");
     if (c.warmup_batches < 0 || c.warmup_batches > 64) return fail(HYDRO_EINVAL, "warmup_batches must be 0..64");
     if (c.stats_window < 1 || c.stats_window > 1024) return fail(HYDRO_EINVAL, "stats_window must be 1..1024");
-    if (c.route_lag < 0 || c.route_lag > 1) return fail(HYDRO_EINVAL, "route_lag must be 0 or 1");
-    if (c.lanes < 0 || c.lanes > 2) return fail(HYDRO_EINVAL, "lanes must be 1 or 2");
-    if (c.lanes == 2 && c.route_lag < 1) return fail(HYDRO_EINVAL, "two lanes need route_lag 1");
+    if (c.route_lag < 0 || c.route_lag > 3) return fail(HYDRO_EINVAL, "route_lag must be 0..3");
+    if (c.lanes < 0 || c.lanes > kMaxLanes) return fail(HYDRO_EINVAL, "lanes must be 1..%d", kMaxLanes);
+    if (c.lanes > c.route_lag + 1) return fail(HYDRO_EINVAL, "lanes must be <= route_lag + 1");
     if (c.max_in_flight < 1 || c.max_in_flight > 64) return fail(HYDRO_EINVAL, "max_in_flight must be 1..64");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -1835,7 +1839,7 @@ hydro_status hydro_destroy_query(hydro_query *q) {
             if (q->ev_done[i]) cudaEventDestroy(q->ev_done[i]);
         if (q->ev_route) cudaEventDestroy(q->ev_route);
         if (q->ev_user) cudaEventDestroy(q->ev_user);
-        for (int l = 0; l < 2; ++l)
+        for (int l = 0; l < kMaxLanes; ++l)
             if (q->own_lane_st[l] && q->lane_st[l]) cudaStreamDestroy(q->lane_st[l]);
         if (q->rst) cudaStreamDestroy(q->rst);
         if (q->own_stream && q->st) cudaStreamDestroy(q->st);

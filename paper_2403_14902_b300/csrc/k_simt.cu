@@ -297,31 +297,42 @@ k_conv3x3_simt(const int *count, const Tin *in, int Cin, int H, int Wd, const Tw
         for (int i = 0; i < 8; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
-        for (int tap = 0; tap < 9; ++tap) {
+        // K steps (tap, 16 input channels); the next step's operands are loaded
+        // into registers while this step's multiply-adds run (latency hiding)
+        const int csteps = Cin / 16, nsteps = 9 * csteps;
+        T ra[8], rw[4];
+        auto fetch = [&](int s) {
+            const int tap = s / csteps, ci0 = (s % csteps) * 16;
             const int yy = ay + tap / 3 - 1, xx = ax + tap % 3 - 1;
             const bool inb = yy >= 0 && yy < H && xx >= 0 && xx < Wd;
-            const Tin *src = fin + ((size_t)yy * Wd + xx) * Cin;
-            for (int ci0 = 0; ci0 < Cin; ci0 += 16) {
+            const Tin *src = fin + ((size_t)(inb ? yy : 0) * Wd + (inb ? xx : 0)) * Cin + ci0 + ach;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) As[ach + e][apx] = inb ? ld_as<T>(src + ci0 + ach + e) : (T)0;
-                const Tw *wsrc = Wt + ((size_t)tap * Cin + ci0 + bk) * Cout + co0 + bn;
+            for (int e = 0; e < 8; ++e) ra[e] = inb ? ld_as<T>(src + e) : (T)0;
+            const Tw *wsrc = Wt + ((size_t)tap * Cin + ci0 + bk) * Cout + co0 + bn;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) Bs[bk][bn + e] = ld_as<T>(wsrc + e);
-                __syncthreads();
+            for (int e = 0; e < 4; ++e) rw[e] = ld_as<T>(wsrc + e);
+        };
+        fetch(0);
+        for (int s = 0; s < nsteps; ++s) {
 #pragma unroll
-                for (int kk = 0; kk < 16; ++kk) {
-                    T a[8], w[4];
+            for (int e = 0; e < 8; ++e) As[ach + e][apx] = ra[e];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) a[i] = As[kk][ty * 8 + i];
+            for (int e = 0; e < 4; ++e) Bs[bk][bn + e] = rw[e];
+            __syncthreads();
+            if (s + 1 < nsteps) fetch(s + 1);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) w[j] = Bs[kk][tx * 4 + j];
+            for (int kk = 0; kk < 16; ++kk) {
+                T a[8], w[4];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < 8; ++i) a[i] = As[kk][ty * 8 + i];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * w[j];
-                }
-                __syncthreads();
+                for (int j = 0; j < 4; ++j) w[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * w[j];
             }
+            __syncthreads();
         }
         Tout *o = out + ((size_t)m * HW + p0 + ty * 8) * Cout + co0 + tx * 4;
 #pragma unroll

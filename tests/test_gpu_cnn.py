@@ -136,20 +136,20 @@ def test_full_stream_sampled_parity_bf16():
     q.close()
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp32"])
-def test_two_lanes_match_one_lane_and_oracle(cnn4, precision):
-    """Batches alternating between two stream lanes (route lag 1): the same
-    orders, counts and pass sets as the oracle's simulation."""
+@pytest.mark.parametrize("precision,lanes,lag", [("bf16", 2, 1), ("fp32", 2, 1), ("bf16", 3, 2), ("bf16", 4, 3)])
+def test_lanes_match_oracle(cnn4, precision, lanes, lag):
+    """Batches on `lanes` stream lanes (route lag `lag`): the same orders,
+    counts and pass sets as the oracle's simulation with that lag."""
     import paper_2403_14902_b300 as H
     w = cnn4["w"]
-    q = H.Query("frame", frame=w.frame, max_batch=B_SMALL, policy="rank", precision=precision, lanes=2,
-                max_in_flight=4)
+    q = H.Query("frame", frame=w.frame, max_batch=B_SMALL, policy="rank", precision=precision, lanes=lanes,
+                lag=lag, max_in_flight=4)
     for i, udf in enumerate(D.predicate_weights(w)):
         q.add_cnn(udf, cnn4["th"][i])
     if precision == "bf16":
         q.calibrate(cnn4["calib_d"])
     res = run_stream(q, cnn4["Fd"], B_SMALL, max_in_flight=4)
-    check_against_oracle(res, cnn4["pm"], B_SMALL, policy="rank", costs=model_costs(w))
+    check_against_oracle(res, cnn4["pm"], B_SMALL, policy="rank", costs=model_costs(w), lag=lag)
     q.close()
 
 
