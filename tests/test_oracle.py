@@ -254,6 +254,18 @@ def test_simulate_hand_worked_trace():
         assert b["bits"].tolist() == [False, True, False, False]
 
 
+def test_simulate_longer_lag_hand_worked():
+    # the trace above with lag 3: batches 1..3 see no finished batch (declared
+    # order); batch 4 sees batch 0 only -> order 1,0; batch 5 sees 0..1
+    pm = np.array([[1, 0], [1, 1], [1, 0], [0, 0]] * 6, bool)
+    sim = O.simulate(pm, batch=4, policy="rank", costs=[10, 10], warmup=1, window=8, lag=3)
+    assert [b["order"] for b in sim[1:4]] == [[0, 1]] * 3
+    assert all(b["counts"].tolist() == [4, 3] for b in sim[1:4])
+    assert sim[4]["order"] == [1, 0] and sim[4]["counts"].tolist() == [1, 4]
+    # batch 5: window = batches 0, 1: e0 = 8, p0 = 6, e1 = 7, p1 = 2 -> 10 * 10/3 > 10 * 9/6 -> 1,0
+    assert sim[5]["order"] == [1, 0]
+
+
 def test_simulate_window_and_fallback_to_warmup_stats():
     # predicate 1 is last and never reached after batch 1 -> its window count
     # is zero and the warmup statistics stand in
