@@ -503,10 +503,12 @@ def ours_drift6(args):
         for item in pending:
             drain(item)
         return npass
-    for name, learned, precision, K in [("learned_session_bf16", True, "bf16", 4),
+    DK = 8   # routing batches per step of the session arms (route lag DK - 1)
+    for name, learned, precision, K in [("learned_session_bf16", True, "bf16", DK),
+                                        ("learned_session_bf16_k4", True, "bf16", 4),
                                         ("learned_session_bf16_k1", True, "bf16", 1),
-                                        ("rank_session_bf16", False, "bf16", 4),
-                                        ("learned_session_fp32", True, "fp32", 4)]:
+                                        ("rank_session_bf16", False, "bf16", DK),
+                                        ("learned_session_fp32", True, "fp32", DK)]:
         s = session(learned, precision, K)
         f = lambda: run_session(s)  # noqa: E731
         for _ in range(args.warmup):
@@ -528,7 +530,7 @@ def ours_drift6(args):
             entry["prof"], _ = s.profile_read()
             s.profile(False)
             Xp = Xh.pin_memory()
-            buf = [torch.empty((4 * w.batch, w.dim), dtype=torch.float32, device="cuda") for _ in range(2)]
+            buf = [torch.empty((s.K * w.batch, w.dim), dtype=torch.float32, device="cuda") for _ in range(2)]
 
             def host_run():
                 pending, k = [], 0
@@ -578,8 +580,8 @@ def ours_drift6(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"drift6: {w.n} x 512 fp32 tuples, 8 Dirichlet(0.5) drift segments, 6 MLP "
                                "predicates 512-h-1 (cost 1:2:4:8:16:32), learned 512-64-6 proxy picks per-tuple "
-                               f"orders (trained every 16 batches), batches of {w.batch}, one-query session with 4 "
-                               "batches per step (route lag 3): BF16 tensor cores + split-BF16/FP32/FP64 recheck, "
+                               f"orders (trained every 16 batches), batches of {w.batch}, one-query session with {DK} "
+                               f"batches per step (route lag {DK - 1}): BF16 tensor cores + split-BF16/FP32/FP64 recheck, "
                                "CUDA graphs",
                    "global_batch": w.n, "routing_batch": w.batch, "parallelism": f"replicas{ws}",
                    "l2": "inputs 2 GiB > 126 MB L2, no flush"},
@@ -798,8 +800,9 @@ def ours_mq64(args):
     results = {}
     # headline: BF16, graphs, four batches of every query per step (route lag 3)
     HEAD, HK = "bf16_graphs_k4", 4
-    variants = [(HEAD, "bf16", True, HK), ("bf16_graphs_k2", "bf16", True, 2), ("bf16_graphs_k1", "bf16", True, 1),
-                ("fp32_graphs_k1", "fp32", True, 1), ("bf16_no_graphs_k1", "bf16", False, 1)]
+    variants = [(HEAD, "bf16", True, HK), ("fp8_graphs_k4", "fp8", True, 4), ("bf16_graphs_k2", "bf16", True, 2),
+                ("bf16_graphs_k1", "bf16", True, 1), ("fp32_graphs_k1", "fp32", True, 1),
+                ("bf16_no_graphs_k1", "bf16", False, 1)]
     if args.headline_only:
         # profilers cannot see kernels inside graphs with conditional nodes: launch kernel by kernel
         variants = [(HEAD, "bf16", not args.no_graphs, HK)]
@@ -818,6 +821,12 @@ def ours_mq64(args):
         entry = {"value": aggregate(total, args.steps, secs, ws), "ms_per_step": secs / args.steps * 1000.0,
                  "pass_count": int(npass[0])}
         _, entry["launches"] = s.profile_read()
+        if precision == "fp8":
+            # level sizes: FP8/BF16 level 0, BF16 level 1 (FP8 set), FP32, FP64
+            stats = []
+            run_all(s, stats=stats)
+            for key in ("evaluated", "recheck_split", "recheck_fp32", "recheck_fp64"):
+                entry[key] = sum(sum(r[key]) for per in stats for r in per)
         if name == HEAD and args.headline_only:
             entry["clocks"] = clocks.stop()
         elif name == HEAD:
@@ -957,6 +966,9 @@ def ours_mq64(args):
         "pass_count_per_step": a["pass_count"],
         "recheck": {"evaluated": a["evaluated"], "split_bf16": a["recheck_split"], "fp32": a["recheck_fp32"],
                     "fp64": a["recheck_fp64"]},
+        "recheck_fp8_session": {k: results["fp8_graphs_k4"].get(v) for k, v in
+                                (("evaluated", "evaluated"), ("bf16", "recheck_split"), ("fp32", "recheck_fp32"),
+                                 ("fp64", "recheck_fp64"))} if "fp8_graphs_k4" in results else None,
         "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3)} for k, v in a["prof"].items()},
         "tuning": [{"udf": t["udf"], "layer": t["layer"], "K": t["K"], "N": t["N"], "tile_n": t["tile_n"],
                     "us": [round(x, 2) for x in t["us"]]} for t in a["tuning"]],

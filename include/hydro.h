@@ -88,11 +88,19 @@ enum {
     HYDRO_PREC_TF32X3 = 3, /* FP32-accurate 3xTF32 on the tensor cores (hi*hi + hi*lo + lo*hi);
                               the first BF16 recheck level of CNN UDFs (hydro_udf_scores on
                               BF16 CNN queries) */
-    HYDRO_PREC_BF16X3 = 4  /* split BF16 on the tensor cores: x = hi + lo with hi = bf16(x),
+    HYDRO_PREC_BF16X3 = 4, /* split BF16 on the tensor cores: x = hi + lo with hi = bf16(x),
                               lo = bf16(x - hi), products hi*hi + hi*lo + lo*hi in one BF16 GEMM
                               over [hi | hi | lo] x [W_hi | W_lo | W_hi] (about 16 significant bits);
                               the first recheck level of BF16 sessions
                               (hydro_session_udf_scores) */
+    HYDRO_PREC_FP8 = 5     /* sessions only: the first layer of every pool UDF in the FP8 set
+                              (first hidden width >= fp8_min_width) runs with E4M3 operands on
+                              the tensor cores (kind::f8f6f4, FP32 accumulation): weights scaled
+                              per output channel (max |w| / 448), each tuple row scaled by its
+                              own max |x| / 448; its other layers and the other UDFs run in
+                              BF16.  Scores within margin_lowp go to a BF16 level (FP8 set) or
+                              straight to FP32 (the others), then FP32 -> FP64 as in BF16
+                              sessions */
 };
 
 /* Where the router's per-tuple cost comes from. */
@@ -375,8 +383,9 @@ typedef struct hydro_session hydro_session;
 typedef struct hydro_session_config {
     int32_t dim;              /* features per fp32 tuple row; a multiple of 64 */
     int32_t max_step_tuples;  /* largest sum of counts one step may pass, 1..4194304 */
-    int32_t precision;        /* HYDRO_PREC_FP32 or HYDRO_PREC_BF16 (tensor cores, pool UDFs
-                                 whose widths are multiples of 64) */
+    int32_t precision;        /* HYDRO_PREC_FP32, HYDRO_PREC_BF16 (tensor cores, pool UDFs
+                                 whose widths are multiples of 64) or HYDRO_PREC_FP8 (as BF16,
+                                 dim a multiple of 128) */
     int32_t warmup_batches;   /* per query, as in hydro_query_config */
     int32_t stats_window;     /* per query, W >= 1 */
     int32_t use_graphs;       /* 1: each in-flight slot replays its step from a CUDA graph
@@ -404,6 +413,8 @@ typedef struct hydro_session_config {
     int32_t route_lag;        /* a query's batch b is routed on its batches <= b - 1 - route_lag
                                  (Sec. 4.1 with a lag, as hydro_query_config.route_lag); must be
                                  >= K - 1 so that every batch of a step sees only earlier steps */
+    int32_t fp8_min_width;    /* HYDRO_PREC_FP8: pool UDFs whose first hidden layer has at least
+                                 this many outputs form the FP8 set (0: 1024) */
 } hydro_session_config;
 
 /* Per query result of one step (hydro_session_poll). */
@@ -415,7 +426,8 @@ typedef struct hydro_step_query {
     int32_t order[HYDRO_MAX_PREDICATES];         /* slots in evaluation order (first n_preds) */
     int64_t evaluated[HYDRO_MAX_PREDICATES];     /* per slot: tuples evaluated at working precision */
     int64_t passed[HYDRO_MAX_PREDICATES];        /* per slot: of those, passed */
-    int64_t recheck_split[HYDRO_MAX_PREDICATES]; /* per slot: re-evaluated in split BF16 (BF16 sessions) */
+    int64_t recheck_split[HYDRO_MAX_PREDICATES]; /* per slot: re-evaluated at level 1 (split BF16 in BF16
+                                                    sessions, BF16 in FP8 sessions) */
     int64_t recheck_fp32[HYDRO_MAX_PREDICATES];  /* per slot: re-evaluated in FP32 (BF16 sessions) */
     int64_t recheck_fp64[HYDRO_MAX_PREDICATES];  /* per slot: re-evaluated in FP64 */
 } hydro_step_query;
@@ -449,22 +461,29 @@ HYDRO_API hydro_status hydro_session_add_query(hydro_session *s, int32_t n_preds
 
 /* Margins of pool UDF udf (absolute score units, >= 0): a score within its
  * level's margin of a threshold is re-evaluated at the next level (BF16
- * sessions: BF16 -> split BF16 -> FP32 -> FP64; FP32 sessions: FP32 -> FP64).
- * Defaults: margin_lowp 0.02, margin_split 1e-3, margin_fp32 1e-5.  Before
- * the first submit. */
+ * sessions: BF16 -> split BF16 -> FP32 -> FP64; FP8 sessions: FP8 -> BF16 ->
+ * FP32 -> FP64 for the FP8 set, BF16 -> FP32 -> FP64 for the others, so
+ * margin_split is the BF16 level's margin there; FP32 sessions: FP32 ->
+ * FP64).  Defaults: margin_lowp 0.02, margin_split 1e-3, margin_fp32 1e-5.
+ * Before the first submit. */
 HYDRO_API hydro_status hydro_session_set_margins(hydro_session *s, int32_t udf, double margin_lowp,
                                                  double margin_split, double margin_fp32);
 
 /* Calibrate every pool UDF's margins on n device tuples, with the rule of
  * hydro_calibrate (margin_fp32 = 16 x max FP32 error, margin_split = 8 x max
  * split-BF16 error, each at least 1e-9 x max |score|; margin_lowp raised to
- * 4 x max BF16 error).  info[n_udfs] nullable (max_err_tf32 / margin_tf32
- * report the split-BF16 level).  Synchronous. */
+ * 4 x max BF16 error).  FP8 sessions: margin_lowp raised to 4 x the max
+ * error of the level-0 scores (HYDRO_PREC_FP8), margin_split = 4 x max BF16
+ * error (at least 1e-9 x max |score|).  info[n_udfs] nullable (max_err_tf32
+ * / margin_tf32 report level 1: split BF16, or BF16 in FP8 sessions).
+ * Synchronous. */
 HYDRO_API hydro_status hydro_session_calibrate(hydro_session *s, const void *d_tuples, int64_t n,
                                                hydro_calib_info *info);
 
 /* Scores of pool UDF udf on n device tuples at HYDRO_PREC_FP64/FP32/BF16/
- * BF16X3 into d_scores (device, n doubles).  Synchronous. */
+ * BF16X3, or FP8 (an FP8 session's level-0 scores: FP8 first layer for the
+ * FP8 set, BF16 for the others) into d_scores (device, n doubles).
+ * Synchronous. */
 HYDRO_API hydro_status hydro_session_udf_scores(hydro_session *s, int32_t udf, int32_t prec, const void *d_tuples,
                                                 int64_t n, double *d_scores);
 

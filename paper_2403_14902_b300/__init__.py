@@ -26,7 +26,7 @@ OK, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEOUT, ESTATE, EDEVICE, ENOTFOUND, EUNSUPP
 
 TUPLE_F32, TUPLE_U8_FRAME = 0, 1
 POLICIES = {"rank": 0, "static": 1, "all": 2, "cost": 3, "selectivity": 4, "learned": 5}
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp64": 2, "tf32x3": 3, "bf16x3": 4}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp64": 2, "tf32x3": 3, "bf16x3": 4, "fp8": 5}
 UDF_MLP, UDF_CNN = 0, 1
 
 EXPORTED = ["hydro_default_config", "hydro_create_query", "hydro_add_predicate", "hydro_add_embedding",
@@ -91,7 +91,8 @@ class SessionConfig(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("max_in_flight", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("learned", ctypes.c_int32), ("proxy_hidden", ctypes.c_int32),
                 ("proxy_refresh", ctypes.c_int32), ("proxy_epochs", ctypes.c_int32), ("proxy_lr", ctypes.c_float),
-                ("proxy_seed", ctypes.c_int32), ("batches_per_step", ctypes.c_int32), ("route_lag", ctypes.c_int32)]
+                ("proxy_seed", ctypes.c_int32), ("batches_per_step", ctypes.c_int32), ("route_lag", ctypes.c_int32),
+                ("fp8_min_width", ctypes.c_int32)]
 
 
 class StepQuery(ctypes.Structure):
@@ -419,7 +420,7 @@ class Session:
                  window: int = 8, graphs: bool = True, autotune: bool = True, max_in_flight: int = 2,
                  device: int = 0, stream=None, learned: bool = False, proxy_hidden: int = 64,
                  proxy_refresh: int = 16, proxy_epochs: int = 1, proxy_lr: float = 1e-3, proxy_seed: int = 1,
-                 batches_per_step: int = 1, lag: int = 0):
+                 batches_per_step: int = 1, lag: int = 0, fp8_min_width: int = 0):
         L = load()
         cfg = SessionConfig()
         L.hydro_session_default_config(ctypes.byref(cfg))
@@ -441,6 +442,7 @@ class Session:
         cfg.proxy_seed = proxy_seed
         cfg.batches_per_step = batches_per_step
         cfg.route_lag = lag
+        cfg.fp8_min_width = fp8_min_width
         self.K = batches_per_step
         self._h = ctypes.c_void_p()
         _check(L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(self._h)), "hydro_session_create")

@@ -318,8 +318,11 @@ __global__ void __launch_bounds__(256) k_mq_classify(MqDev d, int r, int in, int
         StatRow *row = d.rows + q * kMqSlots + slot;
         if (in == LV_MAIN) warp_count(ctr(row, F_EVAL), live);
         warp_count(ctr(row, F_PASS), live && pass);
-        const int pos = warp_append(live && inband ? &next_cnt[g] : nullptr, live && inband);
-        if (live && inband) next_list[(size_t)g * d.cap + pos] = e;
+        // level-0 entries of groups that skip level 1 go to the FP32 level
+        const bool direct = in == LV_MAIN && ((d.lv1_skip >> g) & 1u);
+        const int pos = warp_append(live && inband ? (direct ? &d.rc->n[LV_F32][g] : &next_cnt[g]) : nullptr,
+                                    live && inband);
+        if (live && inband) (direct ? d.list[LV_F32] : next_list)[(size_t)g * d.cap + pos] = e;
         if (rfield >= 0) warp_count(ctr(row, rfield), live && !skipped);
     }
     if (next.flag && last_block(&d.rc->ticket[in]) && threadIdx.x == 0) {

@@ -25,6 +25,9 @@ struct StepHdr {
 // Precision levels of a round.  Every entry of a level's lists is decided
 // there or sent to the next level's list of the same group.
 //   BF16 sessions: 0 BF16 -> 1 split BF16 (tensor cores) -> 2 FP32 -> 3 FP64
+//   FP8 sessions:  0 FP8 first layer (UDFs in the FP8 set) or BF16 (the
+//                  others) -> 1 BF16 (FP8 set only; the others skip to 2)
+//                  -> 2 FP32 -> 3 FP64
 //   FP32 sessions: 0 FP32 -> 3 FP64
 enum { LV_MAIN = 0, LV_X3 = 1, LV_F32 = 2, LV_F64 = 3, LV_N = 4 };
 
@@ -81,6 +84,7 @@ struct MqDev {
     unsigned int *err;
     int *gates;                    // [kMqGates] condition values of the step (0 unless set)
     unsigned char *order_t;        // learned sessions: [cap][8] slot order of each tuple (else nullptr)
+    unsigned lv1_skip;             // groups whose undecided level-0 entries go straight to the FP32 level
 };
 
 // Per-query statistics history (device).

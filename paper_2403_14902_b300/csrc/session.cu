@@ -60,6 +60,9 @@ struct Udf {
     std::vector<__nv_bfloat16 *> dW16;
     std::vector<__nv_bfloat16 *> dW3;   // split-BF16 weights [N][3K] = [W_hi | W_lo | W_hi]
     std::vector<int> nt;     // tensor-core tile width per hidden layer (0: widest dividing N)
+    bool q8 = false;         // FP8 sessions: first layer in E4M3 at level 0
+    unsigned char *dW8 = nullptr;   // E4M3 codes of the first layer [N][K]
+    float *dsw = nullptr;           // per output channel scale of dW8
     MlpDev mlp{};
 };
 
@@ -116,6 +119,9 @@ struct hydro_session {
     float *act32[2] = {};
     __nv_bfloat16 *stage16 = nullptr, *act16[2] = {};
     __nv_bfloat16 *stage3 = nullptr, *act3[2] = {};   // split-BF16 operands (3x the columns)
+    unsigned char *stage8 = nullptr;   // FP8 sessions: E4M3 level-0 operand rows [cap][dim]
+    float *ascale = nullptr;           // and their scales [cap]
+    unsigned q8_mask = 0;              // pool UDFs in the FP8 set
     float *partials = nullptr;
     int pstride = 1;
     void *encode = nullptr;
@@ -178,7 +184,9 @@ hydro_status check(hydro_session *s) {
     return HYDRO_OK;
 }
 
-bool bf16(const hydro_session *s) { return s->cfg.precision == HYDRO_PREC_BF16; }
+// BF16 and FP8 sessions run the tensor-core levels
+bool bf16(const hydro_session *s) { return s->cfg.precision == HYDRO_PREC_BF16 || s->cfg.precision == HYDRO_PREC_FP8; }
+bool fp8(const hydro_session *s) { return s->cfg.precision == HYDRO_PREC_FP8; }
 
 // Bracket the launches of one class with events (profiling steps only).
 int prof_begin(hydro_session *s, int cls) {
@@ -203,14 +211,19 @@ int *rc_n(const MqDev &d, int level) {
 // split-BF16 form, operands [hi | hi | lo] against [W_hi | W_lo | W_hi]).
 // heads_out: return the heads and leave the head partials for a fused
 // classify (no finalize launch); else finalize into score.
+// q8: level 0 of an FP8 session (the FP8 set's first layers in E4M3).
 hydro_status eval_tc(hydro_session *s, const int *counts, const int *lists, float *score, bool split3,
-                     int min_rows = 0, TcHeads *heads_out = nullptr) {
+                     int min_rows = 0, TcHeads *heads_out = nullptr, bool q8 = false) {
     const MqDev &d = s->d;
     const int x = split3 ? 3 : 1;
+    q8 = q8 && !split3 && s->q8_mask;
     __nv_bfloat16 *stage = split3 ? s->stage3 : s->stage16;
     __nv_bfloat16 *const *act = split3 ? s->act3 : s->act16;
     int pe = prof_begin(s, SP_GATHER);
-    if (split3)
+    if (q8)
+        launch_gather_grouped_mixed(d.G, counts, lists, d.cap, reinterpret_cast<const float *const *>(s->d_hdr),
+                                    d.dim, d.dim, s->q8_mask, stage, s->stage8, s->ascale, d.cap, s->sms, s->st);
+    else if (split3)
         launch_gather_grouped_bf16x3(d.G, counts, lists, d.cap, reinterpret_cast<const float *const *>(s->d_hdr),
                                      d.dim, d.dim, stage, d.cap, s->sms, s->st, min_rows);
     else
@@ -235,6 +248,13 @@ hydro_status eval_tc(hydro_session *s, const int *counts, const int *lists, floa
                                 has ? x * u.dims[dd] : 0,
                                 has ? u.dims[dd + 1] : 0,
                                 has ? u.nt[dd] : 0};
+            if (q8 && dd == 0 && u.q8) {
+                gr[g].W = nullptr;
+                gr[g].X8 = s->stage8;
+                gr[g].W8 = u.dW8;
+                gr[g].ascale = s->ascale;
+                gr[g].wscale = u.dsw;
+            }
             if (head) {
                 heads.b[g] = u.b[u.n_layers - 1][0];
                 heads.tiles[g] = tc_gemm_head_parts(u.dims[dd + 1], u.nt[dd]);
@@ -423,10 +443,11 @@ hydro_status enqueue_step(hydro_session *s, Slot &slot) {
         prof_end(s, pe);
         s->step_launches++;
         if (bf) {
-            TRY(eval_tc(s, rc_n(d, LV_MAIN), d.list[LV_MAIN], d.score[LV_MAIN], false, 0, &heads));
+            TRY(eval_tc(s, rc_n(d, LV_MAIN), d.list[LV_MAIN], d.score[LV_MAIN], false, 0, &heads, true));
             classify(r, LV_MAIN, LV_X3, cond_of(s, gate(r, 1)), kMinSplitRows, &heads);
             TRY(open_if(s, slot, gate(r, 1), &sv));
-            TRY(eval_tc(s, rc_n(d, LV_X3), d.list[LV_X3], d.score[LV_X3], true, kMinSplitRows, &heads));
+            // level 1: split BF16 (BF16 sessions) or BF16 (the FP8 set of FP8 sessions)
+            TRY(eval_tc(s, rc_n(d, LV_X3), d.list[LV_X3], d.score[LV_X3], !fp8(s), kMinSplitRows, &heads));
             TRY(close_if(s, slot, gate(r, 1), sv));
             // decides the split level's entries, or forwards them all when it was skipped
             classify(r, LV_X3, LV_F32, cond_of(s, gate(r, 2)), 1, &heads);
@@ -663,6 +684,26 @@ hydro_status finalize(hydro_session *s) {
         for (int k = 0; k < 2; ++k) TRY(dalloc(s, &s->act16[k], sizeof(__nv_bfloat16) * (size_t)cap * s->wmax));
         TRY(dalloc(s, &s->stage3, sizeof(__nv_bfloat16) * (size_t)cap * 3 * c.dim));
         for (int k = 0; k < 2; ++k) TRY(dalloc(s, &s->act3[k], sizeof(__nv_bfloat16) * (size_t)cap * 3 * s->wmax));
+        if (fp8(s)) {
+            // the FP8 set: first layers wide enough, quantised per output channel on the device
+            const int wmin = c.fp8_min_width > 0 ? c.fp8_min_width : 1024;
+            for (int g = 0; g < G; ++g) {
+                Udf &u = s->udfs[g];
+                u.q8 = u.n_layers >= 2 && u.dims[1] >= wmin && tc_gemm_fp8_supported(u.dims[0], u.dims[1]);
+                if (!u.q8) continue;
+                s->q8_mask |= 1u << g;
+                TRY(dalloc(s, &u.dW8, (size_t)u.dims[1] * u.dims[0]));
+                TRY(dalloc(s, &u.dsw, sizeof(float) * u.dims[1]));
+                launch_quant_rows_e4m3(u.dW[0], u.dims[1], u.dims[0], u.dW8, u.dsw, s->sms, s->st);
+            }
+            TRY(dalloc(s, &s->stage8, (size_t)cap * c.dim));
+            TRY(dalloc(s, &s->ascale, sizeof(float) * (size_t)cap));
+            CU(cudaMemsetAsync(s->ascale, 0, sizeof(float) * (size_t)cap, s->st));
+            CU(cudaStreamSynchronize(s->st));
+            CU(cudaGetLastError());
+            // level-0 bands of the UDFs outside the FP8 set (already BF16) skip the BF16 level
+            d.lv1_skip = ((1u << G) - 1u) & ~s->q8_mask;
+        }
         s->pstride = 2 * (s->wmax / 64);
         TRY(dalloc(s, &s->partials, sizeof(float) * (size_t)cap * s->pstride));
         hydro_status rs = tc_gemm_init(&s->encode);
@@ -900,8 +941,10 @@ hydro_status hydro_session_create(const hydro_session_config *cfg, hydro_session
     if (cfg->dim < 64 || cfg->dim % 64) return fail(HYDRO_EINVAL, "dim must be a positive multiple of 64");
     if (cfg->max_step_tuples < 1 || cfg->max_step_tuples > (1 << 22))
         return fail(HYDRO_EINVAL, "max_step_tuples outside 1..4194304");
-    if (cfg->precision != HYDRO_PREC_FP32 && cfg->precision != HYDRO_PREC_BF16)
-        return fail(HYDRO_EINVAL, "precision must be FP32 or BF16");
+    if (cfg->precision != HYDRO_PREC_FP32 && cfg->precision != HYDRO_PREC_BF16 && cfg->precision != HYDRO_PREC_FP8)
+        return fail(HYDRO_EINVAL, "precision must be FP32, BF16 or FP8");
+    if (cfg->precision == HYDRO_PREC_FP8 && (cfg->dim % 128 || cfg->fp8_min_width < 0))
+        return fail(HYDRO_EINVAL, "FP8 sessions need dim a multiple of 128 and fp8_min_width >= 0");
     if (cfg->warmup_batches < 0 || cfg->stats_window < 1) return fail(HYDRO_EINVAL, "bad warmup/window");
     if (cfg->max_in_flight < 1 || cfg->max_in_flight > 8) return fail(HYDRO_EINVAL, "max_in_flight outside 1..8");
     if (cfg->batches_per_step < 1 || cfg->batches_per_step > 8 || cfg->route_lag < cfg->batches_per_step - 1 ||
@@ -992,10 +1035,12 @@ hydro_status hydro_session_udf_scores(hydro_session *s, int32_t udf, int32_t pre
     if (udf < 0 || udf >= (int)s->udfs.size()) return fail(HYDRO_EINVAL, "unknown pool UDF");
     if (n < 0 || (n > 0 && (!d_tuples || !d_scores))) return fail(HYDRO_EINVAL, "bad tuples/scores");
     if ((uintptr_t)d_tuples % 16) return fail(HYDRO_EINVAL, "tuples must be 16-byte aligned");
-    if (prec != HYDRO_PREC_FP64 && prec != HYDRO_PREC_FP32 && prec != HYDRO_PREC_BF16 && prec != HYDRO_PREC_BF16X3)
-        return fail(HYDRO_EINVAL, "precision must be FP64, FP32, BF16 or BF16X3");
+    if (prec != HYDRO_PREC_FP64 && prec != HYDRO_PREC_FP32 && prec != HYDRO_PREC_BF16 && prec != HYDRO_PREC_BF16X3 &&
+        prec != HYDRO_PREC_FP8)
+        return fail(HYDRO_EINVAL, "precision must be FP64, FP32, BF16, BF16X3 or FP8");
     if ((prec == HYDRO_PREC_BF16 || prec == HYDRO_PREC_BF16X3) && !bf16(s))
-        return fail(HYDRO_EINVAL, "BF16 and split-BF16 scores need a BF16 session");
+        return fail(HYDRO_EINVAL, "BF16 and split-BF16 scores need a BF16 or FP8 session");
+    if (prec == HYDRO_PREC_FP8 && !fp8(s)) return fail(HYDRO_EINVAL, "FP8 scores need an FP8 session");
     CU(cudaSetDevice(s->cfg.device));
     TRY(finalize(s));
     for (Slot &sl : s->slots)
@@ -1012,9 +1057,9 @@ hydro_status hydro_session_udf_scores(hydro_session *s, int32_t udf, int32_t pre
             CU(cudaMemcpyAsync(s->d_hdr, &hh, sizeof(void *), cudaMemcpyHostToDevice, s->st));
             k_single_queue<<<std::max(1, std::min((m + 255) / 256, s->sms * 4)), 256, 0, s->st>>>(
                 s->d.rc, udf, m, s->d.list[LV_MAIN], s->d.cap);
-            if (prec == HYDRO_PREC_BF16 || prec == HYDRO_PREC_BF16X3) {
+            if (prec == HYDRO_PREC_BF16 || prec == HYDRO_PREC_BF16X3 || prec == HYDRO_PREC_FP8) {
                 TRY(eval_tc(s, rc_n(s->d, LV_MAIN), s->d.list[LV_MAIN], s->d.score[LV_MAIN],
-                            prec == HYDRO_PREC_BF16X3));
+                            prec == HYDRO_PREC_BF16X3, 0, nullptr, prec == HYDRO_PREC_FP8));
             } else {
                 eval_f32(s, rc_n(s->d, LV_MAIN), s->d.list[LV_MAIN], s->d.score[LV_MAIN]);
             }
@@ -1037,39 +1082,44 @@ hydro_status hydro_session_calibrate(hydro_session *s, const void *d_tuples, int
     CU(cudaSetDevice(s->cfg.device));
     TRY(finalize(s));
     double *d = nullptr;
-    CU(cudaMalloc(&d, sizeof(double) * n * 4));
-    std::vector<double> s64(n), s32(n), s16(n), s3(n);
+    CU(cudaMalloc(&d, sizeof(double) * n * 5));
+    std::vector<double> s64(n), s32(n), s16(n), s3(n), s8(n);
     hydro_status rc = HYDRO_OK;
-    const bool bf = bf16(s);
+    const bool bf = bf16(s), f8 = fp8(s);
     for (int g = 0; g < (int)s->udfs.size() && rc == HYDRO_OK; ++g) {
         rc = hydro_session_udf_scores(s, g, HYDRO_PREC_FP64, d_tuples, n, d);
         if (rc == HYDRO_OK) rc = hydro_session_udf_scores(s, g, HYDRO_PREC_FP32, d_tuples, n, d + n);
         if (rc == HYDRO_OK && bf) rc = hydro_session_udf_scores(s, g, HYDRO_PREC_BF16, d_tuples, n, d + 2 * n);
         if (rc == HYDRO_OK && bf) rc = hydro_session_udf_scores(s, g, HYDRO_PREC_BF16X3, d_tuples, n, d + 3 * n);
+        if (rc == HYDRO_OK && f8) rc = hydro_session_udf_scores(s, g, HYDRO_PREC_FP8, d_tuples, n, d + 4 * n);
         if (rc != HYDRO_OK) break;
         if (cudaMemcpy(s64.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(s32.data(), d + n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
             (bf && cudaMemcpy(s16.data(), d + 2 * n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess) ||
-            (bf && cudaMemcpy(s3.data(), d + 3 * n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)) {
+            (bf && cudaMemcpy(s3.data(), d + 3 * n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+            (f8 && cudaMemcpy(s8.data(), d + 4 * n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)) {
             rc = fail(HYDRO_ECUDA, "copy of calibration scores failed");
             break;
         }
-        double e32 = 0, e16 = 0, e3 = 0, smax = 0;
+        double e32 = 0, e16 = 0, e3 = 0, e8 = 0, smax = 0;
         for (int64_t k = 0; k < n; ++k) {
             e32 = std::max(e32, std::fabs(s32[k] - s64[k]));
             if (bf) e16 = std::max(e16, std::fabs(s16[k] - s64[k]));
             if (bf) e3 = std::max(e3, std::fabs(s3[k] - s64[k]));
+            if (f8) e8 = std::max(e8, std::fabs(s8[k] - s64[k]));
             smax = std::max(smax, std::fabs(s64[k]));
         }
         Udf &u = s->udfs[g];
         u.margin_fp32 = std::max(16.0 * e32, 1e-9 * smax);
-        if (bf) u.margin_x3 = std::max(8.0 * e3, 1e-9 * smax);
-        if (bf && u.margin_lowp < 4.0 * e16) u.margin_lowp = 4.0 * e16;
+        // level 0 (lowp) and level 1 (split BF16; BF16 in FP8 sessions)
+        const double e0 = f8 ? e8 : e16, e1 = f8 ? e16 : e3;
+        if (bf) u.margin_x3 = std::max((f8 ? 4.0 : 8.0) * e1, 1e-9 * smax);
+        if (bf && u.margin_lowp < 4.0 * e0) u.margin_lowp = 4.0 * e0;
         if (info) {
             info[g] = hydro_calib_info{};
             info[g].max_err_fp32 = e32;
-            info[g].max_err_lowp = e16;
-            info[g].max_err_tf32 = e3;
+            info[g].max_err_lowp = e0;
+            info[g].max_err_tf32 = e1;
             info[g].margin_fp32 = u.margin_fp32;
             info[g].margin_lowp = u.margin_lowp;
             info[g].margin_tf32 = u.margin_x3;

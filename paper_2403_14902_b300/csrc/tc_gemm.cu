@@ -9,6 +9,8 @@
 // layer (one output) is folded into the epilogue of the last hidden layer:
 // each row leaves one partial head . relu(...) per column tile, summed in a
 // fixed order by a finalize kernel.
+#include <cuda_fp8.h>
+
 #include <cstring>
 #include <string>
 
@@ -36,7 +38,10 @@ struct __align__(64) TcGroup {
     const int *count;         // rows of the group (device)
     const float *bias;        // [N]
     const float *head_w;      // [N]: fold the one-output head into the epilogue; nullptr: store Y
-    int K, N, NT, pad;
+    const float *ascale;      // FP8 groups: [stacked rows] activation scale per row
+    const float *wscale;      // FP8 groups: [N] weight scale per output channel
+    int K, N, NT;
+    int fp8;                  // 1: E4M3 operands (kind::f8f6f4), 128-element K slices
 };
 
 struct TcLaunch {
@@ -127,15 +132,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
                 const int tiles_n = G.N / G.NT, local = t - start[g];
                 const int m0 = off[g] + (local / tiles_n) * 128, n0 = (local % tiles_n) * G.NT;
                 const uint32_t bytes = (uint32_t)(kA_BYTES + G.NT * 128);
-                for (int kb = 0; kb < G.K / 64; ++kb) {
+                const int kslice = G.fp8 ? 128 : 64;   // elements per 128-byte K slice
+                for (int kb = 0; kb < G.K / kslice; ++kb) {
                     if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
                     unsigned char *sa = smem + s * L.stage_bytes;
                     mbar_expect_tx(&full[s], bytes);
-                    tma_load_2d(sa, &G.tmA, &full[s], kb * 64, m0);
-                    tma_load_2d(sa + kA_BYTES, &G.tmB, &full[s], kb * 64, n0);
+                    tma_load_2d(sa, &G.tmA, &full[s], kb * kslice, m0);
+                    tma_load_2d(sa + kA_BYTES, &G.tmB, &full[s], kb * kslice, n0);
                     issued |= 1u << s;
                     last_par = (last_par & ~(1u << s)) | (ph << s);
                     if (++s == S) {
@@ -159,8 +165,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
                 const int g = tile_group(start, L.n, t);
-                const int NT = L.g[g].NT, kblocks = L.g[g].K / 64;
-                const uint32_t idesc = idesc_bf16(128, NT);
+                const int NT = L.g[g].NT, fp8 = L.g[g].fp8, kblocks = L.g[g].K / (fp8 ? 128 : 64);
+                const uint32_t idesc = fp8 ? idesc_e4m3(128, NT) : idesc_bf16(128, NT);
                 const int buf = tl & 1;
                 const uint32_t tph = (uint32_t)(tl >> 1) & 1u;
                 if (!mbar_wait(&tempty[buf], tph ^ 1u, abort_flag)) {
@@ -177,10 +183,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + s * L.stage_bytes);
                     const uint32_t sb = sa + kA_BYTES;
+                    if (fp8) {
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        mma_bf16(dt, smem_desc(sa + kk * 32, 1024, 2u), smem_desc(sb + kk * 32, 1024, 2u), idesc,
-                                 (kb | kk) != 0);
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_e4m3(dt, smem_desc(sa + kk * 32, 1024, 2u), smem_desc(sb + kk * 32, 1024, 2u), idesc,
+                                     (kb | kk) != 0);
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_bf16(dt, smem_desc(sa + kk * 32, 1024, 2u), smem_desc(sb + kk * 32, 1024, 2u), idesc,
+                                     (kb | kk) != 0);
+                    }
                     mma_commit(&empty[s]);
                     if (++s == S) {
                         s = 0;
@@ -212,12 +225,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
             const size_t row = (size_t)off[g] + m;
             const float *bias = G.bias + n0;
             const float *hw = G.head_w ? G.head_w + n0 : nullptr;
+            // FP8 groups: accumulator x ascale[row] x wscale[col]; BF16: x 1
+            const float asc = G.fp8 && live ? __ldg(G.ascale + row) : 1.f;
+            const float *wsc = G.fp8 ? G.wscale + n0 : nullptr;
             float hsum = 0.f;
 #pragma unroll 1
             for (int c0 = chalf * (NT >> 1); c0 < (chalf + 1) * (NT >> 1); c0 += 32) {
                 uint32_t r[32];
                 tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)(buf * half + c0), r);
                 tmem_ld_wait();
+                if (wsc) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) * (asc * __ldg(wsc + c0 + j)));
+                }
                 if (hw) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
@@ -293,13 +313,16 @@ using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, vo
 
 constexpr int kGemmSmem = 197888;   // S * stage + 1024 (alignment) + 256 (barriers), every NT
 
+// 2-D map over [outer][inner] elements of 2 bytes (BF16) or 1 byte (E4M3
+// codes, as UINT8), row stride ld elements.
 bool encode2d(EncodeFn enc, CUtensorMap *m, const void *base, int inner, long long outer, int ld, int box_inner,
-              int box_outer) {
+              int box_outer, int elem_bytes = 2) {
     const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * elem_bytes};
     const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
     const cuuint32_t es[2] = {1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+    return enc(m, elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+               const_cast<void *>(base), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -360,6 +383,62 @@ __global__ void k_gather_grouped_bf16x3(int n, const int *counts, const int *que
     }
 }
 
+// E4M3 codes of four values already divided by the row scale (saturating
+// to +-448), packed little-endian.
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return lo | (hi << 16);
+}
+
+// One warp per row: max |x| by a shuffle reduction, then 4 codes per lane
+// and 16-byte load (the row is read twice; the second pass hits L1/L2).
+__device__ __forceinline__ void quant_row_e4m3(const float *x, int K, unsigned char *out, float *scale, int lane) {
+    float amax = 0.f;
+    for (int i = lane; i < K / 4; i += 32) {
+        const float4 v = reinterpret_cast<const float4 *>(x)[i];
+        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const float inv = amax > 0.f ? 448.f / amax : 0.f;
+    for (int i = lane; i < K / 4; i += 32) {
+        const float4 v = reinterpret_cast<const float4 *>(x)[i];
+        reinterpret_cast<uint32_t *>(out)[i] = pack_e4m3x4(v.x * inv, v.y * inv, v.z * inv, v.w * inv);
+    }
+    if (lane == 0) *scale = amax / 448.f;
+}
+
+__global__ void k_gather_grouped_mixed(int n, const int *counts, const int *queues, int qstride,
+                                       const float *const *Xp, int ldx, int K, unsigned q8_mask,
+                                       __nv_bfloat16 *out16, unsigned char *out8, float *ascale) {
+    const float *X = *Xp;
+    int off[kMaxGroups + 1];
+    off[0] = 0;
+    for (int g = 0; g < n; ++g) off[g + 1] = off[g] + counts[g];
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < off[n]; e += gridDim.x * wpb) {
+        int g = 0;
+        while (e >= off[g + 1]) ++g;
+        const float *x = X + (size_t)queues[(size_t)g * qstride + (e - off[g])] * ldx;
+        if (q8_mask & (1u << g)) {
+            quant_row_e4m3(x, K, out8 + (size_t)e * K, ascale + e, lane);
+        } else {
+            for (int i = lane; i < K / 4; i += 32) {
+                const float4 v = reinterpret_cast<const float4 *>(x)[i];
+                reinterpret_cast<uint2 *>(out16 + (size_t)e * K)[i] = make_uint2(pack_bf16x2(v.x, v.y), pack_bf16x2(v.z, v.w));
+            }
+        }
+    }
+}
+
+__global__ void k_quant_rows_e4m3(const float *X, int rows, int K, unsigned char *out, float *scale) {
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += gridDim.x * wpb)
+        quant_row_e4m3(X + (size_t)r * K, K, out + (size_t)r * K, scale + r, lane);
+}
+
 __global__ void k_head_finalize_grouped(int n, const int *counts, TcHeads heads, const float *partials, int pstride,
                                         float *score, int sstride, int min_rows) {
     int off[kMaxGroups + 1];
@@ -379,6 +458,8 @@ __global__ void k_head_finalize_grouped(int n, const int *counts, TcHeads heads,
 }  // namespace
 
 bool tc_gemm_supported(int K, int N) { return K >= 64 && K % 64 == 0 && N >= 64 && N % 64 == 0 && K <= 65536; }
+
+bool tc_gemm_fp8_supported(int K, int N) { return tc_gemm_supported(K, N) && K % 128 == 0; }
 
 hydro_status tc_gemm_init(void **encode) {
     void *fn = nullptr;
@@ -411,9 +492,14 @@ hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n,
     long long tiles = 0;
     for (int g = 0; g < n; ++g) {
         const TcGemmGroup &h = groups[g];
-        if (!h.W) {   // rows only: the group takes its place in the stacking, no tiles
+        const bool fp8 = h.W8 != nullptr;
+        if (!h.W && !fp8) {   // rows only: the group takes its place in the stacking, no tiles
             L.g[g].count = h.count;
             continue;
+        }
+        if (fp8 && (!tc_gemm_fp8_supported(h.K, h.N) || !h.X8 || !h.ascale || !h.wscale || (h.ldx % 16) != 0)) {
+            g_gemm_err = "tensor-core GEMM: unsupported FP8 group";
+            return HYDRO_EUNSUPPORTED;
         }
         if (!tc_gemm_supported(h.K, h.N) || (h.nt && (h.nt % 64 || h.nt > 256 || h.N % h.nt)) || h.x_rows < 1 || (h.ldx % 8) != 0 || h.ldx < h.K ||
             (!h.head_w && (split3 ? 3 * h.N : h.N) > ldy) ||
@@ -428,9 +514,15 @@ hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n,
         G.count = h.count;
         G.bias = h.bias;
         G.head_w = h.head_w;
+        G.fp8 = fp8 ? 1 : 0;
+        G.ascale = h.ascale;
+        G.wscale = h.wscale;
         nt_max = G.NT > nt_max ? G.NT : nt_max;
-        if (!encode2d(enc, &G.tmA, h.X, h.K, h.x_rows, h.ldx, 64, 128) ||
-            !encode2d(enc, &G.tmB, h.W, h.K, h.N, h.K, 64, G.NT)) {
+        const bool mapped = fp8 ? encode2d(enc, &G.tmA, h.X8, h.K, h.x_rows, h.ldx, 128, 128, 1) &&
+                                      encode2d(enc, &G.tmB, h.W8, h.K, h.N, h.K, 128, G.NT, 1)
+                                : encode2d(enc, &G.tmA, h.X, h.K, h.x_rows, h.ldx, 64, 128) &&
+                                      encode2d(enc, &G.tmB, h.W, h.K, h.N, h.K, 64, G.NT);
+        if (!mapped) {
             g_gemm_err = "cuTensorMapEncodeTiled failed";
             return HYDRO_ECUDA;
         }
@@ -496,6 +588,24 @@ void launch_gather_grouped_bf16x3(int n, const int *counts, const int *queues, i
     if (grid > sms * 8) grid = sms * 8;
     if (grid < 1) grid = 1;
     k_gather_grouped_bf16x3<<<grid, 256, 0, st>>>(n, counts, queues, qstride, Xp, ldx, K, out, min_rows);
+}
+
+void launch_gather_grouped_mixed(int n, const int *counts, const int *queues, int qstride, const float *const *Xp,
+                                 int ldx, int K, unsigned q8_mask, __nv_bfloat16 *out16, unsigned char *out8,
+                                 float *ascale, int max_rows, int sms, cudaStream_t st) {
+    int grid = (max_rows + 7) / 8;   // 8 warps, one row each
+    if (grid > sms * 8) grid = sms * 8;
+    if (grid < 1) grid = 1;
+    k_gather_grouped_mixed<<<grid, 256, 0, st>>>(n, counts, queues, qstride, Xp, ldx, K, q8_mask, out16, out8,
+                                                 ascale);
+}
+
+void launch_quant_rows_e4m3(const float *X, int rows, int K, unsigned char *out, float *scale, int sms,
+                            cudaStream_t st) {
+    int grid = (rows + 7) / 8;
+    if (grid > sms * 8) grid = sms * 8;
+    if (grid < 1) grid = 1;
+    k_quant_rows_e4m3<<<grid, 256, 0, st>>>(X, rows, K, out, scale);
 }
 
 void launch_head_finalize_grouped(int n, const int *counts, const TcHeads &heads, const float *partials, int pstride,

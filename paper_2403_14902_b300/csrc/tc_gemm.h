@@ -22,16 +22,27 @@ struct TcGemmGroup {
     const float *head_w;         // [N] one-output head folded into the epilogue, or nullptr (store Y)
     int K, N;
     int nt;                      // column-tile width 64/128/256 dividing N; 0: the widest that divides
+    // FP8 (E4M3) group: with W8 set, the layer reads X8 (stacked E4M3 rows,
+    // row stride ldx bytes, K % 128 == 0) and W8 (E4M3 [N][K]) instead of X
+    // and W, and the epilogue scales the accumulator of row m, column n by
+    // ascale[m] * wscale[n] (m: stacked row) before the bias.
+    const unsigned char *X8 = nullptr;
+    const unsigned char *W8 = nullptr;
+    const float *ascale = nullptr;
+    const float *wscale = nullptr;
 };
-// A group with W == nullptr contributes only its row count to the stacking.
+// A group with W == nullptr (and W8 == nullptr) contributes only its row
+// count to the stacking.
 
 struct TcHeads {                 // per group: head bias and head partials per row of the last hidden layer
     float b[kMaxGroups];
     int tiles[kMaxGroups];
 };
 
-// Layer shape K -> N runs on the tensor cores (K, N multiples of 64).
+// Layer shape K -> N runs on the tensor cores (K, N multiples of 64; FP8
+// layers also need K % 128 == 0).
 bool tc_gemm_supported(int K, int N);
+bool tc_gemm_fp8_supported(int K, int N);
 // Look up the tensor-map encoder and set kernel attributes (once per query).
 hydro_status tc_gemm_init(void **encode);
 // Y[m] = relu(X[m] W^T + bias) (bf16, [rows][N]) for m < *count; X is bf16
@@ -67,6 +78,18 @@ void launch_gather_grouped_bf16x3(int n, const int *counts, const int *queues, i
 void launch_head_finalize_grouped(int n, const int *counts, const TcHeads &heads, const float *partials, int pstride,
                                   float *score, int sstride, int max_rows, int sms, cudaStream_t st,
                                   int min_rows = 0);
+// Level-0 operand of a session whose groups in q8_mask run their first layer
+// in FP8: stacked row e of group g (source X[queues[g * qstride + m]]) goes
+// to out8 as E4M3 codes of x / ascale[e], ascale[e] = max_k |x_k| / 448, when
+// bit g of q8_mask is set, else to out16 as BF16.  K % 128 == 0.
+void launch_gather_grouped_mixed(int n, const int *counts, const int *queues, int qstride, const float *const *Xp,
+                                 int ldx, int K, unsigned q8_mask, __nv_bfloat16 *out16, unsigned char *out8,
+                                 float *ascale, int max_rows, int sms, cudaStream_t st);
+// Per-row E4M3 quantisation of a fp32 [rows][K] matrix (K % 128 == 0):
+// scale[r] = max_k |X[r][k]| / 448 and out[r][k] = e4m3(X[r][k] / scale[r])
+// (saturating; an all-zero row gets scale 0 and zero codes).
+void launch_quant_rows_e4m3(const float *X, int rows, int K, unsigned char *out, float *scale, int sms,
+                            cudaStream_t st);
 // out[m] = bf16(X[rows[m]]) for m < *count (K % 8 == 0, 16-byte aligned rows).
 void launch_gather_bf16(const int *count, const int *rows, const float *X, int ldx, int K, __nv_bfloat16 *out,
                         int max_rows, int sms, cudaStream_t st);

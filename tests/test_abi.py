@@ -78,6 +78,18 @@ def test_session_defaults_and_rejections_without_a_device():
     cfg.max_step_tuples = 1024
     cfg.max_in_flight = 9
     assert L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
+    cfg.max_in_flight = 2
+    assert cfg.fp8_min_width == 0
+    cfg.precision = H.PRECISIONS["fp8"]
+    cfg.dim = 192                      # FP8 sessions: E4M3 rows in 128-byte K slices
+    assert L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
+    assert b"FP8" in L.hydro_last_error()
+    cfg.dim = 512
+    cfg.fp8_min_width = -1
+    assert L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
+    cfg.precision = 6                  # no such precision
+    cfg.fp8_min_width = 0
+    assert L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
     assert L.hydro_session_create(None, ctypes.byref(h)) == H.EINVAL
     assert L.hydro_session_destroy(None) == H.EINVAL
     assert L.hydro_session_poll(None, 0, None, None, None, 0) == H.EINVAL

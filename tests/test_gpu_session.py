@@ -139,6 +139,70 @@ def test_session_bf16_exact(small, autotune):
     s.close()
 
 
+def fp8_set(w):
+    """Pool UDFs whose first hidden layer has >= 1,024 outputs (the default FP8 set)."""
+    return [u for u, d in enumerate(w.udfs) if d[1] >= 1024]
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_session_fp8_exact(small, graphs):
+    """FP8 first layers for the widest UDFs: level-0 errors grow, the
+    calibrated margins grow with them, and the pass sets, orders and counts
+    stay those of the oracle.  Only FP8-set slots reach the BF16 level."""
+    import torch
+    w = small["w"]
+    q8 = fp8_set(w)
+    assert q8 == [2, 3, 5, 6, 7]
+    s = make_session(w, small["qs"], small["th"], precision="fp8", graphs=graphs,
+                     cap=len(small["queries"]) * small["chunk"], queries=small["queries"])
+    info = s.calibrate(torch.from_numpy(small["calib"]).cuda())
+    for u, d in enumerate(info):
+        assert d["margin_lowp"] >= 4 * d["max_err_lowp"] > 0
+        assert d["margin_tf32"] >= 4 * d["max_err_tf32"] > 0
+        if u in q8:    # level 0 in FP8, level 1 in BF16
+            assert d["max_err_lowp"] > 2 * d["max_err_tf32"]
+        else:          # level 0 is the BF16 path itself
+            assert d["max_err_lowp"] == d["max_err_tf32"]
+    res = run_session(s, small["streams"], small["chunk"])
+    check_steps(res, small["sims"], len(small["queries"]))
+    lv1 = 0
+    for counts, _, per in res:
+        for k, r in enumerate(per):
+            udfs = small["qs"][small["queries"][k]]["udfs"]
+            for slot, u in enumerate(udfs):
+                if u not in q8:
+                    assert r["recheck_split"][slot] == 0
+                lv1 += r["recheck_split"][slot]
+    assert lv1 > 0
+    s.close()
+
+
+def test_session_fp8_scores_against_oracle(small):
+    """Level-0 scores of an FP8 session: FP8-set UDFs are further from FP64
+    than their BF16 scores but within a few percent; the others are the BF16
+    scores exactly."""
+    import torch
+    w = small["w"]
+    s = make_session(w, small["qs"], small["th"], precision="fp8", cap=1000, queries=small["queries"])
+    X = small["streams"][3][:1000]
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    o8 = torch.empty(X.shape[0], dtype=torch.float64, device="cuda")
+    o16 = torch.empty_like(o8)
+    pool = D.mq_pool_weights(w)
+    for u in range(8):
+        S = O.udf_scores("vec", X, [pool[u]])[:, 0]
+        rms = np.sqrt((S ** 2).mean())
+        s.udf_scores(u, "fp8", Xd, o8)
+        s.udf_scores(u, "bf16", Xd, o16)
+        r8 = np.abs(o8.cpu().numpy() - S) / np.maximum(np.abs(S), rms)
+        r16 = np.abs(o16.cpu().numpy() - S) / np.maximum(np.abs(S), rms)
+        if u in fp8_set(w):
+            assert np.median(r16) < np.median(r8) < 5e-2, (u, np.median(r8), np.median(r16))
+        else:
+            assert torch.equal(o8, o16)
+    s.close()
+
+
 def test_session_wide_margins_recheck_everything(small):
     import torch
     s = make_session(small["w"], small["qs"], small["th"], precision="bf16",
