@@ -756,6 +756,36 @@ __global__ void __launch_bounds__(256) k_mq_tuple_order(MqDev d, const float *lo
     }
 }
 
+// Learned sessions, proxy output layer from the BF16 hidden activations of
+// the tensor-core first layer: Z[e][i] = b2[i] + sum_h W2[i][h] Hb[e][h] for
+// e < *count, a thread per row (H % 8 == 0, P <= 8; W2 staged in shared memory).
+__global__ void __launch_bounds__(256) k_mq_proxy_out(const int *count, const __nv_bfloat16 *Hb, int H,
+                                                      const float *W2, const float *b2, int P, float *Z, int ldz) {
+    extern __shared__ float w2s[];
+    for (int i = threadIdx.x; i < P * H; i += blockDim.x) w2s[i] = W2[i];
+    __syncthreads();
+    const int n = *count;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        float acc[kMqSlots];
+#pragma unroll
+        for (int i = 0; i < kMqSlots; ++i) acc[i] = i < P ? b2[i] : 0.f;
+        const uint4 *row = reinterpret_cast<const uint4 *>(Hb + (size_t)e * H);
+        for (int c = 0; c < H / 8; ++c) {
+            const uint4 v = row[c];
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float h0 = __uint_as_float(w[j] << 16), h1 = __uint_as_float(w[j] & 0xFFFF0000u);
+                const int h = c * 8 + 2 * j;
+#pragma unroll
+                for (int i = 0; i < kMqSlots; ++i)
+                    if (i < P) acc[i] = fmaf(w2s[i * H + h + 1], h1, fmaf(w2s[i * H + h], h0, acc[i]));
+            }
+        }
+        for (int i = 0; i < P; ++i) Z[(size_t)e * ldz + i] = acc[i];
+    }
+}
+
 // FP64 scores of one MLP on n rows (calibration).
 __global__ void __launch_bounds__(256) k_mq_scores_f64(MlpDev mlp, int max_width, const float *X, int ldx, int n,
                                                        double *out) {
@@ -857,6 +887,12 @@ void mq_launch_commit(const MqDev &d, const MqHist &h, StatRow *res_rows, unsign
 
 void mq_launch_tuple_order(const MqDev &d, const float *logits, int ldz, const int *ready, cudaStream_t st, int sms) {
     k_mq_tuple_order<<<grid_for(d.cap, 256, sms, 4), 256, 0, st>>>(d, logits, ldz, ready);
+}
+
+void mq_launch_proxy_out(const int *count, const __nv_bfloat16 *Hb, int H, const float *W2, const float *b2, int P,
+                         float *Z, int ldz, int max_rows, cudaStream_t st, int sms) {
+    k_mq_proxy_out<<<grid_for(max_rows, 256, sms, 2), 256, sizeof(float) * (size_t)P * H, st>>>(count, Hb, H, W2, b2,
+                                                                                                P, Z, ldz);
 }
 
 cudaError_t mq_band_smem_setup(int max_width) {

@@ -154,6 +154,10 @@ cudaError_t mq_band_smem_setup(int max_width);
 // proxy trained (*ready): slots by c_i (1 + e^{z_i}) of the tuple's logits
 // z (row stride ldz), ties to the lower slot; else the query's rank order.
 void mq_launch_tuple_order(const MqDev &d, const float *logits, int ldz, const int *ready, cudaStream_t st, int sms);
+// Learned sessions: proxy logits Z (row stride ldz) of the first *count rows
+// from their BF16 hidden activations Hb [rows][H] (H % 8 == 0, P <= 8).
+void mq_launch_proxy_out(const int *count, const __nv_bfloat16 *Hb, int H, const float *W2, const float *b2, int P,
+                         float *Z, int ldz, int max_rows, cudaStream_t st, int sms);
 // FP64 scores of one UDF on n rows of X (block per row), for calibration.
 void mq_launch_scores_f64(const MlpDev &mlp, int max_width, const float *X, int ldx, int n, double *out,
                           cudaStream_t st, int sms);

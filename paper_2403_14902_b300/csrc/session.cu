@@ -151,6 +151,11 @@ struct hydro_session {
     float *pg = nullptr, *pm = nullptr, *pv = nullptr;
     float *pH = nullptr, *pZ = nullptr, *pdZ = nullptr, *pdH = nullptr, *pinv = nullptr, *ppart = nullptr;
     int *p_ready = nullptr, *p_count = nullptr, *p_rows = nullptr;
+    // tensor-core proxy forward (BF16 sessions, hidden width a multiple of 64): BF16 copy of
+    // the first layer's FP32 master weights, refreshed after every training, and its output
+    bool proxy_tc = false;
+    __nv_bfloat16 *pW1_16 = nullptr, *pH16 = nullptr;
+    int *p_hrows = nullptr;               // device: H (rows of pW1 for the conversion)
     int *h_one = nullptr;                 // pinned 1
     float *ringX = nullptr;
     unsigned char *ringL = nullptr, *ringM = nullptr;
@@ -420,12 +425,29 @@ hydro_status enqueue_step(hydro_session *s, Slot &slot) {
         L2.Y = s->pZ;
         L2.ldy = P;
         L2.l[0] = MqLayer{s->pW2, s->pb2, 0.f, s->pH, s->ph, s->ph, P, 1};
-        pe = prof_begin(s, SP_CTRL);
-        mq_launch_layers_f32(L1, s->st, s->sms);
-        mq_launch_layers_f32(L2, s->st, s->sms);
+        if (s->proxy_tc) {
+            // BF16 rows -> tensor-core hidden layer (ReLU, stored BF16) -> logits
+            pe = prof_begin(s, SP_GATHER);
+            launch_gather_grouped_bf16(1, &d.rc->alive[0], d.alive[0], d.cap,
+                                       reinterpret_cast<const float *const *>(s->d_hdr), d.dim, d.dim, s->stage16,
+                                       d.cap, s->sms, s->st);
+            prof_end(s, pe);
+            TcGemmGroup g{&d.rc->alive[0], s->stage16, d.dim, d.cap, s->pW1_16, s->pb1, nullptr, d.dim, s->ph, 64};
+            pe = prof_begin(s, SP_GEMM);
+            hydro_status rs = tc_gemm_grouped_run(s->encode, &g, 1, s->pH16, s->ph, s->partials, s->pstride, s->sms,
+                                                  s->st, d.err);
+            prof_end(s, pe);
+            if (rs != HYDRO_OK) return fail(rs, "proxy layer: %s", tc_gemm_last_error());
+            pe = prof_begin(s, SP_CTRL);
+            mq_launch_proxy_out(&d.rc->alive[0], s->pH16, s->ph, s->pW2, s->pb2, P, s->pZ, P, d.cap, s->st, s->sms);
+        } else {
+            pe = prof_begin(s, SP_CTRL);
+            mq_launch_layers_f32(L1, s->st, s->sms);
+            mq_launch_layers_f32(L2, s->st, s->sms);
+        }
         mq_launch_tuple_order(d, s->pZ, P, s->p_ready, s->st, s->sms);
         prof_end(s, pe);
-        s->step_launches += 3;
+        s->step_launches += s->proxy_tc ? 4 : 3;
     }
     auto classify = [&](int r, int in, int out, Cond next, int next_min, const TcHeads *heads = nullptr) {
         const int p = prof_begin(s, SP_CTRL);
@@ -752,6 +774,14 @@ hydro_status finalize(hydro_session *s) {
         TRY(dalloc(s, &s->ringM, (size_t)R * cap));
         s->ring_n.assign(R, 0);
         TRY(dalloc(s, &d.order_t, (size_t)cap * kMqSlots));
+        s->proxy_tc = bf16(s) && H % 64 == 0 && tc_gemm_supported(D, H);
+        if (s->proxy_tc) {
+            TRY(dalloc(s, &s->pW1_16, sizeof(__nv_bfloat16) * (size_t)H * D));
+            TRY(dalloc(s, &s->pH16, sizeof(__nv_bfloat16) * (size_t)cap * H));
+            TRY(upload(s, &s->p_hrows, &H, 1));
+            launch_gather_bf16(s->p_hrows, nullptr, s->pW1, D, D, s->pW1_16, H, s->sms, s->st);
+            CU(cudaGetLastError());
+        }
     }
 
     // statistics history
@@ -874,6 +904,10 @@ hydro_status learned_after_step(hydro_session *s, const Slot &slot) {
             launch_proxy_train_step(pt, s->st);
             s->launches += 16;
         }
+    if (s->proxy_tc) {
+        launch_gather_bf16(s->p_hrows, nullptr, s->pW1, D, D, s->pW1_16, H, s->sms, s->st);
+        s->launches++;
+    }
     CU(cudaMemcpyAsync(s->p_ready, s->h_one, sizeof(int), cudaMemcpyHostToDevice, s->st));
     CU(cudaGetLastError());
     return HYDRO_OK;
