@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
+
 namespace hydro {
 
 // Bits of the per-query device error word (latched, reported by poll).
@@ -36,6 +38,21 @@ __device__ __forceinline__ double to_d(double v) { return v; }
 template <typename T> __device__ __forceinline__ T from_f(float v);
 template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// v rounded to the nearest TF32 number (sign, 8 exponent bits, 10 explicit
+// mantissa bits), ties to even, on the fp32 bit pattern (finite v).  The
+// 3xTF32 split forms store hi = tf32_rne(x) and lo = tf32_rne(x - hi): both
+// are exact TF32 values, so the tensor core drops no bits of them, and the
+// rounding errors are unbiased (truncating instead biases every product of a
+// long dot product the same way).
+__host__ __device__ __forceinline__ float tf32_rne(float v) {
+    uint32_t b;
+    memcpy(&b, &v, sizeof b);
+    b = (b + 0x0FFFu + ((b >> 13) & 1u)) & 0xFFFFE000u;
+    float r;
+    memcpy(&r, &b, sizeof r);
+    return r;
+}
 
 template <typename T> struct Acc { using type = float; };
 template <> struct Acc<double> { using type = double; };

@@ -179,8 +179,8 @@ __device__ __forceinline__ void store_relu_row(const T (&acc)[COUT], Tout *o) {
 }
 
 // relu(acc) for COUT channels in the FP32-accurate split form the tensor-core
-// kernel reads: [hi(COUT) | lo(COUT)], hi = value with the low 13 mantissa
-// bits cleared (a TF32 number), lo = value - hi (exact).
+// kernel reads: [hi(COUT) | lo(COUT)], hi = the value rounded to TF32, lo =
+// the remainder rounded to TF32.
 template <int COUT>
 __device__ __forceinline__ void store_relu_row_split(const float (&acc)[COUT], float *o) {
 #pragma unroll
@@ -189,8 +189,8 @@ __device__ __forceinline__ void store_relu_row_split(const float (&acc)[COUT], f
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float v = acc[j + e] > 0.f ? acc[j + e] : 0.f;
-            hi[e] = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-            lo[e] = v - hi[e];
+            hi[e] = tf32_rne(v);
+            lo[e] = tf32_rne(v - hi[e]);
         }
         *reinterpret_cast<float4 *>(o + j) = make_float4(hi[0], hi[1], hi[2], hi[3]);
         *reinterpret_cast<float4 *>(o + COUT + j) = make_float4(lo[0], lo[1], lo[2], lo[3]);

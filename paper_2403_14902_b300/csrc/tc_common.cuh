@@ -151,9 +151,9 @@ static __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 }
 
 // SPLIT: FP32-accurate variant.  Activations and weights are fp32 values
-// split into a high TF32 part (low 13 mantissa bits cleared) and the exact
-// fp32 remainder; the MMA (kind::tf32) accumulates hi*hi + hi*lo + lo*hi,
-// which keeps about 21 significant bits per product (3xTF32).
+// split into hi = x rounded to TF32 and lo = (x - hi) rounded to TF32
+// (tf32_rne); the MMA (kind::tf32) accumulates hi*hi + hi*lo + lo*hi, which
+// keeps about 22 significant bits per product, unbiased (3xTF32).
 // Instruction descriptor, kind::tf32: FP32 accumulate, TF32 A and B (format
 // code 2), both K-major.
 static __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
@@ -170,7 +170,6 @@ static __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc,
         : "memory");
 }
 
-static __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
 
 // 2-D tiled TMA load: box at (c0 innermost, c1).

@@ -33,9 +33,10 @@ namespace {
 
 using namespace tcx;
 thread_local std::string g_tc_err;
-// MT: 128-pixel subtiles per CTA tile (1 or 2).  With MT = 2 one A box of
-// 6 image rows feeds both subtiles and every B box is used twice, which cuts
-// the L2->SM operand traffic per output pixel.
+// MT: 128-pixel subtiles per CTA tile (2 or 4).  One A box of 2 + 2 MT image
+// rows feeds all subtiles and every B box is used MT times, which cuts the
+// L2->SM operand traffic per output pixel (the 64-output layers, whose double-
+// buffered accumulators fit TMEM at MT = 4, are the most operand-bound).
 template <int CC, int N, int S, bool SPLIT, int MT>
 struct TcCfg {
     static constexpr int ESZ = SPLIT ? 4 : 2;             // operand bytes
@@ -237,8 +238,8 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                             for (int e = 0; e < 4; ++e) {
                                 v[e] = __uint_as_float(r[j + e]) + __ldg(bias + c0 + j + e);
                                 v[e] = v[e] > 0.f ? v[e] : 0.f;
-                                hi[e] = tf32_hi(v[e]);
-                                lo[e] = v[e] - hi[e];
+                                hi[e] = tf32_rne(v[e]);
+                                lo[e] = tf32_rne(v[e] - hi[e]);
                             }
                             *reinterpret_cast<float4 *>(o + c0 + j) = make_float4(hi[0], hi[1], hi[2], hi[3]);
                             *reinterpret_cast<float4 *>(o + N + c0 + j) = make_float4(lo[0], lo[1], lo[2], lo[3]);
@@ -324,16 +325,17 @@ cudaError_t set_smem() {
                                 TcCfg<CC, N, S, SPLIT, MT>::SMEM);
 }
 
-// Two 128-pixel subtiles per CTA tile; stage counts per (CC, N) sized to
-// 180-216 KB of shared memory.
-constexpr int kMT = 2;
-constexpr int kS_64_128 = 2, kS_64_64 = 3, kS_32_128 = 4, kS_32_64 = 6;
-constexpr int kS_t32_128 = 2, kS_t32_64 = 3;   // split TF32, CC = 32 fp32 channels
+// 128-output layers: two 128-pixel subtiles per CTA tile (2 x 2 x 128 TMEM
+// columns); 64-output layers: four (2 x 4 x 64).  Stage counts per shape sized
+// to 180-216 KB of shared memory.
+constexpr int kMT = 2, kMT64 = 4;
+constexpr int kS_64_128 = 2, kS_64_64 = 2, kS_32_128 = 4, kS_32_64 = 4;
+constexpr int kS_t32_128 = 2, kS_t32_64 = 2;   // split TF32, CC = 32 fp32 channels
 
 }  // namespace
 
 bool tc_conv_supported(int cin, int cout, int H, int W) {
-    if (W != 64 || H < 4 || (H % 4) != 0) return false;
+    if (W != 64 || H < 8 || (H % 8) != 0) return false;
     if (cout != 64 && cout != 128) return false;
     return cin == 32 || (cin % 64 == 0 && cin <= 512);
 }
@@ -367,13 +369,9 @@ void tc_conv_pack_weights_split(const float *w, int cin, int cout, std::vector<f
                         for (int k = 0; k < CC; ++k) {
                             const int ci = c * CC + k;
                             const float v = w[(((size_t)co * cin + ci) * 3 + ky) * 3 + kx];
-                            uint32_t bits;
-                            std::memcpy(&bits, &v, 4);
-                            bits &= 0xFFFFE000u;
-                            float hi;
-                            std::memcpy(&hi, &bits, 4);
+                            const float hi = tf32_rne(v);
                             const size_t o = ((((size_t)(plane * nch + c) * 3 + kx) * 3 + ky) * cout + co) * CC + k;
-                            out[o] = plane == 0 ? hi : v - hi;
+                            out[o] = plane == 0 ? hi : tf32_rne(v - hi);
                         }
 }
 
@@ -389,11 +387,11 @@ hydro_status tc_conv_init(TcConvPlan *plan, int device) {
     plan->encode = fn;
     cudaError_t r = cudaSuccess;
     if (r == cudaSuccess) r = set_smem<64, 128, kS_64_128, false, kMT>();
-    if (r == cudaSuccess) r = set_smem<64, 64, kS_64_64, false, kMT>();
+    if (r == cudaSuccess) r = set_smem<64, 64, kS_64_64, false, kMT64>();
     if (r == cudaSuccess) r = set_smem<32, 128, kS_32_128, false, kMT>();
-    if (r == cudaSuccess) r = set_smem<32, 64, kS_32_64, false, kMT>();
+    if (r == cudaSuccess) r = set_smem<32, 64, kS_32_64, false, kMT64>();
     if (r == cudaSuccess) r = set_smem<32, 128, kS_t32_128, true, kMT>();
-    if (r == cudaSuccess) r = set_smem<32, 64, kS_t32_64, true, kMT>();
+    if (r == cudaSuccess) r = set_smem<32, 64, kS_t32_64, true, kMT64>();
     if (r != cudaSuccess) {
         g_tc_err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(r);
         return HYDRO_ECUDA;
@@ -423,6 +421,7 @@ hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int
     const int esz = split ? 4 : 2;
     const int planes = split ? 2 : 1;
     const int nch = cin / CC;
+    const int mt = cout == 64 ? kMT64 : kMT;   // 128-pixel subtiles per CTA tile
     const CUtensorMapDataType dt = split ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const CUtensorMapSwizzle swz = CC * esz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     const cuuint64_t ctot = (cuuint64_t)cin * planes;   // channels stored per pixel
@@ -430,7 +429,7 @@ hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int
     {
         const cuuint64_t dims[4] = {ctot, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)max_frames};
         const cuuint64_t strides[3] = {ctot * esz, (cuuint64_t)W * ctot * esz, (cuuint64_t)H * W * ctot * esz};
-        const cuuint32_t box[4] = {(cuuint32_t)CC, 64, (cuuint32_t)(2 + 2 * kMT), 1};
+        const cuuint32_t box[4] = {(cuuint32_t)CC, 64, (cuuint32_t)(2 + 2 * mt), 1};
         const cuuint32_t es[4] = {1, 1, 1, 1};
         CUresult r = enc(&tmA, dt, 4, const_cast<void *>(in), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -452,22 +451,22 @@ hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int
             return HYDRO_ECUDA;
         }
     }
-    const int tpf = H / (2 * kMT);   // CTA tiles per frame (W == 64)
+    const int tpf = H / (2 * mt);   // CTA tiles per frame (W == 64)
     long long tiles = (long long)max_frames * tpf;
     const int grid = (int)(tiles < sms ? tiles : sms);
     const int HW = H * W;
-#define HYDRO_TC_LAUNCH(CC_, N_, S_, SPLIT_)                                                               \
-    k_conv3x3_tc<CC_, N_, S_, SPLIT_, kMT><<<grid, 192, TcCfg<CC_, N_, S_, SPLIT_, kMT>::SMEM, st>>>(    \
+#define HYDRO_TC_LAUNCH(CC_, N_, S_, SPLIT_, MT_)                                                           \
+    k_conv3x3_tc<CC_, N_, S_, SPLIT_, MT_><<<grid, 192, TcCfg<CC_, N_, S_, SPLIT_, MT_>::SMEM, st>>>(    \
         tmA, tmB, count, nch, cin, tpf, HW, bias, out, head_w, partials, err)
     if (split) {
-        if (cout == 128) HYDRO_TC_LAUNCH(32, 128, kS_t32_128, true);
-        else HYDRO_TC_LAUNCH(32, 64, kS_t32_64, true);
+        if (cout == 128) HYDRO_TC_LAUNCH(32, 128, kS_t32_128, true, kMT);
+        else HYDRO_TC_LAUNCH(32, 64, kS_t32_64, true, kMT64);
     } else if (CC == 64) {
-        if (cout == 128) HYDRO_TC_LAUNCH(64, 128, kS_64_128, false);
-        else HYDRO_TC_LAUNCH(64, 64, kS_64_64, false);
+        if (cout == 128) HYDRO_TC_LAUNCH(64, 128, kS_64_128, false, kMT);
+        else HYDRO_TC_LAUNCH(64, 64, kS_64_64, false, kMT64);
     } else {
-        if (cout == 128) HYDRO_TC_LAUNCH(32, 128, kS_32_128, false);
-        else HYDRO_TC_LAUNCH(32, 64, kS_32_64, false);
+        if (cout == 128) HYDRO_TC_LAUNCH(32, 128, kS_32_128, false, kMT);
+        else HYDRO_TC_LAUNCH(32, 64, kS_32_64, false, kMT64);
     }
 #undef HYDRO_TC_LAUNCH
     cudaError_t e = cudaGetLastError();
