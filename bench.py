@@ -472,9 +472,10 @@ def ours_drift6(args):
     # the same query as a one-query session: BF16 tensor cores, CUDA graphs,
     # per-tuple orders from the proxy (learned) or per-batch rank orders
     def session(learned, precision, K):
+        # each Adam step of the proxy trains on a moving 8,192-row window of a stored step
         s = H.Session(dim=w.dim, max_step_tuples=K * w.batch, precision=precision, graphs=True, autotune=True,
                       max_in_flight=2, stream=stream, learned=learned, proxy_refresh=w.extra["refresh"],
-                      proxy_hidden=w.extra["proxy_hidden"], batches_per_step=K, lag=K - 1)
+                      proxy_hidden=w.extra["proxy_hidden"], batches_per_step=K, lag=K - 1, proxy_rows=8192)
         for i in range(len(w.udfs)):
             s.add_udf(full[i])
         s.add_query(list(range(len(w.udfs))), th)
@@ -580,7 +581,8 @@ def ours_drift6(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"drift6: {w.n} x 512 fp32 tuples, 8 Dirichlet(0.5) drift segments, 6 MLP "
                                "predicates 512-h-1 (cost 1:2:4:8:16:32), learned 512-64-6 proxy picks per-tuple "
-                               f"orders (trained every 16 batches), batches of {w.batch}, one-query session with {DK} "
+                               f"orders (trained every 16 batches, 8,192-row window per Adam step), batches of {w.batch}, "
+                               f"one-query session with {DK} "
                                f"batches per step (route lag {DK - 1}): BF16 tensor cores + split-BF16/FP32/FP64 recheck, "
                                "CUDA graphs",
                    "global_batch": w.n, "routing_batch": w.batch, "parallelism": f"replicas{ws}",

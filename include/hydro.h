@@ -415,6 +415,10 @@ typedef struct hydro_session_config {
                                  >= K - 1 so that every batch of a step sees only earlier steps */
     int32_t fp8_min_width;    /* HYDRO_PREC_FP8: pool UDFs whose first hidden layer has at least
                                  this many outputs form the FP8 set (0: 1024) */
+    int32_t proxy_rows;       /* learned: rows of one stored step that one Adam step trains on
+                                 (0: all of them); a contiguous window that moves on by
+                                 proxy_rows at every Adam step, so that the stored rows are
+                                 used in turn */
 } hydro_session_config;
 
 /* Per query result of one step (hydro_session_poll). */

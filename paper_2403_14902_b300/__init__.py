@@ -92,7 +92,7 @@ class SessionConfig(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("learned", ctypes.c_int32), ("proxy_hidden", ctypes.c_int32),
                 ("proxy_refresh", ctypes.c_int32), ("proxy_epochs", ctypes.c_int32), ("proxy_lr", ctypes.c_float),
                 ("proxy_seed", ctypes.c_int32), ("batches_per_step", ctypes.c_int32), ("route_lag", ctypes.c_int32),
-                ("fp8_min_width", ctypes.c_int32)]
+                ("fp8_min_width", ctypes.c_int32), ("proxy_rows", ctypes.c_int32)]
 
 
 class StepQuery(ctypes.Structure):
@@ -420,7 +420,7 @@ class Session:
                  window: int = 8, graphs: bool = True, autotune: bool = True, max_in_flight: int = 2,
                  device: int = 0, stream=None, learned: bool = False, proxy_hidden: int = 64,
                  proxy_refresh: int = 16, proxy_epochs: int = 1, proxy_lr: float = 1e-3, proxy_seed: int = 1,
-                 batches_per_step: int = 1, lag: int = 0, fp8_min_width: int = 0):
+                 batches_per_step: int = 1, lag: int = 0, fp8_min_width: int = 0, proxy_rows: int = 0):
         L = load()
         cfg = SessionConfig()
         L.hydro_session_default_config(ctypes.byref(cfg))
@@ -443,6 +443,7 @@ class Session:
         cfg.batches_per_step = batches_per_step
         cfg.route_lag = lag
         cfg.fp8_min_width = fp8_min_width
+        cfg.proxy_rows = proxy_rows
         self.K = batches_per_step
         self._h = ctypes.c_void_p()
         _check(L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(self._h)), "hydro_session_create")

@@ -161,6 +161,7 @@ struct hydro_session {
     unsigned char *ringL = nullptr, *ringM = nullptr;
     std::vector<int> ring_n;
     long long learned_batches = 0, learned_steps = 0;
+    long long train_off = 0;              // start of the next training window (proxy_rows)
     int adam_t = 0;
     long long last_step_total = -1;       // stacked tuples of the most recent step (debug trace)
 };
@@ -862,9 +863,12 @@ hydro_status learned_after_step(hydro_session *s, const Slot &slot) {
     const size_t nW1 = (size_t)H * D;
     for (int e = 0; e < std::max(1, c.proxy_epochs); ++e)
         for (int k = 0; k < R; ++k) {
-            const int M = s->ring_n[k];
-            if (M <= 0) continue;
-            const float *Xs = s->ringX + (size_t)k * cap * D;
+            const int Mall = s->ring_n[k];
+            if (Mall <= 0) continue;
+            const int M = c.proxy_rows > 0 ? std::min(Mall, c.proxy_rows) : Mall;
+            const int off = M < Mall ? (int)(s->train_off % (Mall - M + 1)) : 0;
+            s->train_off += M;
+            const float *Xs = s->ringX + ((size_t)k * cap + off) * D;
             launch_identity_list(s->p_rows, s->p_count, 0, M, s->st);
             launch_mlp_layer_f32(s->p_count, nullptr, Xs, D, s->pW1, s->pb1, s->pH, D, H, 1, M, s->sms, s->st);
             launch_mlp_layer_f32(s->p_count, nullptr, s->pH, H, s->pW2, s->pb2, s->pZ, H, P, 0, M, s->sms, s->st);
@@ -883,8 +887,8 @@ hydro_status learned_after_step(hydro_session *s, const Slot &slot) {
             pt.dH = s->pdH;
             pt.inv_pairs = s->pinv;
             pt.part = s->ppart;
-            pt.label = s->ringL + (size_t)k * cap;
-            pt.mask = s->ringM + (size_t)k * cap;
+            pt.label = s->ringL + (size_t)k * cap + off;
+            pt.mask = s->ringM + (size_t)k * cap + off;
             pt.W1 = s->pW1;
             pt.b1 = s->pb1;
             pt.W2 = s->pW2;
@@ -985,7 +989,8 @@ hydro_status hydro_session_create(const hydro_session_config *cfg, hydro_session
         cfg->route_lag > 64)
         return fail(HYDRO_EINVAL, "batches_per_step 1..8 with route_lag >= batches_per_step - 1 (<= 64)");
     if (cfg->learned && (cfg->proxy_hidden < 0 || cfg->proxy_hidden > 1024 || cfg->proxy_refresh < 1 ||
-                         cfg->proxy_refresh > 256 || cfg->proxy_epochs < 0 || !(cfg->proxy_lr > 0.f)))
+                         cfg->proxy_refresh > 256 || cfg->proxy_epochs < 0 || !(cfg->proxy_lr > 0.f) ||
+                         cfg->proxy_rows < 0))
         return fail(HYDRO_EINVAL, "bad proxy settings");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)

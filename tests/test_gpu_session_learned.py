@@ -78,11 +78,39 @@ def test_learned_session_exact_and_prefix_consistent(drift6, precision, graphs):
     s.close()
 
 
+def test_learned_session_training_window(drift6):
+    """Each Adam step trains on a 300-row window of a stored step that moves
+    on by 300 rows every step: results stay exact and prefix-consistent, and
+    the proxy still learns tuple-specific orders."""
+    import paper_2403_14902_b300 as H
+    w = drift6["w"]
+    P = len(w.udfs)
+    s = H.Session(dim=w.dim, max_step_tuples=B, precision="bf16", learned=True, proxy_refresh=REFRESH,
+                  proxy_epochs=3, proxy_lr=3e-3, proxy_rows=300)
+    for layers in D.predicate_weights(w):
+        s.add_udf(layers)
+    s.add_query(list(range(P)), drift6["th"])
+    s.calibrate(drift6["calib"])
+    varied = 0
+    for b in range(NB):
+        sid = s.submit(drift6["Xd"][b * B:(b + 1) * B], [B])
+        words, per, _ = s.poll(sid)
+        order, visited = s.debug_trace(sid, B)
+        check_step(drift6["pm"][b * B:(b + 1) * B], H.bits_from_words(words, B), per[0], order, visited, P)
+        if b >= REFRESH:
+            varied += len({tuple(o[:P]) for o in order}) > 1
+    assert varied > 0
+    s.close()
+
+
 def test_learned_session_config_checks():
     import paper_2403_14902_b300 as H
     w = D.workload("drift6")
     with pytest.raises(H.HydroError) as e:
         H.Session(dim=w.dim, max_step_tuples=B, learned=True, proxy_refresh=0)
+    assert e.value.status == H.EINVAL
+    with pytest.raises(H.HydroError) as e:
+        H.Session(dim=w.dim, max_step_tuples=B, learned=True, proxy_rows=-1)
     assert e.value.status == H.EINVAL
     s = H.Session(dim=w.dim, max_step_tuples=B, learned=True)
     for layers in D.predicate_weights(w)[:2]:
