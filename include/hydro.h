@@ -400,8 +400,10 @@ typedef struct hydro_session_config {
                                  one query: a proxy MLP dim -> proxy_hidden -> P predicts each slot's
                                  pass probability p, each tuple visits its slots by c (1 + e^z),
                                  z = logit(p); trained online (Adam, masked BCE) on the outcomes of
-                                 the last proxy_refresh steps every proxy_refresh steps; rank orders
-                                 until the first training.  Sessions with one query only */
+                                 the last proxy_refresh batches every proxy_refresh batches, on a
+                                 stream of its own: a training launched after step j takes effect
+                                 from step j + 2 on (it overlaps step j + 1); rank orders until
+                                 the first training.  Sessions with one query only */
     int32_t proxy_hidden;     /* learned: proxy hidden width (default 64) */
     int32_t proxy_refresh;    /* learned: train after every this many steps (default 16) */
     int32_t proxy_epochs;     /* learned: passes over the stored steps per training (default 1) */

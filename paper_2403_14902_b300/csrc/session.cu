@@ -162,6 +162,17 @@ struct hydro_session {
     std::vector<int> ring_n;
     long long learned_batches = 0, learned_steps = 0;
     long long train_off = 0;              // start of the next training window (proxy_rows)
+    // Training runs on its own stream, overlapping the next step.  Steps read an inference
+    // copy of the parameters (iW1 | ib1 | iW2 | ib2), refreshed from the FP32 masters on the
+    // step stream at the second submit after the step that launched the training (waiting for
+    // it): the weights a step uses depend on the submission order only.
+    cudaStream_t train_st = nullptr;
+    cudaEvent_t ev_ring = nullptr, ev_trained = nullptr;
+    bool train_pending = false;
+    long long train_step = -1;            // step after which the pending training was launched
+    float *iparams = nullptr, *iW1 = nullptr, *ib1 = nullptr, *iW2 = nullptr, *ib2 = nullptr;
+    size_t nparam = 0;
+    float *tH = nullptr, *tZ = nullptr;   // training activations and logits
     int adam_t = 0;
     long long last_step_total = -1;       // stacked tuples of the most recent step (debug trace)
 };
@@ -420,12 +431,12 @@ hydro_status enqueue_step(hydro_session *s, Slot &slot) {
         L1.ldx = d.dim;
         L1.Y = s->pH;
         L1.ldy = s->ph;
-        L1.l[0] = MqLayer{s->pW1, s->pb1, 0.f, nullptr, 0, d.dim, s->ph, 0};
+        L1.l[0] = MqLayer{s->iW1, s->ib1, 0.f, nullptr, 0, d.dim, s->ph, 0};
         MqLayers L2 = L1;
         L2.rows = nullptr;
         L2.Y = s->pZ;
         L2.ldy = P;
-        L2.l[0] = MqLayer{s->pW2, s->pb2, 0.f, s->pH, s->ph, s->ph, P, 1};
+        L2.l[0] = MqLayer{s->iW2, s->ib2, 0.f, s->pH, s->ph, s->ph, P, 1};
         if (s->proxy_tc) {
             // BF16 rows -> tensor-core hidden layer (ReLU, stored BF16) -> logits
             pe = prof_begin(s, SP_GATHER);
@@ -433,14 +444,14 @@ hydro_status enqueue_step(hydro_session *s, Slot &slot) {
                                        reinterpret_cast<const float *const *>(s->d_hdr), d.dim, d.dim, s->stage16,
                                        d.cap, s->sms, s->st);
             prof_end(s, pe);
-            TcGemmGroup g{&d.rc->alive[0], s->stage16, d.dim, d.cap, s->pW1_16, s->pb1, nullptr, d.dim, s->ph, 64};
+            TcGemmGroup g{&d.rc->alive[0], s->stage16, d.dim, d.cap, s->pW1_16, s->ib1, nullptr, d.dim, s->ph, 64};
             pe = prof_begin(s, SP_GEMM);
             hydro_status rs = tc_gemm_grouped_run(s->encode, &g, 1, s->pH16, s->ph, s->partials, s->pstride, s->sms,
                                                   s->st, d.err);
             prof_end(s, pe);
             if (rs != HYDRO_OK) return fail(rs, "proxy layer: %s", tc_gemm_last_error());
             pe = prof_begin(s, SP_CTRL);
-            mq_launch_proxy_out(&d.rc->alive[0], s->pH16, s->ph, s->pW2, s->pb2, P, s->pZ, P, d.cap, s->st, s->sms);
+            mq_launch_proxy_out(&d.rc->alive[0], s->pH16, s->ph, s->iW2, s->ib2, P, s->pZ, P, d.cap, s->st, s->sms);
         } else {
             pe = prof_begin(s, SP_CTRL);
             mq_launch_layers_f32(L1, s->st, s->sms);
@@ -749,6 +760,17 @@ hydro_status finalize(hydro_session *s) {
         s->pb1 = s->pW1 + (size_t)H * D;
         s->pW2 = s->pb1 + H;
         s->pb2 = s->pW2 + (size_t)P * H;
+        s->nparam = nparam;
+        TRY(upload(s, &s->iparams, init.data(), nparam));
+        s->iW1 = s->iparams;
+        s->ib1 = s->iW1 + (size_t)H * D;
+        s->iW2 = s->ib1 + H;
+        s->ib2 = s->iW2 + (size_t)P * H;
+        TRY(dalloc(s, &s->tH, sizeof(float) * (size_t)cap * H));
+        TRY(dalloc(s, &s->tZ, sizeof(float) * (size_t)cap * kMqSlots));
+        CU(cudaStreamCreateWithFlags(&s->train_st, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&s->ev_ring, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&s->ev_trained, cudaEventDisableTiming));
         TRY(dalloc(s, &s->pg, sizeof(float) * nparam));
         TRY(dalloc(s, &s->pm, sizeof(float) * nparam));
         TRY(dalloc(s, &s->pv, sizeof(float) * nparam));
@@ -769,7 +791,9 @@ hydro_status finalize(hydro_session *s) {
         s->host_allocs.push_back(hp);
         s->h_one = (int *)hp;
         *s->h_one = 1;
-        const int R = (std::max(1, c.proxy_refresh) + K - 1) / K;   // steps holding proxy_refresh batches
+        // steps holding proxy_refresh batches, plus the one the next step writes while a
+        // training still reads the others
+        const int R = (std::max(1, c.proxy_refresh) + K - 1) / K + 1;
         TRY(dalloc(s, &s->ringX, sizeof(float) * (size_t)R * cap * D));
         TRY(dalloc(s, &s->ringL, (size_t)R * cap));
         TRY(dalloc(s, &s->ringM, (size_t)R * cap));
@@ -780,7 +804,7 @@ hydro_status finalize(hydro_session *s) {
             TRY(dalloc(s, &s->pW1_16, sizeof(__nv_bfloat16) * (size_t)H * D));
             TRY(dalloc(s, &s->pH16, sizeof(__nv_bfloat16) * (size_t)cap * H));
             TRY(upload(s, &s->p_hrows, &H, 1));
-            launch_gather_bf16(s->p_hrows, nullptr, s->pW1, D, D, s->pW1_16, H, s->sms, s->st);
+            launch_gather_bf16(s->p_hrows, nullptr, s->iW1, D, D, s->pW1_16, H, s->sms, s->st);
             CU(cudaGetLastError());
         }
     }
@@ -835,10 +859,28 @@ hydro_status upload_margins(hydro_session *s) {
     return HYDRO_OK;
 }
 
+// Learned sessions: refresh the steps' inference copy of the proxy from the
+// FP32 masters once the pending training has finished (the step stream
+// waits for it), and mark the proxy ready.
+hydro_status proxy_swap(hydro_session *s) {
+    if (!s->train_pending) return HYDRO_OK;
+    CU(cudaStreamWaitEvent(s->st, s->ev_trained, 0));
+    CU(cudaMemcpyAsync(s->iparams, s->pW1, sizeof(float) * s->nparam, cudaMemcpyDeviceToDevice, s->st));
+    if (s->proxy_tc) {
+        launch_gather_bf16(s->p_hrows, nullptr, s->iW1, s->cfg.dim, s->cfg.dim, s->pW1_16, s->ph, s->sms, s->st);
+        s->launches++;
+    }
+    CU(cudaMemcpyAsync(s->p_ready, s->h_one, sizeof(int), cudaMemcpyHostToDevice, s->st));
+    s->train_pending = false;
+    return HYDRO_OK;
+}
+
 // Learned sessions, after a step: keep its tuples and outcomes in the
-// training ring; every proxy_refresh batches retrain the proxy on the ring
-// (masked BCE on the slots each tuple was evaluated on, Adam) and mark it
-// ready.  Stream-ordered after the step, outside its graph.
+// training ring; every proxy_refresh batches retrain the proxy on the ring's
+// steps holding the last proxy_refresh batches (masked BCE on the slots each
+// tuple was evaluated on, Adam), on the training stream, after the ring copy.
+// The steps see the result from the second step after this one on
+// (proxy_swap at that submit), so training overlaps the next step.
 hydro_status learned_after_step(hydro_session *s, const Slot &slot) {
     int n = 0, nb = 0;   // the step's tuples and batches (one query)
     for (int k = 0; k < s->cfg.batches_per_step; ++k) {
@@ -848,8 +890,9 @@ hydro_status learned_after_step(hydro_session *s, const Slot &slot) {
     if (n <= 0) return HYDRO_OK;
     const hydro_session_config &c = s->cfg;
     const int D = c.dim, H = s->ph, P = s->queries[0].P, cap = s->d.cap;
-    const int R = (int)s->ring_n.size();   // steps kept: those holding the last proxy_refresh batches
-    const int rs = (int)(s->learned_steps % R);
+    const int RR = (int)s->ring_n.size();   // ring entries
+    const int R = RR - 1;                   // entries one training reads
+    const int rs = (int)(s->learned_steps % RR);
     CU(cudaMemcpyAsync(s->ringX + (size_t)rs * cap * D, slot.h_hdr->X, sizeof(float) * (size_t)n * D,
                        cudaMemcpyDeviceToDevice, s->st));
     CU(cudaMemcpyAsync(s->ringL + (size_t)rs * cap, s->d.label, n, cudaMemcpyDeviceToDevice, s->st));
@@ -860,18 +903,27 @@ hydro_status learned_after_step(hydro_session *s, const Slot &slot) {
     s->learned_batches += nb;
     const int refresh = std::max(1, c.proxy_refresh);
     if (before / refresh == s->learned_batches / refresh) return HYDRO_OK;
+    // a training still pending (launched after the previous step) takes effect now,
+    // before the next one changes the masters
+    TRY(proxy_swap(s));
+    CU(cudaEventRecord(s->ev_ring, s->st));
+    CU(cudaStreamWaitEvent(s->train_st, s->ev_ring, 0));
+    const cudaStream_t ts = s->train_st;
     const size_t nW1 = (size_t)H * D;
     for (int e = 0; e < std::max(1, c.proxy_epochs); ++e)
-        for (int k = 0; k < R; ++k) {
+        for (int j = 0; j < R; ++j) {
+            const long long stp = s->learned_steps - R + j;   // oldest first
+            if (stp < 0) continue;
+            const int k = (int)(stp % RR);
             const int Mall = s->ring_n[k];
             if (Mall <= 0) continue;
             const int M = c.proxy_rows > 0 ? std::min(Mall, c.proxy_rows) : Mall;
             const int off = M < Mall ? (int)(s->train_off % (Mall - M + 1)) : 0;
             s->train_off += M;
             const float *Xs = s->ringX + ((size_t)k * cap + off) * D;
-            launch_identity_list(s->p_rows, s->p_count, 0, M, s->st);
-            launch_mlp_layer_f32(s->p_count, nullptr, Xs, D, s->pW1, s->pb1, s->pH, D, H, 1, M, s->sms, s->st);
-            launch_mlp_layer_f32(s->p_count, nullptr, s->pH, H, s->pW2, s->pb2, s->pZ, H, P, 0, M, s->sms, s->st);
+            launch_identity_list(s->p_rows, s->p_count, 0, M, ts);
+            launch_mlp_layer_f32(s->p_count, nullptr, Xs, D, s->pW1, s->pb1, s->tH, D, H, 1, M, s->sms, ts);
+            launch_mlp_layer_f32(s->p_count, nullptr, s->tH, H, s->pW2, s->pb2, s->tZ, H, P, 0, M, s->sms, ts);
             ProxyTrain pt{};
             pt.M = M;
             pt.P = P;
@@ -881,8 +933,8 @@ hydro_status learned_after_step(hydro_session *s, const Slot &slot) {
             pt.t = ++s->adam_t;
             pt.lr = c.proxy_lr;
             pt.X = Xs;
-            pt.Hact = s->pH;
-            pt.Z = s->pZ;
+            pt.Hact = s->tH;
+            pt.Z = s->tZ;
             pt.dZ = s->pdZ;
             pt.dH = s->pdH;
             pt.inv_pairs = s->pinv;
@@ -905,14 +957,12 @@ hydro_status learned_after_step(hydro_session *s, const Slot &slot) {
             pt.vb1 = s->pv + nW1;
             pt.vW2 = pt.vb1 + H;
             pt.vb2 = pt.vW2 + (size_t)P * H;
-            launch_proxy_train_step(pt, s->st);
+            launch_proxy_train_step(pt, ts);
             s->launches += 16;
         }
-    if (s->proxy_tc) {
-        launch_gather_bf16(s->p_hrows, nullptr, s->pW1, D, D, s->pW1_16, H, s->sms, s->st);
-        s->launches++;
-    }
-    CU(cudaMemcpyAsync(s->p_ready, s->h_one, sizeof(int), cudaMemcpyHostToDevice, s->st));
+    CU(cudaEventRecord(s->ev_trained, ts));
+    s->train_pending = true;
+    s->train_step = s->next_step;
     CU(cudaGetLastError());
     return HYDRO_OK;
 }
@@ -1196,6 +1246,7 @@ hydro_status hydro_session_submit(hydro_session *s, const void *d_tuples, const 
         TRY(upload_margins(s));
         if (s->cfg.autotune && bf16(s)) TRY(autotune(s));
     }
+    if (s->cfg.learned && s->train_pending && s->next_step >= s->train_step + 2) TRY(proxy_swap(s));
     slot->h_hdr->X = (const float *)d_tuples;
     for (int q = 0; q < Q; ++q) slot->h_hdr->counts[q] = counts[q];
     slot->counts.assign(counts, counts + Q);
@@ -1273,6 +1324,12 @@ hydro_status hydro_session_poll(hydro_session *s, int64_t step, uint32_t *pass_b
     TRY(wait_ev(slot->ev1, wait_ms, &done));
     if (!done) return fail(HYDRO_EAGAIN, "step %lld not finished", (long long)step);
     slot->busy = false;
+    if (s->cfg.learned && s->train_pending) {
+        // nothing else in flight: later work on the step stream follows the training
+        bool idle = true;
+        for (const Slot &sl : s->slots) idle = idle && !sl.busy;
+        if (idle) CU(cudaStreamWaitEvent(s->st, s->ev_trained, 0));
+    }
     s->launches += slot->launches;
     if (slot->conditional) {
         int g[kMqGates];
@@ -1418,6 +1475,12 @@ hydro_status hydro_session_destroy(hydro_session *s) {
         if (sl.ev1) cudaEventDestroy(sl.ev1);
     }
     if (s->st) cudaStreamSynchronize(s->st);
+    if (s->train_st) {
+        cudaStreamSynchronize(s->train_st);
+        cudaStreamDestroy(s->train_st);
+    }
+    if (s->ev_ring) cudaEventDestroy(s->ev_ring);
+    if (s->ev_trained) cudaEventDestroy(s->ev_trained);
     for (int k = 0; k < 2; ++k)
         if (s->helper[k]) cudaStreamDestroy(s->helper[k]);
     for (void *p : s->allocs) cudaFree(p);
