@@ -1031,6 +1031,60 @@ def ours_gemm_bf16(args):
     }
 
 
+# ---------------------------------------------------------------- conv alone
+
+def ours_conv_bf16(args):
+    """The tensor-core conv layers alone: the deepest CNN UDF of the frame
+    workload (3-32-64-64-128 then 128->128 x 4, 64x64 frames) on 1,024 frames
+    per step through a query that evaluates every frame (one predicate,
+    policy all, BF16, no recheck), with per-launch CUDA-event timing.  Each
+    step launches the tensor-core conv in the order 32->64, 64->64, 64->128,
+    then 128->128 four times."""
+    import torch
+    ws, rank = dist_init("nccl")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_2403_14902_b300 as H
+    w = D.workload("cnn4")
+    n = 1024
+    X = torch.from_numpy(D.stream_tuples(w, n)).cuda()
+    stream = torch.cuda.Stream()
+    q = H.Query(w.kind, frame=w.frame, max_batch=n, policy="all", precision="bf16", max_in_flight=1,
+                stream=stream)
+    q.add_cnn(D.predicate_weights(w)[3], 0.0)
+    q.set_margins(0, 0.0, 0.0, 0.0)   # no recheck: the BF16 layers alone decide
+    f = lambda: q.poll(q.submit(X))[2]["n_pass"]  # noqa: E731
+    for _ in range(args.warmup):
+        f()
+    q.profile(True)
+    secs, _ = timed(f, args.steps, stream, local)
+    prof, launches = q.profile_read()
+    q.close()
+    secs = max_over_ranks(secs, device=torch.device("cuda", local))
+    if rank != 0:
+        return None
+    peaks, src = load_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]))
+    g = prof.get("conv3x3_bf16_tc")
+    achieved = g["flops"] / (g["total_ms"] / 1000.0) / 1e12
+    return {
+        "metric": "tensor-core conv3x3 throughput (BF16, FP32 accumulate)", "value": round(achieved, 2),
+        "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(secs / args.steps * 1000.0, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"conv_bf16: CNN 3-32-64-64-128-128-128-128-128 on {n} frames 3x64x64 per step",
+                   "frames": n, "l2": "activations 1-2 GB per layer > 126 MB L2"},
+        "roofline": {"bound": "tensor", "kernel": "k_conv3x3_tc", "achieved": round(achieved, 2), "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": f"bf16_tflops_sustained ({src})", "launches": g["launches"],
+                     "avg_launch_ms": round(g["total_ms"] / max(1, g["launches"]), 4)},
+        "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
+                        "tflops": round(v["flops"] / max(v["total_ms"], 1e-9) / 1e9, 2),
+                        "gbs": round(v["bytes"] / max(v["total_ms"], 1e-9) / 1e6, 1)} for k, v in prof.items()},
+        "gpu_launches": int(launches), "tuples_per_s": round(aggregate(n, args.steps, secs, ws), 1),
+    }
+
+
 # ---------------------------------------------------------------- reference arm
 
 def reference(args):
@@ -1041,12 +1095,14 @@ def reference(args):
         return None
     import oracle as O
     name = args.workload
+    if name == "gemm_bf16":
+        return reference_gemm(args)
+    if name == "conv_bf16":
+        return reference_conv(args)
     w = D.workload(name)
     th = thresholds(name)
     if name == "mq64":
         return reference_mq64(args, w, th)
-    if name == "gemm_bf16":
-        return reference_gemm(args)
     n = 8 if w.kind == "frame" else 4096
     F = D.stream_tuples(w, n)
     ws_ = D.predicate_weights(w)
@@ -1091,6 +1147,32 @@ def reference_gemm(args):
             "e2e": {"value": round(value, 5), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def reference_conv(args):
+    """Oracle per step: the deepest CNN UDF in FP64 on 2 frames."""
+    import oracle as O
+    ws, _ = dist_env()[:2]
+    w = D.workload("cnn4")
+    udf = D.predicate_weights(w)[3]
+    F = D.stream_tuples(w, 2)
+    for _ in range(args.warmup):
+        O.udf_scores("frame", F[:1], [udf])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.udf_scores("frame", F, [udf])
+    dt = time.perf_counter() - t0
+    chans = [3, 32, 64, 64, 128, 128, 128, 128, 128]
+    flops = 2 * 64 * 64 * 9 * sum(a * b for a, b in zip(chans, chans[1:])) * F.shape[0] * args.steps
+    value = flops / dt / 1e12
+    return {"impl": "reference", "metric": "tensor-core conv3x3 throughput (BF16, FP32 accumulate)",
+            "value": round(value, 6), "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1000.0, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "conv_bf16: oracle FP64 CNN 3-32-64-64-128-128-128-128-128 on 2 frames per step"},
+            "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": O.threads(), "kind": "oracle",
+                             "sample": "2 frames per step"},
+            "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def reference_mq64(args, w, th):
     """Oracle per step: 64 tuples of every query through that query's UDFs."""
     import oracle as O
@@ -1130,13 +1212,14 @@ def main(argv=None):
     ap.add_argument("--no-graphs", action="store_true", help="with --headline-only: launch without CUDA graphs")
     ap.add_argument("--lanes", type=int, default=4, help="cnn4: stream lanes of the query (1..4)")
     ap.add_argument("--lag", type=int, default=3, help="cnn4: route lag (>= lanes - 1)")
-    ap.add_argument("--workload", choices=["cnn4", "drift5", "drift6", "mq64", "gemm_bf16"], default=WORKLOAD)
+    ap.add_argument("--workload", choices=["cnn4", "drift5", "drift6", "mq64", "gemm_bf16", "conv_bf16"],
+                    default=WORKLOAD)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         out = reference(args)
     else:
         out = {"cnn4": ours, "drift5": ours_drift5, "drift6": ours_drift6, "mq64": ours_mq64,
-               "gemm_bf16": ours_gemm_bf16}[args.workload](args)
+               "gemm_bf16": ours_gemm_bf16, "conv_bf16": ours_conv_bf16}[args.workload](args)
     if out is not None:
         print(json.dumps(out), flush=True)
 
