@@ -55,14 +55,20 @@ def load_peaks():
 
 
 def measured_traffic_ratio():
-    """DRAM bytes / algorithmic bytes of the tensor-core BF16 conv, from the
-    committed ncu summary (1,024-frame 128->128 launch), or None."""
+    """DRAM bytes / algorithmic bytes of the tensor-core BF16 conv over the
+    layer shapes of the committed ncu summary (one 1,024-frame launch each,
+    cells "traffic / algorithmic MB = ratio"), or None."""
     p = os.path.join(ROOT, "profiles", "conv3x3_tc_bf16__cnn4_layers.md")
     try:
         with open(p) as f:
             for line in f:
                 if line.startswith("| DRAM traffic / algorithmic bytes"):
-                    return float(line.split("|")[2].split("=")[-1].strip())
+                    num = den = 0.0
+                    for cell in line.split("|")[2:-1]:
+                        a, b = cell.split("=")[0].replace("MB", "").replace(",", "").split("/")
+                        num += float(a)
+                        den += float(b)
+                    return num / den if den > 0 else None
     except (OSError, ValueError, IndexError):
         return None
     return None
@@ -669,8 +675,9 @@ def ours(args):
         traffic = round(d["bytes"] / max(1, d["launches"]) * ratio) if ratio else None
         roof = {"bound": "tensor", "kernel": name, "achieved": round(achieved, 2), "peak": peak,
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "traffic_note": "ncu DRAM bytes of a 1,024-frame 128->128 launch relative to its algorithmic "
-                                "bytes, scaled to this run's algorithmic bytes per launch" if traffic else None,
+                "traffic_note": "ncu DRAM bytes of 1,024-frame launches of the four layer shapes relative to "
+                                "their algorithmic bytes, scaled to this run's algorithmic bytes per launch"
+                                if traffic else None,
                 "peak_source": f"bf16_tflops_sustained ({src})", "launches": d["launches"],
                 "avg_launch_ms": round(d["total_ms"] / max(1, d["launches"]), 4),
                 "note": "per-launch CUDA-event durations on each lane's stream; the two lanes' kernels overlap, "
