@@ -106,7 +106,12 @@ enum {
 /* Where the router's per-tuple cost comes from. */
 enum {
     HYDRO_COST_MODEL = 0,    /* flops per tuple of the UDF (or cost_hint): deterministic */
-    HYDRO_COST_MEASURED = 1  /* device time per evaluated tuple, from CUDA events */
+    HYDRO_COST_MEASURED = 1  /* device time per evaluated tuple (Sec. 4.2 profiles time per tuple):
+                                each stage's duration is taken on the device (global timer from
+                                the stage's first launch to the end of its compaction); c_i = the
+                                window's stage time / tuples evaluated.  Rank and cost policies
+                                with warmup_batches >= 1; orders then depend on timing, so counts
+                                are checked against each batch's reported order only */
 };
 
 /* UDF kinds. */
@@ -176,6 +181,8 @@ typedef struct hydro_batch_info {
     int64_t recheck_fp64[HYDRO_MAX_PREDICATES]; /* re-evaluated in FP64 (FP32 band) */
     int64_t cache_hits[HYDRO_MAX_PREDICATES];   /* evaluated tuples whose upstream output was cached */
     double device_ms;                           /* GPU time from the batch's first to last kernel */
+    int64_t stage_ns[HYDRO_MAX_PREDICATES];     /* HYDRO_COST_MEASURED: device ns of predicate i's stage
+                                                   in this batch (0 if it did not run), else 0 */
 } hydro_batch_info;
 
 /* Cumulative per-predicate statistics (Sec. 3.3 "Metadata for Data Routing"). */

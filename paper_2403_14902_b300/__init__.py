@@ -27,6 +27,7 @@ OK, EINVAL, ENOMEM, ECUDA, EAGAIN, ETIMEOUT, ESTATE, EDEVICE, ENOTFOUND, EUNSUPP
 TUPLE_F32, TUPLE_U8_FRAME = 0, 1
 POLICIES = {"rank": 0, "static": 1, "all": 2, "cost": 3, "selectivity": 4, "learned": 5}
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp64": 2, "tf32x3": 3, "bf16x3": 4, "fp8": 5}
+COSTS = {"model": 0, "measured": 1}
 UDF_MLP, UDF_CNN = 0, 1
 
 EXPORTED = ["hydro_default_config", "hydro_create_query", "hydro_add_predicate", "hydro_add_embedding",
@@ -69,7 +70,7 @@ class BatchInfo(ctypes.Structure):
                 ("passed", ctypes.c_int64 * MAX_PREDICATES), ("recheck_tf32", ctypes.c_int64 * MAX_PREDICATES),
                 ("recheck_fp32", ctypes.c_int64 * MAX_PREDICATES),
                 ("recheck_fp64", ctypes.c_int64 * MAX_PREDICATES), ("cache_hits", ctypes.c_int64 * MAX_PREDICATES),
-                ("device_ms", ctypes.c_double)]
+                ("device_ms", ctypes.c_double), ("stage_ns", ctypes.c_int64 * MAX_PREDICATES)]
 
 
 class PredStats(ctypes.Structure):
@@ -200,7 +201,7 @@ class Query:
                  precision: str = "fp32", warmup: int = 1, window: int = 8, lag: int = 1,
                  max_in_flight: int = 4, device: int = 0, stream=None, proxy_hidden: int = 64,
                  proxy_refresh: int = 16, proxy_epochs: int = 2, proxy_lr: float = 1e-3, proxy_seed: int = 1,
-                 lanes: int = 1):
+                 lanes: int = 1, cost: str = "model"):
         L = load()
         cfg = QueryConfig()
         L.hydro_default_config(ctypes.byref(cfg))
@@ -222,6 +223,7 @@ class Query:
         cfg.proxy_lr = proxy_lr
         cfg.proxy_seed = proxy_seed
         cfg.lanes = lanes
+        cfg.cost_source = COSTS[cost]
         self.kind = kind
         self.cfg = cfg
         self._h = ctypes.c_void_p()
@@ -334,7 +336,8 @@ class Query:
         d = dict(n=info.n, n_pass=info.n_pass, warmup=bool(info.warmup), order=list(info.order[:P]),
                  passed=list(info.passed[:P]), recheck_tf32=list(info.recheck_tf32[:P]),
                  recheck_fp32=list(info.recheck_fp32[:P]), cache_hits=list(info.cache_hits[:P]),
-                 recheck_fp64=list(info.recheck_fp64[:P]), device_ms=info.device_ms)
+                 recheck_fp64=list(info.recheck_fp64[:P]), device_ms=info.device_ms,
+                 stage_ns=list(info.stage_ns[:P]))
         return bitmap[:(n + 31) // 32], counts[:P], d
 
     def debug_trace(self, batch_id: int, n: int):

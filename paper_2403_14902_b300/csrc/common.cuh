@@ -28,6 +28,7 @@ struct StatRow {
     long long recheck32;      // re-evaluated in FP32 (CUDA cores)
     long long recheck64;      // re-evaluated in FP64
     long long hits;           // reuse-cache hits (shared upstream UDF outputs found cached)
+    long long ns;             // measured cost: device time of the stage (0 unless measured)
 };
 
 __device__ __forceinline__ float to_f(float v) { return v; }

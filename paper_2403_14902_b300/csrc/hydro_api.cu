@@ -884,6 +884,12 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
     const ProfCtx pc_main{batch, pi, SRC_MAIN}, pc_rtf{batch, pi, SRC_RTF}, pc_r32{batch, pi, SRC_R32},
         pc_r64{batch, pi, SRC_R64};
     int *miss_count = nullptr;
+    const bool measure = c.cost_source == HYDRO_COST_MEASURED;
+    StatRow *row = q->ring + (batch % q->ring_len) * kMaxPred + pi;
+    if (measure) {
+        launch_stage_start(row, q->st);
+        q->launches++;
+    }
     if (p.upstream) {
         miss_count = q->ints + 5;
         TRY(run_grouped(q, p, in_count, in_list, tuples, ids, (int)(batch + 1), std::max(n, 1), miss_count,
@@ -943,12 +949,11 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
     }
     launch_recheck_classify_f64(b64_count, b64_m, b64_t, q->rscore64, p.threshold, q->pass, q->d_err, q->st);
     q->launches += 2;   // recheck classify + compact
-    StatRow *row = q->ring + (batch % q->ring_len) * kMaxPred + pi;
     StatRow *rrow = (StatRow *)(slot.dres + kRowsOff) + pi;
     StatRow *warm = nullptr;
     if (adaptive(c.policy) && batch < c.warmup_batches) warm = q->warm + batch * kMaxPred + pi;
     launch_compact(in_count, in_list, q->pass, out_list, out_count, eval_all ? q->acc : nullptr, cnt_tf, cnt_32,
-                   b64_count, miss_count, row, rrow, warm, q->st);
+                   b64_count, miss_count, row, rrow, warm, q->st, measure ? 1 : 0);
     return HYDRO_OK;
 }
 
@@ -1203,8 +1208,11 @@ hydro_status hydro_create_query(const hydro_query_config *cfg, hydro_query **out
     if (c.precision != HYDRO_PREC_FP32 && c.precision != HYDRO_PREC_BF16)
         return fail(HYDRO_EINVAL, "precision must be FP32 or BF16");
 
-    if (c.cost_source != HYDRO_COST_MODEL)
-        return fail(HYDRO_EUNSUPPORTED, "only HYDRO_COST_MODEL is built");
+    if (c.cost_source != HYDRO_COST_MODEL && c.cost_source != HYDRO_COST_MEASURED)
+        return fail(HYDRO_EINVAL, "unknown cost source");
+    if (c.cost_source == HYDRO_COST_MEASURED &&
+        ((c.policy != HYDRO_POLICY_RANK && c.policy != HYDRO_POLICY_COST) || c.warmup_batches < 1))
+        return fail(HYDRO_EUNSUPPORTED, "measured cost needs the rank or cost policy and warmup_batches >= 1");
     if (c.warmup_batches < 0 || c.warmup_batches > 64) return fail(HYDRO_EINVAL, "warmup_batches must be 0..64");
     if (c.stats_window < 1 || c.stats_window > 1024) return fail(HYDRO_EINVAL, "stats_window must be 1..1024");
     if (c.route_lag < 0 || c.route_lag > 3) return fail(HYDRO_EINVAL, "route_lag must be 0..3");
@@ -1542,6 +1550,7 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
             }
             for (size_t e = 0; e < q->embs.size(); ++e) costs.cemb[e] = q->embs[e].cost;
             costs.n = n;
+            costs.measured = c.cost_source == HYDRO_COST_MEASURED ? 1 : 0;
             const int pol = (c.policy == HYDRO_POLICY_RANK || c.policy == HYDRO_POLICY_LEARNED) ? 0
                             : c.policy == HYDRO_POLICY_COST                                      ? 1
                                                                                                  : 2;
@@ -1683,6 +1692,7 @@ hydro_status hydro_poll_result(hydro_query *q, int64_t batch_id, uint32_t *pass_
             info->cache_hits[i] = rows[i].hits;
             info->recheck_fp32[i] = rows[i].recheck32;
             info->recheck_fp64[i] = rows[i].recheck64;
+            info->stage_ns[i] = q->cfg.cost_source == HYDRO_COST_MEASURED ? rows[i].ns : 0;
         }
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, slot->start, slot->done) == cudaSuccess) info->device_ms = ms;

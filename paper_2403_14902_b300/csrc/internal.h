@@ -31,6 +31,7 @@ struct RouterCosts {
     int group[8];
     long long cemb[8];
     long long n;   // tuples in the batch
+    int measured;  // 1: c_i = the window's stage time / tuples evaluated (ignores c, cemb)
 };
 
 // k_route.cu
@@ -45,10 +46,13 @@ void launch_recheck_classify_f32(const int *band_count_in, const int *band_m_in,
 void launch_recheck_classify_f64(const int *band_count_in, const int *band_m_in, const int *band_tuple_in,
                                  const double *scores_r, double t, unsigned char *pass, unsigned int *err,
                                  cudaStream_t st);
+// Measured cost: stamp the stage's start (device global timer) into its row;
+// the stage's compaction (measure = 1) turns it into the stage's duration.
+void launch_stage_start(StatRow *row, cudaStream_t st);
 void launch_compact(const int *count_in, const int *alive_in, const unsigned char *pass, int *alive_out,
                     int *count_out, unsigned char *acc, const int *bandt_count, const int *band32_count,
                     const int *band64_count, const int *miss_count, StatRow *row, StatRow *rrow, StatRow *warm,
-                    cudaStream_t st);
+                    cudaStream_t st, int measure = 0);
 
 // k_cache.cu: reuse cache of a shared upstream UDF's outputs, keyed by tuple id.
 // tags[id]: 0 absent, -1 prefilled, b+1 computed by batch b.

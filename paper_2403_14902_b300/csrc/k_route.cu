@@ -117,6 +117,14 @@ k_recheck_classify(const int *band_count_in, const int *band_m_in, const int *ba
     if (threadIdx.x == 0 && next_count) *next_count = base < next_cap ? base : next_cap;
 }
 
+__device__ __forceinline__ long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+
+__global__ void k_stage_start(StatRow *row) { row->ns = global_ns(); }
+
 // Close a stage: record statistics and either drop the failing tuples
 // (short-circuit) or AND the stage's verdict into the all-evaluate
 // accumulator.  row/rrow: this predicate's statistics in the ring and in the
@@ -124,7 +132,8 @@ k_recheck_classify(const int *band_count_in, const int *band_m_in, const int *ba
 __global__ void __launch_bounds__(kScanThreads)
 k_compact(const int *count_in, const int *alive_in, const unsigned char *pass, int *alive_out,
           int *count_out, unsigned char *acc, const int *bandt_count, const int *band32_count,
-          const int *band64_count, const int *miss_count, StatRow *row, StatRow *rrow, StatRow *warm) {
+          const int *band64_count, const int *miss_count, StatRow *row, StatRow *rrow, StatRow *warm,
+          int measure) {
     const int n = *count_in;
     int base = 0;
     for (int m0 = 0; m0 < n; m0 += kScanThreads) {
@@ -148,6 +157,8 @@ k_compact(const int *count_in, const int *alive_in, const unsigned char *pass, i
         r.recheck32 = band32_count ? *band32_count : 0;
         r.recheck64 = band64_count ? *band64_count : 0;
         r.hits = miss_count ? (long long)n - *miss_count : 0;
+        // measured: the stage's start stamp (k_stage_start) to now
+        r.ns = measure ? global_ns() - row->ns : 0;
         *row = r;
         *rrow = r;
         if (warm) *warm = r;
@@ -192,7 +203,7 @@ __global__ void k_router(const StatRow *ring, int ring_len, const StatRow *warm,
                          long long lo, long long last, int P, int policy, RouterCosts costs, const int *vmiss,
                          int *order_out) {
     const int i = threadIdx.x;
-    long long E = 0, Pp = 0;
+    long long E = 0, Pp = 0, NS = 0;
     // per-batch cost scaled by the batch size: c*n (+ misses * embedding cost)
     unsigned long long cost = 0;
     if (i < P) {
@@ -206,23 +217,35 @@ __global__ void k_router(const StatRow *ring, int ring_len, const StatRow *warm,
             const StatRow r = ring[(b % ring_len) * kMaxPred + i];
             E += r.evaluated;
             Pp += r.passed;
+            NS += r.ns;
         }
         if (E == 0) {
             for (int w = 0; w < n_warm_visible; ++w) {
                 E += warm[w * kMaxPred + i].evaluated;
                 Pp += warm[w * kMaxPred + i].passed;
+                NS += warm[w * kMaxPred + i].ns;
             }
         }
     }
+    // measured cost per tuple (ns); a predicate without evaluations costs 0
+    const double cm = costs.measured && E > 0 ? (double)NS / (double)E : 0.0;
     int pos = 0;
     for (int j = 0; j < P; ++j) {
         const long long Ej = __shfl_sync(0xffffffffu, E, j);
         const long long Pj = __shfl_sync(0xffffffffu, Pp, j);
         const unsigned long long cj = __shfl_sync(0xffffffffu, cost, j);
+        const double cmj = __shfl_sync(0xffffffffu, cm, j);
         if (i >= P || j == i) continue;
         const unsigned long long ci = cost;
         bool before;   // does j go before i?
-        if (policy == 0) {
+        if (costs.measured && policy == 0) {
+            // measured rank c/(1-s) in double (the costs are measurements, not exact integers)
+            const double rj = cmj * (double)(Ej + 2) / (double)(Ej - Pj + 1);
+            const double ri = cm * (double)(E + 2) / (double)(E - Pp + 1);
+            before = rj < ri || (rj == ri && j < i);
+        } else if (costs.measured && policy == 1) {
+            before = cmj < cm || (cmj == cm && j < i);
+        } else if (policy == 0) {
             // rank c/(1-s), s = (p+1)/(e+2): c(e+2)/(e-p+1)
             const unsigned __int128 lhs = (unsigned __int128)cj * (unsigned long long)(Ej + 2) *
                                           (unsigned long long)(E - Pp + 1);
@@ -276,10 +299,12 @@ void launch_recheck_classify_f64(const int *band_count_in, const int *band_m_in,
 void launch_compact(const int *count_in, const int *alive_in, const unsigned char *pass, int *alive_out,
                     int *count_out, unsigned char *acc, const int *bandt_count, const int *band32_count,
                     const int *band64_count, const int *miss_count, StatRow *row, StatRow *rrow, StatRow *warm,
-                    cudaStream_t st) {
+                    cudaStream_t st, int measure) {
     k_compact<<<1, kScanThreads, 0, st>>>(count_in, alive_in, pass, alive_out, count_out, acc, bandt_count,
-                                          band32_count, band64_count, miss_count, row, rrow, warm);
+                                          band32_count, band64_count, miss_count, row, rrow, warm, measure);
 }
+
+void launch_stage_start(StatRow *row, cudaStream_t st) { k_stage_start<<<1, 1, 0, st>>>(row); }
 
 void launch_acc_to_alive(const unsigned char *acc, int n, int *alive_out, int *count_out, cudaStream_t st) {
     k_acc_to_alive<<<1, kScanThreads, 0, st>>>(acc, n, alive_out, count_out);

@@ -126,6 +126,16 @@ def test_create_rejects_bad_config_without_touching_a_device():
     cfg.route_lag = 3
     assert L.hydro_create_query(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
     cfg.lanes = 1
+    cfg.cost_source = 2                # no such cost source
+    assert L.hydro_create_query(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
+    cfg.cost_source = H.COSTS["measured"]
+    cfg.warmup_batches = 0             # measured cost needs the warmup statistics
+    assert L.hydro_create_query(ctypes.byref(cfg), ctypes.byref(h)) == H.EUNSUPPORTED
+    cfg.warmup_batches = 1
+    cfg.policy = H.POLICIES["static"]
+    assert L.hydro_create_query(ctypes.byref(cfg), ctypes.byref(h)) == H.EUNSUPPORTED
+    cfg.policy = H.POLICIES["rank"]
+    cfg.cost_source = H.COSTS["model"]
     assert L.hydro_create_query(None, ctypes.byref(h)) == H.EINVAL
 
 

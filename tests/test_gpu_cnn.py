@@ -28,6 +28,31 @@ def cnn4():
                 calib_d=torch.from_numpy(calib[:64]).cuda(), rms=np.sqrt((S ** 2).mean(axis=0)))
 
 
+@pytest.mark.parametrize("policy,precision,lanes", [("rank", "fp32", 1), ("cost", "fp32", 1), ("rank", "bf16", 2)])
+def test_measured_cost_routing(cnn4, policy, precision, lanes):
+    """Measured cost (device time per evaluated tuple): the orders depend on
+    timing, so each batch is checked against its own reported order: exact
+    pass set, evaluation and pass counts from the pass matrix under that
+    order; every stage reports its time, and the 8-layer UDF costs more per
+    tuple than the 2-layer one, so both policies evaluate it last."""
+    w = cnn4["w"]
+    q = make_query(w, cnn4["th"], batch=B_SMALL, policy=policy, precision=precision, cost="measured",
+                   lag=lanes - 1, lanes=lanes)
+    res = run_stream(q, cnn4["Fd"], B_SMALL)
+    for b, (bits, counts, info) in enumerate(res):
+        pm = cnn4["pm"][b * B_SMALL:(b + 1) * B_SMALL]
+        assert np.array_equal(bits, O.result_bits(pm)), f"batch {b}: pass set"
+        assert sorted(info["order"]) == [0, 1, 2, 3]
+        want = [len(pm)] * 4 if info["warmup"] else O.static_counts(pm, info["order"]).tolist()
+        assert counts.tolist() == want, f"batch {b}: counts {counts} vs {want}"
+        assert all(t > 0 for t in info["stage_ns"])
+        if b == 0:
+            assert info["warmup"] and info["stage_ns"][3] > info["stage_ns"][0]
+        else:
+            assert info["order"][-1] == 3, f"batch {b}: order {info['order']}"
+    q.close()
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 @pytest.mark.parametrize("policy", ["rank", "static", "all"])
 def test_small_stream_parity(cnn4, precision, policy):
