@@ -1092,6 +1092,58 @@ def ours_conv_bf16(args):
     }
 
 
+# ---------------------------------------------------------------- peaks
+
+def ours_peaks(args):
+    """Dense matrix-multiply rates of the arithmetic types the recheck levels
+    and the FP8 sessions use, measured with the vendor library (torch matmul /
+    _scaled_mm) as roofline denominators: BF16 (cross-check), TF32, FP32
+    (tensor cores off: CUDA cores), FP64 and FP8 E4M3."""
+    import torch
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    out = {}
+
+    def rate(fn, flops, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return flops * reps / (e0.elapsed_time(e1) / 1000.0) / 1e12
+
+    n = 8192
+    a = torch.randn(n, n, device="cuda")
+    b = torch.randn(n, n, device="cuda")
+    a16, b16 = a.bfloat16(), b.bfloat16()
+    out["bf16_tflops"] = rate(lambda: a16 @ b16, 2.0 * n ** 3, 50)
+    torch.backends.cuda.matmul.allow_tf32 = True
+    out["tf32_tflops"] = rate(lambda: a @ b, 2.0 * n ** 3, 30)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out["fp32_tflops"] = rate(lambda: a @ b, 2.0 * n ** 3, 5)
+    m = 4096
+    a64, b64 = a[:m, :m].double(), b[:m, :m].double()
+    out["fp64_tflops"] = rate(lambda: a64 @ b64, 2.0 * m ** 3, 3)
+    try:
+        a8 = a.to(torch.float8_e4m3fn)
+        b8 = b.to(torch.float8_e4m3fn).t()   # column-major second operand
+        one = torch.ones((), device="cuda")
+        out["fp8_e4m3_tflops"] = rate(lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one,
+                                                               out_dtype=torch.bfloat16), 2.0 * n ** 3, 80)
+    except Exception as e:   # noqa: BLE001
+        out["fp8_e4m3_tflops"] = None
+        out["fp8_note"] = f"unavailable: {type(e).__name__}: {str(e)[:120]}"
+    props = torch.cuda.get_device_properties(local)
+    return {"metric": "dense matmul rate by arithmetic type (vendor library)", "value": round(out["bf16_tflops"], 1),
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": 1, "warmup": 3, "higher_is_better": True,
+            "config": {"workload": f"peaks: {n}^3 GEMMs (FP64 {m}^3)", "sms": props.multi_processor_count},
+            "peaks": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in out.items()}}
+
+
 # ---------------------------------------------------------------- reference arm
 
 def reference(args):
@@ -1106,6 +1158,8 @@ def reference(args):
         return reference_gemm(args)
     if name == "conv_bf16":
         return reference_conv(args)
+    if name == "peaks":
+        return {"impl": "reference", "unavailable": "the peaks probe has no oracle counterpart"}
     w = D.workload(name)
     th = thresholds(name)
     if name == "mq64":
@@ -1219,14 +1273,14 @@ def main(argv=None):
     ap.add_argument("--no-graphs", action="store_true", help="with --headline-only: launch without CUDA graphs")
     ap.add_argument("--lanes", type=int, default=4, help="cnn4: stream lanes of the query (1..4)")
     ap.add_argument("--lag", type=int, default=3, help="cnn4: route lag (>= lanes - 1)")
-    ap.add_argument("--workload", choices=["cnn4", "drift5", "drift6", "mq64", "gemm_bf16", "conv_bf16"],
+    ap.add_argument("--workload", choices=["cnn4", "drift5", "drift6", "mq64", "gemm_bf16", "conv_bf16", "peaks"],
                     default=WORKLOAD)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         out = reference(args)
     else:
         out = {"cnn4": ours, "drift5": ours_drift5, "drift6": ours_drift6, "mq64": ours_mq64,
-               "gemm_bf16": ours_gemm_bf16, "conv_bf16": ours_conv_bf16}[args.workload](args)
+               "gemm_bf16": ours_gemm_bf16, "conv_bf16": ours_conv_bf16, "peaks": ours_peaks}[args.workload](args)
     if out is not None:
         print(json.dumps(out), flush=True)
 

@@ -54,6 +54,22 @@ def test_measured_cost_routing(cnn4, policy, precision, lanes):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_cnn_edge_batches(cnn4, precision):
+    """Empty, one-frame and ragged batches (below one 128-pixel-row tile of
+    frames, not a multiple of the 16-frame batch), static declared order."""
+    import paper_2403_14902_b300 as H
+    w = cnn4["w"]
+    pm = cnn4["pm"]
+    for n in [0, 1, 5, 16]:
+        q = make_query(w, cnn4["th"], batch=B_SMALL, policy="static", precision=precision)
+        bid = q.submit(cnn4["Fd"][:n], n=n)
+        words, counts, _ = q.poll(bid)
+        assert np.array_equal(H.bits_from_words(words, n), O.result_bits(pm[:n]))
+        assert counts.tolist() == O.static_counts(pm[:n], [0, 1, 2, 3]).tolist()
+        q.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
 @pytest.mark.parametrize("policy", ["rank", "static", "all"])
 def test_small_stream_parity(cnn4, precision, policy):
     w = cnn4["w"]
