@@ -121,17 +121,82 @@ def aggregate(units_per_rank: int, steps: int, seconds_max: float, world: int) -
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+    """SM clock and clock-event reasons during the timed region, read through
+    NVML every 5 ms by a thread (plus one reading at start and one at stop,
+    so that a short region still has samples); nvidia-smi every 200 ms when
+    NVML is not importable.  Reads only."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.nv = None
+        self.handle = None
+        self.samples = []
+        self.thread = None
+        self.stop_flag = None
+
+    # NVML clock-event reason bits (nvml.h): hw slowdown, hw thermal, sw thermal, sw power cap
+    MASKS = (0x8, 0x40, 0x20, 0x4)
+
+    def _nvml_handle(self):
+        """The driver's NVML through ctypes, and the handle of this CUDA device
+        (by UUID: CUDA may renumber the visible GPUs; else by index)."""
+        import ctypes
+
+        import torch
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        try:
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(self.gpu).uuid)
+            rc = lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h))
+        except Exception:   # noqa: BLE001
+            rc = -1
+        if rc != 0 and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(h)) != 0:
+            raise RuntimeError("no NVML handle")
+        try:
+            reasons = lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            reasons = lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return (lib, reasons), h
+
+    def _read(self):
+        import ctypes
+        (lib, reasons), h = self.nv, self.handle
+        sm, mx, bits = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        ok = (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(sm)) == 0 and          # 1: NVML_CLOCK_SM
+              lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+              reasons(h, ctypes.byref(bits)) == 0)
+        if not ok:
+            raise RuntimeError("NVML read failed")
+        names = {n for n, m in zip(self.NAMES, self.MASKS) if bits.value & m}
+        self.samples.append((float(sm.value), float(mx.value), names))
 
     def start(self):
+        import threading
+        try:
+            self.nv, self.handle = self._nvml_handle()
+            self._read()
+        except Exception:   # noqa: BLE001
+            self.nv = None
+        if self.nv is not None:
+            self.stop_flag = threading.Event()
+
+            def loop():
+                while not self.stop_flag.wait(0.005):
+                    try:
+                        self._read()
+                    except RuntimeError:
+                        return
+            self.thread = threading.Thread(target=loop, daemon=True)
+            self.thread.start()
+            return
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
@@ -142,6 +207,18 @@ class ClockSampler:
             self.proc = None
 
     def stop(self) -> dict:
+        if self.nv is not None:
+            self.stop_flag.set()
+            self.thread.join()
+            try:
+                self._read()
+            except RuntimeError:
+                pass
+            sm = [a for a, _, _ in self.samples]
+            reasons = set().union(*[r for _, _, r in self.samples]) if self.samples else set()
+            return {"sm_mhz": float(np.median(sm)) if sm else None,
+                    "sm_max_mhz": max(b for _, b, _ in self.samples) if sm else None,
+                    "reasons": sorted(reasons), "samples": len(sm), "source": "nvml"}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -150,7 +227,6 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
@@ -161,12 +237,12 @@ class ClockSampler:
                     mx.append(float(parts[2]))
                 except ValueError:
                     continue
-                for n, v in zip(names, parts[5:9]):
+                for n, v in zip(self.NAMES, parts[5:9]):
                     if v.lower().startswith("active"):
                         reasons.add(n)
         os.unlink(self.path)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi"}
 
 
 # ---------------------------------------------------------------- our arm
@@ -477,11 +553,12 @@ def ours_drift6(args):
         results[name] = entry
     # the same query as a one-query session: BF16 tensor cores, CUDA graphs,
     # per-tuple orders from the proxy (learned) or per-batch rank orders
-    def session(learned, precision, K):
+    def session(learned, precision, K, policy="rank"):
         # each Adam step of the proxy trains on a moving 8,192-row window of a stored step
         s = H.Session(dim=w.dim, max_step_tuples=K * w.batch, precision=precision, graphs=True, autotune=True,
                       max_in_flight=2, stream=stream, learned=learned, proxy_refresh=w.extra["refresh"],
-                      proxy_hidden=w.extra["proxy_hidden"], batches_per_step=K, lag=K - 1, proxy_rows=8192)
+                      proxy_hidden=w.extra["proxy_hidden"], batches_per_step=K, lag=K - 1, proxy_rows=8192,
+                      policy=policy)
         for i in range(len(w.udfs)):
             s.add_udf(full[i])
         s.add_query(list(range(len(w.udfs))), th)
@@ -510,13 +587,18 @@ def ours_drift6(args):
         for item in pending:
             drain(item)
         return npass
-    DK = 8   # routing batches per step of the session arms (route lag DK - 1)
+    # routing batches per step of the session arms (route lag DK - 1): 16 batches = one proxy
+    # refresh per step
+    DK = 16
     for name, learned, precision, K in [("learned_session_bf16", True, "bf16", DK),
+                                        ("learned_session_bf16_k8", True, "bf16", 8),
                                         ("learned_session_bf16_k4", True, "bf16", 4),
                                         ("learned_session_bf16_k1", True, "bf16", 1),
                                         ("rank_session_bf16", False, "bf16", DK),
+                                        ("static_session_bf16", False, "bf16", DK),
+                                        ("static_session_fp32", False, "fp32", DK),
                                         ("learned_session_fp32", True, "fp32", DK)]:
-        s = session(learned, precision, K)
+        s = session(learned, precision, K, "static" if name.startswith("static") else "rank")
         f = lambda: run_session(s)  # noqa: E731
         for _ in range(args.warmup):
             f()
@@ -606,6 +688,8 @@ def ours_drift6(args):
         "speedup_vs_static_fp32": round(a["value"] / results["declared_static"]["value"], 3),
         "speedup_vs_best_static_fp32": round(a["value"] / results["best_static"]["value"], 3),
         "speedup_vs_rank_session_bf16": round(a["value"] / results["rank_session_bf16"]["value"], 3),
+        "speedup_vs_static_session_fp32": round(a["value"] / results["static_session_fp32"]["value"], 3),
+        "speedup_vs_static_session_bf16": round(a["value"] / results["static_session_bf16"]["value"], 3),
         "pass_count_per_step": a["pass_count"],
         "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3)} for k, v in prof.items()},
     }
@@ -773,9 +857,9 @@ def ours_mq64(args):
 
     plans = {1: dev_plan}
 
-    def make(precision, graphs=True, K=1):
+    def make(precision, graphs=True, K=1, policy="rank"):
         s = H.Session(dim=w.dim, max_step_tuples=cap * K, precision=precision, graphs=graphs, autotune=True,
-                      max_in_flight=2, stream=stream, batches_per_step=K, lag=K - 1)
+                      max_in_flight=2, stream=stream, batches_per_step=K, lag=K - 1, policy=policy)
         for layers in pool:
             s.add_udf(layers)
         for q in range(Q):
@@ -809,14 +893,16 @@ def ours_mq64(args):
     results = {}
     # headline: BF16, graphs, four batches of every query per step (route lag 3)
     HEAD, HK = "bf16_graphs_k4", 4
-    variants = [(HEAD, "bf16", True, HK), ("fp8_graphs_k4", "fp8", True, 4), ("bf16_graphs_k2", "bf16", True, 2),
+    variants = [(HEAD, "bf16", True, HK), ("bf16_graphs_k8", "bf16", True, 8), ("fp8_graphs_k4", "fp8", True, 4),
+                ("bf16_graphs_k2", "bf16", True, 2),
                 ("bf16_graphs_k1", "bf16", True, 1), ("fp32_graphs_k1", "fp32", True, 1),
-                ("bf16_no_graphs_k1", "bf16", False, 1)]
+                ("bf16_no_graphs_k1", "bf16", False, 1), ("static_bf16_graphs_k4", "bf16", True, 4),
+                ("static_fp32_graphs_k4", "fp32", True, 4)]
     if args.headline_only:
         # profilers cannot see kernels inside graphs with conditional nodes: launch kernel by kernel
         variants = [(HEAD, "bf16", not args.no_graphs, HK)]
     for name, precision, graphs, K in variants:
-        s = make(precision, graphs, K)
+        s = make(precision, graphs, K, "static" if name.startswith("static") else "rank")
         if K > 1:
             run_all(s)   # builds this K's device plan outside the timed region
         for _ in range(args.warmup):
@@ -972,6 +1058,8 @@ def ours_mq64(args):
                       for k, v in results.items() if k != HEAD},
         "speedup_vs_sequential_fp32": round(a["value"] / results["sequential_fp32"]["value"], 3),
         "speedup_vs_session_fp32": round(a["value"] / results["fp32_graphs_k1"]["value"], 3),
+        "speedup_vs_static_session_fp32_k4": round(a["value"] / results["static_fp32_graphs_k4"]["value"], 3),
+        "speedup_vs_static_session_bf16_k4": round(a["value"] / results["static_bf16_graphs_k4"]["value"], 3),
         "pass_count_per_step": a["pass_count"],
         "recheck": {"evaluated": a["evaluated"], "split_bf16": a["recheck_split"], "fp32": a["recheck_fp32"],
                     "fp64": a["recheck_fp64"]},

@@ -382,7 +382,7 @@ HYDRO_API hydro_status hydro_selftest_bounded_wait(int32_t device, int64_t limit
  * Its pass set, orders and counts therefore equal those of that query run
  * alone over the same chunks.
  */
-#define HYDRO_MAX_QUERIES 256
+#define HYDRO_MAX_QUERIES 512
 #define HYDRO_MAX_POOL 8
 
 typedef struct hydro_session hydro_session;
@@ -416,7 +416,8 @@ typedef struct hydro_session_config {
     int32_t proxy_epochs;     /* learned: passes over the stored steps per training (default 1) */
     float proxy_lr;           /* learned: Adam learning rate (default 1e-3) */
     int32_t proxy_seed;       /* learned: seed of the proxy's initial weights */
-    int32_t batches_per_step; /* K, 1..8: routing batches of each query one step may hold; with K > 1
+    int32_t batches_per_step; /* K, 1..32 (n_queries x K <= 512): routing batches of each query one
+                                 step may hold; with K > 1
                                  counts (submit) and the per-query results (poll) have n_queries x K
                                  entries, entry q K + k being query q's k-th batch of the step */
     int32_t route_lag;        /* a query's batch b is routed on its batches <= b - 1 - route_lag
@@ -428,6 +429,9 @@ typedef struct hydro_session_config {
                                  (0: all of them); a contiguous window that moves on by
                                  proxy_rows at every Adam step, so that the stored rows are
                                  used in turn */
+    int32_t policy;           /* HYDRO_POLICY_RANK (default: per-batch rank order) or
+                                 HYDRO_POLICY_STATIC (every batch in the query's declared slot
+                                 order, no warmup batches) */
 } hydro_session_config;
 
 /* Per query result of one step (hydro_session_poll). */

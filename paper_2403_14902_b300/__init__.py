@@ -40,7 +40,7 @@ EXPORTED = ["hydro_default_config", "hydro_create_query", "hydro_add_predicate",
             "hydro_session_udf_scores", "hydro_session_submit", "hydro_session_poll", "hydro_session_tuning",
             "hydro_session_profile", "hydro_session_profile_read", "hydro_session_debug_trace",
             "hydro_session_destroy", "hydro_destroy_query", "hydro_last_error"]
-MAX_QUERIES = 256
+MAX_QUERIES = 512
 MAX_POOL = 8
 
 
@@ -93,7 +93,7 @@ class SessionConfig(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("learned", ctypes.c_int32), ("proxy_hidden", ctypes.c_int32),
                 ("proxy_refresh", ctypes.c_int32), ("proxy_epochs", ctypes.c_int32), ("proxy_lr", ctypes.c_float),
                 ("proxy_seed", ctypes.c_int32), ("batches_per_step", ctypes.c_int32), ("route_lag", ctypes.c_int32),
-                ("fp8_min_width", ctypes.c_int32), ("proxy_rows", ctypes.c_int32)]
+                ("fp8_min_width", ctypes.c_int32), ("proxy_rows", ctypes.c_int32), ("policy", ctypes.c_int32)]
 
 
 class StepQuery(ctypes.Structure):
@@ -423,7 +423,8 @@ class Session:
                  window: int = 8, graphs: bool = True, autotune: bool = True, max_in_flight: int = 2,
                  device: int = 0, stream=None, learned: bool = False, proxy_hidden: int = 64,
                  proxy_refresh: int = 16, proxy_epochs: int = 1, proxy_lr: float = 1e-3, proxy_seed: int = 1,
-                 batches_per_step: int = 1, lag: int = 0, fp8_min_width: int = 0, proxy_rows: int = 0):
+                 batches_per_step: int = 1, lag: int = 0, fp8_min_width: int = 0, proxy_rows: int = 0,
+                 policy: str = "rank"):
         L = load()
         cfg = SessionConfig()
         L.hydro_session_default_config(ctypes.byref(cfg))
@@ -447,6 +448,7 @@ class Session:
         cfg.route_lag = lag
         cfg.fp8_min_width = fp8_min_width
         cfg.proxy_rows = proxy_rows
+        cfg.policy = POLICIES[policy]
         self.K = batches_per_step
         self._h = ctypes.c_void_p()
         _check(L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(self._h)), "hydro_session_create")

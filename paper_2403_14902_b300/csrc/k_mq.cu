@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_mq_init(MqDev d, Cond round0) {
             if (s_off[mid] <= e) lo = mid;
             else hi = mid - 1;
         }
-        d.qid[e] = (unsigned char)lo;
+        d.qid[e] = (unsigned short)lo;
         d.alive[0][e] = e;
         d.visited[e] = 0;
         d.label[e] = 0;
@@ -152,6 +152,11 @@ __global__ void k_mq_router(MqDev d, MqHist h) {
     // sub-batches are filled in order, so this is the query's batch bdone + k
     const long long b = h.bdone[qq] + (q - qq * d.K);
     if (i == 0) d.bidx[q] = b;
+    if (h.static_order) {
+        if (i == 0) d.evall[q] = 0;
+        if (i < kMqSlots) d.order[q * kMqSlots + i] = (unsigned char)i;
+        return;
+    }
     const long long last = b - 1 - h.lag;
     if (b < h.warmup || last < 0) {
         if (i == 0) d.evall[q] = b < h.warmup ? 1 : 0;

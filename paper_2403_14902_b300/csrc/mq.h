@@ -63,7 +63,7 @@ struct MqDev {
     int K;                         // batches per query per step
     const StepHdr *hdr;
     int *off;                      // [Q+1] stacked offsets of the step
-    unsigned char *qid;            // [cap] query of each stacked tuple
+    unsigned short *qid;           // [cap] virtual query of each stacked tuple
     const unsigned char *np;       // [Q / K] predicates per query
     const unsigned char *udf;      // [Q / K][8] pool UDF of each slot
     const double *thr;             // [Q / K][8] thresholds
@@ -95,6 +95,7 @@ struct MqHist {
     int warmup, window;
     int lag;                       // batch b is routed on batches <= b - 1 - lag
     long long *bdone;              // [queries] batches completed
+    int static_order;              // 1: every batch in declared slot order, no warmup batches
 };
 
 // One depth of the stacked grouped FP32 layers.  Group g's rows are

@@ -681,7 +681,7 @@ hydro_status finalize(hydro_session *s) {
     TRY(dalloc(s, &s->d_hdr, sizeof(StepHdr)));
     d.hdr = s->d_hdr;
     TRY(dalloc(s, &d.off, sizeof(int) * (Q + 1)));
-    TRY(dalloc(s, &d.qid, (size_t)cap));
+    TRY(dalloc(s, &d.qid, sizeof(unsigned short) * (size_t)cap));
     TRY(dalloc(s, &d.order, (size_t)Q * kMqSlots));
     TRY(dalloc(s, &d.evall, (size_t)Q));
     TRY(dalloc(s, &d.bidx, sizeof(long long) * Q));
@@ -813,6 +813,7 @@ hydro_status finalize(hydro_session *s) {
     MqHist &h = s->h;
     h.R = c.stats_window + c.route_lag + 2;
     h.lag = c.route_lag;
+    h.static_order = c.policy == HYDRO_POLICY_STATIC ? 1 : 0;
     h.warmup = c.warmup_batches;
     h.window = c.stats_window;
     TRY(dalloc(s, &h.ring, sizeof(StatRow) * (size_t)NQ * h.R * kMqSlots));
@@ -1034,10 +1035,14 @@ hydro_status hydro_session_create(const hydro_session_config *cfg, hydro_session
     if (cfg->precision == HYDRO_PREC_FP8 && (cfg->dim % 128 || cfg->fp8_min_width < 0))
         return fail(HYDRO_EINVAL, "FP8 sessions need dim a multiple of 128 and fp8_min_width >= 0");
     if (cfg->warmup_batches < 0 || cfg->stats_window < 1) return fail(HYDRO_EINVAL, "bad warmup/window");
+    if (cfg->policy != HYDRO_POLICY_RANK && cfg->policy != HYDRO_POLICY_STATIC)
+        return fail(HYDRO_EINVAL, "session policy must be RANK or STATIC");
+    if (cfg->learned && cfg->policy != HYDRO_POLICY_RANK)
+        return fail(HYDRO_EINVAL, "learned sessions fall back to rank routing (policy RANK)");
     if (cfg->max_in_flight < 1 || cfg->max_in_flight > 8) return fail(HYDRO_EINVAL, "max_in_flight outside 1..8");
-    if (cfg->batches_per_step < 1 || cfg->batches_per_step > 8 || cfg->route_lag < cfg->batches_per_step - 1 ||
+    if (cfg->batches_per_step < 1 || cfg->batches_per_step > 32 || cfg->route_lag < cfg->batches_per_step - 1 ||
         cfg->route_lag > 64)
-        return fail(HYDRO_EINVAL, "batches_per_step 1..8 with route_lag >= batches_per_step - 1 (<= 64)");
+        return fail(HYDRO_EINVAL, "batches_per_step 1..32 with route_lag >= batches_per_step - 1 (<= 64)");
     if (cfg->learned && (cfg->proxy_hidden < 0 || cfg->proxy_hidden > 1024 || cfg->proxy_refresh < 1 ||
                          cfg->proxy_refresh > 256 || cfg->proxy_epochs < 0 || !(cfg->proxy_lr > 0.f) ||
                          cfg->proxy_rows < 0))
@@ -1406,8 +1411,9 @@ hydro_status hydro_session_debug_trace(hydro_session *s, int64_t step, uint8_t *
     if (s->d.order_t) {
         CU(cudaMemcpy(order, s->d.order_t, n * kMqSlots, cudaMemcpyDeviceToHost));
     } else {
-        std::vector<unsigned char> qid(n), ord((size_t)s->d.Q * kMqSlots);
-        CU(cudaMemcpy(qid.data(), s->d.qid, n, cudaMemcpyDeviceToHost));
+        std::vector<unsigned short> qid(n);
+        std::vector<unsigned char> ord((size_t)s->d.Q * kMqSlots);
+        CU(cudaMemcpy(qid.data(), s->d.qid, sizeof(unsigned short) * n, cudaMemcpyDeviceToHost));
         CU(cudaMemcpy(ord.data(), s->d.order, ord.size(), cudaMemcpyDeviceToHost));
         for (size_t e = 0; e < n; ++e) memcpy(order + e * kMqSlots, ord.data() + (size_t)qid[e] * kMqSlots, kMqSlots);
     }

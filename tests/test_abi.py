@@ -87,6 +87,14 @@ def test_session_defaults_and_rejections_without_a_device():
     cfg.dim = 512
     cfg.fp8_min_width = -1
     assert L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
+    cfg.precision = H.PRECISIONS["bf16"]
+    cfg.policy = H.POLICIES["all"]     # sessions route by rank or keep the declared order
+    assert L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
+    cfg.policy = H.POLICIES["static"]
+    cfg.learned = 1                    # a learned session falls back to rank routing
+    assert L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
+    cfg.learned = 0
+    cfg.policy = H.POLICIES["rank"]
     cfg.precision = 6                  # no such precision
     cfg.fp8_min_width = 0
     assert L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL

@@ -21,10 +21,10 @@ def mq_thresholds():
 
 
 def make_session(w, qs, th, *, precision="fp32", cap, graphs=True, autotune=True, warmup=1, window=8,
-                 queries=None):
+                 queries=None, policy="rank"):
     import paper_2403_14902_b300 as H
     s = H.Session(dim=w.dim, max_step_tuples=cap, precision=precision, graphs=graphs, autotune=autotune,
-                  warmup=warmup, window=window)
+                  warmup=warmup, window=window, policy=policy)
     for layers in D.mq_pool_weights(w):
         s.add_udf(layers)
     for q in (range(len(qs)) if queries is None else queries):
@@ -50,7 +50,7 @@ def run_session(s, streams, chunk):
     return out
 
 
-def oracle_per_query(w, qs, th, streams, chunk, queries, warmup=1, window=8):
+def oracle_per_query(w, qs, th, streams, chunk, queries, warmup=1, window=8, policy="rank"):
     pool = D.mq_pool_weights(w)
     sims = {}
     for k, q in enumerate(queries):
@@ -58,7 +58,7 @@ def oracle_per_query(w, qs, th, streams, chunk, queries, warmup=1, window=8):
         S = O.udf_scores("vec", streams[k], [pool[u] for u in Q["udfs"]])
         pm = O.pass_matrix(S, th[q])
         costs = [O.mlp_flops(w.udfs[u]) for u in Q["udfs"]]
-        sims[k] = O.simulate(pm, chunk, policy="rank", costs=costs, warmup=warmup, window=window, lag=0)
+        sims[k] = O.simulate(pm, chunk, policy=policy, costs=costs, warmup=warmup, window=window, lag=0)
     return sims
 
 
@@ -136,6 +136,22 @@ def test_session_bf16_exact(small, autotune):
         for rec in t:
             assert rec["tile_n"] in (64, 128, 256) and rec["N"] % rec["tile_n"] == 0
             assert rec["us"][rec["tile_n"].bit_length() - 7] == min(u for u in rec["us"] if u > 0)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_session_static_order_exact(small, precision):
+    """Static policy: every batch of every query in its declared slot order,
+    no warmup batch; counts are the pass matrix's static counts."""
+    import torch
+    s = make_session(small["w"], small["qs"], small["th"], precision=precision, policy="static",
+                     cap=len(small["queries"]) * small["chunk"], queries=small["queries"])
+    s.calibrate(torch.from_numpy(small["calib"]).cuda())
+    res = run_session(s, small["streams"], small["chunk"])
+    sims = oracle_per_query(small["w"], small["qs"], small["th"], small["streams"], small["chunk"],
+                            small["queries"], policy="static")
+    check_steps(res, sims, len(small["queries"]))
+    assert not any(r["warmup"] for _, _, per in res for r in per)
     s.close()
 
 
@@ -397,7 +413,8 @@ def run_session_multi(s, streams, chunk, K):
     return out
 
 
-@pytest.mark.parametrize("K,lag,precision", [(2, 1, "bf16"), (3, 2, "fp32"), (2, 3, "bf16")])
+@pytest.mark.parametrize("K,lag,precision", [(2, 1, "bf16"), (3, 2, "fp32"), (2, 3, "bf16"), (16, 15, "bf16"),
+                                                   (32, 31, "bf16")])
 def test_session_several_batches_per_step(small, K, lag, precision):
     """Each step holds up to K consecutive batches of every query, routed with
     lag >= K - 1: orders, counts and pass sets equal the oracle's per-query
