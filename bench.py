@@ -1359,7 +1359,7 @@ def main(argv=None):
     ap.add_argument("--headline-only", action="store_true",
                     help="mq64: time the headline variant only (for profiling runs)")
     ap.add_argument("--no-graphs", action="store_true", help="with --headline-only: launch without CUDA graphs")
-    ap.add_argument("--lanes", type=int, default=4, help="cnn4: stream lanes of the query (1..4)")
+    ap.add_argument("--lanes", type=int, default=4, help="cnn4: stream lanes of the query (1..8)")
     ap.add_argument("--lag", type=int, default=3, help="cnn4: route lag (>= lanes - 1)")
     ap.add_argument("--workload", choices=["cnn4", "drift5", "drift6", "mq64", "gemm_bf16", "conv_bf16", "peaks"],
                     default=WORKLOAD)

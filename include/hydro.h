@@ -134,7 +134,7 @@ typedef struct hydro_query_config {
     int32_t warmup_batches;  /* adaptive policies: the first batches evaluate every
                                 predicate on every tuple (Sec. 4.1 "Warmup Phase") */
     int32_t stats_window;    /* W >= 1: router uses the last W visible batches */
-    int32_t route_lag;       /* 0..3: batch b is routed on batches <= b-1-lag */
+    int32_t route_lag;       /* 0..7: batch b is routed on batches <= b-1-lag */
     int32_t max_in_flight;   /* submitted but not yet polled batches, 1..64 */
     int32_t device;          /* CUDA device ordinal */
     void *stream;            /* cudaStream_t the batches run on; NULL = library stream */
@@ -143,7 +143,7 @@ typedef struct hydro_query_config {
     int32_t proxy_epochs;    /* LEARNED: passes over the last proxy_refresh batches per retrain (2) */
     float proxy_lr;          /* LEARNED: Adam learning rate (1e-3) */
     int32_t proxy_seed;      /* LEARNED: seed of the proxy's initial weights */
-    int32_t lanes;           /* 1 (default) .. 4, <= route_lag + 1: batch b runs on stream lane
+    int32_t lanes;           /* 1 (default) .. 8, <= route_lag + 1: batch b runs on stream lane
                                 b % lanes, each lane with its own scratch, so that up to `lanes`
                                 consecutive batches run at once (batch b's order waits only for
                                 batch b - 1 - route_lag).  The batches then run on library streams

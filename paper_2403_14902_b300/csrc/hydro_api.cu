@@ -146,7 +146,7 @@ struct Prof {
 
 }  // namespace
 
-constexpr int kMaxLanes = 4;
+constexpr int kMaxLanes = 8;
 
 // Per-batch scratch of one stream lane.
 struct LaneBufs {
@@ -1215,7 +1215,7 @@ hydro_status hydro_create_query(const hydro_query_config *cfg, hydro_query **out
         return fail(HYDRO_EUNSUPPORTED, "measured cost needs the rank or cost policy and warmup_batches >= 1");
     if (c.warmup_batches < 0 || c.warmup_batches > 64) return fail(HYDRO_EINVAL, "warmup_batches must be 0..64");
     if (c.stats_window < 1 || c.stats_window > 1024) return fail(HYDRO_EINVAL, "stats_window must be 1..1024");
-    if (c.route_lag < 0 || c.route_lag > 3) return fail(HYDRO_EINVAL, "route_lag must be 0..3");
+    if (c.route_lag < 0 || c.route_lag > 7) return fail(HYDRO_EINVAL, "route_lag must be 0..7");
     if (c.lanes < 0 || c.lanes > kMaxLanes) return fail(HYDRO_EINVAL, "lanes must be 1..%d", kMaxLanes);
     if (c.lanes > c.route_lag + 1) return fail(HYDRO_EINVAL, "lanes must be <= route_lag + 1");
     if (c.max_in_flight < 1 || c.max_in_flight > 64) return fail(HYDRO_EINVAL, "max_in_flight must be 1..64");

@@ -125,13 +125,13 @@ def test_create_rejects_bad_config_without_touching_a_device():
     cfg.max_batch = 0
     assert L.hydro_create_query(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
     cfg.max_batch = 16
-    cfg.route_lag = 4
+    cfg.route_lag = 8
     assert L.hydro_create_query(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
     cfg.route_lag = 1
     cfg.lanes = 3                      # more lanes than route_lag + 1
     assert L.hydro_create_query(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
-    cfg.lanes = 5
-    cfg.route_lag = 3
+    cfg.lanes = 9
+    cfg.route_lag = 7
     assert L.hydro_create_query(ctypes.byref(cfg), ctypes.byref(h)) == H.EINVAL
     cfg.lanes = 1
     cfg.cost_source = 2                # no such cost source
