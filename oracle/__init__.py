@@ -255,7 +255,13 @@ def simulate(pm: np.ndarray, batch: int, policy: str = "rank", costs=None, stati
     is ``costs[i] + miss_b / n_b * group_costs[g]`` (the estimated cost of
     the reuse-aware formula, with the hit rate of the batch), where miss_b
     counts the batch's ids not cached by batches finished lag+1 earlier (or
-    prefilled); ``costs[i]`` is then the head's own cost."""
+    prefilled); ``costs[i]`` is then the head's own cost.  That surcharge
+    applies only while no head of the same group precedes it in the batch's
+    order: a later head finds every tuple that reaches it cached by the
+    earlier head.  So the order is built position by position, each time the
+    remaining predicate with the lowest key given the groups already
+    computed (ties to the lower id); without groups this is the ascending
+    key order."""
     assert policy in POLICIES
     n, P = pm.shape
     costs = [1] * P if costs is None else list(costs)
@@ -296,23 +302,38 @@ def simulate(pm: np.ndarray, batch: int, policy: str = "rank", costs=None, stati
                     t = tag[g][bids]
                     visible = (t == -1) | ((t > 0) & (t - 1 <= last))
                     miss[g] = int((~visible).sum())
-                keys = []
+                stats = []
                 for i in range(P):
                     E = sum(stat_e[x][i] for x in range(lo, last + 1))
                     Pp = sum(stat_p[x][i] for x in range(lo, last + 1))
                     if E == 0:
                         E = sum(stat_e[x][i] for x in range(min(warmup, last + 1)))
                         Pp = sum(stat_p[x][i] for x in range(min(warmup, last + 1)))
+                    stats.append((E, Pp))
+
+                def key(i, computed):
+                    # a head pays its group's cost for the batch's misses only while no
+                    # head of the group is placed before it: every tuple reaching a
+                    # later head was cached by the earlier one
                     c = Fraction(costs[i])
-                    if groups[i] is not None and nbt > 0:
-                        c += Fraction(miss[groups[i]], nbt) * group_costs[groups[i]]
+                    g = groups[i]
+                    if g is not None and g not in computed and nbt > 0:
+                        c += Fraction(miss[g], nbt) * group_costs[g]
+                    E, Pp = stats[i]
                     if policy == "rank":
-                        keys.append(c / (1 - smoothed_selectivity(E, Pp)))
-                    elif policy == "cost":
-                        keys.append(c)
-                    else:
-                        keys.append(smoothed_selectivity(E, Pp))
-                order = order_by(keys)
+                        return c / (1 - smoothed_selectivity(E, Pp))
+                    if policy == "cost":
+                        return c
+                    return smoothed_selectivity(E, Pp)
+                # position by position, the remaining predicate with the lowest key under
+                # the groups computed so far (ties to the lower id)
+                order, computed, rest = [], set(), list(range(P))
+                while rest:
+                    pick = min(rest, key=lambda i: (key(i, computed), i))
+                    order.append(pick)
+                    rest.remove(pick)
+                    if groups[pick] is not None:
+                        computed.add(groups[pick])
         counts = np.zeros(P, np.int64)
         passed = np.zeros(P, np.int64)
         hits = np.zeros(P, np.int64)

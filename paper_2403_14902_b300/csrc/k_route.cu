@@ -194,23 +194,29 @@ k_result(const int *count, const int *alive, int n, unsigned int *bitmap, long l
     if (threadIdx.x == 0) *n_pass = c;
 }
 
-// Router: one warp, lane i scores predicate i and finds its position by
-// counting the predicates that go before it (exact integer comparisons; ties
-// to the lower id).  Statistics are the sums over visible batches
-// [lo, last] of the ring; a predicate with no evaluations there falls back to
-// the warmup batches' statistics.
+// Router: one warp, lane i scores predicate i.  The order is built greedily:
+// each position takes the remaining predicate that no other remaining one
+// goes before (exact integer comparisons; ties to the lower id).  A head on a
+// shared upstream UDF pays the upstream's cost for the batch's uncached ids
+// only while no head of its group is placed yet: a later head of the group
+// finds every tuple that reaches it cached by the earlier one (without groups
+// the greedy order is the plain ascending order of the keys).  Statistics are
+// the sums over visible batches [lo, last] of the ring; a predicate with no
+// evaluations there falls back to the warmup batches' statistics.
 __global__ void k_router(const StatRow *ring, int ring_len, const StatRow *warm, int n_warm_visible,
                          long long lo, long long last, int P, int policy, RouterCosts costs, const int *vmiss,
                          int *order_out) {
     const int i = threadIdx.x;
     long long E = 0, Pp = 0, NS = 0;
-    // per-batch cost scaled by the batch size: c*n (+ misses * embedding cost)
-    unsigned long long cost = 0;
+    // per-batch cost scaled by the batch size: c*n, plus misses * upstream cost while the
+    // group's upstream is not yet computed by an earlier head
+    unsigned long long base = 0, extra = 0;
+    const int grp = i < P ? costs.group[i] : -1;
     if (i < P) {
         const long long nn = costs.n > 0 ? costs.n : 1;
-        cost = (unsigned long long)costs.c[i] * (unsigned long long)nn;
-        if (costs.group[i] >= 0 && vmiss && costs.n > 0)
-            cost += (unsigned long long)vmiss[costs.group[i]] * (unsigned long long)costs.cemb[costs.group[i]];
+        base = (unsigned long long)costs.c[i] * (unsigned long long)nn;
+        if (grp >= 0 && vmiss && costs.n > 0)
+            extra = (unsigned long long)vmiss[grp] * (unsigned long long)costs.cemb[grp];
     }
     if (i < P) {
         for (long long b = lo; b <= last; ++b) {
@@ -229,40 +235,51 @@ __global__ void k_router(const StatRow *ring, int ring_len, const StatRow *warm,
     }
     // measured cost per tuple (ns); a predicate without evaluations costs 0
     const double cm = costs.measured && E > 0 ? (double)NS / (double)E : 0.0;
-    int pos = 0;
-    for (int j = 0; j < P; ++j) {
-        const long long Ej = __shfl_sync(0xffffffffu, E, j);
-        const long long Pj = __shfl_sync(0xffffffffu, Pp, j);
-        const unsigned long long cj = __shfl_sync(0xffffffffu, cost, j);
-        const double cmj = __shfl_sync(0xffffffffu, cm, j);
-        if (i >= P || j == i) continue;
-        const unsigned long long ci = cost;
-        bool before;   // does j go before i?
-        if (costs.measured && policy == 0) {
-            // measured rank c/(1-s) in double (the costs are measurements, not exact integers)
-            const double rj = cmj * (double)(Ej + 2) / (double)(Ej - Pj + 1);
-            const double ri = cm * (double)(E + 2) / (double)(E - Pp + 1);
-            before = rj < ri || (rj == ri && j < i);
-        } else if (costs.measured && policy == 1) {
-            before = cmj < cm || (cmj == cm && j < i);
-        } else if (policy == 0) {
-            // rank c/(1-s), s = (p+1)/(e+2): c(e+2)/(e-p+1)
-            const unsigned __int128 lhs = (unsigned __int128)cj * (unsigned long long)(Ej + 2) *
-                                          (unsigned long long)(E - Pp + 1);
-            const unsigned __int128 rhs = (unsigned __int128)ci * (unsigned long long)(E + 2) *
-                                          (unsigned long long)(Ej - Pj + 1);
-            before = lhs < rhs || (lhs == rhs && j < i);
-        } else if (policy == 1) {
-            before = cj < ci || (cj == ci && j < i);
-        } else {
-            // selectivity (p+1)/(e+2)
-            const unsigned __int128 lhs = (unsigned __int128)(unsigned long long)(Pj + 1) * (unsigned long long)(E + 2);
-            const unsigned __int128 rhs = (unsigned __int128)(unsigned long long)(Pp + 1) * (unsigned long long)(Ej + 2);
-            before = lhs < rhs || (lhs == rhs && j < i);
+    unsigned placed = 0, done_groups = 0;
+    for (int k = 0; k < P; ++k) {
+        const unsigned long long cost =
+            base + ((grp >= 0 && !((done_groups >> grp) & 1u)) ? extra : 0ull);
+        const bool mine = i < P && !((placed >> i) & 1u);
+        bool first = mine;   // no other remaining predicate goes before i
+        for (int j = 0; j < P; ++j) {
+            const long long Ej = __shfl_sync(0xffffffffu, E, j);
+            const long long Pj = __shfl_sync(0xffffffffu, Pp, j);
+            const unsigned long long cj = __shfl_sync(0xffffffffu, cost, j);
+            const double cmj = __shfl_sync(0xffffffffu, cm, j);
+            if (!mine || j == i || ((placed >> j) & 1u)) continue;
+            const unsigned long long ci = cost;
+            bool before;   // does j go before i?
+            if (costs.measured && policy == 0) {
+                // measured rank c/(1-s) in double (the costs are measurements, not exact integers)
+                const double rj = cmj * (double)(Ej + 2) / (double)(Ej - Pj + 1);
+                const double ri = cm * (double)(E + 2) / (double)(E - Pp + 1);
+                before = rj < ri || (rj == ri && j < i);
+            } else if (costs.measured && policy == 1) {
+                before = cmj < cm || (cmj == cm && j < i);
+            } else if (policy == 0) {
+                // rank c/(1-s), s = (p+1)/(e+2): c(e+2)/(e-p+1)
+                const unsigned __int128 lhs = (unsigned __int128)cj * (unsigned long long)(Ej + 2) *
+                                              (unsigned long long)(E - Pp + 1);
+                const unsigned __int128 rhs = (unsigned __int128)ci * (unsigned long long)(E + 2) *
+                                              (unsigned long long)(Ej - Pj + 1);
+                before = lhs < rhs || (lhs == rhs && j < i);
+            } else if (policy == 1) {
+                before = cj < ci || (cj == ci && j < i);
+            } else {
+                // selectivity (p+1)/(e+2)
+                const unsigned __int128 lhs = (unsigned __int128)(unsigned long long)(Pj + 1) * (unsigned long long)(E + 2);
+                const unsigned __int128 rhs = (unsigned __int128)(unsigned long long)(Pp + 1) * (unsigned long long)(Ej + 2);
+                before = lhs < rhs || (lhs == rhs && j < i);
+            }
+            if (before) first = false;
         }
-        pos += before;
+        const unsigned m = __ballot_sync(0xffffffffu, first);
+        const int pick = m ? __ffs(m) - 1 : 0;   // exactly one lane: the order is total
+        if (i == 0) order_out[k] = pick;
+        placed |= 1u << pick;
+        const int gp = __shfl_sync(0xffffffffu, grp, pick);
+        if (gp >= 0) done_groups |= 1u << gp;
     }
-    if (i < P) order_out[pos] = i;
 }
 
 // ------------------------------------------------------------ launchers

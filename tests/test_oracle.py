@@ -308,6 +308,22 @@ def test_simulate_reuse_hand_worked_trace():
     assert sim[2]["order"] == [0, 1, 2] and sim[2]["hits"].tolist() == [4, 4, 0]
 
 
+def test_simulate_reuse_later_head_is_cheap():
+    # heads 0 and 1 share "E" (cost 100) under own costs 1 and 30; predicate 2
+    # costs 110; every tuple passes, so the rank keys are proportional to the
+    # costs.  Batch 2 misses all 4 ids: head 0 = 101 goes first; head 1 then
+    # costs 30 (its tuples are cached by head 0) < 110.  Ranking the heads
+    # with the surcharge both ways would give 0, 2, 1 (101 < 110 < 130).
+    pm = np.ones((12, 3), bool)
+    sim = O.simulate(pm, batch=4, policy="rank", costs=[1, 30, 110], groups=["E", "E", None],
+                     group_costs={"E": 100}, ids=np.arange(12), warmup=1, lag=1, window=8)
+    assert sim[2]["order"] == [0, 1, 2] and sim[2]["hits"].tolist() == [0, 4, 0]
+    # cost policy: the same keys without the selectivity factor
+    sim = O.simulate(pm, batch=4, policy="cost", costs=[1, 30, 110], groups=["E", "E", None],
+                     group_costs={"E": 100}, ids=np.arange(12), warmup=1, lag=1, window=8)
+    assert sim[2]["order"] == [0, 1, 2]
+
+
 def test_simulate_reuse_matches_plain_counts():
     # reuse changes costs and hits, never the pass set or which tuples reach a predicate
     g = np.random.default_rng(12)
