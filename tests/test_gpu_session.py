@@ -323,33 +323,35 @@ def test_session_idle_queries_and_empty_step(small):
 
 
 def test_session_full_workload_sampled():
-    """All 64 queries (1.6 M tuples), chunks of 4,096, BF16 with graphs and
-    autotuning: sampled tuples of every query against the oracle, and per
-    step the counting identities of eager dropping along each query's order."""
+    """All 64 queries (1.6 M tuples) in the bench's launch configuration:
+    chunks of 4,096, 8 chunks of every query per step (route lag 7), BF16
+    with graphs and autotuning.  Sampled tuples of every query against the
+    oracle, and per batch the counting identities of eager dropping along
+    its order."""
     import torch
-
     import paper_2403_14902_b300 as H
     w = D.workload("mq64")
     qs = D.mq_queries(w)
     th = mq_thresholds()
     streams = [D.mq_tuples(w, q, None, qs) for q in range(len(qs))]
-    chunk = w.batch
-    s = make_session(w, qs, th, precision="bf16", cap=len(qs) * chunk)
+    chunk, K = w.batch, 8
+    s = H.Session(dim=w.dim, max_step_tuples=len(qs) * chunk * K, precision="bf16", batches_per_step=K,
+                  lag=K - 1)
+    for layers in D.mq_pool_weights(w):
+        s.add_udf(layers)
+    for q in range(len(qs)):
+        s.add_query(qs[q]["udfs"], th[q])
     calib = np.concatenate([D.mq_calib_tuples(w, q, qs)[:64] for q in range(len(qs))])
     s.calibrate(torch.from_numpy(calib).cuda())
+    res = run_session_multi(s, streams, chunk, K)
     bits_q = [[] for _ in qs]
-    done = [0] * len(qs)
-    while any(done[q] < streams[q].shape[0] for q in range(len(qs))):
-        rows, counts = D.mq_stacked_step(streams, done, chunk)
-        sid = s.submit(torch.from_numpy(rows).cuda(), counts)
-        words, per, _ = s.poll(sid)
-        bits = H.bits_from_words(words, rows.shape[0])
+    for counts, bits, per in res:
         off = 0
-        for q, c in enumerate(counts):
+        for v, c in enumerate(counts):
             if c == 0:
                 continue
-            r = per[q]
-            bits_q[q].append(bits[off:off + c])
+            r = per[v]
+            bits_q[v // K].append(bits[off:off + c])
             ev = r["evaluated"]
             if r["warmup"]:
                 assert ev == [c] * len(ev)
@@ -360,12 +362,12 @@ def test_session_full_workload_sampled():
                     assert ev[b] == r["passed"][a]
                 assert r["n_pass"] == r["passed"][o[-1]]
             off += c
-        done = [d + c for d, c in zip(done, counts)]
     pool = D.mq_pool_weights(w)
     rng = np.random.default_rng(11)
     for q in range(len(qs)):
         b = np.concatenate(bits_q[q])
         n = b.shape[0]
+        assert n == streams[q].shape[0]
         idx = np.unique(np.concatenate([rng.choice(n, min(n, 60), replace=False), np.flatnonzero(b)[:20]]))
         S = O.udf_scores("vec", streams[q][idx], [pool[u] for u in qs[q]["udfs"]])
         assert np.array_equal(b[idx], O.result_bits(O.pass_matrix(S, th[q]))), f"query {q}"

@@ -9,7 +9,7 @@ import pytest
 
 import datagen as D
 import oracle as O
-from gpu_helpers import model_costs, oracle_thresholds
+from gpu_helpers import model_costs, oracle_thresholds, stored_thresholds
 
 pytestmark = pytest.mark.gpu
 
@@ -153,4 +153,57 @@ def test_learned_session_several_batches_per_step(drift6):
             check_step(drift6["pm"][b * B:(b + 1) * B], bits[sl], per[k], order[sl], visited[sl], P)
             if b < 2 * REFRESH:
                 assert per[k]["order"] == sim[b]["order"]
+    s.close()
+
+
+def test_learned_session_full_stream_bench_configuration():
+    """The full 1,048,576-tuple drifting stream in the bench's launch
+    configuration: BF16, 16 batches of 4,096 per step (route lag 15), proxy
+    refreshed every 16 batches on 8,192-row windows.  Sampled tuples against
+    the oracle; per batch the counting identities of per-tuple orders (every
+    tuple is evaluated at least once; a passing tuple on every slot)."""
+    import torch
+
+    import paper_2403_14902_b300 as H
+    w = D.workload("drift6")
+    th = stored_thresholds("drift6")
+    X = D.stream_tuples(w)
+    Xd = torch.from_numpy(X).cuda()
+    K = 16
+    s = H.Session(dim=w.dim, max_step_tuples=K * w.batch, precision="bf16", learned=True,
+                  proxy_refresh=w.extra["refresh"], proxy_hidden=w.extra["proxy_hidden"], batches_per_step=K,
+                  lag=K - 1, proxy_rows=8192)
+    for layers in D.predicate_weights(w):
+        s.add_udf(layers)
+    P = len(w.udfs)
+    s.add_query(list(range(P)), th)
+    s.calibrate(torch.from_numpy(D.calib_tuples(w)).cuda())
+    bits = []
+    for b0 in range(0, w.n, K * w.batch):
+        n = min(K * w.batch, w.n - b0)
+        counts = [max(0, min(w.batch, n - k * w.batch)) for k in range(K)]
+        words, per, _ = s.poll(s.submit(Xd[b0:b0 + n], counts), total=n)
+        bb = H.bits_from_words(words, n)
+        bits.append(bb)
+        off = 0
+        for k, c in enumerate(counts):
+            if not c:
+                continue
+            r = per[k]
+            npass = int(bb[off:off + c].sum())
+            assert r["n_pass"] == npass
+            if r["warmup"]:
+                assert r["evaluated"] == [c] * P
+            else:
+                # each tuple is evaluated until its first failing slot
+                assert sum(r["evaluated"]) >= c + npass * (P - 1)
+                assert all(e >= npass for e in r["evaluated"]) and max(r["evaluated"]) <= c
+                assert all(p <= e for p, e in zip(r["passed"], r["evaluated"]))
+            off += c
+    bits = np.concatenate(bits)
+    assert bits.size == w.n
+    rng = np.random.default_rng(5)
+    idx = np.unique(np.concatenate([rng.choice(w.n, 200, replace=False), np.flatnonzero(bits)[:40]]))
+    S = O.udf_scores("vec", X[idx], D.predicate_weights(w))
+    assert np.array_equal(bits[idx], O.result_bits(O.pass_matrix(S, th)))
     s.close()
