@@ -247,10 +247,11 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- our arm
 
-def build_query(H, w, th, *, policy, precision, stream, max_in_flight=8, lanes=2, lag=1):
-    """Stream lanes: up to `lanes` consecutive batches run at once (route lag >= lanes - 1)."""
+def build_query(H, w, th, *, policy, precision, stream, max_in_flight=8, lanes=2, lag=1, split="bf16x3"):
+    """Stream lanes: up to `lanes` consecutive batches run at once (route lag >= lanes - 1);
+    `split`: the first recheck level of the BF16 CNN UDFs."""
     q = H.Query(w.kind, frame=w.frame, max_batch=w.batch, policy=policy, precision=precision,
-                max_in_flight=max_in_flight, stream=stream, lanes=lanes, lag=lag)
+                max_in_flight=max_in_flight, stream=stream, lanes=lanes, lag=lag, split=split)
     for i, udf in enumerate(D.predicate_weights(w)):
         q.add_cnn(udf, th[i])
     return q
@@ -713,7 +714,7 @@ def ours(args):
     stream = torch.cuda.Stream()
     mif = 8
     q = build_query(H, w, th, policy="rank", precision="bf16", stream=stream, max_in_flight=mif, lanes=args.lanes,
-                    lag=args.lag)
+                    lag=args.lag, split=args.split)
     calib = q.calibrate(torch.from_numpy(D.calib_tuples(w)[:64]).cuda())
     step = lambda: run_step(q, X, w.batch, mif)  # noqa: E731
     for _ in range(args.warmup):
@@ -798,10 +799,10 @@ def ours(args):
         "pass_count_per_step": int(npass[0]),
         "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
                         "tflops": round(v["flops"] / max(v["total_ms"], 1e-9) / 1e9, 2)} for k, v in prof.items()},
-        "recheck": {"tf32x3": [s["recheck_tf32"] for s in stats], "fp32": [s["recheck_fp32"] for s in stats],
+        "recheck": {"split_level": [s["recheck_tf32"] for s in stats], "fp32": [s["recheck_fp32"] for s in stats],
                     "fp64": [s["recheck_fp64"] for s in stats],
                     "calib_max_err_bf16": [round(c["max_err_lowp"], 6) for c in calib],
-                    "calib_max_err_tf32x3": [float("%.3g" % c["max_err_tf32"]) for c in calib],
+                    "calib_max_err_split_level": [float("%.3g" % c["max_err_tf32"]) for c in calib],
                     "calib_max_err_fp32": [float("%.3g" % c["max_err_fp32"]) for c in calib]},
     }
     return out
@@ -1366,6 +1367,8 @@ def main(argv=None):
     ap.add_argument("--no-graphs", action="store_true", help="with --headline-only: launch without CUDA graphs")
     ap.add_argument("--lanes", type=int, default=4, help="cnn4: stream lanes of the query (1..8)")
     ap.add_argument("--lag", type=int, default=3, help="cnn4: route lag (>= lanes - 1)")
+    ap.add_argument("--split", choices=["tf32x3", "bf16x3"], default="bf16x3",
+                    help="cnn4: first recheck level of the BF16 CNN UDFs")
     ap.add_argument("--workload", choices=["cnn4", "drift5", "drift6", "mq64", "gemm_bf16", "conv_bf16", "peaks"],
                     default=WORKLOAD)
     args = ap.parse_args(argv)

@@ -80,19 +80,21 @@ enum {
     HYDRO_PREC_FP32 = 0,   /* FP32 everywhere; FP32 scores within margin_fp32 of the
                               threshold are re-evaluated in FP64 */
     HYDRO_PREC_BF16 = 1,   /* BF16 operands, FP32 accumulation on the tensor cores;
-                              scores within margin_lowp are re-evaluated FP32-accurately:
-                              CNN UDFs first by 3xTF32 on the tensor cores (scores within
-                              margin_tf32 go on), then in FP32 on CUDA cores (within
-                              margin_fp32 go on to FP64); MLP UDFs in FP32 then FP64 */
+                              scores within margin_lowp are re-evaluated more accurately:
+                              CNN UDFs first on the tensor cores in split BF16 or 3xTF32
+                              (split_precision; scores within margin_tf32 go on), then in FP32
+                              on CUDA cores (within margin_fp32 go on to FP64); MLP UDFs in
+                              FP32 then FP64 */
     HYDRO_PREC_FP64 = 2,   /* FP64 (only for hydro_udf_scores) */
-    HYDRO_PREC_TF32X3 = 3, /* FP32-accurate 3xTF32 on the tensor cores (hi*hi + hi*lo + lo*hi);
-                              the first BF16 recheck level of CNN UDFs (hydro_udf_scores on
+    HYDRO_PREC_TF32X3 = 3, /* 3xTF32 on the tensor cores (hi*hi + hi*lo + lo*hi): a first BF16
+                              recheck level of CNN UDFs (split_precision; hydro_udf_scores on
                               BF16 CNN queries) */
     HYDRO_PREC_BF16X3 = 4, /* split BF16 on the tensor cores: x = hi + lo with hi = bf16(x),
                               lo = bf16(x - hi), products hi*hi + hi*lo + lo*hi in one BF16 GEMM
                               over [hi | hi | lo] x [W_hi | W_lo | W_hi] (about 16 significant bits);
                               the first recheck level of BF16 sessions
-                              (hydro_session_udf_scores) */
+                              (hydro_session_udf_scores) and, by default, of BF16 CNN queries
+                              ([hi | lo] BF16 planes of the activations and weights) */
     HYDRO_PREC_FP8 = 5     /* sessions only: the first layer of every pool UDF in the FP8 set
                               (first hidden width >= fp8_min_width) runs with E4M3 operands on
                               the tensor cores (kind::f8f6f4, FP32 accumulation): weights scaled
@@ -149,6 +151,11 @@ typedef struct hydro_query_config {
                                 batch b - 1 - route_lag).  The batches then run on library streams
                                 that wait for the caller's stream at each submit.  Not with
                                 embeddings or the LEARNED policy */
+    int32_t split_precision; /* BF16 queries with tensor-core CNN UDFs: the first recheck level,
+                                HYDRO_PREC_BF16X3 (default; 0 also selects it: split BF16 [hi | lo]
+                                operands, three BF16 passes) or HYDRO_PREC_TF32X3 (3xTF32).  On the
+                                CNN workload split BF16 runs at twice the MMA rate with half the
+                                operand bytes and misses FP64 by less than 3xTF32 does */
 } hydro_query_config;
 
 typedef struct hydro_udf_desc {

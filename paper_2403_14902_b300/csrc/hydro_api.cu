@@ -85,6 +85,7 @@ struct Pred {
     std::vector<__nv_bfloat16 *> dWt16;   // CNN layer l >= 1: [tap][ci][co] bf16
     std::vector<void *> dWtc;             // CNN layer l >= 1: tensor-core layout (bf16)
     std::vector<void *> dWts;             // CNN layer l >= 1: tensor-core split-TF32 layout (fp32 hi, lo)
+    std::vector<void *> dWbs;             // CNN layer l >= 1: tensor-core split-BF16 layout (bf16 hi, lo)
     bool tc_all = false;                  // every layer l >= 1 has tensor-core weights
     std::vector<__nv_bfloat16 *> dW16;    // MLP hidden layers: bf16 weights for the tensor cores
     bool tc_mlp = false;                  // MLP: every hidden layer runs on the tensor cores
@@ -131,7 +132,7 @@ struct ProfRec {
 };
 const char *const kProfNames[] = {"conv3x3_bf16_tc", "conv3x3_bf16_simt", "conv3x3_f32_simt", "conv3x3_f64_simt",
                                   "conv1_u8",        "pool_head",         "mlp_layer_f32",    "mlp_dot_f32",
-                                  "mlp_band_f32",    "mlp_band_f64",      "conv3x3_tf32x3_tc", "mlp_layer_bf16_tc",
+                                  "mlp_band_f32",    "mlp_band_f64",      "conv3x3_split_tc",  "mlp_layer_bf16_tc",
                                   "gather_rows_bf16"};
 enum { PC_CONV_TC = 0, PC_CONV_BF16, PC_CONV_F32, PC_CONV_F64, PC_CONV1, PC_POOL, PC_MLP, PC_DOT, PC_BAND32,
        PC_BAND64, PC_CONV_TF32, PC_MLP_TC, PC_GATHER, PC_N };
@@ -581,6 +582,7 @@ hydro_status finalize(hydro_query *q) {
             p.dWt16.assign(p.n_layers, nullptr);
             p.dWtc.assign(p.n_layers, nullptr);
             p.dWts.assign(p.n_layers, nullptr);
+            p.dWbs.assign(p.n_layers, nullptr);
             p.tc_all = c.precision == HYDRO_PREC_BF16 && p.n_layers > 1;
             for (int l = 1; l < p.n_layers; ++l) {
                 const int ci_n = p.dims[l], co_n = p.dims[l + 1];
@@ -607,6 +609,11 @@ hydro_status finalize(hydro_query *q) {
                     float *ds = nullptr;
                     TRY(upload(q, &ds, ts.data(), ts.size()));
                     p.dWts[l] = ds;
+                    std::vector<__nv_bfloat16> tb;
+                    tc_conv_pack_weights_split_bf16(p.W[l].data(), ci_n, co_n, tb);
+                    __nv_bfloat16 *db = nullptr;
+                    TRY(upload(q, &db, tb.data(), tb.size()));
+                    p.dWbs[l] = db;
                 } else {
                     p.tc_all = false;
                 }
@@ -727,24 +734,26 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
     // CNN
     const int H = c.height, Wd = c.width;
     const double hw = (double)H * Wd;
-    if (prec == PREC_TF32X3) {
-        if (!p.tc_all || !q->partials) return fail(HYDRO_EUNSUPPORTED, "3xTF32 needs tensor-core CNN layers");
-        // FP32-accurate evaluation on the tensor cores (3xTF32 split form)
+    if (prec == PREC_TF32X3 || prec == PREC_BF16X3) {
+        if (!p.tc_all || !q->partials) return fail(HYDRO_EUNSUPPORTED, "split forms need tensor-core CNN layers");
+        // the first recheck level on the tensor cores: 3xTF32 or split-BF16 [hi | lo] operands
+        const bool sb = prec == PREC_BF16X3;
         const unsigned char *frames = (const unsigned char *)tuples;
-        int e = prof_begin(q, pc, PC_CONV1, 2.0 * hw * 9 * p.dims[0] * p.dims[1], hw * (p.dims[0] + 8.0 * p.dims[1]),
+        const double pb = sb ? 4.0 : 8.0;   // bytes per channel of a [hi | lo] pixel
+        int e = prof_begin(q, pc, PC_CONV1, 2.0 * hw * 9 * p.dims[0] * p.dims[1], hw * (p.dims[0] + pb * p.dims[1]),
                            4.0 * 9 * p.dims[0] * p.dims[1]);
-        launch_conv1_split(count, list, frames, c.channels, H, Wd, p.dW[0], p.db[0], p.dims[1], (float *)act[0],
-                           max_rows, q->sms, q->st);
+        launch_conv1_split(count, list, frames, c.channels, H, Wd, p.dW[0], p.db[0], p.dims[1], act[0], max_rows,
+                           q->sms, q->st, sb);
         prof_end(q, e);
         q->launches++;
         int cur = 0;
         for (int l = 1; l < p.n_layers; ++l) {
             const bool last = l + 1 == p.n_layers;
             e = prof_begin(q, pc, PC_CONV_TF32, 2.0 * hw * 9 * p.dims[l] * p.dims[l + 1],
-                           hw * 8.0 * (p.dims[l] + (last ? 0 : p.dims[l + 1])), 8.0 * 9 * p.dims[l] * p.dims[l + 1]);
-            hydro_status rs = tc_conv_run(&q->tc, count, act[cur], p.dims[l], H, Wd, p.dWts[l], p.db[l],
-                                          p.dims[l + 1], act[1 - cur], max_rows, q->sms, q->st, q->d_err,
-                                          last ? p.dHead : nullptr, last ? q->partials : nullptr, true);
+                           hw * pb * (p.dims[l] + (last ? 0 : p.dims[l + 1])), pb * 9 * p.dims[l] * p.dims[l + 1]);
+            hydro_status rs = tc_conv_run(&q->tc, count, act[cur], p.dims[l], H, Wd, sb ? p.dWbs[l] : p.dWts[l],
+                                          p.db[l], p.dims[l + 1], act[1 - cur], max_rows, q->sms, q->st, q->d_err,
+                                          last ? p.dHead : nullptr, last ? q->partials : nullptr, sb ? 2 : 1);
             prof_end(q, e);
             if (rs != HYDRO_OK) return fail(rs, "tensor-core conv (split): %s", tc_conv_last_error());
             q->launches++;
@@ -871,6 +880,11 @@ hydro_status run_grouped(hydro_query *q, const Pred &p, const int *count, const 
 //   BF16 query, CNN UDF: BF16 tensor cores -> 3xTF32 tensor cores -> FP32 CUDA cores -> FP64
 //   BF16 query, MLP UDF: (not built)
 //   FP32 query:          FP32 -> FP64
+// The first recheck level of BF16 tensor-core CNN UDFs (hydro_query_config.split_precision).
+int split_prec(const hydro_query_config &c) {
+    return c.split_precision == HYDRO_PREC_TF32X3 ? PREC_TF32X3 : PREC_BF16X3;
+}
+
 hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *in_list, int *out_list,
                        int *out_count, bool eval_all, const void *tuples, const long long *ids, int n,
                        long long batch, Slot &slot) {
@@ -908,7 +922,7 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
         // FP32-level input: band 1 directly, or what 3xTF32 leaves undecided
         const int *b32_count = band1_count, *b32_m = q->band1_m, *b32_t = q->band1_t;
         if (tf32_level) {
-            TRY(run_udf(q, p, PREC_TF32X3, band1_count, q->band1_t, tuples, q->cap1, q->ract32, q->rscore_t,
+            TRY(run_udf(q, p, split_prec(c), band1_count, q->band1_t, tuples, q->cap1, q->ract32, q->rscore_t,
                         nullptr, &pc_rtf));
             launch_recheck_classify_f32(band1_count, q->band1_m, q->band1_t, q->rscore_t, p.threshold,
                                         p.margin_tf32, q->pass, q->band2_m, q->band2_t, band2_count, q->cap2,
@@ -1208,6 +1222,8 @@ hydro_status hydro_create_query(const hydro_query_config *cfg, hydro_query **out
     if (c.precision != HYDRO_PREC_FP32 && c.precision != HYDRO_PREC_BF16)
         return fail(HYDRO_EINVAL, "precision must be FP32 or BF16");
 
+    if (c.split_precision != 0 && c.split_precision != HYDRO_PREC_TF32X3 && c.split_precision != HYDRO_PREC_BF16X3)
+        return fail(HYDRO_EINVAL, "split_precision must be TF32X3 or BF16X3");
     if (c.cost_source != HYDRO_COST_MODEL && c.cost_source != HYDRO_COST_MEASURED)
         return fail(HYDRO_EINVAL, "unknown cost source");
     if (c.cost_source == HYDRO_COST_MEASURED &&
@@ -1418,18 +1434,20 @@ hydro_status hydro_udf_scores(hydro_query *q, int32_t pred, int32_t prec, const 
     if (q->finalized) TRY(quiesce(q));
     if (pred < 0 || pred >= (int)q->preds.size()) return fail(HYDRO_EINVAL, "unknown predicate");
     if (n < 0 || (n > 0 && (!d_tuples || !d_scores))) return fail(HYDRO_EINVAL, "bad tuples/scores");
-    if (prec != HYDRO_PREC_FP32 && prec != HYDRO_PREC_FP64 && prec != HYDRO_PREC_BF16 && prec != HYDRO_PREC_TF32X3)
+    if (prec != HYDRO_PREC_FP32 && prec != HYDRO_PREC_FP64 && prec != HYDRO_PREC_BF16 && prec != HYDRO_PREC_TF32X3 &&
+        prec != HYDRO_PREC_BF16X3)
         return fail(HYDRO_EINVAL, "unknown precision");
-    if ((prec == HYDRO_PREC_BF16 || prec == HYDRO_PREC_TF32X3) && q->cfg.precision != HYDRO_PREC_BF16)
-        return fail(HYDRO_EINVAL, "BF16 and 3xTF32 scores need a BF16 query");
+    const bool split = prec == HYDRO_PREC_TF32X3 || prec == HYDRO_PREC_BF16X3;
+    if ((prec == HYDRO_PREC_BF16 || split) && q->cfg.precision != HYDRO_PREC_BF16)
+        return fail(HYDRO_EINVAL, "BF16, 3xTF32 and split-BF16 scores need a BF16 query");
     CU(cudaSetDevice(q->cfg.device));
     TRY(finalize(q));
     const Pred &p = q->preds[pred];
-    if (prec == HYDRO_PREC_TF32X3 && !p.tc_all) return fail(HYDRO_EINVAL, "3xTF32 scores need a tensor-core CNN UDF");
+    if (split && !p.tc_all) return fail(HYDRO_EINVAL, "split-form scores need a tensor-core CNN UDF");
     const int B = q->cfg.max_batch;
     const bool cnn = p.kind == HYDRO_UDF_CNN;
     const bool recheck_buf = cnn && q->cfg.precision == HYDRO_PREC_BF16 &&
-                             (prec == HYDRO_PREC_FP32 || prec == HYDRO_PREC_TF32X3);
+                             (prec == HYDRO_PREC_FP32 || split);
     int *list = q->alive[0], *count = q->ints + 0;
     const int chunk = (prec == HYDRO_PREC_FP64 && cnn) ? q->cap3 : recheck_buf ? std::min(q->cap1, q->cap2) : B;
     const size_t tb = (size_t)tuple_bytes(q->cfg);
@@ -1441,7 +1459,10 @@ hydro_status hydro_udf_scores(hydro_query *q, int32_t pred, int32_t prec, const 
             TRY(run_udf(q, p, PREC_F64, count, list, base, m, cnn ? q->ract64 : q->act, nullptr, d_scores + s));
         } else {
             void *const *act = recheck_buf ? q->ract32 : q->act;
-            const int ip = prec == HYDRO_PREC_BF16 ? PREC_BF16 : prec == HYDRO_PREC_TF32X3 ? PREC_TF32X3 : PREC_F32;
+            const int ip = prec == HYDRO_PREC_BF16     ? PREC_BF16
+                           : prec == HYDRO_PREC_TF32X3 ? PREC_TF32X3
+                           : prec == HYDRO_PREC_BF16X3 ? PREC_BF16X3
+                                                       : PREC_F32;
             TRY(run_udf(q, p, ip, count, list, base, m, act, q->score32, nullptr));
             launch_f32_to_f64(q->score32, d_scores + s, m, q->st);
         }
@@ -1472,7 +1493,9 @@ hydro_status hydro_calibrate(hydro_query *q, const void *d_tuples, int64_t n, hy
         rc = hydro_udf_scores(q, i, HYDRO_PREC_FP64, d_tuples, n, d);
         if (rc == HYDRO_OK) rc = hydro_udf_scores(q, i, HYDRO_PREC_FP32, d_tuples, n, d + n);
         if (rc == HYDRO_OK && bf) rc = hydro_udf_scores(q, i, HYDRO_PREC_BF16, d_tuples, n, d + 2 * n);
-        if (rc == HYDRO_OK && tf) rc = hydro_udf_scores(q, i, HYDRO_PREC_TF32X3, d_tuples, n, d + 3 * n);
+        // the first recheck level as configured
+        const int lv1 = q->cfg.split_precision == HYDRO_PREC_TF32X3 ? HYDRO_PREC_TF32X3 : HYDRO_PREC_BF16X3;
+        if (rc == HYDRO_OK && tf) rc = hydro_udf_scores(q, i, lv1, d_tuples, n, d + 3 * n);
         if (rc != HYDRO_OK) break;
         if (cudaMemcpy(s64.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(s32.data(), d + n, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||

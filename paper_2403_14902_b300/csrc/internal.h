@@ -9,7 +9,7 @@ namespace hydro {
 
 struct StatRow;
 
-enum { PREC_F32 = 0, PREC_BF16 = 1, PREC_F64 = 2, PREC_TF32X3 = 3 };
+enum { PREC_F32 = 0, PREC_BF16 = 1, PREC_F64 = 2, PREC_TF32X3 = 3, PREC_BF16X3 = 4 };
 
 constexpr int kMaxLayers = 16;
 
@@ -84,10 +84,12 @@ cudaError_t mlp_band_smem_setup(int max_width);
 void launch_conv1(int prec, const int *count, const int *list, const unsigned char *frames, int C0, int H,
                   int Wd, const float *W, const float *bias, int Cout, void *out, int max_frames, int sms,
                   cudaStream_t st);
-// First conv layer in the FP32-accurate split form [hi(Cout) | lo(Cout)] fp32.
+// First conv layer (FP32) in a split form [hi(Cout) | lo(Cout)] per pixel:
+// TF32 planes in fp32 (3xTF32 level), or with bf16_planes BF16 planes
+// (split-BF16 level).
 void launch_conv1_split(const int *count, const int *list, const unsigned char *frames, int C0, int H, int Wd,
-                        const float *W, const float *bias, int Cout, float *out, int max_frames, int sms,
-                        cudaStream_t st);
+                        const float *W, const float *bias, int Cout, void *out, int max_frames, int sms,
+                        cudaStream_t st, bool bf16_planes = false);
 void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,
                          const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st);
 void launch_pool_head(int prec, const int *count, const void *act, int HW, int C, const float *hw, double hb,

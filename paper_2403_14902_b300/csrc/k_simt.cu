@@ -182,6 +182,18 @@ __device__ __forceinline__ void store_relu_row(const T (&acc)[COUT], Tout *o) {
 // kernel reads: [hi(COUT) | lo(COUT)], hi = the value rounded to TF32, lo =
 // the remainder rounded to TF32.
 template <int COUT>
+__device__ __forceinline__ void store_relu_row_split(const float (&acc)[COUT], __nv_bfloat16 *o) {
+    // split-BF16 planes: hi = bf16(value), lo = bf16(value - hi)
+#pragma unroll
+    for (int j = 0; j < COUT; ++j) {
+        const float v = acc[j] > 0.f ? acc[j] : 0.f;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        o[j] = hi;
+        o[COUT + j] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
+template <int COUT>
 __device__ __forceinline__ void store_relu_row_split(const float (&acc)[COUT], float *o) {
 #pragma unroll
     for (int j = 0; j < COUT; j += 4) {
@@ -469,12 +481,23 @@ void launch_conv1(int prec, const int *count, const int *list, const unsigned ch
 }
 
 void launch_conv1_split(const int *count, const int *list, const unsigned char *frames, int C0, int H, int Wd,
-                        const float *W, const float *bias, int Cout, float *out, int max_frames, int sms,
-                        cudaStream_t st) {
+                        const float *W, const float *bias, int Cout, void *out, int max_frames, int sms,
+                        cudaStream_t st, bool bf16_planes) {
+    if (bf16_planes) {
+        __nv_bfloat16 *o = (__nv_bfloat16 *)out;
+        if (Wd % 4 == 0)
+            conv1_dispatch<float, __nv_bfloat16, 4, true>(count, list, frames, C0, H, Wd, W, bias, Cout, o, max_frames,
+                                                          sms, st);
+        else
+            conv1_dispatch<float, __nv_bfloat16, 1, true>(count, list, frames, C0, H, Wd, W, bias, Cout, o, max_frames,
+                                                          sms, st);
+        return;
+    }
+    float *o = (float *)out;
     if (Wd % 4 == 0)
-        conv1_dispatch<float, float, 4, true>(count, list, frames, C0, H, Wd, W, bias, Cout, out, max_frames, sms, st);
+        conv1_dispatch<float, float, 4, true>(count, list, frames, C0, H, Wd, W, bias, Cout, o, max_frames, sms, st);
     else
-        conv1_dispatch<float, float, 1, true>(count, list, frames, C0, H, Wd, W, bias, Cout, out, max_frames, sms, st);
+        conv1_dispatch<float, float, 1, true>(count, list, frames, C0, H, Wd, W, bias, Cout, o, max_frames, sms, st);
 }
 
 void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,

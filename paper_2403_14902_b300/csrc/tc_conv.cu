@@ -37,9 +37,13 @@ thread_local std::string g_tc_err;
 // rows feeds all subtiles and every B box is used MT times, which cuts the
 // L2->SM operand traffic per output pixel (the 64-output layers, whose double-
 // buffered accumulators fit TMEM at MT = 4, are the most operand-bound).
-template <int CC, int N, int S, bool SPLIT, int MT>
+// MODE: 0 BF16; 1 3xTF32 (fp32 [hi | lo] TF32 planes, kind::tf32); 2 split
+// BF16 ([hi | lo] BF16 planes, kind::f16).  Modes 1 and 2 run three passes
+// (A hi, B hi), (A hi, B lo), (A lo, B hi) into one accumulator.
+template <int CC, int N, int S, int MODE, int MT>
 struct TcCfg {
-    static constexpr int ESZ = SPLIT ? 4 : 2;             // operand bytes
+    static constexpr bool SPLIT = MODE != 0;
+    static constexpr int ESZ = MODE == 1 ? 4 : 2;         // operand bytes
     static constexpr int ROWB = CC * ESZ;                 // bytes of one pixel's K chunk
     static constexpr int A_ROWS = 2 + 2 * MT;             // image rows per A box (halo included)
     static constexpr int A_BYTES = A_ROWS * 64 * ROWB;
@@ -53,12 +57,13 @@ struct TcCfg {
     static constexpr int SMEM = S * STAGE + 1024 /*align*/ + 256 /*barriers*/;
 };
 
-template <int CC, int N, int S, bool SPLIT, int MT>
+template <int CC, int N, int S, int MODE, int MT>
 __global__ void __launch_bounds__(192, 1)
 k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const int *count,
              int nchunks, int cin, int tiles_per_frame, int HW, const float *__restrict__ bias, void *out,
              const float *__restrict__ head_w, float *partials, unsigned int *err) {
-    using C = TcCfg<CC, N, S, SPLIT, MT>;
+    using C = TcCfg<CC, N, S, MODE, MT>;
+    constexpr bool SPLIT = C::SPLIT;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * C::STAGE);
@@ -137,7 +142,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer
-            constexpr uint32_t idesc = SPLIT ? idesc_tf32(128, N) : idesc_bf16(128, N);
+            constexpr uint32_t idesc = MODE == 1 ? idesc_tf32(128, N) : idesc_bf16(128, N);
             int s = 0;
             uint32_t ph = 0;
             int tl = 0;
@@ -169,7 +174,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                                 const uint64_t ad =
                                     smem_desc(sa + (2 * sub + ky) * 64 * C::ROWB + kk * 32, C::SBO, C::SWZ);
                                 const uint64_t bd = smem_desc(sb + ky * C::B_TAP + kk * 32, C::SBO, C::SWZ);
-                                if constexpr (SPLIT)
+                                if constexpr (MODE == 1)
                                     mma_tf32(dt, ad, bd, idesc, (k | ky | kk) != 0);
                                 else
                                     mma_bf16(dt, ad, bd, idesc, (k | ky | kk) != 0);
@@ -223,7 +228,32 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 #pragma unroll
                     for (int d = 16; d > 0; d >>= 1) hsum += __shfl_xor_sync(0xffffffffu, hsum, d);
                     if (lane == 0) partials[((size_t)t * MT + sub) * 4 + qtr] = hsum;
-                } else if constexpr (SPLIT) {
+                } else if constexpr (MODE == 2) {
+                    // split-BF16 output as two planes per pixel: [hi(N) | lo(N)]
+                    __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out) + ((size_t)m * HW + p0 + row) * (2 * N);
+#pragma unroll
+                    for (int c0 = 0; c0 < N; c0 += 32) {
+                        uint32_t r[32];
+                        tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + col0 + (uint32_t)c0, r);
+                        tmem_ld_wait();
+                        uint32_t hi[16], lo[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            float v0 = __uint_as_float(r[2 * j]) + __ldg(bias + c0 + 2 * j);
+                            float v1 = __uint_as_float(r[2 * j + 1]) + __ldg(bias + c0 + 2 * j + 1);
+                            v0 = v0 > 0.f ? v0 : 0.f;
+                            v1 = v1 > 0.f ? v1 : 0.f;
+                            hi[j] = pack_bf16x2(v0, v1);
+                            lo[j] = pack_bf16x2(v0 - __uint_as_float(hi[j] << 16), v1 - __uint_as_float(hi[j] & 0xFFFF0000u));
+                        }
+                        uint4 *dh = reinterpret_cast<uint4 *>(o + c0), *dl = reinterpret_cast<uint4 *>(o + N + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            dh[j] = make_uint4(hi[4 * j], hi[4 * j + 1], hi[4 * j + 2], hi[4 * j + 3]);
+                            dl[j] = make_uint4(lo[4 * j], lo[4 * j + 1], lo[4 * j + 2], lo[4 * j + 3]);
+                        }
+                    }
+                } else if constexpr (MODE == 1) {
                     // fp32 output as two planes per pixel: [hi(N) | lo(N)]
                     float *o = static_cast<float *>(out) + ((size_t)m * HW + p0 + row) * (2 * N);
 #pragma unroll
@@ -319,10 +349,10 @@ using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, vo
                               const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-template <int CC, int N, int S, bool SPLIT, int MT>
+template <int CC, int N, int S, int MODE, int MT>
 cudaError_t set_smem() {
-    return cudaFuncSetAttribute(k_conv3x3_tc<CC, N, S, SPLIT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                TcCfg<CC, N, S, SPLIT, MT>::SMEM);
+    return cudaFuncSetAttribute(k_conv3x3_tc<CC, N, S, MODE, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcCfg<CC, N, S, MODE, MT>::SMEM);
 }
 
 // 128-output layers: two 128-pixel subtiles per CTA tile (2 x 2 x 128 TMEM
@@ -356,6 +386,25 @@ void tc_conv_pack_weights(const float *w, int cin, int cout, std::vector<__nv_bf
                     }
 }
 
+void tc_conv_pack_weights_split_bf16(const float *w, int cin, int cout, std::vector<__nv_bfloat16> &out) {
+    const int CC = cin == 32 ? 32 : 64;
+    const int nch = cin / CC;
+    out.assign((size_t)2 * nch * 9 * cout * CC, __float2bfloat16_rn(0.f));
+    // layout [((plane*nch + c)*3 + kx)*3 + ky][co][k]; plane 0 = bf16(w), 1 = bf16(w - plane 0)
+    for (int plane = 0; plane < 2; ++plane)
+        for (int c = 0; c < nch; ++c)
+            for (int kx = 0; kx < 3; ++kx)
+                for (int ky = 0; ky < 3; ++ky)
+                    for (int co = 0; co < cout; ++co)
+                        for (int k = 0; k < CC; ++k) {
+                            const int ci = c * CC + k;
+                            const float v = w[(((size_t)co * cin + ci) * 3 + ky) * 3 + kx];
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                            const size_t o = ((((size_t)(plane * nch + c) * 3 + kx) * 3 + ky) * cout + co) * CC + k;
+                            out[o] = plane == 0 ? hi : __float2bfloat16_rn(v - __bfloat162float(hi));
+                        }
+}
+
 void tc_conv_pack_weights_split(const float *w, int cin, int cout, std::vector<float> &out) {
     const int CC = 32;
     const int nch = cin / CC;
@@ -386,12 +435,16 @@ hydro_status tc_conv_init(TcConvPlan *plan, int device) {
     }
     plan->encode = fn;
     cudaError_t r = cudaSuccess;
-    if (r == cudaSuccess) r = set_smem<64, 128, kS_64_128, false, kMT>();
-    if (r == cudaSuccess) r = set_smem<64, 64, kS_64_64, false, kMT64>();
-    if (r == cudaSuccess) r = set_smem<32, 128, kS_32_128, false, kMT>();
-    if (r == cudaSuccess) r = set_smem<32, 64, kS_32_64, false, kMT64>();
-    if (r == cudaSuccess) r = set_smem<32, 128, kS_t32_128, true, kMT>();
-    if (r == cudaSuccess) r = set_smem<32, 64, kS_t32_64, true, kMT64>();
+    if (r == cudaSuccess) r = set_smem<64, 128, kS_64_128, 0, kMT>();
+    if (r == cudaSuccess) r = set_smem<64, 64, kS_64_64, 0, kMT64>();
+    if (r == cudaSuccess) r = set_smem<32, 128, kS_32_128, 0, kMT>();
+    if (r == cudaSuccess) r = set_smem<32, 64, kS_32_64, 0, kMT64>();
+    if (r == cudaSuccess) r = set_smem<32, 128, kS_t32_128, 1, kMT>();
+    if (r == cudaSuccess) r = set_smem<32, 64, kS_t32_64, 1, kMT64>();
+    if (r == cudaSuccess) r = set_smem<64, 128, kS_64_128, 2, kMT>();
+    if (r == cudaSuccess) r = set_smem<64, 64, kS_64_64, 2, kMT64>();
+    if (r == cudaSuccess) r = set_smem<32, 128, kS_32_128, 2, kMT>();
+    if (r == cudaSuccess) r = set_smem<32, 64, kS_32_64, 2, kMT64>();
     if (r != cudaSuccess) {
         g_tc_err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(r);
         return HYDRO_ECUDA;
@@ -410,19 +463,20 @@ void tc_head_finalize(const int *count, const float *partials, int parts_per_fra
 
 hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int cin, int H, int W,
                          const void *wpacked, const float *bias, int cout, void *out, int max_frames, int sms,
-                         cudaStream_t st, unsigned int *err, const float *head_w, float *partials, bool split) {
+                         cudaStream_t st, unsigned int *err, const float *head_w, float *partials, int mode) {
     if (!plan->ready || !tc_conv_supported(cin, cout, H, W)) {
         g_tc_err = "tensor-core conv not ready or shape unsupported";
         return HYDRO_EUNSUPPORTED;
     }
     EncodeFn enc = reinterpret_cast<EncodeFn>(plan->encode);
-    // operand chunk: 64 bf16 / 32 bf16 (128 B or 64 B rows); split fp32: 32 (128 B rows)
-    const int CC = split ? 32 : (cin == 32 ? 32 : 64);
-    const int esz = split ? 4 : 2;
-    const int planes = split ? 2 : 1;
+    // operand chunk: 64 bf16 / 32 bf16 (128 B or 64 B rows); 3xTF32 fp32: 32 (128 B rows)
+    const bool tf32 = mode == 1;
+    const int CC = tf32 ? 32 : (cin == 32 ? 32 : 64);
+    const int esz = tf32 ? 4 : 2;
+    const int planes = mode ? 2 : 1;
     const int nch = cin / CC;
     const int mt = cout == 64 ? kMT64 : kMT;   // 128-pixel subtiles per CTA tile
-    const CUtensorMapDataType dt = split ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const CUtensorMapSwizzle swz = CC * esz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     const cuuint64_t ctot = (cuuint64_t)cin * planes;   // channels stored per pixel
     CUtensorMap tmA, tmB;
@@ -455,18 +509,23 @@ hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int
     long long tiles = (long long)max_frames * tpf;
     const int grid = (int)(tiles < sms ? tiles : sms);
     const int HW = H * W;
-#define HYDRO_TC_LAUNCH(CC_, N_, S_, SPLIT_, MT_)                                                           \
-    k_conv3x3_tc<CC_, N_, S_, SPLIT_, MT_><<<grid, 192, TcCfg<CC_, N_, S_, SPLIT_, MT_>::SMEM, st>>>(    \
+#define HYDRO_TC_LAUNCH(CC_, N_, S_, MODE_, MT_)                                                            \
+    k_conv3x3_tc<CC_, N_, S_, MODE_, MT_><<<grid, 192, TcCfg<CC_, N_, S_, MODE_, MT_>::SMEM, st>>>(      \
         tmA, tmB, count, nch, cin, tpf, HW, bias, out, head_w, partials, err)
-    if (split) {
-        if (cout == 128) HYDRO_TC_LAUNCH(32, 128, kS_t32_128, true, kMT);
-        else HYDRO_TC_LAUNCH(32, 64, kS_t32_64, true, kMT64);
+    if (tf32) {
+        if (cout == 128) HYDRO_TC_LAUNCH(32, 128, kS_t32_128, 1, kMT);
+        else HYDRO_TC_LAUNCH(32, 64, kS_t32_64, 1, kMT64);
+    } else if (mode == 2) {
+        if (CC == 64 && cout == 128) HYDRO_TC_LAUNCH(64, 128, kS_64_128, 2, kMT);
+        else if (CC == 64) HYDRO_TC_LAUNCH(64, 64, kS_64_64, 2, kMT64);
+        else if (cout == 128) HYDRO_TC_LAUNCH(32, 128, kS_32_128, 2, kMT);
+        else HYDRO_TC_LAUNCH(32, 64, kS_32_64, 2, kMT64);
     } else if (CC == 64) {
-        if (cout == 128) HYDRO_TC_LAUNCH(64, 128, kS_64_128, false, kMT);
-        else HYDRO_TC_LAUNCH(64, 64, kS_64_64, false, kMT64);
+        if (cout == 128) HYDRO_TC_LAUNCH(64, 128, kS_64_128, 0, kMT);
+        else HYDRO_TC_LAUNCH(64, 64, kS_64_64, 0, kMT64);
     } else {
-        if (cout == 128) HYDRO_TC_LAUNCH(32, 128, kS_32_128, false, kMT);
-        else HYDRO_TC_LAUNCH(32, 64, kS_32_64, false, kMT64);
+        if (cout == 128) HYDRO_TC_LAUNCH(32, 128, kS_32_128, 0, kMT);
+        else HYDRO_TC_LAUNCH(32, 64, kS_32_64, 0, kMT64);
     }
 #undef HYDRO_TC_LAUNCH
     cudaError_t e = cudaGetLastError();

@@ -28,6 +28,8 @@ void launch_conv1_tc(const int *count, const int *list, const unsigned char *fra
 void tc_conv_pack_weights(const float *w, int cin, int cout, std::vector<__nv_bfloat16> &out);
 // FP32-accurate split form: [plane(hi, lo)][chunk of 32][kx][ky][cout][32] fp32.
 void tc_conv_pack_weights_split(const float *w, int cin, int cout, std::vector<float> &out);
+// Split-BF16 form: [plane(bf16(w), bf16(w - plane 0))][chunk][kx][ky][cout][chunk] bf16.
+void tc_conv_pack_weights_split_bf16(const float *w, int cin, int cout, std::vector<__nv_bfloat16> &out);
 hydro_status tc_conv_init(TcConvPlan *plan, int device);
 // out[m] = relu(conv3x3(in[m]) + bias) for m < *count (device), NHWC bf16.
 // With head_w != nullptr the layer is the UDF's last: nothing is stored to
@@ -36,10 +38,11 @@ hydro_status tc_conv_init(TcConvPlan *plan, int device);
 hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int cin, int H, int W,
                          const void *wpacked, const float *bias, int cout, void *out, int max_frames, int sms,
                          cudaStream_t st, unsigned int *err, const float *head_w = nullptr,
-                         float *partials = nullptr, bool split = false);
-// With split = true the layer is FP32-accurate (3xTF32): `in` and `out` are
-// fp32 [frame][pixel][hi(C) | lo(C)] and wpacked comes from
-// tc_conv_pack_weights_split.
+                         float *partials = nullptr, int mode = 0);
+// mode 1: 3xTF32 (FP32-accurate up to the accumulation): `in` and `out` are
+// fp32 [frame][pixel][hi(C) | lo(C)] TF32 planes and wpacked comes from
+// tc_conv_pack_weights_split.  mode 2: split BF16, `in` and `out` bf16
+// [frame][pixel][hi(C) | lo(C)] and wpacked from tc_conv_pack_weights_split_bf16.
 // score[m] = hb + sum(partials of frame m) / HW for m < *count.
 void tc_head_finalize(const int *count, const float *partials, int parts_per_frame, double hb, int HW,
                       float *score, int max_frames, int sms, cudaStream_t st);

@@ -30,13 +30,14 @@ def model_costs(w):
 
 def make_query(w, thresholds, *, batch, policy="rank", precision="fp32", warmup=1, window=8, lag=1,
                static_order=None, max_in_flight=4, preds=None, reuse=False, id_capacity=None, cost="model",
-               lanes=1):
+               lanes=1, split="bf16x3"):
     """A query over the workload's predicates.  With ``reuse`` the predicates
     listed in ``extra['emb_preds']`` run as heads on one shared, cached
     embedding (query.emb_id)."""
     import paper_2403_14902_b300 as H
     q = H.Query(w.kind, dim=w.dim, frame=w.frame, max_batch=batch, policy=policy, precision=precision,
-                warmup=warmup, window=window, lag=lag, max_in_flight=max_in_flight, cost=cost, lanes=lanes)
+                warmup=warmup, window=window, lag=lag, max_in_flight=max_in_flight, cost=cost, lanes=lanes,
+                split=split)
     weights = D.predicate_weights(w)
     idx = list(range(len(weights))) if preds is None else list(preds)
     shared = set(w.extra.get("emb_preds", ())) if (reuse and w.extra) else set()

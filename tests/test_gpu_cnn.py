@@ -136,6 +136,31 @@ def test_udf_scores_error(cnn4):
     q.close()
 
 
+def test_split_bf16_recheck_level(cnn4):
+    """The first recheck level in split BF16 ([hi | lo] operands, three BF16
+    passes): its scores are within the FP32 tolerance like 3xTF32's, its
+    calibrated margin covers its error, and the stream stays exact."""
+    import torch
+    w = cnn4["w"]
+    q = make_query(w, cnn4["th"], batch=B_SMALL, precision="bf16", split="bf16x3")
+    n = 40
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    for i in range(4):
+        s64 = cnn4["S"][:n, i]
+        q.udf_scores(i, "bf16x3", cnn4["Fd"][:n], out)
+        e_sb = np.max(np.abs(out.cpu().numpy() - s64))
+        q.udf_scores(i, "bf16", cnn4["Fd"][:n], out)
+        e16 = np.max(np.abs(out.cpu().numpy() - s64))
+        assert e_sb < 0.2 * e16, (i, e_sb, e16)
+    info = q.calibrate(cnn4["calib_d"])
+    for d in info:
+        assert 0 < d["max_err_tf32"] < 5e-3 and d["margin_tf32"] >= 8 * d["max_err_tf32"]
+    res = run_stream(q, cnn4["Fd"], B_SMALL)
+    check_against_oracle(res, cnn4["pm"], B_SMALL, policy="rank", costs=model_costs(w))
+    assert sum(sum(r[2]["recheck_tf32"]) for r in res) > 0
+    q.close()
+
+
 def test_calibrate_bf16(cnn4):
     w = cnn4["w"]
     q = make_query(w, cnn4["th"], batch=B_SMALL, precision="bf16")
