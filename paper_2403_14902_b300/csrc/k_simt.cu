@@ -183,13 +183,22 @@ __device__ __forceinline__ void store_relu_row(const T (&acc)[COUT], Tout *o) {
 // the remainder rounded to TF32.
 template <int COUT>
 __device__ __forceinline__ void store_relu_row_split(const float (&acc)[COUT], __nv_bfloat16 *o) {
-    // split-BF16 planes: hi = bf16(value), lo = bf16(value - hi)
+    // split-BF16 planes: hi = bf16(value), lo = bf16(value - hi); 8 values per 16-byte store
+    static_assert(COUT % 8 == 0, "16-byte stores of 8 BF16 values");
 #pragma unroll
-    for (int j = 0; j < COUT; ++j) {
-        const float v = acc[j] > 0.f ? acc[j] : 0.f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        o[j] = hi;
-        o[COUT + j] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    for (int j = 0; j < COUT; j += 8) {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float v0 = acc[j + 2 * e] > 0.f ? acc[j + 2 * e] : 0.f;
+            const float v1 = acc[j + 2 * e + 1] > 0.f ? acc[j + 2 * e + 1] : 0.f;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
+            hi[e] = *reinterpret_cast<const uint32_t *>(&h);
+            lo[e] = *reinterpret_cast<const uint32_t *>(&l);
+        }
+        *reinterpret_cast<uint4 *>(o + j) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4 *>(o + COUT + j) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
 }
 
