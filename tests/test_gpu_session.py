@@ -416,7 +416,7 @@ def run_session_multi(s, streams, chunk, K):
 
 
 @pytest.mark.parametrize("K,lag,precision", [(2, 1, "bf16"), (3, 2, "fp32"), (2, 3, "bf16"), (16, 15, "bf16"),
-                                                   (32, 31, "bf16")])
+                                              (4, 3, "fp8"), (32, 31, "bf16")])
 def test_session_several_batches_per_step(small, K, lag, precision):
     """Each step holds up to K consecutive batches of every query, routed with
     lag >= K - 1: orders, counts and pass sets equal the oracle's per-query
