@@ -409,7 +409,7 @@ def ours_drift5(args):
                                        ("adaptive_model_cost", "rank", None, args.steps),
                                        ("best_static", "static", best, args.steps),
                                        ("declared_static", "static", None, 1)]:
-        q, e = make(policy, order, "model" if name.endswith("model_cost") else "measured")
+        q, e = make(policy, order, "measured" if name == "adaptive" else "model")
         f = step_fn(q, e)
         for _ in range(args.warmup if name != "declared_static" else 1):
             f()
