@@ -81,6 +81,8 @@ __device__ __forceinline__ int tile_group(const int *start, int n, int t) {
 constexpr int kGemmThreads = 320;
 constexpr int kEpiWarps = 8;
 
+// HAS_FP8: some group of the launch has E4M3 operands (its branches compile out otherwise).
+template <bool HAS_FP8>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const __grid_constant__ TcLaunch L) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
                 const int tiles_n = G.N / G.NT, local = t - start[g];
                 const int m0 = off[g] + (local / tiles_n) * 128, n0 = (local % tiles_n) * G.NT;
                 const uint32_t bytes = (uint32_t)(kA_BYTES + G.NT * 128);
-                const int kslice = G.fp8 ? 128 : 64;   // elements per 128-byte K slice
+                const int kslice = HAS_FP8 && G.fp8 ? 128 : 64;   // elements per 128-byte K slice
                 for (int kb = 0; kb < G.K / kslice; ++kb) {
                     if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
                         ok = false;
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
                 const int g = tile_group(start, L.n, t);
-                const int NT = L.g[g].NT, fp8 = L.g[g].fp8, kblocks = L.g[g].K / (fp8 ? 128 : 64);
+                const int NT = L.g[g].NT, fp8 = HAS_FP8 && L.g[g].fp8, kblocks = L.g[g].K / (fp8 ? 128 : 64);
                 const uint32_t idesc = fp8 ? idesc_e4m3(128, NT) : idesc_bf16(128, NT);
                 const int buf = tl & 1;
                 const uint32_t tph = (uint32_t)(tl >> 1) & 1u;
@@ -226,8 +228,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
             const float *bias = G.bias + n0;
             const float *hw = G.head_w ? G.head_w + n0 : nullptr;
             // FP8 groups: accumulator x ascale[row] x wscale[col]; BF16: x 1
-            const float asc = G.fp8 && live ? __ldg(G.ascale + row) : 1.f;
-            const float *wsc = G.fp8 ? G.wscale + n0 : nullptr;
+            const float asc = HAS_FP8 && G.fp8 && live ? __ldg(G.ascale + row) : 1.f;
+            const float *wsc = HAS_FP8 && G.fp8 ? G.wscale + n0 : nullptr;
             float hsum = 0.f;
 #pragma unroll 1
             for (int c0 = chalf * (NT >> 1); c0 < (chalf + 1) * (NT >> 1); c0 += 32) {
@@ -470,7 +472,10 @@ hydro_status tc_gemm_init(void **encode) {
         return HYDRO_ECUDA;
     }
     *encode = fn;
-    cudaError_t r = cudaFuncSetAttribute(k_gemm_grouped_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+    cudaError_t r = cudaFuncSetAttribute(k_gemm_grouped_bf16_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kGemmSmem);
+    if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(k_gemm_grouped_bf16_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
     if (r != cudaSuccess) {
         g_gemm_err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(r);
         return HYDRO_ECUDA;
@@ -542,7 +547,12 @@ hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n,
     L.min_rows = min_rows;
     if (tiles == 0) return HYDRO_OK;   // only rows-only groups
     const int grid = (int)(tiles < sms ? tiles : sms);
-    k_gemm_grouped_bf16_tc<<<grid, kGemmThreads, kGemmSmem, st>>>(L);
+    bool any_fp8 = false;
+    for (int g = 0; g < n; ++g) any_fp8 = any_fp8 || L.g[g].fp8;
+    if (any_fp8)
+        k_gemm_grouped_bf16_tc<true><<<grid, kGemmThreads, kGemmSmem, st>>>(L);
+    else
+        k_gemm_grouped_bf16_tc<false><<<grid, kGemmThreads, kGemmSmem, st>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         g_gemm_err = std::string("launch: ") + cudaGetErrorString(e);
