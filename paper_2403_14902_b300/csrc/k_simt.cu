@@ -228,13 +228,16 @@ k_conv1_u8(const int *count, const int *list, const unsigned char *frames, int C
            const float *W, const float *bias, Tout *out) {
     __shared__ T Ws[8 * 9][COUT];   // [ci*9 + ky*3 + kx][co], C0 <= 8
     __shared__ T Bs[COUT];
+    const int M = *count;
+    // an empty band (the usual case of the recheck levels) leaves before staging the weights;
+    // M is the same for every thread, so no thread skips the barrier below alone
+    if (M == 0) return;
     for (int i = threadIdx.x; i < C0 * 9 * COUT; i += blockDim.x) {
         const int co = i % COUT, r = i / COUT;   // r = ci*9 + tap
         Ws[r][co] = (T)W[(size_t)co * C0 * 9 + r];
     }
     for (int i = threadIdx.x; i < COUT; i += blockDim.x) Bs[i] = (T)bias[i];
     __syncthreads();
-    const int M = *count;
     const int HW = H * Wd;
     const int per_block = 256 * PX;
     const int blocks_per_frame = (HW + per_block - 1) / per_block;
