@@ -68,7 +68,6 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
              const float *__restrict__ head_w, float *partials, unsigned int *err) {
     using C = TcCfg<CC, N, S, MODE, MT, RES>;
     static_assert(!RES || MODE == 0, "resident weights: BF16 layers with one input chunk");
-    constexpr bool SPLIT = C::SPLIT;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *wres = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *smem = wres + C::RES_BYTES;   // stages

@@ -19,8 +19,9 @@ struct TcConvPlan {
 // Whether a layer of this shape runs on the tensor-core kernel.
 bool tc_conv_supported(int cin, int cout, int H, int W);
 // First conv layer on the tensor cores (BF16 output): uint8 frames with C0 <= 3
-// channels, Cout == 32, H*W a multiple of 128.
-bool tc_conv1_supported(int C0, int H, int W, int Cout);
+// channels, Cout == 32, 8 <= W <= 512, H*W a multiple of 128, and fp32 weights
+// w [32][C0][3][3] and biases b [32] (host) of moderate size.
+bool tc_conv1_supported(int C0, int H, int W, int Cout, const float *w, const float *b);
 void launch_conv1_tc(const int *count, const int *list, const unsigned char *frames, int C0, int H, int Wd,
                      const float *W, const float *bias, __nv_bfloat16 *out, int max_frames, int sms,
                      unsigned int *err, cudaStream_t st);

@@ -33,7 +33,7 @@ thread_local std::string g_gemm_err;
 constexpr int kA_BYTES = 128 * 128;   // 128 rows x 64 bf16 (one 128-byte swizzled K slice)
 constexpr int kMaxStages = 8;
 
-struct __align__(64) TcGroup {
+struct TcGroup {   // aligned as its tensor maps
     CUtensorMap tmA, tmB;
     const int *count;         // rows of the group (device)
     const float *bias;        // [N]

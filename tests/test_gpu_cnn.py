@@ -230,3 +230,36 @@ def test_two_lanes_need_route_lag():
     with pytest.raises(H.HydroError) as e:
         H.Query("frame", frame=(3, 64, 64), max_batch=8, lanes=2, lag=0)
     assert e.value.status == H.EINVAL
+
+
+@pytest.mark.parametrize("frame", [(1, 16, 8), (3, 8, 48), (2, 4, 256), (3, 2, 512), (3, 1, 640)])
+@pytest.mark.parametrize("aligned", [True, False])
+def test_first_layer_geometries(frame, aligned):
+    """The first conv layer over frame shapes whose 128-pixel tiles span 16
+    rows down to a fraction of one row (the tensor-core layer reads a window
+    of rows around each tile; 640 columns go to the CUDA-core layer), from
+    16-byte-aligned frames and from frames one byte off: the BF16 scores of a
+    3-32-64 CNN stay within BF16 error of the oracle's FP64 scores, and the
+    FP32 scores within FP32 tolerance."""
+    import torch
+    import paper_2403_14902_b300 as H
+    C, Hh, Wd = frame
+    w = D.workload("cnn4", frame=frame, udfs=((C, 32, 64),), selectivity=(0.5,), head_gain=(8.0,))
+    weights = D.cnn_weights(w, 11, (C, 32, 64), 8.0)
+    n = 24
+    F = D.blob_frames(w, 5, n)
+    S = O.udf_scores("frame", F, [weights])[:, 0]
+    buf = torch.zeros(F.size + 16, dtype=torch.uint8, device="cuda")
+    off = 0 if aligned else 1
+    Fd = buf[off:off + F.size].view(F.shape)
+    Fd.copy_(torch.from_numpy(F))
+    assert (Fd.data_ptr() % 16 == 0) == aligned
+    q = H.Query("frame", frame=frame, max_batch=32, precision="bf16")
+    q.add_cnn(weights, 0.0)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    q.udf_scores(0, "fp32", Fd, out)
+    assert score_tolerance_ok(out.cpu().numpy(), S, np.sqrt((S ** 2).mean())).all()
+    q.udf_scores(0, "bf16", Fd, out)
+    err = np.max(np.abs(out.cpu().numpy() - S))
+    assert err < 0.02 * np.max(np.abs(S)), (err, np.max(np.abs(S)))
+    q.close()
