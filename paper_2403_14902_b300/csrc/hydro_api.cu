@@ -88,6 +88,7 @@ struct Pred {
     std::vector<void *> dWbs;             // CNN layer l >= 1: tensor-core split-BF16 layout (bf16 hi, lo)
     bool tc_all = false;                  // every layer l >= 1 has tensor-core weights
     bool tc_conv1 = false;                // CNN, BF16: the first layer runs on the tensor cores
+    __half *dWc1 = nullptr;               //   with this packed FP16 weight tile (bias folded in)
     std::vector<__nv_bfloat16 *> dW16;    // MLP hidden layers: bf16 weights for the tensor cores
     bool tc_mlp = false;                  // MLP: every hidden layer runs on the tensor cores
     float *dHead = nullptr;
@@ -586,7 +587,13 @@ hydro_status finalize(hydro_query *q) {
             p.dWbs.assign(p.n_layers, nullptr);
             p.tc_all = c.precision == HYDRO_PREC_BF16 && p.n_layers > 1;
             p.tc_conv1 = c.precision == HYDRO_PREC_BF16 &&
-                         tc_conv1_supported(c.channels, c.height, c.width, p.dims[1], p.W[0].data(), p.b[0].data());
+                         tc_conv1_supported(c.channels, c.height, c.width, p.dims[1], c.max_batch, p.W[0].data(),
+                                            p.b[0].data());
+            if (p.tc_conv1) {
+                std::vector<__half> c1;
+                tc_conv1_pack_weights(p.W[0].data(), p.b[0].data(), c.channels, c1);
+                TRY(upload(q, &p.dWc1, c1.data(), c1.size()));
+            }
             for (int l = 1; l < p.n_layers; ++l) {
                 const int ci_n = p.dims[l], co_n = p.dims[l + 1];
                 std::vector<float> t32((size_t)9 * ci_n * co_n);
@@ -770,12 +777,14 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
     const unsigned char *frames = (const unsigned char *)tuples;
     int e = prof_begin(q, pc, PC_CONV1, 2.0 * hw * 9 * p.dims[0] * p.dims[1], hw * (p.dims[0] + esz * p.dims[1]),
                        4.0 * 9 * p.dims[0] * p.dims[1]);
-    if (prec == PREC_BF16 && p.tc_conv1)
-        launch_conv1_tc(count, list, frames, c.channels, H, Wd, p.dW[0], p.db[0], (__nv_bfloat16 *)act[0], max_rows,
-                        q->sms, q->d_err, st);
-    else
+    if (prec == PREC_BF16 && p.tc_conv1) {
+        hydro_status rs = launch_conv1_tc(&q->tc, count, list, frames, c.channels, H, Wd, p.dWc1,
+                                          (__nv_bfloat16 *)act[0], max_rows, q->sms, q->d_err, st);
+        if (rs != HYDRO_OK) return fail(rs, "tensor-core first conv layer launch failed");
+    } else {
         launch_conv1(prec, count, list, frames, c.channels, H, Wd, p.dW[0], p.db[0], p.dims[1], act[0], max_rows,
                      q->sms, st);
+    }
     prof_end(q, e);
     q->launches++;
     int cur = 0;

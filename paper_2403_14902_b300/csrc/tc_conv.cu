@@ -451,6 +451,10 @@ hydro_status tc_conv_init(TcConvPlan *plan, int device) {
         return HYDRO_ECUDA;
     }
     plan->encode = fn;
+    if (cudaDeviceGetAttribute(&plan->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess) {
+        g_tc_err = "cudaDeviceGetAttribute(shared memory per SM) failed";
+        return HYDRO_ECUDA;
+    }
     cudaError_t r = cudaSuccess;
     if (r == cudaSuccess) r = set_smem<64, 128, kS_64_128, 0, kMT>();
     if (r == cudaSuccess) r = set_smem<64, 64, kS_64_64, 0, kMT64>();

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -14,17 +15,22 @@ struct TcConvPlan {
     bool ready = false;
     int device = -1;
     void *encode = nullptr;   // cuTensorMapEncodeTiled entry point
+    int smem_per_sm = 0;      // shared memory per SM (bytes)
 };
 
 // Whether a layer of this shape runs on the tensor-core kernel.
 bool tc_conv_supported(int cin, int cout, int H, int W);
 // First conv layer on the tensor cores (BF16 output): uint8 frames with C0 <= 3
-// channels, Cout == 32, 8 <= W <= 512, H*W a multiple of 128, and fp32 weights
+// channels, Cout == 32, 8 <= W <= 512, H*W a multiple of 128 below 2^22,
+// batches of max_frames * H * W < 2^31 pixels, and fp32 weights
 // w [32][C0][3][3] and biases b [32] (host) of moderate size.
-bool tc_conv1_supported(int C0, int H, int W, int Cout, const float *w, const float *b);
-void launch_conv1_tc(const int *count, const int *list, const unsigned char *frames, int C0, int H, int Wd,
-                     const float *W, const float *bias, __nv_bfloat16 *out, int max_frames, int sms,
-                     unsigned int *err, cudaStream_t st);
+bool tc_conv1_supported(int C0, int H, int W, int Cout, int max_frames, const float *w, const float *b);
+hydro_status launch_conv1_tc(TcConvPlan *plan, const int *count, const int *list, const unsigned char *frames,
+                             int C0, int H, int Wd, const void *Bt, __nv_bfloat16 *out, int max_frames, int sms,
+                             unsigned int *err, cudaStream_t st);
+// The first layer's FP16 weight tile with the bias folded in (device copy
+// passed to launch_conv1_tc as Bt): w [32][C0][3][3], b [32].
+void tc_conv1_pack_weights(const float *w, const float *b, int C0, std::vector<__half> &out);
 // Repack fp32 weights [cout][cin][3][3] into the kernel's bf16 layout.
 void tc_conv_pack_weights(const float *w, int cin, int cout, std::vector<__nv_bfloat16> &out);
 // FP32-accurate split form: [plane(hi, lo)][chunk of 32][kx][ky][cout][32] fp32.

@@ -19,18 +19,22 @@
 //    two kind::f16 MMAs), so the result carries the FP16 rounding of W / 255
 //    and FP32 accumulation error of about 2^-24 times the 1024-offset sum.
 //  - Epilogue: ReLU and rounding to BF16 in one conversion per channel pair;
-//    the tile's 128 BF16 NHWC rows (8 KB, contiguous in the output) replace
-//    the A tile in shared memory and one thread stores them with a bulk copy.
-//    The A/output buffers alternate between tiles, so a tile's store drains
-//    while the next one computes.
+//    the tile's 128 BF16 NHWC rows (64 B each) replace the A tile in shared
+//    memory in the 64-byte swizzled layout (16-byte chunk j of row r at chunk
+//    j ^ ((r >> 1) & 3)), so a warp's 16-byte stores hit distinct banks, and
+//    one thread stores the tile with a TMA tensor store that writes it back
+//    linear.  The A/output buffers alternate between tiles, so a tile's store
+//    drains while the next one computes.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
 #include "internal.h"
 #include "tc_common.cuh"
+#include "tc_conv.h"
 
 namespace hydro {
 
@@ -83,8 +87,10 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-__device__ __forceinline__ void bulk_store(void *g, uint32_t saddr, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(g), "r"(saddr), "r"(bytes)
+// 128 output rows of 32 BF16 from shared memory to rows y .. y + 127
+__device__ __forceinline__ void tma_store_rows(const CUtensorMap *map, uint32_t saddr, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(map),
+                 "r"(saddr), "r"(0), "r"(y)
                  : "memory");
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
@@ -98,89 +104,113 @@ __device__ __forceinline__ uint32_t relu_bf16x2(uint32_t lo, uint32_t hi) {
     return d;
 }
 
-// Copies tile w's window into sw.  With vec (16-byte aligned frames, Wd a
-// multiple of 16) the rows move as 16-byte cp.async, otherwise byte by byte.
-// A tile inside one row takes only columns x0 - 16 .. x0 + 143 of it.
+// n / d for 0 <= n < 2^22 through the FP32 reciprocal, corrected to the
+// exact quotient (the FP32 estimate is off by at most one).
+struct FDiv {
+    int d;
+    float inv;
+    __device__ explicit FDiv(int d_) : d(d_), inv(1.0f / (float)d_) {}
+    __device__ __forceinline__ int q(int n) const {
+        int v = __float2int_rz((float)n * inv);
+        const int r = n - v * d;
+        v += (r >= d) - (r < 0);
+        return v;
+    }
+};
+
+// Copies the window of the tile at pixel p0 of frame `frame` into sw.  With
+// vec (16-byte aligned frames, Wd a multiple of 16) the rows move as 16-byte
+// cp.async, otherwise byte by byte.  A tile inside one row takes only
+// columns x0 - 16 .. x0 + 143 of it.
 template <int C0>
-__device__ __forceinline__ void load_window(unsigned char *sw, const C1Geom &g, const unsigned char *frames,
-                                            const int *list, int w, bool vec) {
-    const int m = w / g.tiles, p0 = (w % g.tiles) * 128;
-    const int y_first = p0 / g.Wd, y_last = (p0 + 127) / g.Wd, R = y_last - y_first + 3;
+__device__ __forceinline__ void load_window(unsigned char *sw, const C1Geom &g, const FDiv &fw,
+                                            const unsigned char *frames, int frame, int p0, bool vec) {
+    const int y_first = fw.q(p0), y_last = fw.q(p0 + 127), R = y_last - y_first + 3;
     const int x0 = p0 - y_first * g.Wd;
     const bool single = y_first == y_last;
     const int c_lo = single ? max(0, x0 - 16) : 0, c_hi = single ? min(g.Wd, x0 + 144) : g.Wd;
-    const unsigned char *f = frames + (size_t)list[m] * C0 * g.HW;
-    if (vec) {
-        const int n16 = (c_hi - c_lo) >> 4, per_ch = R * n16;
-        for (int i = threadIdx.x; i < C0 * per_ch; i += kC1Threads) {
-            const int ci = i / per_ch, rem = i - ci * per_ch, r = rem / n16, c = c_lo + (rem - r * n16) * 16;
-            const int yy = y_first - 1 + r;
-            unsigned char *dst = sw + ci * g.CS + r * g.RS + 16 + c;
-            if (yy >= 0 && yy < g.H)
-                cp_async16(smem_u32(dst), f + (size_t)ci * g.HW + (size_t)yy * g.Wd + c);
+    const unsigned char *f = frames + (size_t)frame * C0 * g.HW;
+    const int per_row = vec ? (c_hi - c_lo) >> 4 : c_hi - c_lo, n = C0 * R * per_row;
+    if ((int)threadIdx.x >= n) return;
+    const FDiv fr(per_row);
+    for (int i = threadIdx.x; i < n; i += kC1Threads) {
+        const int rr = fr.q(i), c = c_lo + (i - rr * per_row) * (vec ? 16 : 1);
+        const int ci = rr >= 2 * R ? 2 : rr >= R ? 1 : 0;
+        const int r = rr - ci * R, yy = y_first - 1 + r;
+        const bool in = yy >= 0 && yy < g.H;
+        unsigned char *dst = sw + ci * g.CS + r * g.RS + 16 + c;
+        const unsigned char *src = f + (size_t)ci * g.HW + (size_t)(in ? yy : 0) * g.Wd + c;
+        if (vec) {
+            if (in)
+                cp_async16(smem_u32(dst), src);
             else
                 *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
-        }
-    } else {
-        const int n = c_hi - c_lo, per_ch = R * n;
-        for (int i = threadIdx.x; i < C0 * per_ch; i += kC1Threads) {
-            const int ci = i / per_ch, rem = i - ci * per_ch, r = rem / n, c = c_lo + (rem - r * n);
-            const int yy = y_first - 1 + r;
-            sw[ci * g.CS + r * g.RS + 16 + c] =
-                (yy >= 0 && yy < g.H) ? f[(size_t)ci * g.HW + (size_t)yy * g.Wd + c] : (unsigned char)0;
+        } else {
+            *dst = in ? *src : (unsigned char)0;
         }
     }
 }
 
+// Epilogue of one tile: accumulator columns tcol -> ReLU -> BF16 rows in the
+// swizzled layout at sO.
+__device__ __forceinline__ void store_rows(uint32_t tmem, int warp, int t, unsigned char *sO) {
+    uint32_t r[32];
+    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), r);
+    tmem_ld_wait();
+    unsigned char *row = sO + t * 64;
+    const int sw = (t >> 1) & 3;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        *reinterpret_cast<uint4 *>(row + ((j ^ sw) << 4)) =
+            make_uint4(relu_bf16x2(r[8 * j + 0], r[8 * j + 1]), relu_bf16x2(r[8 * j + 2], r[8 * j + 3]),
+                       relu_bf16x2(r[8 * j + 4], r[8 * j + 5]), relu_bf16x2(r[8 * j + 6], r[8 * j + 7]));
+}
+
+// Tiles w = blockIdx.x + k * gridDim.x.  Iteration i builds tile i's A in
+// buffer i % 3 and issues its MMA into accumulator i % 2, then runs tile
+// i - 1's epilogue (its MMA has had a whole build to finish) into that
+// tile's own buffer and stores it.  Buffer i % 3 was last stored from in
+// iteration i - 2, so one outstanding store may still be reading.
 template <int C0>
-__global__ void __launch_bounds__(kC1Threads) k_conv1_tc(const int *count, const int *list,
+__global__ void __launch_bounds__(kC1Threads) k_conv1_tc(const __grid_constant__ CUtensorMap tmOut,
+                                                         const int *count, const int *list,
                                                          const unsigned char *frames, int H, int Wd,
-                                                         const float *W, const float *bias, __nv_bfloat16 *out,
-                                                         unsigned int *err, int vec) {
+                                                         const uint4 *__restrict__ Bt, unsigned int *err, int vec) {
     constexpr int K = 9 * C0;
-    extern __shared__ __align__(1024) unsigned char dsm[];
-    unsigned char *sX = dsm;                    // [2][128 x 64 B]: A tile, then the output tile
-    unsigned char *sB = dsm + 2 * 8192;         // [32 x 64 B]
-    unsigned char *sWin = dsm + 2 * 8192 + 2048;   // [2][C0 x CS]
-    __shared__ __align__(8) uint64_t bar;
+    extern __shared__ __align__(16) unsigned char dsm_raw[];
+    // the swizzle pattern repeats every 512 bytes of shared address
+    unsigned char *dsm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *sX = dsm;                        // [3][128 x 64 B]: A tile, then the output tile
+    unsigned char *sB = dsm + 3 * 8192;             // [32 x 64 B]
+    unsigned char *sWin = dsm + 3 * 8192 + 2048;    // [2][C0 x CS]
+    __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     const int t = threadIdx.x, warp = t >> 5;
     const C1Geom g = c1_geom(H, Wd);
-    // weights: B[co][k] = FP16(W[co][k] / 255) for k < K, zero up to tap 28,
-    // and the bias less 1024 * sum_k B[co][k] in three FP16 parts at 29..31
-    if (t < 32) {
-        const int co = t;
-        double off = 0.0;
-        for (int k = 0; k < 29; ++k) {
-            const __half h = __float2half_rn(k < K ? W[co * K + k] * (1.0f / 255.0f) : 0.f);
-            off += 1024.0 * (double)__half2float(h);
-            *reinterpret_cast<__half *>(sB + core_off(co, k)) = h;
-        }
-        double rb = (double)bias[co] - off;
-        for (int k = 29; k < 32; ++k) {
-            const __half h = __float2half_rn((float)rb);
-            rb -= (double)__half2float(h);
-            *reinterpret_cast<__half *>(sB + core_off(co, k)) = h;
-        }
-    }
+    const FDiv fw(Wd);
+    // the packed FP16 weight tile, bias taps included (2 KB)
+    for (int i = t; i < 2048 / 16; i += kC1Threads) reinterpret_cast<uint4 *>(sB)[i] = Bt[i];
     // zero both windows once: the border columns are never written again
     for (int i = t * 16; i < 2 * C0 * g.CS; i += kC1Threads * 16)
         *reinterpret_cast<uint4 *>(sWin + i) = make_uint4(0, 0, 0, 0);
     if (t == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(32u)
+                     "r"(64u)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     __syncthreads();   // the zeroed windows before any row lands in them
     const int total = *count * g.tiles;
-    if (blockIdx.x < total) load_window<C0>(sWin, g, frames, list, blockIdx.x, vec != 0);
+    const int G = gridDim.x, Gq = G / g.tiles, Gr = G - Gq * g.tiles;
+    int m = blockIdx.x / g.tiles, j = blockIdx.x - m * g.tiles;   // frame slot and tile of w
+    if (blockIdx.x < total) load_window<C0>(sWin, g, fw, frames, list[m], j * 128, vec != 0);
     cp_async_commit();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
@@ -194,24 +224,28 @@ __global__ void __launch_bounds__(kC1Threads) k_conv1_tc(const int *count, const
     for (int ci = 0; ci < C0; ++ci)
 #pragma unroll
         for (int ky = 0; ky < 3; ++ky) roff[ci * 3 + ky] = ci * g.CS + ky * g.RS;
-    uint32_t phase = 0;
-    int it = 0;
-    for (int w = blockIdx.x; w < total; w += gridDim.x, ++it) {
+    uint32_t phase = 0;   // bit b: parity of accumulator b's next completion
+    int it = 0, b3 = 0, prev_row = 0;
+    bool aborted = false;
+    for (int w = blockIdx.x; w < total; w += G, ++it) {
         const int b = it & 1;
-        const int wn = w + gridDim.x;
+        int mn = m + Gq, jn = j + Gr;
+        if (jn >= g.tiles) {
+            jn -= g.tiles;
+            ++mn;
+        }
         unsigned char *win = sWin + b * C0 * g.CS;
         // the other window was last read while building the previous tile's
         // A, which every thread finished before that tile's MMA
-        if (wn < total) load_window<C0>(sWin + (b ^ 1) * C0 * g.CS, g, frames, list, wn, vec != 0);
+        if (w + G < total) load_window<C0>(sWin + (b ^ 1) * C0 * g.CS, g, fw, frames, list[mn], jn * 128, vec != 0);
         cp_async_commit();
         cp_async_wait1();   // this tile's window (committed one group earlier) has landed
-        if (t == 0) bulk_wait_read1();   // sX[b]'s store from two tiles back has been read out
+        if (t == 0) bulk_wait_read1();   // buffer b3's store from two iterations back has been read out
         __syncthreads();
-        const int m = w / g.tiles, p0 = (w % g.tiles) * 128;
-        const int p = p0 + t;
-        const int y = p / Wd, x = p - y * Wd;
+        const int p0 = j * 128, p = p0 + t;
+        const int y = fw.q(p), x = p - y * Wd;
         // window byte of the pixel's top-left tap: row y - 1 is window row y - y_first
-        const unsigned char *px = win + (y - p0 / Wd) * g.RS + 15 + x;
+        const unsigned char *px = win + (y - fw.q(p0)) * g.RS + 15 + x;
         uint32_t u[K];
 #pragma unroll
         for (int r = 0; r < 3 * C0; ++r)
@@ -219,16 +253,16 @@ __global__ void __launch_bounds__(kC1Threads) k_conv1_tc(const int *count, const
             for (int kx = 0; kx < 3; ++kx) u[r * 3 + kx] = px[roff[r] + kx];
         uint32_t a[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int k0 = 2 * j, k1 = 2 * j + 1;
+        for (int q = 0; q < 16; ++q) {
+            const int k0 = 2 * q, k1 = 2 * q + 1;
             uint32_t v = 0;
             if (k0 < K) v |= 0x6400u | u[k0 < K ? k0 : 0];
             if (k1 < K) v |= (0x6400u | u[k1 < K ? k1 : 0]) << 16;
             if (k0 >= 29) v |= 0x3C00u;
             if (k1 >= 29) v |= 0x3C00u << 16;
-            a[j] = v;
+            a[q] = v;
         }
-        unsigned char *sA = sX + b * 8192;
+        unsigned char *sA = sX + b3 * 8192;
 #pragma unroll
         for (int kc = 0; kc < 4; ++kc)
             *reinterpret_cast<uint4 *>(sA + core_off(t, kc * 8)) =
@@ -241,33 +275,47 @@ __global__ void __launch_bounds__(kC1Threads) k_conv1_tc(const int *count, const
             tc_fence_after();
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks)
-                mma_bf16(tmem, desc_noswizzle(smem_u32(sA) + ks * 256, 128, 512),
+                mma_bf16(tmem + b * 32, desc_noswizzle(smem_u32(sA) + ks * 256, 128, 512),
                          desc_noswizzle(smem_u32(sB) + ks * 256, 128, 512), idesc, ks > 0);
-            mma_commit(&bar);
-            volatile int *ab = &abort_flag;
-            if (!mbar_wait(&bar, phase, ab)) {
-                *ab = 1;
+            mma_commit(&bar[b]);
+        }
+        if (it > 0) {
+            // the previous tile: its accumulator, then its rows into its own buffer
+            const int pb = b ^ 1, pb3 = b3 == 0 ? 2 : b3 - 1;
+            if (!mbar_wait(&bar[pb], (phase >> pb) & 1u, &abort_flag)) {
+                abort_flag = 1;
                 atomicOr(err, ERR_TC_TIMEOUT);
             }
+            phase ^= 1u << pb;
+            tc_fence_after();
+            store_rows(tmem + pb * 32, warp, t, sX + pb3 * 8192);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+            __syncthreads();   // its rows are in place and its accumulator is free
+            if (*(volatile int *)&abort_flag) {
+                aborted = true;
+                break;
+            }
+            if (t == 0) tma_store_rows(&tmOut, smem_u32(sX + pb3 * 8192), prev_row);
         }
-        phase ^= 1u;
-        __syncthreads();
-        if (*(volatile int *)&abort_flag) break;
+        prev_row = m * g.HW + p0;
+        m = mn;
+        j = jn;
+        b3 = b3 == 2 ? 0 : b3 + 1;
+    }
+    if (it > 0 && !aborted) {
+        // the last tile's epilogue
+        const int pb = (it - 1) & 1, pb3 = b3 == 0 ? 2 : b3 - 1;
+        if (!mbar_wait(&bar[pb], (phase >> pb) & 1u, &abort_flag)) {
+            abort_flag = 1;
+            atomicOr(err, ERR_TC_TIMEOUT);
+        }
         tc_fence_after();
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), r);
-        tmem_ld_wait();
-        // the MMA has read sA, so the tile's output rows (pixel-major, 64 B
-        // each) take its place
-        uint4 *dst = reinterpret_cast<uint4 *>(sA + t * 64);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            dst[j] = make_uint4(relu_bf16x2(r[8 * j + 0], r[8 * j + 1]), relu_bf16x2(r[8 * j + 2], r[8 * j + 3]),
-                                relu_bf16x2(r[8 * j + 4], r[8 * j + 5]), relu_bf16x2(r[8 * j + 6], r[8 * j + 7]));
+        store_rows(tmem + pb * 32, warp, t, sX + pb3 * 8192);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
-        __syncthreads();   // TMEM is free for the next tile and the output rows are in place
-        if (t == 0) bulk_store(out + ((size_t)m * g.HW + p0) * 32, smem_u32(sA), 128 * 64);
+        __syncthreads();
+        if (t == 0 && !*(volatile int *)&abort_flag) tma_store_rows(&tmOut, smem_u32(sX + pb3 * 8192), prev_row);
     }
     cp_async_wait0();
     if (t == 0) bulk_wait_all();
@@ -275,18 +323,45 @@ __global__ void __launch_bounds__(kC1Threads) k_conv1_tc(const int *count, const
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64u) : "memory");
     }
 }
 
-size_t c1_smem_bytes(int C0, int H, int Wd) { return 2 * 8192 + 2048 + 2 * (size_t)C0 * c1_geom(H, Wd).CS; }
+size_t c1_smem_bytes(int C0, int H, int Wd) { return 1024 + 3 * 8192 + 2048 + 2 * (size_t)C0 * c1_geom(H, Wd).CS; }
 
 }  // namespace
 
-// Frames 8 to 512 columns wide (a window then fits well inside 48 KB), and
-// weights whose FP16 forms and 1024-offset bias stay far inside FP16 range.
-bool tc_conv1_supported(int C0, int H, int W, int Cout, const float *w, const float *b) {
-    if (!(C0 >= 1 && C0 <= 3 && Cout == 32 && W >= 8 && W <= 512 && (H * W) % 128 == 0)) return false;
+// B[co][k] = FP16(w[co][k] / 255) for k < 9 * C0, zero up to tap 28, and
+// b[co] - 1024 * sum_k B[co][k] in three FP16 parts at taps 29..31, in the
+// kernel's core-matrix order (2 KB).
+void tc_conv1_pack_weights(const float *w, const float *b, int C0, std::vector<__half> &out) {
+    const int K = 9 * C0;
+    out.assign(32 * 32, __float2half_rn(0.f));
+    auto at = [](int row, int k) { return (((row >> 3) * 4 + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2) / 2; };
+    for (int co = 0; co < 32; ++co) {
+        double off = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const __half h = __float2half_rn(w[co * K + k] * (1.0f / 255.0f));
+            off += 1024.0 * (double)__half2float(h);
+            out[at(co, k)] = h;
+        }
+        double rb = (double)b[co] - off;
+        for (int k = 29; k < 32; ++k) {
+            const __half h = __float2half_rn((float)rb);
+            rb -= (double)__half2float(h);
+            out[at(co, k)] = h;
+        }
+    }
+}
+
+// Frames 8 to 512 columns wide (a window then fits well inside 48 KB) of
+// fewer than 2^22 pixels (exact FP32-reciprocal division), batches of fewer
+// than 2^31 pixels (32-bit tensor coordinates), and weights whose FP16 forms
+// and 1024-offset bias stay far inside FP16 range.
+bool tc_conv1_supported(int C0, int H, int W, int Cout, int max_frames, const float *w, const float *b) {
+    if (!(C0 >= 1 && C0 <= 3 && Cout == 32 && W >= 8 && W <= 512 && (H * W) % 128 == 0 && H * W < (1 << 22) &&
+          (long long)max_frames * H * W < (1LL << 31)))
+        return false;
     for (int co = 0; co < 32; ++co) {
         double off = std::fabs((double)b[co]);
         for (int k = 0; k < 9 * C0; ++k) off += 1024.0 * std::fabs((double)w[co * 9 * C0 + k] / 255.0);
@@ -295,20 +370,43 @@ bool tc_conv1_supported(int C0, int H, int W, int Cout, const float *w, const fl
     return true;
 }
 
-void launch_conv1_tc(const int *count, const int *list, const unsigned char *frames, int C0, int H, int Wd,
-                     const float *W, const float *bias, __nv_bfloat16 *out, int max_frames, int sms,
-                     unsigned int *err, cudaStream_t st) {
-    long long work = (long long)max_frames * (H * Wd / 128);
-    int grid = (int)(work < (long long)sms * 8 ? work : (long long)sms * 8);
-    if (grid < 1) grid = 1;
+hydro_status launch_conv1_tc(TcConvPlan *plan, const int *count, const int *list, const unsigned char *frames,
+                             int C0, int H, int Wd, const void *Bt, __nv_bfloat16 *out, int max_frames, int sms,
+                             unsigned int *err, cudaStream_t st) {
+    if (!plan->ready || (long long)max_frames * H * Wd >= (1LL << 31)) return HYDRO_EUNSUPPORTED;
+    // the output as rows of 32 BF16 channels, one row per pixel, 128-row boxes
+    CUtensorMap tmOut;
+    {
+        using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                      const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                      CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                      CUtensorMapFloatOOBfill);
+        const cuuint64_t dims[2] = {32, (cuuint64_t)max_frames * H * Wd};
+        const cuuint64_t strides[1] = {64};
+        const cuuint32_t box[2] = {32, 128};
+        const cuuint32_t es[2] = {1, 1};
+        CUresult r = reinterpret_cast<EncodeFn>(plan->encode)(
+            &tmOut, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, out, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return HYDRO_ECUDA;
+    }
+    const long long work = (long long)max_frames * (H * Wd / 128);
     const int vec = ((uintptr_t)frames & 15) == 0 && Wd % 16 == 0;
     const size_t smem = c1_smem_bytes(C0, H, Wd);
+    // persistent: as many CTAs as fit on an SM (1 KB of shared memory is
+    // reserved per CTA; 64 TMEM columns each allow 8), all resident
+    const int per_sm = std::max(1, std::min(8, plan->smem_per_sm / (int)(smem + 1024)));
+    const int grid = (int)std::max(1LL, std::min(work, (long long)sms * per_sm));
+    auto run = [&](auto kern) {
+        kern<<<grid, kC1Threads, smem, st>>>(tmOut, count, list, frames, H, Wd, (const uint4 *)Bt, err, vec);
+    };
     if (C0 == 1)
-        k_conv1_tc<1><<<grid, kC1Threads, smem, st>>>(count, list, frames, H, Wd, W, bias, out, err, vec);
+        run(k_conv1_tc<1>);
     else if (C0 == 2)
-        k_conv1_tc<2><<<grid, kC1Threads, smem, st>>>(count, list, frames, H, Wd, W, bias, out, err, vec);
+        run(k_conv1_tc<2>);
     else
-        k_conv1_tc<3><<<grid, kC1Threads, smem, st>>>(count, list, frames, H, Wd, W, bias, out, err, vec);
+        run(k_conv1_tc<3>);
+    return cudaPeekAtLastError() == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }
 
 }  // namespace hydro
