@@ -770,7 +770,7 @@ def ours(args):
                                 if traffic else None,
                 "peak_source": f"bf16_tflops_sustained ({src})", "launches": d["launches"],
                 "avg_launch_ms": round(d["total_ms"] / max(1, d["launches"]), 4),
-                "note": "per-launch CUDA-event durations on each lane's stream; the two lanes' kernels overlap, "
+                "note": "per-launch CUDA-event durations on each lane's stream; the lanes' kernels overlap, "
                         "so a launch's duration includes the SMs it shares with the other lane's kernels",
                 "achieved_over_step_time": round(d["flops"] / max(1, args.steps) / (secs_max / args.steps) / 1e12, 2)}
     h2d = int(np.prod(Xh.shape))
