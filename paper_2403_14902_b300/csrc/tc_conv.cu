@@ -82,6 +82,9 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int total = (*count) * tiles_per_frame;
     const int ksteps = C::PASSES * nchunks * 3;
+    // a CTA without tiles takes neither barriers nor TMEM (small recheck
+    // bands leave most of the grid idle)
+    if ((int)blockIdx.x >= total) return;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {

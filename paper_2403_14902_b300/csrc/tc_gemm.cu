@@ -98,6 +98,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
     int off[kMaxGroups], cnt[kMaxGroups], start[kMaxGroups + 1];
     group_layout(L, off, cnt, start);
     const int total = start[L.n];
+    // a CTA without tiles takes neither barriers nor TMEM (late rounds and
+    // recheck levels leave most of the grid idle)
+    if ((int)blockIdx.x >= total) return;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
