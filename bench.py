@@ -932,19 +932,25 @@ def ours_mq64(args):
             entry["clocks"] = clocks.stop()
         elif name == HEAD:
             entry["clocks"] = clocks.stop()
-            # per-query latency: every query admitted at t0, done when its last step is
-            t0 = torch.cuda.Event(enable_timing=True)
-            evs = []
-            torch.cuda.synchronize()
-            t0.record(stream)
-            run_all(s, events=evs)
-            torch.cuda.synchronize()
+            # per-query latency: every query admitted at t0, done when its last step is;
+            # each query's median over three passes (a single pass now and then runs
+            # several times slower than the timed passes)
             hplan = mq_plan(w, streams, HK)
             hlast = [max(k for k, (_, c) in enumerate(hplan) if sum(c[q * HK:(q + 1) * HK]) > 0) for q in range(Q)]
-            lat = np.array([t0.elapsed_time(evs[hlast[q]]) for q in range(Q)])
+            reps = []
+            for _ in range(3):
+                t0 = torch.cuda.Event(enable_timing=True)
+                evs = []
+                torch.cuda.synchronize()
+                t0.record(stream)
+                run_all(s, events=evs)
+                torch.cuda.synchronize()
+                reps.append([t0.elapsed_time(evs[hlast[q]]) for q in range(Q)])
+            lat = np.median(np.array(reps), axis=0)
             entry["latency_ms"] = {"p50": round(float(np.percentile(lat, 50)), 3),
                                    "p99": round(float(np.percentile(lat, 99)), 3),
-                                   "max": round(float(lat.max()), 3)}
+                                   "max": round(float(lat.max()), 3), "passes": 3,
+                                   "pass_ms": [round(max(r), 3) for r in reps]}
             # kernel classes and the grouped GEMM's algorithmic flops
             s.profile(True)
             stats = []
