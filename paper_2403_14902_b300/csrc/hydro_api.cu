@@ -669,7 +669,7 @@ void prof_end(hydro_query *q, int e) {
 // sized for max_rows rows/frames.
 hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, const int *list,
                      const void *tuples, int max_rows, void *const act[2], float *score32, double *score64,
-                     const ProfCtx *pc = nullptr) {
+                     const ProfCtx *pc = nullptr, bool band = false) {
     const hydro_query_config &c = q->cfg;
     cudaStream_t st = q->st;
     if (p.kind == HYDRO_UDF_MLP) {
@@ -808,7 +808,7 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
             e = prof_begin(q, pc, cls, fpi, bpi, wb);
             const void *w = prec == PREC_BF16 ? (const void *)p.dWt16[l] : (const void *)p.dWt32[l];
             launch_conv3x3_simt(prec, count, act[cur], p.dims[l], H, Wd, w, p.db[l], p.dims[l + 1], act[1 - cur],
-                                max_rows, q->sms, st);
+                                max_rows, q->sms, st, band);
             prof_end(q, e);
         }
         q->launches++;
@@ -955,7 +955,7 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
             TRY(run_udf(q, p, PREC_F32, b32_count, b32_t, tuples, q->cap1, q->act, q->rscore32, nullptr, &pc_r32));
         } else {
             TRY(run_udf(q, p, PREC_F32, b32_count, b32_t, tuples, tf32_level ? q->cap2 : q->cap1, q->ract32,
-                        q->rscore32, nullptr, &pc_r32));
+                        q->rscore32, nullptr, &pc_r32, true));
         }
         launch_recheck_classify_f32(b32_count, b32_m, b32_t, q->rscore32, p.threshold, p.margin_fp32, q->pass,
                                     q->band3_m, q->band3_t, band3_count, q->cap3, q->d_err, q->st);
@@ -971,7 +971,7 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
         prof_end(q, e);
         q->launches++;
     } else {
-        TRY(run_udf(q, p, PREC_F64, b64_count, b64_t, tuples, q->cap3, q->ract64, nullptr, q->rscore64, &pc_r64));
+        TRY(run_udf(q, p, PREC_F64, b64_count, b64_t, tuples, q->cap3, q->ract64, nullptr, q->rscore64, &pc_r64, true));
     }
     launch_recheck_classify_f64(b64_count, b64_m, b64_t, q->rscore64, p.threshold, q->pass, q->d_err, q->st);
     q->launches += 2;   // recheck classify + compact

@@ -91,7 +91,8 @@ void launch_conv1_split(const int *count, const int *list, const unsigned char *
                         const float *W, const float *bias, int Cout, void *out, int max_frames, int sms,
                         cudaStream_t st, bool bf16_planes = false);
 void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,
-                         const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st);
+                         const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st,
+                         bool band = false);
 void launch_pool_head(int prec, const int *count, const void *act, int HW, int C, const float *hw, double hb,
                       void *score, int max_frames, int sms, cudaStream_t st);
 

@@ -296,42 +296,46 @@ template <> __device__ __forceinline__ __nv_bfloat16 st_as<__nv_bfloat16, float>
 // conv3x3 (stride 1, zero pad 1) + bias + ReLU on NHWC activations of the
 // first *count frames, as an implicit GEMM on CUDA cores:
 //   out[m][p][co] = relu(b[co] + sum_{tap, ci} in[m][p + shift(tap)][ci] * Wt[tap][ci][co])
-// Tiles of 128 pixels x 64 output channels; K walks (tap, 16 input channels).
+// Tiles of PX (128 or 64) pixels x 64 output channels; K walks (tap, 16 input
+// channels), so a tile's latency is its K loop: recheck bands of a few frames
+// take 64-pixel tiles (half the work per step, twice the CTAs).
 // Requires Cin % 16 == 0, Cout % 64 == 0, H*W % 128 == 0.
-template <typename Tin, typename Tw, typename T, typename Tout>
+template <int PX, typename Tin, typename Tw, typename T, typename Tout>
 __global__ void __launch_bounds__(256)
 k_conv3x3_simt(const int *count, const Tin *in, int Cin, int H, int Wd, const Tw *Wt, const float *bias,
                int Cout, Tout *out) {
-    __shared__ T As[16][128 + 4];
+    constexpr int RI = PX / 16;       // output pixels per thread, A elements per loader thread
+    constexpr int APT = 16 / RI;      // loader threads per pixel
+    __shared__ T As[16][PX + 4];
     __shared__ T Bs[16][64 + 4];
     const int M = *count;
     const int HW = H * Wd;
-    const int tiles_p = HW / 128, tiles_c = Cout / 64;
+    const int tiles_p = HW / PX, tiles_c = Cout / 64;
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-    const int apx = t >> 1, ach = (t & 1) * 8;   // A loader: pixel, channel offset
+    const int apx = t / APT, ach = (t % APT) * RI;   // A loader: pixel, channel offset
     const int bk = t >> 4, bn = (t & 15) * 4;    // B loader: k row, channel offset
     for (long long tile = blockIdx.x; tile < (long long)M * tiles_p * tiles_c; tile += gridDim.x) {
         const int m = (int)(tile / (tiles_p * tiles_c));
         const int r = (int)(tile % (tiles_p * tiles_c));
-        const int p0 = (r / tiles_c) * 128, co0 = (r % tiles_c) * 64;
+        const int p0 = (r / tiles_c) * PX, co0 = (r % tiles_c) * 64;
         const Tin *fin = in + (size_t)m * HW * Cin;
         const int ap = p0 + apx, ay = ap / Wd, ax = ap % Wd;
-        T acc[8][4];
+        T acc[RI][4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < RI; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
         // K steps (tap, 16 input channels); the next step's operands are loaded
         // into registers while this step's multiply-adds run (latency hiding)
         const int csteps = Cin / 16, nsteps = 9 * csteps;
-        T ra[8], rw[4];
+        T ra[RI], rw[4];
         auto fetch = [&](int s) {
             const int tap = s / csteps, ci0 = (s % csteps) * 16;
             const int yy = ay + tap / 3 - 1, xx = ax + tap % 3 - 1;
             const bool inb = yy >= 0 && yy < H && xx >= 0 && xx < Wd;
             const Tin *src = fin + ((size_t)(inb ? yy : 0) * Wd + (inb ? xx : 0)) * Cin + ci0 + ach;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) ra[e] = inb ? ld_as<T>(src + e) : (T)0;
+            for (int e = 0; e < RI; ++e) ra[e] = inb ? ld_as<T>(src + e) : (T)0;
             const Tw *wsrc = Wt + ((size_t)tap * Cin + ci0 + bk) * Cout + co0 + bn;
 #pragma unroll
             for (int e = 0; e < 4; ++e) rw[e] = ld_as<T>(wsrc + e);
@@ -339,28 +343,28 @@ k_conv3x3_simt(const int *count, const Tin *in, int Cin, int H, int Wd, const Tw
         fetch(0);
         for (int s = 0; s < nsteps; ++s) {
 #pragma unroll
-            for (int e = 0; e < 8; ++e) As[ach + e][apx] = ra[e];
+            for (int e = 0; e < RI; ++e) As[ach + e][apx] = ra[e];
 #pragma unroll
             for (int e = 0; e < 4; ++e) Bs[bk][bn + e] = rw[e];
             __syncthreads();
             if (s + 1 < nsteps) fetch(s + 1);
 #pragma unroll
             for (int kk = 0; kk < 16; ++kk) {
-                T a[8], w[4];
+                T a[RI], w[4];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) a[i] = As[kk][ty * 8 + i];
+                for (int i = 0; i < RI; ++i) a[i] = As[kk][ty * RI + i];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) w[j] = Bs[kk][tx * 4 + j];
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < RI; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * w[j];
             }
             __syncthreads();
         }
-        Tout *o = out + ((size_t)m * HW + p0 + ty * 8) * Cout + co0 + tx * 4;
+        Tout *o = out + ((size_t)m * HW + p0 + ty * RI) * Cout + co0 + tx * 4;
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < RI; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 T v = acc[i][j] + (T)bias[co0 + tx * 4 + j];
@@ -513,20 +517,28 @@ void launch_conv1_split(const int *count, const int *list, const unsigned char *
 }
 
 void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,
-                         const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st) {
-    const long long tiles = (long long)max_frames * (H * Wd / 128) * (Cout / 64);
+                         const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st, bool band) {
+    const int px = band ? 64 : 128;
+    const long long tiles = (long long)max_frames * (H * Wd / px) * (Cout / 64);
     int grid = tiles < grid_for(sms, 4) ? (int)tiles : grid_for(sms, 4);
     if (grid < 1) grid = 1;
-    if (prec == PREC_F64)
-        k_conv3x3_simt<double, float, double, double><<<grid, 256, 0, st>>>(
-            count, (const double *)in, Cin, H, Wd, (const float *)Wt, bias, Cout, (double *)out);
-    else if (prec == PREC_F32)
-        k_conv3x3_simt<float, float, float, float><<<grid, 256, 0, st>>>(
-            count, (const float *)in, Cin, H, Wd, (const float *)Wt, bias, Cout, (float *)out);
-    else
-        k_conv3x3_simt<__nv_bfloat16, __nv_bfloat16, float, __nv_bfloat16><<<grid, 256, 0, st>>>(
-            count, (const __nv_bfloat16 *)in, Cin, H, Wd, (const __nv_bfloat16 *)Wt, bias, Cout,
-            (__nv_bfloat16 *)out);
+    auto run = [&](auto kern, const auto *xin, const auto *w, auto *xout) {
+        kern<<<grid, 256, 0, st>>>(count, xin, Cin, H, Wd, w, bias, Cout, xout);
+    };
+    if (prec == PREC_F64) {
+        if (band)
+            run(k_conv3x3_simt<64, double, float, double, double>, (const double *)in, (const float *)Wt, (double *)out);
+        else
+            run(k_conv3x3_simt<128, double, float, double, double>, (const double *)in, (const float *)Wt, (double *)out);
+    } else if (prec == PREC_F32) {
+        if (band)
+            run(k_conv3x3_simt<64, float, float, float, float>, (const float *)in, (const float *)Wt, (float *)out);
+        else
+            run(k_conv3x3_simt<128, float, float, float, float>, (const float *)in, (const float *)Wt, (float *)out);
+    } else {
+        run(k_conv3x3_simt<128, __nv_bfloat16, __nv_bfloat16, float, __nv_bfloat16>, (const __nv_bfloat16 *)in,
+            (const __nv_bfloat16 *)Wt, (__nv_bfloat16 *)out);
+    }
 }
 
 void launch_pool_head(int prec, const int *count, const void *act, int HW, int C, const float *hw, double hb,
