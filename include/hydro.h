@@ -79,7 +79,9 @@ enum {
 enum {
     HYDRO_PREC_FP32 = 0,   /* FP32 everywhere; FP32 scores within margin_fp32 of the
                               threshold are re-evaluated in FP64 */
-    HYDRO_PREC_BF16 = 1,   /* BF16 operands, FP32 accumulation on the tensor cores;
+    HYDRO_PREC_BF16 = 1,   /* BF16 operands, FP32 accumulation on the tensor cores (the
+                              first CNN layer takes FP16 operands: pixels exact as 1024 + b,
+                              weights W/255 in FP16, bias folded in; frames 8..512 wide);
                               scores within margin_lowp are re-evaluated more accurately:
                               CNN UDFs first on the tensor cores in split BF16 or 3xTF32
                               (split_precision; scores within margin_tf32 go on), then in FP32
