@@ -335,11 +335,13 @@ HYDRO_API hydro_status hydro_profile_read(hydro_query *q, hydro_kernel_profile *
                                           int64_t *total_launches);
 
 /* Allocation-free FP32 MLP scores.  The paper has no counterpart: this
- * entry point is for callers that cannot allocate device memory while they
- * run, such as code recording a CUDA graph (cudaMalloc is not permitted
- * during stream capture) or code inside a framework that owns the device
- * memory pool.  It computes the same scores as hydro_udf_scores(FP32) on an
- * MLP UDF, with the caller's device buffers:
+ * entry point is for callers that cannot allocate device memory once they
+ * are running: code inside a framework that owns the device memory pool and
+ * forbids allocations from outside it, a latency-bound service that cannot
+ * take the device-wide synchronisation and unbounded time of a cudaMalloc,
+ * or a process that reserved nearly all device memory up front.  It
+ * computes the same scores as hydro_udf_scores(FP32) on an MLP UDF, with
+ * the caller's device buffers:
  *   d_x        device fp32 [n][dims[0]] tuples
  *   dims       host, n_layers+1 widths, dims[n_layers] == 1
  *   d_weights  host array of n_layers DEVICE pointers, layer l [dims[l+1]][dims[l]]
@@ -352,7 +354,8 @@ HYDRO_API hydro_status hydro_profile_read(hydro_query *q, hydro_kernel_profile *
  * hidden layer must not exceed 1,048,576 (else HYDRO_EINVAL).  It calls no
  * allocator.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current, so make that
- * first call before any stream capture.  All calls share the array and keep
+ * first call before any stream capture.  The address is kept for the life
+ * of the process: do not cudaDeviceReset a device this entry point is used on.  All calls share the array and keep
  * the last call's contents: calls whose kernels overlap on the GPU (other
  * streams, other threads) race on it and must be serialised by the caller.
  * Asynchronous on `stream`; errors are returned as status codes. */

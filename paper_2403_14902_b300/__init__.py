@@ -392,8 +392,34 @@ class Query:
 def mlp_scores_noalloc(x, weights, biases, out, stream=None):
     """FP32 MLP scores with no device allocation (see hydro.h): ``x`` device
     fp32 [n, dim]; ``weights``/``biases`` lists of device fp32 tensors
-    ([out, in] / [out]); ``out`` device float64 [n]."""
+    ([out, in] / [out]); ``out`` device float64 [n].
+
+    The C entry point takes raw pointers and cannot see shapes, dtypes or
+    strides, so every tensor is checked here first (ValueError on a
+    mismatch): a wrong shape or dtype would make its kernels read or write
+    outside the caller's buffers."""
+    import torch
+
+    def _need(ok, what):
+        if not ok:
+            raise ValueError(f"mlp_scores_noalloc: {what}")
+
+    _need(isinstance(x, torch.Tensor) and x.is_cuda and x.dim() == 2 and x.dtype == torch.float32
+          and x.is_contiguous(), "x must be a contiguous 2-D float32 CUDA tensor")
+    _need(len(weights) >= 1 and len(weights) == len(biases), "need one bias per weight, at least one layer")
+    dev = x.device
     dims = [int(x.shape[1])] + [int(w.shape[0]) for w in weights]
+    for l, (W, b) in enumerate(zip(weights, biases)):
+        _need(isinstance(W, torch.Tensor) and W.device == dev and W.dtype == torch.float32 and W.is_contiguous()
+              and W.dim() == 2 and tuple(W.shape) == (dims[l + 1], dims[l]),
+              f"weight {l} must be a contiguous float32 tensor of shape ({dims[l + 1]}, {dims[l]}) on {dev}")
+        _need(isinstance(b, torch.Tensor) and b.device == dev and b.dtype == torch.float32 and b.is_contiguous()
+              and b.numel() == dims[l + 1], f"bias {l} must be a contiguous float32 tensor of {dims[l + 1]} "
+              f"elements on {dev}")
+    _need(dims[-1] == 1, "the last layer must have one output")
+    _need(isinstance(out, torch.Tensor) and out.device == dev and out.dtype == torch.float64 and out.is_contiguous()
+          and out.numel() >= int(x.shape[0]), f"out must be a contiguous float64 tensor of >= {x.shape[0]} "
+          f"elements on {dev}")
     d = (ctypes.c_int32 * len(dims))(*dims)
     wp = (ctypes.c_void_p * len(weights))(*[w.data_ptr() for w in weights])
     bp = (ctypes.c_void_p * len(biases))(*[b.data_ptr() for b in biases])

@@ -2,11 +2,13 @@
 // query path, with the inter-layer activations in a fixed device array that
 // lives in this library's module instead of memory from cudaMalloc.
 //
-// Who needs this: callers that must not allocate device memory while they
-// run, e.g. code that is recording a CUDA graph (cudaMalloc is not allowed
-// during stream capture) or code inside a framework that owns the device
-// memory pool and forbids outside allocations during its steps.  They pass
-// their own inputs, weights and outputs; the library allocates nothing.
+// Who needs this: callers that must not allocate device memory once they
+// are running.  A framework that owns the device memory pool may forbid
+// allocations from outside it during its steps; a latency-bound service may
+// not take the device-wide synchronisation and unbounded time a cudaMalloc
+// can cost; a process that reserved nearly all device memory up front has
+// nothing left to allocate from.  They pass their own inputs, weights and
+// outputs; the library allocates nothing.
 #include <cstdio>
 #include <mutex>
 
@@ -62,11 +64,11 @@ extern "C" HYDRO_API hydro_status hydro_mlp_scores_noalloc(const float *d_x, int
     }
     for (int l = 0; l < n_layers; ++l)
         if (!d_weights[l] || !d_biases[l]) return noalloc_fail(HYDRO_EINVAL, "NULL weights");
-    if (n * wmax > kNoAllocFloats)
+    // n is bounded before any product is formed, so nothing here can overflow
+    if (n > kNoAllocFloats || n > kNoAllocFloats / wmax)
         return noalloc_fail(HYDRO_EINVAL,
                             "n * widest hidden layer exceeds the static scratch of 1,048,576 floats per buffer");
     if (n == 0) return HYDRO_OK;
-    if (n > (1LL << 30)) return noalloc_fail(HYDRO_EINVAL, "n too large");
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
@@ -75,7 +77,10 @@ extern "C" HYDRO_API hydro_status hydro_mlp_scores_noalloc(const float *d_x, int
     }
     float *base = nullptr;
     {
-        // once per device, with that device current: device address of the array
+        // once per device, with that device current: device address of the
+        // array.  The address is kept for the life of the process; after a
+        // cudaDeviceReset of that device it is stale (the module is unloaded),
+        // so callers must not reset a device they keep using this entry point on.
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
         if (!g_noalloc_ptr[dev]) {
             void *p = nullptr;
@@ -96,7 +101,7 @@ extern "C" HYDRO_API hydro_status hydro_mlp_scores_noalloc(const float *d_x, int
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float *act[2] = {base, base + kNoAllocFloats};
     int *count = reinterpret_cast<int *>(base + 2 * kNoAllocFloats);
-    float *score32 = act[1];   // the last layer reads act[cur] and writes here only when cur == 0
+    float *score32 = nullptr;   // the buffer the last layer writes; every branch below sets it
     const int rows = (int)n;
     // the row count is rewritten on every call before any kernel reads it
     k_set_count<<<1, 32, 0, st>>>(count, rows);
