@@ -96,7 +96,10 @@ enum {
                               over [hi | hi | lo] x [W_hi | W_lo | W_hi] (about 16 significant bits);
                               the first recheck level of BF16 sessions
                               (hydro_session_udf_scores) and, by default, of BF16 CNN queries
-                              ([hi | lo] BF16 planes of the activations and weights) */
+                              ([hi | lo] BF16 planes of the activations and weights).  As the
+                              working precision of a frame (CNN) query it gives FP32-class
+                              scores on the tensor cores: scores within margin_tf32 go to FP32
+                              on CUDA cores, and those within margin_fp32 on to FP64 */
     HYDRO_PREC_FP8 = 5     /* sessions only: the first layer of every pool UDF in the FP8 set
                               (first hidden width >= fp8_min_width) runs with E4M3 operands on
                               the tensor cores (kind::f8f6f4, FP32 accumulation): weights scaled
@@ -133,7 +136,9 @@ typedef struct hydro_query_config {
     int32_t width;           /* U8_FRAME: frame width (64) */
     int32_t max_batch;       /* largest n a submit may pass, 1..65536 */
     int32_t policy;          /* HYDRO_POLICY_* */
-    int32_t precision;       /* HYDRO_PREC_FP32 or HYDRO_PREC_BF16 */
+    int32_t precision;       /* HYDRO_PREC_FP32, HYDRO_PREC_BF16, or (U8_FRAME tuples, CNN
+                                UDFs whose layers after the first run on the tensor cores)
+                                HYDRO_PREC_BF16X3 */
     int32_t cost_source;     /* HYDRO_COST_* */
     int32_t warmup_batches;  /* adaptive policies: the first batches evaluate every
                                 predicate on every tuple (Sec. 4.1 "Warmup Phase") */
@@ -158,6 +163,12 @@ typedef struct hydro_query_config {
                                 operands, three BF16 passes) or HYDRO_PREC_TF32X3 (3xTF32).  On the
                                 CNN workload split BF16 runs at twice the MMA rate with half the
                                 operand bytes and misses FP64 by less than 3xTF32 does */
+    int32_t recheck_graphs;  /* 1 (hydro_default_config): a stage's recheck levels replay from a
+                                CUDA graph captured once per stream lane and predicate, each
+                                level an IF node that runs only when its band is not empty (the
+                                band's tuples are first copied to a per-lane staging buffer, so
+                                the graph never sees the batch's own tuple pointer); 0: every
+                                level's kernels are launched for every stage, empty or not */
 } hydro_query_config;
 
 typedef struct hydro_udf_desc {
@@ -324,12 +335,15 @@ HYDRO_API hydro_status hydro_get_stats(hydro_query *q, hydro_pred_stats *out, in
 /* Start (enable = 1, clearing earlier records) or stop (enable = 0)
  * per-launch timing of the UDF layer kernels: each recorded launch is
  * bracketed by CUDA events on the query's stream.  Also resets the launch
- * counter read by hydro_profile_read. */
+ * counter read by hydro_profile_read (waits for the query's batches to
+ * finish first).  With recheck_graphs the recheck levels replay from graphs
+ * and are not timed; their kernels are counted on the device. */
 HYDRO_API hydro_status hydro_profile(hydro_query *q, int32_t enable);
 
 /* Per kernel class totals since the last hydro_profile(q, 1), for batches
  * polled since then.  out[max] receives up to max classes, *n_out how many;
- * *total_launches (nullable) every kernel this query launched since then.
+ * *total_launches (nullable) every kernel this query launched since then,
+ * counting inside recheck graphs the gates and the bodies that ran.
  * Synchronises the query's stream. */
 HYDRO_API hydro_status hydro_profile_read(hydro_query *q, hydro_kernel_profile *out, int32_t max, int32_t *n_out,
                                           int64_t *total_launches);

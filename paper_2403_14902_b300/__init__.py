@@ -52,7 +52,7 @@ class QueryConfig(ctypes.Structure):
                 ("route_lag", ctypes.c_int32), ("max_in_flight", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("proxy_hidden", ctypes.c_int32), ("proxy_refresh", ctypes.c_int32),
                 ("proxy_epochs", ctypes.c_int32), ("proxy_lr", ctypes.c_float), ("proxy_seed", ctypes.c_int32),
-                ("lanes", ctypes.c_int32), ("split_precision", ctypes.c_int32)]
+                ("lanes", ctypes.c_int32), ("split_precision", ctypes.c_int32), ("recheck_graphs", ctypes.c_int32)]
 
 
 class UdfDesc(ctypes.Structure):
@@ -201,7 +201,7 @@ class Query:
                  precision: str = "fp32", warmup: int = 1, window: int = 8, lag: int = 1,
                  max_in_flight: int = 4, device: int = 0, stream=None, proxy_hidden: int = 64,
                  proxy_refresh: int = 16, proxy_epochs: int = 2, proxy_lr: float = 1e-3, proxy_seed: int = 1,
-                 lanes: int = 1, cost: str = "model", split: str = "bf16x3"):
+                 lanes: int = 1, cost: str = "model", split: str = "bf16x3", recheck_graphs: bool = True):
         L = load()
         cfg = QueryConfig()
         L.hydro_default_config(ctypes.byref(cfg))
@@ -225,7 +225,9 @@ class Query:
         cfg.lanes = lanes
         cfg.cost_source = COSTS[cost]
         cfg.split_precision = PRECISIONS[split]
+        cfg.recheck_graphs = 1 if recheck_graphs else 0
         self.kind = kind
+        self.policy = policy
         self.cfg = cfg
         self._h = ctypes.c_void_p()
         _check(L.hydro_create_query(ctypes.byref(cfg), ctypes.byref(self._h)), "hydro_create_query")

@@ -164,6 +164,7 @@ struct LaneBufs {
     void *act[2] = {}, *ract32[2] = {}, *ract64[2] = {};
     float *partials = nullptr;
     __nv_bfloat16 *stage16 = nullptr, *act16[2] = {};
+    void *band_rows = nullptr;
 };
 
 struct hydro_query {
@@ -243,6 +244,17 @@ struct hydro_query {
     bool own_lane_st[kMaxLanes] = {};
     cudaEvent_t ev_user = nullptr;   // input-ready point on the caller's stream (the batch's lane waits on it)
     cudaStream_t home_st = nullptr;  // with two lanes: the caller's (or the library's) stream
+    int cur_lane = 0;
+    // recheck graphs: the recheck levels of predicate p on lane l replay from tail[l][p]
+    void *band_rows = nullptr;       // current lane's staging buffer of the band's tuples [cap1][tuple bytes]
+    cudaGraphExec_t tail[kMaxLanes][kMaxPred] = {};
+    int tail_gates[kMaxLanes][kMaxPred] = {};
+    int *d_body_n = nullptr;         // [kMaxLanes][kMaxPred][3] kernels per conditional body
+    unsigned long long *d_launch_ctr = nullptr;   // kernels the conditional bodies ran
+    cudaStream_t cap_st = nullptr, cap_body_st = nullptr;
+    bool capturing = false;
+    cudaGraph_t cap_graph = nullptr;
+    std::vector<std::pair<int *, int>> cap_body_counts;   // (device slot, kernels) of the bodies just captured
 };
 
 namespace {
@@ -288,6 +300,13 @@ long long model_cost(const Pred &p, const hydro_query_config &c) {
         f += 2LL * p.dims[p.n_layers];
     }
     return f;
+}
+
+// Tensor-core query: BF16 working precision, or split BF16 as the working
+// precision of a frame query (FP32-class scores on the tensor cores).  Both
+// prepare the same tensor-core weights and buffers.
+bool tc_query(const hydro_query_config &c) {
+    return c.precision == HYDRO_PREC_BF16 || c.precision == HYDRO_PREC_BF16X3;
 }
 
 bool adaptive(int policy) {
@@ -393,12 +412,13 @@ hydro_status alloc_scratch(hydro_query *q) {
     TRY(dalloc(q, &q->rscore64, sizeof(double) * std::max(q->cap1, q->cap3)));
     if (cnn) {
         const size_t px = (size_t)c.height * c.width * wmax;
+        // BF16 activations, or [hi | lo] BF16 planes (split working precision) / FP32
         const size_t esz = c.precision == HYDRO_PREC_BF16 ? 2 : 4;
         for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->act[k], esz * px * B));
-        if (c.precision == HYDRO_PREC_BF16)   // 3xTF32 (two fp32 planes) and FP32 recheck levels
+        if (tc_query(c))   // 3xTF32 (two fp32 planes) and FP32 recheck levels
             for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->ract32[k], 8 * px * std::max(q->cap1, q->cap2)));
         for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->ract64[k], 8 * px * q->cap3));
-        if (c.precision == HYDRO_PREC_BF16)
+        if (tc_query(c))
             TRY(dalloc(q, &q->partials, sizeof(float) * (size_t)B * (c.height * c.width / 128) * 4));
     } else {
         for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->act[k], sizeof(float) * (size_t)wmax * B));
@@ -411,6 +431,7 @@ hydro_status alloc_scratch(hydro_query *q) {
             if (s != HYDRO_OK) return fail(s, "tensor-core GEMM init failed: %s", tc_gemm_last_error());
         }
     }
+    if (c.recheck_graphs) TRY(dalloc(q, (unsigned char **)&q->band_rows, (size_t)q->cap1 * tuple_bytes(c)));
     return HYDRO_OK;
 }
 
@@ -438,6 +459,7 @@ void save_lane(hydro_query *q, int l) {
     L.rscore64 = q->rscore64;
     L.partials = q->partials;
     L.stage16 = q->stage16;
+    L.band_rows = q->band_rows;
 }
 
 // Make lane l current: its scratch and its stream.
@@ -465,7 +487,9 @@ void load_lane(hydro_query *q, int l) {
     q->rscore64 = L.rscore64;
     q->partials = L.partials;
     q->stage16 = L.stage16;
+    q->band_rows = L.band_rows;
     q->st = q->lane_st[l];
+    q->cur_lane = l;
 }
 
 // Every lane's work done; lane 0 current (calls that use the scratch outside batches).
@@ -527,6 +551,14 @@ hydro_status finalize(hydro_query *q) {
     CU(cudaMemset(q->d_err, 0, sizeof(unsigned int)));
     TRY(dalloc(q, &q->vmiss, sizeof(int) * kMaxPred));
     TRY(dalloc(q, &q->miss_list, sizeof(int) * B));
+    if (c.recheck_graphs) {
+        TRY(dalloc(q, &q->d_body_n, sizeof(int) * kMaxLanes * kMaxPred * 3));
+        CU(cudaMemset(q->d_body_n, 0, sizeof(int) * kMaxLanes * kMaxPred * 3));
+        TRY(dalloc(q, &q->d_launch_ctr, sizeof(unsigned long long)));
+        CU(cudaMemset(q->d_launch_ctr, 0, sizeof(unsigned long long)));
+        CU(cudaStreamCreateWithFlags(&q->cap_st, cudaStreamNonBlocking));
+        CU(cudaStreamCreateWithFlags(&q->cap_body_st, cudaStreamNonBlocking));
+    }
     for (Emb &e : q->embs) {
         e.dW.resize(e.n_layers);
         e.db.resize(e.n_layers);
@@ -585,8 +617,8 @@ hydro_status finalize(hydro_query *q) {
             p.dWtc.assign(p.n_layers, nullptr);
             p.dWts.assign(p.n_layers, nullptr);
             p.dWbs.assign(p.n_layers, nullptr);
-            p.tc_all = c.precision == HYDRO_PREC_BF16 && p.n_layers > 1;
-            p.tc_conv1 = c.precision == HYDRO_PREC_BF16 &&
+            p.tc_all = tc_query(c) && p.n_layers > 1;
+            p.tc_conv1 = tc_query(c) &&
                          tc_conv1_supported(c.channels, c.height, c.width, p.dims[1], c.max_batch, p.W[0].data(),
                                             p.b[0].data());
             if (p.tc_conv1) {
@@ -608,7 +640,7 @@ hydro_status finalize(hydro_query *q) {
                         }
                 TRY(upload(q, &p.dWt32[l], t32.data(), t32.size()));
                 TRY(upload(q, &p.dWt16[l], t16.data(), t16.size()));
-                if (c.precision == HYDRO_PREC_BF16 && tc_conv_supported(ci_n, co_n, c.height, c.width)) {
+                if (tc_query(c) && tc_conv_supported(ci_n, co_n, c.height, c.width)) {
                     std::vector<__nv_bfloat16> tc;
                     tc_conv_pack_weights(p.W[l].data(), ci_n, co_n, tc);
                     __nv_bfloat16 *d = nullptr;
@@ -629,10 +661,12 @@ hydro_status finalize(hydro_query *q) {
                 }
             }
         }
+        if (c.precision == HYDRO_PREC_BF16X3 && !p.tc_all)
+            return fail(HYDRO_EUNSUPPORTED, "split-BF16 working precision needs tensor-core CNN layers");
         if (p.margin_fp32 < 0.0) p.margin_fp32 = 1e-5 * std::max(1.0, std::fabs(p.threshold));
         if (p.margin_tf32 < 0.0) p.margin_tf32 = 5e-3 * std::max(1.0, std::fabs(p.threshold));
     }
-    if (cnn && c.precision == HYDRO_PREC_BF16) {
+    if (cnn && tc_query(c)) {
         hydro_status s = tc_conv_init(&q->tc, c.device);
         if (s != HYDRO_OK) return fail(s, "tensor-core conv init failed: %s", tc_conv_last_error());
     }
@@ -889,12 +923,174 @@ hydro_status run_grouped(hydro_query *q, const Pred &p, const int *count, const 
 // One stage: evaluate predicate p on the alive list (in_list, in_count),
 // decide pass/fail exactly and close the stage.  Scores within a level's
 // margin of the threshold go to the next level of the cascade:
-//   BF16 query, CNN UDF: BF16 tensor cores -> 3xTF32 tensor cores -> FP32 CUDA cores -> FP64
-//   BF16 query, MLP UDF: (not built)
-//   FP32 query:          FP32 -> FP64
+//   BF16 query, CNN UDF:       BF16 tensor cores -> split BF16 (or 3xTF32) tensor cores
+//                              -> FP32 CUDA cores -> FP64
+//   split-BF16 query (CNN):    split BF16 tensor cores -> FP32 CUDA cores -> FP64
+//   BF16 query, MLP UDF:       BF16 tensor cores -> FP32 -> FP64
+//   FP32 query:                FP32 -> FP64
 // The first recheck level of BF16 tensor-core CNN UDFs (hydro_query_config.split_precision).
 int split_prec(const hydro_query_config &c) {
     return c.split_precision == HYDRO_PREC_TF32X3 ? PREC_TF32X3 : PREC_BF16X3;
+}
+
+// The recheck levels of stage pi, after the working-precision classify has
+// filled band 1; `bt` is what the band entries index (the batch's tuples, or
+// the lane's staging buffer).  Directly: every level's kernels are launched.
+// While capturing (q->capturing): each level is a gate kernel followed by an
+// IF node whose body holds the level's kernels, so a level with an empty band
+// costs one tiny kernel.
+hydro_status enqueue_rechecks(hydro_query *q, int pi, const void *bt, long long batch) {
+    const hydro_query_config &c = q->cfg;
+    const Pred &p = q->preds[pi];
+    const bool bf16 = tc_query(c);
+    const bool cnn = p.kind == HYDRO_UDF_CNN;
+    const bool tf32_level = c.precision == HYDRO_PREC_BF16 && cnn && p.tc_all && q->partials;
+    int *band1_count = q->ints + 2, *band2_count = q->ints + 3, *band3_count = q->ints + 4;
+    const bool cap = q->capturing;
+    const ProfCtx pc_rtf{batch, pi, SRC_RTF}, pc_r32{batch, pi, SRC_R32}, pc_r64{batch, pi, SRC_R64};
+    const ProfCtx *prtf = cap ? nullptr : &pc_rtf, *pr32 = cap ? nullptr : &pc_r32, *pr64 = cap ? nullptr : &pc_r64;
+    int gate = 0;
+    // one level: directly, or as gate + IF node (body captured on the body stream)
+    auto level = [&](const int *count, int *z0, int *z1, auto body) -> hydro_status {
+        if (!cap) return body();
+        if (gate >= 3) return fail(HYDRO_ECUDA, "more than three recheck levels");
+        cudaGraphConditionalHandle h;
+        CU(cudaGraphConditionalHandleCreate(&h, q->cap_graph, 0, cudaGraphCondAssignDefault));
+        int *body_n = q->d_body_n + ((size_t)q->cur_lane * kMaxPred + pi) * 3 + gate;
+        launch_gate(count, (unsigned long long)h, z0, z1, q->d_launch_ctr, body_n, q->st);
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        const cudaGraphEdgeData *ed = nullptr;
+        size_t nd = 0;
+        CU(cudaStreamGetCaptureInfo(q->st, &cs, nullptr, &g, &deps, &ed, &nd));
+        alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
+        std::memset(pbuf, 0, sizeof pbuf);
+        cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(pbuf);   // zeroed, as the API requires
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        CU(cudaGraphAddNode(&node, g, deps, ed, nd, &np));
+        CU(cudaStreamUpdateCaptureDependencies(q->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        CU(cudaStreamBeginCaptureToGraph(q->cap_body_st, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal));
+        const cudaStream_t top = q->st;
+        q->st = q->cap_body_st;
+        const long long l0 = q->launches;
+        hydro_status rs = body();
+        const int n_body = (int)(q->launches - l0);
+        cudaGraph_t out = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(q->cap_body_st, &out);
+        q->st = top;
+        if (rs != HYDRO_OK) return rs;
+        CU(ee);
+        q->cap_body_counts.push_back({body_n, n_body});   // written once the capture has ended
+        ++gate;
+        q->launches = l0 + 1;   // at capture time only the gate is a launch of every replay
+        return HYDRO_OK;
+    };
+    const int *b64_count = band1_count, *b64_m = q->band1_m, *b64_t = q->band1_t;
+    if (bf16) {
+        // FP32-level input: band 1 directly, or what the split level leaves undecided
+        const int *b32_count = band1_count, *b32_m = q->band1_m, *b32_t = q->band1_t;
+        if (tf32_level) {
+            TRY(level(band1_count, band2_count, band3_count, [&]() -> hydro_status {
+                TRY(run_udf(q, p, split_prec(c), band1_count, q->band1_t, bt, q->cap1, q->ract32, q->rscore_t,
+                            nullptr, prtf));
+                launch_recheck_classify_f32(band1_count, q->band1_m, q->band1_t, q->rscore_t, p.threshold,
+                                            p.margin_tf32, q->pass, q->band2_m, q->band2_t, band2_count, q->cap2,
+                                            q->d_err, q->st);
+                q->launches++;
+                return HYDRO_OK;
+            }));
+            b32_count = band2_count;
+            b32_m = q->band2_m;
+            b32_t = q->band2_t;
+        }
+        TRY(level(b32_count, band3_count, nullptr, [&]() -> hydro_status {
+            if (!cnn && p.upstream) {
+                const int e = prof_begin(q, pr32, PC_BAND32, (double)p.cost, 4.0 * c.dim, 0);
+                launch_mlp_band_f32(b32_count, b32_t, (const float *)bt, c.dim, p.mlp, q->rscore32, q->sms, q->st);
+                prof_end(q, e);
+                q->launches++;
+            } else if (!cnn) {
+                // the band as a (short) GEMM: weight tiles shared by the band's rows
+                TRY(run_udf(q, p, PREC_F32, b32_count, b32_t, bt, q->cap1, q->act, q->rscore32, nullptr, pr32));
+            } else {
+                TRY(run_udf(q, p, PREC_F32, b32_count, b32_t, bt, tf32_level ? q->cap2 : q->cap1, q->ract32,
+                            q->rscore32, nullptr, pr32, true));
+            }
+            launch_recheck_classify_f32(b32_count, b32_m, b32_t, q->rscore32, p.threshold, p.margin_fp32, q->pass,
+                                        q->band3_m, q->band3_t, band3_count, q->cap3, q->d_err, q->st);
+            q->launches++;
+            return HYDRO_OK;
+        }));
+        b64_count = band3_count;
+        b64_m = q->band3_m;
+        b64_t = q->band3_t;
+    }
+    TRY(level(b64_count, nullptr, nullptr, [&]() -> hydro_status {
+        if (!cnn) {
+            const int e = prof_begin(q, pr64, PC_BAND64, (double)p.cost, 4.0 * c.dim, 0);
+            launch_mlp_band_f64(b64_count, b64_t, (const float *)bt, c.dim, p.mlp, q->rscore64, q->sms, q->st);
+            prof_end(q, e);
+            q->launches++;
+        } else {
+            TRY(run_udf(q, p, PREC_F64, b64_count, b64_t, bt, q->cap3, q->ract64, nullptr, q->rscore64, pr64, true));
+        }
+        launch_recheck_classify_f64(b64_count, b64_m, b64_t, q->rscore64, p.threshold, q->pass, q->d_err, q->st);
+        q->launches++;
+        return HYDRO_OK;
+    }));
+    return HYDRO_OK;
+}
+
+// Capture the recheck levels of predicate pi on the current lane into a graph
+// (once per lane and predicate): its tuples are the lane's staging buffer.
+hydro_status ensure_tail(hydro_query *q, int pi) {
+    const int l = q->cur_lane;
+    if (q->tail[l][pi]) return HYDRO_OK;
+    const cudaStream_t saved = q->st;
+    const long long l0 = q->launches;
+    q->st = q->cap_st;
+    q->cap_body_counts.clear();
+    CU(cudaStreamBeginCapture(q->cap_st, cudaStreamCaptureModeThreadLocal));
+    cudaStreamCaptureStatus cs;
+    hydro_status rs = HYDRO_OK;
+    if (cudaStreamGetCaptureInfo(q->cap_st, &cs, nullptr, &q->cap_graph, nullptr, nullptr, nullptr) != cudaSuccess)
+        rs = fail(HYDRO_ECUDA, "capture info of the recheck graph");
+    q->capturing = true;
+    if (rs == HYDRO_OK) rs = enqueue_rechecks(q, pi, q->band_rows, -1);
+    q->capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(q->cap_st, &g);
+    q->st = saved;
+    q->cap_graph = nullptr;
+    const int gates = (int)(q->launches - l0);
+    q->launches = l0;
+    if (rs != HYDRO_OK) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rs;
+    }
+    if (ee != cudaSuccess || !g) {
+        cudaGetLastError();
+        return fail(HYDRO_ECUDA, "capture of the recheck graph failed: %s", cudaGetErrorString(ee));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&q->tail[l][pi], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        q->tail[l][pi] = nullptr;
+        cudaGetLastError();
+        return fail(HYDRO_ECUDA, "instantiating the recheck graph failed: %s", cudaGetErrorString(ie));
+    }
+    q->tail_gates[l][pi] = gates;
+    // the bodies' kernel counts, read by the gates (nothing of this graph runs yet)
+    for (const auto &bc : q->cap_body_counts) CU(cudaMemcpy(bc.first, &bc.second, sizeof(int), cudaMemcpyHostToDevice));
+    q->cap_body_counts.clear();
+    return HYDRO_OK;
 }
 
 hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *in_list, int *out_list,
@@ -902,13 +1098,15 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
                        long long batch, Slot &slot) {
     const hydro_query_config &c = q->cfg;
     const Pred &p = q->preds[pi];
-    const bool bf16 = c.precision == HYDRO_PREC_BF16;
+    // split_main: split BF16 is the working precision, so the cascade is
+    // split BF16 -> FP32 -> FP64 (band 1 goes straight to the FP32 level)
+    const bool split_main = c.precision == HYDRO_PREC_BF16X3;
+    const bool bf16 = tc_query(c);
     const bool cnn = p.kind == HYDRO_UDF_CNN;
-    const bool tf32_level = bf16 && cnn && p.tc_all && q->partials;
-    const int wprec = bf16 ? PREC_BF16 : PREC_F32;
+    const bool tf32_level = c.precision == HYDRO_PREC_BF16 && cnn && p.tc_all && q->partials;
+    const int wprec = split_main ? split_prec(c) : bf16 ? PREC_BF16 : PREC_F32;
     int *band1_count = q->ints + 2, *band2_count = q->ints + 3, *band3_count = q->ints + 4;
-    const ProfCtx pc_main{batch, pi, SRC_MAIN}, pc_rtf{batch, pi, SRC_RTF}, pc_r32{batch, pi, SRC_R32},
-        pc_r64{batch, pi, SRC_R64};
+    const ProfCtx pc_main{batch, pi, SRC_MAIN};
     int *miss_count = nullptr;
     const bool measure = c.cost_source == HYDRO_COST_MEASURED;
     StatRow *row = q->ring + (batch % q->ring_len) * kMaxPred + pi;
@@ -925,61 +1123,31 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
     }
 
     // level 0 -> band 1 (FP32 queries: band 1 is the FP64 band, capacity cap3)
-    launch_classify_f32(in_count, in_list, q->score32, p.threshold, bf16 ? p.margin_lowp : p.margin_fp32, q->pass,
+    const double margin0 = split_main ? p.margin_tf32 : bf16 ? p.margin_lowp : p.margin_fp32;
+    launch_classify_f32(in_count, in_list, q->score32, p.threshold, margin0, q->pass,
                         q->band1_m, q->band1_t, band1_count, bf16 ? q->cap1 : q->cap3, q->d_err, q->st);
     q->launches++;
-    const int *cnt_tf = nullptr, *cnt_32 = nullptr;
-    const int *b64_count = band1_count, *b64_m = q->band1_m, *b64_t = q->band1_t;
-    if (bf16) {
-        // FP32-level input: band 1 directly, or what 3xTF32 leaves undecided
-        const int *b32_count = band1_count, *b32_m = q->band1_m, *b32_t = q->band1_t;
-        if (tf32_level) {
-            TRY(run_udf(q, p, split_prec(c), band1_count, q->band1_t, tuples, q->cap1, q->ract32, q->rscore_t,
-                        nullptr, &pc_rtf));
-            launch_recheck_classify_f32(band1_count, q->band1_m, q->band1_t, q->rscore_t, p.threshold,
-                                        p.margin_tf32, q->pass, q->band2_m, q->band2_t, band2_count, q->cap2,
-                                        q->d_err, q->st);
-            q->launches++;
-            cnt_tf = band1_count;
-            b32_count = band2_count;
-            b32_m = q->band2_m;
-            b32_t = q->band2_t;
-        }
-        if (!cnn && p.upstream) {
-            const int e = prof_begin(q, &pc_r32, PC_BAND32, (double)p.cost, 4.0 * c.dim, 0);
-            launch_mlp_band_f32(b32_count, b32_t, (const float *)tuples, c.dim, p.mlp, q->rscore32, q->sms, q->st);
-            prof_end(q, e);
-            q->launches++;
-        } else if (!cnn) {
-            // the band as a (short) GEMM: weight tiles shared by the band's rows
-            TRY(run_udf(q, p, PREC_F32, b32_count, b32_t, tuples, q->cap1, q->act, q->rscore32, nullptr, &pc_r32));
-        } else {
-            TRY(run_udf(q, p, PREC_F32, b32_count, b32_t, tuples, tf32_level ? q->cap2 : q->cap1, q->ract32,
-                        q->rscore32, nullptr, &pc_r32, true));
-        }
-        launch_recheck_classify_f32(b32_count, b32_m, b32_t, q->rscore32, p.threshold, p.margin_fp32, q->pass,
-                                    q->band3_m, q->band3_t, band3_count, q->cap3, q->d_err, q->st);
+    if (c.recheck_graphs) {
+        // the band's tuples to the lane's staging buffer, then the captured levels
+        launch_band_stage(band1_count, q->band1_t, tuples, tuple_bytes(c), q->band_rows, bf16 ? q->cap1 : q->cap3,
+                          q->sms, q->st);
         q->launches++;
-        cnt_32 = b32_count;
-        b64_count = band3_count;
-        b64_m = q->band3_m;
-        b64_t = q->band3_t;
-    }
-    if (!cnn) {
-        const int e = prof_begin(q, &pc_r64, PC_BAND64, (double)p.cost, 4.0 * c.dim, 0);
-        launch_mlp_band_f64(b64_count, b64_t, (const float *)tuples, c.dim, p.mlp, q->rscore64, q->sms, q->st);
-        prof_end(q, e);
-        q->launches++;
+        TRY(ensure_tail(q, pi));
+        CU(cudaGraphLaunch(q->tail[q->cur_lane][pi], q->st));
+        q->launches += q->tail_gates[q->cur_lane][pi];
     } else {
-        TRY(run_udf(q, p, PREC_F64, b64_count, b64_t, tuples, q->cap3, q->ract64, nullptr, q->rscore64, &pc_r64, true));
+        TRY(enqueue_rechecks(q, pi, tuples, batch));
     }
-    launch_recheck_classify_f64(b64_count, b64_m, b64_t, q->rscore64, p.threshold, q->pass, q->d_err, q->st);
-    q->launches += 2;   // recheck classify + compact
+    // the band counts each level saw, for the statistics row
+    const int *cnt_tf = tf32_level ? band1_count : nullptr;
+    const int *cnt_32 = bf16 ? (tf32_level ? band2_count : band1_count) : nullptr;
+    const int *b64_count = bf16 ? band3_count : band1_count;
     StatRow *rrow = (StatRow *)(slot.dres + kRowsOff) + pi;
     StatRow *warm = nullptr;
     if (adaptive(c.policy) && batch < c.warmup_batches) warm = q->warm + batch * kMaxPred + pi;
     launch_compact(in_count, in_list, q->pass, out_list, out_count, eval_all ? q->acc : nullptr, cnt_tf, cnt_32,
                    b64_count, miss_count, row, rrow, warm, q->st, measure ? 1 : 0);
+    q->launches++;
     return HYDRO_OK;
 }
 
@@ -1207,6 +1375,7 @@ void hydro_default_config(hydro_query_config *cfg) {
     cfg->proxy_epochs = 2;
     cfg->proxy_lr = 1e-3f;
     cfg->proxy_seed = 1;
+    cfg->recheck_graphs = 1;
 }
 
 hydro_status hydro_create_query(const hydro_query_config *cfg, hydro_query **out) {
@@ -1231,8 +1400,12 @@ hydro_status hydro_create_query(const hydro_query_config *cfg, hydro_query **out
             !(c.proxy_lr >= 0.f))
             return fail(HYDRO_EINVAL, "bad proxy settings");
     }
-    if (c.precision != HYDRO_PREC_FP32 && c.precision != HYDRO_PREC_BF16)
-        return fail(HYDRO_EINVAL, "precision must be FP32 or BF16");
+    if (c.precision != HYDRO_PREC_FP32 && c.precision != HYDRO_PREC_BF16 && c.precision != HYDRO_PREC_BF16X3)
+        return fail(HYDRO_EINVAL, "precision must be FP32, BF16 or (frame tuples) BF16X3");
+    if (c.precision == HYDRO_PREC_BF16X3 && c.tuple_kind != HYDRO_TUPLE_U8_FRAME)
+        return fail(HYDRO_EUNSUPPORTED, "split-BF16 working precision is built for frame (CNN) queries");
+    if (c.precision == HYDRO_PREC_BF16X3 && c.split_precision == HYDRO_PREC_TF32X3)
+        return fail(HYDRO_EUNSUPPORTED, "split-BF16 working precision takes split_precision BF16X3 (or 0)");
 
     if (c.split_precision != 0 && c.split_precision != HYDRO_PREC_TF32X3 && c.split_precision != HYDRO_PREC_BF16X3)
         return fail(HYDRO_EINVAL, "split_precision must be TF32X3 or BF16X3");
@@ -1450,15 +1623,15 @@ hydro_status hydro_udf_scores(hydro_query *q, int32_t pred, int32_t prec, const 
         prec != HYDRO_PREC_BF16X3)
         return fail(HYDRO_EINVAL, "unknown precision");
     const bool split = prec == HYDRO_PREC_TF32X3 || prec == HYDRO_PREC_BF16X3;
-    if ((prec == HYDRO_PREC_BF16 || split) && q->cfg.precision != HYDRO_PREC_BF16)
-        return fail(HYDRO_EINVAL, "BF16, 3xTF32 and split-BF16 scores need a BF16 query");
+    if ((prec == HYDRO_PREC_BF16 || split) && !tc_query(q->cfg))
+        return fail(HYDRO_EINVAL, "BF16, 3xTF32 and split-BF16 scores need a BF16 or split-BF16 query");
     CU(cudaSetDevice(q->cfg.device));
     TRY(finalize(q));
     const Pred &p = q->preds[pred];
     if (split && !p.tc_all) return fail(HYDRO_EINVAL, "split-form scores need a tensor-core CNN UDF");
     const int B = q->cfg.max_batch;
     const bool cnn = p.kind == HYDRO_UDF_CNN;
-    const bool recheck_buf = cnn && q->cfg.precision == HYDRO_PREC_BF16 &&
+    const bool recheck_buf = cnn && tc_query(q->cfg) &&
                              (prec == HYDRO_PREC_FP32 || split);
     int *list = q->alive[0], *count = q->ints + 0;
     const int chunk = (prec == HYDRO_PREC_FP64 && cnn) ? q->cap3 : recheck_buf ? std::min(q->cap1, q->cap2) : B;
@@ -1499,7 +1672,7 @@ hydro_status hydro_calibrate(hydro_query *q, const void *d_tuples, int64_t n, hy
     CU(cudaMalloc(&d, sizeof(double) * n * 4));
     std::vector<double> s64(n), s32(n), s16(n), stf(n);
     hydro_status rc = HYDRO_OK;
-    const bool bf = q->cfg.precision == HYDRO_PREC_BF16;
+    const bool bf = tc_query(q->cfg);
     for (int i = 0; i < (int)q->preds.size() && rc == HYDRO_OK; ++i) {
         const bool tf = bf && q->preds[i].tc_all;
         rc = hydro_udf_scores(q, i, HYDRO_PREC_FP64, d_tuples, n, d);
@@ -1784,6 +1957,11 @@ hydro_status hydro_profile(hydro_query *q, int32_t enable) {
     q->prof.rows.clear();
     q->prof.base = q->next_batch;
     q->launches = 0;
+    if (q->d_launch_ctr) {
+        // the recheck graphs' body counter: no batch may be running while it is cleared
+        TRY(quiesce(q));
+        CU(cudaMemset(q->d_launch_ctr, 0, sizeof(unsigned long long)));
+    }
     return HYDRO_OK;
 }
 
@@ -1829,7 +2007,13 @@ hydro_status hydro_profile_read(hydro_query *q, hydro_kernel_profile *out, int32
         ++n;
     }
     *n_out = n < max ? n : max;
-    if (total_launches) *total_launches = q->launches;
+    long long body = 0;
+    if (q->d_launch_ctr) {
+        unsigned long long v = 0;
+        CU(cudaMemcpy(&v, q->d_launch_ctr, sizeof v, cudaMemcpyDeviceToHost));
+        body = (long long)v;
+    }
+    if (total_launches) *total_launches = q->launches + body;
     return HYDRO_OK;
 }
 
@@ -1870,6 +2054,11 @@ hydro_status hydro_destroy_query(hydro_query *q) {
             if (q->own_stream) cudaStreamSynchronize(q->st);
         }
         if (q->n_lanes > 1) q->st = q->home_st;
+        for (int l = 0; l < kMaxLanes; ++l)
+            for (int i = 0; i < kMaxPred; ++i)
+                if (q->tail[l][i]) cudaGraphExecDestroy(q->tail[l][i]);
+        if (q->cap_st) cudaStreamDestroy(q->cap_st);
+        if (q->cap_body_st) cudaStreamDestroy(q->cap_body_st);
         tc_conv_destroy(&q->tc);
         for (cudaEvent_t e : q->prof.ev) cudaEventDestroy(e);
         for (Slot &s : q->slots) {

@@ -49,6 +49,14 @@ void launch_recheck_classify_f64(const int *band_count_in, const int *band_m_in,
 // Measured cost: stamp the stage's start (device global timer) into its row;
 // the stage's compaction (measure = 1) turns it into the stage's duration.
 void launch_stage_start(StatRow *row, cudaStream_t st);
+// Copy the band's tuples into a fixed staging buffer (entry j -> slot j) and
+// turn the band's tuple indices into staging slots.
+void launch_band_stage(const int *band_count, int *band_tuple, const void *tuples, long long tuple_bytes,
+                       void *staging, int max_entries, int sms, cudaStream_t st);
+// Inside a captured graph: set a conditional IF node's handle to (*count > 0);
+// zero the later band counts when it is off; count the body's kernels when on.
+void launch_gate(const int *count, unsigned long long handle, int *zero0, int *zero1, unsigned long long *launch_ctr,
+                 const int *body_kernels, cudaStream_t st);
 void launch_compact(const int *count_in, const int *alive_in, const unsigned char *pass, int *alive_out,
                     int *count_out, unsigned char *acc, const int *bandt_count, const int *band32_count,
                     const int *band64_count, const int *miss_count, StatRow *row, StatRow *rrow, StatRow *warm,

@@ -282,6 +282,52 @@ __global__ void k_router(const StatRow *ring, int ring_len, const StatRow *warm,
     }
 }
 
+// ------------------------------------------------------------ band staging and gates
+// Recheck band staging: the band's tuples (rows or frames of the batch) are
+// copied into a fixed per-lane buffer, entry j to slot j, and the band's
+// tuple index becomes j.  The recheck levels then read only buffers whose
+// addresses never change, so they can replay from a captured graph while
+// every batch brings its own tuple pointer.  One CTA per entry, 16-byte
+// copies when the batch and the tuple size allow it.
+__global__ void __launch_bounds__(256)
+k_band_stage(const int *band_count, int *band_tuple, const unsigned char *tuples, long long tuple_bytes,
+             unsigned char *staging) {
+    const int n = *band_count;
+    const bool v16 = ((reinterpret_cast<uintptr_t>(tuples) | (uintptr_t)tuple_bytes) & 15u) == 0;
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const long long t = band_tuple[j];
+        const unsigned char *src = tuples + t * tuple_bytes;
+        unsigned char *dst = staging + (long long)j * tuple_bytes;
+        if (v16) {
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+            for (long long k = threadIdx.x; k < tuple_bytes / 16; k += blockDim.x) d4[k] = s4[k];
+        } else {
+            for (long long k = threadIdx.x; k < tuple_bytes; k += blockDim.x) dst[k] = src[k];
+        }
+        __syncthreads();   // every thread has read band_tuple[j] before it is rewritten
+        if (threadIdx.x == 0) band_tuple[j] = j;
+    }
+}
+
+// Gate of a conditional recheck level inside a captured graph: the level's
+// body runs iff its band is not empty.  An empty band zeroes the band counts
+// of the later levels (their bodies will not run to write them), and a body
+// that runs adds its kernel count to the launch counter.
+__global__ void k_gate(const int *count, unsigned long long handle, int *zero0, int *zero1,
+                       unsigned long long *launch_ctr, const int *body_kernels) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const bool on = *count > 0;
+    cudaGraphSetConditional((cudaGraphConditionalHandle)handle, on ? 1u : 0u);
+    if (!on) {
+        if (zero0) *zero0 = 0;
+        if (zero1) *zero1 = 0;
+    } else if (launch_ctr && body_kernels) {
+        atomicAdd(launch_ctr, (unsigned long long)*body_kernels);
+    }
+}
+
+
 // ------------------------------------------------------------ launchers
 
 void launch_init_alive(int *alive, int *count, int n, unsigned char *acc, cudaStream_t st) {
@@ -322,6 +368,18 @@ void launch_compact(const int *count_in, const int *alive_in, const unsigned cha
 }
 
 void launch_stage_start(StatRow *row, cudaStream_t st) { k_stage_start<<<1, 1, 0, st>>>(row); }
+
+void launch_band_stage(const int *band_count, int *band_tuple, const void *tuples, long long tuple_bytes,
+                       void *staging, int max_entries, int sms, cudaStream_t st) {
+    const int grid = max_entries < 4 * sms ? (max_entries > 0 ? max_entries : 1) : 4 * sms;
+    k_band_stage<<<grid, 256, 0, st>>>(band_count, band_tuple, static_cast<const unsigned char *>(tuples),
+                                       tuple_bytes, static_cast<unsigned char *>(staging));
+}
+
+void launch_gate(const int *count, unsigned long long handle, int *zero0, int *zero1, unsigned long long *launch_ctr,
+                 const int *body_kernels, cudaStream_t st) {
+    k_gate<<<1, 32, 0, st>>>(count, handle, zero0, zero1, launch_ctr, body_kernels);
+}
 
 void launch_acc_to_alive(const unsigned char *acc, int n, int *alive_out, int *count_out, cudaStream_t st) {
     k_acc_to_alive<<<1, kScanThreads, 0, st>>>(acc, n, alive_out, count_out);

@@ -16,6 +16,31 @@ def stored_thresholds(name):
         return json.load(f)["thresholds"]
 
 
+def stored_pass_matrix(name, q=None):
+    """The oracle's [n, P] pass matrix of a whole benchmarked stream (bool),
+    written by ``tests/golden/make_full_oracle.py``; ``q`` selects one query
+    of the many-query workload."""
+    z = np.load(os.path.join(GOLDEN, f"{name}_oracle.npz"))
+    key, kn, kp = ("pm", "n", "P") if q is None else (f"pm_{q}", f"n_{q}", f"P_{q}")
+    n, P = int(z[kn]), int(z[kp])
+    return np.unpackbits(z[key], bitorder="little")[:n * P].reshape(n, P).astype(bool)
+
+
+def prefix_visits(pm, order):
+    """Per tuple, the bit set of predicates a per-tuple order evaluates: its
+    order up to and including the first failing predicate (all of them if
+    the tuple passes).  ``order`` is [n, >=P] uint8."""
+    n, P = pm.shape
+    want = np.zeros(n, np.uint16)
+    alive = np.ones(n, bool)
+    rows = np.arange(n)
+    for k in range(P):
+        i = order[:, k].astype(np.int64)
+        want[alive] |= (np.uint16(1) << i[alive].astype(np.uint16))
+        alive &= pm[rows, i]
+    return want
+
+
 def oracle_thresholds(w):
     S = O.udf_scores(w.kind, D.calib_tuples(w), D.predicate_weights(w))
     return [O.threshold_for_selectivity(S[:, i], s) for i, s in enumerate(w.selectivity)], S
@@ -30,14 +55,14 @@ def model_costs(w):
 
 def make_query(w, thresholds, *, batch, policy="rank", precision="fp32", warmup=1, window=8, lag=1,
                static_order=None, max_in_flight=4, preds=None, reuse=False, id_capacity=None, cost="model",
-               lanes=1, split="bf16x3"):
+               lanes=1, split="bf16x3", recheck_graphs=True):
     """A query over the workload's predicates.  With ``reuse`` the predicates
     listed in ``extra['emb_preds']`` run as heads on one shared, cached
     embedding (query.emb_id)."""
     import paper_2403_14902_b300 as H
     q = H.Query(w.kind, dim=w.dim, frame=w.frame, max_batch=batch, policy=policy, precision=precision,
                 warmup=warmup, window=window, lag=lag, max_in_flight=max_in_flight, cost=cost, lanes=lanes,
-                split=split)
+                split=split, recheck_graphs=recheck_graphs)
     weights = D.predicate_weights(w)
     idx = list(range(len(weights))) if preds is None else list(preds)
     shared = set(w.extra.get("emb_preds", ())) if (reuse and w.extra) else set()

@@ -1,14 +1,15 @@
 """GPU parity of the CNN path (3x64x64 uint8 frames, four CNN UDFs with 2/4/6/8
-conv3x3 layers) against the oracle: FP32 and BF16-with-recheck, small
-streams element by element and the full 65,536-frame stream in the bench's
-launch configuration on sampled frames."""
+conv3x3 layers) against the oracle: FP32, BF16-with-recheck and split-BF16
+working precision, small streams element by element and the full
+65,536-frame stream in the bench's launch configuration against the stored
+oracle pass matrix of the whole stream."""
 import numpy as np
 import pytest
 
 import datagen as D
 import oracle as O
 from gpu_helpers import (check_against_oracle, make_query, model_costs, run_stream, score_tolerance_ok,
-                         stored_thresholds)
+                         stored_pass_matrix, stored_thresholds)
 
 pytestmark = pytest.mark.gpu
 
@@ -83,6 +84,64 @@ def test_small_stream_parity(cnn4, precision, policy):
     if precision == "bf16":
         assert sum(sum(r[2]["recheck_fp32"]) for r in res) >= 0
     q.close()
+
+
+@pytest.mark.parametrize("policy", ["rank", "static", "all"])
+def test_split_working_precision_parity(cnn4, policy):
+    """Split BF16 as the working precision (FP32-class scores on the tensor
+    cores, the static arm that isolates routing from precision): orders,
+    counts and pass sets exact against the oracle; its calibrated margin
+    sends the few close scores to the FP32 level."""
+    w = cnn4["w"]
+    q = make_query(w, cnn4["th"], batch=B_SMALL, policy=policy, precision="bf16x3")
+    info = q.calibrate(cnn4["calib_d"])
+    for d in info:
+        assert 0 < d["max_err_tf32"] < 5e-3 and d["margin_tf32"] >= 8 * d["max_err_tf32"]
+    res = run_stream(q, cnn4["Fd"], B_SMALL)
+    check_against_oracle(res, cnn4["pm"], B_SMALL, policy=policy, costs=model_costs(w))
+    assert sum(sum(r[2]["recheck_tf32"]) for r in res) == 0, "no split level after a split working level"
+    q.close()
+
+
+def test_split_working_precision_wide_margin(cnn4):
+    """Every split-BF16 score sent on to FP32 (margin wider than the score
+    spread) and every FP32 score on to FP64: the pass set does not move."""
+    w = cnn4["w"]
+    q = make_query(w, cnn4["th"], batch=B_SMALL, policy="rank", precision="bf16x3")
+    for i in range(4):
+        q.set_margins(i, 0.02, 10.0, 10.0)
+    res = run_stream(q, cnn4["Fd"][:40], B_SMALL)
+    check_against_oracle(res, cnn4["pm"][:40], B_SMALL, policy="rank", costs=model_costs(w))
+    evaluated = sum(int(r[1].sum()) for r in res)
+    assert sum(sum(r[2]["recheck_fp32"]) for r in res) == evaluated
+    assert sum(sum(r[2]["recheck_fp64"]) for r in res) == evaluated
+    q.close()
+
+
+@pytest.mark.parametrize("precision,margins", [("bf16", None), ("bf16", (10.0, 10.0, 1e-5)),
+                                               ("fp32", (0.02, 5e-3, 0.05))])
+def test_recheck_graphs_match_direct_launches(cnn4, precision, margins):
+    """The recheck levels replayed from captured graphs (each level an IF node
+    behind a gate kernel, band tuples staged per lane) give the same orders,
+    counts and pass sets as launching every level directly, on two stream
+    lanes; with mostly empty bands they launch fewer kernels.  Wide margins
+    drive every level of the cascade through the graphs."""
+    w = cnn4["w"]
+    launches = {}
+    for graphs in (True, False):
+        q = make_query(w, cnn4["th"], batch=B_SMALL, policy="rank", precision=precision, lanes=2, lag=1,
+                       recheck_graphs=graphs)
+        if margins:
+            for i in range(4):
+                q.set_margins(i, *margins)
+        q.profile(False)
+        res = run_stream(q, cnn4["Fd"], B_SMALL)
+        check_against_oracle(res, cnn4["pm"], B_SMALL, policy="rank", costs=model_costs(w))
+        launches[graphs] = q.profile_read()[1]
+        q.close()
+    assert launches[True] > 0
+    if margins is None:
+        assert launches[True] < launches[False], launches
 
 
 @pytest.mark.parametrize("tf32_margin", [5e-3, 10.0])
@@ -175,36 +234,43 @@ def test_calibrate_bf16(cnn4):
     q.close()
 
 
-def test_full_stream_sampled_parity_bf16():
+def test_full_stream_parity_bf16():
     """The full 65,536-frame stream in the bench's launch configuration:
-    batches of 1,024, rank routing, BF16 with recheck, four stream lanes
-    (route lag 3), 8 batches in flight.  Sampled frames are checked against
-    the oracle one by one; every batch is checked for the short-circuit
-    invariants."""
+    batches of 1,024, rank routing, BF16 with the recheck cascade, four
+    stream lanes (route lag 3), 8 batches in flight.  Every frame's result
+    and every batch's order, evaluation and pass counts equal the oracle's
+    (its stored FP64 pass matrix of the whole stream and its router
+    simulation with lag 3)."""
     import torch
     w = D.workload("cnn4")
     th = stored_thresholds("cnn4")
+    pm = stored_pass_matrix("cnn4")
+    assert pm.shape == (w.n, 4)
     Fd = torch.from_numpy(D.stream_tuples(w)).cuda()
     q = make_query(w, th, batch=w.batch, policy="rank", precision="bf16", lanes=4, lag=3, max_in_flight=8)
     q.calibrate(torch.from_numpy(D.calib_tuples(w)[:64]).cuda())
     res = run_stream(q, Fd, w.batch, max_in_flight=8)
     bits = np.concatenate([r[0] for r in res])
-    assert bits.size == w.n
-    rng = np.random.default_rng(1234)
-    sample = np.unique(np.concatenate([rng.choice(w.n, 20, replace=False), np.flatnonzero(bits)[:4]]))
-    S = O.udf_scores("frame", D.stream_tuples(w)[sample], D.predicate_weights(w))
-    want = O.result_bits(O.pass_matrix(S, th))
-    assert np.array_equal(bits[sample], want)
-    for b, (bb, counts, info) in enumerate(res):
-        order = info["order"]
-        assert sorted(order) == [0, 1, 2, 3]
-        if info["warmup"]:
-            assert counts.tolist() == [w.batch] * 4
-            continue
-        assert counts[order[0]] == bb.size
-        for k in range(3):
-            assert counts[order[k + 1]] == info["passed"][order[k]]
-        assert info["passed"][order[-1]] == int(bb.sum()) == info["n_pass"]
+    assert np.array_equal(bits, O.result_bits(pm)), f"{int((bits != O.result_bits(pm)).sum())} frames differ"
+    check_against_oracle(res, pm, w.batch, policy="rank", costs=model_costs(w), lag=3)
+    q.close()
+
+
+@pytest.mark.parametrize("policy,precision,lanes,lag", [("static", "bf16x3", 4, 3), ("all", "bf16", 4, 3)])
+def test_full_stream_parity_static_arms(policy, precision, lanes, lag):
+    """The bench's static arms over the full stream: split BF16 as the
+    working precision in declared order, and every predicate on every frame
+    in BF16.  Every frame's result and every batch's counts equal the
+    oracle's."""
+    import torch
+    w = D.workload("cnn4")
+    th = stored_thresholds("cnn4")
+    pm = stored_pass_matrix("cnn4")
+    Fd = torch.from_numpy(D.stream_tuples(w)).cuda()
+    q = make_query(w, th, batch=w.batch, policy=policy, precision=precision, lanes=lanes, lag=lag, max_in_flight=8)
+    q.calibrate(torch.from_numpy(D.calib_tuples(w)[:64]).cuda())
+    res = run_stream(q, Fd, w.batch, max_in_flight=8)
+    check_against_oracle(res, pm, w.batch, policy=policy, costs=model_costs(w), lag=lag)
     q.close()
 
 

@@ -9,6 +9,7 @@ import pytest
 
 import datagen as D
 import oracle as O
+from gpu_helpers import stored_pass_matrix
 
 pytestmark = pytest.mark.gpu
 
@@ -322,12 +323,13 @@ def test_session_idle_queries_and_empty_step(small):
     s.close()
 
 
-def test_session_full_workload_sampled():
+def test_session_full_workload_exact():
     """All 64 queries (1.6 M tuples) in the bench's launch configuration:
     chunks of 4,096, 8 chunks of every query per step (route lag 7), BF16
-    with graphs and autotuning.  Sampled tuples of every query against the
-    oracle, and per batch the counting identities of eager dropping along
-    its order."""
+    with graphs and autotuning.  Every tuple of every query, and every
+    batch's order, evaluation and pass counts, equal the oracle's (its
+    stored FP64 pass matrix of each query's whole stream and its router
+    simulation of that query with lag 7)."""
     import torch
     import paper_2403_14902_b300 as H
     w = D.workload("mq64")
@@ -344,33 +346,25 @@ def test_session_full_workload_sampled():
     calib = np.concatenate([D.mq_calib_tuples(w, q, qs)[:64] for q in range(len(qs))])
     s.calibrate(torch.from_numpy(calib).cuda())
     res = run_session_multi(s, streams, chunk, K)
-    bits_q = [[] for _ in qs]
+    got = [[] for _ in qs]
     for counts, bits, per in res:
         off = 0
         for v, c in enumerate(counts):
-            if c == 0:
-                continue
-            r = per[v]
-            bits_q[v // K].append(bits[off:off + c])
-            ev = r["evaluated"]
-            if r["warmup"]:
-                assert ev == [c] * len(ev)
-            else:
-                o = r["order"]
-                assert ev[o[0]] == c
-                for a, b in zip(o[:-1], o[1:]):
-                    assert ev[b] == r["passed"][a]
-                assert r["n_pass"] == r["passed"][o[-1]]
+            if c:
+                got[v // K].append((bits[off:off + c], per[v]))
             off += c
-    pool = D.mq_pool_weights(w)
-    rng = np.random.default_rng(11)
     for q in range(len(qs)):
-        b = np.concatenate(bits_q[q])
-        n = b.shape[0]
-        assert n == streams[q].shape[0]
-        idx = np.unique(np.concatenate([rng.choice(n, min(n, 60), replace=False), np.flatnonzero(b)[:20]]))
-        S = O.udf_scores("vec", streams[q][idx], [pool[u] for u in qs[q]["udfs"]])
-        assert np.array_equal(b[idx], O.result_bits(O.pass_matrix(S, th[q]))), f"query {q}"
+        pm = stored_pass_matrix("mq64", q)
+        assert pm.shape[0] == streams[q].shape[0]
+        sim = O.simulate(pm, chunk, policy="rank", costs=[O.mlp_flops(w.udfs[u]) for u in qs[q]["udfs"]],
+                         lag=K - 1)
+        assert len(got[q]) == len(sim), f"query {q}: batches"
+        for b, ((bits, r), sm) in enumerate(zip(got[q], sim)):
+            assert r["batch"] == b
+            assert np.array_equal(bits, sm["bits"]), f"query {q} batch {b}: pass set"
+            assert r["order"] == sm["order"], f"query {q} batch {b}: order {r['order']} vs {sm['order']}"
+            assert r["evaluated"] == sm["counts"].tolist(), f"query {q} batch {b}: counts"
+            assert r["passed"] == sm["passed"].tolist(), f"query {q} batch {b}: passed"
     s.close()
 
 

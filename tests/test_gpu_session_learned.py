@@ -9,7 +9,7 @@ import pytest
 
 import datagen as D
 import oracle as O
-from gpu_helpers import model_costs, oracle_thresholds, stored_thresholds
+from gpu_helpers import model_costs, oracle_thresholds, prefix_visits, stored_pass_matrix, stored_thresholds
 
 pytestmark = pytest.mark.gpu
 
@@ -159,14 +159,18 @@ def test_learned_session_several_batches_per_step(drift6):
 def test_learned_session_full_stream_bench_configuration():
     """The full 1,048,576-tuple drifting stream in the bench's launch
     configuration: BF16, 16 batches of 4,096 per step (route lag 15), proxy
-    refreshed every 16 batches on 8,192-row windows.  Sampled tuples against
-    the oracle; per batch the counting identities of per-tuple orders (every
-    tuple is evaluated at least once; a passing tuple on every slot)."""
+    refreshed every 16 batches on 8,192-row windows.  Every tuple's result
+    equals the oracle's (its stored FP64 pass matrix of the whole stream);
+    every tuple was evaluated on exactly the prefix of its own order up to
+    its first failing predicate, every batch's evaluation and pass counts
+    follow from those sets, and until the first training every batch takes
+    the oracle's rank order (lag 15)."""
     import torch
 
     import paper_2403_14902_b300 as H
     w = D.workload("drift6")
     th = stored_thresholds("drift6")
+    pm = stored_pass_matrix("drift6")
     X = D.stream_tuples(w)
     Xd = torch.from_numpy(X).cuda()
     K = 16
@@ -178,11 +182,15 @@ def test_learned_session_full_stream_bench_configuration():
     P = len(w.udfs)
     s.add_query(list(range(P)), th)
     s.calibrate(torch.from_numpy(D.calib_tuples(w)).cuda())
+    sim = O.simulate(pm, w.batch, policy="rank", costs=model_costs(w), lag=K - 1)
     bits = []
+    b = 0
     for b0 in range(0, w.n, K * w.batch):
         n = min(K * w.batch, w.n - b0)
         counts = [max(0, min(w.batch, n - k * w.batch)) for k in range(K)]
-        words, per, _ = s.poll(s.submit(Xd[b0:b0 + n], counts), total=n)
+        sid = s.submit(Xd[b0:b0 + n], counts)
+        words, per, _ = s.poll(sid, total=n)
+        order, visited = s.debug_trace(sid, n)
         bb = H.bits_from_words(words, n)
         bits.append(bb)
         off = 0
@@ -190,20 +198,22 @@ def test_learned_session_full_stream_bench_configuration():
             if not c:
                 continue
             r = per[k]
-            npass = int(bb[off:off + c].sum())
-            assert r["n_pass"] == npass
-            if r["warmup"]:
-                assert r["evaluated"] == [c] * P
-            else:
-                # each tuple is evaluated until its first failing slot
-                assert sum(r["evaluated"]) >= c + npass * (P - 1)
-                assert all(e >= npass for e in r["evaluated"]) and max(r["evaluated"]) <= c
-                assert all(p <= e for p, e in zip(r["passed"], r["evaluated"]))
+            pmb = pm[b0 + off:b0 + off + c]
+            vis = visited[off:off + c].astype(np.uint16)
+            assert all(sorted(o[:P].tolist()) == list(range(P)) for o in np.unique(order[off:off + c, :P], axis=0))
+            want = np.full(c, (1 << P) - 1, np.uint16) if r["warmup"] else prefix_visits(pmb, order[off:off + c])
+            assert np.array_equal(vis, want), f"batch {b}: evaluated sets"
+            for i in range(P):
+                ev = ((vis >> i) & 1).astype(bool)
+                assert r["evaluated"][i] == int(ev.sum()), f"batch {b}: evaluated[{i}]"
+                assert r["passed"][i] == int((ev & pmb[:, i]).sum()), f"batch {b}: passed[{i}]"
+            assert r["n_pass"] == int(bb[off:off + c].sum())
+            if b < w.extra["refresh"] + K:
+                # no trained proxy is visible yet: every tuple takes the batch's rank order
+                assert r["order"] == sim[b]["order"], f"batch {b}: order {r['order']} vs {sim[b]['order']}"
+                assert r["evaluated"] == sim[b]["counts"].tolist()
             off += c
+            b += 1
     bits = np.concatenate(bits)
-    assert bits.size == w.n
-    rng = np.random.default_rng(5)
-    idx = np.unique(np.concatenate([rng.choice(w.n, 200, replace=False), np.flatnonzero(bits)[:40]]))
-    S = O.udf_scores("vec", X[idx], D.predicate_weights(w))
-    assert np.array_equal(bits[idx], O.result_bits(O.pass_matrix(S, th)))
+    assert np.array_equal(bits, O.result_bits(pm)), f"{int((bits != O.result_bits(pm)).sum())} tuples differ"
     s.close()
