@@ -107,7 +107,8 @@ def check_step(res, pm, batch):
     """A step's per-batch results against the oracle's pass matrix: every
     bit of the result, and every batch's evaluation counts under the order
     the batch reports.  Returns (bits_exact, counts_exact, bitmap fold)."""
-    bits = np.concatenate([r["bits"] for r in res]) if res else np.zeros(0, bool)
+    import paper_2403_14902_b300 as H
+    bits = np.concatenate([H.bits_from_words(r["words"], r["n"]) for r in res]) if res else np.zeros(0, bool)
     want = pm.all(axis=1)
     bits_ok = bits.shape == want.shape and bool(np.array_equal(bits, want))
     counts_ok = True
@@ -312,12 +313,11 @@ def run_step(q, X, batch, max_in_flight):
     """The whole stream through the query; per batch in submission order:
     its result bits, evaluation counts, order and whether every predicate
     ran on every tuple (warm-up batches, policy all)."""
-    import paper_2403_14902_b300 as H
     pending, out = [], []
 
     def take(b):
         words, counts, info = q.poll(b)
-        out.append({"bits": H.bits_from_words(words, info["n"]), "counts": counts, "order": info["order"],
+        out.append({"words": words, "n": info["n"], "counts": counts, "order": info["order"],
                     "all": info["warmup"] or q.policy == "all", "n_pass": info["n_pass"]})
     for b0 in range(0, X.shape[0], batch):
         pending.append(q.submit(X[b0:b0 + batch]))
@@ -1013,9 +1013,10 @@ def ours_mq64(args):
 
     plans = {1: dev_plan}
 
-    def make(precision, graphs=True, K=1, policy="rank"):
+    def make(precision, graphs=True, K=1, policy="rank", tile_sched=None):
         s = H.Session(dim=w.dim, max_step_tuples=cap * K, precision=precision, graphs=graphs, autotune=True,
-                      max_in_flight=2, stream=stream, batches_per_step=K, lag=K - 1, policy=policy)
+                      max_in_flight=2, stream=stream, batches_per_step=K, lag=K - 1, policy=policy,
+                      tile_sched=tile_sched)
         for layers in pool:
             s.add_udf(layers)
         for q in range(Q):
@@ -1023,19 +1024,23 @@ def ours_mq64(args):
         s.calibrate(calib)
         return s
 
-    def run_all(s, events=None, stats=None):
+    def run_all(s, events=None, stats=None, box=None):
+        """One pass of every query's stream; ``box["steps"]`` receives each
+        step's (counts, result bits) for the parity check."""
         pending, npass = [], 0
         if s.K not in plans:
             plans[s.K] = [(torch.from_numpy(rows).cuda(), counts) for rows, counts in mq_plan(w, streams, s.K)]
+        got = []
 
         def drain(sid):
             nonlocal npass
-            _, per, _ = s.poll(sid[0], total=sid[1])
+            words, per, _ = s.poll(sid[0], total=sid[1])
             npass += sum(r["n_pass"] for r in per)
+            got.append((sid[2], words, sid[1]))   # unpacked after the timed region
             if stats is not None:
                 stats.append(per)
         for X, counts in plans[s.K]:
-            pending.append((s.submit(X, counts), int(sum(counts))))
+            pending.append((s.submit(X, counts), int(sum(counts)), counts))
             if events is not None:
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(stream)
@@ -1044,12 +1049,39 @@ def ours_mq64(args):
                 drain(pending.pop(0))
         for sid in pending:
             drain(sid)
+        if box is not None:
+            box["steps"] = got
         return npass
+
+    pms = None
+    if os.path.exists(os.path.join(ROOT, "tests", "golden", "mq64_oracle.npz")):
+        z = np.load(os.path.join(ROOT, "tests", "golden", "mq64_oracle.npz"))
+        pms = [np.unpackbits(z[f"pm_{q}"], bitorder="little")[:int(z[f"n_{q}"]) * int(z[f"P_{q}"])]
+               .reshape(int(z[f"n_{q}"]), int(z[f"P_{q}"])).astype(bool) for q in range(Q)]
+
+    def parity_of(box, K):
+        """Every query's whole result against the oracle's stored pass matrix."""
+        if pms is None:
+            return "unchecked: no stored oracle pass matrix"
+        per_q = [[] for _ in range(Q)]
+        for counts, words, n in box["steps"]:
+            bits = H.bits_from_words(words, n)
+            off = 0
+            for v, c in enumerate(counts):
+                per_q[v // K].append(bits[off:off + c])
+                off += c
+        ok = all(np.array_equal(np.concatenate(per_q[q]) if per_q[q] else np.zeros(0, bool), pms[q].all(axis=1))
+                 for q in range(Q))
+        return "exact" if ok else "NOT EXACT"
 
     results = {}
     # headline: BF16, graphs, eight batches of every query per step (route lag 7)
     HEAD, HK = "bf16_graphs_k8", 8
-    variants = [(HEAD, "bf16", True, HK), ("bf16_graphs_k4", "bf16", True, 4), ("fp8_graphs_k4", "fp8", True, 4),
+    # the headline with the other tile scheduler of the grouped launches (static round robin
+    # vs data-aware: heaviest tiles first, claimed by the CTA that is ready)
+    ALT = "bf16_graphs_k8_other_tile_sched"
+    variants = [(HEAD, "bf16", True, HK), (ALT, "bf16", True, HK),
+                ("bf16_graphs_k4", "bf16", True, 4), ("fp8_graphs_k4", "fp8", True, 4),
                 ("bf16_graphs_k2", "bf16", True, 2),
                 ("bf16_graphs_k1", "bf16", True, 1), ("fp32_graphs_k1", "fp32", True, 1),
                 ("bf16_no_graphs_k1", "bf16", False, 1), ("static_bf16_graphs_k4", "bf16", True, 4),
@@ -1057,8 +1089,10 @@ def ours_mq64(args):
     if args.headline_only:
         # profilers cannot see kernels inside graphs with conditional nodes: launch kernel by kernel
         variants = [(HEAD, "bf16", not args.no_graphs, HK)]
+    head_sched = None
     for name, precision, graphs, K in variants:
-        s = make(precision, graphs, K, "static" if name.startswith("static") else "rank")
+        s = make(precision, graphs, K, "static" if name.startswith("static") else "rank",
+                 tile_sched=({"static": "data_aware", "data_aware": "static"}[head_sched] if name == ALT else None))
         if K > 1:
             run_all(s)   # builds this K's device plan outside the timed region
         for _ in range(args.warmup):
@@ -1067,11 +1101,33 @@ def ours_mq64(args):
         if name == HEAD:
             clocks.start()
         s.profile(False)   # resets the launch counter
-        secs, npass = timed(lambda: run_all(s), args.steps, stream, local)
+        box = {}
+        secs, npass = timed(lambda: run_all(s, box=box), args.steps, stream, local)
         secs = max_over_ranks(secs, device=torch.device("cuda", local))
         entry = {"value": aggregate(total, args.steps, secs, ws), "ms_per_step": secs / args.steps * 1000.0,
-                 "pass_count": int(npass[0])}
+                 "pass_count": int(npass[0]), "parity": parity_of(box, K)}
         _, entry["launches"] = s.profile_read()
+        if name in (HEAD, ALT):
+            # load balance of the grouped launches over one more pass (device stamps per CTA)
+            entry["tile_sched"] = s.tile_sched
+            if name == HEAD:
+                head_sched = s.tile_sched
+            s.balance(True)
+            run_all(s)
+            b = s.balance(False)
+            n = max(1, b["launches"])
+            busy = np.array(b["cta_busy_ms"])
+            entry["balance"] = {"tile_sched": s.tile_sched, "grouped_launches_per_pass": b["launches"],
+                                "makespan_ms_per_pass": round(b["makespan_ms"], 3),
+                                "mean_cta_busy_over_makespan": round(b["busy_mean_ms"] / max(b["makespan_ms"], 1e-12), 4),
+                                "max_over_mean_cta_busy": round(b["busy_max_ms"] / max(b["busy_mean_ms"], 1e-12), 4),
+                                "per_cta_busy_ms": {"min": round(float(busy.min()), 3),
+                                                    "mean": round(float(busy.mean()), 3),
+                                                    "max": round(float(busy.max()), 3)},
+                                "per_sm_group_busy_ms": [round(float(x), 3) for x in
+                                                         busy[:148].reshape(4, 37).sum(axis=1)] if busy.size >= 148
+                                else None,
+                                "launch_mean_ms": round(b["makespan_ms"] / n, 4)}
         if precision == "fp8":
             # level sizes: FP8/BF16 level 0, BF16 level 1 (FP8 set), FP32, FP64
             stats = []
@@ -1216,8 +1272,10 @@ def ours_mq64(args):
         "gpu_launches": int(a["launches"]),
         "clocks": a["clocks"],
         "latency_ms": a["latency_ms"],
-        "baselines": {k: {"value": round(v["value"], 1), "unit": "tuples/s", "ms_per_step": round(v["ms_per_step"], 3)}
+        "baselines": {k: {"value": round(v["value"], 1), "unit": "tuples/s", "ms_per_step": round(v["ms_per_step"], 3),
+                          "parity": v.get("parity")}
                       for k, v in results.items() if k != HEAD},
+        "parity": a["parity"],
         "speedup_vs_sequential_fp32": round(a["value"] / results["sequential_fp32"]["value"], 3),
         "speedup_vs_session_fp32": round(a["value"] / results["fp32_graphs_k1"]["value"], 3),
         "speedup_vs_static_session_fp32_k4": round(a["value"] / results["static_fp32_graphs_k4"]["value"], 3),
@@ -1229,8 +1287,130 @@ def ours_mq64(args):
                                 (("evaluated", "evaluated"), ("bf16", "recheck_split"), ("fp32", "recheck_fp32"),
                                  ("fp64", "recheck_fp64"))} if "fp8_graphs_k4" in results else None,
         "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3)} for k, v in a["prof"].items()},
+        "load_balance": {"headline": a.get("balance"), "other_tile_sched": results.get(ALT, {}).get("balance"),
+                         "other_tile_sched_value": round(results[ALT]["value"], 1) if ALT in results else None},
         "tuning": [{"udf": t["udf"], "layer": t["layer"], "K": t["K"], "N": t["N"], "tile_n": t["tile_n"],
                     "us": [round(x, 2) for x in t["us"]]} for t in a["tuning"]],
+    }
+
+
+# ---------------------------------------------------------------- concurrent predicates
+
+def ours_uc1(args):
+    """Two synthetic-cost predicates run as concurrent workers (Sec. 4.1
+    "Cost-Driven Routing Policy", "Example comparison"; Sec. 4.2 "Sensitive
+    Analysis using Synthetic Queries"): A = MLP 512-1024-1 and B = MLP
+    512-2048-1 (cost ratio 1:2, FP32 with the FP64 recheck) on 262,144 tuples
+    in batches of 4,096.  In the pipeline mode every position of the order
+    runs on its own stream with half of the SMs, so batches flow through A's
+    and B's workers concurrently, as the paper's CPU and GPU predicates do.
+    For each pair of selectivities the query time of the cost-driven policy
+    (cheapest first), the score-driven one (rank c/(1-s)) and the
+    selectivity-driven one are measured; the worked example (A: cost 1,
+    selectivity 0.6; B: cost 2, selectivity 0.1) heads the line, and the
+    same query on the whole GPU (no pipeline) shows the shared-resource case
+    where the score-driven rank is the right policy."""
+    import torch
+    import paper_2403_14902_b300 as H
+    ws, rank = dist_init("nccl")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    name = "uc1"
+    w = D.workload(name)
+    with open(os.path.join(ROOT, "tests", "golden", f"{name}_thresholds.json")) as f:
+        G = json.load(f)
+    pmz = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.npz")
+    z = np.load(pmz) if os.path.exists(pmz) else None
+
+    def pm_of(sa, sb):
+        if z is None:
+            return None
+        n = int(z["n"])
+        A = np.unpackbits(z["pm_A"], bitorder="little")[:n * int(z["P_A"])].reshape(n, -1).astype(bool)
+        B = np.unpackbits(z["pm_B"], bitorder="little")[:n * int(z["P_B"])].reshape(n, -1).astype(bool)
+        ia = [f"{v:.1f}" for v in z["sel_A"]].index(f"{sa:.1f}")
+        ib = [f"{v:.1f}" for v in z["sel_B"]].index(f"{sb:.1f}")
+        return np.stack([A[:, ia], B[:, ib]], axis=1)
+
+    X = torch.from_numpy(D.stream_tuples(w)).cuda()
+    stream = torch.cuda.Stream()
+    layers = D.predicate_weights(w)
+    mif = 8
+    costs = np.asarray(model_costs_of(w), np.float64)
+    parity = {}
+
+    def run(sa, sb, policy, pipeline, steps):
+        q = H.Query("vec", dim=w.dim, max_batch=w.batch, policy=policy, precision="fp32", max_in_flight=mif,
+                    stream=stream, lanes=4, lag=3, pipeline=pipeline)
+        pipeline = bool(pipeline)
+        q.add_mlp(layers[0], G["A"][f"{sa:.1f}"])
+        q.add_mlp(layers[1], G["B"][f"{sb:.1f}"])
+        f = lambda: run_step(q, X, w.batch, mif)  # noqa: E731
+        f()
+        secs, outs = timed(f, steps, stream, local)
+        secs = max_over_ranks(secs, device=dev)
+        q.close()
+        pm = pm_of(sa, sb)
+        key = f"A{sa:.1f}_B{sb:.1f}_{policy}_{'pipe' if pipeline else 'shared'}"
+        if pm is None:
+            parity[key] = "unchecked: no stored oracle pass matrix"
+        else:
+            parity[key] = "exact" if all(b and c for b, c, _ in (check_step(o, pm, w.batch) for o in outs)) \
+                else "NOT EXACT"
+        ev = np.sum([r["counts"] for r in outs[-1]], axis=0)
+        order = [int(i) for i in outs[-1][-1]["order"]]
+        return {"ms": round(secs / steps * 1000.0, 3), "evaluated": [int(v) for v in ev], "order": order}
+
+    steps = max(2, args.steps)
+    clocks = ClockSampler(local)
+    clocks.start()
+    PIPE = args.pipeline
+    head = {p: run(0.6, 0.1, p, PIPE, steps) for p in ("cost", "rank", "selectivity")}
+    clk = clocks.stop()
+    shared = {p: run(0.6, 0.1, p, False, steps) for p in ("cost", "rank", "selectivity")}
+    grid = {}
+    for sb in w.extra["sel_B"]:
+        for sa in (0.1, 0.3, 0.5, 0.7, 0.9):
+            r = {p: run(sa, sb, p, PIPE, 2)["ms"] for p in ("cost", "rank", "selectivity")}
+            grid[f"A{sa:.1f}_B{sb:.1f}"] = {"ms": r, "cost_over_score": round(r["rank"] / r["cost"], 3),
+                                           "cost_over_selectivity": round(r["selectivity"] / r["cost"], 3)}
+    if rank != 0:
+        return None
+    value = aggregate(w.n, 1, head["cost"]["ms"] / 1000.0, ws)
+    worst = min(v["cost_over_score"] for v in grid.values()), min(v["cost_over_selectivity"] for v in grid.values())
+    return {
+        "metric": METRIC, "value": round(value, 1), "unit": "tuples/s", "n_gpus": ws, "steps": steps,
+        "warmup": 1, "ms_per_step": head["cost"]["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{name}: {w.n} x {w.dim} fp32 tuples, predicates A = MLP 512-1024-1 (cost 1) and "
+                               "B = MLP 512-2048-1 (cost 2), selectivities A 0.6 / B 0.1 (the paper's worked "
+                               "example), batches of 4096, positions pipelined on two streams, each on "
+                               + ("its own hardware partition of half of the SMs" if PIPE == "partitions" else
+                                  "half of the SMs by grid size") + ", cost-driven routing, FP32 + FP64 recheck",
+                   "pipeline": PIPE,
+                   "global_batch": w.n, "routing_batch": w.batch, "parallelism": f"replicas{ws}",
+                   "l2": "inputs 512 MiB > 126 MB L2, no flush"},
+        "parity": ("unchecked: no stored oracle pass matrix" if z is None else
+                   "exact" if all(v == "exact" for v in parity.values()) else "NOT EXACT"),
+        "parity_detail": parity,
+        "clocks": clk,
+        "worked_example": {
+            "pipeline_ms": {p: v["ms"] for p, v in head.items()},
+            "orders": {p: v["order"] for p, v in head.items()},
+            "evaluated": {p: v["evaluated"] for p, v in head.items()},
+            "cost_first_over_expensive_first": round(head["cost"]["ms"] / head["rank"]["ms"], 3),
+            "paper_example": "14 vs 20 time units (cost-driven vs score-/selectivity-driven), ratio 0.7",
+            "shared_gpu_ms": {p: v["ms"] for p, v in shared.items()}},
+        "synthetic_sweep": grid,
+        "sweep_claims": {"cost_never_worse_than_score_min_ratio": worst[0],
+                         "cost_never_worse_than_selectivity_min_ratio": worst[1],
+                         "selectivity_slowest_mean": round(float(np.mean([v["ms"]["selectivity"] for v in grid.values()])), 3),
+                         "score_mean": round(float(np.mean([v["ms"]["rank"] for v in grid.values()])), 3),
+                         "cost_mean": round(float(np.mean([v["ms"]["cost"] for v in grid.values()])), 3)},
+        "roofline": None, "gpu_launches": None,
+        "cpu_baseline": cpu_baseline(w, G["thresholds"], n_frames=2048),
+        "e2e": None,
     }
 
 
@@ -1662,16 +1842,18 @@ def main(argv=None):
                     help="mq64: time the headline variant only (for profiling runs)")
     ap.add_argument("--no-graphs", action="store_true", help="with --headline-only: launch without CUDA graphs")
     ap.add_argument("--lanes", type=int, default=4, help="cnn4: stream lanes of the query (1..8)")
+    ap.add_argument("--pipeline", choices=["partitions", "shares"], default="partitions",
+                    help="uc1: SM partitions (green contexts) or SM shares by grid size for the positions")
     ap.add_argument("--lag", type=int, default=3, help="cnn4: route lag (>= lanes - 1)")
     ap.add_argument("--split", choices=["tf32x3", "bf16x3"], default="bf16x3",
                     help="cnn4: first recheck level of the BF16 CNN UDFs")
-    ap.add_argument("--workload", choices=["cnn4", "mlp3", "drift5", "drift6", "mq64", "gemm_bf16", "conv_bf16", "peaks"],
+    ap.add_argument("--workload", choices=["cnn4", "mlp3", "uc1", "drift5", "drift6", "mq64", "gemm_bf16", "conv_bf16", "peaks"],
                     default=WORKLOAD)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         out = reference(args)
     else:
-        out = {"cnn4": ours, "mlp3": ours_mlp3, "drift5": ours_drift5, "drift6": ours_drift6, "mq64": ours_mq64,
+        out = {"cnn4": ours, "mlp3": ours_mlp3, "uc1": ours_uc1, "drift5": ours_drift5, "drift6": ours_drift6, "mq64": ours_mq64,
                "gemm_bf16": ours_gemm_bf16, "conv_bf16": ours_conv_bf16, "peaks": ours_peaks}[args.workload](args)
     if out is not None:
         print(json.dumps(out), flush=True)

@@ -27,6 +27,10 @@ for them with the shapes of the build's five configurations):
   then 512-256-1, 512-1024-1024-1, 512-2048-1; batches of 4,096.
 * ``drift6`` - the same drifting stream under six MLPs 512-h-1, h = 64 ... 2048
   (costs 1:2:4:8:16:32), for per-tuple routing by a learned proxy.
+* ``uc1`` - 262,144 x 512 fp32 tuples from one isotropic Gaussian and two
+  synthetic-cost MLP predicates, A = 512-1024-1 and B = 512-2048-1 (cost ratio
+  1:2), with thresholds for a grid of selectivities of each, for the
+  concurrent-worker (pipeline) experiments.
 * ``mq64`` - 64 concurrent queries over 512-dim fp32 tuples: query q has a
   lognormal tuple count (median 20,000, clipped to 1,000 ... 200,000), its
   own Dirichlet(0.5) cluster mixture, and a conjunction of 2-6 distinct UDFs
@@ -96,6 +100,15 @@ WORKLOADS = {
         udfs=tuple((512, 64 << k, 1) for k in range(6)),
         selectivity=(0.6, 0.5, 0.4, 0.5, 0.3, 0.5), n_calib=1024,
         extra={"segments": 8, "dirichlet": 0.5, "weight_stream": 40, "proxy_hidden": 64, "refresh": 16}),
+    # two synthetic-cost predicates for the concurrent-worker experiments: A = 512-1024-1 and
+    # B = 512-2048-1 (cost ratio 1:2), tuples from one isotropic Gaussian, thresholds for each
+    # selectivity of the grids below (Sec. 4.1 "Example comparison", "Sensitive Analysis
+    # using Synthetic Queries")
+    "uc1": Workload(
+        name="uc1", wid=6, kind="vec", n=262144, batch=4096, dim=512,
+        udfs=((512, 1024, 1), (512, 2048, 1)), selectivity=(0.6, 0.1), n_calib=4096, n_clusters=1,
+        cluster_spread=0.0,
+        extra={"sel_A": (0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9), "sel_B": (0.1, 0.5, 0.9)}),
     # 64 queries over one pool of eight MLP UDFs; ``n`` caps a query's
     # tuple count, ``batch`` is the per-query chunk of one step
     "mq64": Workload(

@@ -169,6 +169,19 @@ typedef struct hydro_query_config {
                                 band's tuples are first copied to a per-lane staging buffer, so
                                 the graph never sees the batch's own tuple pointer); 0: every
                                 level's kernels are launched for every stage, empty or not */
+    int32_t pipeline;        /* 1: predicates as concurrent workers on separate resources (Sec. 4.1
+                                "Example comparison"): position k of every batch's order runs on a
+                                stream of its own with 1/P of the SMs (every kernel's grid sized to
+                                that share), so that batches flow through the positions like a
+                                pipeline; batch b's position k waits for its position k - 1 only.
+                                Needs lanes >= 2 (each batch in the pipeline keeps its own
+                                scratch) and a query without embeddings or the LEARNED policy.
+                                With the COST policy (cheapest predicate first) this is the
+                                paper's cost-driven routing for concurrent predicates.
+                                2: the same with hardware SM partitions: the SMs are split into
+                                P equal partitions (multiples of 8 SMs; CUDA green contexts) and
+                                position k's stream runs only on partition k (recheck levels are
+                                then launched directly, not from graphs).  0: off */
 } hydro_query_config;
 
 typedef struct hydro_udf_desc {
@@ -458,7 +471,26 @@ typedef struct hydro_session_config {
     int32_t policy;           /* HYDRO_POLICY_RANK (default: per-batch rank order) or
                                  HYDRO_POLICY_STATIC (every batch in the query's declared slot
                                  order, no warmup batches) */
+    int32_t tile_sched;       /* tile scheduling of the grouped tensor-core launches:
+                                 0 = static round robin over the tiles in UDF order;
+                                 1 = data-aware (Sec. 5.3 "Data-Aware Load Balancing" on one GPU):
+                                 tiles numbered by estimated work (K x tile width), heaviest
+                                 first, each CTA claiming its next tile when it is ready for one */
 } hydro_session_config;
+
+/* Load balance of a session's grouped tensor-core launches (Sec. 5.3 and
+ * 5.4: per-worker load), measured on the device: each CTA (one per SM)
+ * stamps the global timer when it starts and when its last tile is done. */
+#define HYDRO_BALANCE_CTAS 160
+typedef struct hydro_balance_info {
+    int64_t launches;         /* grouped launches measured (with at least one tile) */
+    int32_t ctas;             /* most CTAs with work in one launch */
+    int32_t reserved;
+    double makespan_ms;       /* sum over launches: last CTA end - first CTA start */
+    double busy_mean_ms;      /* sum over launches: mean busy time of the CTAs with work */
+    double busy_max_ms;       /* sum over launches: the longest CTA busy time */
+    double cta_busy_ms[HYDRO_BALANCE_CTAS];   /* per CTA index: busy time summed over the launches */
+} hydro_balance_info;
 
 /* Per query result of one step (hydro_session_poll). */
 typedef struct hydro_step_query {
@@ -568,6 +600,13 @@ HYDRO_API hydro_status hydro_session_profile(hydro_session *s, int32_t enable);
  * on the per-query counts the caller reads from the polls); *total_launches
  * (nullable) = kernel launches of all steps polled since then, graph
  * replays included. */
+/* Start (enable = 1, clearing the totals) or stop (enable = 0) collecting the
+ * load balance of the grouped launches of the steps polled from now on (a
+ * device-to-host copy of the step's records at each poll); any other value
+ * only reads.  out (nullable) receives the totals so far.  No step may be in
+ * flight when collection starts or stops. */
+HYDRO_API hydro_status hydro_session_balance(hydro_session *s, int32_t enable, hydro_balance_info *out);
+
 HYDRO_API hydro_status hydro_session_profile_read(hydro_session *s, hydro_kernel_profile *out, int32_t max,
                                                   int32_t *n_out, int64_t *total_launches);
 

@@ -38,7 +38,7 @@ EXPORTED = ["hydro_default_config", "hydro_create_query", "hydro_add_predicate",
             "hydro_session_default_config", "hydro_session_create", "hydro_session_add_udf",
             "hydro_session_add_query", "hydro_session_set_margins", "hydro_session_calibrate",
             "hydro_session_udf_scores", "hydro_session_submit", "hydro_session_poll", "hydro_session_tuning",
-            "hydro_session_profile", "hydro_session_profile_read", "hydro_session_debug_trace",
+            "hydro_session_profile", "hydro_session_profile_read", "hydro_session_debug_trace", "hydro_session_balance",
             "hydro_session_destroy", "hydro_destroy_query", "hydro_last_error"]
 MAX_QUERIES = 512
 MAX_POOL = 8
@@ -52,7 +52,8 @@ class QueryConfig(ctypes.Structure):
                 ("route_lag", ctypes.c_int32), ("max_in_flight", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("proxy_hidden", ctypes.c_int32), ("proxy_refresh", ctypes.c_int32),
                 ("proxy_epochs", ctypes.c_int32), ("proxy_lr", ctypes.c_float), ("proxy_seed", ctypes.c_int32),
-                ("lanes", ctypes.c_int32), ("split_precision", ctypes.c_int32), ("recheck_graphs", ctypes.c_int32)]
+                ("lanes", ctypes.c_int32), ("split_precision", ctypes.c_int32), ("recheck_graphs", ctypes.c_int32),
+                ("pipeline", ctypes.c_int32)]
 
 
 class UdfDesc(ctypes.Structure):
@@ -93,7 +94,17 @@ class SessionConfig(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("learned", ctypes.c_int32), ("proxy_hidden", ctypes.c_int32),
                 ("proxy_refresh", ctypes.c_int32), ("proxy_epochs", ctypes.c_int32), ("proxy_lr", ctypes.c_float),
                 ("proxy_seed", ctypes.c_int32), ("batches_per_step", ctypes.c_int32), ("route_lag", ctypes.c_int32),
-                ("fp8_min_width", ctypes.c_int32), ("proxy_rows", ctypes.c_int32), ("policy", ctypes.c_int32)]
+                ("fp8_min_width", ctypes.c_int32), ("proxy_rows", ctypes.c_int32), ("policy", ctypes.c_int32),
+                ("tile_sched", ctypes.c_int32)]
+
+
+BALANCE_CTAS = 160
+
+
+class BalanceInfo(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ctas", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("makespan_ms", ctypes.c_double), ("busy_mean_ms", ctypes.c_double), ("busy_max_ms", ctypes.c_double),
+                ("cta_busy_ms", ctypes.c_double * BALANCE_CTAS)]
 
 
 class StepQuery(ctypes.Structure):
@@ -159,6 +170,7 @@ def load():
     L.hydro_session_tuning.argtypes = [vp, P(TileChoice), i32, P(i32)]
     L.hydro_session_destroy.argtypes = [vp]
     L.hydro_session_profile.argtypes = [vp, i32]
+    L.hydro_session_balance.argtypes = [vp, i32, P(BalanceInfo)]
     L.hydro_session_debug_trace.argtypes = [vp, i64, P(ctypes.c_uint8), P(ctypes.c_uint8)]
     L.hydro_session_profile_read.argtypes = [vp, P(KernelProfile), i32, P(i32), P(i64)]
     L.hydro_last_error.argtypes = []
@@ -201,7 +213,8 @@ class Query:
                  precision: str = "fp32", warmup: int = 1, window: int = 8, lag: int = 1,
                  max_in_flight: int = 4, device: int = 0, stream=None, proxy_hidden: int = 64,
                  proxy_refresh: int = 16, proxy_epochs: int = 2, proxy_lr: float = 1e-3, proxy_seed: int = 1,
-                 lanes: int = 1, cost: str = "model", split: str = "bf16x3", recheck_graphs: bool = True):
+                 lanes: int = 1, cost: str = "model", split: str = "bf16x3", recheck_graphs: bool = True,
+                 pipeline: bool = False):
         L = load()
         cfg = QueryConfig()
         L.hydro_default_config(ctypes.byref(cfg))
@@ -226,6 +239,7 @@ class Query:
         cfg.cost_source = COSTS[cost]
         cfg.split_precision = PRECISIONS[split]
         cfg.recheck_graphs = 1 if recheck_graphs else 0
+        cfg.pipeline = {False: 0, True: 1, "shares": 1, "partitions": 2}[pipeline]
         self.kind = kind
         self.policy = policy
         self.cfg = cfg
@@ -453,7 +467,7 @@ class Session:
                  device: int = 0, stream=None, learned: bool = False, proxy_hidden: int = 64,
                  proxy_refresh: int = 16, proxy_epochs: int = 1, proxy_lr: float = 1e-3, proxy_seed: int = 1,
                  batches_per_step: int = 1, lag: int = 0, fp8_min_width: int = 0, proxy_rows: int = 0,
-                 policy: str = "rank"):
+                 policy: str = "rank", tile_sched: str | None = None):
         L = load()
         cfg = SessionConfig()
         L.hydro_session_default_config(ctypes.byref(cfg))
@@ -478,6 +492,9 @@ class Session:
         cfg.fp8_min_width = fp8_min_width
         cfg.proxy_rows = proxy_rows
         cfg.policy = POLICIES[policy]
+        if tile_sched is not None:
+            cfg.tile_sched = {"static": 0, "data_aware": 1}[tile_sched]
+        self.tile_sched = {0: "static", 1: "data_aware"}[cfg.tile_sched]
         self.K = batches_per_step
         self._h = ctypes.c_void_p()
         _check(L.hydro_session_create(ctypes.byref(cfg), ctypes.byref(self._h)), "hydro_session_create")
@@ -563,6 +580,19 @@ class Session:
                "hydro_session_profile_read")
         return {out[i].name.decode(): dict(launches=out[i].launches, total_ms=out[i].total_ms)
                 for i in range(n.value)}, tot.value
+
+    def balance(self, enable: bool | None = None):
+        """Load balance of the grouped tensor-core launches of the steps polled
+        since ``balance(True)``: launches, summed makespan / mean / max CTA busy
+        ms and per-CTA busy ms.  ``enable`` True (re)starts, False stops, None
+        only reads."""
+        out = BalanceInfo()
+        en = -1 if enable is None else (1 if enable else 0)
+        _check(load().hydro_session_balance(self._h, en, ctypes.byref(out)), "hydro_session_balance")
+        n = max(1, out.ctas)
+        return dict(launches=out.launches, ctas=out.ctas, makespan_ms=out.makespan_ms,
+                    busy_mean_ms=out.busy_mean_ms, busy_max_ms=out.busy_max_ms,
+                    cta_busy_ms=[out.cta_busy_ms[i] for i in range(n)])
 
     def debug_trace(self, step: int, total: int):
         """(order uint8 [total, 8], visited uint8 [total]) of a polled step."""

@@ -21,6 +21,8 @@
 #include <thread>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/hydro.h"
 #include "common.cuh"
 #include "internal.h"
@@ -255,6 +257,13 @@ struct hydro_query {
     bool capturing = false;
     cudaGraph_t cap_graph = nullptr;
     std::vector<std::pair<int *, int>> cap_body_counts;   // (device slot, kernels) of the bodies just captured
+    // pipeline: order position k runs on pos_st[k] with sms_pos SMs; ev_stage[l][k] closes
+    // position k of the batch on lane l
+    bool pipe = false;
+    int sms_full = 0, sms_pos = 0;
+    cudaStream_t pos_st[kMaxPred] = {};
+    cudaEvent_t ev_stage[kMaxLanes][kMaxPred] = {};
+    CUgreenCtx gctx[kMaxPred] = {};   // pipeline 2: one SM partition per position
 };
 
 namespace {
@@ -419,7 +428,7 @@ hydro_status alloc_scratch(hydro_query *q) {
             for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->ract32[k], 8 * px * std::max(q->cap1, q->cap2)));
         for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->ract64[k], 8 * px * q->cap3));
         if (tc_query(c))
-            TRY(dalloc(q, &q->partials, sizeof(float) * (size_t)B * (c.height * c.width / 128) * 4));
+            TRY(dalloc(q, &q->partials, sizeof(float) * (size_t)B * tc_conv_max_head_parts(c.height, c.width)));
     } else {
         for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->act[k], sizeof(float) * (size_t)wmax * B));
         CU(mlp_band_smem_setup(wmax));
@@ -496,7 +505,66 @@ void load_lane(hydro_query *q, int l) {
 hydro_status quiesce(hydro_query *q) {
     for (int l = 0; l < q->n_lanes; ++l)
         if (q->lane_st[l]) CU(cudaStreamSynchronize(q->lane_st[l]));
+    for (int k = 0; k < kMaxPred; ++k)
+        if (q->pos_st[k]) CU(cudaStreamSynchronize(q->pos_st[k]));
     if (q->n_lanes > 1) load_lane(q, 0);
+    return HYDRO_OK;
+}
+
+// Driver entry points for SM partitions (green contexts), looked up through
+// the runtime so that the library needs no link-time libcuda.
+struct GreenApi {
+    CUresult (*get_resource)(CUdevice, CUdevResource *, CUdevResourceType) = nullptr;
+    CUresult (*split)(CUdevResource *, unsigned int *, const CUdevResource *, CUdevResource *, unsigned int,
+                      unsigned int) = nullptr;
+    CUresult (*gen_desc)(CUdevResourceDesc *, CUdevResource *, unsigned int) = nullptr;
+    CUresult (*create)(CUgreenCtx *, CUdevResourceDesc, CUdevice, unsigned int) = nullptr;
+    CUresult (*stream_create)(CUstream *, CUgreenCtx, unsigned int, int) = nullptr;
+    CUresult (*destroy)(CUgreenCtx) = nullptr;
+    CUresult (*stream_destroy)(CUstream) = nullptr;
+};
+
+bool green_api(GreenApi *g) {
+    auto get = [](const char *name, void **fn) {
+        cudaDriverEntryPointQueryResult qr;
+        return cudaGetDriverEntryPointByVersion(name, fn, CUDA_VERSION, cudaEnableDefault, &qr) == cudaSuccess &&
+               qr == cudaDriverEntryPointSuccess && *fn;
+    };
+    return get("cuDeviceGetDevResource", (void **)&g->get_resource) &&
+           get("cuDevSmResourceSplitByCount", (void **)&g->split) &&
+           get("cuDevResourceGenerateDesc", (void **)&g->gen_desc) && get("cuGreenCtxCreate", (void **)&g->create) &&
+           get("cuGreenCtxStreamCreate", (void **)&g->stream_create) &&
+           get("cuGreenCtxDestroy", (void **)&g->destroy) && get("cuStreamDestroy", (void **)&g->stream_destroy);
+}
+
+// Pipeline 2: split the device's SMs into P equal partitions (multiples of
+// 8 SMs, the split granularity) and give position k a stream of partition k.
+hydro_status make_partitions(hydro_query *q, int P) {
+    GreenApi g;
+    if (!green_api(&g)) return fail(HYDRO_EUNSUPPORTED, "SM partitions (green contexts) are not available");
+    CUdevice dev = q->cfg.device;
+    CUdevResource all{};
+    if (g.get_resource(dev, &all, CU_DEV_RESOURCE_TYPE_SM) != CUDA_SUCCESS)
+        return fail(HYDRO_ECUDA, "cuDeviceGetDevResource failed");
+    const unsigned per = all.sm.smCount / (unsigned)P / 8u * 8u;
+    if (per < 8) return fail(HYDRO_EUNSUPPORTED, "too few SMs for %d partitions", P);
+    CUdevResource parts[kMaxPred], rest{};
+    unsigned ng = (unsigned)P;
+    if (g.split(parts, &ng, &all, &rest, 0, per) != CUDA_SUCCESS || ng < (unsigned)P)
+        return fail(HYDRO_ECUDA, "cuDevSmResourceSplitByCount failed");
+    int smin = 1 << 30;
+    for (int k = 0; k < P; ++k) {
+        CUdevResourceDesc desc;
+        if (g.gen_desc(&desc, &parts[k], 1) != CUDA_SUCCESS ||
+            g.create(&q->gctx[k], desc, dev, CU_GREEN_CTX_DEFAULT_STREAM) != CUDA_SUCCESS)
+            return fail(HYDRO_ECUDA, "green context %d could not be created", k);
+        CUstream st = nullptr;
+        if (g.stream_create(&st, q->gctx[k], CU_STREAM_NON_BLOCKING, 0) != CUDA_SUCCESS)
+            return fail(HYDRO_ECUDA, "stream of green context %d could not be created", k);
+        q->pos_st[k] = (cudaStream_t)st;
+        smin = std::min(smin, (int)parts[k].sm.smCount);
+    }
+    q->sms_pos = smin;
     return HYDRO_OK;
 }
 
@@ -538,6 +606,20 @@ hydro_status finalize(hydro_query *q) {
         CU(cudaEventCreateWithFlags(&q->ev_user, cudaEventDisableTiming));
         q->home_st = q->st;
         load_lane(q, 0);
+    }
+    if (c.pipeline) {
+        if (q->n_lanes < 2) return fail(HYDRO_EUNSUPPORTED, "pipeline needs lanes >= 2");
+        const int P = (int)q->preds.size();
+        q->pipe = true;
+        q->sms_full = q->sms;
+        if (c.pipeline == 2) {
+            TRY(make_partitions(q, P));
+        } else {
+            q->sms_pos = std::max(1, q->sms / P);
+            for (int k = 0; k < P; ++k) CU(cudaStreamCreateWithFlags(&q->pos_st[k], cudaStreamNonBlocking));
+        }
+        for (int l = 0; l < q->n_lanes; ++l)
+            for (int k = 0; k < P; ++k) CU(cudaEventCreateWithFlags(&q->ev_stage[l][k], cudaEventDisableTiming));
     }
     q->ring_len = c.stats_window + c.route_lag + 4;
     TRY(dalloc(q, &q->ring, sizeof(StatRow) * kMaxPred * q->ring_len));
@@ -803,7 +885,9 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
             q->launches++;
             cur = 1 - cur;
         }
-        tc_head_finalize(count, q->partials, H * Wd / 128 * 4, p.head_b, H * Wd, score32, max_rows, q->sms, q->st);
+        tc_head_finalize(count, q->partials,
+                         tc_conv_head_parts(p.dims[p.n_layers - 1], p.dims[p.n_layers], H, Wd, sb ? 2 : 1), p.head_b,
+                         H * Wd, score32, max_rows, q->sms, q->st);
         q->launches++;
         return HYDRO_OK;
     }
@@ -849,7 +933,8 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
         cur = 1 - cur;
     }
     if (fused_head) {
-        tc_head_finalize(count, q->partials, H * Wd / 128 * 4, p.head_b, H * Wd, score32, max_rows, q->sms, st);
+        tc_head_finalize(count, q->partials, tc_conv_head_parts(p.dims[p.n_layers - 1], p.dims[p.n_layers], H, Wd, 0),
+                         p.head_b, H * Wd, score32, max_rows, q->sms, st);
         q->launches++;
         return HYDRO_OK;
     }
@@ -1127,7 +1212,7 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
     launch_classify_f32(in_count, in_list, q->score32, p.threshold, margin0, q->pass,
                         q->band1_m, q->band1_t, band1_count, bf16 ? q->cap1 : q->cap3, q->d_err, q->st);
     q->launches++;
-    if (c.recheck_graphs) {
+    if (c.recheck_graphs && !q->gctx[0]) {
         // the band's tuples to the lane's staging buffer, then the captured levels
         launch_band_stage(band1_count, q->band1_t, tuples, tuple_bytes(c), q->band_rows, bf16 ? q->cap1 : q->cap3,
                           q->sms, q->st);
@@ -1420,6 +1505,9 @@ hydro_status hydro_create_query(const hydro_query_config *cfg, hydro_query **out
     if (c.lanes < 0 || c.lanes > kMaxLanes) return fail(HYDRO_EINVAL, "lanes must be 1..%d", kMaxLanes);
     if (c.lanes > c.route_lag + 1) return fail(HYDRO_EINVAL, "lanes must be <= route_lag + 1");
     if (c.max_in_flight < 1 || c.max_in_flight > 64) return fail(HYDRO_EINVAL, "max_in_flight must be 1..64");
+    if (c.pipeline < 0 || c.pipeline > 2) return fail(HYDRO_EINVAL, "pipeline must be 0, 1 or 2");
+    if (c.pipeline && (c.lanes < 2 || c.policy == HYDRO_POLICY_LEARNED))
+        return fail(HYDRO_EUNSUPPORTED, "pipeline needs lanes >= 2 and a policy other than LEARNED");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess) {
@@ -1793,6 +1881,12 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
         // this batch's lane; it starts after the caller's work so far (its inputs)
         load_lane(q, (int)(b % q->n_lanes));
         CU(cudaEventRecord(q->ev_user, q->home_st));
+        if (q->pipe) {
+            // the first position's stream; the lane's scratch is free once the batch that
+            // used it before (b - lanes) has left the last position
+            q->st = q->pos_st[0];
+            if (b >= q->n_lanes) CU(cudaStreamWaitEvent(q->st, q->ev_done[(b - q->n_lanes) % kEvRing], 0));
+        }
         CU(cudaStreamWaitEvent(q->st, q->ev_user, 0));
     }
     slot->batch = b;
@@ -1816,8 +1910,18 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
         q->launches++;
     }
     for (int k = 0; k < P && !learned; ++k) {
+        if (q->pipe) {
+            // position k: its own stream and SM share, after position k - 1 of this batch
+            q->st = q->pos_st[k];
+            if (k > 0) CU(cudaStreamWaitEvent(q->st, q->ev_stage[q->cur_lane][k - 1], 0));
+            q->sms = q->sms_pos;
+        }
         hydro_status s = run_stage(q, order[k], cnt + cur, q->alive[cur], q->alive[1 - cur], cnt + 1 - cur, eval_all,
                                    d_tuples, (const long long *)d_ids, (int)n, b, *slot);
+        if (q->pipe) {
+            q->sms = q->sms_full;
+            if (s == HYDRO_OK) CU(cudaEventRecord(q->ev_stage[q->cur_lane][k], q->st));
+        }
         if (s != HYDRO_OK) {
             slot->busy = false;
             q->dead = true;
@@ -2055,8 +2159,22 @@ hydro_status hydro_destroy_query(hydro_query *q) {
         }
         if (q->n_lanes > 1) q->st = q->home_st;
         for (int l = 0; l < kMaxLanes; ++l)
-            for (int i = 0; i < kMaxPred; ++i)
+            for (int i = 0; i < kMaxPred; ++i) {
                 if (q->tail[l][i]) cudaGraphExecDestroy(q->tail[l][i]);
+                if (q->ev_stage[l][i]) cudaEventDestroy(q->ev_stage[l][i]);
+            }
+        GreenApi g;
+        const bool green = q->gctx[0] && green_api(&g);
+        for (int k = 0; k < kMaxPred; ++k)
+            if (q->pos_st[k]) {
+                cudaStreamSynchronize(q->pos_st[k]);
+                if (green)
+                    g.stream_destroy((CUstream)q->pos_st[k]);
+                else
+                    cudaStreamDestroy(q->pos_st[k]);
+            }
+        for (int k = 0; k < kMaxPred; ++k)
+            if (q->gctx[k] && green) g.destroy(q->gctx[k]);
         if (q->cap_st) cudaStreamDestroy(q->cap_st);
         if (q->cap_body_st) cudaStreamDestroy(q->cap_body_st);
         tc_conv_destroy(&q->tc);

@@ -13,30 +13,28 @@ namespace hydro {
 
 constexpr int kScanThreads = 1024;
 
-// Exclusive block scan of one int per thread (1024 threads); returns the
-// exclusive prefix and writes the block total to *total.
-__device__ __forceinline__ int block_scan_1024(int v, int *total) {
+// Exclusive block scan of one 0/1 flag per thread (1024 threads): a warp's
+// flags are one __ballot_sync word, a lane's prefix is the popcount of the
+// word's lower lanes, and the 32 warp totals are scanned by warp 0.  Returns
+// the thread's exclusive prefix and writes the block total to *total.
+__device__ __forceinline__ int block_scan_1024(int flag, int *total) {
     __shared__ int warp_sums[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
+    const unsigned word = __ballot_sync(0xffffffffu, flag != 0);
+    const int in_warp = __popc(word & ((1u << lane) - 1u));
+    if (lane == 0) warp_sums[warp] = __popc(word);
     __syncthreads();
     if (warp == 0) {
         int w = warp_sums[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, w, o);
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += y;
         }
-        warp_sums[lane] = w;
+        warp_sums[lane] = w;   // inclusive
     }
     __syncthreads();
-    int excl = x - v + (warp ? warp_sums[warp - 1] : 0);
+    const int excl = in_warp + (warp ? warp_sums[warp - 1] : 0);
     *total = warp_sums[31];
     __syncthreads();
     return excl;

@@ -100,7 +100,15 @@ struct Slot {
     long long *bidx = nullptr, *npass = nullptr;
     int *total = nullptr;
     std::vector<int> counts;
+    // load balance of the grouped launches: per launch of the step, the data-aware
+    // scheduler's counters and every CTA's {first, last} global-timer stamps
+    int *sched = nullptr;
+    unsigned long long *rec = nullptr;
+    int n_rec = 0;
 };
+
+constexpr int kRecLaunches = 128;                // grouped launches per step with counters and records
+constexpr int kRecCtas = HYDRO_BALANCE_CTAS;
 
 }  // namespace
 
@@ -137,6 +145,11 @@ struct hydro_session {
     long long prof_n[SP_N] = {};
     long long launches = 0;         // kernel launches of polled steps since profiling was (re)started
     long long step_launches = 0;    // launches of the step being enqueued (current region)
+    // load balance (hydro_session_balance)
+    Slot *cur_slot = nullptr;       // the slot whose step is being enqueued
+    int rec_idx = 0;                // its grouped launches so far
+    bool bal_on = false;
+    hydro_balance_info bal{};
     // graph capture with conditional regions
     bool capturing = false;
     int if_depth = 0;
@@ -277,9 +290,19 @@ hydro_status eval_tc(hydro_session *s, const int *counts, const int *lists, floa
                 heads.tiles[g] = tc_gemm_head_parts(u.dims[dd + 1], u.nt[dd]);
             }
         }
+        // a step's launches get their own scheduler counters and balance records
+        TcSched ts;
+        const TcSched *tsp = nullptr;
+        if (s->cur_slot && s->rec_idx < kRecLaunches && s->sms <= kRecCtas) {
+            ts.data_aware = s->cfg.tile_sched;
+            ts.counters = s->cur_slot->sched + 2 * s->rec_idx;
+            ts.rec = s->cur_slot->rec + (size_t)s->rec_idx * kRecCtas * 2;
+            tsp = &ts;
+            ++s->rec_idx;
+        }
         pe = prof_begin(s, SP_GEMM);
         hydro_status rs = tc_gemm_grouped_run(s->encode, gr, d.G, act[dd % 2], x * s->wmax, s->partials, s->pstride,
-                                              s->sms, s->st, d.err, split3, min_rows);
+                                              s->sms, s->st, d.err, split3, min_rows, tsp);
         prof_end(s, pe);
         if (rs != HYDRO_OK) return fail(rs, "grouped tensor-core GEMM: %s", tc_gemm_last_error());
         s->step_launches++;
@@ -411,6 +434,10 @@ hydro_status enqueue_step(hydro_session *s, Slot &slot) {
     const bool bf = bf16(s);
     auto gate = [](int r, int k) { return 4 * r + k; };   // k: 0 round, 1 split, 2 FP32 band, 3 FP64 band
     CU(cudaMemcpyAsync(s->d_hdr, slot.h_hdr, sizeof(StepHdr), cudaMemcpyHostToDevice, s->st));
+    // balance records of this step: launches that do not run (empty rounds) leave zeros
+    CU(cudaMemsetAsync(slot.rec, 0, sizeof(unsigned long long) * 2 * kRecCtas * kRecLaunches, s->st));
+    s->cur_slot = &slot;
+    s->rec_idx = 0;
     s->step_launches = 0;
     s->frames.clear();
     for (int k = 0; k < kMqGates; ++k) slot.gate_body[k] = 0;
@@ -516,6 +543,8 @@ hydro_status enqueue_step(hydro_session *s, Slot &slot) {
     s->step_launches += 2;
     slot.launches = s->step_launches;
     slot.conditional = s->capturing;
+    slot.n_rec = s->rec_idx;
+    s->cur_slot = nullptr;
     CU(cudaGetLastError());
     return HYDRO_OK;
 }
@@ -841,6 +870,10 @@ hydro_status finalize(hydro_session *s) {
         TRY(dalloc(s, &sl.npass, sizeof(long long) * Q));
         TRY(dalloc(s, &sl.total, sizeof(int)));
         TRY(dalloc(s, &sl.gates, sizeof(int) * kMqGates));
+        TRY(dalloc(s, &sl.sched, sizeof(int) * 2 * kRecLaunches));
+        CU(cudaMemset(sl.sched, 0, sizeof(int) * 2 * kRecLaunches));
+        TRY(dalloc(s, &sl.rec, sizeof(unsigned long long) * 2 * kRecCtas * kRecLaunches));
+        CU(cudaMemset(sl.rec, 0, sizeof(unsigned long long) * 2 * kRecCtas * kRecLaunches));
     }
     s->finalized = true;
     return HYDRO_OK;
@@ -1040,6 +1073,7 @@ hydro_status hydro_session_create(const hydro_session_config *cfg, hydro_session
     if (cfg->learned && cfg->policy != HYDRO_POLICY_RANK)
         return fail(HYDRO_EINVAL, "learned sessions fall back to rank routing (policy RANK)");
     if (cfg->max_in_flight < 1 || cfg->max_in_flight > 8) return fail(HYDRO_EINVAL, "max_in_flight outside 1..8");
+    if (cfg->tile_sched != 0 && cfg->tile_sched != 1) return fail(HYDRO_EINVAL, "tile_sched must be 0 or 1");
     if (cfg->batches_per_step < 1 || cfg->batches_per_step > 32 || cfg->route_lag < cfg->batches_per_step - 1 ||
         cfg->route_lag > 64)
         return fail(HYDRO_EINVAL, "batches_per_step 1..32 with route_lag >= batches_per_step - 1 (<= 64)");
@@ -1277,6 +1311,7 @@ hydro_status hydro_session_submit(hydro_session *s, const void *d_tuples, const 
             s->if_depth = 0;
             const cudaStream_t main_st = s->st;
             hydro_status rs = enqueue_step(s, *slot);
+            s->cur_slot = nullptr;
             s->capturing = false;
             // a failure inside a region leaves helper captures open: close them
             while (s->if_depth > 0) {
@@ -1305,6 +1340,7 @@ hydro_status hydro_session_submit(hydro_session *s, const void *d_tuples, const 
         s->prof_slot = s->prof_on ? slot : nullptr;
         hydro_status rs = enqueue_step(s, *slot);
         s->prof_slot = nullptr;
+        s->cur_slot = nullptr;
         TRY(rs);
     }
     CU(cudaEventRecord(slot->ev1, s->st));
@@ -1351,6 +1387,34 @@ hydro_status hydro_session_poll(hydro_session *s, int64_t step, uint32_t *pass_b
         cudaEventDestroy(r.b);
     }
     slot->prof.clear();
+    if (s->bal_on && slot->n_rec > 0) {
+        // per grouped launch: CTAs with work have a start stamp; busy = last - first
+        std::vector<unsigned long long> rec((size_t)slot->n_rec * kRecCtas * 2);
+        CU(cudaMemcpy(rec.data(), slot->rec, sizeof(unsigned long long) * rec.size(), cudaMemcpyDeviceToHost));
+        hydro_balance_info &B = s->bal;
+        for (int k = 0; k < slot->n_rec; ++k) {
+            const unsigned long long *r = rec.data() + (size_t)k * kRecCtas * 2;
+            unsigned long long t0 = ~0ull, t1 = 0;
+            double sum = 0, mx = 0;
+            int n = 0;
+            for (int c = 0; c < kRecCtas; ++c) {
+                if (!r[2 * c] || r[2 * c + 1] < r[2 * c]) continue;
+                const double busy = (double)(r[2 * c + 1] - r[2 * c]) * 1e-6;
+                t0 = std::min(t0, r[2 * c]);
+                t1 = std::max(t1, r[2 * c + 1]);
+                sum += busy;
+                mx = std::max(mx, busy);
+                B.cta_busy_ms[c] += busy;
+                ++n;
+            }
+            if (!n) continue;
+            B.launches++;
+            B.ctas = std::max(B.ctas, n);
+            B.makespan_ms += (double)(t1 - t0) * 1e-6;
+            B.busy_mean_ms += sum / n;
+            B.busy_max_ms += mx;
+        }
+    }
     unsigned int err = 0;
     CU(cudaMemcpy(&err, s->d.err, sizeof err, cudaMemcpyDeviceToHost));
     if (err) {
@@ -1441,6 +1505,19 @@ hydro_status hydro_session_profile(hydro_session *s, int32_t enable) {
         s->prof_n[k] = 0;
     }
     s->launches = 0;
+    return HYDRO_OK;
+}
+
+hydro_status hydro_session_balance(hydro_session *s, int32_t enable, hydro_balance_info *out) {
+    set_last_error("");
+    TRY(check(s));
+    if (enable == 0 || enable == 1) {
+        for (Slot &sl : s->slots)
+            if (sl.busy) return fail(HYDRO_ESTATE, "poll every step before switching the balance record");
+        s->bal_on = enable == 1;
+        if (enable == 1) s->bal = hydro_balance_info{};
+    }
+    if (out) *out = s->bal;
     return HYDRO_OK;
 }
 

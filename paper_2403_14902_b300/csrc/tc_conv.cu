@@ -333,6 +333,265 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     if (threadIdx.x == 0 && *abort_flag) atomicOr(err, ERR_TC_TIMEOUT);
 }
 
+// ---------------------------------------------------------------------------
+// Window variant for the 64-output BF16 layers (Cin 32 or 64).  The
+// narrow layers are bound by operand traffic from L2 when every horizontal
+// tap loads its own shifted box.  Here the output pixels are numbered in a
+// padded frame of WP = 66 columns (q = y * 66 + x; x = 64, 65 are padding
+// and never stored), so every tap (ky, kx) reads the input at the uniform
+// shift (ky - 1) * 66 + kx of one window box {32 channels, 66 columns
+// x = -1 .. 64, 9 rows} that TMA zero-fills outside the frame.  One box per
+// 32-channel chunk feeds all nine taps of three 128-pixel subtiles: the
+// MMA's A descriptor starts at the shifted pixel row, which need not be
+// aligned to the 64-byte swizzle atom: the tensor core applies the swizzle
+// to absolute shared-memory address bits, as TMA does when it writes the box,
+// so a start at any pixel row reads that row (base-offset field 0; measured
+// on this GPU for every row shift of 64- and 128-byte swizzled operands).  The weights stay in
+// shared memory for the whole launch.  The padded pixels cost 3 % more MMA
+// work; the operand bytes per output pixel drop 2.3x.
+constexpr int kWP = 66;                        // padded frame width
+constexpr int kWMT = 3;                        // 128-pixel subtiles per CTA tile (384 padded pixels)
+constexpr int kWRows = 9;                      // window rows: up to 7 output rows + 2 halo rows
+constexpr int kWBox = kWRows * kWP * 64;       // one 32-channel window box (bytes)
+constexpr int kWStage = (kWBox + 1023) / 1024 * 1024;
+// Warp roles: 0 TMA, 1 MMA, 2-9 epilogue.  With 64 output channels an MMA
+// takes half as long per output value as with 128, so the epilogue is split
+// over eight warps: warp w drains TMEM lanes 32 (w % 4) .. + 31 and the
+// column half (w - 2) / 4, with its 32 biases (and head weights) in registers.
+constexpr int kWThreads = 320;
+constexpr int kWEpi = 8;
+
+template <int CIN, int S>
+struct TcWCfg {
+    static constexpr int CCB = CIN == 32 ? 32 : 64;        // weight packing chunk (channels)
+    static constexpr int ROWB_B = CCB * 2;
+    static constexpr int B_TAP = 64 * ROWB_B;               // one tap's weights [64 co][CCB]
+    static constexpr int B_BYTES = 3 * B_TAP;               // one (chunk, kx) box
+    static constexpr int RES_BYTES = (CIN / CCB) * 3 * B_BYTES;
+    static constexpr uint32_t SWZ_B = ROWB_B == 128 ? 2u : 4u;
+    static constexpr int NCH = CIN / 32;                    // window boxes (stages) per tile
+    static constexpr int TMEM_COLS = 512;                   // 2 x 3 x 64 used
+    static constexpr int SMEM = RES_BYTES + S * kWStage + 1024 + 256;
+};
+
+// K-major SW64 descriptor of an A operand starting at any pixel row (64 B).
+__device__ __forceinline__ uint64_t wdesc_a(uint32_t saddr) { return smem_desc(saddr, 512, 4u); }
+
+template <int CIN, int S>
+__global__ void __launch_bounds__(kWThreads, 1)
+k_conv3x3_tcw(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const int *count,
+              int H, int tiles_per_frame, const float *__restrict__ bias, __nv_bfloat16 *out,
+              const float *__restrict__ head_w, float *partials, unsigned int *err) {
+    using C = TcWCfg<CIN, S>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *wres = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *smem = wres + C::RES_BYTES;   // window stages
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * kWStage);
+    uint64_t *empty = full + S;
+    uint64_t *tfull = empty + S;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *wbar = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wbar + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int total = (*count) * tiles_per_frame;
+    if ((int)blockIdx.x >= total) return;
+    const int Q = H * kWP;   // padded pixels per frame
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kWEpi);
+        }
+        mbar_init(wbar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer: the weights once, then one window box per 32-channel chunk
+            int s = 0;
+            uint32_t ph = 0, issued = 0, last_par = 0;
+            bool ok = true;
+            mbar_expect_tx(wbar, (uint32_t)C::RES_BYTES);
+            for (int cb = 0; cb < CIN / C::CCB; ++cb)
+                for (int kx = 0; kx < 3; ++kx)
+                    tma_load_3d(wres + (cb * 3 + kx) * C::B_BYTES, &tmB, wbar, 0, 0, (cb * 3 + kx) * 3);
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const int m = t / tiles_per_frame;
+                const int q0 = (t % tiles_per_frame) * 128 * kWMT;
+                const int y_lo = q0 / kWP - 1;
+                for (int c = 0; c < C::NCH; ++c) {
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], (uint32_t)kWBox);
+                    tma_load_4d(smem + s * kWStage, &tmA, &full[s], c * 32, -1, y_lo, m);
+                    issued |= 1u << s;
+                    last_par = (last_par & ~(1u << s)) | (ph << s);
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                volatile int never = 0;
+                for (int k = 0; k < S; ++k)
+                    if (issued & (1u << k)) mbar_wait(&full[k], (last_par >> k) & 1u, &never, 100000000ull);
+                mbar_wait(wbar, 0u, &never, 100000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer: 3 subtiles x 9 taps x 2 K-steps per window box
+            constexpr uint32_t idesc = idesc_bf16(128, 64);
+            int s = 0;
+            uint32_t ph = 0;
+            int tl = 0;
+            bool ok = mbar_wait(wbar, 0u, abort_flag);
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
+                const int buf = tl & 1;
+                const uint32_t tph = (uint32_t)(tl >> 1) & 1u;
+                if (!mbar_wait(&tempty[buf], tph ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const int q0 = (t % tiles_per_frame) * 128 * kWMT;
+                const int pix0 = q0 % kWP + kWP;   // padded pixel q0 in the window (row y_lo + 1)
+                for (int c = 0; c < C::NCH; ++c) {
+                    if (!mbar_wait(&full[s], ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + s * kWStage);
+                    // weights of this 32-channel chunk: packing chunk cb, K offset kb inside its rows
+                    const int cb = (c * 32) / C::CCB, kb = (c * 32) % C::CCB;
+#pragma unroll
+                    for (int sub = 0; sub < kWMT; ++sub) {
+                        const uint32_t dt = tmem_base + (uint32_t)((buf * kWMT + sub) * 64);
+#pragma unroll
+                        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                            for (int kx = 0; kx < 3; ++kx) {
+                                const int pix = pix0 + 128 * sub + (ky - 1) * kWP + kx;
+                                const uint32_t sb = smem_u32(wres) + (uint32_t)((cb * 3 + kx) * C::B_BYTES + ky * C::B_TAP);
+#pragma unroll
+                                for (int kk = 0; kk < 2; ++kk) {
+                                    const uint64_t ad = wdesc_a(sa + (uint32_t)(pix * 64 + kk * 32));
+                                    const uint64_t bd = smem_desc(sb + (uint32_t)(kb * 2 + kk * 32), 8 * C::ROWB_B, C::SWZ_B);
+                                    mma_bf16(dt, ad, bd, idesc, (c | ky | kx | kk) != 0);
+                                }
+                            }
+                    }
+                    mma_commit(&empty[s]);
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (ok) mma_commit(&tfull[buf]);
+            }
+            if (!ok) *abort_flag = 1;
+        }
+    } else {
+        // ---- epilogue: warps 2..9, TMEM lane quarter = warp % 4, column half (warp - 2) / 4;
+        // padded pixels are dropped
+        const int qtr = warp & 3, ch = (warp - 2) >> 2;
+        const int row = qtr * 32 + lane;
+        float bv[32], hv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            bv[j] = __ldg(bias + ch * 32 + j);
+            hv[j] = head_w ? __ldg(head_w + ch * 32 + j) : 0.f;
+        }
+        int tl = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
+            const int buf = tl & 1;
+            const uint32_t tph = (uint32_t)(tl >> 1) & 1u;
+            if (!mbar_wait(&tfull[buf], tph, abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const int m = t / tiles_per_frame;
+            const int q0 = (t % tiles_per_frame) * 128 * kWMT;
+#pragma unroll
+            for (int sub = 0; sub < kWMT; ++sub) {
+                const int q = q0 + 128 * sub + row;
+                const int y = q / kWP, x = q - (q / kWP) * kWP;
+                const bool valid = q < Q && x < 64;
+                uint32_t r[32];
+                tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)((buf * kWMT + sub) * 64 + ch * 32), r);
+                tmem_ld_wait();
+                if (head_w) {
+                    float hsum = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        float v = __uint_as_float(r[j]) + bv[j];
+                        v = v > 0.f ? v : 0.f;
+                        hsum = fmaf(hv[j], v, hsum);
+                    }
+                    hsum = valid ? hsum : 0.f;
+#pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) hsum += __shfl_xor_sync(0xffffffffu, hsum, d);
+                    if (lane == 0) partials[(((size_t)t * kWMT + sub) * 4 + qtr) * 2 + ch] = hsum;
+                } else {
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        float v0 = __uint_as_float(r[2 * j]) + bv[2 * j];
+                        float v1 = __uint_as_float(r[2 * j + 1]) + bv[2 * j + 1];
+                        v0 = v0 > 0.f ? v0 : 0.f;
+                        v1 = v1 > 0.f ? v1 : 0.f;
+                        pk[j] = pack_bf16x2(v0, v1);
+                    }
+                    if (valid) {
+                        uint4 *dst = reinterpret_cast<uint4 *>(out + ((size_t)m * H * 64 + (size_t)y * 64 + x) * 64 +
+                                                               ch * 32);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicOr(err, ERR_TC_TIMEOUT);
+}
+
+constexpr int kSW32 = 4, kSW64 = 3;   // window stages for Cin 32 / 64
+
 // score[m] = hb + (sum of the frame's epilogue partials) / HW, one warp per
 // frame, fixed lane order and butterfly reduction (deterministic).
 __global__ void k_head_finalize(const int *count, const float *partials, int parts_per_frame, double hb, int HW,
@@ -470,6 +729,12 @@ hydro_status tc_conv_init(TcConvPlan *plan, int device) {
     if (r == cudaSuccess) r = set_smem<64, 64, kS_64_64, 2, kMT64>();
     if (r == cudaSuccess) r = set_smem<32, 128, kS_32_128, 2, kMT>();
     if (r == cudaSuccess) r = set_smem<32, 64, kS_32_64, 2, kMT64>();
+    if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(k_conv3x3_tcw<32, kSW32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TcWCfg<32, kSW32>::SMEM);
+    if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(k_conv3x3_tcw<64, kSW64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TcWCfg<64, kSW64>::SMEM);
     if (r != cudaSuccess) {
         g_tc_err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(r);
         return HYDRO_ECUDA;
@@ -486,6 +751,71 @@ void tc_head_finalize(const int *count, const float *partials, int parts_per_fra
     k_head_finalize<<<grid, 256, 0, st>>>(count, partials, parts_per_frame, hb, HW, score);
 }
 
+// The window kernel serves the BF16 64-output layers of 32 or 64 input channels.
+bool use_window(int cin, int cout, int mode) { return mode == 0 && cout == 64 && (cin == 32 || cin == 64); }
+
+int window_tiles_per_frame(int H) { return (H * kWP + 128 * kWMT - 1) / (128 * kWMT); }
+
+hydro_status tc_conv_run_window(TcConvPlan *plan, const int *count, const void *in, int cin, int H,
+                                const void *wpacked, const float *bias, void *out, int max_frames, int sms,
+                                cudaStream_t st, unsigned int *err, const float *head_w, float *partials) {
+    EncodeFn enc = reinterpret_cast<EncodeFn>(plan->encode);
+    CUtensorMap tmA, tmB;
+    {
+        // activations [frame][y][x][cin] bf16; window box {32 channels, 66 columns, 9 rows, 1 frame}
+        const cuuint64_t dims[4] = {(cuuint64_t)cin, 64, (cuuint64_t)H, (cuuint64_t)max_frames};
+        const cuuint64_t strides[3] = {(cuuint64_t)cin * 2, (cuuint64_t)64 * cin * 2, (cuuint64_t)H * 64 * cin * 2};
+        const cuuint32_t box[4] = {32, (cuuint32_t)kWP, (cuuint32_t)kWRows, 1};
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        CUresult r = enc(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(in), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            g_tc_err = "cuTensorMapEncodeTiled(window activations) failed: " + std::to_string((int)r);
+            return HYDRO_ECUDA;
+        }
+    }
+    {
+        const int CC = cin == 32 ? 32 : 64;
+        const cuuint64_t dims[3] = {(cuuint64_t)CC, 64, (cuuint64_t)(cin / CC) * 9};
+        const cuuint64_t strides[2] = {(cuuint64_t)CC * 2, (cuuint64_t)64 * CC * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)CC, 64, 3};
+        const cuuint32_t es[3] = {1, 1, 1};
+        CUresult r = enc(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(wpacked), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            g_tc_err = "cuTensorMapEncodeTiled(window weights) failed: " + std::to_string((int)r);
+            return HYDRO_ECUDA;
+        }
+    }
+    const int tpf = window_tiles_per_frame(H);
+    const long long tiles = (long long)max_frames * tpf;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out);
+    if (cin == 32)
+        k_conv3x3_tcw<32, kSW32><<<grid, kWThreads, TcWCfg<32, kSW32>::SMEM, st>>>(tmA, tmB, count, H, tpf, bias, o, head_w,
+                                                                            partials, err);
+    else
+        k_conv3x3_tcw<64, kSW64><<<grid, kWThreads, TcWCfg<64, kSW64>::SMEM, st>>>(tmA, tmB, count, H, tpf, bias, o, head_w,
+                                                                            partials, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_tc_err = std::string("launch: ") + cudaGetErrorString(e);
+        return HYDRO_ECUDA;
+    }
+    return HYDRO_OK;
+}
+
+int tc_conv_head_parts(int cin, int cout, int H, int W, int mode) {
+    return use_window(cin, cout, mode) ? window_tiles_per_frame(H) * kWMT * 8 : H * W / 128 * 4;
+}
+
+int tc_conv_max_head_parts(int H, int W) {
+    const int a = H * W / 128 * 4, b = window_tiles_per_frame(H) * kWMT * 8;
+    return a > b ? a : b;
+}
+
 hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int cin, int H, int W,
                          const void *wpacked, const float *bias, int cout, void *out, int max_frames, int sms,
                          cudaStream_t st, unsigned int *err, const float *head_w, float *partials, int mode) {
@@ -493,6 +823,9 @@ hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int
         g_tc_err = "tensor-core conv not ready or shape unsupported";
         return HYDRO_EUNSUPPORTED;
     }
+    if (use_window(cin, cout, mode))
+        return tc_conv_run_window(plan, count, in, cin, H, wpacked, bias, out, max_frames, sms, st, err, head_w,
+                                  partials);
     EncodeFn enc = reinterpret_cast<EncodeFn>(plan->encode);
     // operand chunk: 64 bf16 / 32 bf16 (128 B or 64 B rows); 3xTF32 fp32: 32 (128 B rows)
     const bool tf32 = mode == 1;

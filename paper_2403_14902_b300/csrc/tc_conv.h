@@ -40,8 +40,9 @@ void tc_conv_pack_weights_split_bf16(const float *w, int cin, int cout, std::vec
 hydro_status tc_conv_init(TcConvPlan *plan, int device);
 // out[m] = relu(conv3x3(in[m]) + bias) for m < *count (device), NHWC bf16.
 // With head_w != nullptr the layer is the UDF's last: nothing is stored to
-// `out`; instead partials[(m * H*W/128 + tile) * 4 + q] receives the sum over
-// 32 pixels of head_w . relu(conv + bias) (4 partials per 128-pixel tile).
+// `out`; instead the frame's tc_conv_head_parts(...) partials (from
+// partials + m * that count on) receive sums over 32 pixels of
+// head_w . relu(conv + bias) (4 partials per 128-pixel subtile).
 hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int cin, int H, int W,
                          const void *wpacked, const float *bias, int cout, void *out, int max_frames, int sms,
                          cudaStream_t st, unsigned int *err, const float *head_w = nullptr,
@@ -50,6 +51,11 @@ hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int
 // fp32 [frame][pixel][hi(C) | lo(C)] TF32 planes and wpacked comes from
 // tc_conv_pack_weights_split.  mode 2: split BF16, `in` and `out` bf16
 // [frame][pixel][hi(C) | lo(C)] and wpacked from tc_conv_pack_weights_split_bf16.
+// Head partials per frame that a fused-head layer leaves (the window kernel of
+// the BF16 64-output layers has 3 subtiles of 128 padded pixels per tile),
+// and the most any layer of an H x W frame leaves (for sizing the buffer).
+int tc_conv_head_parts(int cin, int cout, int H, int W, int mode);
+int tc_conv_max_head_parts(int H, int W);
 // score[m] = hb + sum(partials of frame m) / HW for m < *count.
 void tc_head_finalize(const int *count, const float *partials, int parts_per_frame, double hb, int HW,
                       float *score, int max_frames, int sms, cudaStream_t st);

@@ -13,6 +13,7 @@
 
 #include <cstring>
 #include <string>
+#include <utility>
 
 #include "common.cuh"
 #include "tc_common.cuh"
@@ -52,28 +53,47 @@ struct TcLaunch {
     int n, ldy, pstride, S, stage_bytes, tmem_cols;
     int split3;               // store Y as [hi | hi | lo] BF16 splits (3N columns) for a split-BF16 next layer
     int min_rows;             // fewer stacked rows than this in all groups: no tiles
+    int order[kMaxGroups];    // tiles are numbered group order[0] first, then order[1], ...
+    int *sched;               // data-aware scheduling: {next tile to claim, CTAs done}, zero between launches
+    unsigned long long *rec;  // nullable: per CTA {first, last} global-timer ns of its work
 };
 
-__device__ __forceinline__ void group_layout(const TcLaunch &L, int *off, int *cnt, int *start) {
-    int o = 0, t = 0;
+// Rows of group g start at off[g] (groups stacked in index order); its tiles
+// are numbered from tstart[k] on, k its position in L.order.
+__device__ __forceinline__ void group_layout(const TcLaunch &L, int *off, int *cnt, int *tstart) {
+    int o = 0;
     for (int g = 0; g < L.n; ++g) {
         const int c = *L.g[g].count;
         off[g] = o;
         cnt[g] = c;
-        start[g] = t;
         o += c;
-        if (L.g[g].NT) t += ((c + 127) / 128) * (L.g[g].N / L.g[g].NT);
     }
-    start[L.n] = t;
+    int t = 0;
+    for (int k = 0; k < L.n; ++k) {
+        const int g = L.order[k];
+        tstart[k] = t;
+        if (L.g[g].NT) t += ((cnt[g] + 127) / 128) * (L.g[g].N / L.g[g].NT);
+    }
+    tstart[L.n] = t;
     if (o < L.min_rows)
-        for (int g = 0; g <= L.n; ++g) start[g] = 0;
+        for (int k = 0; k <= L.n; ++k) tstart[k] = 0;
 }
 
-__device__ __forceinline__ int tile_group(const int *start, int n, int t) {
-    int g = 0;
-    while (g + 1 < n && t >= start[g + 1]) ++g;   // groups without tiles have start[g] == start[g + 1]
-    return g;
+// Tile t: its group and its index within the group.
+__device__ __forceinline__ int tile_group(const TcLaunch &L, const int *tstart, int t, int *local) {
+    int k = 0;
+    while (k + 1 < L.n && t >= tstart[k + 1]) ++k;   // groups without tiles have tstart[k] == tstart[k + 1]
+    *local = t - tstart[k];
+    return L.order[k];
 }
+
+// Data-aware scheduling (the paper's load balancing by estimated work,
+// Sec. 5.3, on one GPU): tiles are numbered heaviest first and every CTA
+// claims its next tile only when its producer is ready for one, so the CTA
+// with the least work in hand takes the next tile.  The producer publishes
+// each claimed tile (or -1 at the end) in a small ring that the MMA warp and
+// the epilogue warps read.
+constexpr int kTileRing = 4;
 
 // Warp roles: 0 TMA, 1 MMA (owns TMEM), 2-9 epilogue.  Epilogue warp w reads
 // TMEM lanes 32 (w % 4) .. + 31 (its rows) and one half of the tile's
@@ -82,7 +102,8 @@ constexpr int kGemmThreads = 320;
 constexpr int kEpiWarps = 8;
 
 // HAS_FP8: some group of the launch has E4M3 operands (its branches compile out otherwise).
-template <bool HAS_FP8>
+// DYN: data-aware scheduling (claimed tiles, L.sched), else static round robin.
+template <bool HAS_FP8, bool DYN>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const __grid_constant__ TcLaunch L) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -91,7 +112,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
     uint64_t *empty = full + kMaxStages;
     uint64_t *tfull = empty + kMaxStages;
     uint64_t *tempty = tfull + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    uint64_t *rfull = tempty + 2;          // tile ring: claimed tile published
+    uint64_t *rempty = rfull + kTileRing;  // tile ring: read by the MMA warp and every epilogue warp
+    int *ring = reinterpret_cast<int *>(rempty + kTileRing);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ring + kTileRing);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -101,6 +125,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
     // a CTA without tiles takes neither barriers nor TMEM (late rounds and
     // recheck levels leave most of the grid idle)
     if ((int)blockIdx.x >= total) return;
+    if (L.rec && threadIdx.x == 0) L.rec[2 * blockIdx.x] = gtimer();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -110,6 +135,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], kEpiWarps);
+        }
+        for (int r = 0; r < kTileRing; ++r) {
+            mbar_init(&rfull[r], 1);
+            mbar_init(&rempty[r], 1 + kEpiWarps);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -131,10 +160,26 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
             int s = 0;
             uint32_t ph = 0, issued = 0, last_par = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const int g = tile_group(start, L.n, t);
+            for (int j = 0, t = blockIdx.x; ok; ++j, t += gridDim.x) {
+                if constexpr (DYN) {
+                    // claim the next tile and publish it (or the end) to the other roles
+                    const int r = j % kTileRing;
+                    if (!mbar_wait(&rempty[r], (uint32_t)((j / kTileRing) & 1) ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    t = atomicAdd(L.sched, 1);
+                    if (t >= total) t = -1;
+                    ring[r] = t;
+                    mbar_arrive(&rfull[r]);
+                    if (t < 0) break;
+                } else if (t >= total) {
+                    break;
+                }
+                int local;
+                const int g = tile_group(L, start, t, &local);
                 const TcGroup &G = L.g[g];
-                const int tiles_n = G.N / G.NT, local = t - start[g];
+                const int tiles_n = G.N / G.NT;
                 const int m0 = off[g] + (local / tiles_n) * 128, n0 = (local % tiles_n) * G.NT;
                 const uint32_t bytes = (uint32_t)(kA_BYTES + G.NT * 128);
                 const int kslice = HAS_FP8 && G.fp8 ? 128 : 64;   // elements per 128-byte K slice
@@ -168,8 +213,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
             uint32_t ph = 0;
             int tl = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
-                const int g = tile_group(start, L.n, t);
+            for (int t = blockIdx.x; ok; t += gridDim.x, ++tl) {
+                if constexpr (DYN) {
+                    const int r = tl % kTileRing;
+                    if (!mbar_wait(&rfull[r], (uint32_t)((tl / kTileRing) & 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    t = ring[r];
+                    mbar_arrive(&rempty[r]);
+                    if (t < 0) break;
+                } else if (t >= total) {
+                    break;
+                }
+                int local;
+                const int g = tile_group(L, start, t, &local);
+                (void)local;
                 const int NT = L.g[g].NT, fp8 = HAS_FP8 && L.g[g].fp8, kblocks = L.g[g].K / (fp8 ? 128 : 64);
                 const uint32_t idesc = fp8 ? idesc_e4m3(128, NT) : idesc_bf16(128, NT);
                 const int buf = tl & 1;
@@ -213,7 +272,23 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
         const int qtr = warp & 3;
         const int chalf = (warp - 2) >> 2;
         int tl = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
+        for (int t = blockIdx.x;; t += gridDim.x, ++tl) {
+            if constexpr (DYN) {
+                const int r = tl % kTileRing;
+                int v = -1;
+                if (lane == 0) {
+                    if (mbar_wait(&rfull[r], (uint32_t)((tl / kTileRing) & 1), abort_flag)) {
+                        v = ring[r];
+                        mbar_arrive(&rempty[r]);
+                    } else {
+                        *abort_flag = 1;
+                    }
+                }
+                t = __shfl_sync(0xffffffffu, v, 0);
+                if (t < 0) break;
+            } else if (t >= total) {
+                break;
+            }
             const int buf = tl & 1;
             const uint32_t tph = (uint32_t)(tl >> 1) & 1u;
             if (!mbar_wait(&tfull[buf], tph, abort_flag)) {
@@ -221,9 +296,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
                 break;
             }
             tc_fence_after();
-            const int g = tile_group(start, L.n, t);
+            int local;
+            const int g = tile_group(L, start, t, &local);
             const TcGroup &G = L.g[g];
-            const int NT = G.NT, tiles_n = G.N / NT, local = t - start[g];
+            const int NT = G.NT, tiles_n = G.N / NT;
             const int tn = local % tiles_n;
             const int m = (local / tiles_n) * 128 + qtr * 32 + lane, n0 = tn * NT;
             const bool live = m < cnt[g];
@@ -292,7 +368,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const 
                      "r"((uint32_t)L.tmem_cols)
                      : "memory");
     }
-    if (threadIdx.x == 0 && *abort_flag) atomicOr(L.err, ERR_TC_TIMEOUT);
+    if (threadIdx.x == 0) {
+        if (*abort_flag) atomicOr(L.err, ERR_TC_TIMEOUT);
+        if (L.rec) L.rec[2 * blockIdx.x + 1] = gtimer();
+        if constexpr (DYN) {
+            // the last CTA with tiles to finish clears the counters for the next launch
+            // (every CTA's producer has stopped claiming before it counts itself done)
+            const int participants = total < (int)gridDim.x ? total : (int)gridDim.x;
+            __threadfence();
+            if (atomicAdd(L.sched + 1, 1) == participants - 1) {
+                L.sched[0] = 0;
+                L.sched[1] = 0;
+                __threadfence();
+            }
+        }
+    }
 }
 
 // Gather the listed fp32 rows into a dense BF16 matrix, 8 values per thread:
@@ -475,10 +565,17 @@ hydro_status tc_gemm_init(void **encode) {
         return HYDRO_ECUDA;
     }
     *encode = fn;
-    cudaError_t r = cudaFuncSetAttribute(k_gemm_grouped_bf16_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kGemmSmem);
+    cudaError_t r = cudaFuncSetAttribute(k_gemm_grouped_bf16_tc<false, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
     if (r == cudaSuccess)
-        r = cudaFuncSetAttribute(k_gemm_grouped_bf16_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+        r = cudaFuncSetAttribute(k_gemm_grouped_bf16_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kGemmSmem);
+    if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(k_gemm_grouped_bf16_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kGemmSmem);
+    if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(k_gemm_grouped_bf16_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kGemmSmem);
     if (r != cudaSuccess) {
         g_gemm_err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(r);
         return HYDRO_ECUDA;
@@ -488,7 +585,7 @@ hydro_status tc_gemm_init(void **encode) {
 
 hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n, __nv_bfloat16 *Y, int ldy,
                                  float *partials, int pstride, int sms, cudaStream_t st, unsigned int *err,
-                                 bool split3, int min_rows) {
+                                 bool split3, int min_rows, const TcSched *sched) {
     if (!encode || n < 1 || n > kMaxGroups || (ldy % 8) != 0) {
         g_gemm_err = "tensor-core GEMM not ready or bad group list";
         return HYDRO_EUNSUPPORTED;
@@ -548,14 +645,31 @@ hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n,
     L.tmem_cols = 2 * nt_max;
     L.split3 = split3 ? 1 : 0;
     L.min_rows = min_rows;
+    for (int g = 0; g < n; ++g) L.order[g] = g;
+    const bool dyn = sched && sched->data_aware && sched->counters;
+    if (dyn) {
+        // heaviest tiles first: a tile's work is 128 rows x NT columns x K (half for E4M3 operands)
+        auto work = [&](int g) -> long long {
+            const TcGroup &G = L.g[g];
+            return G.NT ? (long long)G.K * G.NT / (G.fp8 ? 2 : 1) : 0;
+        };
+        for (int a = 1; a < n; ++a)
+            for (int b = a; b > 0 && work(L.order[b]) > work(L.order[b - 1]); --b) std::swap(L.order[b], L.order[b - 1]);
+        L.sched = sched->counters;
+    }
+    L.rec = sched ? sched->rec : nullptr;
     if (tiles == 0) return HYDRO_OK;   // only rows-only groups
     const int grid = (int)(tiles < sms ? tiles : sms);
     bool any_fp8 = false;
     for (int g = 0; g < n; ++g) any_fp8 = any_fp8 || L.g[g].fp8;
-    if (any_fp8)
-        k_gemm_grouped_bf16_tc<true><<<grid, kGemmThreads, kGemmSmem, st>>>(L);
+    if (any_fp8 && dyn)
+        k_gemm_grouped_bf16_tc<true, true><<<grid, kGemmThreads, kGemmSmem, st>>>(L);
+    else if (any_fp8)
+        k_gemm_grouped_bf16_tc<true, false><<<grid, kGemmThreads, kGemmSmem, st>>>(L);
+    else if (dyn)
+        k_gemm_grouped_bf16_tc<false, true><<<grid, kGemmThreads, kGemmSmem, st>>>(L);
     else
-        k_gemm_grouped_bf16_tc<false><<<grid, kGemmThreads, kGemmSmem, st>>>(L);
+        k_gemm_grouped_bf16_tc<false, false><<<grid, kGemmThreads, kGemmSmem, st>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         g_gemm_err = std::string("launch: ") + cudaGetErrorString(e);

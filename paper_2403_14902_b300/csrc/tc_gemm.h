@@ -56,6 +56,17 @@ hydro_status tc_gemm_run(void *encode, const int *count, const __nv_bfloat16 *X,
 // tile: the epilogue's column halves); nt as in TcGemmGroup.
 int tc_gemm_col_tiles(int N);
 int tc_gemm_head_parts(int N, int nt);
+// Tile scheduling of a grouped launch.  data_aware: tiles numbered heaviest
+// first (K x column-tile width) and claimed one at a time by the CTA that is
+// ready for one, through counters (two ints, zero before the first launch;
+// the launch leaves them zero); else static round robin in group order.
+// rec (nullable): per CTA the global-timer ns of its first and last work,
+// [grid][2] (CTAs without tiles leave theirs untouched).
+struct TcSched {
+    int data_aware = 0;
+    int *counters = nullptr;
+    unsigned long long *rec = nullptr;
+};
 // All groups' layers of one depth in one persistent launch.  Y (stacked,
 // row stride ldy) receives the groups without a head; partials (stacked, row
 // stride pstride) the head partials of the others.
@@ -64,7 +75,7 @@ int tc_gemm_head_parts(int N, int nt);
 // (read on the device) the launch does nothing.
 hydro_status tc_gemm_grouped_run(void *encode, const TcGemmGroup *groups, int n, __nv_bfloat16 *Y, int ldy,
                                  float *partials, int pstride, int sms, cudaStream_t st, unsigned int *err,
-                                 bool split3 = false, int min_rows = 0);
+                                 bool split3 = false, int min_rows = 0, const TcSched *sched = nullptr);
 // out[off_g + m] = bf16(X[queues[g * qstride + m]]) for m < counts[g], X = *Xp
 // (read on the device, so a captured launch follows the pointer's updates).
 void launch_gather_grouped_bf16(int n, const int *counts, const int *queues, int qstride, const float *const *Xp,

@@ -15,7 +15,10 @@ Output ``<name>_oracle.npz``:
     frame workload adds ``scores_f32`` = the FP64 scores rounded to fp32
     (its oracle takes hours; the pass bits come from the FP64 scores);
   * the many-query workload: per query ``pm_<q>`` packed the same way with
-    ``n_<q>`` and ``P_<q>``.
+    ``n_<q>`` and ``P_<q>``;
+  * the synthetic two-predicate workload: ``pm`` at its own selectivities
+    plus ``pm_A`` / ``pm_B``, every threshold of each predicate's
+    selectivity grid.
 
 The frame workload is computed in chunks whose scores are kept under
 ``tests/golden/.partial/`` (not committed) so that an interrupted run
@@ -84,6 +87,30 @@ def single_stream(name, threads):
           "conjunction", float(O.result_bits(pm).mean()), f"{secs:.0f} s", flush=True)
 
 
+def grid_stream(name, threads):
+    """Synthetic two-predicate workload: the FP64 scores of A and B on the
+    whole stream against every threshold of their selectivity grids;
+    ``pm_A`` [n, |grid A|] and ``pm_B`` [n, |grid B|] packed like ``pm``
+    (``pm`` itself at the workload's own pair of selectivities)."""
+    w = D.workload(name)
+    with open(os.path.join(HERE, f"{name}_thresholds.json")) as f:
+        G = json.load(f)
+    t0 = time.time()
+    S = O.udf_scores(w.kind, D.stream_tuples(w), D.predicate_weights(w), threads)
+    out = {}
+    for i, key in enumerate(("A", "B")):
+        th = [G[key][f"{s:.1f}"] for s in w.extra[f"sel_{key}"]]
+        pm = S[:, i:i + 1] > np.asarray(th, np.float64)[None, :]
+        out[f"pm_{key}"] = _pack(pm)
+        out[f"P_{key}"] = len(th)
+        out[f"sel_{key}"] = np.asarray(w.extra[f"sel_{key}"], np.float64)
+    pm = O.pass_matrix(S, G["thresholds"])
+    np.savez_compressed(os.path.join(HERE, f"{name}_oracle.npz"), pm=_pack(pm), n=w.n, P=2,
+                        thresholds=np.asarray(G["thresholds"], np.float64), oracle_seconds=time.time() - t0,
+                        oracle_threads=threads or O.threads(), **out)
+    print(name, "pass fraction", pm.mean(axis=0).round(4).tolist(), f"{time.time() - t0:.0f} s", flush=True)
+
+
 def many_queries(name, threads):
     w = D.workload(name)
     th = _thresholds(name)
@@ -104,12 +131,14 @@ def many_queries(name, threads):
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
-    ap.add_argument("names", nargs="*", default=["mlp3", "drift6", "drift5", "mq64", "cnn4"])
+    ap.add_argument("names", nargs="*", default=["mlp3", "uc1", "drift6", "drift5", "mq64", "cnn4"])
     ap.add_argument("--threads", type=int, default=0)
     a = ap.parse_args()
     for nm in a.names:
         w = D.workload(nm)
         if w.extra and "queries" in w.extra:
             many_queries(nm, a.threads)
+        elif w.extra and "sel_A" in w.extra:
+            grid_stream(nm, a.threads)
         else:
             single_stream(nm, a.threads)

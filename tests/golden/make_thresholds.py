@@ -33,10 +33,29 @@ def mq_thresholds(name: str) -> dict:
             "oracle_threads": O.threads()}
 
 
+def grid_thresholds(name: str) -> dict:
+    """Per predicate (A, B), the threshold of every selectivity of its grid
+    on the calibration draw; ``thresholds`` holds the pair at the workload's
+    own selectivities."""
+    w = D.workload(name)
+    t0 = time.time()
+    S = O.udf_scores(w.kind, D.calib_tuples(w), D.predicate_weights(w))
+    out = {"workload": name, "n_calib": w.n_calib}
+    for i, key in enumerate(("A", "B")):
+        out[key] = {f"{s:.1f}": O.threshold_for_selectivity(S[:, i], s) for s in w.extra[f"sel_{key}"]}
+    out["selectivity"] = list(w.selectivity)
+    out["thresholds"] = [O.threshold_for_selectivity(S[:, i], s) for i, s in enumerate(w.selectivity)]
+    out["oracle_seconds"] = round(time.time() - t0, 1)
+    out["oracle_threads"] = O.threads()
+    return out
+
+
 def thresholds(name: str) -> dict:
     w = D.workload(name)
     if w.extra and "queries" in w.extra:
         return mq_thresholds(name)
+    if w.extra and "sel_A" in w.extra:
+        return grid_thresholds(name)
     t0 = time.time()
     S = O.udf_scores(w.kind, D.calib_tuples(w), D.predicate_weights(w))
     th = [O.threshold_for_selectivity(S[:, i], s) for i, s in enumerate(w.selectivity)]

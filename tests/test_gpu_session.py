@@ -22,10 +22,10 @@ def mq_thresholds():
 
 
 def make_session(w, qs, th, *, precision="fp32", cap, graphs=True, autotune=True, warmup=1, window=8,
-                 queries=None, policy="rank"):
+                 queries=None, policy="rank", tile_sched=None):
     import paper_2403_14902_b300 as H
     s = H.Session(dim=w.dim, max_step_tuples=cap, precision=precision, graphs=graphs, autotune=autotune,
-                  warmup=warmup, window=window, policy=policy)
+                  warmup=warmup, window=window, policy=policy, tile_sched=tile_sched)
     for layers in D.mq_pool_weights(w):
         s.add_udf(layers)
     for q in (range(len(qs)) if queries is None else queries):
@@ -112,6 +112,29 @@ def test_session_fp32_exact(small, graphs):
     s.calibrate(torch.from_numpy(small["calib"]).cuda())
     res = run_session(s, small["streams"], small["chunk"])
     check_steps(res, small["sims"], len(small["queries"]))
+    s.close()
+
+
+@pytest.mark.parametrize("tile_sched", ["static", "data_aware"])
+@pytest.mark.parametrize("precision,graphs", [("bf16", True), ("bf16", False), ("fp8", True)])
+def test_session_tile_schedulers_exact_and_balance(small, tile_sched, precision, graphs):
+    """Both tile schedulers of the grouped tensor-core launches (static round
+    robin; data-aware: heaviest tiles first, claimed by the CTA that is ready)
+    give the oracle's orders, counts and pass sets, with and without graphs;
+    the load-balance record covers the grouped launches: every CTA's busy
+    time lies inside its launch's makespan."""
+    import torch
+    s = make_session(small["w"], small["qs"], small["th"], precision=precision,
+                     cap=len(small["queries"]) * small["chunk"], graphs=graphs, queries=small["queries"],
+                     tile_sched=tile_sched)
+    s.calibrate(torch.from_numpy(small["calib"]).cuda())
+    s.balance(True)
+    res = run_session(s, small["streams"], small["chunk"])
+    check_steps(res, small["sims"], len(small["queries"]))
+    b = s.balance(False)
+    assert b["launches"] > 0 and 0 < b["ctas"] <= 148
+    assert 0 < b["busy_mean_ms"] <= b["busy_max_ms"] * (1 + 1e-9) <= b["makespan_ms"] * (1 + 1e-6)
+    assert abs(sum(b["cta_busy_ms"]) - 0) > 0
     s.close()
 
 
