@@ -425,9 +425,9 @@ def ours_drift5(args):
     shared = set(w.extra["emb_preds"])
     calib = torch.from_numpy(D.calib_tuples(w)).cuda()
 
-    def make(policy, order=None, cost="model"):
+    def make(policy, order=None, cost="model", lag=1):
         q = H.Query("vec", dim=w.dim, max_batch=w.batch, policy=policy, max_in_flight=mif, stream=stream,
-                    cost=cost)
+                    cost=cost, lag=lag)
         e = q.add_embedding(D.embedding_weights(w), w.n)
         full = D.predicate_weights(w)
         for i in range(len(w.udfs)):
@@ -440,18 +440,42 @@ def ours_drift5(args):
         q.calibrate(calib)
         return q, e
 
-    def step_fn(q, e):
+    def step_fn(q, e, box=None):
         def f():
             q.cache_clear(e)        # every pass starts from an empty cache
-            pending, n_pass = [], 0
+            pending, got = [], []
+
+            def take(b):
+                words, counts, info = q.poll(b)
+                got.append({"words": words, "n": info["n"], "counts": counts, "order": info["order"],
+                            "all": info["warmup"] or q.policy == "all", "n_pass": info["n_pass"]})
             for b0 in range(0, w.n, w.batch):
                 pending.append(q.submit(X[b0:b0 + w.batch], ids[b0:b0 + w.batch]))
                 if len(pending) >= mif:
-                    n_pass += q.poll(pending.pop(0))[2]["n_pass"]
+                    take(pending.pop(0))
             for b in pending:
-                n_pass += q.poll(b)[2]["n_pass"]
-            return n_pass
+                take(b)
+            if box is not None:
+                box["res"] = got
+            return n_pass_of(got)
         return f
+
+    def timed_steps(f, steps):
+        """Per-step CUDA events (the spread between steps) and the total."""
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        barrier()
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        outs = []
+        for k in range(steps):
+            outs.append(f())
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+        return sum(per) / 1000.0, outs, per
+
+    pm = stored_pass_matrix("drift5")
 
     # profile pass: every predicate on every tuple gives the global selectivities
     qa, ea = make("all")
@@ -464,30 +488,55 @@ def ours_drift5(args):
     emb = w.extra["embedding"]
     c_emb = sum(2 * emb[l] * emb[l + 1] for l in range(len(emb) - 1))
     best = best_static_order(costs, groups, c_emb, sel)
+    best_pm = None
+    if pm is not None:
+        from itertools import permutations
+        for perm in permutations(range(len(costs))):
+            cnt = order_counts(pm, perm)
+            first_head = next(i for i in perm if groups[i] is not None)
+            c = float(np.dot(cnt, costs)) + float(cnt[first_head]) * c_emb
+            if best_pm is None or c < best_pm[1]:
+                best_pm = (list(perm), c)
+    parity = {}
 
     results = {}
     # headline: rank routing on the flop-model costs (deterministic, oracle-exact orders);
     # routing on measured stage times per tuple (the paper's cost source) as a variant
-    for name, policy, order, steps in [("adaptive", "rank", None, args.steps),
-                                       ("adaptive_measured_cost", "rank", None, args.steps),
-                                       ("best_static", "static", best, args.steps),
-                                       ("declared_static", "static", None, 1)]:
-        q, e = make(policy, order, "measured" if name == "adaptive_measured_cost" else "model")
-        f = step_fn(q, e)
+    arms = [("adaptive", "rank", None, args.steps, args.lag),
+            ("adaptive_lag1", "rank", None, args.steps, 1),
+            ("adaptive_measured_cost", "rank", None, args.steps, args.lag),
+            ("best_static", "static", best, args.steps, 1),
+            ("declared_static", "static", None, 1, 1)]
+    if best_pm is not None and best_pm[0] != best:
+        arms.insert(4, ("best_static_from_pass_matrix", "static", best_pm[0], args.steps, 1))
+    for name, policy, order, steps, lag in arms:
+        q, e = make(policy, order, "measured" if name == "adaptive_measured_cost" else "model", lag=lag)
+        box = {}
+        f = step_fn(q, e, box)
         for _ in range(args.warmup if name != "declared_static" else 1):
             f()
         clocks = ClockSampler(local)
         if name == "adaptive":
             clocks.start()
-            q.profile(True)
-        secs, npass = timed(f, steps, stream, local)
+            q.profile(False)   # clears the launch counter; no per-launch events in the timed region
+        secs, npass, per = timed_steps(f, steps)
         secs = max_over_ranks(secs, device=torch.device("cuda", local))
         entry = {"value": aggregate(w.n, steps, secs, ws), "ms_per_step": secs / steps * 1000.0,
-                 "pass_count": int(npass[0]), "steps": steps}
+                 "pass_count": int(npass[0]), "steps": steps, "route_lag": lag,
+                 "step_ms": [round(x, 3) for x in per],
+                 "spread": round((max(per) - min(per)) / float(np.median(per)), 4) if per else None}
+        if pm is not None:
+            ok = all(b and c for b, c, _ in [check_step(box["res"], pm, w.batch)])
+            parity[name] = "exact" if ok else "NOT EXACT"
         if name == "adaptive":
-            entry["prof"], entry["launches"] = q.profile_read()
+            _, entry["launches"] = q.profile_read()
             entry["clocks"] = clocks.stop()
             entry["stats"] = q.stats()
+            # kernel classes over one more pass with per-launch events
+            q.profile(True)
+            f()
+            entry["prof"], _ = q.profile_read()
+            q.profile(False)
             # end to end from pinned host memory
             Xp = Xh.pin_memory()
             bufs = [torch.empty((w.batch, w.dim), dtype=torch.float32, device="cuda") for _ in range(mif)]
@@ -544,6 +593,12 @@ def ours_drift5(args):
         "baselines": {k: {"value": round(v["value"], 1), "unit": "tuples/s", "ms_per_step": round(v["ms_per_step"], 3)}
                       for k, v in results.items() if k != "adaptive"},
         "best_static_order": best, "profiled_selectivity": [round(x, 4) for x in sel],
+        "best_static_order_from_pass_matrix": best_pm,
+        "parity": ("unchecked: no stored oracle pass matrix" if pm is None else
+                   "exact" if all(v == "exact" for v in parity.values()) else "NOT EXACT"),
+        "parity_detail": parity,
+        "step_spread": {k: {"route_lag": v["route_lag"], "spread": v["spread"], "step_ms": v["step_ms"]}
+                        for k, v in results.items()},
         "speedup_vs_best_static": round(a["value"] / results["best_static"]["value"], 3),
         "speedup_vs_declared_static": round(a["value"] / results["declared_static"]["value"], 3),
         "pass_count_per_step": a["pass_count"],
@@ -779,7 +834,7 @@ def ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     import paper_2403_14902_b300 as H
-    w = D.workload(WORKLOAD)
+    w = D.workload(WORKLOAD, batch=args.batch) if args.batch else D.workload(WORKLOAD)
     th = thresholds(WORKLOAD)
     pm = stored_pass_matrix(WORKLOAD)
     costs = np.asarray(model_costs_of(w), np.float64)
@@ -1372,13 +1427,18 @@ def ours_uc1(args):
     grid = {}
     for sb in w.extra["sel_B"]:
         for sa in (0.1, 0.3, 0.5, 0.7, 0.9):
-            r = {p: run(sa, sb, p, PIPE, 2)["ms"] for p in ("cost", "rank", "selectivity")}
-            grid[f"A{sa:.1f}_B{sb:.1f}"] = {"ms": r, "cost_over_score": round(r["rank"] / r["cost"], 3),
+            rr = {p: run(sa, sb, p, PIPE, 3) for p in ("cost", "rank", "selectivity")}
+            r = {p: v["ms"] for p, v in rr.items()}
+            grid[f"A{sa:.1f}_B{sb:.1f}"] = {"ms": r, "orders": {p: v["order"] for p, v in rr.items()},
+                                           "cost_over_score": round(r["rank"] / r["cost"], 3),
                                            "cost_over_selectivity": round(r["selectivity"] / r["cost"], 3)}
     if rank != 0:
         return None
     value = aggregate(w.n, 1, head["cost"]["ms"] / 1000.0, ws)
-    worst = min(v["cost_over_score"] for v in grid.values()), min(v["cost_over_selectivity"] for v in grid.values())
+    # cells where the policies pick different orders (equal orders differ only by run-to-run noise)
+    diff_s = [v["cost_over_score"] for v in grid.values() if v["orders"]["cost"] != v["orders"]["rank"]]
+    diff_l = [v["cost_over_selectivity"] for v in grid.values() if v["orders"]["cost"] != v["orders"]["selectivity"]]
+    worst = (min(diff_s) if diff_s else None, min(diff_l) if diff_l else None)
     return {
         "metric": METRIC, "value": round(value, 1), "unit": "tuples/s", "n_gpus": ws, "steps": steps,
         "warmup": 1, "ms_per_step": head["cost"]["ms"], "higher_is_better": True, "scaling": "weak",
@@ -1403,8 +1463,9 @@ def ours_uc1(args):
             "paper_example": "14 vs 20 time units (cost-driven vs score-/selectivity-driven), ratio 0.7",
             "shared_gpu_ms": {p: v["ms"] for p, v in shared.items()}},
         "synthetic_sweep": grid,
-        "sweep_claims": {"cost_never_worse_than_score_min_ratio": worst[0],
-                         "cost_never_worse_than_selectivity_min_ratio": worst[1],
+        "sweep_claims": {"cost_never_worse_than_score_min_ratio_where_orders_differ": worst[0],
+                         "cost_never_worse_than_selectivity_min_ratio_where_orders_differ": worst[1],
+                         "cells_where_orders_differ": {"score": len(diff_s), "selectivity": len(diff_l)},
                          "selectivity_slowest_mean": round(float(np.mean([v["ms"]["selectivity"] for v in grid.values()])), 3),
                          "score_mean": round(float(np.mean([v["ms"]["rank"] for v in grid.values()])), 3),
                          "cost_mean": round(float(np.mean([v["ms"]["cost"] for v in grid.values()])), 3)},
@@ -1552,6 +1613,76 @@ def ours_mlp3(args):
                 "h2d_bytes_per_step": int(w.n * w.dim * 4),
                 "d2h_bytes_per_step": int(w.n // w.batch * (4 * (w.batch // 32) + 64 + 32 * 8))},
     }
+
+
+# ---------------------------------------------------------------- routing-side kernels
+
+def ours_routing(args):
+    """The routing-side kernels on the drifting stream's first 65,536 tuples
+    (512-d fp32, five MLP predicates, batches of 4,096): a BF16 query (row
+    gather, tensor-core layers, classify, band staging, compaction, result)
+    and an FP32 query whose two heads share a cached embedding (reuse-cache
+    probe and store).  The line reports each query's tuples/s; its use is
+    as the command that ncu captures these kernels from."""
+    import torch
+    import paper_2403_14902_b300 as H
+    ws, rank = dist_init("nccl")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    w = D.workload("drift5")
+    n = 16 * w.batch
+    th = thresholds("drift5")
+    X = torch.from_numpy(D.stream_tuples(w, n)).cuda()
+    ids = torch.arange(n, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    out = {}
+
+    def bf16_query():
+        q = H.Query("vec", dim=w.dim, max_batch=w.batch, policy="rank", precision="bf16", max_in_flight=8,
+                    stream=stream)
+        for i, layers in enumerate(D.predicate_weights(w)):
+            q.add_mlp(layers, th[i])
+        q.calibrate(X[:1024])
+        return q, lambda: run_step(q, X, w.batch, 8)
+
+    def reuse_query():
+        q = H.Query("vec", dim=w.dim, max_batch=w.batch, policy="rank", precision="fp32", max_in_flight=8,
+                    stream=stream)
+        emb = q.add_embedding(D.embedding_weights(w), n)
+        for i in range(len(w.udfs)):
+            if i in w.extra["emb_preds"]:
+                q.add_mlp(D.head_weights(w, i), th[i], upstream=emb)
+            else:
+                q.add_mlp(D.predicate_weights(w)[i], th[i])
+
+        def step():
+            q.cache_clear(emb)
+            pending, res = [], []
+            for b0 in range(0, n, w.batch):
+                pending.append(q.submit(X[b0:b0 + w.batch], ids[b0:b0 + w.batch]))
+                if len(pending) >= 8:
+                    res.append(q.poll(pending.pop(0)))
+            res += [q.poll(b) for b in pending]
+            return res
+        return q, step
+
+    for name, make in (("bf16_query", bf16_query), ("reuse_query_fp32", reuse_query)):
+        q, f = make()
+        for _ in range(args.warmup):
+            f()
+        secs, _ = timed(f, args.steps, stream, local)
+        q.close()
+        out[name] = {"value": round(n * args.steps / secs, 1), "unit": "tuples/s",
+                     "ms_per_step": round(secs / args.steps * 1000.0, 3)}
+    if rank != 0:
+        return None
+    a = out["bf16_query"]
+    return {"metric": "routing-side kernels: query tuples/sec", "value": a["value"], "unit": "tuples/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": a["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"routing: drift5 prefix of {n} x {w.dim} fp32 tuples, five MLP predicates, batches "
+                                   f"of {w.batch}; a BF16 query and an FP32 query with a cached shared embedding"},
+            "queries": out}
 
 
 # ---------------------------------------------------------------- GEMM alone
@@ -1730,6 +1861,8 @@ def reference(args):
         return reference_conv(args)
     if name == "peaks":
         return {"impl": "reference", "unavailable": "the peaks probe has no oracle counterpart"}
+    if name == "routing":
+        return {"impl": "reference", "unavailable": "the routing-kernel micro workload has no oracle counterpart"}
     w = D.workload(name)
     th = thresholds(name)
     if name == "mq64":
@@ -1844,16 +1977,17 @@ def main(argv=None):
     ap.add_argument("--lanes", type=int, default=4, help="cnn4: stream lanes of the query (1..8)")
     ap.add_argument("--pipeline", choices=["partitions", "shares"], default="partitions",
                     help="uc1: SM partitions (green contexts) or SM shares by grid size for the positions")
-    ap.add_argument("--lag", type=int, default=3, help="cnn4: route lag (>= lanes - 1)")
+    ap.add_argument("--lag", type=int, default=3, help="cnn4, drift5: route lag (cnn4: >= lanes - 1)")
+    ap.add_argument("--batch", type=int, default=0, help="cnn4: routing batch size (0: the workload's 1,024)")
     ap.add_argument("--split", choices=["tf32x3", "bf16x3"], default="bf16x3",
                     help="cnn4: first recheck level of the BF16 CNN UDFs")
-    ap.add_argument("--workload", choices=["cnn4", "mlp3", "uc1", "drift5", "drift6", "mq64", "gemm_bf16", "conv_bf16", "peaks"],
+    ap.add_argument("--workload", choices=["cnn4", "mlp3", "uc1", "routing", "drift5", "drift6", "mq64", "gemm_bf16", "conv_bf16", "peaks"],
                     default=WORKLOAD)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         out = reference(args)
     else:
-        out = {"cnn4": ours, "mlp3": ours_mlp3, "uc1": ours_uc1, "drift5": ours_drift5, "drift6": ours_drift6, "mq64": ours_mq64,
+        out = {"cnn4": ours, "mlp3": ours_mlp3, "uc1": ours_uc1, "routing": ours_routing, "drift5": ours_drift5, "drift6": ours_drift6, "mq64": ours_mq64,
                "gemm_bf16": ours_gemm_bf16, "conv_bf16": ours_conv_bf16, "peaks": ours_peaks}[args.workload](args)
     if out is not None:
         print(json.dumps(out), flush=True)

@@ -106,13 +106,16 @@ struct Slot {
     cudaEvent_t start = nullptr, done = nullptr;
     unsigned char *dres = nullptr;   // device result block
     unsigned char *hres = nullptr;   // pinned host mirror
+    bool dev = false;                // routed and dispatched on the device (order in the result header)
 };
 
 // Result block layout (device and pinned host).
 struct ResHdr {
     long long n_pass;
     unsigned int err;
-    unsigned int pad[13];
+    unsigned int pad0;
+    int order[8];        // device-dispatched batches: the order the router chose
+    unsigned int pad[4];
 };
 static_assert(sizeof(ResHdr) == 64, "header size");
 constexpr size_t kRowsOff = sizeof(ResHdr);
@@ -167,6 +170,9 @@ struct LaneBufs {
     float *partials = nullptr;
     __nv_bfloat16 *stage16 = nullptr, *act16[2] = {};
     void *band_rows = nullptr;
+    void *batch_rows = nullptr;       // device dispatch: the batch's tuples
+    unsigned char *lres = nullptr;    // device dispatch: the batch's result block
+    int *lord = nullptr, *ln = nullptr;   // device dispatch: router order, batch size
 };
 
 struct hydro_query {
@@ -249,11 +255,19 @@ struct hydro_query {
     int cur_lane = 0;
     // recheck graphs: the recheck levels of predicate p on lane l replay from tail[l][p]
     void *band_rows = nullptr;       // current lane's staging buffer of the band's tuples [cap1][tuple bytes]
+    // device-dispatched batches: each lane's batch graph (a SWITCH per position)
+    void *batch_rows = nullptr;
+    unsigned char *lres = nullptr;
+    int *lord = nullptr, *ln = nullptr;
+    cudaGraphExec_t bgraph[kMaxLanes] = {};
+    int *d_switch_n = nullptr;       // [kMaxLanes][8 positions][8 predicates] kernels per switch body
     cudaGraphExec_t tail[kMaxLanes][kMaxPred] = {};
     int tail_gates[kMaxLanes][kMaxPred] = {};
     int *d_body_n = nullptr;         // [kMaxLanes][kMaxPred][3] kernels per conditional body
     unsigned long long *d_launch_ctr = nullptr;   // kernels the conditional bodies ran
-    cudaStream_t cap_st = nullptr, cap_body_st = nullptr;
+    cudaStream_t cap_st = nullptr;
+    cudaStream_t cap_help[3] = {};   // capture streams of nested conditional bodies
+    int cap_depth = 0;
     bool capturing = false;
     cudaGraph_t cap_graph = nullptr;
     std::vector<std::pair<int *, int>> cap_body_counts;   // (device slot, kernels) of the bodies just captured
@@ -316,6 +330,16 @@ long long model_cost(const Pred &p, const hydro_query_config &c) {
 // prepare the same tensor-core weights and buffers.
 bool tc_query(const hydro_query_config &c) {
     return c.precision == HYDRO_PREC_BF16 || c.precision == HYDRO_PREC_BF16X3;
+}
+
+bool adaptive(int policy);
+
+// Routed batches of this query can run from a per-lane graph whose SWITCH
+// nodes take the order the router writes on the device (no host round trip).
+bool device_dispatch(const hydro_query *q) {
+    const hydro_query_config &c = q->cfg;
+    return c.recheck_graphs && !c.pipeline && q->embs.empty() &&
+           (c.policy == HYDRO_POLICY_RANK || c.policy == HYDRO_POLICY_COST || c.policy == HYDRO_POLICY_SELECTIVITY);
 }
 
 bool adaptive(int policy) {
@@ -441,6 +465,14 @@ hydro_status alloc_scratch(hydro_query *q) {
         }
     }
     if (c.recheck_graphs) TRY(dalloc(q, (unsigned char **)&q->band_rows, (size_t)q->cap1 * tuple_bytes(c)));
+    if (device_dispatch(q)) {
+        TRY(dalloc(q, (unsigned char **)&q->batch_rows, (size_t)B * tuple_bytes(c)));
+        TRY(dalloc(q, &q->lres, kBitmapOff + sizeof(unsigned int) * (size_t)((B + 31) / 32)));
+        TRY(dalloc(q, &q->lord, sizeof(int) * kMaxPred));
+        TRY(dalloc(q, &q->ln, sizeof(int)));
+        CU(cudaMemset(q->lord, 0, sizeof(int) * kMaxPred));
+        CU(cudaMemset(q->ln, 0, sizeof(int)));
+    }
     return HYDRO_OK;
 }
 
@@ -469,6 +501,10 @@ void save_lane(hydro_query *q, int l) {
     L.partials = q->partials;
     L.stage16 = q->stage16;
     L.band_rows = q->band_rows;
+    L.batch_rows = q->batch_rows;
+    L.lres = q->lres;
+    L.lord = q->lord;
+    L.ln = q->ln;
 }
 
 // Make lane l current: its scratch and its stream.
@@ -497,6 +533,10 @@ void load_lane(hydro_query *q, int l) {
     q->partials = L.partials;
     q->stage16 = L.stage16;
     q->band_rows = L.band_rows;
+    q->batch_rows = L.batch_rows;
+    q->lres = L.lres;
+    q->lord = L.lord;
+    q->ln = L.ln;
     q->st = q->lane_st[l];
     q->cur_lane = l;
 }
@@ -634,12 +674,14 @@ hydro_status finalize(hydro_query *q) {
     TRY(dalloc(q, &q->vmiss, sizeof(int) * kMaxPred));
     TRY(dalloc(q, &q->miss_list, sizeof(int) * B));
     if (c.recheck_graphs) {
+        TRY(dalloc(q, &q->d_switch_n, sizeof(int) * kMaxLanes * kMaxPred * kMaxPred));
+        CU(cudaMemset(q->d_switch_n, 0, sizeof(int) * kMaxLanes * kMaxPred * kMaxPred));
         TRY(dalloc(q, &q->d_body_n, sizeof(int) * kMaxLanes * kMaxPred * 3));
         CU(cudaMemset(q->d_body_n, 0, sizeof(int) * kMaxLanes * kMaxPred * 3));
         TRY(dalloc(q, &q->d_launch_ctr, sizeof(unsigned long long)));
         CU(cudaMemset(q->d_launch_ctr, 0, sizeof(unsigned long long)));
         CU(cudaStreamCreateWithFlags(&q->cap_st, cudaStreamNonBlocking));
-        CU(cudaStreamCreateWithFlags(&q->cap_body_st, cudaStreamNonBlocking));
+        for (int k = 0; k < 3; ++k) CU(cudaStreamCreateWithFlags(&q->cap_help[k], cudaStreamNonBlocking));
     }
     for (Emb &e : q->embs) {
         e.dW.resize(e.n_layers);
@@ -1059,15 +1101,18 @@ hydro_status enqueue_rechecks(hydro_query *q, int pi, const void *bt, long long 
         cudaGraphNode_t node;
         CU(cudaGraphAddNode(&node, g, deps, ed, nd, &np));
         CU(cudaStreamUpdateCaptureDependencies(q->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-        CU(cudaStreamBeginCaptureToGraph(q->cap_body_st, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+        if (q->cap_depth >= 3) return fail(HYDRO_ECUDA, "conditional bodies nest too deep");
+        const cudaStream_t hs = q->cap_help[q->cap_depth++];
+        CU(cudaStreamBeginCaptureToGraph(hs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                          cudaStreamCaptureModeThreadLocal));
         const cudaStream_t top = q->st;
-        q->st = q->cap_body_st;
+        q->st = hs;
         const long long l0 = q->launches;
         hydro_status rs = body();
         const int n_body = (int)(q->launches - l0);
         cudaGraph_t out = nullptr;
-        cudaError_t ee = cudaStreamEndCapture(q->cap_body_st, &out);
+        cudaError_t ee = cudaStreamEndCapture(hs, &out);
+        q->cap_depth--;
         q->st = top;
         if (rs != HYDRO_OK) return rs;
         CU(ee);
@@ -1178,9 +1223,12 @@ hydro_status ensure_tail(hydro_query *q, int pi) {
     return HYDRO_OK;
 }
 
+// dev_rows (device-dispatched batches, while capturing the lane's batch
+// graph): the stage's statistics go to the lane's result rows and its recheck
+// levels become IF nodes that read the lane's copy of the batch directly.
 hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *in_list, int *out_list,
                        int *out_count, bool eval_all, const void *tuples, const long long *ids, int n,
-                       long long batch, Slot &slot) {
+                       long long batch, Slot *slot, StatRow *dev_rows = nullptr) {
     const hydro_query_config &c = q->cfg;
     const Pred &p = q->preds[pi];
     // split_main: split BF16 is the working precision, so the cascade is
@@ -1194,7 +1242,7 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
     const ProfCtx pc_main{batch, pi, SRC_MAIN};
     int *miss_count = nullptr;
     const bool measure = c.cost_source == HYDRO_COST_MEASURED;
-    StatRow *row = q->ring + (batch % q->ring_len) * kMaxPred + pi;
+    StatRow *row = dev_rows ? dev_rows + pi : q->ring + (batch % q->ring_len) * kMaxPred + pi;
     if (measure) {
         launch_stage_start(row, q->st);
         q->launches++;
@@ -1212,7 +1260,9 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
     launch_classify_f32(in_count, in_list, q->score32, p.threshold, margin0, q->pass,
                         q->band1_m, q->band1_t, band1_count, bf16 ? q->cap1 : q->cap3, q->d_err, q->st);
     q->launches++;
-    if (c.recheck_graphs && !q->gctx[0]) {
+    if (dev_rows) {
+        TRY(enqueue_rechecks(q, pi, tuples, batch));
+    } else if (c.recheck_graphs && !q->gctx[0]) {
         // the band's tuples to the lane's staging buffer, then the captured levels
         launch_band_stage(band1_count, q->band1_t, tuples, tuple_bytes(c), q->band_rows, bf16 ? q->cap1 : q->cap3,
                           q->sms, q->st);
@@ -1227,12 +1277,122 @@ hydro_status run_stage(hydro_query *q, int pi, const int *in_count, const int *i
     const int *cnt_tf = tf32_level ? band1_count : nullptr;
     const int *cnt_32 = bf16 ? (tf32_level ? band2_count : band1_count) : nullptr;
     const int *b64_count = bf16 ? band3_count : band1_count;
-    StatRow *rrow = (StatRow *)(slot.dres + kRowsOff) + pi;
+    StatRow *rrow = dev_rows ? row : (StatRow *)(slot->dres + kRowsOff) + pi;
     StatRow *warm = nullptr;
-    if (adaptive(c.policy) && batch < c.warmup_batches) warm = q->warm + batch * kMaxPred + pi;
+    if (!dev_rows && adaptive(c.policy) && batch < c.warmup_batches) warm = q->warm + batch * kMaxPred + pi;
     launch_compact(in_count, in_list, q->pass, out_list, out_count, eval_all ? q->acc : nullptr, cnt_tf, cnt_32,
                    b64_count, miss_count, row, rrow, warm, q->st, measure ? 1 : 0);
     q->launches++;
+    return HYDRO_OK;
+}
+
+// Capture the current lane's batch graph (once): the initial alive list, the
+// dispatch kernel (order -> SWITCH values), one SWITCH node per position with
+// one body per predicate (that predicate's whole stage at that position,
+// recheck levels as nested IF nodes), and the result bitmap.
+hydro_status ensure_batch_graph(hydro_query *q) {
+    const int l = q->cur_lane;
+    if (q->bgraph[l]) return HYDRO_OK;
+    const int P = (int)q->preds.size();
+    const cudaStream_t saved = q->st;
+    const long long l0 = q->launches;
+    ResHdr *hdr = (ResHdr *)q->lres;
+    int *bodyn = q->d_switch_n + (size_t)l * kMaxPred * kMaxPred;
+    std::vector<int> hbody((size_t)P * P, 0);
+    q->st = q->cap_st;
+    q->cap_body_counts.clear();
+    q->cap_depth = 0;
+    CU(cudaStreamBeginCapture(q->cap_st, cudaStreamCaptureModeThreadLocal));
+    hydro_status rs = HYDRO_OK;
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamGetCaptureInfo(q->cap_st, &cs, nullptr, &q->cap_graph, nullptr, nullptr, nullptr) != cudaSuccess)
+        rs = fail(HYDRO_ECUDA, "capture info of the batch graph");
+    q->capturing = true;
+    SwitchHandles sh{};
+    for (int k = 0; k < P && rs == HYDRO_OK; ++k) {
+        cudaGraphConditionalHandle h;
+        if (cudaGraphConditionalHandleCreate(&h, q->cap_graph, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+            rs = fail(HYDRO_ECUDA, "conditional handle of position %d", k);
+        sh.h[k] = (unsigned long long)h;
+    }
+    if (rs == HYDRO_OK) {
+        launch_init_alive_dev(q->alive[0], q->ints + 0, q->ln, q->cfg.max_batch, q->st);
+        launch_dispatch(q->lord, sh, P, bodyn, q->d_launch_ctr, hdr->order, q->st);
+    }
+    int cur = 0;
+    for (int k = 0; k < P && rs == HYDRO_OK; ++k) {
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        const cudaGraphEdgeData *ed = nullptr;
+        size_t nd = 0;
+        if (cudaStreamGetCaptureInfo(q->st, &cs, nullptr, &g, &deps, &ed, &nd) != cudaSuccess) {
+            rs = fail(HYDRO_ECUDA, "capture info at position %d", k);
+            break;
+        }
+        alignas(cudaGraphNodeParams) unsigned char pbuf[sizeof(cudaGraphNodeParams)];
+        std::memset(pbuf, 0, sizeof pbuf);
+        cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(pbuf);   // zeroed, as the API requires
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = (cudaGraphConditionalHandle)sh.h[k];
+        np.conditional.type = cudaGraphCondTypeSwitch;
+        np.conditional.size = (unsigned)P;
+        cudaGraphNode_t node;
+        if (cudaGraphAddNode(&node, g, deps, ed, nd, &np) != cudaSuccess ||
+            cudaStreamUpdateCaptureDependencies(q->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+                cudaSuccess) {
+            rs = fail(HYDRO_ECUDA, "SWITCH node of position %d", k);
+            break;
+        }
+        for (int i = 0; i < P && rs == HYDRO_OK; ++i) {
+            const cudaStream_t hs = q->cap_help[q->cap_depth++];
+            if (cudaStreamBeginCaptureToGraph(hs, np.conditional.phGraph_out[i], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                q->cap_depth--;
+                rs = fail(HYDRO_ECUDA, "capture of position %d, predicate %d", k, i);
+                break;
+            }
+            q->st = hs;
+            const long long b0 = q->launches;
+            rs = run_stage(q, i, q->ints + cur, q->alive[cur], q->alive[1 - cur], q->ints + 1 - cur, false,
+                           q->batch_rows, nullptr, q->cfg.max_batch, -1, nullptr, (StatRow *)(q->lres + kRowsOff));
+            hbody[(size_t)k * P + i] = (int)(q->launches - b0);
+            cudaGraph_t out = nullptr;
+            cudaError_t ee = cudaStreamEndCapture(hs, &out);
+            q->cap_depth--;
+            q->st = q->cap_st;
+            if (rs == HYDRO_OK && ee != cudaSuccess) rs = fail(HYDRO_ECUDA, "end of capture: %s", cudaGetErrorString(ee));
+        }
+        cur = 1 - cur;
+    }
+    if (rs == HYDRO_OK)
+        launch_result_dev(q->ints + cur, q->alive[cur], q->ln, (unsigned int *)(q->lres + kBitmapOff), &hdr->n_pass,
+                          q->st);
+    q->capturing = false;
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(q->cap_st, &graph);
+    q->st = saved;
+    q->cap_graph = nullptr;
+    q->launches = l0;
+    if (rs != HYDRO_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rs;
+    }
+    if (ee != cudaSuccess || !graph) {
+        cudaGetLastError();
+        return fail(HYDRO_ECUDA, "capture of the batch graph failed: %s", cudaGetErrorString(ee));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&q->bgraph[l], graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        q->bgraph[l] = nullptr;
+        cudaGetLastError();
+        return fail(HYDRO_ECUDA, "instantiating the batch graph failed: %s", cudaGetErrorString(ie));
+    }
+    // kernel counts of the bodies (the dispatch kernel adds the chosen ones, the gates theirs)
+    CU(cudaMemcpy(bodyn, hbody.data(), sizeof(int) * hbody.size(), cudaMemcpyHostToDevice));
+    for (const auto &bc : q->cap_body_counts) CU(cudaMemcpy(bc.first, &bc.second, sizeof(int), cudaMemcpyHostToDevice));
+    q->cap_body_counts.clear();
     return HYDRO_OK;
 }
 
@@ -1834,25 +1994,32 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
     if (!eval_all && c.policy == HYDRO_POLICY_STATIC) {
         if (!q->static_order.empty())
             for (int i = 0; i < P; ++i) order[i] = q->static_order[i];
-    } else if (!eval_all) {
-        const long long last = b - 1 - c.route_lag;
-        if (last >= 0) {
-            const long long lo = std::max(0LL, last - c.stats_window + 1);
-            const int nwv = (int)std::min<long long>(c.warmup_batches, last + 1);
-            RouterCosts costs{};
-            for (int i = 0; i < P; ++i) {
-                costs.c[i] = q->preds[i].cost;
-                costs.group[i] = q->preds[i].upstream - 1;
-            }
-            for (size_t e = 0; e < q->embs.size(); ++e) costs.cemb[e] = q->embs[e].cost;
-            costs.n = n;
-            costs.measured = c.cost_source == HYDRO_COST_MEASURED ? 1 : 0;
-            const int pol = (c.policy == HYDRO_POLICY_RANK || c.policy == HYDRO_POLICY_LEARNED) ? 0
-                            : c.policy == HYDRO_POLICY_COST                                      ? 1
-                                                                                                 : 2;
+    }
+    // routed batch: its order comes from the statistics of batches <= last
+    const long long last = b - 1 - c.route_lag;
+    const bool routed = !eval_all && c.policy != HYDRO_POLICY_STATIC && last >= 0;
+    // device dispatch: the router and the stages run from the lane's batch graph, no host wait
+    const bool dev = routed && device_dispatch(q) && !q->prof.on;
+    const long long lo = std::max(0LL, last - c.stats_window + 1);
+    const int nwv = (int)std::min<long long>(c.warmup_batches, last + 1);
+    RouterCosts costs{};
+    for (int i = 0; i < P; ++i) {
+        costs.c[i] = q->preds[i].cost;
+        costs.group[i] = q->preds[i].upstream - 1;
+    }
+    for (size_t e = 0; e < q->embs.size(); ++e) costs.cemb[e] = q->embs[e].cost;
+    costs.n = n;
+    costs.measured = c.cost_source == HYDRO_COST_MEASURED ? 1 : 0;
+    const int pol = (c.policy == HYDRO_POLICY_RANK || c.policy == HYDRO_POLICY_LEARNED) ? 0
+                    : c.policy == HYDRO_POLICY_COST                                      ? 1
+                                                                                         : 2;
+    if (routed && !dev) {
+        {
             int *dord = q->d_order + slot_idx * kMaxPred;
             int *hord = q->h_order + slot_idx * kMaxPred;
-            CU(cudaStreamWaitEvent(q->rst, q->ev_done[last % kEvRing], 0));
+            // every lane's latest batch <= last: with lanes, batch last - 1 may finish after batch last
+            for (long long x = std::max(0LL, last - q->n_lanes + 1); x <= last; ++x)
+                CU(cudaStreamWaitEvent(q->rst, q->ev_done[x % kEvRing], 0));
             if (!q->embs.empty()) {
                 // reuse-aware cost: this batch's ids not cached by batches <= last
                 CU(cudaMemsetAsync(q->vmiss, 0, sizeof(int) * kMaxPred, q->rst));
@@ -1893,8 +2060,44 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
     slot->n = (int)n;
     slot->busy = true;
     slot->warmup = eval_all && c.policy != HYDRO_POLICY_ALL;
+    slot->dev = dev;
     std::memcpy(slot->order, order, sizeof order);
     CU(cudaEventRecord(slot->start, q->st));
+    if (dev) {
+        // the batch into the lane's buffer, the router on this stream once batch `last` is done,
+        // then the lane's graph picks every position's predicate from the router's order
+        const size_t tb = (size_t)tuple_bytes(c);
+        if (n > 0) CU(cudaMemcpyAsync(q->batch_rows, d_tuples, tb * (size_t)n, cudaMemcpyDeviceToDevice, q->st));
+        launch_set_int(q->ln, (int)n, q->st);
+        for (long long x = std::max(0LL, last - q->n_lanes + 1); x <= last; ++x)
+            CU(cudaStreamWaitEvent(q->st, q->ev_done[x % kEvRing], 0));
+        launch_router(q->ring, q->ring_len, q->warm, nwv, lo, last, P, pol, costs, nullptr, q->lord, q->st);
+        q->launches += 2;
+        hydro_status gs = ensure_batch_graph(q);
+        if (gs != HYDRO_OK) {
+            slot->busy = false;
+            q->dead = true;
+            return gs;
+        }
+        CU(cudaGraphLaunch(q->bgraph[q->cur_lane], q->st));
+        q->launches += 3;   // initial list, dispatch and result; the bodies are counted on the device
+        launch_commit_rows((const StatRow *)(q->lres + kRowsOff), q->ring + (b % q->ring_len) * kMaxPred, P, q->st);
+        q->launches++;
+        ResHdr *lh = (ResHdr *)q->lres;
+        CU(cudaMemcpyAsync(&lh->err, q->d_err, sizeof(unsigned int), cudaMemcpyDeviceToDevice, q->st));
+        const size_t bytes = kBitmapOff + sizeof(unsigned int) * (size_t)((n + 31) / 32);
+        CU(cudaMemcpyAsync(slot->hres, q->lres, bytes, cudaMemcpyDeviceToHost, q->st));
+        CU(cudaEventRecord(slot->done, q->st));
+        CU(cudaEventRecord(q->ev_done[b % kEvRing], q->st));
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) {
+            q->dead = true;
+            return fail(HYDRO_ECUDA, "kernel launch failed: %s", cudaGetErrorString(le));
+        }
+        q->next_batch = b + 1;
+        *out_batch_id = b;
+        return HYDRO_OK;
+    }
     int *cnt = q->ints;
     int cur = 0;
     const bool learned = c.policy == HYDRO_POLICY_LEARNED;
@@ -1917,7 +2120,7 @@ hydro_status hydro_submit_batch(hydro_query *q, const void *d_tuples, const int6
             q->sms = q->sms_pos;
         }
         hydro_status s = run_stage(q, order[k], cnt + cur, q->alive[cur], q->alive[1 - cur], cnt + 1 - cur, eval_all,
-                                   d_tuples, (const long long *)d_ids, (int)n, b, *slot);
+                                   d_tuples, (const long long *)d_ids, (int)n, b, slot);
         if (q->pipe) {
             q->sms = q->sms_full;
             if (s == HYDRO_OK) CU(cudaEventRecord(q->ev_stage[q->cur_lane][k], q->st));
@@ -1998,7 +2201,7 @@ hydro_status hydro_poll_result(hydro_query *q, int64_t batch_id, uint32_t *pass_
         info->n_predicates = P;
         info->warmup = slot->warmup ? 1 : 0;
         for (int i = 0; i < P; ++i) {
-            info->order[i] = slot->order[i];
+            info->order[i] = slot->dev ? hdr->order[i] : slot->order[i];
             info->passed[i] = rows[i].passed;
             info->recheck_tf32[i] = rows[i].recheck_tf32;
             info->cache_hits[i] = rows[i].hits;
@@ -2161,6 +2364,7 @@ hydro_status hydro_destroy_query(hydro_query *q) {
         for (int l = 0; l < kMaxLanes; ++l)
             for (int i = 0; i < kMaxPred; ++i) {
                 if (q->tail[l][i]) cudaGraphExecDestroy(q->tail[l][i]);
+                if (i == 0 && q->bgraph[l]) cudaGraphExecDestroy(q->bgraph[l]);
                 if (q->ev_stage[l][i]) cudaEventDestroy(q->ev_stage[l][i]);
             }
         GreenApi g;
@@ -2176,7 +2380,8 @@ hydro_status hydro_destroy_query(hydro_query *q) {
         for (int k = 0; k < kMaxPred; ++k)
             if (q->gctx[k] && green) g.destroy(q->gctx[k]);
         if (q->cap_st) cudaStreamDestroy(q->cap_st);
-        if (q->cap_body_st) cudaStreamDestroy(q->cap_body_st);
+        for (int k = 0; k < 3; ++k)
+            if (q->cap_help[k]) cudaStreamDestroy(q->cap_help[k]);
         tc_conv_destroy(&q->tc);
         for (cudaEvent_t e : q->prof.ev) cudaEventDestroy(e);
         for (Slot &s : q->slots) {

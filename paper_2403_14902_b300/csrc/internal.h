@@ -62,6 +62,20 @@ void launch_compact(const int *count_in, const int *alive_in, const unsigned cha
                     const int *band64_count, const int *miss_count, StatRow *row, StatRow *rrow, StatRow *warm,
                     cudaStream_t st, int measure = 0);
 
+// Device-dispatched batches (a graph per stream lane): the switch handles of
+// the positions, the batch size on the device, the first and last kernels
+// and the copy of the batch's statistics rows into the ring.
+struct SwitchHandles {
+    unsigned long long h[8];
+};
+void launch_set_int(int *dst, int v, cudaStream_t st);
+void launch_init_alive_dev(int *alive, int *count, const int *n_dev, int max_n, cudaStream_t st);
+void launch_dispatch(const int *order, const SwitchHandles &h, int P, const int *body_n, unsigned long long *ctr,
+                     int *order_out, cudaStream_t st);
+void launch_result_dev(const int *count, const int *alive, const int *n_dev, unsigned int *bitmap, long long *n_pass,
+                       cudaStream_t st);
+void launch_commit_rows(const StatRow *src, StatRow *dst, int P, cudaStream_t st);
+
 // k_cache.cu: reuse cache of a shared upstream UDF's outputs, keyed by tuple id.
 // tags[id]: 0 absent, -1 prefilled, b+1 computed by batch b.
 void launch_cache_probe_miss(const int *count_in, const int *list_in, const long long *ids, const int *tags,

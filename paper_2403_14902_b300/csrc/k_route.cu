@@ -326,6 +326,55 @@ __global__ void k_gate(const int *count, unsigned long long handle, int *zero0, 
 }
 
 
+// ------------------------------------------------------------ device-dispatched batches
+// A routed batch can replay from a graph captured once per stream lane: the
+// batch's tuples are first copied into the lane's buffer and its size into
+// *n_dev, the router writes the lane's order, and the graph's first kernel
+// turns the order into the values of one SWITCH node per position.
+
+__global__ void k_set_int(int *dst, int v) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *dst = v;
+}
+
+__global__ void k_init_alive_dev(int *alive, int *count, const int *n_dev) {
+    const int n = *n_dev;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) alive[i] = i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count = n;
+}
+
+// Position k's SWITCH selects the body of predicate order[k]; the bodies'
+// kernel counts go to the launch counter; the order goes to the result block.
+__global__ void k_dispatch(const int *order, SwitchHandles h, int P, const int *body_n, unsigned long long *ctr,
+                           int *order_out) {
+    const int k = threadIdx.x;
+    if (blockIdx.x != 0 || k >= P) return;
+    const int i = order[k];
+    const int v = (i >= 0 && i < P) ? i : 0;
+    cudaGraphSetConditional((cudaGraphConditionalHandle)h.h[k], (unsigned)v);
+    if (order_out) order_out[k] = i;
+    if (ctr && body_n) atomicAdd(ctr, (unsigned long long)body_n[k * P + v]);
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_result_dev(const int *count, const int *alive, const int *n_dev, unsigned int *bitmap, long long *n_pass) {
+    const int n = *n_dev;
+    const int words = (n + 31) >> 5;
+    for (int w = threadIdx.x; w < words; w += blockDim.x) bitmap[w] = 0u;
+    __syncthreads();
+    const int c = *count;
+    for (int m = threadIdx.x; m < c; m += blockDim.x) {
+        const int j = alive[m];
+        atomicOr(&bitmap[j >> 5], 1u << (j & 31));
+    }
+    if (threadIdx.x == 0) *n_pass = c;
+}
+
+// The batch's statistics rows into its slot of the ring (the router's source).
+__global__ void k_commit_rows(const StatRow *src, StatRow *dst, int P) {
+    const int i = threadIdx.x;
+    if (blockIdx.x == 0 && i < P) dst[i] = src[i];
+}
+
 // ------------------------------------------------------------ launchers
 
 void launch_init_alive(int *alive, int *count, int n, unsigned char *acc, cudaStream_t st) {
@@ -386,6 +435,27 @@ void launch_acc_to_alive(const unsigned char *acc, int n, int *alive_out, int *c
 void launch_result(const int *count, const int *alive, int n, unsigned int *bitmap, long long *n_pass,
                    cudaStream_t st) {
     k_result<<<1, kScanThreads, 0, st>>>(count, alive, n, bitmap, n_pass);
+}
+
+void launch_set_int(int *dst, int v, cudaStream_t st) { k_set_int<<<1, 32, 0, st>>>(dst, v); }
+
+void launch_init_alive_dev(int *alive, int *count, const int *n_dev, int max_n, cudaStream_t st) {
+    const int blocks = max_n > 0 ? (max_n + 255) / 256 : 1;
+    k_init_alive_dev<<<blocks < 1024 ? blocks : 1024, 256, 0, st>>>(alive, count, n_dev);
+}
+
+void launch_dispatch(const int *order, const SwitchHandles &h, int P, const int *body_n, unsigned long long *ctr,
+                     int *order_out, cudaStream_t st) {
+    k_dispatch<<<1, 32, 0, st>>>(order, h, P, body_n, ctr, order_out);
+}
+
+void launch_result_dev(const int *count, const int *alive, const int *n_dev, unsigned int *bitmap, long long *n_pass,
+                       cudaStream_t st) {
+    k_result_dev<<<1, kScanThreads, 0, st>>>(count, alive, n_dev, bitmap, n_pass);
+}
+
+void launch_commit_rows(const StatRow *src, StatRow *dst, int P, cudaStream_t st) {
+    k_commit_rows<<<1, 32, 0, st>>>(src, dst, P);
 }
 
 void launch_router(const StatRow *ring, int ring_len, const StatRow *warm, int n_warm_visible,

@@ -31,6 +31,50 @@ def test_full_stream_parity(mlp3, policy):
     q.close()
 
 
+@pytest.mark.parametrize("policy,lag,precision,lanes", [("rank", 0, "fp32", 1), ("rank", 1, "fp32", 1),
+                                                        ("cost", 2, "fp32", 1), ("selectivity", 1, "fp32", 1),
+                                                        ("rank", 1, "bf16", 1), ("rank", 3, "bf16", 4)])
+def test_device_dispatch_matches_host_routing(mlp3, policy, lag, precision, lanes):
+    """Routed batches dispatched on the device (the router writes the order,
+    the lane's graph picks each position's predicate through SWITCH nodes)
+    against the same query routed on the host (recheck graphs off, the host
+    reads the order and launches the stages): identical orders, counts and
+    pass sets, both equal to the oracle's simulation."""
+    w = mlp3["w"]
+    got = {}
+    for graphs in (True, False):
+        q = make_query(w, mlp3["th"], batch=w.batch, policy=policy, lag=lag, window=2, precision=precision,
+                       lanes=lanes, max_in_flight=8, recheck_graphs=graphs)
+        if precision == "bf16":
+            q.calibrate(mlp3["Xd"][:512])
+        res = run_stream(q, mlp3["Xd"], w.batch, max_in_flight=8)
+        check_against_oracle(res, mlp3["pm"], w.batch, policy=policy, costs=model_costs(w), lag=lag, window=2)
+        got[graphs] = [(r[2]["order"], r[1].tolist(), r[0].tolist()) for r in res]
+        q.close()
+    assert got[True] == got[False]
+
+
+def test_device_dispatch_on_a_drifting_stream():
+    """Eight segments of 4,096 tuples with their own cluster mixtures (six
+    MLPs of cost 1:2:...:32): the orders change between batches; device
+    dispatch and host routing agree with each other and with the oracle."""
+    import torch
+    w = D.workload("drift6", n=8 * 4096, extra=dict(D.WORKLOADS["drift6"].extra, segment_len=4096))
+    th, _ = oracle_thresholds(w)
+    X = D.stream_tuples(w)
+    pm = O.pass_matrix(O.udf_scores("vec", X, D.predicate_weights(w)), th)
+    Xd = torch.from_numpy(X).cuda()
+    got = {}
+    for graphs in (True, False):
+        q = make_query(w, th, batch=1024, policy="rank", lag=1, window=2, recheck_graphs=graphs, max_in_flight=8)
+        res = run_stream(q, Xd, 1024, max_in_flight=8)
+        check_against_oracle(res, pm, 1024, policy="rank", costs=model_costs(w), lag=1, window=2)
+        got[graphs] = [r[2]["order"] for r in res]
+        q.close()
+    assert got[True] == got[False]
+    assert len({tuple(o) for o in got[True]}) > 1, "the drifting stream should change the order"
+
+
 def test_static_permuted_order_and_lag0(mlp3):
     w = mlp3["w"]
     q = make_query(w, mlp3["th"], batch=w.batch, policy="static", static_order=[2, 0, 1])
