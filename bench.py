@@ -3,11 +3,11 @@
 Workload: the 65,536-frame stream (3x64x64 uint8, seeded Gaussian-like blobs
 on noise), four random-init CNN UDF predicates (2/4/6/8 conv3x3 layers of
 32-128 channels + global average pool + linear head) with target
-selectivities 0.3/0.6/0.1/0.9, routing batches of 1,024, rank c/(1-s)
+selectivities 0.3/0.6/0.1/0.9, routing batches of 2,048, rank c/(1-s)
 routing, BF16 tensor-core inference with FP32 accumulation and an FP32/FP64
 recheck of every score within 0.02 of its threshold.
 
-One step = the whole stream through the query (64 batches submitted and
+One step = the whole stream through the query (32 batches submitted and
 polled).  Inputs (805 MB) exceed L2 (126 MB), so no flush is needed between
 steps.  Printed as one JSON line on rank 0.
 
@@ -862,7 +862,9 @@ def ours(args):
         step()
     clocks = ClockSampler(local)
     clocks.start()
-    q.profile(False)            # clears the launch count; no per-launch events in the headline region
+    # clears the launch count; no per-launch events in the headline region (with --profile-launches:
+    # per-launch events, so routed batches take the host path and their kernels are visible to ncu)
+    q.profile(bool(args.profile_launches))
     secs, outs = timed(step, args.steps, stream, local)
     _, launches = q.profile_read()
     clk = clocks.stop()
@@ -870,6 +872,14 @@ def ours(args):
     value = aggregate(w.n, args.steps, secs_max, ws)
     folds = {"adaptive_bf16": verify("adaptive_bf16", outs)}
     evaluated = np.sum([r["counts"] for r in outs[-1]], axis=0)
+    if args.headline_only:
+        # a sweep or profiling run: the timed headline steps only
+        q.close()
+        return None if rank != 0 else {
+            "metric": METRIC, "value": round(value, 1), "unit": "tuples/s", "headline_only": True,
+            "ms_per_step": round(secs_max / args.steps * 1000.0, 3), "gpu_launches": int(launches), "clocks": clk,
+            "parity": parity.get("adaptive_bf16"),
+            "config": {"lanes": args.lanes, "route_lag": args.lag, "routing_batch": w.batch}}
 
     # end to end from pinned host memory
     Xp = Xh.pin_memory()
@@ -1147,7 +1157,8 @@ def ours_mq64(args):
     head_sched = None
     for name, precision, graphs, K in variants:
         s = make(precision, graphs, K, "static" if name.startswith("static") else "rank",
-                 tile_sched=({"static": "data_aware", "data_aware": "static"}[head_sched] if name == ALT else None))
+                 tile_sched=({"static": "data_aware", "data_aware": "static"}[head_sched] if name == ALT else
+                             args.tile_sched if name == HEAD else None))
         if K > 1:
             run_all(s)   # builds this K's device plan outside the timed region
         for _ in range(args.warmup):
@@ -1978,7 +1989,11 @@ def main(argv=None):
     ap.add_argument("--pipeline", choices=["partitions", "shares"], default="partitions",
                     help="uc1: SM partitions (green contexts) or SM shares by grid size for the positions")
     ap.add_argument("--lag", type=int, default=3, help="cnn4, drift5: route lag (cnn4: >= lanes - 1)")
-    ap.add_argument("--batch", type=int, default=0, help="cnn4: routing batch size (0: the workload's 1,024)")
+    ap.add_argument("--batch", type=int, default=0, help="cnn4: routing batch size (0: the workload's 2,048)")
+    ap.add_argument("--profile-launches", action="store_true",
+                    help="cnn4 --headline-only: per-launch events (host-routed batches, for a launch list)")
+    ap.add_argument("--tile-sched", choices=["static", "data_aware"], default=None,
+                    help="mq64: tile scheduler of the headline session's grouped launches (default: the library's)")
     ap.add_argument("--split", choices=["tf32x3", "bf16x3"], default="bf16x3",
                     help="cnn4: first recheck level of the BF16 CNN UDFs")
     ap.add_argument("--workload", choices=["cnn4", "mlp3", "uc1", "routing", "drift5", "drift6", "mq64", "gemm_bf16", "conv_bf16", "peaks"],

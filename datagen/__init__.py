@@ -19,7 +19,7 @@ for them with the shapes of the build's five configurations):
 * ``cnn4``  - 65,536 frames of 3x64x64 uint8 (Gaussian-like blobs on noise),
   four CNN UDFs with 2/4/6/8 conv3x3 layers of 32-128 channels + global
   average pool + linear, target selectivities 0.3/0.6/0.1/0.9, batches of
-  1,024.
+  2,048.
 * ``drift5`` - 1,048,576 x 512 fp32 tuples in 8 segments whose 8-cluster
   mixture weights are drawn from Dirichlet(0.5) per segment (so each
   predicate's selectivity drifts between segments); five MLP UDFs, the first
@@ -84,7 +84,7 @@ WORKLOADS = {
         udfs=((256, 128, 1), (256, 512, 512, 1), (256, 1024, 1024, 1024, 1)),
         selectivity=(0.5, 0.2, 0.8), n_calib=1024),
     "cnn4": Workload(
-        name="cnn4", wid=2, kind="frame", n=65536, batch=1024,
+        name="cnn4", wid=2, kind="frame", n=65536, batch=2048,
         udfs=((3, 32, 64), (3, 32, 64, 64, 128), (3, 32, 64, 64, 128, 128, 128),
               (3, 32, 64, 64, 128, 128, 128, 128, 128)),
         selectivity=(0.3, 0.6, 0.1, 0.9), n_calib=256, head_gain=(8.0, 8.0, 6.0, 4.0)),

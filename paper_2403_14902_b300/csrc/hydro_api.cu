@@ -217,6 +217,7 @@ struct hydro_query {
     int *band1_m = nullptr, *band1_t = nullptr, *band2_m = nullptr, *band2_t = nullptr;
     int *band3_m = nullptr, *band3_t = nullptr;
     int cap1 = 0, cap2 = 0, cap3 = 0;   // band capacities (entries / frames)
+    int ract_esz = 8;                   // bytes a channel of the CNN recheck activations
     float *rscore_t = nullptr;    // 3xTF32 recheck scores (band 1)
     float *rscore32 = nullptr;    // FP32 recheck scores
     double *rscore64 = nullptr;   // FP64 recheck scores
@@ -448,8 +449,12 @@ hydro_status alloc_scratch(hydro_query *q) {
         // BF16 activations, or [hi | lo] BF16 planes (split working precision) / FP32
         const size_t esz = c.precision == HYDRO_PREC_BF16 ? 2 : 4;
         for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->act[k], esz * px * B));
-        if (tc_query(c))   // 3xTF32 (two fp32 planes) and FP32 recheck levels
-            for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->ract32[k], 8 * px * std::max(q->cap1, q->cap2)));
+        // recheck levels: split BF16 ([hi | lo] bf16, 4 B a channel) and FP32 (4 B); 3xTF32 as the
+        // configured split level needs two fp32 planes (8 B)
+        q->ract_esz = (c.precision == HYDRO_PREC_BF16 && c.split_precision == HYDRO_PREC_TF32X3) ? 8 : 4;
+        if (tc_query(c))
+            for (int k = 0; k < 2; ++k)
+                TRY(dalloc(q, &q->ract32[k], (size_t)q->ract_esz * px * std::max(q->cap1, q->cap2)));
         for (int k = 0; k < 2; ++k) TRY(dalloc(q, &q->ract64[k], 8 * px * q->cap3));
         if (tc_query(c))
             TRY(dalloc(q, &q->partials, sizeof(float) * (size_t)B * tc_conv_max_head_parts(c.height, c.width)));
@@ -1882,7 +1887,9 @@ hydro_status hydro_udf_scores(hydro_query *q, int32_t pred, int32_t prec, const 
     const bool recheck_buf = cnn && tc_query(q->cfg) &&
                              (prec == HYDRO_PREC_FP32 || split);
     int *list = q->alive[0], *count = q->ints + 0;
-    const int chunk = (prec == HYDRO_PREC_FP64 && cnn) ? q->cap3 : recheck_buf ? std::min(q->cap1, q->cap2) : B;
+    // 3xTF32 scores need 8 B a channel: half as many frames fit a 4-byte recheck buffer
+    const int rchunk = std::max(1, std::min(q->cap1, q->cap2) / (prec == HYDRO_PREC_TF32X3 && q->ract_esz < 8 ? 2 : 1));
+    const int chunk = (prec == HYDRO_PREC_FP64 && cnn) ? q->cap3 : recheck_buf ? rchunk : B;
     const size_t tb = (size_t)tuple_bytes(q->cfg);
     for (int64_t s = 0; s < n; s += chunk) {
         const int m = (int)std::min<int64_t>(chunk, n - s);
