@@ -299,11 +299,14 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- our arm
 
-def build_query(H, w, th, *, policy, precision, stream, max_in_flight=8, lanes=2, lag=1, split="bf16x3"):
+def build_query(H, w, th, *, policy, precision, stream, max_in_flight=8, lanes=2, lag=1, split="bf16x3",
+                recheck_graphs=True):
     """Stream lanes: up to `lanes` consecutive batches run at once (route lag >= lanes - 1);
-    `split`: the first recheck level of the BF16 CNN UDFs."""
+    `split`: the first recheck level of the BF16 CNN UDFs; `recheck_graphs` False: every
+    recheck level launched directly (no conditional graph nodes, so ncu sees each kernel)."""
     q = H.Query(w.kind, frame=w.frame, max_batch=w.batch, policy=policy, precision=precision,
-                max_in_flight=max_in_flight, stream=stream, lanes=lanes, lag=lag, split=split)
+                max_in_flight=max_in_flight, stream=stream, lanes=lanes, lag=lag, split=split,
+                recheck_graphs=recheck_graphs)
     for i, udf in enumerate(D.predicate_weights(w)):
         q.add_cnn(udf, th[i])
     return q
@@ -855,7 +858,7 @@ def ours(args):
         return checks[-1][2]
 
     q = build_query(H, w, th, policy="rank", precision="bf16", stream=stream, max_in_flight=mif, lanes=args.lanes,
-                    lag=args.lag, split=args.split)
+                    lag=args.lag, split=args.split, recheck_graphs=not (args.headline_only and args.no_graphs))
     calib = q.calibrate(calib_d)
     step = lambda: run_step(q, X, w.batch, mif)  # noqa: E731
     for _ in range(args.warmup):
@@ -879,7 +882,8 @@ def ours(args):
             "metric": METRIC, "value": round(value, 1), "unit": "tuples/s", "headline_only": True,
             "ms_per_step": round(secs_max / args.steps * 1000.0, 3), "gpu_launches": int(launches), "clocks": clk,
             "parity": parity.get("adaptive_bf16"),
-            "config": {"lanes": args.lanes, "route_lag": args.lag, "routing_batch": w.batch}}
+            "config": {"lanes": args.lanes, "route_lag": args.lag, "routing_batch": w.batch,
+                       "recheck_graphs": not args.no_graphs}}
 
     # end to end from pinned host memory
     Xp = Xh.pin_memory()
@@ -1984,7 +1988,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--headline-only", action="store_true",
                     help="mq64: time the headline variant only (for profiling runs)")
-    ap.add_argument("--no-graphs", action="store_true", help="with --headline-only: launch without CUDA graphs")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="with --headline-only: launch without CUDA graphs (mq64 sessions; cnn4 recheck levels)")
     ap.add_argument("--lanes", type=int, default=4, help="cnn4: stream lanes of the query (1..8)")
     ap.add_argument("--pipeline", choices=["partitions", "shares"], default="partitions",
                     help="uc1: SM partitions (green contexts) or SM shares by grid size for the positions")

@@ -55,6 +55,34 @@ __host__ __device__ __forceinline__ float tf32_rne(float v) {
     return r;
 }
 
+// Exclusive prefix of one 0/1 flag per thread over a 1,024-thread block
+// (nonzero counts as 1): a warp's flags are one __ballot_sync word, a lane's
+// prefix is the popcount of the word's lower lanes, and warp 0 scans the 32
+// warp totals.  Returns the thread's exclusive prefix and writes the block
+// total to *total; every thread of the block must call it.
+__device__ __forceinline__ int block_scan_flags_1024(int flag, int *total) {
+    __shared__ int warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned word = __ballot_sync(0xffffffffu, flag != 0);
+    const int in_warp = __popc(word & ((1u << lane) - 1u));
+    if (lane == 0) warp_sums[warp] = __popc(word);
+    __syncthreads();
+    if (warp == 0) {
+        int w = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;   // inclusive
+    }
+    __syncthreads();
+    const int excl = in_warp + (warp ? warp_sums[warp - 1] : 0);
+    *total = warp_sums[31];
+    __syncthreads();
+    return excl;
+}
+
 template <typename T> struct Acc { using type = float; };
 template <> struct Acc<double> { using type = double; };
 

@@ -9,55 +9,40 @@ namespace hydro {
 
 constexpr int kProbeThreads = 1024;
 
-// Exclusive block scan of one int per thread (1024 threads).
-__device__ __forceinline__ int scan_1024(int v, int *total) {
-    __shared__ int sums[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        int w = sums[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        sums[lane] = w;
-    }
-    __syncthreads();
-    const int excl = x - v + (warp ? sums[warp - 1] : 0);
-    *total = sums[31];
-    __syncthreads();
-    return excl;
-}
-
 // Alive tuples whose id is not cached yet, in alive-list order.
 __global__ void __launch_bounds__(kProbeThreads)
 k_cache_probe_miss(const int *count_in, const int *list_in, const long long *ids, const int *tags, long long cap,
                    int *miss_list, int *miss_count, unsigned int *err) {
     const int n = *count_in;
     int base = 0;
-    for (int m0 = 0; m0 < n; m0 += kProbeThreads) {
-        const int m = m0 + threadIdx.x;
-        int miss = 0;
-        if (m < n) {
-            const long long id = ids[list_in[m]];
-            if (id < 0 || id >= cap) {
-                atomicOr(err, ERR_ID_RANGE);
-            } else {
-                miss = tags[id] == 0;
+    // four chunks of 1,024 entries: their dependent loads (list, id, tag) are
+    // in flight together, then the four scans run back to back
+    constexpr int K = 4;
+    for (int m0 = 0; m0 < n; m0 += K * kProbeThreads) {
+        int lv[K], miss[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int m = m0 + k * kProbeThreads + threadIdx.x;
+            lv[k] = m < n ? list_in[m] : -1;
+        }
+        long long idv[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) idv[k] = lv[k] >= 0 ? ids[lv[k]] : 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            miss[k] = 0;
+            if (lv[k] >= 0) {
+                if (idv[k] < 0 || idv[k] >= cap) atomicOr(err, ERR_ID_RANGE);
+                else miss[k] = tags[idv[k]] == 0;
             }
         }
-        int total;
-        const int pos = base + scan_1024(miss, &total);
-        if (miss) miss_list[pos] = list_in[m];
-        base += total;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            int total;
+            const int pos = base + block_scan_flags_1024(miss[k], &total);
+            if (miss[k]) miss_list[pos] = lv[k];
+            base += total;
+        }
     }
     if (threadIdx.x == 0) *miss_count = base;
 }

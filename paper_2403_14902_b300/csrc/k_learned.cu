@@ -19,33 +19,6 @@ namespace hydro {
 
 constexpr int kLThreads = 1024;
 
-__device__ __forceinline__ int lscan_1024(int v, int *total) {
-    __shared__ int sums[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        int w = sums[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        sums[lane] = w;
-    }
-    __syncthreads();
-    const int excl = x - v + (warp ? sums[warp - 1] : 0);
-    *total = sums[31];
-    __syncthreads();
-    return excl;
-}
-
 // ------------------------------------------------------------ orders
 
 // Per-tuple order for tuples 0..n-1: ascending c_i * (1 + exp(z_i)) =
@@ -99,7 +72,7 @@ k_partition(const int *count, const int *alive, const unsigned char *order, int 
         }
         for (int p = 0; p < P; ++p) {
             int total;
-            const int pos = base[p] + lscan_1024(pred == p, &total);
+            const int pos = base[p] + block_scan_flags_1024(pred == p, &total);
             if (pred == p) queues[(size_t)p * qstride + pos] = t;
             base[p] += total;
         }
@@ -179,8 +152,8 @@ k_grouped_classify(int P, const int *qcount, const int *queues, int qstride, con
                 }
             }
             int tot_b, tot_p;
-            const int pos = base + lscan_1024(inband, &tot_b);
-            (void)lscan_1024(pass, &tot_p);
+            const int pos = base + block_scan_flags_1024(inband, &tot_b);
+            (void)block_scan_flags_1024(pass, &tot_p);
             if (inband) {
                 if (pos < band_cap) {
                     band_g[pos] = p;
@@ -264,7 +237,7 @@ k_survivors(const int *count_in, const int *alive_in, const unsigned char *ok, i
         const int m = m0 + threadIdx.x;
         const int p = m < n ? (int)ok[alive_in[m]] : 0;
         int total;
-        const int pos = base + lscan_1024(p, &total);
+        const int pos = base + block_scan_flags_1024(p, &total);
         if (p) alive_out[pos] = alive_in[m];
         base += total;
     }

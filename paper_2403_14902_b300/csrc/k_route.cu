@@ -12,33 +12,10 @@
 namespace hydro {
 
 constexpr int kScanThreads = 1024;
-
-// Exclusive block scan of one 0/1 flag per thread (1024 threads): a warp's
-// flags are one __ballot_sync word, a lane's prefix is the popcount of the
-// word's lower lanes, and the 32 warp totals are scanned by warp 0.  Returns
-// the thread's exclusive prefix and writes the block total to *total.
-__device__ __forceinline__ int block_scan_1024(int flag, int *total) {
-    __shared__ int warp_sums[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned word = __ballot_sync(0xffffffffu, flag != 0);
-    const int in_warp = __popc(word & ((1u << lane) - 1u));
-    if (lane == 0) warp_sums[warp] = __popc(word);
-    __syncthreads();
-    if (warp == 0) {
-        int w = warp_sums[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        warp_sums[lane] = w;   // inclusive
-    }
-    __syncthreads();
-    const int excl = in_warp + (warp ? warp_sums[warp - 1] : 0);
-    *total = warp_sums[31];
-    __syncthreads();
-    return excl;
-}
+// Chunks of kScanThreads entries whose loads a thread issues before the first
+// of their scans, so a batch of up to 4,096 entries waits for its global loads
+// once instead of once per chunk.
+constexpr int kScanChunks = 4;
 
 __global__ void k_init_alive(int *alive, int *count, int n, unsigned char *acc) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -59,25 +36,34 @@ k_classify(const int *count_in, const int *alive_in, const S *scores, double t, 
            unsigned int *err) {
     const int n = *count_in;
     int base = 0;
-    for (int m0 = 0; m0 < n; m0 += kScanThreads) {
-        const int m = m0 + threadIdx.x;
-        int inband = 0;
-        if (m < n) {
-            const double s = (double)scores[m];
-            inband = fabs(s - t) <= margin;
-            pass[m] = (!inband && s > t) ? 1 : 0;
+    for (int m0 = 0; m0 < n; m0 += kScanChunks * kScanThreads) {
+        S sv[kScanChunks];
+#pragma unroll
+        for (int k = 0; k < kScanChunks; ++k) {
+            const int m = m0 + k * kScanThreads + threadIdx.x;
+            sv[k] = m < n ? scores[m] : S(0);
         }
-        int total;
-        const int pos = base + block_scan_1024(inband, &total);
-        if (inband) {
-            if (pos < band_cap) {
-                band_m[pos] = m;
-                band_tuple[pos] = alive_in[m];
-            } else {
-                atomicOr(err, ERR_BAND_OVERFLOW);
+#pragma unroll
+        for (int k = 0; k < kScanChunks; ++k) {
+            const int m = m0 + k * kScanThreads + threadIdx.x;
+            int inband = 0;
+            if (m < n) {
+                const double s = (double)sv[k];
+                inband = fabs(s - t) <= margin;
+                pass[m] = (!inband && s > t) ? 1 : 0;
             }
+            int total;
+            const int pos = base + block_scan_flags_1024(inband, &total);
+            if (inband) {
+                if (pos < band_cap) {
+                    band_m[pos] = m;
+                    band_tuple[pos] = alive_in[m];
+                } else {
+                    atomicOr(err, ERR_BAND_OVERFLOW);
+                }
+            }
+            base += total;
         }
-        base += total;
     }
     if (threadIdx.x == 0) *band_count = base < band_cap ? base : band_cap;
 }
@@ -101,7 +87,7 @@ k_recheck_classify(const int *band_count_in, const int *band_m_in, const int *ba
             if (!fwd) pass[band_m_in[j]] = s > t ? 1 : 0;
         }
         int total;
-        const int pos = base + block_scan_1024(fwd, &total);
+        const int pos = base + block_scan_flags_1024(fwd, &total);
         if (fwd) {
             if (pos < next_cap) {
                 next_m[pos] = band_m_in[j];
@@ -134,17 +120,27 @@ k_compact(const int *count_in, const int *alive_in, const unsigned char *pass, i
           int measure) {
     const int n = *count_in;
     int base = 0;
-    for (int m0 = 0; m0 < n; m0 += kScanThreads) {
-        const int m = m0 + threadIdx.x;
-        const int p = (m < n) ? (int)pass[m] : 0;
-        int total;
-        const int pos = base + block_scan_1024(p, &total);
-        if (acc) {
-            if (m < n && !p) acc[alive_in[m]] = 0;
-        } else if (p) {
-            alive_out[pos] = alive_in[m];
+    for (int m0 = 0; m0 < n; m0 += kScanChunks * kScanThreads) {
+        int pv[kScanChunks], tv[kScanChunks];
+#pragma unroll
+        for (int k = 0; k < kScanChunks; ++k) {
+            const int m = m0 + k * kScanThreads + threadIdx.x;
+            pv[k] = m < n ? (int)pass[m] : 0;
+            tv[k] = m < n ? alive_in[m] : 0;
         }
-        base += total;
+#pragma unroll
+        for (int k = 0; k < kScanChunks; ++k) {
+            const int m = m0 + k * kScanThreads + threadIdx.x;
+            const int p = pv[k];
+            int total;
+            const int pos = base + block_scan_flags_1024(p, &total);
+            if (acc) {
+                if (m < n && !p) acc[tv[k]] = 0;
+            } else if (p) {
+                alive_out[pos] = tv[k];
+            }
+            base += total;
+        }
     }
     if (threadIdx.x == 0) {
         if (!acc) *count_out = base;
@@ -171,7 +167,7 @@ k_acc_to_alive(const unsigned char *acc, int n, int *alive_out, int *count_out) 
         const int m = m0 + threadIdx.x;
         const int p = (m < n) ? (int)acc[m] : 0;
         int total;
-        const int pos = base + block_scan_1024(p, &total);
+        const int pos = base + block_scan_flags_1024(p, &total);
         if (p) alive_out[pos] = m;
         base += total;
     }

@@ -93,6 +93,16 @@ static __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sb
     return d;
 }
 
+// The descriptor of the operand `byte_off` bytes after the one `d` describes
+// (byte_off a multiple of 16, possibly negative).  The start address sits in
+// bits 0..13 as (address & 0x3FFFF) >> 4; every shared-memory address of a CTA
+// is below 2^18, so the shifted sum stays inside those 14 bits and the add
+// reaches no other field.  This keeps the MMA issue loops to one add per
+// operand instead of rebuilding the descriptor.
+static __device__ __forceinline__ uint64_t desc_add(uint64_t d, int byte_off) {
+    return d + (uint64_t)(int64_t)(byte_off >> 4);
+}
+
 // Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 static __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {

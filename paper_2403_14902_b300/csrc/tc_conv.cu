@@ -58,7 +58,9 @@ struct TcCfg {
     static constexpr uint32_t SBO = 8 * ROWB;              // 8-row group stride
     static constexpr int TMEM_COLS = 2 * MT * N;          // double-buffered accumulators
     static constexpr int PASSES = SPLIT ? 3 : 1;
-    static constexpr int SMEM = RES_BYTES + S * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr int EPI_STG = MODE == 0 ? 4 * 32 * 64 : 0;   // BF16 stores: 32 pixels x 64 B a warp
+    static constexpr int SMEM = RES_BYTES + S * STAGE + 1024 /*align*/ + 256 /*barriers*/ + EPI_STG;
+    static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
 
 template <int CC, int N, int S, int MODE, int MT, bool RES = false>
@@ -78,6 +80,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     uint64_t *wbar = tempty + 2;   // resident weights loaded
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wbar + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint4 *stg_all = reinterpret_cast<uint4 *>(smem + S * C::STAGE + 256);   // C::EPI_STG bytes
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int total = (*count) * tiles_per_frame;
@@ -182,6 +185,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     const uint32_t sa = smem_u32(smem + s * C::STAGE);
                     // resident weights: step k of the single chunk is tap column kx = k
                     const uint32_t sb = RES ? smem_u32(wres) + (uint32_t)(k * C::B_BYTES) : sa + C::A_BYTES;
+                    const uint64_t a0 = smem_desc(sa, C::SBO, C::SWZ), b0 = smem_desc(sb, C::SBO, C::SWZ);
 #pragma unroll
                     for (int sub = 0; sub < MT; ++sub) {
                         // subtile sub covers output rows y0 + 2*sub, +1: A rows start at 64*(2*sub + ky)
@@ -190,9 +194,8 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                         for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
                             for (int kk = 0; kk < C::ROWB / 32; ++kk) {
-                                const uint64_t ad =
-                                    smem_desc(sa + (2 * sub + ky) * 64 * C::ROWB + kk * 32, C::SBO, C::SWZ);
-                                const uint64_t bd = smem_desc(sb + ky * C::B_TAP + kk * 32, C::SBO, C::SWZ);
+                                const uint64_t ad = desc_add(a0, (2 * sub + ky) * 64 * C::ROWB + kk * 32);
+                                const uint64_t bd = desc_add(b0, ky * C::B_TAP + kk * 32);
                                 if constexpr (MODE == 1)
                                     mma_tf32(dt, ad, bd, idesc, (k | ky | kk) != 0);
                                 else
@@ -295,7 +298,11 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                         }
                     }
                 } else {
-                    __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out) + ((size_t)m * HW + p0 + row) * N;
+                    // through the warp's staging rows (chunk j of pixel p at slot j ^ ((p >> 1) & 3)):
+                    // each store instruction then writes the 64-byte channel group of 8 pixels whole
+                    __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out) + ((size_t)m * HW + p0 + qtr * 32) * N;
+                    uint4 *stg = stg_all + (warp - 2) * (32 * 64 / 16);
+                    const int sw = (lane >> 1) & 3;
 #pragma unroll
                     for (int c0 = 0; c0 < N; c0 += 32) {
                         uint32_t r[32];
@@ -310,10 +317,16 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                             v1 = v1 > 0.f ? v1 : 0.f;
                             pk[j] = pack_bf16x2(v0, v1);
                         }
-                        uint4 *dst = reinterpret_cast<uint4 *>(o + c0);
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
-                            dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                            stg[lane * 4 + (j ^ sw)] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                        __syncwarp();
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int pp = i * 8 + (lane >> 2), cq = lane & 3;
+                            reinterpret_cast<uint4 *>(o + (size_t)pp * N + c0)[cq] = stg[pp * 4 + (cq ^ ((pp >> 1) & 3))];
+                        }
+                        __syncwarp();
                     }
                 }
             }
@@ -360,6 +373,7 @@ constexpr int kWStage = (kWBox + 1023) / 1024 * 1024;
 // column half (w - 2) / 4, with its 32 biases (and head weights) in registers.
 constexpr int kWThreads = 320;
 constexpr int kWEpi = 8;
+constexpr int kWStg = 32 * 64;                 // an epilogue warp's store staging: 32 pixels x 64 B
 
 template <int CIN, int S>
 struct TcWCfg {
@@ -371,7 +385,8 @@ struct TcWCfg {
     static constexpr uint32_t SWZ_B = ROWB_B == 128 ? 2u : 4u;
     static constexpr int NCH = CIN / 32;                    // window boxes (stages) per tile
     static constexpr int TMEM_COLS = 512;                   // 2 x 3 x 64 used
-    static constexpr int SMEM = RES_BYTES + S * kWStage + 1024 + 256;
+    static constexpr int SMEM = RES_BYTES + S * kWStage + 1024 + 256 + kWEpi * kWStg;
+    static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
 
 // K-major SW64 descriptor of an A operand starting at any pixel row (64 B).
@@ -393,6 +408,7 @@ k_conv3x3_tcw(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     uint64_t *wbar = tempty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wbar + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint4 *stg_all = reinterpret_cast<uint4 *>(smem + S * kWStage + 256);   // kWEpi x kWStg bytes
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int total = (*count) * tiles_per_frame;
@@ -487,6 +503,10 @@ k_conv3x3_tcw(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     const uint32_t sa = smem_u32(smem + s * kWStage);
                     // weights of this 32-channel chunk: packing chunk cb, K offset kb inside its rows
                     const int cb = (c * 32) / C::CCB, kb = (c * 32) % C::CCB;
+                    // descriptors of the chunk's first A row (padded pixel pix0) and first weight row
+                    const uint64_t a0 = wdesc_a(sa + (uint32_t)(pix0 * 64));
+                    const uint64_t b0 = smem_desc(smem_u32(wres) + (uint32_t)(cb * 3 * C::B_BYTES + kb * 2),
+                                                  8 * C::ROWB_B, C::SWZ_B);
 #pragma unroll
                     for (int sub = 0; sub < kWMT; ++sub) {
                         const uint32_t dt = tmem_base + (uint32_t)((buf * kWMT + sub) * 64);
@@ -494,12 +514,11 @@ k_conv3x3_tcw(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
                             for (int kx = 0; kx < 3; ++kx) {
-                                const int pix = pix0 + 128 * sub + (ky - 1) * kWP + kx;
-                                const uint32_t sb = smem_u32(wres) + (uint32_t)((cb * 3 + kx) * C::B_BYTES + ky * C::B_TAP);
+                                const int dpix = 128 * sub + (ky - 1) * kWP + kx;
 #pragma unroll
                                 for (int kk = 0; kk < 2; ++kk) {
-                                    const uint64_t ad = wdesc_a(sa + (uint32_t)(pix * 64 + kk * 32));
-                                    const uint64_t bd = smem_desc(sb + (uint32_t)(kb * 2 + kk * 32), 8 * C::ROWB_B, C::SWZ_B);
+                                    const uint64_t ad = desc_add(a0, dpix * 64 + kk * 32);
+                                    const uint64_t bd = desc_add(b0, kx * C::B_BYTES + ky * C::B_TAP + kk * 32);
                                     mma_bf16(dt, ad, bd, idesc, (c | ky | kx | kk) != 0);
                                 }
                             }
@@ -516,9 +535,12 @@ k_conv3x3_tcw(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
     } else {
         // ---- epilogue: warps 2..9, TMEM lane quarter = warp % 4, column half (warp - 2) / 4;
-        // padded pixels are dropped
+        // padded pixels are dropped.  Stores go through the warp's staging rows (16-byte chunk j
+        // of pixel p at slot j ^ ((p >> 1) & 3), conflict-free both ways) so that each store
+        // instruction writes whole 64-byte pixel halves of 8 pixels: full 32-byte sectors.
         const int qtr = warp & 3, ch = (warp - 2) >> 2;
         const int row = qtr * 32 + lane;
+        uint4 *stg = stg_all + (warp - 2) * (kWStg / 16);
         float bv[32], hv[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -566,12 +588,23 @@ k_conv3x3_tcw(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         v1 = v1 > 0.f ? v1 : 0.f;
                         pk[j] = pack_bf16x2(v0, v1);
                     }
-                    if (valid) {
-                        uint4 *dst = reinterpret_cast<uint4 *>(out + ((size_t)m * H * 64 + (size_t)y * 64 + x) * 64 +
-                                                               ch * 32);
+                    const int sw = (lane >> 1) & 3;
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    for (int j = 0; j < 4; ++j)
+                        stg[lane * 4 + (j ^ sw)] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    __syncwarp();
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        // lanes 4k .. 4k+3 write the four chunks of pixel 8 i + k of the warp's 32
+                        const int pp = i * 8 + (lane >> 2), cq = lane & 3;
+                        const uint4 v = stg[pp * 4 + (cq ^ ((pp >> 1) & 3))];
+                        const int qp = q0 + 128 * sub + qtr * 32 + pp;
+                        const int yp = qp / kWP, xp = qp - (qp / kWP) * kWP;
+                        if (qp < Q && xp < 64)
+                            reinterpret_cast<uint4 *>(out + ((size_t)m * H * 64 + (size_t)yp * 64 + xp) * 64 +
+                                                      ch * 32)[cq] = v;
                     }
+                    __syncwarp();
                 }
             }
             tc_fence_before();
