@@ -55,10 +55,10 @@ def load_peaks():
 
 
 # DRAM traffic of the tensor-core BF16 conv, one 1,024-frame launch of each layer shape of the CNN
-# workload (ncu dram__bytes_read.sum + dram__bytes_write.sum, MB), against the launch's algorithmic
-# bytes (input + output activations, MB); profiles/conv3x3_tc_bf16__cnn4_layers.md gives the command.
-CONV_TC_TRAFFIC_MB = {"32->64": (751.0, 805.0), "64->64": (1019.0, 1074.0), "64->128": (1555.0, 1611.0),
-                      "128->128": (2095.0, 2148.0)}
+# workload (ncu dram__bytes_read.sum + dram__bytes_write.sum over `--workload conv_bf16`, MB),
+# against the launch's algorithmic bytes (input + output activations, MB).
+CONV_TC_TRAFFIC_MB = {"32->64": (750.1, 805.3), "64->64": (1025.3, 1073.7), "64->128": (1555.8, 1610.6),
+                      "128->128": (2103.3, 2147.5)}
 
 
 def conv_traffic_ratio():
