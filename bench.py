@@ -79,6 +79,49 @@ def stored_pass_matrix(name):
     return np.unpackbits(z["pm"], bitorder="little")[:n * P].reshape(n, P).astype(bool)
 
 
+def stored_scores(name):
+    """The oracle's FP64 scores of the whole frame stream rounded to fp32 ([n, P]), or None."""
+    p = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.npz")
+    if not os.path.exists(p):
+        return None
+    z = np.load(p)
+    return z["scores_f32"].astype(np.float64) if "scores_f32" in z.files else None
+
+
+def bf16_stream_error(H, w, th, X, stream, calib_rows):
+    """Per predicate, the largest |BF16 score - oracle score| over the whole stream (the stored
+    FP64 oracle scores) against the largest error on the calibration frames, and the fraction of
+    the evaluated frames inside the recheck band at the query's margin.  The band is correct
+    only while the stream's error stays under the margin, which this measures."""
+    import torch
+    ref = stored_scores(w.name)
+    if ref is None:
+        return None
+    q = build_query(H, w, th, policy="all", precision="bf16", stream=stream, max_in_flight=1, lanes=1, lag=0)
+    calib = q.calibrate(calib_rows)
+    out = torch.empty(w.batch, dtype=torch.float64, device="cuda")
+    res = {"stream_max_err": [], "calib_max_err": [], "ratio": [], "margin": [], "band_frac": [],
+           "band_frac_at_4x_calib": [], "calib_frames": int(calib_rows.shape[0])}
+    for i in range(len(w.udfs)):
+        s = np.empty(w.n)
+        with torch.cuda.stream(stream):
+            for b0 in range(0, w.n, w.batch):
+                n = min(w.batch, w.n - b0)
+                q.udf_scores(i, "bf16", X[b0:b0 + n], out[:n])
+                s[b0:b0 + n] = out[:n].cpu().numpy()
+        err = float(np.abs(s - ref[:, i]).max())
+        ce = float(calib[i]["max_err_lowp"])
+        d = np.abs(ref[:, i] - th[i])
+        res["stream_max_err"].append(round(err, 6))
+        res["calib_max_err"].append(round(ce, 6))
+        res["ratio"].append(round(err / max(ce, 1e-30), 3))
+        res["margin"].append(round(float(calib[i]["margin_lowp"]), 6))
+        res["band_frac"].append(round(float((d <= calib[i]["margin_lowp"]).mean()), 5))
+        res["band_frac_at_4x_calib"].append(round(float((d <= 4.0 * ce).mean()), 5))
+    q.close()
+    return res
+
+
 def order_counts(pm, order):
     """Evaluations per predicate when the tuples of ``pm`` go through ``order``
     with failing tuples dropped at once (eager materialization)."""
@@ -908,6 +951,7 @@ def ours(args):
     q1.profile(False)
     q1.close()
     folds["adaptive_bf16_one_lane"] = verify("adaptive_bf16_one_lane", o1)
+    bf16_err = bf16_stream_error(H, w, th, X, stream, calib_d)
 
     def arm(name, policy, precision, order=None, steps=2, lanes=args.lanes):
         qa = build_query(H, w, th, policy=policy, precision=precision, stream=stream, max_in_flight=mif,
@@ -1011,6 +1055,7 @@ def ours(args):
                     "calib_max_err_bf16": [round(c["max_err_lowp"], 6) for c in calib],
                     "calib_max_err_split_level": [float("%.3g" % c["max_err_tf32"]) for c in calib],
                     "calib_max_err_fp32": [float("%.3g" % c["max_err_fp32"]) for c in calib]},
+        "bf16_error_stream": bf16_err,
     }
     return out
 
