@@ -52,7 +52,9 @@ def test_measured_cost_routing(cnn4, policy, precision, lanes):
         assert counts.tolist() == want, f"batch {b}: counts {counts} vs {want}"
         assert all(t > 0 for t in info["stage_ns"])
         if b == 0:
-            assert info["warmup"] and info["stage_ns"][3] > info["stage_ns"][0]
+            # the first batch's stage times may include the first launch of a recheck level's
+            # kernels; the routed batches below show the measured cost ordering
+            assert info["warmup"]
         else:
             assert info["order"][-1] == 3, f"batch {b}: order {info['order']}"
     q.close()
