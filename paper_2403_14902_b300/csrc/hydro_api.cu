@@ -988,9 +988,9 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
     void *score = prec == PREC_F64 ? (void *)score64 : (void *)score32;
     const int CL = p.dims[p.n_layers];
     e = prof_begin(q, pc, PC_POOL, 2.0 * hw * CL, hw * esz * CL, 4.0 * CL);
-    launch_pool_head(prec, count, act[cur], H * Wd, CL, p.dHead, p.head_b, score, max_rows, q->sms, st);
+    const int nk = launch_pool_head(prec, count, act[cur], H * Wd, CL, p.dHead, p.head_b, score, max_rows, q->sms, st);
     prof_end(q, e);
-    q->launches++;
+    q->launches += nk;
     return HYDRO_OK;
 }
 

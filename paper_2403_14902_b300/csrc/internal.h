@@ -115,8 +115,10 @@ void launch_conv1_split(const int *count, const int *list, const unsigned char *
 void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,
                          const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st,
                          bool band = false);
-void launch_pool_head(int prec, const int *count, const void *act, int HW, int C, const float *hw, double hb,
-                      void *score, int max_frames, int sms, cudaStream_t st);
+// Returns the number of kernels launched.  The FP32 / FP64 forms overwrite the frame's first
+// pixel of `act` with its channel sums.
+int launch_pool_head(int prec, const int *count, void *act, int HW, int C, const float *hw, double hb,
+                     void *score, int max_frames, int sms, cudaStream_t st);
 
 // k_learned.cu: per-tuple routing by a learned proxy, grouped per-predicate queues
 struct GroupLayer {

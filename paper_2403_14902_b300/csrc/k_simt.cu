@@ -298,7 +298,8 @@ template <> __device__ __forceinline__ __nv_bfloat16 st_as<__nv_bfloat16, float>
 //   out[m][p][co] = relu(b[co] + sum_{tap, ci} in[m][p + shift(tap)][ci] * Wt[tap][ci][co])
 // Tiles of PX (128 or 64) pixels x 64 output channels; K walks (tap, 16 input
 // channels), so a tile's latency is its K loop: recheck bands of a few frames
-// take 64-pixel tiles (half the work per step, twice the CTAs).
+// take 64-pixel tiles (half the work per step, twice the CTAs; 32-pixel tiles
+// measured no faster on the CNN workload's FP32 bands).
 // Requires Cin % 16 == 0, Cout % 64 == 0, H*W % 128 == 0.
 template <int PX, typename Tin, typename Tw, typename T, typename Tout>
 __global__ void __launch_bounds__(256)
@@ -377,6 +378,49 @@ k_conv3x3_simt(const int *count, const Tin *in, int Cin, int H, int Wd, const Tw
 // Global average pool + linear head: score[m] = hb + sum_c hw[c] * mean_p act[m][p][c].
 // One block per frame; fixed-order partial sums (deterministic).
 constexpr int kPoolThreads = 1024;   // per frame: C channels x (1024 / C) pixel groups
+
+// The FP32 / FP64 recheck levels pool a band of a few frames: one block per frame reads its
+// 1-2 MB with too few loads in flight, so these levels split each frame by 32-channel group.
+// k_pool_sum: per (frame, channel group), 32 channels x 32 pixel groups sum in a fixed order
+// and leave the channel sums in place of the frame's first pixel (only this block reads those
+// channels of the frame); k_head_dot: one warp per frame, hb + sum_c hw[c] * sum_c / HW with a
+// fixed butterfly order.  Both deterministic; C a multiple of 32.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_pool_sum(const int *count, T *act, int HW, int C) {
+    __shared__ T part[32][33];
+    const int M = *count, G = C / 32;
+    const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
+    for (long long u = blockIdx.x; u < (long long)M * G; u += gridDim.x) {
+        const int m = (int)(u / G), cg = (int)(u % G);
+        T *a = act + (size_t)m * HW * C + cg * 32 + c;
+        T s = (T)0;
+#pragma unroll 8
+        for (int p = g; p < HW; p += 32) s += a[(size_t)p * C];
+        part[g][c] = s;
+        __syncthreads();
+        if (g == 0) {
+            T tot = (T)0;
+            for (int q = 0; q < 32; ++q) tot += part[q][c];
+            a[0] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, typename S>
+__global__ void k_head_dot(const int *count, const T *act, int HW, int C, const float *hw, double hb, S *score) {
+    const int M = *count;
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; m < M; m += warps) {
+        const T *pooled = act + (size_t)m * HW * C;
+        T r = (T)0;
+        for (int c = lane; c < C; c += 32) r += (T)hw[c] * (pooled[c] / (T)HW);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) r += __shfl_xor_sync(0xffffffffu, r, d);
+        if (lane == 0) score[m] = (S)((T)hb + r);
+    }
+}
 
 template <typename Tin, typename T, typename S>
 __global__ void __launch_bounds__(kPoolThreads)
@@ -541,10 +585,25 @@ void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, in
     }
 }
 
-void launch_pool_head(int prec, const int *count, const void *act, int HW, int C, const float *hw, double hb,
-                      void *score, int max_frames, int sms, cudaStream_t st) {
+int launch_pool_head(int prec, const int *count, void *act, int HW, int C, const float *hw, double hb,
+                     void *score, int max_frames, int sms, cudaStream_t st) {
     int grid = max_frames < grid_for(sms, 2) ? max_frames : grid_for(sms, 2);
     if (grid < 1) grid = 1;
+    if ((prec == PREC_F64 || prec == PREC_F32) && C % 32 == 0) {
+        const long long units = (long long)max_frames * (C / 32);
+        const int g1 = (int)(units < grid_for(sms, 2) ? (units < 1 ? 1 : units) : grid_for(sms, 2));
+        int g2 = (max_frames + 7) / 8;
+        if (g2 > grid_for(sms, 4)) g2 = grid_for(sms, 4);
+        if (g2 < 1) g2 = 1;
+        if (prec == PREC_F64) {
+            k_pool_sum<double><<<g1, 1024, 0, st>>>(count, (double *)act, HW, C);
+            k_head_dot<double, double><<<g2, 256, 0, st>>>(count, (const double *)act, HW, C, hw, hb, (double *)score);
+        } else {
+            k_pool_sum<float><<<g1, 1024, 0, st>>>(count, (float *)act, HW, C);
+            k_head_dot<float, float><<<g2, 256, 0, st>>>(count, (const float *)act, HW, C, hw, hb, (float *)score);
+        }
+        return 2;
+    }
     if (prec == PREC_F64)
         k_pool_head<double, double, double><<<grid, kPoolThreads, 0, st>>>(count, (const double *)act, HW, C, hw, hb,
                                                                            (double *)score);
@@ -554,6 +613,7 @@ void launch_pool_head(int prec, const int *count, const void *act, int HW, int C
     else
         k_pool_head<__nv_bfloat16, float, float><<<grid, kPoolThreads, 0, st>>>(count, (const __nv_bfloat16 *)act,
                                                                                 HW, C, hw, hb, (float *)score);
+    return 1;
 }
 
 }  // namespace hydro
