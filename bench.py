@@ -4,8 +4,10 @@ Workload: the 65,536-frame stream (3x64x64 uint8, seeded Gaussian-like blobs
 on noise), four random-init CNN UDF predicates (2/4/6/8 conv3x3 layers of
 32-128 channels + global average pool + linear head) with target
 selectivities 0.3/0.6/0.1/0.9, routing batches of 2,048, rank c/(1-s)
-routing, BF16 tensor-core inference with FP32 accumulation and an FP32/FP64
-recheck of every score within 0.02 of its threshold.
+routing, BF16 tensor-core inference with FP32 accumulation and an exact
+recheck cascade (split BF16 on the tensor cores, FP32, FP64) of every score
+closer to its threshold than 4x the largest BF16 error on 256 calibration
+frames (8x / 16x the next levels' errors).
 
 One step = the whole stream through the query (32 batches submitted and
 polled).  Inputs (805 MB) exceed L2 (126 MB), so no flush is needed between
@@ -343,15 +345,20 @@ class ClockSampler:
 # ---------------------------------------------------------------- our arm
 
 def build_query(H, w, th, *, policy, precision, stream, max_in_flight=8, lanes=2, lag=1, split="bf16x3",
-                recheck_graphs=True):
+                recheck_graphs=True, calib_margins=True):
     """Stream lanes: up to `lanes` consecutive batches run at once (route lag >= lanes - 1);
     `split`: the first recheck level of the BF16 CNN UDFs; `recheck_graphs` False: every
-    recheck level launched directly (no conditional graph nodes, so ncu sees each kernel)."""
+    recheck level launched directly (no conditional graph nodes, so ncu sees each kernel).
+    `calib_margins`: no fixed floor under the recheck margins, so calibration sets each band to
+    4x (BF16), 8x (split level) and 16x (FP32) the largest error of that level on the
+    calibration frames (the query must be calibrated before its first batch)."""
     q = H.Query(w.kind, frame=w.frame, max_batch=w.batch, policy=policy, precision=precision,
                 max_in_flight=max_in_flight, stream=stream, lanes=lanes, lag=lag, split=split,
                 recheck_graphs=recheck_graphs)
     for i, udf in enumerate(D.predicate_weights(w)):
         q.add_cnn(udf, th[i])
+        if calib_margins:
+            q.set_margins(i, 0.0, 0.0, 0.0)
     return q
 
 
@@ -888,7 +895,7 @@ def ours(args):
     X = Xh.cuda()
     stream = torch.cuda.Stream()
     mif = 8
-    calib_d = torch.from_numpy(D.calib_tuples(w)[:64]).cuda()
+    calib_d = torch.from_numpy(D.calib_tuples(w)).cuda()   # 256 frames
     parity = {}
 
     def verify(name, outs):
@@ -1017,7 +1024,8 @@ def ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: {w.n} frames 3x64x64 uint8, 4 CNN UDF predicates (2/4/6/8 conv3x3 "
                                f"layers, 32-128 ch), selectivities 0.3/0.6/0.1/0.9, batches of {w.batch}, rank "
-                               "c/(1-s) routing, BF16 tensor cores + FP32/FP64 recheck within 0.02",
+                               "c/(1-s) routing, BF16 tensor cores + split-BF16/FP32/FP64 recheck of scores "
+                               "within 4x the largest BF16 error on 256 calibration frames",
                    "global_batch": w.n, "routing_batch": w.batch, "parallelism": f"replicas{ws}",
                    "lanes": args.lanes, "route_lag": args.lag,
                    "l2": "inputs 805 MB > 126 MB L2, no flush"},
