@@ -6,8 +6,8 @@ on noise), four random-init CNN UDF predicates (2/4/6/8 conv3x3 layers of
 selectivities 0.3/0.6/0.1/0.9, routing batches of 2,048, rank c/(1-s)
 routing, BF16 tensor-core inference with FP32 accumulation and an exact
 recheck cascade (split BF16 on the tensor cores, FP32, FP64) of every score
-closer to its threshold than 4x the largest BF16 error on 256 calibration
-frames (8x / 16x the next levels' errors).
+within 0.02 of its threshold (the next levels' bands 8x / 16x their errors on
+the calibration frames).
 
 One step = the whole stream through the query (32 batches submitted and
 polled).  Inputs (805 MB) exceed L2 (126 MB), so no flush is needed between
@@ -345,13 +345,14 @@ class ClockSampler:
 # ---------------------------------------------------------------- our arm
 
 def build_query(H, w, th, *, policy, precision, stream, max_in_flight=8, lanes=2, lag=1, split="bf16x3",
-                recheck_graphs=True, calib_margins=True):
+                recheck_graphs=True, calib_margins=False):
     """Stream lanes: up to `lanes` consecutive batches run at once (route lag >= lanes - 1);
     `split`: the first recheck level of the BF16 CNN UDFs; `recheck_graphs` False: every
     recheck level launched directly (no conditional graph nodes, so ncu sees each kernel).
-    `calib_margins`: no fixed floor under the recheck margins, so calibration sets each band to
-    4x (BF16), 8x (split level) and 16x (FP32) the largest error of that level on the
-    calibration frames (the query must be calibrated before its first batch)."""
+    `calib_margins`: no 0.02 floor under the BF16 margin (the workload's stated one), so
+    calibration sets each band to 4x (BF16), 8x (split level) and 16x (FP32) the largest error
+    of that level on the calibration frames (the query must be calibrated before its first
+    batch).  Without it the BF16 band is 0.02, raised only if 4x the calibration error is larger."""
     q = H.Query(w.kind, frame=w.frame, max_batch=w.batch, policy=policy, precision=precision,
                 max_in_flight=max_in_flight, stream=stream, lanes=lanes, lag=lag, split=split,
                 recheck_graphs=recheck_graphs)
@@ -895,7 +896,8 @@ def ours(args):
     X = Xh.cuda()
     stream = torch.cuda.Stream()
     mif = 8
-    calib_d = torch.from_numpy(D.calib_tuples(w)).cuda()   # 256 frames
+    calib_all = torch.from_numpy(D.calib_tuples(w)).cuda()   # 256 frames
+    calib_d = calib_all[:64]
     parity = {}
 
     def verify(name, outs):
@@ -958,14 +960,14 @@ def ours(args):
     q1.profile(False)
     q1.close()
     folds["adaptive_bf16_one_lane"] = verify("adaptive_bf16_one_lane", o1)
-    bf16_err = bf16_stream_error(H, w, th, X, stream, calib_d)
+    bf16_err = bf16_stream_error(H, w, th, X, stream, calib_all)
 
-    def arm(name, policy, precision, order=None, steps=2, lanes=args.lanes):
+    def arm(name, policy, precision, order=None, steps=2, lanes=args.lanes, calib_margins=False):
         qa = build_query(H, w, th, policy=policy, precision=precision, stream=stream, max_in_flight=mif,
-                         lanes=lanes, lag=args.lag, split=args.split)
+                         lanes=lanes, lag=args.lag, split=args.split, calib_margins=calib_margins)
         if order is not None:
             qa.set_static_order(order)
-        qa.calibrate(calib_d if precision != "fp32" else calib_d[:16])
+        qa.calibrate(calib_all if calib_margins else calib_d if precision != "fp32" else calib_d[:16])
         f = lambda: run_step(qa, X, w.batch, mif)  # noqa: E731
         f()
         sa, oa = timed(f, steps, stream, local)
@@ -989,6 +991,10 @@ def ours(args):
     arms["adaptive_split_bf16"] = arm("adaptive_split_bf16", "rank", "bf16x3")
     arms["static_fp32_cuda_cores_declared_order"] = arm("static_fp32_cuda_cores_declared_order", "static", "fp32",
                                                         declared, steps=1)
+    # the same adaptive BF16 query with its recheck bands from calibration alone (4x the largest
+    # BF16 error on 256 frames) instead of the stated 0.02
+    arms["adaptive_bf16_calibrated_margins"] = arm("adaptive_bf16_calibrated_margins", "rank", "bf16", steps=3,
+                                                   calib_margins=True)
     same_bits = len({v for v in folds.values() if v is not None}) <= 1
 
     if rank != 0:
@@ -1025,7 +1031,7 @@ def ours(args):
         "config": {"workload": f"{WORKLOAD}: {w.n} frames 3x64x64 uint8, 4 CNN UDF predicates (2/4/6/8 conv3x3 "
                                f"layers, 32-128 ch), selectivities 0.3/0.6/0.1/0.9, batches of {w.batch}, rank "
                                "c/(1-s) routing, BF16 tensor cores + split-BF16/FP32/FP64 recheck of scores "
-                               "within 4x the largest BF16 error on 256 calibration frames",
+                               "within 0.02 of the threshold",
                    "global_batch": w.n, "routing_batch": w.batch, "parallelism": f"replicas{ws}",
                    "lanes": args.lanes, "route_lag": args.lag,
                    "l2": "inputs 805 MB > 126 MB L2, no flush"},
@@ -1046,6 +1052,8 @@ def ours(args):
             "routing_vs_static_declared_bf16": round(value / sb, 3),
             "routing_vs_best_static_bf16": round(value / best_v, 3) if best_v else None,
             "routing_vs_all_evaluate_bf16": round(value / arms["all_evaluate_bf16"]["value"], 3),
+            "calibrated_margins_vs_stated_margin_bf16": round(arms["adaptive_bf16_calibrated_margins"]["value"] /
+                                                              value, 3),
             "routing_vs_static_declared_split_bf16": round(arms["adaptive_split_bf16"]["value"] /
                                                           arms["static_split_bf16_declared_order"]["value"], 3),
             "precision_bf16_vs_split_bf16_static": round(sb / arms["static_split_bf16_declared_order"]["value"], 3),
