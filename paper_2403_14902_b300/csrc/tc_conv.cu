@@ -58,7 +58,7 @@ struct TcCfg {
     static constexpr uint32_t SBO = 8 * ROWB;              // 8-row group stride
     static constexpr int TMEM_COLS = 2 * MT * N;          // double-buffered accumulators
     static constexpr int PASSES = SPLIT ? 3 : 1;
-    static constexpr int EPI_STG = MODE == 0 ? 4 * 32 * 64 : 0;   // BF16 stores: 32 pixels x 64 B a warp
+    static constexpr int EPI_STG = MODE == 0 ? 4 * 32 * N * 2 : 0;   // BF16 stores: 32 pixel rows a warp
     static constexpr int SMEM = RES_BYTES + S * STAGE + 1024 /*align*/ + 256 /*barriers*/ + EPI_STG;
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
@@ -298,11 +298,15 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                         }
                     }
                 } else {
-                    // through the warp's staging rows (chunk j of pixel p at slot j ^ ((p >> 1) & 3)):
-                    // each store instruction then writes the 64-byte channel group of 8 pixels whole
+                    // through the warp's staging rows, one per pixel (16-byte chunk j of pixel p at slot
+                    // j ^ (p % Q), conflict-free both ways).  Layers with several input chunks (long MMA
+                    // phases) store whole pixel rows once all channel groups are staged: 32 / Q complete
+                    // rows per instruction, full 128-byte lines.  One-chunk layers, whose epilogue is
+                    // closer to the MMA time, store each 64-byte channel group as soon as it is staged.
+                    constexpr int Q = N / 8;   // 16-byte chunks per pixel row
                     __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out) + ((size_t)m * HW + p0 + qtr * 32) * N;
-                    uint4 *stg = stg_all + (warp - 2) * (32 * 64 / 16);
-                    const int sw = (lane >> 1) & 3;
+                    uint4 *stg = stg_all + (warp - 2) * (32 * Q);
+                    const bool rows = nchunks > 1;
 #pragma unroll
                     for (int c0 = 0; c0 < N; c0 += 32) {
                         uint32_t r[32];
@@ -319,12 +323,25 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                         }
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
-                            stg[lane * 4 + (j ^ sw)] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                            stg[lane * Q + ((c0 / 8 + j) ^ (lane % Q))] =
+                                make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                        if (!rows) {
+                            __syncwarp();
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                // lanes 4k .. 4k+3 write the four chunks of this group of pixel 8 i + k
+                                const int pp = i * 8 + (lane >> 2), cq = c0 / 8 + (lane & 3);
+                                reinterpret_cast<uint4 *>(o + (size_t)pp * N)[cq] = stg[pp * Q + (cq ^ (pp % Q))];
+                            }
+                            __syncwarp();
+                        }
+                    }
+                    if (rows) {
                         __syncwarp();
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int pp = i * 8 + (lane >> 2), cq = lane & 3;
-                            reinterpret_cast<uint4 *>(o + (size_t)pp * N + c0)[cq] = stg[pp * 4 + (cq ^ ((pp >> 1) & 3))];
+                        for (int i = 0; i < Q; ++i) {
+                            const int pp = i * (32 / Q) + lane / Q, cq = lane % Q;
+                            reinterpret_cast<uint4 *>(o + (size_t)pp * N)[cq] = stg[pp * Q + (cq ^ (pp % Q))];
                         }
                         __syncwarp();
                     }
