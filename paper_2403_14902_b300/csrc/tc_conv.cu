@@ -58,7 +58,8 @@ struct TcCfg {
     static constexpr uint32_t SBO = 8 * ROWB;              // 8-row group stride
     static constexpr int TMEM_COLS = 2 * MT * N;          // double-buffered accumulators
     static constexpr int PASSES = SPLIT ? 3 : 1;
-    static constexpr int EPI_STG = MODE == 0 ? 4 * 32 * N * 2 : 0;   // BF16 stores: 32 pixel rows a warp
+    // staging of the stores: BF16 32 pixel rows a warp; split BF16 32 pixels x 128 B (one channel group)
+    static constexpr int EPI_STG = MODE == 0 ? 4 * 32 * N * 2 : MODE == 2 ? 4 * 32 * 128 : 0;
     static constexpr int SMEM = RES_BYTES + S * STAGE + 1024 /*align*/ + 256 /*barriers*/ + EPI_STG;
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
@@ -251,8 +252,12 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     for (int d = 16; d > 0; d >>= 1) hsum += __shfl_xor_sync(0xffffffffu, hsum, d);
                     if (lane == 0) partials[((size_t)t * MT + sub) * 4 + qtr] = hsum;
                 } else if constexpr (MODE == 2) {
-                    // split-BF16 output as two planes per pixel: [hi(N) | lo(N)]
-                    __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out) + ((size_t)m * HW + p0 + row) * (2 * N);
+                    // split-BF16 output as two planes per pixel: [hi(N) | lo(N)].  Each 32-channel group's
+                    // hi and lo halves go through the warp's staging rows (128 B a pixel, 16-byte chunk j
+                    // at slot j ^ (p % 8)) so that a store instruction writes both 64-byte halves of 4
+                    // pixels whole
+                    __nv_bfloat16 *o = static_cast<__nv_bfloat16 *>(out) + ((size_t)m * HW + p0 + qtr * 32) * (2 * N);
+                    uint4 *stg = stg_all + (warp - 2) * (32 * 8);
 #pragma unroll
                     for (int c0 = 0; c0 < N; c0 += 32) {
                         uint32_t r[32];
@@ -268,12 +273,21 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                             hi[j] = pack_bf16x2(v0, v1);
                             lo[j] = pack_bf16x2(v0 - __uint_as_float(hi[j] << 16), v1 - __uint_as_float(hi[j] & 0xFFFF0000u));
                         }
-                        uint4 *dh = reinterpret_cast<uint4 *>(o + c0), *dl = reinterpret_cast<uint4 *>(o + N + c0);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            dh[j] = make_uint4(hi[4 * j], hi[4 * j + 1], hi[4 * j + 2], hi[4 * j + 3]);
-                            dl[j] = make_uint4(lo[4 * j], lo[4 * j + 1], lo[4 * j + 2], lo[4 * j + 3]);
+                            stg[lane * 8 + (j ^ (lane & 7))] = make_uint4(hi[4 * j], hi[4 * j + 1], hi[4 * j + 2], hi[4 * j + 3]);
+                            stg[lane * 8 + ((4 + j) ^ (lane & 7))] =
+                                make_uint4(lo[4 * j], lo[4 * j + 1], lo[4 * j + 2], lo[4 * j + 3]);
                         }
+                        __syncwarp();
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            // lanes 8k .. 8k+7: the hi (chunks 0..3) and lo (4..7) halves of pixel 4 i + k
+                            const int pp = i * 4 + (lane >> 3), cq = lane & 7;
+                            const int dst = cq < 4 ? c0 + cq * 8 : N + c0 + (cq - 4) * 8;
+                            *reinterpret_cast<uint4 *>(o + (size_t)pp * (2 * N) + dst) = stg[pp * 8 + (cq ^ (pp & 7))];
+                        }
+                        __syncwarp();
                     }
                 } else if constexpr (MODE == 1) {
                     // fp32 output as two planes per pixel: [hi(N) | lo(N)]
