@@ -1218,7 +1218,7 @@ def ours_mq64(args):
                 ("static_fp32_graphs_k4", "fp32", True, 4)]
     if args.headline_only:
         # profilers cannot see kernels inside graphs with conditional nodes: launch kernel by kernel
-        variants = [(HEAD, "bf16", not args.no_graphs, HK)]
+        variants = [(HEAD, args.mq_precision, not args.no_graphs, HK)]
     head_sched = None
     for name, precision, graphs, K in variants:
         s = make(precision, graphs, K, "static" if name.startswith("static") else "rank",
@@ -2058,6 +2058,8 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=0, help="cnn4: routing batch size (0: the workload's 2,048)")
     ap.add_argument("--profile-launches", action="store_true",
                     help="cnn4 --headline-only: per-launch events (host-routed batches, for a launch list)")
+    ap.add_argument("--mq-precision", choices=["bf16", "fp8"], default="bf16",
+                    help="mq64 --headline-only: precision of the timed session (fp8: the FP8 groups, for profiling)")
     ap.add_argument("--tile-sched", choices=["static", "data_aware"], default=None,
                     help="mq64: tile scheduler of the headline session's grouped launches (default: the library's)")
     ap.add_argument("--split", choices=["tf32x3", "bf16x3"], default="bf16x3",
