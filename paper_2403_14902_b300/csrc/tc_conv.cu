@@ -40,10 +40,7 @@ thread_local std::string g_tc_err;
 // MODE: 0 BF16; 1 3xTF32 (fp32 [hi | lo] TF32 planes, kind::tf32); 2 split
 // BF16 ([hi | lo] BF16 planes, kind::f16).  Modes 1 and 2 run three passes
 // (A hi, B hi), (A hi, B lo), (A lo, B hi) into one accumulator.
-// RES: the layer's weights stay resident in shared memory (one input chunk,
-// BF16: the three horizontal taps' boxes are loaded once per CTA), and the
-// stages carry the activation boxes only.
-template <int CC, int N, int S, int MODE, int MT, bool RES = false>
+template <int CC, int N, int S, int MODE, int MT>
 struct TcCfg {
     static constexpr bool SPLIT = MODE != 0;
     static constexpr int ESZ = MODE == 1 ? 4 : 2;         // operand bytes
@@ -52,34 +49,30 @@ struct TcCfg {
     static constexpr int A_BYTES = A_ROWS * 64 * ROWB;
     static constexpr int B_TAP = N * ROWB;                // one tap's weights
     static constexpr int B_BYTES = 3 * B_TAP;
-    static constexpr int STAGE = A_BYTES + (RES ? 0 : B_BYTES);
-    static constexpr int RES_BYTES = RES ? 3 * B_BYTES : 0;   // resident weights: kx = 0, 1, 2
+    static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr uint32_t SWZ = ROWB == 128 ? 2u : 4u;  // 128B or 64B swizzle
     static constexpr uint32_t SBO = 8 * ROWB;              // 8-row group stride
     static constexpr int TMEM_COLS = 2 * MT * N;          // double-buffered accumulators
     static constexpr int PASSES = SPLIT ? 3 : 1;
     // staging of the stores: BF16 32 pixel rows a warp; split BF16 32 pixels x 128 B (one channel group)
     static constexpr int EPI_STG = MODE == 0 ? 4 * 32 * N * 2 : MODE == 2 ? 4 * 32 * 128 : 0;
-    static constexpr int SMEM = RES_BYTES + S * STAGE + 1024 /*align*/ + 256 /*barriers*/ + EPI_STG;
+    static constexpr int SMEM = S * STAGE + 1024 /*align*/ + 256 /*barriers*/ + EPI_STG;
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
 
-template <int CC, int N, int S, int MODE, int MT, bool RES = false>
+template <int CC, int N, int S, int MODE, int MT>
 __global__ void __launch_bounds__(192, 1)
 k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const int *count,
              int nchunks, int cin, int tiles_per_frame, int HW, const float *__restrict__ bias, void *out,
              const float *__restrict__ head_w, float *partials, unsigned int *err) {
-    using C = TcCfg<CC, N, S, MODE, MT, RES>;
-    static_assert(!RES || MODE == 0, "resident weights: BF16 layers with one input chunk");
+    using C = TcCfg<CC, N, S, MODE, MT>;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *wres = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char *smem = wres + C::RES_BYTES;   // stages
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * C::STAGE);
     uint64_t *empty = full + S;
     uint64_t *tfull = empty + S;
     uint64_t *tempty = tfull + 2;
-    uint64_t *wbar = tempty + 2;   // resident weights loaded
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wbar + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     uint4 *stg_all = reinterpret_cast<uint4 *>(smem + S * C::STAGE + 256);   // C::EPI_STG bytes
 
@@ -99,7 +92,6 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 4);
         }
-        mbar_init(wbar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -121,11 +113,6 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             uint32_t ph = 0;
             uint32_t issued = 0, last_par = 0;   // per stage bit: load in flight, its parity
             bool ok = true;
-            const bool wload = RES && blockIdx.x < total;
-            if (wload) {
-                mbar_expect_tx(wbar, (uint32_t)C::RES_BYTES);
-                for (int kx = 0; kx < 3; ++kx) tma_load_3d(wres + kx * C::B_BYTES, &tmB, wbar, 0, 0, kx * 3);
-            }
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 const int m = t / tiles_per_frame;
                 const int y0 = (t % tiles_per_frame) * 2 * MT;
@@ -141,8 +128,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                         unsigned char *sa = smem + s * C::STAGE;
                         mbar_expect_tx(&full[s], (uint32_t)C::STAGE);
                         tma_load_4d(sa, &tmA, &full[s], pa * cin + c * CC, kx - 1, y0 - 1, m);
-                        if constexpr (!RES)
-                            tma_load_3d(sa + C::A_BYTES, &tmB, &full[s], 0, 0, ((pb * nchunks + c) * 3 + kx) * 3);
+                        tma_load_3d(sa + C::A_BYTES, &tmB, &full[s], 0, 0, ((pb * nchunks + c) * 3 + kx) * 3);
                         issued |= 1u << s;
                         last_par = (last_par & ~(1u << s)) | (ph << s);
                         if (++s == S) {
@@ -157,7 +143,6 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                 volatile int never = 0;
                 for (int k = 0; k < S; ++k)
                     if (issued & (1u << k)) mbar_wait(&full[k], (last_par >> k) & 1u, &never, 100000000ull);
-                if (wload) mbar_wait(wbar, 0u, &never, 100000000ull);
             }
         }
     } else if (warp == 1) {
@@ -168,7 +153,6 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             uint32_t ph = 0;
             int tl = 0;
             bool ok = true;
-            if (RES && blockIdx.x < total && !mbar_wait(wbar, 0u, abort_flag)) ok = false;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
                 const int buf = tl & 1;
                 const uint32_t tph = (uint32_t)(tl >> 1) & 1u;
@@ -184,8 +168,7 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + s * C::STAGE);
-                    // resident weights: step k of the single chunk is tap column kx = k
-                    const uint32_t sb = RES ? smem_u32(wres) + (uint32_t)(k * C::B_BYTES) : sa + C::A_BYTES;
+                    const uint32_t sb = sa + C::A_BYTES;
                     const uint64_t a0 = smem_desc(sa, C::SBO, C::SWZ), b0 = smem_desc(sb, C::SBO, C::SWZ);
 #pragma unroll
                     for (int sub = 0; sub < MT; ++sub) {
@@ -691,10 +674,10 @@ using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, vo
                               const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-template <int CC, int N, int S, int MODE, int MT, bool RES = false>
+template <int CC, int N, int S, int MODE, int MT>
 cudaError_t set_smem() {
-    return cudaFuncSetAttribute(k_conv3x3_tc<CC, N, S, MODE, MT, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                TcCfg<CC, N, S, MODE, MT, RES>::SMEM);
+    return cudaFuncSetAttribute(k_conv3x3_tc<CC, N, S, MODE, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcCfg<CC, N, S, MODE, MT>::SMEM);
 }
 
 // 128-output layers: two 128-pixel subtiles per CTA tile (2 x 2 x 128 TMEM
@@ -703,7 +686,6 @@ cudaError_t set_smem() {
 constexpr int kMT = 2, kMT64 = 4;
 constexpr int kS_64_128 = 2, kS_64_64 = 2, kS_32_128 = 4, kS_32_64 = 4;
 constexpr int kS_t32_128 = 2, kS_t32_64 = 2;   // split TF32, CC = 32 fp32 channels
-constexpr int kS_32_64r = 4;                    // 32 -> 64 with resident weights (36 KB + 4 x 40 KB)
 
 }  // namespace
 
@@ -785,8 +767,6 @@ hydro_status tc_conv_init(TcConvPlan *plan, int device) {
     if (r == cudaSuccess) r = set_smem<64, 128, kS_64_128, 0, kMT>();
     if (r == cudaSuccess) r = set_smem<64, 64, kS_64_64, 0, kMT64>();
     if (r == cudaSuccess) r = set_smem<32, 128, kS_32_128, 0, kMT>();
-    if (r == cudaSuccess) r = set_smem<32, 64, kS_32_64, 0, kMT64>();
-    if (r == cudaSuccess) r = set_smem<32, 64, kS_32_64r, 0, kMT64, true>();
     if (r == cudaSuccess) r = set_smem<32, 128, kS_t32_128, 1, kMT>();
     if (r == cudaSuccess) r = set_smem<32, 64, kS_t32_64, 1, kMT64>();
     if (r == cudaSuccess) r = set_smem<64, 128, kS_64_128, 2, kMT>();
@@ -946,12 +926,8 @@ hydro_status tc_conv_run(TcConvPlan *plan, const int *count, const void *in, int
         if (cout == 128) HYDRO_TC_LAUNCH(64, 128, kS_64_128, 0, kMT);
         else HYDRO_TC_LAUNCH(64, 64, kS_64_64, 0, kMT64);
     } else {
-        if (cout == 128) HYDRO_TC_LAUNCH(32, 128, kS_32_128, 0, kMT);
-        else if (nch == 1)   // the weights of one 32-channel chunk stay in shared memory
-            k_conv3x3_tc<32, 64, kS_32_64r, 0, kMT64, true><<<grid, 192, TcCfg<32, 64, kS_32_64r, 0, kMT64, true>::SMEM,
-                                                              st>>>(tmA, tmB, count, nch, cin, tpf, HW, bias, out,
-                                                                    head_w, partials, err);
-        else HYDRO_TC_LAUNCH(32, 64, kS_32_64, 0, kMT64);
+        // Cin 32: the 64-output BF16 layer runs the window kernel (use_window)
+        HYDRO_TC_LAUNCH(32, 128, kS_32_128, 0, kMT);
     }
 #undef HYDRO_TC_LAUNCH
     cudaError_t e = cudaGetLastError();
