@@ -21,12 +21,15 @@ namespace hydro {
 // Y[m][n] = act(sum_k X[row(m)][k] * W[n][k] + b[n]) for m < *count, with
 // row(m) = rows[m] when rows != nullptr, and ids[rows[m]] when ids is given
 // too (rows of a cache indexed by tuple id).  64x64 output tiles, 16-deep K
-// slices, 4x4 outputs per thread.
+// slices, 4x4 outputs per thread.  The K slices are double-buffered in shared
+// memory and the next slice's global loads (16 bytes per row when vec4: K and
+// ldx multiples of 4) are in flight while the current one is multiplied; the
+// multiply-adds of every output run in k order, as with one buffer.
 __global__ void __launch_bounds__(256)
 k_mlp_layer_f32(const int *count, const int *rows, const float *X, int ldx, const float *W,
-                const float *b, float *Y, int K, int N, int relu, const long long *ids) {
-    __shared__ float As[16][64 + 4];
-    __shared__ float Ws[16][64 + 4];
+                const float *b, float *Y, int K, int N, int relu, const long long *ids, int vec4) {
+    __shared__ __align__(16) float As[2][16][64 + 4];
+    __shared__ __align__(16) float Ws[2][16][64 + 4];
     const int M = *count;
     const int tiles_m = (M + 63) / 64, tiles_n = (N + 63) / 64;
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
@@ -42,27 +45,55 @@ k_mlp_layer_f32(const int *count, const int *rows, const float *X, int ldx, cons
         }
         const int wn = n0 + lr;
         const float *wrow = wn < N ? W + (size_t)wn * K : nullptr;
-        for (int k0 = 0; k0 < K; k0 += 16) {
+        float ra[4], rw[4];
+        auto fetch = [&](int k0) {
+            const int k = k0 + lk;
+            if (vec4) {
+                // K % 4 == 0: the four k of this thread are all in range or all out
+                const float4 a4 = (arow && k < K) ? *reinterpret_cast<const float4 *>(arow + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 w4 = (wrow && k < K) ? *reinterpret_cast<const float4 *>(wrow + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                ra[0] = a4.x, ra[1] = a4.y, ra[2] = a4.z, ra[3] = a4.w;
+                rw[0] = w4.x, rw[1] = w4.y, rw[2] = w4.z, rw[3] = w4.w;
+            } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int k = k0 + lk + e;
-                As[lk + e][lr] = (arow && k < K) ? arow[k] : 0.f;
-                Ws[lk + e][lr] = (wrow && k < K) ? wrow[k] : 0.f;
+                for (int e = 0; e < 4; ++e) {
+                    ra[e] = (arow && k + e < K) ? arow[k + e] : 0.f;
+                    rw[e] = (wrow && k + e < K) ? wrow[k + e] : 0.f;
+                }
             }
-            __syncthreads();
+        };
+        fetch(0);
+        int buf = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            As[0][lk + e][lr] = ra[e];
+            Ws[0][lk + e][lr] = rw[e];
+        }
+        __syncthreads();
+        for (int k0 = 0; k0 < K; k0 += 16) {
+            const bool more = k0 + 16 < K;
+            if (more) fetch(k0 + 16);
 #pragma unroll
             for (int kk = 0; kk < 16; ++kk) {
                 float a[4], w[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+                for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty * 4 + i];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) w[j] = Ws[kk][tx * 4 + j];
+                for (int j = 0; j < 4; ++j) w[j] = Ws[buf][kk][tx * 4 + j];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
             }
+            if (more) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    As[buf ^ 1][lk + e][lr] = ra[e];
+                    Ws[buf ^ 1][lk + e][lr] = rw[e];
+                }
+            }
             __syncthreads();
+            buf ^= 1;
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -463,7 +494,9 @@ void launch_mlp_layer_f32(const int *count, const int *rows, const float *X, int
     const int tiles = ((max_rows + 63) / 64) * ((N + 63) / 64);
     int grid = tiles < grid_for(sms, 4) ? tiles : grid_for(sms, 4);
     if (grid < 1) grid = 1;
-    k_mlp_layer_f32<<<grid, 256, 0, st>>>(count, rows, X, ldx, W, b, Y, K, N, relu, ids);
+    const int vec4 = (K % 4 == 0 && ldx % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+                      (reinterpret_cast<uintptr_t>(W) & 15) == 0) ? 1 : 0;
+    k_mlp_layer_f32<<<grid, 256, 0, st>>>(count, rows, X, ldx, W, b, Y, K, N, relu, ids, vec4);
 }
 
 void launch_mlp_dot_f32(const int *count, const int *rows, const float *X, int ldx, const float *w,
