@@ -103,14 +103,28 @@ def bf16_stream_error(H, w, th, X, stream, calib_rows):
     calib = q.calibrate(calib_rows)
     out = torch.empty(w.batch, dtype=torch.float64, device="cuda")
     res = {"stream_max_err": [], "calib_max_err": [], "ratio": [], "margin": [], "band_frac": [],
-           "band_frac_at_4x_calib": [], "calib_frames": int(calib_rows.shape[0])}
-    for i in range(len(w.udfs)):
+           "band_frac_at_4x_calib": [], "calib_frames": int(calib_rows.shape[0]),
+           "split_level": {"stream_max_err": [], "calib_max_err": [], "ratio": [], "margin": [], "band_frac": []}}
+
+    def scores(i, prec):
         s = np.empty(w.n)
         with torch.cuda.stream(stream):
             for b0 in range(0, w.n, w.batch):
                 n = min(w.batch, w.n - b0)
-                q.udf_scores(i, "bf16", X[b0:b0 + n], out[:n])
+                q.udf_scores(i, prec, X[b0:b0 + n], out[:n])
                 s[b0:b0 + n] = out[:n].cpu().numpy()
+        return s
+    for i in range(len(w.udfs)):
+        # the split level (the first recheck level) on every frame, against its calibration error
+        e3 = float(np.abs(scores(i, "bf16x3") - ref[:, i]).max())
+        sl = res["split_level"]
+        c3 = float(calib[i]["max_err_tf32"])
+        sl["stream_max_err"].append(float("%.3g" % e3))
+        sl["calib_max_err"].append(float("%.3g" % c3))
+        sl["ratio"].append(round(e3 / max(c3, 1e-30), 3))
+        sl["margin"].append(float("%.3g" % calib[i]["margin_tf32"]))
+        sl["band_frac"].append(round(float((np.abs(ref[:, i] - th[i]) <= calib[i]["margin_tf32"]).mean()), 6))
+        s = scores(i, "bf16")
         err = float(np.abs(s - ref[:, i]).max())
         ce = float(calib[i]["max_err_lowp"])
         d = np.abs(ref[:, i] - th[i])
