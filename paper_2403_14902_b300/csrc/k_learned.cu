@@ -85,8 +85,8 @@ k_partition(const int *count, const int *alive, const unsigned char *order, int 
 // All groups' hidden layers of one depth in one launch: tiles are numbered
 // group by group and walked grid-stride, so uneven queues share the SMs.
 __global__ void __launch_bounds__(256) k_grouped_layer_f32(GroupedLayers g) {
-    __shared__ float As[16][68];
-    __shared__ float Ws[16][68];
+    __shared__ __align__(16) float As[2][16][68];
+    __shared__ __align__(16) float Ws[2][16][68];
     int tiles[kMaxPred], start[kMaxPred + 1];
     start[0] = 0;
     for (int i = 0; i < g.n; ++i) {

@@ -222,8 +222,8 @@ __global__ void __launch_bounds__(256) k_mq_partition(MqDev d, int r) {
 // Stacked grouped FP32 layer: tiles group by group, rows of group g at
 // off_g; depth 0 reads X rows through the queue lists.
 __global__ void __launch_bounds__(256) k_mq_layer_f32(MqLayers L) {
-    __shared__ float As[16][68];
-    __shared__ float Ws[16][68];
+    __shared__ __align__(16) float As[2][16][68];
+    __shared__ __align__(16) float Ws[2][16][68];
     int off[kMqPool + 1], start[kMqPool + 1];
     off[0] = 0;
     start[0] = 0;
