@@ -934,7 +934,9 @@ def ours(args):
     # clears the launch count; no per-launch events in the headline region (with --profile-launches:
     # per-launch events, so routed batches take the host path and their kernels are visible to ncu)
     q.profile(bool(args.profile_launches))
+    st0 = q.stats()
     secs, outs = timed(step, args.steps, stream, local)
+    st1 = q.stats()
     _, launches = q.profile_read()
     clk = clocks.stop()
     secs_max = max_over_ranks(secs, device=dev)
@@ -959,7 +961,6 @@ def ours(args):
     e2e_steps = max(1, min(args.steps, 3))
     esecs, _ = timed(hstep, e2e_steps, stream, local)
     esecs = max_over_ranks(esecs, device=dev)
-    stats = q.stats()
     q.close()
 
     # the conv kernel's roofline from one lane: the same orders (same route lag), but its
@@ -1080,8 +1081,11 @@ def ours(args):
         "kernels_one_lane": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
                                  "tflops": round(v["flops"] / max(v["total_ms"], 1e-9) / 1e9, 2)}
                              for k, v in prof.items()},
-        "recheck": {"split_level": [s["recheck_tf32"] for s in stats], "fp32": [s["recheck_fp32"] for s in stats],
-                    "fp64": [s["recheck_fp64"] for s in stats],
+        # frames each recheck level took per step (the timed steps), per predicate
+        "recheck": {"per_step": True,
+                    "split_level": [(b["recheck_tf32"] - a["recheck_tf32"]) / args.steps for a, b in zip(st0, st1)],
+                    "fp32": [(b["recheck_fp32"] - a["recheck_fp32"]) / args.steps for a, b in zip(st0, st1)],
+                    "fp64": [(b["recheck_fp64"] - a["recheck_fp64"]) / args.steps for a, b in zip(st0, st1)],
                     "calib_max_err_bf16": [round(c["max_err_lowp"], 6) for c in calib],
                     "calib_max_err_split_level": [float("%.3g" % c["max_err_tf32"]) for c in calib],
                     "calib_max_err_fp32": [float("%.3g" % c["max_err_fp32"]) for c in calib]},

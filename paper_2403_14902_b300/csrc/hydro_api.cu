@@ -972,9 +972,10 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
             const int cls = prec == PREC_BF16 ? PC_CONV_BF16 : prec == PREC_F32 ? PC_CONV_F32 : PC_CONV_F64;
             e = prof_begin(q, pc, cls, fpi, bpi, wb);
             const void *w = prec == PREC_BF16 ? (const void *)p.dWt16[l] : (const void *)p.dWt32[l];
-            launch_conv3x3_simt(prec, count, act[cur], p.dims[l], H, Wd, w, p.db[l], p.dims[l + 1], act[1 - cur],
-                                max_rows, q->sms, st, band);
+            const int nk = launch_conv3x3_simt(prec, count, act[cur], p.dims[l], H, Wd, w, p.db[l], p.dims[l + 1],
+                                               act[1 - cur], max_rows, q->sms, st, band);
             prof_end(q, e);
+            q->launches += nk - 1;
         }
         q->launches++;
         cur = 1 - cur;

@@ -331,24 +331,35 @@ template <> __device__ __forceinline__ __nv_bfloat16 st_as<__nv_bfloat16, float>
 // channels), so a tile's latency is its K loop: recheck bands of a few frames
 // take 64-pixel tiles (half the work per step, twice the CTAs; 32-pixel tiles
 // measured no faster on the CNN workload's FP32 bands).
+// KS = 3 (bands only): when *count <= split_frames, the K loop is split by kernel
+// row (taps 3j..3j+2 for split j), so a band of a few frames has three times the
+// CTAs with a third of the K loop each.  Each split writes its raw sums to plane j
+// of a partial buffer placed after the first split_frames frames of `out`
+// ([KS][split_frames][H*W][Cout] elements of T, so `out` must hold 4 x
+// split_frames frames); k_conv_splitk_sum adds the planes in order 0, 1, 2, then
+// the bias, and applies the ReLU.  Above split_frames the kernel runs unsplit.
 // Requires Cin % 16 == 0, Cout % 64 == 0, H*W % 128 == 0.
-template <int PX, typename Tin, typename Tw, typename T, typename Tout>
+template <int PX, int KS, typename Tin, typename Tw, typename T, typename Tout>
 __global__ void __launch_bounds__(256)
 k_conv3x3_simt(const int *count, const Tin *in, int Cin, int H, int Wd, const Tw *Wt, const float *bias,
-               int Cout, Tout *out) {
+               int Cout, Tout *out, int split_frames) {
+    static_assert(KS == 1 || KS == 3, "K splits: 1, or 3 (one kernel row each)");
     constexpr int RI = PX / 16;       // output pixels per thread, A elements per loader thread
     constexpr int APT = 16 / RI;      // loader threads per pixel
     __shared__ T As[16][PX + 4];
     __shared__ T Bs[16][64 + 4];
     const int M = *count;
+    const int ks = (KS > 1 && M <= split_frames) ? KS : 1;
     const int HW = H * Wd;
     const int tiles_p = HW / PX, tiles_c = Cout / 64;
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
     const int apx = t / APT, ach = (t % APT) * RI;   // A loader: pixel, channel offset
     const int bk = t >> 4, bn = (t & 15) * 4;    // B loader: k row, channel offset
-    for (long long tile = blockIdx.x; tile < (long long)M * tiles_p * tiles_c; tile += gridDim.x) {
-        const int m = (int)(tile / (tiles_p * tiles_c));
-        const int r = (int)(tile % (tiles_p * tiles_c));
+    for (long long tile = blockIdx.x; tile < (long long)M * tiles_p * tiles_c * ks; tile += gridDim.x) {
+        const int j = (int)(tile % ks);
+        const long long u = tile / ks;
+        const int m = (int)(u / (tiles_p * tiles_c));
+        const int r = (int)(u % (tiles_p * tiles_c));
         const int p0 = (r / tiles_c) * PX, co0 = (r % tiles_c) * 64;
         const Tin *fin = in + (size_t)m * HW * Cin;
         const int ap = p0 + apx, ay = ap / Wd, ax = ap % Wd;
@@ -359,10 +370,10 @@ k_conv3x3_simt(const int *count, const Tin *in, int Cin, int H, int Wd, const Tw
             for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
         // K steps (tap, 16 input channels); the next step's operands are loaded
         // into registers while this step's multiply-adds run (latency hiding)
-        const int csteps = Cin / 16, nsteps = 9 * csteps;
+        const int csteps = Cin / 16, tap0 = j * (9 / ks), nsteps = (9 / ks) * csteps;
         T ra[RI], rw[4];
         auto fetch = [&](int s) {
-            const int tap = s / csteps, ci0 = (s % csteps) * 16;
+            const int tap = tap0 + s / csteps, ci0 = (s % csteps) * 16;
             const int yy = ay + tap / 3 - 1, xx = ax + tap % 3 - 1;
             const bool inb = yy >= 0 && yy < H && xx >= 0 && xx < Wd;
             const Tin *src = fin + ((size_t)(inb ? yy : 0) * Wd + (inb ? xx : 0)) * Cin + ci0 + ach;
@@ -394,15 +405,43 @@ k_conv3x3_simt(const int *count, const Tin *in, int Cin, int H, int Wd, const Tw
             }
             __syncthreads();
         }
+        if constexpr (KS > 1) {
+            if (ks > 1) {
+                T *o = reinterpret_cast<T *>(out) + ((size_t)(j + 1) * split_frames + m) * HW * Cout +
+                       (size_t)(p0 + ty * RI) * Cout + co0 + tx * 4;
+#pragma unroll
+                for (int i = 0; i < RI; ++i)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) o[(size_t)i * Cout + e] = acc[i][e];
+                continue;
+            }
+        }
         Tout *o = out + ((size_t)m * HW + p0 + ty * RI) * Cout + co0 + tx * 4;
 #pragma unroll
         for (int i = 0; i < RI; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                T v = acc[i][j] + (T)bias[co0 + tx * 4 + j];
+            for (int e = 0; e < 4; ++e) {
+                T v = acc[i][e] + (T)bias[co0 + tx * 4 + e];
                 if (v < (T)0) v = (T)0;
-                o[(size_t)i * Cout + j] = st_as<Tout, T>(v);
+                o[(size_t)i * Cout + e] = st_as<Tout, T>(v);
             }
+    }
+}
+
+// Second half of a K-split band conv: out[m][p][co] = relu(P0 + P1 + P2 + b[co]) with the
+// planes added in that order; does nothing when *count > split_frames (the conv ran unsplit).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_conv_splitk_sum(const int *count, int HW, int Cout, const float *bias, T *out, int split_frames, int ks) {
+    const int M = *count;
+    if (M > split_frames) return;
+    const size_t plane = (size_t)split_frames * HW * Cout, n = (size_t)M * HW * Cout;
+    const T *part = out + plane;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        T v = part[i];
+        for (int j = 1; j < ks; ++j) v += part[j * plane + i];
+        v += (T)bias[i % Cout];
+        out[i] = v < (T)0 ? (T)0 : v;
     }
 }
 
@@ -593,29 +632,51 @@ void launch_conv1_split(const int *count, const int *list, const unsigned char *
         conv1_dispatch<float, float, 1, true>(count, list, frames, C0, H, Wd, W, bias, Cout, o, max_frames, sms, st);
 }
 
-void launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,
-                         const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st, bool band) {
+int launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,
+                        const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st, bool band) {
     const int px = band ? 64 : 128;
-    const long long tiles = (long long)max_frames * (H * Wd / px) * (Cout / 64);
+    // FP32 / FP64 bands of up to split_frames frames split the K loop three ways; the partial
+    // planes live in `out` behind the first split_frames frames (4 x split_frames <= max_frames)
+    const int split_frames = band && (prec == PREC_F64 || prec == PREC_F32) ? std::min(8, max_frames / 4) : 0;
+    const int ks = split_frames > 0 ? 3 : 1;
+    const long long tiles = (long long)std::max(max_frames, ks * split_frames) * (H * Wd / px) * (Cout / 64);
     int grid = tiles < grid_for(sms, 4) ? (int)tiles : grid_for(sms, 4);
     if (grid < 1) grid = 1;
     auto run = [&](auto kern, const auto *xin, const auto *w, auto *xout) {
-        kern<<<grid, 256, 0, st>>>(count, xin, Cin, H, Wd, w, bias, Cout, xout);
+        kern<<<grid, 256, 0, st>>>(count, xin, Cin, H, Wd, w, bias, Cout, xout, split_frames);
+    };
+    auto finish = [&](auto *xout) {
+        const long long n = (long long)split_frames * H * Wd * Cout;
+        const int g = (int)std::min<long long>((n + 255) / 256, grid_for(sms, 8));
+        k_conv_splitk_sum<<<g, 256, 0, st>>>(count, H * Wd, Cout, bias, xout, split_frames, ks);
+        return 2;
     };
     if (prec == PREC_F64) {
+        if (ks > 1) {
+            run(k_conv3x3_simt<64, 3, double, float, double, double>, (const double *)in, (const float *)Wt,
+                (double *)out);
+            return finish((double *)out);
+        }
         if (band)
-            run(k_conv3x3_simt<64, double, float, double, double>, (const double *)in, (const float *)Wt, (double *)out);
+            run(k_conv3x3_simt<64, 1, double, float, double, double>, (const double *)in, (const float *)Wt,
+                (double *)out);
         else
-            run(k_conv3x3_simt<128, double, float, double, double>, (const double *)in, (const float *)Wt, (double *)out);
+            run(k_conv3x3_simt<128, 1, double, float, double, double>, (const double *)in, (const float *)Wt,
+                (double *)out);
     } else if (prec == PREC_F32) {
+        if (ks > 1) {
+            run(k_conv3x3_simt<64, 3, float, float, float, float>, (const float *)in, (const float *)Wt, (float *)out);
+            return finish((float *)out);
+        }
         if (band)
-            run(k_conv3x3_simt<64, float, float, float, float>, (const float *)in, (const float *)Wt, (float *)out);
+            run(k_conv3x3_simt<64, 1, float, float, float, float>, (const float *)in, (const float *)Wt, (float *)out);
         else
-            run(k_conv3x3_simt<128, float, float, float, float>, (const float *)in, (const float *)Wt, (float *)out);
+            run(k_conv3x3_simt<128, 1, float, float, float, float>, (const float *)in, (const float *)Wt, (float *)out);
     } else {
-        run(k_conv3x3_simt<128, __nv_bfloat16, __nv_bfloat16, float, __nv_bfloat16>, (const __nv_bfloat16 *)in,
+        run(k_conv3x3_simt<128, 1, __nv_bfloat16, __nv_bfloat16, float, __nv_bfloat16>, (const __nv_bfloat16 *)in,
             (const __nv_bfloat16 *)Wt, (__nv_bfloat16 *)out);
     }
+    return 1;
 }
 
 int launch_pool_head(int prec, const int *count, void *act, int HW, int C, const float *hw, double hb,
