@@ -346,8 +346,10 @@ k_conv3x3_simt(const int *count, const Tin *in, int Cin, int H, int Wd, const Tw
     static_assert(KS == 1 || KS == 3, "K splits: 1, or 3 (one kernel row each)");
     constexpr int RI = PX / 16;       // output pixels per thread, A elements per loader thread
     constexpr int APT = 16 / RI;      // loader threads per pixel
-    __shared__ T As[16][PX + 4];
-    __shared__ T Bs[16][64 + 4];
+    // 16-byte aligned rows (PX + 4 and 68 elements): a thread's RI A values and 4 B values
+    // of a K row are contiguous and aligned, so they can be read with vector loads
+    __shared__ __align__(16) T As[16][PX + 4];
+    __shared__ __align__(16) T Bs[16][64 + 4];
     const int M = *count;
     const int ks = (KS > 1 && M <= split_frames) ? KS : 1;
     const int HW = H * Wd;

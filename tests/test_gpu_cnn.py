@@ -164,6 +164,24 @@ def test_bf16_wide_margin_rechecks_and_stays_exact(cnn4, tf32_margin):
     q.close()
 
 
+def test_fp32_level_both_band_conv_forms(cnn4):
+    """Batches of 32 with every evaluated frame sent through the split level on
+    to FP32: the FP32 bands' conv layers take the K-split form (three partial
+    planes, summed in order) for bands of up to a quarter of the batch capacity
+    (8 frames) and the unsplit form above; both occur here, and the pass set is
+    the oracle's."""
+    w = cnn4["w"]
+    q = make_query(w, cnn4["th"], batch=32, policy="rank", precision="bf16")
+    for i in range(4):
+        q.set_margins(i, 10.0, 10.0, 1e-5)
+    res = run_stream(q, cnn4["Fd"], 32)
+    check_against_oracle(res, cnn4["pm"], 32, policy="rank", costs=model_costs(w))
+    bands = [n for r in res for n in r[2]["recheck_fp32"]]
+    assert sum(bands) == sum(int(r[1].sum()) for r in res)
+    assert any(0 < n <= 8 for n in bands) and any(n > 8 for n in bands), bands
+    q.close()
+
+
 def test_fp32_wide_margin_goes_to_fp64(cnn4):
     w = cnn4["w"]
     q = make_query(w, cnn4["th"], batch=B_SMALL, policy="static", precision="fp32")
