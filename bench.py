@@ -703,8 +703,23 @@ def ours_drift6(args):
         q.calibrate(calib)
         return q
 
+    pm = stored_pass_matrix("drift6")
+    want = pm.all(axis=1) if pm is not None else None
+    box = {}
+
     def step_fn(q):
-        return lambda: n_pass_of(run_step(q, X, w.batch, mif))
+        def f():
+            box["outs"] = run_step(q, X, w.batch, mif)
+            return n_pass_of(box["outs"])
+        return f
+
+    def parity_bits(chunks):
+        """The step's whole result bitmap (per-batch or per-step words, in stream order)
+        against the oracle's stored pass matrix."""
+        if want is None:
+            return "unchecked: no stored oracle pass matrix"
+        bits = np.concatenate([H.bits_from_words(words, n) for words, n in chunks]) if chunks else np.zeros(0, bool)
+        return "exact" if bits.shape == want.shape and np.array_equal(bits, want) else "NOT EXACT"
 
     qa = make("all")
     step_fn(qa)()
@@ -728,7 +743,12 @@ def ours_drift6(args):
         secs, npass = timed(f, steps, stream, local)
         secs = max_over_ranks(secs, device=torch.device("cuda", local))
         entry = {"value": aggregate(w.n, steps, secs, ws), "ms_per_step": secs / steps * 1000.0,
-                 "pass_count": int(npass[0])}
+                 "pass_count": int(npass[0]),
+                 "parity": parity_bits([(r["words"], r["n"]) for r in box["outs"]])}
+        if want is not None and policy != "learned" and entry["parity"] == "exact":
+            # batch orders: every batch's evaluation counts under its reported order, too
+            if not check_step(box["outs"], pm, w.batch)[1]:
+                entry["parity"] = "counts differ"
         st = q.stats()
         entry["evaluations"] = sum(s["evaluated"] for s in st)
         entry["eval_flops"] = sum(s["evaluated"] * s["model_cost"] for s in st)
@@ -757,14 +777,18 @@ def ours_drift6(args):
         s.calibrate(calib)
         return s
 
-    def run_session(s, stats=None):
-        # each step: the next K batches of 4,096 (K = s.K)
+    def run_session(s, stats=None, chunks=None):
+        # each step: the next K batches of 4,096 (K = s.K); chunks receives each step's
+        # (result words, tuples) for the parity check
         pending, npass = [], 0
 
         def drain(item):
             nonlocal npass
             sid, n = item
-            for r in s.poll(sid, total=n)[1]:
+            words, per, _ = s.poll(sid, total=n)
+            if chunks is not None:
+                chunks.append((words, n))
+            for r in per:
                 if r["batch"] >= 0:
                     npass += r["n_pass"]
                     if stats is not None:
@@ -791,7 +815,11 @@ def ours_drift6(args):
                                         ("static_session_fp32", False, "fp32", DK),
                                         ("learned_session_fp32", True, "fp32", DK)]:
         s = session(learned, precision, K, "static" if name.startswith("static") else "rank")
-        f = lambda: run_session(s)  # noqa: E731
+        chunks = []
+
+        def f():
+            chunks.clear()
+            return run_session(s, chunks=chunks)
         for _ in range(args.warmup):
             f()
         s.profile(False)
@@ -801,7 +829,7 @@ def ours_drift6(args):
         secs, npass = timed(f, args.steps, stream, local)
         secs = max_over_ranks(secs, device=torch.device("cuda", local))
         entry = {"value": aggregate(w.n, args.steps, secs, ws), "ms_per_step": secs / args.steps * 1000.0,
-                 "pass_count": int(npass[0])}
+                 "pass_count": int(npass[0]), "parity": parity_bits(chunks)}
         _, entry["launches"] = s.profile_read()
         if name == "learned_session_bf16":
             entry["clocks"] = clocks.stop()
@@ -875,6 +903,9 @@ def ours_drift6(args):
         "clocks": a["clocks"],
         "baselines": {k: {"value": round(v["value"], 1), "unit": "tuples/s", "ms_per_step": round(v["ms_per_step"], 3)}
                       for k, v in results.items() if k != "learned_session_bf16"},
+        "parity": "exact" if all(v["parity"] == "exact" for v in results.values()) else
+                  next(v["parity"] for v in results.values() if v["parity"] != "exact"),
+        "parity_detail": {k: v["parity"] for k, v in results.items()},
         "eval_gflop_per_step": round(ev / 1e9, 2),
         "best_static_order": best, "profiled_selectivity": [round(x, 4) for x in sel],
         "speedup_vs_static_fp32": round(a["value"] / results["declared_static"]["value"], 3),
@@ -1483,14 +1514,18 @@ def ours_uc1(args):
         ib = [f"{v:.1f}" for v in z["sel_B"]].index(f"{sb:.1f}")
         return np.stack([A[:, ia], B[:, ib]], axis=1)
 
-    X = torch.from_numpy(D.stream_tuples(w)).cuda()
+    Xh = torch.from_numpy(D.stream_tuples(w))
+    X = Xh.cuda()
     stream = torch.cuda.Stream()
     layers = D.predicate_weights(w)
     mif = 8
     costs = np.asarray(model_costs_of(w), np.float64)
     parity = {}
 
-    def run(sa, sb, policy, pipeline, steps):
+    def run(sa, sb, policy, pipeline, steps, extra=None):
+        """One configuration's timed steps; with ``extra`` (a dict) also the launches of
+        the timed region, one profiled pass (per-launch CUDA events) and the end-to-end
+        rate from pinned host memory."""
         q = H.Query("vec", dim=w.dim, max_batch=w.batch, policy=policy, precision="fp32", max_in_flight=mif,
                     stream=stream, lanes=4, lag=3, pipeline=pipeline)
         pipeline = bool(pipeline)
@@ -1498,8 +1533,21 @@ def ours_uc1(args):
         q.add_mlp(layers[1], G["B"][f"{sb:.1f}"])
         f = lambda: run_step(q, X, w.batch, mif)  # noqa: E731
         f()
+        q.profile(False)   # resets the launch counter
         secs, outs = timed(f, steps, stream, local)
         secs = max_over_ranks(secs, device=dev)
+        if extra is not None:
+            _, extra["launches"] = q.profile_read()
+            q.profile(True)
+            f()
+            extra["prof"], _ = q.profile_read()
+            q.profile(False)
+            Xp = Xh.pin_memory()
+            bufs = [torch.empty((w.batch, w.dim), dtype=torch.float32, device=dev) for _ in range(mif)]
+            hstep = lambda: run_step_host(q, Xp, bufs, w.batch, mif, stream)  # noqa: E731
+            hstep()
+            esecs, _ = timed(hstep, 2, stream, local)
+            extra["e2e_secs"] = max_over_ranks(esecs, device=dev) / 2
         q.close()
         pm = pm_of(sa, sb)
         key = f"A{sa:.1f}_B{sb:.1f}_{policy}_{'pipe' if pipeline else 'shared'}"
@@ -1516,7 +1564,8 @@ def ours_uc1(args):
     clocks = ClockSampler(local)
     clocks.start()
     PIPE = args.pipeline
-    head = {p: run(0.6, 0.1, p, PIPE, steps) for p in ("cost", "rank", "selectivity")}
+    hx = {}
+    head = {p: run(0.6, 0.1, p, PIPE, steps, hx if p == "cost" else None) for p in ("cost", "rank", "selectivity")}
     clk = clocks.stop()
     shared = {p: run(0.6, 0.1, p, False, steps) for p in ("cost", "rank", "selectivity")}
     grid = {}
@@ -1530,6 +1579,19 @@ def ours_uc1(args):
     if rank != 0:
         return None
     value = aggregate(w.n, 1, head["cost"]["ms"] / 1000.0, ws)
+    # the FP32 layer kernel of the cost-driven pass: per-launch CUDA events; in the pipeline
+    # each position runs on half of the SMs, so its peak is that partition's FMA rate
+    roof = None
+    g = hx["prof"].get("mlp_layer_f32")
+    if g and g["total_ms"] > 0:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        part = sms // 2 // 8 * 8 if PIPE == "partitions" else sms // 2
+        peak = fp32_simt_peak_tflops() * part / sms
+        achieved = g["flops"] / (g["total_ms"] / 1000.0) / 1e12
+        roof = {"bound": "alu", "kernel": "mlp_layer_f32", "achieved": round(achieved, 2), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"FP32 FMA rate of {part} SMs x 128 lanes x 2 x max SM clock (derived)",
+                "launches": g["launches"], "avg_launch_ms": round(g["total_ms"] / max(1, g["launches"]), 4)}
     # cells where the policies pick different orders (equal orders differ only by run-to-run noise)
     diff_s = [v["cost_over_score"] for v in grid.values() if v["orders"]["cost"] != v["orders"]["rank"]]
     diff_l = [v["cost_over_selectivity"] for v in grid.values() if v["orders"]["cost"] != v["orders"]["selectivity"]]
@@ -1564,9 +1626,12 @@ def ours_uc1(args):
                          "selectivity_slowest_mean": round(float(np.mean([v["ms"]["selectivity"] for v in grid.values()])), 3),
                          "score_mean": round(float(np.mean([v["ms"]["rank"] for v in grid.values()])), 3),
                          "cost_mean": round(float(np.mean([v["ms"]["cost"] for v in grid.values()])), 3)},
-        "roofline": None, "gpu_launches": None,
+        "roofline": roof,
+        "gpu_launches": int(hx["launches"]),
         "cpu_baseline": cpu_baseline(w, G["thresholds"], n_frames=2048),
-        "e2e": None,
+        "e2e": {"value": round(aggregate(w.n, 1, hx["e2e_secs"], ws), 1), "unit": "tuples/s",
+                "h2d_bytes_per_step": int(w.n * w.dim * 4),
+                "d2h_bytes_per_step": int(((w.n + w.batch - 1) // w.batch) * (4 * ((w.batch + 31) // 32) + 8 * 2))},
     }
 
 
