@@ -156,8 +156,10 @@ typedef struct hydro_query_config {
                                 b % lanes, each lane with its own scratch, so that up to `lanes`
                                 consecutive batches run at once (batch b's order waits only for
                                 batch b - 1 - route_lag).  The batches then run on library streams
-                                that wait for the caller's stream at each submit.  Not with
-                                embeddings or the LEARNED policy */
+                                that wait for the caller's stream at each submit.  With
+                                embeddings each lane probes the shared cache into its own miss
+                                list (the cache is indexed by tuple id).  Not with the LEARNED
+                                policy */
     int32_t split_precision; /* BF16 queries with tensor-core CNN UDFs: the first recheck level,
                                 HYDRO_PREC_BF16X3 (default; 0 also selects it: split BF16 [hi | lo]
                                 operands, three BF16 passes) or HYDRO_PREC_TF32X3 (3xTF32).  On the

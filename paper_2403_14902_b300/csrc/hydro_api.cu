@@ -173,6 +173,7 @@ struct LaneBufs {
     void *batch_rows = nullptr;       // device dispatch: the batch's tuples
     unsigned char *lres = nullptr;    // device dispatch: the batch's result block
     int *lord = nullptr, *ln = nullptr;   // device dispatch: router order, batch size
+    int *miss_list = nullptr;             // stage probe of a cached embedding
 };
 
 struct hydro_query {
@@ -427,6 +428,7 @@ hydro_status alloc_scratch(hydro_query *q) {
     TRY(dalloc(q, &q->alive[0], sizeof(int) * B));
     TRY(dalloc(q, &q->alive[1], sizeof(int) * B));
     TRY(dalloc(q, &q->ints, sizeof(int) * 16));
+    if (!q->embs.empty()) TRY(dalloc(q, &q->miss_list, sizeof(int) * B));
     TRY(dalloc(q, &q->pass, B));
     TRY(dalloc(q, &q->acc, B));
     TRY(dalloc(q, &q->score32, sizeof(float) * B));
@@ -510,6 +512,7 @@ void save_lane(hydro_query *q, int l) {
     L.lres = q->lres;
     L.lord = q->lord;
     L.ln = q->ln;
+    L.miss_list = q->miss_list;
 }
 
 // Make lane l current: its scratch and its stream.
@@ -542,6 +545,7 @@ void load_lane(hydro_query *q, int l) {
     q->lres = L.lres;
     q->lord = L.lord;
     q->ln = L.ln;
+    q->miss_list = L.miss_list;
     q->st = q->lane_st[l];
     q->cur_lane = l;
 }
@@ -637,8 +641,9 @@ hydro_status finalize(hydro_query *q) {
     save_lane(q, 0);
     q->n_lanes = std::max(1, c.lanes);
     if (q->n_lanes > 1) {
-        if (!q->embs.empty() || c.policy == HYDRO_POLICY_LEARNED)
-            return fail(HYDRO_EUNSUPPORTED, "lanes need a query without embeddings and not LEARNED");
+        // embeddings: each lane probes into its own miss list; the cache itself is indexed by
+        // tuple id, and batches in flight on different lanes hold different ids
+        if (c.policy == HYDRO_POLICY_LEARNED) return fail(HYDRO_EUNSUPPORTED, "lanes need a policy other than LEARNED");
         for (int l = 1; l < q->n_lanes; ++l) {
             TRY(alloc_scratch(q));
             save_lane(q, l);
@@ -677,7 +682,6 @@ hydro_status finalize(hydro_query *q) {
     TRY(dalloc(q, &q->d_err, sizeof(unsigned int)));
     CU(cudaMemset(q->d_err, 0, sizeof(unsigned int)));
     TRY(dalloc(q, &q->vmiss, sizeof(int) * kMaxPred));
-    TRY(dalloc(q, &q->miss_list, sizeof(int) * B));
     if (c.recheck_graphs) {
         TRY(dalloc(q, &q->d_switch_n, sizeof(int) * kMaxLanes * kMaxPred * kMaxPred));
         CU(cudaMemset(q->d_switch_n, 0, sizeof(int) * kMaxLanes * kMaxPred * kMaxPred));

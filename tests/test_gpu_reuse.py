@@ -49,6 +49,23 @@ def test_reuse_parity(drift, policy, prefill):
     q.close()
 
 
+@pytest.mark.parametrize("policy", ["rank", "cost"])
+def test_reuse_parity_two_lanes(drift, policy):
+    """Two stream lanes (route lag 1) with the cached embedding and part of
+    the stream prefilled: each lane probes the cache into its own miss list;
+    every batch's order, counts and cache hits and the pass set are the
+    oracle's."""
+    w = drift["w"]
+    costs, groups, gcost = _costs(w)
+    q = make_query(w, drift["th"], batch=4096, policy=policy, reuse=True, id_capacity=N, lanes=2, lag=1)
+    pre = np.arange(2 * 4096, 4 * 4096)
+    q.cache_prefill(q.emb_id, drift["Xd"][pre[0]:pre[-1] + 1], drift["ids"][pre[0]:pre[-1] + 1])
+    res = run_stream(q, drift["Xd"], 4096, ids=drift["ids"])
+    check_against_oracle(res, drift["pm"], 4096, policy=policy, costs=costs, groups=groups, group_costs=gcost,
+                         ids=np.arange(N), prefilled=pre, lag=1)
+    q.close()
+
+
 def test_reuse_changes_order_not_result(drift):
     # prefilling the embedding for part of the stream makes its heads cheap
     # there; the router must pick a different order for those batches while
@@ -71,7 +88,8 @@ def test_reuse_changes_order_not_result(drift):
 
 def test_full_drift_stream_exact():
     """1,048,576 tuples in batches of 4,096 with the cached embedding, in the
-    bench's configuration: every tuple's result, and every batch's order,
+    bench's configuration (route lag 3, four stream lanes): every tuple's
+    result, and every batch's order,
     evaluation counts, pass counts and cache hits, equal the oracle's (its
     stored FP64 pass matrix of the whole stream and its router and cache
     simulation)."""
@@ -82,10 +100,10 @@ def test_full_drift_stream_exact():
     X = D.stream_tuples(w)
     Xd = torch.from_numpy(X).cuda()
     ids = torch.arange(w.n, dtype=torch.int64, device="cuda")
-    q = make_query(w, th, batch=w.batch, policy="rank", reuse=True, max_in_flight=8)
+    q = make_query(w, th, batch=w.batch, policy="rank", reuse=True, max_in_flight=8, lag=3, lanes=4)
     res = run_stream(q, Xd, w.batch, max_in_flight=8, ids=ids)
     costs, groups, gcost = _costs(w)
     sim = check_against_oracle(res, pm, w.batch, policy="rank", costs=costs, groups=groups, group_costs=gcost,
-                               ids=np.arange(w.n))
+                               ids=np.arange(w.n), lag=3)
     assert len({tuple(x["order"]) for x in sim}) > 1, "the drifting stream should make the router change its order"
     q.close()
