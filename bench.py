@@ -1686,8 +1686,9 @@ def ours_mlp3(args):
     parity = {}
 
     def make(policy, precision, order=None):
+        # route lag 1 on two stream lanes: batch b runs while batch b + 1 is routed and started
         q = H.Query("vec", dim=w.dim, max_batch=w.batch, policy=policy, precision=precision, max_in_flight=mif,
-                    stream=stream)
+                    stream=stream, lag=1, lanes=2)
         for i, lw in enumerate(layers):
             q.add_mlp(lw, th[i])
         if order is not None:
@@ -1759,7 +1760,8 @@ def ours_mlp3(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{name}: {w.n} x {w.dim} fp32 tuples (8-cluster Gaussian mixture), 3 MLP UDFs "
                                "256-128-1, 256-512-512-1, 256-1024-1024-1024-1, selectivities 0.5/0.2/0.8, batches "
-                               f"of {w.batch}, rank c/(1-s) routing, FP32 + FP64 recheck",
+                               f"of {w.batch}, rank c/(1-s) routing (route lag 1, two stream lanes), FP32 + FP64 "
+                               "recheck",
                    "global_batch": w.n, "routing_batch": w.batch, "parallelism": f"replicas{ws}",
                    "l2": "inputs 4 MiB fit in L2: a 256 MB write flushes L2 before every timed step"},
         "parity": ("unchecked: no stored oracle pass matrix" if pm is None else
