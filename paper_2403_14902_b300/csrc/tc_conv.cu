@@ -67,7 +67,9 @@ k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
              const float *__restrict__ head_w, float *partials, unsigned int *err) {
     using C = TcCfg<CC, N, S, MODE, MT>;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // aligned to 1 KB by pointer arithmetic on the shared array itself, so that the compiler
+    // keeps every access through it in the shared state space (no generic loads or stores)
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * C::STAGE);
     uint64_t *empty = full + S;
     uint64_t *tfull = empty + S;
@@ -413,7 +415,9 @@ k_conv3x3_tcw(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
               const float *__restrict__ head_w, float *partials, unsigned int *err) {
     using C = TcWCfg<CIN, S>;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *wres = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // aligned to 1 KB by pointer arithmetic on the shared array itself, so that the compiler
+    // keeps every access through it in the shared state space (no generic loads or stores)
+    unsigned char *wres = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char *smem = wres + C::RES_BYTES;   // window stages
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * kWStage);
     uint64_t *empty = full + S;

@@ -179,7 +179,9 @@ __global__ void __launch_bounds__(kC1Threads) k_conv1_tc(const __grid_constant__
     constexpr int K = 9 * C0;
     extern __shared__ __align__(16) unsigned char dsm_raw[];
     // the swizzle pattern repeats every 512 bytes of shared address
-    unsigned char *dsm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+    // aligned to 1 KB by pointer arithmetic on the shared array itself, so that the compiler
+    // keeps every access through it in the shared state space (no generic loads or stores)
+    unsigned char *dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
     unsigned char *sX = dsm;                        // [3][128 x 64 B]: A tile, then the output tile
     unsigned char *sB = dsm + 3 * 8192;             // [32 x 64 B]
     unsigned char *sWin = dsm + 3 * 8192 + 2048;    // [2][C0 x CS]

@@ -106,7 +106,9 @@ constexpr int kEpiWarps = 8;
 template <bool HAS_FP8, bool DYN>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_grouped_bf16_tc(const __grid_constant__ TcLaunch L) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // aligned to 1 KB by pointer arithmetic on the shared array itself, so that the compiler
+    // keeps every access through it in the shared state space (no generic loads or stores)
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int S = L.S;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * L.stage_bytes);
     uint64_t *empty = full + kMaxStages;
