@@ -59,8 +59,8 @@ def load_peaks():
 # DRAM traffic of the tensor-core BF16 conv, one 1,024-frame launch of each layer shape of the CNN
 # workload (ncu dram__bytes_read.sum + dram__bytes_write.sum over `--workload conv_bf16`, MB),
 # against the launch's algorithmic bytes (input + output activations, MB).
-CONV_TC_TRAFFIC_MB = {"32->64": (749.9, 805.3), "64->64": (1025.4, 1073.7), "64->128": (1555.0, 1610.6),
-                      "128->128": (2100.2, 2147.5)}
+CONV_TC_TRAFFIC_MB = {"32->64": (746.9, 805.3), "64->64": (1022.6, 1073.7), "64->128": (1555.6, 1610.6),
+                      "128->128": (2099.8, 2147.5)}
 
 
 def conv_traffic_ratio():
