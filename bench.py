@@ -1847,6 +1847,7 @@ def ours_routing(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": f"routing: drift5 prefix of {n} x {w.dim} fp32 tuples, five MLP predicates, batches "
                                    f"of {w.batch}; a BF16 query and an FP32 query with a cached shared embedding"},
+            "scope": "kernel workload: the same kernels as the query path, timed and profiled alone (the profiles' commands); their parity is in the GPU tests, the query lines carry e2e and baselines",
             "queries": out}
 
 
@@ -1887,6 +1888,7 @@ def ours_gemm_bf16(args):
     achieved = g["flops"] / (g["total_ms"] / 1000.0) / 1e12
     return {
         "metric": "tensor-core MLP GEMM throughput (BF16, FP32 accumulate)", "value": round(achieved, 2),
+        "scope": "kernel workload: the same kernels as the query path, timed and profiled alone (the profiles' commands); their parity is in the GPU tests, the query lines carry e2e and baselines",
         "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(secs / args.steps * 1000.0, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
@@ -1942,6 +1944,7 @@ def ours_conv_bf16(args):
     achieved = g["flops"] / (g["total_ms"] / 1000.0) / 1e12
     return {
         "metric": "tensor-core conv3x3 throughput (BF16, FP32 accumulate)", "value": round(achieved, 2),
+        "scope": "kernel workload: the same kernels as the query path, timed and profiled alone (the profiles' commands); their parity is in the GPU tests, the query lines carry e2e and baselines",
         "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(secs / args.steps * 1000.0, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
