@@ -952,7 +952,7 @@ hydro_status run_udf(hydro_query *q, const Pred &p, int prec, const int *count, 
         if (rs != HYDRO_OK) return fail(rs, "tensor-core first conv layer launch failed");
     } else {
         launch_conv1(prec, count, list, frames, c.channels, H, Wd, p.dW[0], p.db[0], p.dims[1], act[0], max_rows,
-                     q->sms, st);
+                     q->sms, st, band);
     }
     prof_end(q, e);
     q->launches++;

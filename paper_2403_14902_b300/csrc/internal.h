@@ -103,9 +103,10 @@ void launch_mlp_band_f32(const int *band_count, const int *band_tuple, const flo
 void launch_mlp_band_f64(const int *band_count, const int *band_tuple, const float *X, int ldx,
                          const MlpDev &mlp, double *score_out, int sms, cudaStream_t st);
 cudaError_t mlp_band_smem_setup(int max_width);
+// band: a recheck band of a few frames (one pixel per thread instead of four)
 void launch_conv1(int prec, const int *count, const int *list, const unsigned char *frames, int C0, int H,
                   int Wd, const float *W, const float *bias, int Cout, void *out, int max_frames, int sms,
-                  cudaStream_t st);
+                  cudaStream_t st, bool band = false);
 // First conv layer (FP32) in a split form [hi(Cout) | lo(Cout)] per pixel:
 // TF32 planes in fp32 (3xTF32 level), or with bf16_planes BF16 planes
 // (split-BF16 level).

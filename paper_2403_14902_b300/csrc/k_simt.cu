@@ -592,8 +592,9 @@ static void conv1_dispatch(const int *count, const int *list, const unsigned cha
 
 void launch_conv1(int prec, const int *count, const int *list, const unsigned char *frames, int C0, int H,
                   int Wd, const float *W, const float *bias, int Cout, void *out, int max_frames, int sms,
-                  cudaStream_t st) {
-    const bool px4 = Wd % 4 == 0;
+                  cudaStream_t st, bool band) {
+    // a recheck band (often one frame) takes one pixel per thread: four times the threads
+    const bool px4 = Wd % 4 == 0 && !band;
     if (prec == PREC_F64)
         conv1_dispatch<double, double, 1>(count, list, frames, C0, H, Wd, W, bias, Cout, (double *)out, max_frames,
                                           sms, st);
@@ -618,9 +619,12 @@ void launch_conv1_split(const int *count, const int *list, const unsigned char *
                         const float *W, const float *bias, int Cout, void *out, int max_frames, int sms,
                         cudaStream_t st, bool bf16_planes) {
     if (bf16_planes) {
+        // the split-BF16 level runs on recheck bands of a few dozen frames: two pixels per
+        // thread give twice the threads of four, with the same weight reads per multiply-add
+        // pair
         __nv_bfloat16 *o = (__nv_bfloat16 *)out;
-        if (Wd % 4 == 0)
-            conv1_dispatch<float, __nv_bfloat16, 4, true>(count, list, frames, C0, H, Wd, W, bias, Cout, o, max_frames,
+        if (Wd % 2 == 0)
+            conv1_dispatch<float, __nv_bfloat16, 2, true>(count, list, frames, C0, H, Wd, W, bias, Cout, o, max_frames,
                                                           sms, st);
         else
             conv1_dispatch<float, __nv_bfloat16, 1, true>(count, list, frames, C0, H, Wd, W, bias, Cout, o, max_frames,
