@@ -118,8 +118,9 @@ void launch_conv1_split(const int *count, const int *list, const unsigned char *
 int launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,
                         const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st,
                         bool band = false);
-// Returns the number of kernels launched.  The FP32 / FP64 forms overwrite the frame's first
-// pixel of `act` with its channel sums.
+// Returns the number of kernels launched.  The FP32 / FP64 forms overwrite the first pixel of
+// each of the frame's pixel ranges (16 ranges when H*W is a multiple of 512) in `act` with the
+// range's channel sums.
 int launch_pool_head(int prec, const int *count, void *act, int HW, int C, const float *hw, double hb,
                      void *score, int max_frames, int sms, cudaStream_t st);
 

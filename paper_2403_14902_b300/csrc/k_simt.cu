@@ -451,23 +451,27 @@ k_conv_splitk_sum(const int *count, int HW, int Cout, const float *bias, T *out,
 // One block per frame; fixed-order partial sums (deterministic).
 constexpr int kPoolThreads = 1024;   // per frame: C channels x (1024 / C) pixel groups
 
-// The FP32 / FP64 recheck levels pool a band of a few frames: one block per frame reads its
-// 1-2 MB with too few loads in flight, so these levels split each frame by 32-channel group.
-// k_pool_sum: per (frame, channel group), 32 channels x 32 pixel groups sum in a fixed order
-// and leave the channel sums in place of the frame's first pixel (only this block reads those
-// channels of the frame); k_head_dot: one warp per frame, hb + sum_c hw[c] * sum_c / HW with a
-// fixed butterfly order.  Both deterministic; C a multiple of 32.
+// The FP32 / FP64 recheck levels pool a band of a few frames (often one): one block per frame
+// reads its 1-2 MB with too few loads in flight, so these levels split each frame by 32-channel
+// group and by PS pixel ranges of HW / PS pixels.
+// k_pool_sum: per (frame, channel group, pixel range j), 32 channels x 32 pixel groups sum in a
+// fixed order and leave the range's channel sums in place of the range's first pixel j * HW / PS
+// (only this block reads those channels of that range); k_head_dot: one warp per frame,
+// hb + sum_c hw[c] * (sum over j = 0 .. PS-1 in order of the range sums) / HW with a fixed
+// butterfly order.  Both deterministic; C a multiple of 32, HW a multiple of 32 * PS.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_pool_sum(const int *count, T *act, int HW, int C) {
+__global__ void __launch_bounds__(1024) k_pool_sum(const int *count, T *act, int HW, int C, int ps) {
     __shared__ T part[32][33];
-    const int M = *count, G = C / 32;
+    const int M = *count, G = C / 32, R = HW / ps;
     const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
-    for (long long u = blockIdx.x; u < (long long)M * G; u += gridDim.x) {
-        const int m = (int)(u / G), cg = (int)(u % G);
-        T *a = act + (size_t)m * HW * C + cg * 32 + c;
+    for (long long u = blockIdx.x; u < (long long)M * G * ps; u += gridDim.x) {
+        const int j = (int)(u % ps);
+        const long long v = u / ps;
+        const int m = (int)(v / G), cg = (int)(v % G);
+        T *a = act + ((size_t)m * HW + (size_t)j * R) * C + cg * 32 + c;
         T s = (T)0;
 #pragma unroll 8
-        for (int p = g; p < HW; p += 32) s += a[(size_t)p * C];
+        for (int p = g; p < R; p += 32) s += a[(size_t)p * C];
         part[g][c] = s;
         __syncthreads();
         if (g == 0) {
@@ -480,14 +484,29 @@ __global__ void __launch_bounds__(1024) k_pool_sum(const int *count, T *act, int
 }
 
 template <typename T, typename S>
-__global__ void k_head_dot(const int *count, const T *act, int HW, int C, const float *hw, double hb, S *score) {
+__global__ void k_head_dot(const int *count, const T *act, int HW, int C, int ps, const float *hw, double hb,
+                           S *score) {
     const int M = *count;
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
+    const size_t range = (size_t)(HW / ps) * C;
     for (int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; m < M; m += warps) {
         const T *pooled = act + (size_t)m * HW * C;
         T r = (T)0;
-        for (int c = lane; c < C; c += 32) r += (T)hw[c] * (pooled[c] / (T)HW);
+        for (int c = lane; c < C; c += 32) {
+            // the range sums' loads issue together; the adds stay in order j = 0 .. ps-1
+            T v[16];
+            T sc = (T)0;
+            for (int j0 = 0; j0 < ps; j0 += 16) {
+                const int nj = ps - j0 < 16 ? ps - j0 : 16;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = j < nj ? pooled[(j0 + j) * range + c] : (T)0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (j < nj) sc += v[j];
+            }
+            r += (T)hw[c] * (sc / (T)HW);
+        }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) r += __shfl_xor_sync(0xffffffffu, r, d);
         if (lane == 0) score[m] = (S)((T)hb + r);
@@ -690,17 +709,20 @@ int launch_pool_head(int prec, const int *count, void *act, int HW, int C, const
     int grid = max_frames < grid_for(sms, 2) ? max_frames : grid_for(sms, 2);
     if (grid < 1) grid = 1;
     if ((prec == PREC_F64 || prec == PREC_F32) && C % 32 == 0) {
-        const long long units = (long long)max_frames * (C / 32);
+        const int ps = HW % (32 * 16) == 0 ? 16 : 1;   // pixel ranges per (frame, channel group)
+        const long long units = (long long)max_frames * (C / 32) * ps;
         const int g1 = (int)(units < grid_for(sms, 2) ? (units < 1 ? 1 : units) : grid_for(sms, 2));
         int g2 = (max_frames + 7) / 8;
         if (g2 > grid_for(sms, 4)) g2 = grid_for(sms, 4);
         if (g2 < 1) g2 = 1;
         if (prec == PREC_F64) {
-            k_pool_sum<double><<<g1, 1024, 0, st>>>(count, (double *)act, HW, C);
-            k_head_dot<double, double><<<g2, 256, 0, st>>>(count, (const double *)act, HW, C, hw, hb, (double *)score);
+            k_pool_sum<double><<<g1, 1024, 0, st>>>(count, (double *)act, HW, C, ps);
+            k_head_dot<double, double><<<g2, 256, 0, st>>>(count, (const double *)act, HW, C, ps, hw, hb,
+                                                           (double *)score);
         } else {
-            k_pool_sum<float><<<g1, 1024, 0, st>>>(count, (float *)act, HW, C);
-            k_head_dot<float, float><<<g2, 256, 0, st>>>(count, (const float *)act, HW, C, hw, hb, (float *)score);
+            k_pool_sum<float><<<g1, 1024, 0, st>>>(count, (float *)act, HW, C, ps);
+            k_head_dot<float, float><<<g2, 256, 0, st>>>(count, (const float *)act, HW, C, ps, hw, hb,
+                                                         (float *)score);
         }
         return 2;
     }
