@@ -331,19 +331,20 @@ template <> __device__ __forceinline__ __nv_bfloat16 st_as<__nv_bfloat16, float>
 // channels), so a tile's latency is its K loop: recheck bands of a few frames
 // take 64-pixel tiles (half the work per step, twice the CTAs; 32-pixel tiles
 // measured no faster on the CNN workload's FP32 bands).
-// KS = 3 (bands only): when *count <= split_frames, the K loop is split by kernel
-// row (taps 3j..3j+2 for split j), so a band of a few frames has three times the
-// CTAs with a third of the K loop each.  Each split writes its raw sums to plane j
-// of a partial buffer placed after the first split_frames frames of `out`
-// ([KS][split_frames][H*W][Cout] elements of T, so `out` must hold 4 x
-// split_frames frames); k_conv_splitk_sum adds the planes in order 0, 1, 2, then
-// the bias, and applies the ReLU.  Above split_frames the kernel runs unsplit.
+// KS = 3 or 9 (bands only): when *count <= split_frames, the K loop is split by
+// kernel row (KS = 3: taps 3j..3j+2 for split j) or by tap (KS = 9), so a band of a
+// few frames has KS times the CTAs with 1/KS of the K loop each.  Each split writes
+// its raw sums to plane j of a partial buffer placed after the first split_frames
+// frames of `out` ([KS][split_frames][H*W][Cout] elements of T, so `out` must hold
+// (KS + 1) x split_frames frames); k_conv_splitk_sum adds the planes in order 0, 1,
+// ..., then the bias, and applies the ReLU.  Above split_frames the kernel runs
+// unsplit.
 // Requires Cin % 16 == 0, Cout % 64 == 0, H*W % 128 == 0.
 template <int PX, int KS, typename Tin, typename Tw, typename T, typename Tout>
 __global__ void __launch_bounds__(256)
 k_conv3x3_simt(const int *count, const Tin *in, int Cin, int H, int Wd, const Tw *Wt, const float *bias,
                int Cout, Tout *out, int split_frames) {
-    static_assert(KS == 1 || KS == 3, "K splits: 1, or 3 (one kernel row each)");
+    static_assert(KS == 1 || KS == 3 || KS == 9, "K splits: 1, 3 (one kernel row each) or 9 (one tap each)");
     constexpr int RI = PX / 16;       // output pixels per thread, A elements per loader thread
     constexpr int APT = 16 / RI;      // loader threads per pixel
     // 16-byte aligned rows (PX + 4 and 68 elements): a thread's RI A values and 4 B values
@@ -430,20 +431,45 @@ k_conv3x3_simt(const int *count, const Tin *in, int Cin, int H, int Wd, const Tw
     }
 }
 
-// Second half of a K-split band conv: out[m][p][co] = relu(P0 + P1 + P2 + b[co]) with the
-// planes added in that order; does nothing when *count > split_frames (the conv ran unsplit).
+// Second half of a K-split band conv: out[m][p][co] = relu(P0 + P1 + ... + b[co]) with the
+// planes added in order 0, 1, ..., ks-1; does nothing when *count > split_frames (the conv ran
+// unsplit).  Each thread takes 16 bytes (4 floats or 2 doubles) of every plane with one load.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using V = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using V = double2; static constexpr int N = 2; };
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_conv_splitk_sum(const int *count, int HW, int Cout, const float *bias, T *out, int split_frames, int ks) {
+    using V = typename Vec16<T>::V;
+    constexpr int N = Vec16<T>::N;
     const int M = *count;
     if (M > split_frames) return;
-    const size_t plane = (size_t)split_frames * HW * Cout, n = (size_t)M * HW * Cout;
+    const size_t plane = (size_t)split_frames * HW * Cout, nv = (size_t)M * HW * Cout / N;
     const T *part = out + plane;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        T v = part[i];
-        for (int j = 1; j < ks; ++j) v += part[j * plane + i];
-        v += (T)bias[i % Cout];
-        out[i] = v < (T)0 ? (T)0 : v;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (size_t)gridDim.x * blockDim.x) {
+        T acc[N];
+        {
+            const V v = reinterpret_cast<const V *>(part)[i];
+            const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+            for (int k = 0; k < N; ++k) acc[k] = e[k];
+        }
+        for (int j = 1; j < ks; ++j) {
+            const V v = reinterpret_cast<const V *>(part + j * plane)[i];
+            const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+            for (int k = 0; k < N; ++k) acc[k] += e[k];
+        }
+        V o;
+        T *oe = reinterpret_cast<T *>(&o);
+        const int co = (int)((i * N) % Cout);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const T v = acc[k] + (T)bias[co + k];
+            oe[k] = v < (T)0 ? (T)0 : v;
+        }
+        reinterpret_cast<V *>(out)[i] = o;
     }
 }
 
@@ -660,10 +686,13 @@ void launch_conv1_split(const int *count, const int *list, const unsigned char *
 int launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,
                         const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st, bool band) {
     const int px = band ? 64 : 128;
-    // FP32 / FP64 bands of up to split_frames frames split the K loop three ways; the partial
-    // planes live in `out` behind the first split_frames frames (4 x split_frames <= max_frames)
-    const int split_frames = band && (prec == PREC_F64 || prec == PREC_F32) ? std::min(8, max_frames / 4) : 0;
-    const int ks = split_frames > 0 ? 3 : 1;
+    // FP32 / FP64 bands of up to split_frames frames split the K loop; the partial planes live
+    // in `out` behind the first split_frames frames ((ks + 1) x split_frames <= max_frames)
+    // (FP32: nine splits, one tap each; FP64: three)
+    const int ks_want = prec == PREC_F32 ? 9 : 3;
+    const int split_frames =
+        band && (prec == PREC_F64 || prec == PREC_F32) ? std::min(8, max_frames / (ks_want + 1)) : 0;
+    const int ks = split_frames > 0 ? ks_want : 1;
     const long long tiles = (long long)std::max(max_frames, ks * split_frames) * (H * Wd / px) * (Cout / 64);
     int grid = tiles < grid_for(sms, 4) ? (int)tiles : grid_for(sms, 4);
     if (grid < 1) grid = 1;
@@ -671,7 +700,7 @@ int launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int
         kern<<<grid, 256, 0, st>>>(count, xin, Cin, H, Wd, w, bias, Cout, xout, split_frames);
     };
     auto finish = [&](auto *xout) {
-        const long long n = (long long)split_frames * H * Wd * Cout;
+        const long long n = (long long)split_frames * H * Wd * Cout / 4;   // 16-byte vectors of floats
         const int g = (int)std::min<long long>((n + 255) / 256, grid_for(sms, 8));
         k_conv_splitk_sum<<<g, 256, 0, st>>>(count, H * Wd, Cout, bias, xout, split_frames, ks);
         return 2;
@@ -690,7 +719,7 @@ int launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int
                 (double *)out);
     } else if (prec == PREC_F32) {
         if (ks > 1) {
-            run(k_conv3x3_simt<64, 3, float, float, float, float>, (const float *)in, (const float *)Wt, (float *)out);
+            run(k_conv3x3_simt<64, 9, float, float, float, float>, (const float *)in, (const float *)Wt, (float *)out);
             return finish((float *)out);
         }
         if (band)

@@ -166,10 +166,10 @@ def test_bf16_wide_margin_rechecks_and_stays_exact(cnn4, tf32_margin):
 
 def test_fp32_level_both_band_conv_forms(cnn4):
     """Batches of 32 with every evaluated frame sent through the split level on
-    to FP32: the FP32 bands' conv layers take the K-split form (three partial
-    planes, summed in order) for bands of up to a quarter of the batch capacity
-    (8 frames) and the unsplit form above; both occur here, and the pass set is
-    the oracle's."""
+    to FP32: the FP32 bands' conv layers take the K-split form (nine partial
+    planes, one per tap, summed in order) for bands of up to a tenth of the
+    batch capacity (3 frames here) and the unsplit form above; both occur here
+    (bands of 32, 10, 8, 3 and 1 frames), and the pass set is the oracle's."""
     w = cnn4["w"]
     q = make_query(w, cnn4["th"], batch=32, policy="rank", precision="bf16")
     for i in range(4):
@@ -178,7 +178,8 @@ def test_fp32_level_both_band_conv_forms(cnn4):
     check_against_oracle(res, cnn4["pm"], 32, policy="rank", costs=model_costs(w))
     bands = [n for r in res for n in r[2]["recheck_fp32"]]
     assert sum(bands) == sum(int(r[1].sum()) for r in res)
-    assert any(0 < n <= 8 for n in bands) and any(n > 8 for n in bands), bands
+    split_frames = min(8, 32 // 10)
+    assert any(0 < n <= split_frames for n in bands) and any(n > split_frames for n in bands), bands
     q.close()
 
 
