@@ -183,6 +183,35 @@ def test_fp32_level_both_band_conv_forms(cnn4):
     q.close()
 
 
+@pytest.mark.parametrize("precision,margins", [("fp32", (0.02, 5e-3, 10.0)), ("bf16", (10.0, 10.0, 1e-5))])
+def test_other_frame_size(cnn4, precision, margins):
+    """Frames of 3 x 16 x 24 with the workload's four CNN UDFs: H*W = 384 is a
+    multiple of 128 but not of 512 (the recheck levels pool each frame as one
+    pixel range) and the width is not the tensor-core conv's 64, so the layers
+    after the first run on CUDA cores; the first layer's tensor-core kernel
+    takes tiles spanning several rows.  Margins send every evaluated frame
+    through every recheck level; pass set and counts exact."""
+    import torch
+    import paper_2403_14902_b300 as H
+    w = cnn4["w"]
+    rng = np.random.default_rng(11)
+    F = rng.integers(0, 48, size=(40, 3, 16, 24), dtype=np.uint8)
+    weights = D.predicate_weights(w)
+    S = O.udf_scores("frame", F, weights)
+    th = [float(np.median(S[:, i])) for i in range(S.shape[1])]
+    pm = O.pass_matrix(S, th)
+    q = H.Query("frame", frame=(3, 16, 24), max_batch=16, policy="static", precision=precision)
+    for i, u in enumerate(weights):
+        q.add_cnn(u, th[i])
+        q.set_margins(i, *margins)
+    res = run_stream(q, torch.from_numpy(F).cuda(), 16)
+    check_against_oracle(res, pm, 16, policy="static", costs=model_costs(w))
+    evaluated = sum(int(r[1].sum()) for r in res)
+    level = "recheck_fp64" if precision == "fp32" else "recheck_fp32"
+    assert sum(sum(r[2][level]) for r in res) == evaluated
+    q.close()
+
+
 def test_fp32_wide_margin_goes_to_fp64(cnn4):
     w = cnn4["w"]
     q = make_query(w, cnn4["th"], batch=B_SMALL, policy="static", precision="fp32")
