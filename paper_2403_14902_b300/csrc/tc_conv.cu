@@ -579,7 +579,7 @@ k_conv3x3_tcw(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
             for (int sub = 0; sub < kWMT; ++sub) {
                 const int q = q0 + 128 * sub + row;
-                const int y = q / kWP, x = q - (q / kWP) * kWP;
+                const int x = q - (q / kWP) * kWP;
                 const bool valid = q < Q && x < 64;
                 uint32_t r[32];
                 tmem_ld32(tmem_base + ((uint32_t)(qtr * 32) << 16) + (uint32_t)((buf * kWMT + sub) * 64 + ch * 32), r);
