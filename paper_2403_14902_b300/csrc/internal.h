@@ -113,8 +113,9 @@ void launch_conv1(int prec, const int *count, const int *list, const unsigned ch
 void launch_conv1_split(const int *count, const int *list, const unsigned char *frames, int C0, int H, int Wd,
                         const float *W, const float *bias, int Cout, void *out, int max_frames, int sms,
                         cudaStream_t st, bool bf16_planes = false);
-// Returns the number of kernels launched (2 for an FP32 / FP64 band with the K-split form, whose
-// partial sums use `out` beyond its first max_frames / 4 frames as scratch).
+// Returns the number of kernels launched (2 for an FP32 / FP64 band with the K-split form: the
+// FP32 form's nine and the FP64 form's three partial planes use the whole of `out`, up to
+// max_frames frames, as scratch, behind its first max_frames / 10 (FP64: / 4) frames).
 int launch_conv3x3_simt(int prec, const int *count, const void *in, int Cin, int H, int Wd, const void *Wt,
                         const float *bias, int Cout, void *out, int max_frames, int sms, cudaStream_t st,
                         bool band = false);
