@@ -53,7 +53,7 @@ typedef enum hydro_status {
     HYDRO_ESTATE = 6,       /* the call is not valid in the query's current state */
     HYDRO_EDEVICE = 7,      /* a kernel reported an error through the error word */
     HYDRO_ENOTFOUND = 8,    /* unknown or already-polled batch id */
-    HYDRO_EUNSUPPORTED = 9  /* valid request this build does not implement */
+    HYDRO_EUNSUPPORTED = 9  /* valid request the library does not implement */
 } hydro_status;
 
 /* Tuple layouts. */
